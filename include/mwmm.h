@@ -1,0 +1,188 @@
+/*
+ * mwmm.h -- C ABI of libmwmm: the multiword modular matrix product
+ *           C = A B mod p for primes p < 2^52, on one B300 GPU (sm_103a).
+ *
+ * Method: Berthomieu, Graillat, Lesnoff, Mary, "Multiword matrix
+ * multiplication over large finite fields in floating-point arithmetic".
+ * A and B are split into words, A = sum_i alpha^i A_i and
+ * B = sum_j beta^j B_j (Alg. 4), the u*v word products A_i B_j are
+ * accumulated exactly in K-chunks that no partial sum can overflow
+ * (Alg. 3, Prop. 2.3, Prop. 3.3), each chunk is reduced mod p (Alg. 1), and
+ * the products are recombined with alpha^i beta^j mod p (Alg. 2, Alg. 5).
+ *
+ * Two forms compute the same, unique result (every output in [0, p)):
+ *
+ *   MWMM_FORM_FP64  the paper's method as stated: FP64 words from Alg. 4
+ *                   with alpha = ceil(p^(1/u)), FP64 (DFMA) accumulation with
+ *                   an Alg. 1 reduction every lambda k-steps (lambda from
+ *                   Prop. 3.3, or Sec. 2.2 for (u,v) = (1,1)), and the
+ *                   Alg. 2 scaling by gamma_ij = alpha^i beta^j mod p fused
+ *                   into the epilogue (the workspace variant of Sec. 3.2).
+ *
+ *   MWMM_FORM_INT8  the narrower-word form of the paper's second
+ *                   perspective (Sec. 6): words are balanced base-2^8 digits
+ *                   in [-128, 127] of the signed representative of each
+ *                   entry (so alpha = beta = 256), multiplied on the tcgen05
+ *                   tensor pipe.  On sm_103a the tensor pipe has no INT8
+ *                   kind, so the INT8 digits are carried exactly in bf16 and
+ *                   accumulated in FP32 tensor memory, which is exact while
+ *                   |partial sum| <= 2^24: a chunk holds at most 1024 digit
+ *                   products (2^24 / 2^14).  Chunks are drained into exact
+ *                   INT32 sums S_s = sum_{i+j=s} A_i B_j, K-chunked so that
+ *                   |S_s| < 2^31, and C = sum_s 256^s S_s mod p is
+ *                   recombined with exact 64-bit integer arithmetic.
+ *
+ * Conventions for every entry point:
+ *   - Matrices are row-major uint64 with a leading dimension (in elements)
+ *     >= the row length.  A is m x k, B is k x n, C is m x n.
+ *   - Entries of A and B must lie in [0, p) (the paper's inputs are in F_p);
+ *     with plan option `validate` an entry >= p is reported as
+ *     MWMM_ERR_RANGE, otherwise the result is unspecified.
+ *   - C must not overlap A, B or the workspace.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Device-pointer calls are asynchronous on that stream; their
+ *     device-side errors (range violation, expired bounded wait) are
+ *     reported by mwmm_plan_check(), which synchronises the stream.
+ *   - Every call returns a status; nothing exits, traps or prints.
+ *   - A plan is not thread-safe: calls on one plan must be serialised and
+ *     the plan's own workspace is shared by its calls on one stream.
+ */
+#ifndef MWMM_H
+#define MWMM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    MWMM_OK = 0,
+    MWMM_ERR_ARG = 1,         /* null pointer, bad size or leading dimension */
+    MWMM_ERR_PRIME = 2,       /* p even, p < 5 or p >= 2^52 */
+    MWMM_ERR_BOUND = 3,       /* no block size >= 1 for the requested (u,v) */
+    MWMM_ERR_RANGE = 4,       /* an input entry >= p (validation on) */
+    MWMM_ERR_NOMEM = 5,       /* device allocation failed */
+    MWMM_ERR_BUDGET = 6,      /* request larger than the memory budget */
+    MWMM_ERR_CUDA = 7,        /* a CUDA runtime call failed */
+    MWMM_ERR_TIMEOUT = 8,     /* a bounded device-side wait expired */
+    MWMM_ERR_BUSY = 9,        /* queue full / workspace too small */
+    MWMM_ERR_UNSUPPORTED = 10 /* form not available on this device */
+} mwmm_status;
+
+typedef enum {
+    MWMM_FORM_AUTO = 0, /* INT8 form (the faster form on B300 at every bitsize) */
+    MWMM_FORM_FP64 = 1,
+    MWMM_FORM_INT8 = 2
+} mwmm_form;
+
+typedef struct mwmm_plan_s *mwmm_plan_t;
+
+/* Optional plan settings; pass NULL for defaults (all fields zero). */
+typedef struct {
+    int64_t lambda;   /* FP64 form: block size to use, 1..lambda_max (0: lambda_max) */
+    int32_t validate; /* nonzero: check 0 <= entry < p on the device */
+    int32_t tc_chunk; /* INT8 form: digit products per FP32 chunk, a multiple of
+                         64 in [64, 1024] (0: 1024) */
+    int64_t kc;       /* INT8 form: k-range of one INT32 sum, a multiple of 64
+                         (0: the largest allowed by |S_s| < 2^31) */
+    int32_t reserved[8];
+} mwmm_plan_opts;
+
+/* What a plan decided (mwmm_plan_info). */
+typedef struct {
+    int64_t m, n, k;
+    uint64_t p;
+    int32_t form;           /* MWMM_FORM_FP64 or MWMM_FORM_INT8 */
+    int32_t u, v;           /* words of A and of B */
+    uint64_t alpha, beta;   /* word radices: ceil(p^(1/u)), ceil(p^(1/v)); 256 for INT8 */
+    int64_t lambda;         /* FP64: k-steps between Alg. 1 reductions */
+    int64_t lambda_max;     /* FP64: largest block size allowed by Prop. 3.3 */
+    int64_t tc_chunk;       /* INT8: digit products per FP32 tensor-memory chunk */
+    int64_t kc;             /* INT8: k-range of one INT32 diagonal sum */
+    int32_t nkc;            /* INT8: number of k-ranges, ceil(k / kc) */
+    int32_t nsums;          /* INT8: number of diagonal sums u + v - 1 */
+    double q;               /* fl(1/p) */
+    /* Workspace layout (byte offsets into the workspace).
+     * Words of side X (A: rows = m; B: rows = n, i.e. B is stored transposed,
+     * K-contiguous) are stored as 128-byte row chunks:
+     *   chunk(word w, k-block kb, row r) at X_off + ((w * nkb + kb) * X_rows + r) * 128
+     * where nkb = ceil(k / kb_elems) and X_rows = A_rows or B_rows (padded).
+     * Inside a chunk the 16-byte granule g (elements g*E .. g*E+E-1 of the
+     * k-block, E = 16 / element size) is stored at granule position
+     * g ^ (r mod 8).  Element type: double (FP64 form, kb_elems = 16) or
+     * bf16 holding an integer digit (INT8 form, kb_elems = 64).  Padding is 0.
+     * INT8 form only: S (int32) at S_off, laid out [nsums][nkc][A_rows][B_rows]. */
+    int64_t kb_elems, nkb, A_rows, B_rows;
+    uint64_t A_off, B_off, S_off;
+    uint64_t workspace_bytes;
+} mwmm_plan_desc;
+
+/* Plan a product of an m x k by a k x n matrix mod p.
+ * u = v = 0 picks the words automatically: FP64 form, the (u,v) of least
+ * modelled cost u*v*(1 + 6/lambda) among (1,1),(1,2),(1,3),(1,4),(2,2),(2,3)
+ * with lambda >= 1 (Sec. 3.3, Table 1); INT8 form, the fewest digits that
+ * represent (p-1)/2.  Explicit (u,v) are validated (FP64: Prop. 3.3 must give
+ * lambda >= 1, else MWMM_ERR_BOUND; INT8: u and v must be at least the
+ * fewest digits).  Pure host logic: makes no CUDA call and allocates no
+ * device memory.  m, n, k >= 0; k may be 0 (C = 0).
+ * Errors: MWMM_ERR_ARG, MWMM_ERR_PRIME, MWMM_ERR_BOUND. */
+mwmm_status mwmm_plan(mwmm_plan_t *out, int64_t m, int64_t n, int64_t k, uint64_t p,
+                      int u, int v, mwmm_form form, const mwmm_plan_opts *opts);
+
+mwmm_status mwmm_plan_info(mwmm_plan_t plan, mwmm_plan_desc *out);
+
+/* Bytes of device workspace one mwmm_matmul call needs (0 for a NULL plan). */
+size_t mwmm_workspace_size(mwmm_plan_t plan);
+
+/* C = A B mod p with device pointers, asynchronously on `stream`.
+ * workspace: device memory of at least mwmm_workspace_size(plan) bytes,
+ * 256-byte aligned, owned by the caller; or NULL, in which case the plan
+ * allocates its own on the first call and keeps it until destroyed.
+ * Errors: MWMM_ERR_ARG, MWMM_ERR_NOMEM, MWMM_ERR_CUDA (launch failures). */
+mwmm_status mwmm_matmul(mwmm_plan_t plan, const uint64_t *dA, int64_t lda,
+                        const uint64_t *dB, int64_t ldb, uint64_t *dC, int64_t ldc,
+                        void *workspace, size_t workspace_bytes, void *stream);
+
+/* Same product with HOST matrices: copies A and B to plan-owned device
+ * buffers, computes, copies C back and synchronises `stream`.  For the
+ * copies to overlap nothing else, pass page-locked host memory.
+ * Device-side errors are checked before returning. */
+mwmm_status mwmm_matmul_host(mwmm_plan_t plan, const uint64_t *hA, int64_t lda,
+                             const uint64_t *hB, int64_t ldb, uint64_t *hC, int64_t ldc,
+                             void *stream);
+
+/* Synchronise `stream` and report device-side errors raised by this plan's
+ * earlier calls (MWMM_ERR_RANGE, MWMM_ERR_TIMEOUT); clears them. */
+mwmm_status mwmm_plan_check(mwmm_plan_t plan, void *stream);
+
+void mwmm_plan_destroy(mwmm_plan_t plan);
+
+/* ---- step-level entry points (used to check single steps of the path) ---- */
+
+/* Alg. 4 / INT8 digits: write the words of A (side 0, M is m x k) or of B
+ * (side 1, M is k x n) into `words` using the plan's word layout (see
+ * mwmm_plan_desc; `words` receives the X_off..X_off+size region only, i.e.
+ * the first chunk lands at words + 0). */
+mwmm_status mwmm_split(mwmm_plan_t plan, int side, const uint64_t *dM, int64_t ld,
+                       void *words, void *stream);
+
+/* Alg. 1 on the device: out[e] = x[e] mod p, for integer-valued doubles
+ * 0 <= x[e] <= 2^51 p (Prop. 2.1), using q = fl(1/p).  5 <= p < 2^52. */
+mwmm_status mwmm_fmod(const double *dx, int64_t count, uint64_t p, double *dout, void *stream);
+
+/* Alg. 2 on the device: out[e] = x[e] y[e] mod p for integer-valued doubles
+ * x, y in [0, p).  For p <= 2^52/3 this is Alg. 2 as printed (Prop. 2.2);
+ * above, y is split as y_h 2^26 + y_l and two Alg. 2 calls are combined so
+ * that each product stays within Prop. 2.2's bound. */
+mwmm_status mwmm_mulmod(const double *dx, const double *dy, int64_t count, uint64_t p,
+                        double *dout, void *stream);
+
+const char *mwmm_status_str(mwmm_status s);
+const char *mwmm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MWMM_H */

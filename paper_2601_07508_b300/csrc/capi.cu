@@ -1,0 +1,252 @@
+// C ABI of libmwmm (declared in include/mwmm.h).
+#include <cuda_runtime.h>
+
+#include <cstring>
+#include <new>
+
+#include "mwmm_internal.h"
+
+using mwmm::Plan;
+
+struct mwmm_plan_s {
+    Plan pl;
+};
+
+namespace {
+
+mwmm_status cuda_status(int e) {
+    if (e == 0) return MWMM_OK;
+    if (e == (int)cudaErrorMemoryAllocation) return MWMM_ERR_NOMEM;
+    return MWMM_ERR_CUDA;
+}
+
+// Device resources every call needs: the error flags (allocated on the first
+// device call, on the device current at that time).
+mwmm_status ensure_device(Plan &pl) {
+    if (pl.err_dev) return MWMM_OK;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return MWMM_ERR_CUDA;
+    void *p = nullptr;
+    cudaError_t e = cudaMalloc(&p, 256);
+    if (e != cudaSuccess) return cuda_status((int)e);
+    e = cudaMemset(p, 0, 256);
+    if (e != cudaSuccess) {
+        cudaFree(p);
+        return MWMM_ERR_CUDA;
+    }
+    pl.err_dev = static_cast<int *>(p);
+    pl.device = dev;
+    return MWMM_OK;
+}
+
+mwmm_status ensure_own_ws(Plan &pl) {
+    if (pl.own_ws_bytes >= pl.ws_bytes && (pl.own_ws || pl.ws_bytes == 0)) return MWMM_OK;
+    if (pl.own_ws) cudaFree(pl.own_ws);
+    pl.own_ws = nullptr;
+    pl.own_ws_bytes = 0;
+    void *p = nullptr;
+    cudaError_t e = cudaMalloc(&p, pl.ws_bytes);
+    if (e != cudaSuccess) return cuda_status((int)e);
+    pl.own_ws = p;
+    pl.own_ws_bytes = pl.ws_bytes;
+    return MWMM_OK;
+}
+
+bool valid_ld(const Plan &pl, int64_t lda, int64_t ldb, int64_t ldc) {
+    return lda >= (pl.k > 0 ? pl.k : 1) && ldb >= (pl.n > 0 ? pl.n : 1) && ldc >= (pl.n > 0 ? pl.n : 1);
+}
+
+// Run the product on device pointers with a given workspace.
+mwmm_status run_product(Plan &pl, const uint64_t *dA, int64_t lda, const uint64_t *dB, int64_t ldb,
+                        uint64_t *dC, int64_t ldc, uint8_t *ws, void *stream) {
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (pl.m == 0 || pl.n == 0) return MWMM_OK;
+    if (pl.k == 0)  // empty sum: C = 0
+        return cuda_status((int)cudaMemset2DAsync(dC, (size_t)ldc * 8, 0, (size_t)pl.n * 8, (size_t)pl.m, s));
+    int e = mwmm::launch_split(pl, 0, dA, lda, ws + pl.A_off, stream);
+    if (e) return cuda_status(e);
+    e = mwmm::launch_split(pl, 1, dB, ldb, ws + pl.B_off, stream);
+    if (e) return cuda_status(e);
+    if (pl.form == MWMM_FORM_FP64) {
+        e = mwmm::launch_gemm_fp64(pl, ws + pl.A_off, ws + pl.B_off, dC, ldc, pl.err_dev, stream);
+        return cuda_status(e);
+    }
+    int32_t *S = reinterpret_cast<int32_t *>(ws + pl.S_off);
+    e = mwmm::launch_gemm_tc(pl, ws + pl.A_off, ws + pl.B_off, S, pl.err_dev, stream);
+    if (e) return cuda_status(e);
+    e = mwmm::launch_recombine(pl, S, dC, ldc, stream);
+    return cuda_status(e);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *mwmm_version(void) { return "mwmm 0.1 (sm_103a)"; }
+
+const char *mwmm_status_str(mwmm_status s) {
+    switch (s) {
+        case MWMM_OK: return "ok";
+        case MWMM_ERR_ARG: return "invalid argument";
+        case MWMM_ERR_PRIME: return "p must be odd with 5 <= p < 2^52";
+        case MWMM_ERR_BOUND: return "no block size >= 1 for this (u,v) and p";
+        case MWMM_ERR_RANGE: return "an input entry is >= p";
+        case MWMM_ERR_NOMEM: return "device allocation failed";
+        case MWMM_ERR_BUDGET: return "request exceeds the memory budget";
+        case MWMM_ERR_CUDA: return "CUDA runtime error";
+        case MWMM_ERR_TIMEOUT: return "a bounded device wait expired";
+        case MWMM_ERR_BUSY: return "busy";
+        case MWMM_ERR_UNSUPPORTED: return "unsupported on this device";
+    }
+    return "unknown status";
+}
+
+mwmm_status mwmm_plan(mwmm_plan_t *out, int64_t m, int64_t n, int64_t k, uint64_t p, int u, int v,
+                      mwmm_form form, const mwmm_plan_opts *opts) {
+    if (!out) return MWMM_ERR_ARG;
+    *out = nullptr;
+    mwmm_plan_s *h = new (std::nothrow) mwmm_plan_s();
+    if (!h) return MWMM_ERR_NOMEM;
+    mwmm_status st = mwmm::make_plan(&h->pl, m, n, k, p, u, v, (int)form, opts);
+    if (st != MWMM_OK) {
+        delete h;
+        return st;
+    }
+    *out = h;
+    return MWMM_OK;
+}
+
+mwmm_status mwmm_plan_info(mwmm_plan_t plan, mwmm_plan_desc *d) {
+    if (!plan || !d) return MWMM_ERR_ARG;
+    const Plan &P = plan->pl;
+    std::memset(d, 0, sizeof(*d));
+    d->m = P.m; d->n = P.n; d->k = P.k; d->p = P.p;
+    d->form = P.form; d->u = P.u; d->v = P.v;
+    d->alpha = P.alpha; d->beta = P.beta;
+    d->lambda = P.lambda; d->lambda_max = P.lambda_max;
+    d->tc_chunk = P.tc_chunk; d->kc = P.kc; d->nkc = P.nkc; d->nsums = P.nsums;
+    d->q = P.q;
+    d->kb_elems = P.kb_elems; d->nkb = P.nkb; d->A_rows = P.A_rows; d->B_rows = P.B_rows;
+    d->A_off = P.A_off; d->B_off = P.B_off; d->S_off = P.S_off;
+    d->workspace_bytes = P.ws_bytes;
+    return MWMM_OK;
+}
+
+size_t mwmm_workspace_size(mwmm_plan_t plan) { return plan ? (size_t)plan->pl.ws_bytes : 0; }
+
+mwmm_status mwmm_matmul(mwmm_plan_t plan, const uint64_t *dA, int64_t lda, const uint64_t *dB, int64_t ldb,
+                        uint64_t *dC, int64_t ldc, void *workspace, size_t workspace_bytes, void *stream) {
+    if (!plan) return MWMM_ERR_ARG;
+    Plan &pl = plan->pl;
+    if (pl.m == 0 || pl.n == 0) return MWMM_OK;
+    if (!dC || (pl.k > 0 && (!dA || !dB)) || !valid_ld(pl, lda, ldb, ldc)) return MWMM_ERR_ARG;
+    if (workspace && (workspace_bytes < pl.ws_bytes || (reinterpret_cast<uintptr_t>(workspace) & 255)))
+        return MWMM_ERR_ARG;
+    mwmm_status st = ensure_device(pl);
+    if (st != MWMM_OK) return st;
+    if (!workspace) {
+        st = ensure_own_ws(pl);
+        if (st != MWMM_OK) return st;
+        workspace = pl.own_ws;
+    }
+    return run_product(pl, dA, lda, dB, ldb, dC, ldc, static_cast<uint8_t *>(workspace), stream);
+}
+
+mwmm_status mwmm_plan_check(mwmm_plan_t plan, void *stream) {
+    if (!plan) return MWMM_ERR_ARG;
+    Plan &pl = plan->pl;
+    cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return MWMM_ERR_CUDA;
+    if (!pl.err_dev) return MWMM_OK;
+    int flags[2] = {0, 0};
+    e = cudaMemcpy(flags, pl.err_dev, sizeof(flags), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return MWMM_ERR_CUDA;
+    if (flags[0] || flags[1]) {
+        e = cudaMemset(pl.err_dev, 0, sizeof(flags));
+        if (e != cudaSuccess) return MWMM_ERR_CUDA;
+    }
+    if (flags[0]) return MWMM_ERR_TIMEOUT;
+    if (flags[1]) return MWMM_ERR_RANGE;
+    return MWMM_OK;
+}
+
+mwmm_status mwmm_matmul_host(mwmm_plan_t plan, const uint64_t *hA, int64_t lda, const uint64_t *hB, int64_t ldb,
+                             uint64_t *hC, int64_t ldc, void *stream) {
+    if (!plan) return MWMM_ERR_ARG;
+    Plan &pl = plan->pl;
+    if (pl.m == 0 || pl.n == 0) return MWMM_OK;
+    if (!hC || (pl.k > 0 && (!hA || !hB)) || !valid_ld(pl, lda, ldb, ldc)) return MWMM_ERR_ARG;
+    mwmm_status st = ensure_device(pl);
+    if (st != MWMM_OK) return st;
+    st = ensure_own_ws(pl);
+    if (st != MWMM_OK) return st;
+    const uint64_t abytes = (uint64_t)pl.m * pl.k * 8, bbytes = (uint64_t)pl.k * pl.n * 8,
+                   cbytes = (uint64_t)pl.m * pl.n * 8;
+    const uint64_t need = ((abytes + 255) & ~uint64_t(255)) + ((bbytes + 255) & ~uint64_t(255)) + cbytes;
+    if (pl.hostbuf_bytes < need) {
+        if (pl.hostbuf_dev) cudaFree(pl.hostbuf_dev);
+        pl.hostbuf_dev = nullptr;
+        pl.hostbuf_bytes = 0;
+        void *p = nullptr;
+        cudaError_t e = cudaMalloc(&p, need);
+        if (e != cudaSuccess) return cuda_status((int)e);
+        pl.hostbuf_dev = static_cast<uint64_t *>(p);
+        pl.hostbuf_bytes = need;
+    }
+    uint8_t *base = reinterpret_cast<uint8_t *>(pl.hostbuf_dev);
+    uint64_t *dA = reinterpret_cast<uint64_t *>(base);
+    uint64_t *dB = reinterpret_cast<uint64_t *>(base + ((abytes + 255) & ~uint64_t(255)));
+    uint64_t *dC = reinterpret_cast<uint64_t *>(base + ((abytes + 255) & ~uint64_t(255)) +
+                                                ((bbytes + 255) & ~uint64_t(255)));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaSuccess;
+    if (pl.k > 0) {
+        e = cudaMemcpy2DAsync(dA, (size_t)pl.k * 8, hA, (size_t)lda * 8, (size_t)pl.k * 8, (size_t)pl.m,
+                              cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess)
+            e = cudaMemcpy2DAsync(dB, (size_t)pl.n * 8, hB, (size_t)ldb * 8, (size_t)pl.n * 8, (size_t)pl.k,
+                                  cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) return MWMM_ERR_CUDA;
+    }
+    st = run_product(pl, dA, pl.k > 0 ? pl.k : 1, dB, pl.n, dC, pl.n, static_cast<uint8_t *>(pl.own_ws), stream);
+    if (st != MWMM_OK) return st;
+    e = cudaMemcpy2DAsync(hC, (size_t)ldc * 8, dC, (size_t)pl.n * 8, (size_t)pl.n * 8, (size_t)pl.m,
+                          cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return MWMM_ERR_CUDA;
+    return mwmm_plan_check(plan, stream);
+}
+
+void mwmm_plan_destroy(mwmm_plan_t plan) {
+    if (!plan) return;
+    Plan &pl = plan->pl;
+    if (pl.own_ws) cudaFree(pl.own_ws);
+    if (pl.hostbuf_dev) cudaFree(pl.hostbuf_dev);
+    if (pl.err_dev) cudaFree(pl.err_dev);
+    delete plan;
+}
+
+mwmm_status mwmm_split(mwmm_plan_t plan, int side, const uint64_t *dM, int64_t ld, void *words, void *stream) {
+    if (!plan || (side != 0 && side != 1) || !words) return MWMM_ERR_ARG;
+    Plan &pl = plan->pl;
+    const int64_t rowlen = side == 0 ? pl.k : pl.n;
+    if (ld < (rowlen > 0 ? rowlen : 1) || (!dM && pl.k > 0 && (side == 0 ? pl.m : pl.n) > 0)) return MWMM_ERR_ARG;
+    if (reinterpret_cast<uintptr_t>(words) & 15) return MWMM_ERR_ARG;
+    mwmm_status st = ensure_device(pl);
+    if (st != MWMM_OK) return st;
+    return cuda_status(mwmm::launch_split(pl, side, dM, ld, words, stream));
+}
+
+mwmm_status mwmm_fmod(const double *dx, int64_t count, uint64_t p, double *dout, void *stream) {
+    if (count < 0 || (count > 0 && (!dx || !dout))) return MWMM_ERR_ARG;
+    if (p < 5 || (p & 1) == 0 || p >= (uint64_t(1) << 52)) return MWMM_ERR_PRIME;
+    return cuda_status(mwmm::launch_fmod(dx, count, p, dout, stream));
+}
+
+mwmm_status mwmm_mulmod(const double *dx, const double *dy, int64_t count, uint64_t p, double *dout,
+                        void *stream) {
+    if (count < 0 || (count > 0 && (!dx || !dy || !dout))) return MWMM_ERR_ARG;
+    if (p < 5 || (p & 1) == 0 || p >= (uint64_t(1) << 52)) return MWMM_ERR_PRIME;
+    return cuda_status(mwmm::launch_mulmod(dx, dy, count, p, dout, stream));
+}
+
+}  // extern "C"

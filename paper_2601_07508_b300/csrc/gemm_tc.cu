@@ -1,0 +1,348 @@
+// INT8-word form on the tcgen05 tensor pipe (sm_103a).
+//
+// Computes the diagonal word sums S_s = sum_{i+j=s} A_i B_j (exact integers)
+// of the INT8 digit decomposition; recombine.cu then forms
+// C = sum_s 256^s S_s mod p.  This is the paper's second perspective (Sec. 6):
+// narrower words, more of them, multiplied on tensor cores.
+//
+// Exactness.  sm_103a's tcgen05 has no INT8 kind, so the digits (integers in
+// [-128, 127]) are carried exactly in bf16 and multiplied with
+// tcgen05.mma.kind::f16 into FP32 tensor memory.  Every product is an integer
+// of magnitude <= 2^14, so as long as a chunk sums at most 1024 of them every
+// partial sum is an integer of magnitude <= 2^24, which FP32 represents
+// exactly whatever the order or alignment of the additions: the block
+// condition of Prop. 2.3 with a 24-bit significand in place of 53 bits.  Each
+// chunk is drained from tensor memory into INT32 registers (the K-chunking of
+// Alg. 3, with the reduction postponed to the exact integer recombination).
+//
+// Schedule.  Work item = (128-row tile, 256-col tile, diagonal s, K-range kc);
+// its k-loop runs over the virtual k-blocks (pair (i, s-i), 64-wide k-block):
+// the pairs of one diagonal are concatenated along K (the K-dimension analogue
+// of Alg. 6's concatenation).  Items go round-robin over a persistent grid of
+// one CTA per SM, heaviest diagonals first.
+//
+// Warp roles (320 threads):
+//   warp 0      one lane issues bulk TMA copies of the pre-swizzled word tiles
+//               (A 16 KB + B 32 KB per stage, 4 stages);
+//   warp 1      allocates 512 TMEM columns (two 128 x 256 FP32 accumulators);
+//               one lane issues 4 MMAs (128 x 256 x 16) per stage;
+//   warps 2-9   drain a finished accumulator (warp w reads TMEM lanes
+//               32 (w mod 4) .. +31, columns half (w-2)/4), convert to INT32,
+//               sum the chunks of an item, store S_s.
+// Every wait is bounded (device_common.cuh); a timeout raises the plan's
+// error flag and all roles leave their loops.
+#include <cuda_bf16.h>
+
+#include "device_common.cuh"
+#include "mwmm_internal.h"
+
+namespace mwmm {
+
+namespace {
+
+constexpr int BM = kTcBM;  // 128
+constexpr int BN = kTcBN;  // 256
+constexpr int STAGES = 4;
+constexpr int EPI_WARPS = 8;
+constexpr int THREADS = 32 * (2 + EPI_WARPS);
+constexpr uint32_t kTileA = BM * kTileBytes;  // 16 KB
+constexpr uint32_t kTileB = BN * kTileBytes;  // 32 KB
+constexpr uint32_t kTmemCols = 2 * BN;        // 512: two accumulator buffers
+constexpr int kSmemBytes = STAGES * (kTileA + kTileB) + 1024;
+
+struct TcParams {
+    const uint8_t *Aw, *Bw;
+    int32_t *S;
+    int64_t nkb, A_rows, B_rows, kcb, nitems;
+    int u, v, nsums, nkc, chunk_blocks, mt_count, nt_count;
+    int diag_order[2 * kMaxWords];
+    int *err;
+};
+
+struct Item {
+    int64_t mt, nt, kb0, nkbc;
+    int s, kc, i0, w;
+};
+
+__device__ __forceinline__ Item get_item(const TcParams &P, int64_t idx) {
+    Item it;
+    const int64_t ntiles = (int64_t)P.mt_count * P.nt_count;
+    const int64_t tile = idx % ntiles;
+    const int64_t rest = idx / ntiles;
+    it.kc = (int)(rest % P.nkc);
+    it.s = P.diag_order[rest / P.nkc];
+    it.mt = tile / P.nt_count;
+    it.nt = tile % P.nt_count;
+    const int ilo = it.s - (P.v - 1) > 0 ? it.s - (P.v - 1) : 0;
+    const int ihi = it.s < P.u - 1 ? it.s : P.u - 1;
+    it.i0 = ilo;
+    it.w = ihi - ilo + 1;
+    it.kb0 = (int64_t)it.kc * P.kcb;
+    const int64_t left = P.nkb - it.kb0;
+    it.nkbc = left < P.kcb ? left : P.kcb;
+    return it;
+}
+
+// ---- tcgen05 wrappers -------------------------------------------------------
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
+// 1024 bytes apart (SBO), descriptor version 1.
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;             // LBO (unused for swizzled K-major)
+    d |= (uint64_t)(1024 >> 4) << 32;   // SBO
+    d |= (uint64_t)1 << 46;             // version
+    d |= (uint64_t)2 << 61;             // SWIZZLE_128B
+    return d;
+}
+
+// Instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major.
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                            ((uint32_t)(BM >> 4) << 24);
+
+__device__ __forceinline__ void mma_bf16(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
+        "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(acc)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// 32 consecutive FP32 columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+          "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+          "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+          "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_constant__ TcParams P) {
+    extern __shared__ uint8_t smem_raw[];
+    __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES], tfull[2], tempty[2], done;
+    __shared__ uint32_t tmem_base_sh;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t raw = smem_u32(smem_raw);
+    const uint32_t pad = ((raw + 1023u) & ~1023u) - raw;
+    uint8_t *sA = smem_raw + pad;
+    uint8_t *sB = sA + STAGES * kTileA;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&tfull[b], 1);
+            mbar_init(&tempty[b], EPI_WARPS);
+        }
+        mbar_init(&done, 1);
+        fence_mbar_init();
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&tmem_base_sh)),
+                     "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = tmem_base_sh;
+
+    if (warp == 0) {
+        if (lane == 0) {  // ---------------- TMA producer
+            uint64_t g = 0;
+            bool alive = true;
+            for (int64_t idx = blockIdx.x; alive && idx < P.nitems; idx += gridDim.x) {
+                const Item it = get_item(P, idx);
+                const int64_t nvb = (int64_t)it.w * it.nkbc;
+                for (int64_t t = 0; t < nvb; ++t, ++g) {
+                    const int slot = (int)(g % STAGES);
+                    if (!mbar_wait(&empty[slot], (uint32_t)(((g / STAGES) & 1) ^ 1), P.err)) {
+                        alive = false;
+                        break;
+                    }
+                    const int i = it.i0 + (int)(t / it.nkbc);
+                    const int j = it.s - i;
+                    const int64_t kb = it.kb0 + t % it.nkbc;
+                    const uint8_t *a = P.Aw + (((int64_t)i * P.nkb + kb) * P.A_rows + it.mt * BM) * kTileBytes;
+                    const uint8_t *b = P.Bw + (((int64_t)j * P.nkb + kb) * P.B_rows + it.nt * BN) * kTileBytes;
+                    mbar_arrive_expect_tx(&full[slot], kTileA + kTileB);
+                    bulk_g2s(sA + slot * kTileA, a, kTileA, &full[slot]);
+                    bulk_g2s(sB + slot * kTileB, b, kTileB, &full[slot]);
+                }
+            }
+            // Let every copy this lane started land before the CTA can exit.
+            for (int s = 0; s < STAGES; ++s) {
+                const uint64_t armed = g > (uint64_t)s ? (g - s + STAGES - 1) / STAGES : 0;
+                if (armed) mbar_wait(&full[s], (uint32_t)((armed - 1) & 1), P.err);
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {  // ---------------- MMA issuer
+            uint64_t g = 0, c = 0;
+            bool alive = true;
+            const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
+            for (int64_t idx = blockIdx.x; alive && idx < P.nitems; idx += gridDim.x) {
+                const Item it = get_item(P, idx);
+                const int64_t nvb = (int64_t)it.w * it.nkbc;
+                for (int64_t t0 = 0; alive && t0 < nvb; t0 += P.chunk_blocks, ++c) {
+                    const int buf = (int)(c & 1);
+                    if (!mbar_wait(&tempty[buf], (uint32_t)(((c >> 1) & 1) ^ 1), P.err)) {
+                        alive = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t dt = tmem_base + (uint32_t)(buf * BN);
+                    const int64_t tend = t0 + P.chunk_blocks < nvb ? t0 + P.chunk_blocks : nvb;
+                    for (int64_t t = t0; t < tend; ++t, ++g) {
+                        const int slot = (int)(g % STAGES);
+                        if (!mbar_wait(&full[slot], (uint32_t)((g / STAGES) & 1), P.err)) {
+                            alive = false;
+                            break;
+                        }
+                        tc_fence_after();
+                        const uint64_t ad = sdesc(a0 + slot * kTileA), bd = sdesc(b0 + slot * kTileB);
+#pragma unroll
+                        for (int kk = 0; kk < 4; ++kk)  // K = 16 per MMA: +32 bytes = +2 in the address field
+                            mma_bf16(dt, ad + 2 * kk, bd + 2 * kk, (t > t0 || kk > 0) ? 1u : 0u);
+                        mma_commit(&empty[slot]);
+                    }
+                    mma_commit(&tfull[buf]);
+                }
+            }
+            // All MMAs this lane issued have completed once `done` flips.
+            mma_commit(&done);
+            mbar_wait(&done, 0, P.err);
+        }
+    } else {  // -------------------------------- epilogue warps 2..9
+        const int quarter = warp & 3;
+        const int half = (warp - 2) >> 2;
+        const uint32_t tlane = tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(half * 128);
+        uint64_t c = 0;
+        bool alive = true;
+        for (int64_t idx = blockIdx.x; alive && idx < P.nitems; idx += gridDim.x) {
+            const Item it = get_item(P, idx);
+            const int64_t nvb = (int64_t)it.w * it.nkbc;
+            const int64_t nch = (nvb + P.chunk_blocks - 1) / P.chunk_blocks;
+            int32_t acc[128];
+#pragma unroll
+            for (int e = 0; e < 128; ++e) acc[e] = 0;
+            for (int64_t ch = 0; ch < nch; ++ch, ++c) {
+                const int buf = (int)(c & 1);
+                const bool ok = mbar_wait(&tfull[buf], (uint32_t)((c >> 1) & 1), P.err);
+                if (!__all_sync(0xffffffffu, ok)) {
+                    alive = false;
+                    break;
+                }
+                tc_fence_after();
+#pragma unroll
+                for (int jb = 0; jb < 4; ++jb) {
+                    uint32_t r[32];
+                    tmem_ld32(tlane + (uint32_t)(buf * BN + jb * 32), r);
+#pragma unroll
+                    for (int e = 0; e < 32; ++e) acc[jb * 32 + e] += __float2int_rn(__uint_as_float(r[e]));
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&tempty[buf]);
+            }
+            if (!alive) break;
+            const int64_t row = it.mt * BM + quarter * 32 + lane;
+            int32_t *dst = P.S + (((int64_t)it.s * P.nkc + it.kc) * P.A_rows + row) * P.B_rows + it.nt * BN +
+                           half * 128;
+#pragma unroll
+            for (int q4 = 0; q4 < 32; ++q4)
+                reinterpret_cast<int4 *>(dst)[q4] =
+                    make_int4(acc[4 * q4], acc[4 * q4 + 1], acc[4 * q4 + 2], acc[4 * q4 + 3]);
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 1)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(kTmemCols)
+                     : "memory");
+}
+
+int sm_count() {
+    static int cached[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 148;
+    if (!cached[dev]) {
+        int n = 0;
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 148;
+        cached[dev] = n;
+    }
+    return cached[dev];
+}
+
+}  // namespace
+
+int launch_gemm_tc(const Plan &pl, const void *Aw, const void *Bw, int32_t *S, int *err, void *stream) {
+    TcParams P;
+    P.Aw = static_cast<const uint8_t *>(Aw);
+    P.Bw = static_cast<const uint8_t *>(Bw);
+    P.S = S;
+    P.nkb = pl.nkb;
+    P.A_rows = pl.A_rows;
+    P.B_rows = pl.B_rows;
+    P.kcb = pl.kc / kTcKB;
+    P.u = pl.u;
+    P.v = pl.v;
+    P.nsums = pl.nsums;
+    P.nkc = pl.nkc;
+    P.chunk_blocks = (int)(pl.tc_chunk / kTcKB);
+    P.mt_count = (int)(pl.A_rows / BM);
+    P.nt_count = (int)(pl.B_rows / BN);
+    P.nitems = (int64_t)P.mt_count * P.nt_count * pl.nsums * pl.nkc;
+    P.err = err;
+    // diagonals by decreasing number of word pairs (heaviest items first)
+    int order[2 * kMaxWords];
+    int w[2 * kMaxWords];
+    for (int s = 0; s < pl.nsums; ++s) {
+        const int lo = s - (pl.v - 1) > 0 ? s - (pl.v - 1) : 0, hi = s < pl.u - 1 ? s : pl.u - 1;
+        w[s] = hi - lo + 1;
+        order[s] = s;
+    }
+    for (int a = 1; a < pl.nsums; ++a)
+        for (int b = a; b > 0 && w[order[b]] > w[order[b - 1]]; --b) {
+            int t = order[b];
+            order[b] = order[b - 1];
+            order[b - 1] = t;
+        }
+    for (int s = 0; s < 2 * kMaxWords; ++s) P.diag_order[s] = s < pl.nsums ? order[s] : 0;
+    if (P.nitems == 0) return 0;
+    cudaError_t e = set_smem_attr(reinterpret_cast<const void *>(gemm_tc_kernel), kSmemBytes);
+    if (e != cudaSuccess) return (int)e;
+    const int64_t sms = sm_count();
+    const unsigned grid = (unsigned)(P.nitems < sms ? P.nitems : sms);
+    gemm_tc_kernel<<<grid, THREADS, kSmemBytes, static_cast<cudaStream_t>(stream)>>>(P);
+    return (int)cudaGetLastError();
+}
+
+}  // namespace mwmm

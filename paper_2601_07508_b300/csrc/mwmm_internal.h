@@ -1,0 +1,69 @@
+// Internal declarations shared by the libmwmm translation units.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include "mwmm.h"
+
+namespace mwmm {
+
+constexpr int kMaxWords = 8;            // u, v <= 8 in either form
+constexpr int kTileBytes = 128;         // one k-block row chunk of the word layout
+// FP64 form tiling
+constexpr int kF64KB = 16;              // doubles per k-block (128 B)
+constexpr int kF64BM = 64;              // CTA rows
+constexpr int kF64BN = 64;              // CTA cols
+// INT8 (tcgen05) form tiling
+constexpr int kTcKB = 64;               // bf16 digits per k-block (128 B)
+constexpr int kTcBM = 128;              // MMA M (one CTA, TMEM lanes)
+constexpr int kTcBN = 256;              // MMA N
+constexpr int kTcMaxChunk = 1024;       // 2^24 / 2^14 digit products per FP32 chunk
+constexpr int64_t kInt32SumLimit = 131071; // floor((2^31 - 1) / 2^14): products per INT32 sum
+
+struct Plan {
+    int64_t m = 0, n = 0, k = 0;
+    uint64_t p = 0;
+    int form = 0;
+    int u = 0, v = 0;
+    uint64_t alpha = 0, beta = 0;
+    int64_t lambda = 0, lambda_max = 0;
+    double pd = 0, q = 0;
+    int validate = 0;
+    // FP64 form recombination constants, indexed i * v + j
+    double gamma[kMaxWords * kMaxWords] = {};
+    double gamma26[kMaxWords * kMaxWords] = {};  // gamma * 2^26 mod p
+    int big_p = 0;                               // p > 2^52 / 3: split Alg. 2
+    // INT8 form
+    int64_t tc_chunk = 0, kc = 0;
+    int nkc = 0, nsums = 0;
+    // layout
+    int64_t kb_elems = 0, nkb = 0, A_rows = 0, B_rows = 0;
+    uint64_t A_off = 0, B_off = 0, S_off = 0, ws_bytes = 0;
+    // owned device resources (lazily created)
+    int device = -1;
+    void *own_ws = nullptr;
+    uint64_t own_ws_bytes = 0;
+    int *err_dev = nullptr;      // [0]: timeout, [1]: range violation
+    uint64_t *hostbuf_dev = nullptr;  // A, B, C device copies for mwmm_matmul_host
+    uint64_t hostbuf_bytes = 0;
+};
+
+// plan.cpp
+mwmm_status make_plan(Plan *pl, int64_t m, int64_t n, int64_t k, uint64_t p, int u, int v,
+                      int form, const mwmm_plan_opts *opts);
+uint64_t ceil_root(uint64_t p, int u);
+uint64_t block_size(uint64_t p, int u, int v);  // Prop. 3.3 / Sec. 2.2, 0 if none
+int int8_digits(uint64_t p);
+uint64_t mulmod_u64(uint64_t a, uint64_t b, uint64_t p);
+
+// launches (return cudaError_t as int)
+int launch_split(const Plan &pl, int side, const uint64_t *M, int64_t ld, void *words, void *stream);
+int launch_gemm_fp64(const Plan &pl, const void *Aw, const void *Bw, uint64_t *C, int64_t ldc,
+                     int *err, void *stream);
+int launch_gemm_tc(const Plan &pl, const void *Aw, const void *Bw, int32_t *S, int *err, void *stream);
+int launch_recombine(const Plan &pl, const int32_t *S, uint64_t *C, int64_t ldc, void *stream);
+int launch_fmod(const double *x, int64_t count, uint64_t p, double *out, void *stream);
+int launch_mulmod(const double *x, const double *y, int64_t count, uint64_t p, double *out, void *stream);
+
+}  // namespace mwmm

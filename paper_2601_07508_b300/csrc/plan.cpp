@@ -1,0 +1,184 @@
+// Planner: word counts, radices and block sizes of the multiword product.
+//
+// Pure host logic (no CUDA calls), so plans can be made and inspected on a
+// machine without a GPU.
+#include <cmath>
+#include <cstring>
+
+#include "mwmm_internal.h"
+
+namespace mwmm {
+
+typedef unsigned __int128 u128;
+
+static int64_t round_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
+static uint64_t align256(uint64_t x) { return (x + 255) & ~uint64_t(255); }
+
+uint64_t mulmod_u64(uint64_t a, uint64_t b, uint64_t p) { return (uint64_t)((u128)a * b % p); }
+
+// Smallest a >= 1 with a^u >= p: alpha = ceil(p^(1/u)) of Alg. 4, in exact
+// integer arithmetic (a floating pow() can round across an integer).
+uint64_t ceil_root(uint64_t p, int u) {
+    if (u <= 1) return p;
+    auto ge = [&](uint64_t a) {
+        u128 pw = 1;
+        for (int i = 0; i < u; ++i) {
+            pw *= a;
+            if (pw >= p) return true;
+        }
+        return false;
+    };
+    uint64_t hi = 1;
+    while (!ge(hi)) hi *= 2;
+    uint64_t lo = hi / 2 + (hi == 1);
+    while (lo < hi) {
+        uint64_t mid = lo + (hi - lo) / 2;
+        if (ge(mid)) hi = mid; else lo = mid + 1;
+    }
+    return lo;
+}
+
+// Largest lambda with lambda * max(A_i) * max(B_j) + p - 1 <= 2^53.
+// (u,v) = (1,1): the matrices are not split and their entries are <= p - 1,
+// so lambda = floor((2^t - p + 1) / (p - 1)^2)  (Sec. 2.2).
+// Otherwise the word bounds alpha, beta of Prop. 3.2 give Prop. 3.3's
+// lambda = floor((2^t - p + 1) / (alpha beta)).  Returns 0 when < 1.
+uint64_t block_size(uint64_t p, int u, int v) {
+    const u128 two_t = (u128)1 << 53;
+    if ((u128)p > two_t + 1) return 0;
+    u128 prod = (u == 1 && v == 1) ? (u128)(p - 1) * (p - 1)
+                                   : (u128)ceil_root(p, u) * ceil_root(p, v);
+    if (prod == 0) return UINT64_MAX;
+    u128 lam = (two_t - p + 1) / prod;
+    return lam > (u128)UINT64_MAX ? UINT64_MAX : (uint64_t)lam;
+}
+
+// Fewest balanced base-2^8 digits in [-128, 127] that represent every signed
+// representative in [-(p-1)/2, (p-1)/2]; u digits reach 127 (256^u - 1) / 255.
+int int8_digits(uint64_t p) {
+    const u128 half = (p - 1) / 2;
+    int u = 1;
+    u128 pw = 256;
+    while ((u128)127 * (pw - 1) / 255 < half) {
+        ++u;
+        pw *= 256;
+    }
+    return u;
+}
+
+static int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+mwmm_status make_plan(Plan *pl, int64_t m, int64_t n, int64_t k, uint64_t p, int u, int v,
+                      int form, const mwmm_plan_opts *opts) {
+    if (m < 0 || n < 0 || k < 0 || u < 0 || v < 0 || u > kMaxWords || v > kMaxWords)
+        return MWMM_ERR_ARG;
+    if ((u == 0) != (v == 0)) return MWMM_ERR_ARG;
+    // Alg. 1 needs p < 2^(t-1) (Prop. 2.1); the paper also assumes p >= 5.
+    if (p < 5 || (p & 1) == 0 || p >= (uint64_t(1) << 52)) return MWMM_ERR_PRIME;
+    if (form == MWMM_FORM_AUTO) form = MWMM_FORM_INT8;
+    if (form != MWMM_FORM_FP64 && form != MWMM_FORM_INT8) return MWMM_ERR_ARG;
+    mwmm_plan_opts o;
+    std::memset(&o, 0, sizeof(o));
+    if (opts) o = *opts;
+
+    Plan P;
+    P.m = m; P.n = n; P.k = k; P.p = p; P.form = form;
+    P.pd = (double)p;
+    P.q = 1.0 / (double)p;  // q = fl(1/p): IEEE division, round to nearest
+    P.validate = o.validate != 0;
+
+    if (form == MWMM_FORM_FP64) {
+        if (u == 0) {
+            // Least modelled cost: u*v word products of k steps, plus an
+            // Alg. 1 reduction (about 6 FP64 operations) every lambda steps.
+            static const int cand[6][2] = {{1, 1}, {1, 2}, {1, 3}, {1, 4}, {2, 2}, {2, 3}};
+            double best = 0;
+            for (auto &c : cand) {
+                uint64_t lam = block_size(p, c[0], c[1]);
+                if (lam < 1) continue;
+                int64_t kk = k > 0 ? k : 1;
+                int64_t nred = (lam >= (uint64_t)kk) ? 1 : ceil_div(kk, (int64_t)lam);
+                double cost = (double)(c[0] * c[1]) * ((double)kk + 6.0 * (double)nred + 12.0);
+                if (u == 0 || cost < best) { u = c[0]; v = c[1]; best = cost; }
+            }
+            if (u == 0) return MWMM_ERR_BOUND;
+        }
+        uint64_t lam = block_size(p, u, v);
+        if (lam < 1) return MWMM_ERR_BOUND;
+        P.u = u; P.v = v;
+        P.alpha = ceil_root(p, u);
+        P.beta = ceil_root(p, v);
+        P.lambda_max = lam > (uint64_t)INT64_MAX ? INT64_MAX : (int64_t)lam;
+        P.lambda = P.lambda_max;
+        if (o.lambda != 0) {
+            if (o.lambda < 1 || o.lambda > P.lambda_max) return MWMM_ERR_BOUND;
+            P.lambda = o.lambda;
+        }
+        // gamma_ij = alpha^i beta^j mod p, and gamma_ij 2^26 mod p for the
+        // split form of Alg. 2 used when p > 2^52 / 3.
+        uint64_t ai = 1 % p;
+        for (int i = 0; i < u; ++i) {
+            uint64_t g = ai;
+            for (int j = 0; j < v; ++j) {
+                P.gamma[i * v + j] = (double)g;
+                P.gamma26[i * v + j] = (double)mulmod_u64(g, uint64_t(1) << 26, p);
+                g = mulmod_u64(g, P.beta % p, p);
+            }
+            ai = mulmod_u64(ai, P.alpha % p, p);
+        }
+        // Prop. 2.2 covers x y <= (2^52 / 3) p; with x, y <= p - 1 that holds
+        // iff 3 (p-1)^2 <= 2^52 p.
+        P.big_p = (u128)3 * (p - 1) * (p - 1) > ((u128)p << 52);
+        P.kb_elems = kF64KB;
+        P.nkb = ceil_div(k, kF64KB);
+        P.A_rows = round_up(m > 0 ? m : 1, kF64BM);
+        P.B_rows = round_up(n > 0 ? n : 1, kF64BN);
+        uint64_t abytes = (uint64_t)u * P.nkb * P.A_rows * kTileBytes;
+        uint64_t bbytes = (uint64_t)v * P.nkb * P.B_rows * kTileBytes;
+        P.A_off = 0;
+        P.B_off = align256(abytes);
+        P.S_off = align256(P.B_off + bbytes);
+        P.ws_bytes = P.S_off;
+    } else {
+        const int need = int8_digits(p);
+        if (u == 0) { u = need; v = need; }
+        if (u < need || v < need) return MWMM_ERR_BOUND;
+        P.u = u; P.v = v;
+        P.alpha = 256; P.beta = 256;
+        P.nsums = u + v - 1;
+        P.tc_chunk = kTcMaxChunk;
+        if (o.tc_chunk != 0) {
+            if (o.tc_chunk < 64 || o.tc_chunk > kTcMaxChunk || o.tc_chunk % 64) return MWMM_ERR_ARG;
+            P.tc_chunk = o.tc_chunk;
+        }
+        // One INT32 sum S_s collects w = min(u,v) pairs (at most) over kc
+        // k-steps, each product |d_a d_b| <= 2^14: need kc * w <= 131071.
+        const int w = u < v ? u : v;
+        int64_t kcmax = (kInt32SumLimit / w) / kTcKB * kTcKB;
+        int64_t kc = kcmax;
+        if (o.kc != 0) {
+            if (o.kc < kTcKB || o.kc % kTcKB || o.kc > kcmax) return MWMM_ERR_ARG;
+            kc = o.kc;
+        }
+        int64_t kpad = round_up(k, kTcKB);
+        if (kc > kpad) kc = kpad > 0 ? kpad : kTcKB;
+        P.kc = kc;
+        P.nkc = k > 0 ? (int)ceil_div(k, kc) : 0;
+        P.kb_elems = kTcKB;
+        P.nkb = ceil_div(k, kTcKB);
+        P.A_rows = round_up(m > 0 ? m : 1, kTcBM);
+        P.B_rows = round_up(n > 0 ? n : 1, kTcBN);
+        uint64_t abytes = (uint64_t)u * P.nkb * P.A_rows * kTileBytes;
+        uint64_t bbytes = (uint64_t)v * P.nkb * P.B_rows * kTileBytes;
+        uint64_t sbytes = (uint64_t)P.nsums * P.nkc * P.A_rows * P.B_rows * 4;
+        P.A_off = 0;
+        P.B_off = align256(abytes);
+        P.S_off = align256(P.B_off + bbytes);
+        P.ws_bytes = align256(P.S_off + sbytes);
+    }
+    if (m == 0 || n == 0) P.ws_bytes = 0;
+    *pl = P;
+    return MWMM_OK;
+}
+
+}  // namespace mwmm

@@ -1,0 +1,85 @@
+// Recombination of the INT8 form:
+//   C = sum_{s=0}^{u+v-2} 256^s S_s mod p,  S_s = sum_{i+j=s} A_i B_j
+// evaluated by Horner's rule from the top diagonal down,
+//   R <- (256 R + S_s) mod p,
+// in exact 64-bit integer arithmetic.  This is the alpha^i beta^j mod p
+// recombination of Alg. 5 with alpha = beta = 256 and the pairs of equal
+// i + j grouped; B300's FP64 pipe runs at 1/64 of its integer rate, so the
+// reduction uses a Barrett reciprocal instead of Alg. 1 / Alg. 2.
+//
+// Bounds: 0 <= R < p < 2^52, so 256 R < 2^60; |S_s| < 2^31 per K-range and at
+// most nkc K-ranges, so y = 256 R + S_s + off with off = p * ceil(2^31 nkc / p)
+// lies in [0, 2^64) and y mod p = (256 R + S_s) mod p.
+#include "device_common.cuh"
+#include "mwmm_internal.h"
+
+namespace mwmm {
+
+namespace {
+
+struct RecParams {
+    const int32_t *S;
+    uint64_t *C;
+    int64_t ldc, m, n, A_rows, B_rows;
+    int nsums, nkc;
+    uint64_t p, mu, off;  // mu = floor((2^64 - 1) / p)
+};
+
+__device__ __forceinline__ uint64_t reduce_u64(uint64_t y, uint64_t p, uint64_t mu) {
+    const uint64_t qh = __umul64hi(y, mu);  // floor(y / p) - {0, 1, 2}
+    uint64_t r = y - qh * p;
+    if (r >= p) r -= p;
+    if (r >= p) r -= p;
+    return r;
+}
+
+// Each thread produces 4 consecutive outputs of one row.
+__global__ void __launch_bounds__(256) recombine_kernel(const __grid_constant__ RecParams P) {
+    const int64_t c0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4;
+    if (c0 >= P.n) return;
+    const int64_t plane = P.A_rows * P.B_rows;
+    for (int64_t row = blockIdx.y; row < P.m; row += gridDim.y) {
+    uint64_t R[4] = {0, 0, 0, 0};
+    for (int s = P.nsums - 1; s >= 0; --s) {
+        int64_t x[4] = {0, 0, 0, 0};
+        for (int kc = 0; kc < P.nkc; ++kc) {
+            const int4 v = *reinterpret_cast<const int4 *>(P.S + ((int64_t)s * P.nkc + kc) * plane +
+                                                           row * P.B_rows + c0);
+            x[0] += v.x; x[1] += v.y; x[2] += v.z; x[3] += v.w;
+        }
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+            R[e] = reduce_u64((R[e] << 8) + (uint64_t)(x[e] + (int64_t)P.off), P.p, P.mu);
+    }
+    uint64_t *out = P.C + row * P.ldc + c0;
+#pragma unroll
+    for (int e = 0; e < 4; ++e)
+        if (c0 + e < P.n) out[e] = R[e];
+    }
+}
+
+}  // namespace
+
+int launch_recombine(const Plan &pl, const int32_t *S, uint64_t *C, int64_t ldc, void *stream) {
+    RecParams P;
+    P.S = S;
+    P.C = C;
+    P.ldc = ldc;
+    P.m = pl.m;
+    P.n = pl.n;
+    P.A_rows = pl.A_rows;
+    P.B_rows = pl.B_rows;
+    P.nsums = pl.nsums;
+    P.nkc = pl.nkc;
+    P.p = pl.p;
+    P.mu = (~uint64_t(0)) / pl.p;
+    const unsigned __int128 need = (unsigned __int128)pl.nkc << 31;
+    P.off = (uint64_t)((need + pl.p - 1) / pl.p * pl.p);
+    if (pl.m == 0 || pl.n == 0) return 0;
+    const int64_t groups = (pl.n + 3) / 4;
+    dim3 grid((unsigned)((groups + 255) / 256), (unsigned)(pl.m < 65535 ? pl.m : 65535));
+    recombine_kernel<<<grid, 256, 0, static_cast<cudaStream_t>(stream)>>>(P);
+    return (int)cudaGetLastError();
+}
+
+}  // namespace mwmm

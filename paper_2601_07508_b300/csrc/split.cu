@@ -1,0 +1,174 @@
+// Split kernels: uint64 matrices -> word matrices in the tiled layout.
+//
+// FP64 form: Alg. 4 (MW-Decomposition) with integer alpha = ceil(p^(1/u)):
+//   T = M; for i < u-1 { R = floor(T / alpha); M_i = T - alpha R; T = R }; M_{u-1} = T.
+// The quotient is taken in exact 64-bit integer arithmetic (a Barrett
+// reciprocal of alpha plus a correction); Lemma 3.1 shows that the paper's
+// floor(fl(T / alpha)) is the same integer, so the words are identical.
+//
+// INT8 form: the signed representative s of M mod p (M, or M - p when
+// M > (p-1)/2) is written as balanced base-2^8 digits in [-128, 127],
+// s = sum_i 256^i d_i; the digits are stored exactly as bf16.
+//
+// Output layout (see mwmm_plan_desc): word w, k-block kb, row r occupies the
+// 128-byte chunk ((w * nkb + kb) * rows_pad + r); inside it the 16-byte
+// granule g sits at position g ^ (r & 7), which is the 128-byte swizzle the
+// tcgen05 shared-memory descriptors expect, and keeps the FP64 kernel's
+// shared-memory reads spread over all banks.
+#include <cuda_bf16.h>
+
+#include "device_common.cuh"
+#include "mwmm_internal.h"
+
+namespace mwmm {
+
+namespace {
+
+constexpr int kST = 64;  // tile: 64 word-layout rows x 64 k
+
+struct SplitParams {
+    const uint64_t *M;
+    int64_t ld;
+    int side;        // 0: M is rows x K (A); 1: M is K x rows (B, transposed on output)
+    int64_t rows;    // m (A) or n (B)
+    int64_t K;
+    int64_t rows_pad, nkb;
+    uint8_t *out;
+    int words;
+    uint64_t p;
+    uint64_t alpha, mu;  // FP64: radix and floor((2^64 - 1) / alpha)
+    int validate;
+    int *err;
+};
+
+__device__ __forceinline__ uint64_t load_tile_elem(const SplitParams &P, int64_t r, int64_t l) {
+    if (r >= P.rows || l >= P.K) return 0;
+    return P.side == 0 ? P.M[r * P.ld + l] : P.M[l * P.ld + r];
+}
+
+// Read a 64 x 64 tile of M (coalesced along M's contiguous dimension) into
+// shared memory as tile[row][k].
+__device__ __forceinline__ void load_tile(const SplitParams &P, uint64_t (*tile)[kST + 1], int64_t r0,
+                                          int64_t l0) {
+    const int t = threadIdx.x;
+    bool bad = false;
+#pragma unroll 4
+    for (int it = 0; it < (kST * kST) / 256; ++it) {
+        const int a = t / kST + it * (256 / kST), b = t % kST;
+        // side 0: a = row offset, b = k offset (contiguous);  side 1: a = k, b = row
+        const int rr = P.side == 0 ? a : b, ll = P.side == 0 ? b : a;
+        const uint64_t x = load_tile_elem(P, r0 + rr, l0 + ll);
+        bad |= (x >= P.p);
+        tile[rr][ll] = x;
+    }
+    if (P.validate && bad) atomicExch(P.err + 1, 1);
+    __syncthreads();
+}
+
+// Next Alg. 4 word of the running value T (exact division by alpha through
+// the reciprocal mu = floor((2^64 - 1) / alpha)); the last word is T itself.
+__device__ __forceinline__ double alg4_next(uint64_t &T, uint64_t alpha, uint64_t mu, bool last) {
+    if (last) return (double)T;
+    uint64_t R = __umul64hi(T, mu);
+    uint64_t rem = T - R * alpha;
+    while (rem >= alpha) {  // at most two corrections
+        ++R;
+        rem -= alpha;
+    }
+    T = R;
+    return (double)rem;
+}
+
+// Next balanced base-2^8 digit of the running signed value s; the last digit
+// is s itself.
+__device__ __forceinline__ float int8_next(int64_t &s, bool last) {
+    if (last) return (float)s;
+    const int64_t d = ((s + 128) & 255) - 128;
+    s = (s - d) >> 8;  // exact: s - d is a multiple of 256
+    return (float)d;
+}
+
+// FP64 form: a 64 x 64 tile covers 4 k-blocks of 16 doubles, 8 granules each.
+__global__ void __launch_bounds__(256) split_fp64_kernel(const __grid_constant__ SplitParams P) {
+    __shared__ uint64_t tile[kST][kST + 1];
+    const int64_t r0 = (int64_t)blockIdx.y * kST, l0 = (int64_t)blockIdx.x * kST;
+    load_tile(P, tile, r0, l0);
+    // units: (row, granule) with 32 granules (2 doubles) per row of the tile
+    for (int unit = threadIdx.x; unit < kST * 32; unit += 256) {
+        const int rr = unit / 32, gg = unit % 32;
+        const int64_t kb = (l0 / kF64KB) + gg / 8;
+        if (kb >= P.nkb) continue;
+        const int g = gg % 8;
+        uint64_t T0 = tile[rr][2 * gg], T1 = tile[rr][2 * gg + 1];
+        const int64_t r = r0 + rr;
+        for (int w = 0; w < P.words; ++w) {
+            const bool last = (w == P.words - 1);
+            const double w0 = alg4_next(T0, P.alpha, P.mu, last);
+            const double w1 = alg4_next(T1, P.alpha, P.mu, last);
+            uint8_t *dst = P.out + (((int64_t)w * P.nkb + kb) * P.rows_pad + r) * kTileBytes +
+                           ((g ^ (int)(r & 7)) * 16);
+            *reinterpret_cast<double2 *>(dst) = make_double2(w0, w1);
+        }
+    }
+}
+
+// INT8 form: a 64 x 64 tile is exactly one k-block of 64 bf16, 8 granules.
+__global__ void __launch_bounds__(256) split_int8_kernel(const __grid_constant__ SplitParams P) {
+    __shared__ uint64_t tile[kST][kST + 1];
+    const int64_t r0 = (int64_t)blockIdx.y * kST, l0 = (int64_t)blockIdx.x * kST;
+    load_tile(P, tile, r0, l0);
+    const int64_t kb = l0 / kTcKB;
+    const uint64_t half = (P.p - 1) / 2;
+    for (int unit = threadIdx.x; unit < kST * 8; unit += 256) {
+        const int rr = unit / 8, g = unit % 8;
+        int64_t s[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const uint64_t x = tile[rr][8 * g + e];
+            s[e] = (x <= half) ? (int64_t)x : (int64_t)x - (int64_t)P.p;
+        }
+        const int64_t r = r0 + rr;
+        for (int w = 0; w < P.words; ++w) {
+            const bool last = (w == P.words - 1);
+            __align__(16) __nv_bfloat16 h[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) h[e] = __float2bfloat16_rn(int8_next(s[e], last));
+            uint8_t *dst = P.out + (((int64_t)w * P.nkb + kb) * P.rows_pad + r) * kTileBytes +
+                           ((g ^ (int)(r & 7)) * 16);
+            *reinterpret_cast<uint4 *>(dst) = *reinterpret_cast<const uint4 *>(h);
+        }
+    }
+}
+
+}  // namespace
+
+int launch_split(const Plan &pl, int side, const uint64_t *M, int64_t ld, void *words, void *stream) {
+    SplitParams P;
+    P.M = M;
+    P.ld = ld;
+    P.side = side;
+    P.rows = side == 0 ? pl.m : pl.n;
+    P.K = pl.k;
+    P.rows_pad = side == 0 ? pl.A_rows : pl.B_rows;
+    P.nkb = pl.nkb;
+    P.out = static_cast<uint8_t *>(words);
+    P.words = side == 0 ? pl.u : pl.v;
+    P.p = pl.p;
+    P.alpha = side == 0 ? pl.alpha : pl.beta;
+    P.mu = P.alpha >= 2 ? (~uint64_t(0)) / P.alpha : 0;
+    P.validate = pl.validate;
+    P.err = pl.err_dev;
+    if (pl.nkb == 0 || P.rows_pad == 0) return 0;
+    const int64_t kcols = pl.nkb * pl.kb_elems;
+    dim3 grid((unsigned)((kcols + kST - 1) / kST), (unsigned)(P.rows_pad / kST));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (pl.form == MWMM_FORM_FP64) {
+        // Words equal to the input when u == 1 (alpha = p): Alg. 4 has no loop.
+        split_fp64_kernel<<<grid, 256, 0, s>>>(P);
+    } else {
+        split_int8_kernel<<<grid, 256, 0, s>>>(P);
+    }
+    return (int)cudaGetLastError();
+}
+
+}  // namespace mwmm

@@ -1,0 +1,272 @@
+"""Thin Python binding over libmwmm (include/mwmm.h): argument marshalling only.
+
+Every step of the product runs in the library's CUDA kernels; this module
+only turns torch tensors / numpy arrays into pointers, sizes and streams.
+PyTorch supplies device memory and streams.  If the library has not been
+built, or cannot be loaded, every call raises: there is no CPU fallback.
+
+The functions carry the C names (mwmm_plan, mwmm_matmul, ...); ``Plan`` is a
+small owner object around a plan handle.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmwmm.so")
+HEADER = os.path.join(os.path.dirname(_HERE), "include", "mwmm.h")
+
+MWMM_OK = 0
+STATUS = {0: "MWMM_OK", 1: "MWMM_ERR_ARG", 2: "MWMM_ERR_PRIME", 3: "MWMM_ERR_BOUND", 4: "MWMM_ERR_RANGE",
+          5: "MWMM_ERR_NOMEM", 6: "MWMM_ERR_BUDGET", 7: "MWMM_ERR_CUDA", 8: "MWMM_ERR_TIMEOUT",
+          9: "MWMM_ERR_BUSY", 10: "MWMM_ERR_UNSUPPORTED"}
+FORM_AUTO, FORM_FP64, FORM_INT8 = 0, 1, 2
+FORMS = {"auto": FORM_AUTO, "fp64": FORM_FP64, "int8": FORM_INT8}
+
+
+class MwmmError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = status
+        super().__init__("%s%s (%d: %s)" % (what + ": " if what else "", STATUS.get(status, "?"), status,
+                                            _status_str(status)))
+
+
+class PlanOpts(ctypes.Structure):
+    _fields_ = [("lambda_", ctypes.c_int64), ("validate", ctypes.c_int32), ("tc_chunk", ctypes.c_int32),
+                ("kc", ctypes.c_int64), ("reserved", ctypes.c_int32 * 8)]
+
+
+class PlanDesc(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int64), ("n", ctypes.c_int64), ("k", ctypes.c_int64), ("p", ctypes.c_uint64),
+                ("form", ctypes.c_int32), ("u", ctypes.c_int32), ("v", ctypes.c_int32),
+                ("alpha", ctypes.c_uint64), ("beta", ctypes.c_uint64),
+                ("lambda_", ctypes.c_int64), ("lambda_max", ctypes.c_int64), ("tc_chunk", ctypes.c_int64),
+                ("kc", ctypes.c_int64), ("nkc", ctypes.c_int32), ("nsums", ctypes.c_int32), ("q", ctypes.c_double),
+                ("kb_elems", ctypes.c_int64), ("nkb", ctypes.c_int64), ("A_rows", ctypes.c_int64),
+                ("B_rows", ctypes.c_int64), ("A_off", ctypes.c_uint64), ("B_off", ctypes.c_uint64),
+                ("S_off", ctypes.c_uint64), ("workspace_bytes", ctypes.c_uint64)]
+
+    def as_dict(self):
+        d = {}
+        for name, _ in self._fields_:
+            d[name.rstrip("_")] = getattr(self, name)
+        return d
+
+
+_lib: Optional[ctypes.CDLL] = None
+_vp = ctypes.c_void_p
+_i64 = ctypes.c_int64
+_u64 = ctypes.c_uint64
+
+
+def lib() -> ctypes.CDLL:
+    """Load libmwmm.so (raises if it is missing: no fallback path exists)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("libmwmm.so is not built (run python -m paper_2601_07508_b300.build); "
+                          "the mwmm product has no CPU fallback")
+    L = ctypes.CDLL(LIB_PATH)
+    L.mwmm_plan.argtypes = [ctypes.POINTER(_vp), _i64, _i64, _i64, _u64, ctypes.c_int, ctypes.c_int,
+                            ctypes.c_int, ctypes.POINTER(PlanOpts)]
+    L.mwmm_plan_info.argtypes = [_vp, ctypes.POINTER(PlanDesc)]
+    L.mwmm_workspace_size.argtypes = [_vp]
+    L.mwmm_workspace_size.restype = ctypes.c_size_t
+    L.mwmm_matmul.argtypes = [_vp, _vp, _i64, _vp, _i64, _vp, _i64, _vp, ctypes.c_size_t, _vp]
+    L.mwmm_matmul_host.argtypes = [_vp, _vp, _i64, _vp, _i64, _vp, _i64, _vp]
+    L.mwmm_plan_check.argtypes = [_vp, _vp]
+    L.mwmm_plan_destroy.argtypes = [_vp]
+    L.mwmm_plan_destroy.restype = None
+    L.mwmm_split.argtypes = [_vp, ctypes.c_int, _vp, _i64, _vp, _vp]
+    L.mwmm_fmod.argtypes = [_vp, _i64, _u64, _vp, _vp]
+    L.mwmm_mulmod.argtypes = [_vp, _vp, _i64, _u64, _vp, _vp]
+    L.mwmm_status_str.argtypes = [ctypes.c_int]
+    L.mwmm_status_str.restype = ctypes.c_char_p
+    L.mwmm_version.restype = ctypes.c_char_p
+    _lib = L
+    return L
+
+
+def _status_str(s: int) -> str:
+    try:
+        return lib().mwmm_status_str(s).decode()
+    except Exception:
+        return "?"
+
+
+def _check(st: int, what: str):
+    if st != MWMM_OK:
+        raise MwmmError(st, what)
+
+
+def declared_symbols():
+    """Names of the functions include/mwmm.h declares."""
+    with open(HEADER) as f:
+        text = f.read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(mwmm_\w+)\s*\(", text)))
+
+
+# --------------------------------------------------------------------------- marshalling
+def _stream_ptr(stream) -> Optional[int]:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _dev_ptr(t, dtypes=None) -> int:
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("expected a CUDA tensor")
+    if dtypes is not None and t.dtype not in dtypes:
+        raise TypeError("unexpected dtype %s" % t.dtype)
+    return t.data_ptr()
+
+
+def _u64_dtypes():
+    import torch
+    return (torch.int64, torch.uint64)
+
+
+def _ld(t) -> int:
+    if t.dim() != 2 or t.stride(1) != 1:
+        raise ValueError("expected a row-major 2-D matrix")
+    return max(t.stride(0), 1)
+
+
+# --------------------------------------------------------------------------- C-named calls
+def mwmm_plan(m: int, n: int, k: int, p: int, u: int = 0, v: int = 0, form="auto", lam: int = 0,
+              validate: bool = False, tc_chunk: int = 0, kc: int = 0) -> int:
+    if isinstance(form, str):
+        form = FORMS[form]
+    h = _vp()
+    o = PlanOpts()
+    o.lambda_ = lam
+    o.validate = 1 if validate else 0
+    o.tc_chunk = tc_chunk
+    o.kc = kc
+    _check(lib().mwmm_plan(ctypes.byref(h), m, n, k, p, u, v, form, ctypes.byref(o)), "mwmm_plan")
+    return h.value
+
+
+def mwmm_plan_info(h: int) -> dict:
+    d = PlanDesc()
+    _check(lib().mwmm_plan_info(h, ctypes.byref(d)), "mwmm_plan_info")
+    return d.as_dict()
+
+
+def mwmm_workspace_size(h: int) -> int:
+    return int(lib().mwmm_workspace_size(h))
+
+
+def mwmm_matmul(h: int, A, B, C, workspace=None, stream=None):
+    """C = A B mod p on device tensors (int64 or uint64 holding entries < p)."""
+    dt = _u64_dtypes()
+    ws_ptr, ws_bytes = None, 0
+    if workspace is not None:
+        ws_ptr, ws_bytes = _dev_ptr(workspace), workspace.numel() * workspace.element_size()
+    _check(lib().mwmm_matmul(h, _dev_ptr(A, dt), _ld(A), _dev_ptr(B, dt), _ld(B), _dev_ptr(C, dt), _ld(C),
+                             ws_ptr, ws_bytes, _stream_ptr(stream)), "mwmm_matmul")
+
+
+def mwmm_matmul_host(h: int, A: np.ndarray, B: np.ndarray, C: np.ndarray, stream=None):
+    """Same product with host arrays (uint64/int64, row-major)."""
+    for x in (A, B, C):
+        if x.dtype not in (np.uint64, np.int64) or not x.flags["C_CONTIGUOUS"]:
+            raise TypeError("host matrices must be C-contiguous uint64/int64")
+    _check(lib().mwmm_matmul_host(h, A.ctypes.data, max(A.shape[1], 1), B.ctypes.data, max(B.shape[1], 1),
+                                  C.ctypes.data, max(C.shape[1], 1), _stream_ptr(stream)), "mwmm_matmul_host")
+
+
+def mwmm_matmul_host_ptr(h: int, a_ptr: int, lda: int, b_ptr: int, ldb: int, c_ptr: int, ldc: int, stream=None):
+    _check(lib().mwmm_matmul_host(h, a_ptr, lda, b_ptr, ldb, c_ptr, ldc, _stream_ptr(stream)), "mwmm_matmul_host")
+
+
+def mwmm_plan_check(h: int, stream=None) -> int:
+    """Synchronise and return the device-side status (0 = ok)."""
+    return int(lib().mwmm_plan_check(h, _stream_ptr(stream)))
+
+
+def mwmm_plan_destroy(h: int):
+    lib().mwmm_plan_destroy(h)
+
+
+def mwmm_split(h: int, side: int, M, words, stream=None):
+    _check(lib().mwmm_split(h, side, _dev_ptr(M, _u64_dtypes()), _ld(M), _dev_ptr(words), _stream_ptr(stream)),
+           "mwmm_split")
+
+
+def mwmm_fmod(x, p: int, out, stream=None):
+    import torch
+    _check(lib().mwmm_fmod(_dev_ptr(x, (torch.float64,)), x.numel(), p, _dev_ptr(out, (torch.float64,)),
+                           _stream_ptr(stream)), "mwmm_fmod")
+
+
+def mwmm_mulmod(x, y, p: int, out, stream=None):
+    import torch
+    f = (torch.float64,)
+    _check(lib().mwmm_mulmod(_dev_ptr(x, f), _dev_ptr(y, f), x.numel(), p, _dev_ptr(out, f), _stream_ptr(stream)),
+           "mwmm_mulmod")
+
+
+def mwmm_status_str(s: int) -> str:
+    return _status_str(s)
+
+
+def mwmm_version() -> str:
+    return lib().mwmm_version().decode()
+
+
+# --------------------------------------------------------------------------- owner object
+class Plan:
+    """Owns a plan handle: ``Plan(m, n, k, p, form="int8")``, then ``.matmul(A, B)``."""
+
+    def __init__(self, m: int, n: int, k: int, p: int, u: int = 0, v: int = 0, form="auto", lam: int = 0,
+                 validate: bool = False, tc_chunk: int = 0, kc: int = 0):
+        self.handle = mwmm_plan(m, n, k, p, u, v, form, lam, validate, tc_chunk, kc)
+        self.info = mwmm_plan_info(self.handle)
+        self.workspace = None
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h:
+            try:
+                mwmm_plan_destroy(h)
+            except Exception:
+                pass
+            self.handle = None
+
+    @property
+    def workspace_bytes(self) -> int:
+        return int(self.info["workspace_bytes"])
+
+    def alloc_workspace(self, device="cuda"):
+        """Allocate the workspace through PyTorch (256-byte aligned by the caching allocator)."""
+        import torch
+        if self.workspace is None and self.workspace_bytes > 0:
+            self.workspace = torch.empty(self.workspace_bytes, dtype=torch.uint8, device=device)
+        return self.workspace
+
+    def matmul(self, A, B, C=None, stream=None):
+        import torch
+        if C is None:
+            C = torch.empty((self.info["m"], self.info["n"]), dtype=A.dtype, device=A.device)
+        mwmm_matmul(self.handle, A, B, C, self.alloc_workspace(A.device), stream)
+        return C
+
+    def matmul_host(self, A: np.ndarray, B: np.ndarray) -> np.ndarray:
+        C = np.empty((self.info["m"], self.info["n"]), dtype=np.uint64)
+        mwmm_matmul_host(self.handle, np.ascontiguousarray(A), np.ascontiguousarray(B), C)
+        return C
+
+    def check(self, stream=None) -> int:
+        return mwmm_plan_check(self.handle, stream)

@@ -1,0 +1,21 @@
+"""Host-side reading of the library's word layout (documented in include/mwmm.h)."""
+import numpy as np
+
+
+def unpack_words(buf: np.ndarray, words: int, nkb: int, rows_pad: int, kind: str) -> np.ndarray:
+    """buf: uint8 bytes of one side's word region.  Returns [words][rows_pad][nkb*kb_elems]
+    as float64 (FP64 words) or int32 (INT8 digits stored as bf16)."""
+    n = words * nkb * rows_pad * 128
+    a = np.asarray(buf[:n]).reshape(words, nkb, rows_pad, 8, 16)
+    r = np.arange(rows_pad) & 7
+    out = np.empty_like(a)
+    for g in range(8):
+        # logical granule g of row r sits at position g ^ (r & 7)
+        out[:, :, :, g, :] = a[:, :, np.arange(rows_pad), g ^ r, :]
+    if kind == "fp64":
+        el = out.reshape(words, nkb, rows_pad, 128).view(np.float64)          # 16 per chunk
+    else:
+        u16 = out.reshape(words, nkb, rows_pad, 128).view(np.uint16)          # 64 bf16 per chunk
+        el = (u16.astype(np.uint32) << 16).view(np.float32).astype(np.float64)
+    kbe = el.shape[-1]
+    return el.transpose(0, 2, 1, 3).reshape(words, rows_pad, nkb * kbe)

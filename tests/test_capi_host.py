@@ -1,0 +1,122 @@
+"""The C-ABI library without a GPU: it loads, exports every symbol that
+include/mwmm.h declares, and its planner (pure host logic) agrees with the
+oracle's block sizes and the paper's variant choices."""
+import ctypes
+import os
+
+import pytest
+
+from paper_2601_07508_b300 import build, inputs
+
+SWEEP = {b: inputs.largest_prime_below_pow2(b) for b in inputs.SWEEP_BITS}
+
+
+@pytest.fixture(scope="module")
+def M():
+    build.build()
+    from paper_2601_07508_b300 import mwmm
+    mwmm.lib()
+    return mwmm
+
+
+def test_library_exports_every_declared_symbol(M):
+    L = ctypes.CDLL(M.LIB_PATH)
+    names = M.declared_symbols()
+    assert len(names) >= 10
+    missing = [n for n in names if not hasattr(L, n)]
+    assert not missing, missing
+
+
+def test_status_strings(M):
+    assert M.mwmm_status_str(0) == "ok"
+    assert "prime" in M.mwmm_status_str(2) or "p must" in M.mwmm_status_str(2)
+    assert "sm_103a" in M.mwmm_version()
+
+
+@pytest.mark.parametrize("b", inputs.SWEEP_BITS)
+@pytest.mark.parametrize("uv", [(1, 1), (1, 2), (1, 3), (1, 4), (2, 2), (2, 3)])
+def test_fp64_plan_block_size_matches_oracle(M, oracle, b, uv):
+    p = SWEEP[b]
+    u, v = uv
+    lam = oracle.lam(p, u, v)
+    if lam < 1:
+        with pytest.raises(M.MwmmError) as e:
+            M.mwmm_plan(64, 64, 64, p, u, v, "fp64")
+        assert e.value.status == 3  # MWMM_ERR_BOUND
+        return
+    h = M.mwmm_plan(64, 64, 64, p, u, v, "fp64")
+    d = M.mwmm_plan_info(h)
+    M.mwmm_plan_destroy(h)
+    assert d["lambda_max"] == min(lam, 2 ** 63 - 1)
+    assert d["lambda"] == d["lambda_max"]
+    assert d["alpha"] == oracle.ceil_root(p, u) and d["beta"] == oracle.ceil_root(p, v)
+    assert d["q"] == 1.0 / p
+
+
+def test_fp64_bound_rule_of_the_sweep(M, oracle):
+    """(1,1) where its block size is >= 1, else (1,2), else (2,2): the rule the
+    bitsize sweep uses; it is reproduced here from the oracle's block sizes."""
+    expect = {}
+    for b, p in SWEEP.items():
+        for uv in ((1, 1), (1, 2), (2, 2)):
+            if oracle.lam(p, *uv) >= 1:
+                expect[b] = uv
+                break
+    assert expect == {20: (1, 1), 23: (1, 1), 26: (1, 1), 32: (1, 2), 40: (2, 2), 48: (2, 2), 52: (2, 2)}
+
+
+def test_fp64_auto_variant_follows_cost_model(M, oracle):
+    # With k large the modelled cost u v (1 + 6 / lambda) decides; the paper's
+    # Table 4 (GPU, square) picks (2,3) at 46-52 bits and (1,1) at small bitsizes.
+    for b, want in ((20, (1, 1)), (52, (2, 3)), (40, (2, 2))):
+        h = M.mwmm_plan(4096, 4096, 4096, SWEEP[b], 0, 0, "fp64")
+        d = M.mwmm_plan_info(h)
+        M.mwmm_plan_destroy(h)
+        assert (d["u"], d["v"]) == want, (b, d["u"], d["v"])
+
+
+@pytest.mark.parametrize("p", list(SWEEP.values()) + [5, 7, 257, (1 << 31) - 1])
+def test_int8_plan_digits_match_oracle(M, oracle, p):
+    h = M.mwmm_plan(100, 300, 5000, p, 0, 0, "int8")
+    d = M.mwmm_plan_info(h)
+    M.mwmm_plan_destroy(h)
+    u = oracle.int8_words(p)
+    assert (d["u"], d["v"], d["alpha"], d["nsums"]) == (u, u, 256, 2 * u - 1)
+    # INT32 sums hold kc * min(u, v) products of magnitude <= 2^14
+    assert d["kc"] % 64 == 0 and d["kc"] * min(u, u) * 2 ** 14 < 2 ** 31
+    assert d["nkc"] == -(-5000 // d["kc"])
+    assert d["tc_chunk"] == 1024 and d["tc_chunk"] * 2 ** 14 <= 2 ** 24
+    assert d["A_rows"] == 128 and d["B_rows"] == 512
+
+
+def test_plan_errors(M):
+    for p in (2, 4, 3, 1 << 52, (1 << 52) + 1, 1 << 60):
+        with pytest.raises(M.MwmmError) as e:
+            M.mwmm_plan(8, 8, 8, p)
+        assert e.value.status == 2
+    with pytest.raises(M.MwmmError) as e:
+        M.mwmm_plan(-1, 8, 8, SWEEP[40])
+    assert e.value.status == 1
+    with pytest.raises(M.MwmmError) as e:  # (1,1) cannot handle 40-bit primes
+        M.mwmm_plan(8, 8, 8, SWEEP[40], 1, 1, "fp64")
+    assert e.value.status == 3
+    with pytest.raises(M.MwmmError) as e:  # too few INT8 digits
+        M.mwmm_plan(8, 8, 8, SWEEP[52], 3, 3, "int8")
+    assert e.value.status == 3
+    with pytest.raises(M.MwmmError) as e:  # lambda override beyond the bound
+        M.mwmm_plan(8, 8, 8, SWEEP[48], 2, 2, "fp64", lam=32)
+    assert e.value.status == 3
+
+
+def test_workspace_layout_sizes(M):
+    p = SWEEP[40]
+    h = M.mwmm_plan(300, 200, 100, p, 2, 2, "fp64")
+    d = M.mwmm_plan_info(h)
+    M.mwmm_plan_destroy(h)
+    nkb = -(-100 // 16)
+    assert d["nkb"] == nkb and d["A_rows"] == 320 and d["B_rows"] == 256
+    assert d["B_off"] >= 2 * nkb * 320 * 128
+    assert d["workspace_bytes"] >= d["B_off"] + 2 * nkb * 256 * 128
+    h = M.mwmm_plan(0, 200, 100, p, 2, 2, "fp64")
+    assert M.mwmm_workspace_size(h) == 0
+    M.mwmm_plan_destroy(h)

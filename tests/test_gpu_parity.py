@@ -1,0 +1,253 @@
+"""Bit-exact parity of the CUDA path with the CPU oracle (needs a B300).
+
+Every call goes through libmwmm's C ABI (via the ctypes binding); every
+expected value comes from oracle/ on the same seeded inputs."""
+import numpy as np
+import pytest
+
+from paper_2601_07508_b300 import build, inputs
+from layout import unpack_words
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+SWEEP = {b: inputs.largest_prime_below_pow2(b) for b in inputs.SWEEP_BITS}
+P50 = inputs.largest_prime_below_pow2(50)
+P51 = inputs.largest_prime_below_pow2(51)
+
+
+@pytest.fixture(scope="module")
+def M():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    build.build()
+    from paper_2601_07508_b300 import mwmm
+    mwmm.lib()
+    return mwmm
+
+
+def dev(x: np.ndarray):
+    return torch.from_numpy(np.ascontiguousarray(x).view(np.int64)).cuda()
+
+
+def host(t) -> np.ndarray:
+    return t.cpu().numpy().view(np.uint64)
+
+
+def gpu_product(M, A, B, p, **kw):
+    m, k = A.shape
+    n = B.shape[1]
+    plan = M.Plan(m, n, k, p, **kw)
+    C = plan.matmul(dev(A), dev(B))
+    assert plan.check() == 0
+    return host(C), plan
+
+
+# ------------------------------------------------------------------ whole product
+@pytest.mark.parametrize("form", ["fp64", "int8"])
+def test_small_config_256cube_40bit(M, oracle, form):
+    """256^3, p = largest prime below 2^40, seed 0; (2,2) in the FP64 form."""
+    p = SWEEP[40]
+    A, B = inputs.problem(0, 256, 256, 256, p)
+    kw = dict(u=2, v=2) if form == "fp64" else {}
+    C, plan = gpu_product(M, A, B, p, form=form, **kw)
+    assert np.array_equal(C, oracle.matmul_mod(A, B, p))
+
+
+SHAPES = [(1, 1, 1), (5, 3, 7), (64, 64, 16), (100, 70, 50), (129, 65, 33), (130, 300, 257)]
+FP64_VARIANTS = [(1, 1), (1, 2), (1, 3), (1, 4), (2, 2), (2, 3)]
+
+
+@pytest.mark.parametrize("b", [20, 26, 32, 40, 48, 52])
+@pytest.mark.parametrize("uv", FP64_VARIANTS)
+def test_fp64_variants_ragged(M, oracle, b, uv):
+    p = SWEEP[b]
+    if oracle.lam(p, *uv) < 1:
+        pytest.skip("variant cannot handle this bitsize")
+    for seed, (m, n, k) in enumerate(SHAPES):
+        A, B = inputs.problem(100 * b + seed, m, n, k, p)
+        C, _ = gpu_product(M, A, B, p, form="fp64", u=uv[0], v=uv[1])
+        assert np.array_equal(C, oracle.matmul_mod(A, B, p)), (m, n, k)
+
+
+@pytest.mark.parametrize("lam", [1, 2, 3, 7, 16, 17])
+def test_fp64_block_size_boundaries(M, oracle, lam):
+    """Reductions at every lambda-th k-step (including inside a 16-wide k-block)."""
+    p = SWEEP[48]
+    A, B = inputs.problem(7, 70, 90, 100, p)
+    C, _ = gpu_product(M, A, B, p, form="fp64", u=2, v=2, lam=lam)
+    assert np.array_equal(C, oracle.matmul_mod(A, B, p))
+
+
+@pytest.mark.parametrize("b,uv", [(26, (1, 1)), (32, (1, 2)), (40, (2, 2)), (52, (2, 2)), (52, (2, 3))])
+def test_fp64_all_max_entries(M, oracle, b, uv):
+    """All entries p - 1: every word is at its maximum, so every chunk sum
+    reaches the largest value Prop. 3.3 allows."""
+    p = SWEEP[b]
+    A = np.full((70, 300), p - 1, dtype=np.uint64)
+    B = np.full((300, 90), p - 1, dtype=np.uint64)
+    C, _ = gpu_product(M, A, B, p, form="fp64", u=uv[0], v=uv[1])
+    assert np.all(C == 300 % p)
+
+
+@pytest.mark.parametrize("b", list(inputs.SWEEP_BITS) + [50])
+def test_int8_all_bitsizes_ragged(M, oracle, b):
+    p = SWEEP.get(b, P50)
+    for seed, (m, n, k) in enumerate(SHAPES + [(300, 520, 1000)]):
+        A, B = inputs.problem(1000 + 10 * b + seed, m, n, k, p)
+        C, _ = gpu_product(M, A, B, p, form="int8")
+        assert np.array_equal(C, oracle.matmul_mod(A, B, p)), (m, n, k)
+
+
+@pytest.mark.parametrize("tc_chunk,kc", [(64, 0), (192, 0), (1024, 64), (512, 320)])
+def test_int8_chunk_boundaries(M, oracle, tc_chunk, kc):
+    """FP32 chunks of 1..16 k-blocks and INT32 K-ranges of 1..5 k-blocks."""
+    p = SWEEP[52]
+    A, B = inputs.problem(11, 200, 300, 777, p)
+    C, _ = gpu_product(M, A, B, p, form="int8", tc_chunk=tc_chunk, kc=kc)
+    assert np.array_equal(C, oracle.matmul_mod(A, B, p))
+
+
+def _extreme(p: int, u: int, digit: int):
+    """(entry, L): the entry whose L lowest balanced digits all equal `digit`
+    and whose other digits are 0, with L <= u - 1 as large as the signed range
+    [-(p-1)/2, (p-1)/2] allows."""
+    for L in range(u - 1, 0, -1):
+        s = digit * (256 ** L - 1) // 255
+        if abs(s) <= (p - 1) // 2:
+            return (s if s >= 0 else s + p), L
+    raise ValueError("no room for an extreme digit pattern")
+
+
+@pytest.mark.parametrize("b", [20, 40, 52])
+@pytest.mark.parametrize("da,db", [(-128, -128), (127, 127), (-128, 127)])
+def test_int8_extreme_digits_fill_the_fp32_chunk(M, oracle, b, da, db):
+    """Digits at the ends of [-128, 127] make every product +-2^14 (or -16256),
+    so a full 1024-product chunk reaches |sum| = 2^24: the exactness limit of
+    the FP32 tensor-memory accumulator."""
+    p = SWEEP[b]
+    u = oracle.int8_words(p)
+    (a, La), (bb, Lb) = _extreme(p, u, da), _extreme(p, u, db)
+    Aw = oracle.split_signed8(np.array([a], np.uint64), p, u)[:, 0]
+    Bw = oracle.split_signed8(np.array([bb], np.uint64), p, u)[:, 0]
+    assert list(Aw) == [da] * La + [0] * (u - La) and list(Bw) == [db] * Lb + [0] * (u - Lb)
+    A = np.full((130, 1024 + 64), a, dtype=np.uint64)
+    B = np.full((1024 + 64, 260), bb, dtype=np.uint64)
+    C, _ = gpu_product(M, A, B, p, form="int8")
+    assert np.all(C == (a * bb * (1024 + 64)) % p)
+
+
+@pytest.mark.parametrize("form", ["fp64", "int8"])
+def test_leading_dimensions_and_degenerate_shapes(M, oracle, form):
+    p = SWEEP[32]
+    A, B = inputs.problem(5, 40, 30, 20, p)
+    Abig = np.zeros((40, 33), np.uint64)
+    Abig[:, :20] = A
+    Bbig = np.zeros((20, 35), np.uint64)
+    Bbig[:, :30] = B
+    plan = M.Plan(40, 30, 20, p, form=form)
+    Cbig = torch.zeros((40, 41), dtype=torch.int64, device="cuda")
+    M.mwmm_matmul(plan.handle, dev(Abig)[:, :20], dev(Bbig)[:, :30], Cbig[:, :30], stream=None)
+    assert plan.check() == 0
+    got = host(Cbig)
+    assert np.array_equal(got[:, :30], oracle.matmul_mod(A, B, p))
+    assert np.all(got[:, 30:] == 0)
+    # k = 0: empty sum
+    plan0 = M.Plan(7, 9, 0, p, form=form)
+    C0 = plan0.matmul(torch.zeros((7, 1), dtype=torch.int64, device="cuda"),
+                      torch.zeros((1, 9), dtype=torch.int64, device="cuda"),
+                      torch.full((7, 9), 5, dtype=torch.int64, device="cuda"))
+    assert plan0.check() == 0 and int(C0.abs().sum()) == 0
+
+
+@pytest.mark.parametrize("form", ["fp64", "int8"])
+def test_host_entry_point(M, oracle, form):
+    p = SWEEP[48]
+    A, B = inputs.problem(21, 150, 140, 130, p)
+    plan = M.Plan(150, 140, 130, p, form=form)
+    C = plan.matmul_host(A, B)
+    assert np.array_equal(C, oracle.matmul_mod(A, B, p))
+
+
+def test_validation_reports_entries_out_of_range(M):
+    p = SWEEP[40]
+    A, B = inputs.problem(3, 64, 64, 64, p)
+    A[3, 5] = p  # not in F_p
+    plan = M.Plan(64, 64, 64, p, form="int8", validate=True)
+    plan.matmul(dev(A), dev(B))
+    assert plan.check() == 4  # MWMM_ERR_RANGE
+    A[3, 5] = 0
+    plan.matmul(dev(A), dev(B))
+    assert plan.check() == 0
+
+
+# ------------------------------------------------------------------ single steps
+@pytest.mark.parametrize("form,b,uv", [("fp64", 40, (2, 2)), ("fp64", 52, (2, 3)), ("fp64", 32, (1, 4)),
+                                       ("int8", 52, None), ("int8", 23, None)])
+def test_split_words_match_oracle(M, oracle, form, b, uv):
+    p = SWEEP[b]
+    m, n, k = 70, 90, 150
+    A, B = inputs.problem(31, m, n, k, p)
+    kw = dict(u=uv[0], v=uv[1]) if uv else {}
+    plan = M.Plan(m, n, k, p, form=form, **kw)
+    d = plan.info
+    for side, Mx, rows in ((0, A, m), (1, B, n)):
+        words = d["u"] if side == 0 else d["v"]
+        rows_pad = d["A_rows"] if side == 0 else d["B_rows"]
+        buf = torch.zeros(words * d["nkb"] * rows_pad * 128, dtype=torch.uint8, device="cuda")
+        M.mwmm_split(plan.handle, side, dev(Mx), buf)
+        torch.cuda.synchronize()
+        W = unpack_words(buf.cpu().numpy(), words, d["nkb"], rows_pad, form)
+        src = Mx if side == 0 else Mx.T.copy()       # rows x k
+        if form == "fp64":
+            ref = oracle.split_alpha(src, d["alpha"] if side == 0 else d["beta"], words).astype(np.float64)
+        else:
+            ref = oracle.split_signed8(src, p, words).astype(np.float64)
+        assert np.array_equal(W[:, :rows, :k], ref)
+        assert np.all(W[:, rows:, :] == 0) and np.all(W[:, :, k:] == 0)
+
+
+@pytest.mark.parametrize("b", [20, 52])
+def test_int8_diagonal_sums_match_oracle(M, oracle, b):
+    """S_s = sum_{i+j=s} A_i B_j read from the workspace after a product."""
+    p = SWEEP[b]
+    m, n, k = 130, 260, 700
+    A, B = inputs.problem(41, m, n, k, p)
+    plan = M.Plan(m, n, k, p, form="int8", kc=256)
+    ws = plan.alloc_workspace()
+    plan.matmul(dev(A), dev(B))
+    assert plan.check() == 0
+    d = plan.info
+    S = ws[d["S_off"]:d["S_off"] + d["nsums"] * d["nkc"] * d["A_rows"] * d["B_rows"] * 4]
+    S = S.cpu().numpy().view(np.int32).reshape(d["nsums"], d["nkc"], d["A_rows"], d["B_rows"])
+    u = d["u"]
+    Aw = oracle.split_signed8(A, p, u)
+    Bw = oracle.split_signed8(B, p, u)
+    for kc in range(d["nkc"]):
+        sl = slice(kc * d["kc"], min(k, (kc + 1) * d["kc"]))
+        ref = oracle.diag_sums(np.ascontiguousarray(Aw[:, :, sl]), np.ascontiguousarray(Bw[:, sl, :]))
+        assert np.array_equal(S[:, kc, :m, :n].astype(np.int64), ref)
+
+
+@pytest.mark.parametrize("p", [5, 7, 65521, SWEEP[26], SWEEP[40], P50, P51, SWEEP[52]])
+def test_fmod_alg1_matches_x_mod_p(M, oracle, p):
+    xs = np.concatenate([
+        inputs.uniform_mod(p % 997, 1, 20000, 1 << 53).astype(np.float64),
+        np.array([0, 1, p - 1, p, p + 1, 2 * p - 1, 2.0 ** 53, 2.0 ** 53 - 1, float(p) * 2.0 ** 51], np.float64),
+        (np.arange(1, 2001, dtype=np.float64) * 2.0 ** 40)])
+    xs = xs[xs <= float(p) * 2.0 ** 51]
+    out = torch.empty(xs.size, dtype=torch.float64, device="cuda")
+    M.mwmm_fmod(torch.from_numpy(xs).cuda(), p, out)
+    got = out.cpu().numpy()
+    assert np.array_equal(got.astype(np.uint64), oracle.mod_vec(xs, p))
+    assert np.all(got == np.floor(got))
+
+
+@pytest.mark.parametrize("p", [5, 7, 65521, SWEEP[26], SWEEP[40], P50, P51, SWEEP[52]])
+def test_mulmod_alg2_matches_xy_mod_p(M, oracle, p):
+    x = np.concatenate([inputs.uniform_mod(3, 1, 20000, p), np.array([p - 1, p - 1, 0, 1], np.uint64)])
+    y = np.concatenate([inputs.uniform_mod(3, 2, 20000, p), np.array([p - 1, 1, p - 1, p - 1], np.uint64)])
+    out = torch.empty(x.size, dtype=torch.float64, device="cuda")
+    M.mwmm_mulmod(torch.from_numpy(x.astype(np.float64)).cuda(), torch.from_numpy(y.astype(np.float64)).cuda(),
+                  p, out)
+    assert np.array_equal(out.cpu().numpy().astype(np.uint64), oracle.mulmod_vec(x, y, p))
