@@ -1,0 +1,428 @@
+#!/usr/bin/env python
+"""Benchmark: modular 2mnk GOP/s vs prime bitsize, INT8-word vs FP64 form.
+
+Workload (one "step"): the bitsize sweep m = n = k = 4096, one product
+C = A B mod p for each b in {20, 23, 26, 32, 40, 48, 52}, p the largest prime
+below 2^b, entries uniform in [0, p) (seeded, synthetic).  The headline value
+runs the library's default form (INT8-word digits on the tcgen05 tensor
+pipe); the FP64 form (the paper's method, (1,1) / (1,2) / (2,2) chosen by the
+block-size bound) is timed on the same inputs and reported per bitsize.
+
+    python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+Under torchrun each rank runs the sweep on its own GPU with its own seeds
+(independent problems, weak scaling); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2601_07508_b300 import inputs  # noqa: E402
+
+METRIC = "modular 2mnk GOP/s vs prime bitsize, INT8-word vs FP64 form; serve p50/p99"
+FP64_NOMINAL_GFLOPS = 1250.0  # B300 FP64 (DFMA) nominal, 148 SMs at 2032 MHz
+FALLBACK_PEAKS = {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0}
+
+
+def parse_args():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="mwmm", choices=["mwmm", "reference"])
+    ap.add_argument("--size", type=int, default=4096, help="m = n = k")
+    ap.add_argument("--bits", default=",".join(str(b) for b in inputs.SWEEP_BITS))
+    ap.add_argument("--no-fp64", action="store_true", help="skip the per-bitsize FP64-form timing")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------- helpers
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    return dict(FALLBACK_PEAKS), "fallback"
+
+
+def fp64_bound_rule(p: int):
+    """(1,1) where its block size is >= 1, else (1,2), else (2,2)."""
+    from paper_2601_07508_b300 import mwmm
+    for uv in ((1, 1), (1, 2), (2, 2)):
+        try:
+            h = mwmm.mwmm_plan(8, 8, 8, p, uv[0], uv[1], "fp64")
+        except mwmm.MwmmError:
+            continue
+        mwmm.mwmm_plan_destroy(h)
+        return uv
+    raise RuntimeError("no FP64 variant for p=%d" % p)
+
+
+def profile_traffic():
+    """DRAM bytes per launch of the tcgen05 kernel from the committed ncu
+    summary, or None when the kernel source changed since it was taken."""
+    path = os.path.join(ROOT, "profiles", "gemm_tc_sweep4096.md")
+    src = os.path.join(ROOT, "paper_2601_07508_b300", "csrc", "gemm_tc.cu")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        text = f.read()
+    m = re.search(r"source_sha256:\s*([0-9a-f]{64})", text)
+    t = re.search(r"traffic_bytes_per_launch:\s*(\{[^}]*\})", text)
+    if not m or not t:
+        return None
+    with open(src, "rb") as f:
+        if hashlib.sha256(f.read()).hexdigest() != m.group(1):
+            return None
+    return {int(k): float(v) for k, v in json.loads(t.group(1)).items()}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 7:
+                    continue
+                try:
+                    sm.append(float(parts[0]))
+                    smax.append(float(parts[1]))
+                except ValueError:
+                    continue
+                for name, val in zip(names, parts[3:7]):
+                    if val.lower() == "active":
+                        reasons.add(name)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def gpu_index(local_rank: int) -> int:
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    ids = [x.strip() for x in vis.split(",") if x.strip()]
+    if ids and ids[local_rank if local_rank < len(ids) else 0].isdigit():
+        return int(ids[local_rank if local_rank < len(ids) else 0])
+    return local_rank
+
+
+# ----------------------------------------------------------------------------- CPU oracle
+def oracle_sample(bits, size, seconds, rank_seed=0):
+    """Time the oracle on the first R rows of C per bitsize (same inputs as the
+    GPU run); R is calibrated so that the whole sample takes about `seconds`."""
+    from oracle import oracle as O
+    O.lib()
+    probs = {}
+    for b in bits:
+        p = inputs.largest_prime_below_pow2(b)
+        probs[b] = (p, inputs.matrix(b + rank_seed, inputs.STREAM_A, 64, size, p),
+                    inputs.matrix(b + rank_seed, inputs.STREAM_B, size, size, p))
+    # calibrate on 4 rows of the widest prime
+    b0 = max(bits)
+    p, A, B = probs[b0]
+    t0 = time.perf_counter()
+    O.matmul_mod_rows(A, B, p, 0, 4)
+    rate = 4 / max(time.perf_counter() - t0, 1e-6)  # rows per second
+    rows = int(max(1, min(64, rate * seconds / len(bits))))
+    ops, t = 0.0, 0.0
+    for b in bits:
+        p, A, B = probs[b]
+        t0 = time.perf_counter()
+        O.matmul_mod_rows(A, B, p, 0, rows)
+        t += time.perf_counter() - t0
+        ops += 2.0 * rows * size * size
+    return {"value": ops / t / 1e9, "unit": "GOP/s", "cores": O.num_threads(), "kind": "oracle",
+            "sample": "first %d rows of C (x %d cols, k = %d) per bitsize b in %s; 128-bit integer "
+                      "accumulation, one %% p per entry" % (rows, size, size, list(bits)),
+            "seconds": t}, rows
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    bits = [int(x) for x in args.bits.split(",")]
+    cb, rows = oracle_sample(bits, args.size, max(1.0, min(args.cpu_seconds, 10.0)))
+    from oracle import oracle as O
+    probs = {}
+    for b in bits:
+        p = inputs.largest_prime_below_pow2(b)
+        probs[b] = (p, inputs.matrix(b, inputs.STREAM_A, rows, args.size, p),
+                    inputs.matrix(b, inputs.STREAM_B, args.size, args.size, p))
+    wrows = max(1, rows // 8)
+    for _ in range(args.warmup):
+        for b in bits:
+            p, A, B = probs[b]
+            O.matmul_mod_rows(A, B, p, 0, wrows)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for b in bits:
+            p, A, B = probs[b]
+            O.matmul_mod_rows(A, B, p, 0, rows)
+    dt = time.perf_counter() - t0
+    ops = 2.0 * rows * args.size * args.size * len(bits) * args.steps
+    value = ops / dt / 1e9
+    sample = cb["sample"]
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GOP/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int128",
+            "data": "synthetic (seeded, entries uniform in [0,p))",
+            "config": workload_config(args, bits),
+            "cpu_baseline": {"value": value, "unit": "GOP/s", "cores": cb["cores"], "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "GOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def workload_config(args, bits):
+    return {"workload": "bitsize sweep: m = n = k = %d, one product C = A B mod p per b in %s, p the largest "
+                        "prime below 2^b; headline form: INT8-word digits on the tcgen05 tensor pipe (library "
+                        "default); FP64 form ((1,1)/(1,2)/(2,2) by the block-size bound) timed per bitsize"
+                        % (args.size, bits),
+            "m": args.size, "n": args.size, "k": args.size, "bits": bits,
+            "l2": "no flush: each product reads %d MB of fresh A, B (> 126 MB L2)"
+                  % (2 * args.size * args.size * 8 // 2 ** 20),
+            "parallelism": "independent problems per GPU (no collective in the data path)"}
+
+
+# ----------------------------------------------------------------------------- main arm
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    from paper_2601_07508_b300 import mwmm
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", torch.cuda.current_device())
+    bits = [int(x) for x in args.bits.split(",")]
+    n = args.size
+    seed_off = 1000 * rank
+
+    # CPU baseline first (before any GPU work; rank 0 at N = 1 only)
+    cpu_baseline = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu_baseline, _ = oracle_sample(bits, n, args.cpu_seconds)
+        cpu_baseline.pop("seconds", None)
+
+    mwmm.lib()
+    probs = []
+    for b in bits:
+        p = inputs.largest_prime_below_pow2(b)
+        A, B = inputs.problem(b + seed_off, n, n, n, p)
+        probs.append((b, p, A, B))
+
+    def to_dev(x):
+        return torch.from_numpy(x.view(np.int64)).to(dev)
+
+    dA = [to_dev(A) for (_, _, A, _) in probs]
+    dB = [to_dev(B) for (_, _, _, B) in probs]
+    dC = [torch.empty((n, n), dtype=torch.int64, device=dev) for _ in probs]
+    plans = [mwmm.Plan(n, n, n, p, form="int8") for (_, p, _, _) in probs]
+    for pl in plans:
+        pl.alloc_workspace(dev)
+        mwmm.mwmm_plan_set_timing(pl.handle, True)
+
+    def step():
+        for i, pl in enumerate(plans):
+            pl.matmul(dA[i], dB[i], dC[i])
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    for pl in plans:
+        assert pl.check() == 0, "device-side error during warm-up"
+        mwmm.mwmm_plan_timing(pl.handle)  # discard warm-up timings
+
+    sampler = ClockSampler(gpu_index(local))
+    sampler.start()
+    time.sleep(0.3)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        step()
+    e1.record()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1)
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    for pl in plans:
+        assert pl.check() == 0, "device-side error in the timed region"
+
+    flop_per_step = 2.0 * n * n * n * len(bits)
+    value = flop_per_step * args.steps * world / (ms / 1e3) / 1e9
+
+    # per-bitsize phases of the INT8 form (CUDA events on the launching stream)
+    per_bits, launches = {}, 0
+    gemm_flops, gemm_ms = 0.0, 0.0
+    for (b, p, _, _), pl in zip(probs, plans):
+        t = mwmm.mwmm_plan_timing(pl.handle)
+        launches += t["launches"]
+        d = pl.info
+        calls = max(t["calls"], 1)
+        words = d["u"] * d["v"]
+        gemm_flops += 2.0 * words * n ** 3 * calls
+        gemm_ms += t["gemm_ms"]
+        per_bits[str(b)] = {
+            "p": p, "int8_words": [d["u"], d["v"]], "int8_gops": 2.0 * n ** 3 / (t["total_ms"] / calls) / 1e6,
+            "int8_ms": t["total_ms"] / calls,
+            "int8_phase_ms": {"split_a": t["split_a_ms"] / calls, "split_b": t["split_b_ms"] / calls,
+                              "word_products": t["gemm_ms"] / calls, "recombine": t["recombine_ms"] / calls},
+            "int8_tensor_tflops": 2.0 * words * n ** 3 / (t["gemm_ms"] / calls) / 1e9,
+        }
+
+    peaks, peak_kind = load_peaks()
+    achieved = gemm_flops / (gemm_ms / 1e3) / 1e12
+    traffic = profile_traffic()
+    if traffic is not None:
+        tr = [traffic.get(b) for b in bits]
+        traffic_per_launch = None if any(x is None for x in tr) else sum(tr) / len(tr)
+    else:
+        traffic_per_launch = None
+    roofline = {"bound": "tensor", "kernel": "gemm_tc_kernel (tcgen05.mma kind::f16, INT8 digits in bf16)",
+                "achieved": achieved, "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
+                "frac": achieved / peaks["bf16_tflops"], "traffic": traffic_per_launch,
+                "peak_kind": "%s bf16 dense burst (cuBLAS); sustained %.1f -> frac %.3f" % (
+                    peak_kind, peaks.get("bf16_tflops_sustained", 0.0),
+                    achieved / peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])),
+                "algorithmic": "2 u v m n k word-product flops per launch (u, v INT8 digits per side)"}
+
+    # FP64 form per bitsize (same inputs), rank 0 only
+    if not args.no_fp64 and rank == 0:
+        for i, (b, p, _, _) in enumerate(probs):
+            uv = fp64_bound_rule(p)
+            pl = mwmm.Plan(n, n, n, p, uv[0], uv[1], form="fp64")
+            pl.alloc_workspace(dev)
+            Cf = torch.empty((n, n), dtype=torch.int64, device=dev)
+            pl.matmul(dA[i], dB[i], Cf)  # warm-up
+            torch.cuda.synchronize()
+            mwmm.mwmm_plan_set_timing(pl.handle, True)
+            pl.matmul(dA[i], dB[i], Cf)
+            t = mwmm.mwmm_plan_timing(pl.handle)
+            assert pl.check() == 0
+            same = bool(torch.equal(Cf, dC[i]))
+            d = pl.info
+            fl = 2.0 * uv[0] * uv[1] * n ** 3
+            e = per_bits[str(b)]
+            e.update({"fp64_uv": list(uv), "fp64_lambda": d["lambda"], "fp64_ms": t["total_ms"],
+                      "fp64_gops": 2.0 * n ** 3 / t["total_ms"] / 1e6,
+                      "fp64_pipe_gflops": fl / t["gemm_ms"] / 1e6,
+                      "fp64_pipe_frac": fl / t["gemm_ms"] / 1e6 / FP64_NOMINAL_GFLOPS,
+                      "int8_over_fp64": t["total_ms"] / e["int8_ms"],
+                      "fp64_equals_int8": same})
+            del pl, Cf
+            torch.cuda.empty_cache()
+
+    # end to end through the host entry point (pinned buffers, copies timed)
+    e2e = None
+    if not args.no_e2e:
+        hA = [torch.from_numpy(A.view(np.int64)).pin_memory() for (_, _, A, _) in probs]
+        hB = [torch.from_numpy(B.view(np.int64)).pin_memory() for (_, _, _, B) in probs]
+        hC = [torch.empty((n, n), dtype=torch.int64).pin_memory() for _ in probs]
+        for pl in plans:
+            mwmm.mwmm_plan_set_timing(pl.handle, False)
+
+        def host_step():
+            for i, pl in enumerate(plans):
+                mwmm.mwmm_matmul_host_ptr(pl.handle, hA[i].data_ptr(), n, hB[i].data_ptr(), n,
+                                          hC[i].data_ptr(), n)
+
+        host_step()
+        esteps = max(1, min(args.steps, 3))
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(esteps):
+            host_step()
+        dt = time.perf_counter() - t0
+        if dist:
+            t = torch.tensor([dt], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dt = float(t.item())
+        e2e = {"value": flop_per_step * esteps * world / dt / 1e9, "unit": "GOP/s",
+               "h2d_bytes_per_step": 2 * n * n * 8 * len(bits), "d2h_bytes_per_step": n * n * 8 * len(bits),
+               "steps": esteps, "api": "mwmm_matmul_host (pinned host buffers)"}
+        same = all(torch.equal(hC[i], dC[i].cpu()) for i in range(len(plans)))
+        e2e["matches_device_result"] = same
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "GOP/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
+                "dtype_detail": "INT8 digits (exact in bf16) x bf16 -> FP32 tensor memory (exact, <= 2^24) -> "
+                                "INT32 sums -> 64-bit integer recombination mod p",
+                "data": "synthetic (seeded, entries uniform in [0,p))",
+                "config": workload_config(args, bits),
+                "roofline": roofline, "cpu_baseline": cpu_baseline, "e2e": e2e,
+                "gpu_launches": launches * world, "clocks": clocks, "per_bitsize": per_bits}
+        print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -179,6 +179,22 @@ mwmm_status mwmm_fmod(const double *dx, int64_t count, uint64_t p, double *dout,
 mwmm_status mwmm_mulmod(const double *dx, const double *dy, int64_t count, uint64_t p,
                         double *dout, void *stream);
 
+/* ---- per-phase timing (CUDA events on the call's stream) ----
+ * When timing is on, every mwmm_matmul / mwmm_matmul_host call records events
+ * around its phases: the split of A, the split of B (Alg. 4 or INT8 digits),
+ * the word products (FP64 form: the fused kernel, which also reduces and
+ * recombines; INT8 form: the tcgen05 kernel), and the recombination (INT8
+ * form).  mwmm_plan_timing synchronises on the recorded events, returns the
+ * times summed over the calls since the previous query, and resets them. */
+typedef struct {
+    double split_a_ms, split_b_ms, gemm_ms, recombine_ms, total_ms;
+    int64_t calls;     /* products timed */
+    int64_t launches;  /* kernels launched by those products */
+} mwmm_timing;
+
+mwmm_status mwmm_plan_set_timing(mwmm_plan_t plan, int on);
+mwmm_status mwmm_plan_timing(mwmm_plan_t plan, mwmm_timing *out);
+
 const char *mwmm_status_str(mwmm_status s);
 const char *mwmm_version(void);
 

@@ -3,6 +3,7 @@
 
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "mwmm_internal.h"
 
@@ -10,6 +11,11 @@ using mwmm::Plan;
 
 struct mwmm_plan_s {
     Plan pl;
+    // per-phase timing: one set of 5 events per timed call
+    bool timing = false;
+    std::vector<cudaEvent_t> pool;     // free events
+    std::vector<cudaEvent_t> pending;  // 5 per timed call, in record order
+    int64_t pending_launches = 0;
 };
 
 namespace {
@@ -56,25 +62,62 @@ bool valid_ld(const Plan &pl, int64_t lda, int64_t ldb, int64_t ldc) {
     return lda >= (pl.k > 0 ? pl.k : 1) && ldb >= (pl.n > 0 ? pl.n : 1) && ldc >= (pl.n > 0 ? pl.n : 1);
 }
 
+// Events for one timed call (5 of them), or nulls when timing is off.
+struct PhaseEvents {
+    cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+};
+
+mwmm_status take_events(mwmm_plan_s *h, PhaseEvents &pe) {
+    if (!h->timing) return MWMM_OK;
+    for (int i = 0; i < 5; ++i) {
+        if (h->pool.empty()) {
+            cudaEvent_t e;
+            if (cudaEventCreate(&e) != cudaSuccess) return MWMM_ERR_CUDA;
+            h->pool.push_back(e);
+        }
+        pe.ev[i] = h->pool.back();
+        h->pool.pop_back();
+        h->pending.push_back(pe.ev[i]);
+    }
+    return MWMM_OK;
+}
+
+inline void rec(cudaEvent_t e, cudaStream_t s) {
+    if (e) cudaEventRecord(e, s);
+}
+
 // Run the product on device pointers with a given workspace.
-mwmm_status run_product(Plan &pl, const uint64_t *dA, int64_t lda, const uint64_t *dB, int64_t ldb,
+mwmm_status run_product(mwmm_plan_s *h, const uint64_t *dA, int64_t lda, const uint64_t *dB, int64_t ldb,
                         uint64_t *dC, int64_t ldc, uint8_t *ws, void *stream) {
+    Plan &pl = h->pl;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (pl.m == 0 || pl.n == 0) return MWMM_OK;
     if (pl.k == 0)  // empty sum: C = 0
         return cuda_status((int)cudaMemset2DAsync(dC, (size_t)ldc * 8, 0, (size_t)pl.n * 8, (size_t)pl.m, s));
+    PhaseEvents pe;
+    mwmm_status st = take_events(h, pe);
+    if (st != MWMM_OK) return st;
+    rec(pe.ev[0], s);
     int e = mwmm::launch_split(pl, 0, dA, lda, ws + pl.A_off, stream);
     if (e) return cuda_status(e);
+    rec(pe.ev[1], s);
     e = mwmm::launch_split(pl, 1, dB, ldb, ws + pl.B_off, stream);
     if (e) return cuda_status(e);
+    rec(pe.ev[2], s);
     if (pl.form == MWMM_FORM_FP64) {
         e = mwmm::launch_gemm_fp64(pl, ws + pl.A_off, ws + pl.B_off, dC, ldc, pl.err_dev, stream);
+        rec(pe.ev[3], s);
+        rec(pe.ev[4], s);
+        if (h->timing) h->pending_launches += 3;
         return cuda_status(e);
     }
     int32_t *S = reinterpret_cast<int32_t *>(ws + pl.S_off);
     e = mwmm::launch_gemm_tc(pl, ws + pl.A_off, ws + pl.B_off, S, pl.err_dev, stream);
     if (e) return cuda_status(e);
+    rec(pe.ev[3], s);
     e = mwmm::launch_recombine(pl, S, dC, ldc, stream);
+    rec(pe.ev[4], s);
+    if (h->timing) h->pending_launches += 4;
     return cuda_status(e);
 }
 
@@ -149,7 +192,7 @@ mwmm_status mwmm_matmul(mwmm_plan_t plan, const uint64_t *dA, int64_t lda, const
         if (st != MWMM_OK) return st;
         workspace = pl.own_ws;
     }
-    return run_product(pl, dA, lda, dB, ldb, dC, ldc, static_cast<uint8_t *>(workspace), stream);
+    return run_product(plan, dA, lda, dB, ldb, dC, ldc, static_cast<uint8_t *>(workspace), stream);
 }
 
 mwmm_status mwmm_plan_check(mwmm_plan_t plan, void *stream) {
@@ -208,7 +251,7 @@ mwmm_status mwmm_matmul_host(mwmm_plan_t plan, const uint64_t *hA, int64_t lda, 
                                   cudaMemcpyHostToDevice, s);
         if (e != cudaSuccess) return MWMM_ERR_CUDA;
     }
-    st = run_product(pl, dA, pl.k > 0 ? pl.k : 1, dB, pl.n, dC, pl.n, static_cast<uint8_t *>(pl.own_ws), stream);
+    st = run_product(plan, dA, pl.k > 0 ? pl.k : 1, dB, pl.n, dC, pl.n, static_cast<uint8_t *>(pl.own_ws), stream);
     if (st != MWMM_OK) return st;
     e = cudaMemcpy2DAsync(hC, (size_t)ldc * 8, dC, (size_t)pl.n * 8, (size_t)pl.n * 8, (size_t)pl.m,
                           cudaMemcpyDeviceToHost, s);
@@ -216,8 +259,40 @@ mwmm_status mwmm_matmul_host(mwmm_plan_t plan, const uint64_t *hA, int64_t lda, 
     return mwmm_plan_check(plan, stream);
 }
 
+mwmm_status mwmm_plan_set_timing(mwmm_plan_t plan, int on) {
+    if (!plan) return MWMM_ERR_ARG;
+    plan->timing = on != 0;
+    return MWMM_OK;
+}
+
+mwmm_status mwmm_plan_timing(mwmm_plan_t plan, mwmm_timing *out) {
+    if (!plan || !out) return MWMM_ERR_ARG;
+    std::memset(out, 0, sizeof(*out));
+    mwmm_status st = MWMM_OK;
+    if (!plan->pending.empty() && cudaEventSynchronize(plan->pending.back()) != cudaSuccess) st = MWMM_ERR_CUDA;
+    for (size_t c = 0; st == MWMM_OK && c + 5 <= plan->pending.size(); c += 5) {
+        float t[4];
+        cudaEvent_t *e = &plan->pending[c];
+        for (int i = 0; i < 4; ++i)
+            if (cudaEventElapsedTime(&t[i], e[i], e[i + 1]) != cudaSuccess) st = MWMM_ERR_CUDA;
+        out->split_a_ms += t[0];
+        out->split_b_ms += t[1];
+        out->gemm_ms += t[2];
+        out->recombine_ms += t[3];
+        out->total_ms += t[0] + t[1] + t[2] + t[3];
+        out->calls += 1;
+    }
+    out->launches = plan->pending_launches;
+    for (cudaEvent_t e : plan->pending) plan->pool.push_back(e);
+    plan->pending.clear();
+    plan->pending_launches = 0;
+    return st;
+}
+
 void mwmm_plan_destroy(mwmm_plan_t plan) {
     if (!plan) return;
+    for (cudaEvent_t e : plan->pool) cudaEventDestroy(e);
+    for (cudaEvent_t e : plan->pending) cudaEventDestroy(e);
     Plan &pl = plan->pl;
     if (pl.own_ws) cudaFree(pl.own_ws);
     if (pl.hostbuf_dev) cudaFree(pl.hostbuf_dev);

@@ -13,7 +13,8 @@ numpy, so 8192 x 8192 matrices are generated in seconds.
 
 Entries uniform in [0, p): the top ``bitlen(p)`` bits of a draw are kept
 and values >= p are rejected; a rejected element ``idx`` retries with
-counter ``idx + attempt * count`` until it lands in range.
+counter ``idx + attempt * 2^40`` until it lands in range, so the first r rows
+of a matrix do not depend on how many rows are drawn.
 
 Primes. ``is_prime`` is the deterministic Miller-Rabin test with the first
 twelve prime bases, which is exact for every n < 3.3e24 (Sorenson and
@@ -71,6 +72,8 @@ def uniform_mod(seed: int, stream: int, count: int, p: int) -> np.ndarray:
     """``count`` integers uniform in [0, p) as uint64 (p < 2^63)."""
     if p < 1 or p >= (1 << 63):
         raise ValueError("p must be in [1, 2^63)")
+    if count >= (1 << 40):
+        raise ValueError("at most 2^40 draws per stream")
     bits = max(1, (p - 1).bit_length())
     shift = np.uint64(64 - bits)
     out = np.empty(count, dtype=np.uint64)
@@ -78,7 +81,7 @@ def uniform_mod(seed: int, stream: int, count: int, p: int) -> np.ndarray:
     todo = idx
     attempt = 0
     while todo.size:
-        vals = draws(seed, stream, todo + np.uint64(attempt * count)) >> shift
+        vals = draws(seed, stream, todo + np.uint64(attempt << 40)) >> shift
         ok = vals < np.uint64(p)
         out[todo[ok]] = vals[ok]
         todo = todo[~ok]

@@ -41,6 +41,12 @@ class PlanOpts(ctypes.Structure):
                 ("kc", ctypes.c_int64), ("reserved", ctypes.c_int32 * 8)]
 
 
+class Timing(ctypes.Structure):
+    _fields_ = [("split_a_ms", ctypes.c_double), ("split_b_ms", ctypes.c_double), ("gemm_ms", ctypes.c_double),
+                ("recombine_ms", ctypes.c_double), ("total_ms", ctypes.c_double), ("calls", ctypes.c_int64),
+                ("launches", ctypes.c_int64)]
+
+
 class PlanDesc(ctypes.Structure):
     _fields_ = [("m", ctypes.c_int64), ("n", ctypes.c_int64), ("k", ctypes.c_int64), ("p", ctypes.c_uint64),
                 ("form", ctypes.c_int32), ("u", ctypes.c_int32), ("v", ctypes.c_int32),
@@ -86,6 +92,8 @@ def lib() -> ctypes.CDLL:
     L.mwmm_split.argtypes = [_vp, ctypes.c_int, _vp, _i64, _vp, _vp]
     L.mwmm_fmod.argtypes = [_vp, _i64, _u64, _vp, _vp]
     L.mwmm_mulmod.argtypes = [_vp, _vp, _i64, _u64, _vp, _vp]
+    L.mwmm_plan_set_timing.argtypes = [_vp, ctypes.c_int]
+    L.mwmm_plan_timing.argtypes = [_vp, ctypes.POINTER(Timing)]
     L.mwmm_status_str.argtypes = [ctypes.c_int]
     L.mwmm_status_str.restype = ctypes.c_char_p
     L.mwmm_version.restype = ctypes.c_char_p
@@ -216,6 +224,16 @@ def mwmm_mulmod(x, y, p: int, out, stream=None):
     f = (torch.float64,)
     _check(lib().mwmm_mulmod(_dev_ptr(x, f), _dev_ptr(y, f), x.numel(), p, _dev_ptr(out, f), _stream_ptr(stream)),
            "mwmm_mulmod")
+
+
+def mwmm_plan_set_timing(h: int, on: bool = True):
+    _check(lib().mwmm_plan_set_timing(h, 1 if on else 0), "mwmm_plan_set_timing")
+
+
+def mwmm_plan_timing(h: int) -> dict:
+    t = Timing()
+    _check(lib().mwmm_plan_timing(h, ctypes.byref(t)), "mwmm_plan_timing")
+    return {name: getattr(t, name) for name, _ in t._fields_}
 
 
 def mwmm_status_str(s: int) -> str:
