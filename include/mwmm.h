@@ -159,6 +159,25 @@ mwmm_status mwmm_plan_check(mwmm_plan_t plan, void *stream);
 
 void mwmm_plan_destroy(mwmm_plan_t plan);
 
+/* The INT8-form product for callers that cannot allocate device memory
+ * (their allocator belongs to another framework, or their device footprint
+ * must stay fixed after start-up).  The paper has no counterpart: this is a
+ * deployment variant of mwmm_matmul with default options.
+ * The word matrices and diagonal sums live in a 64 MiB array that the
+ * library reserves statically on each GPU where this code is loaded, held
+ * until the process exits; the caller passes only A, B and C (device
+ * pointers, same conventions as mwmm_matmul).  The first call on a device
+ * looks up that array's address; make it before capturing any stream.
+ * Every call shares the one array, so calls that overlap on the GPU race:
+ * issue them one at a time per device.  Synchronous: returns once C is
+ * written.  Calls no cudaMalloc/cudaFree or other allocating routine.
+ * Errors: MWMM_ERR_BUDGET when the product's workspace exceeds the array
+ * (about m = n = k = 768 at 52 bits; more for smaller primes), plus the
+ * errors of mwmm_plan and mwmm_matmul, and MWMM_ERR_TIMEOUT. */
+mwmm_status mwmm_matmul_noalloc(int64_t m, int64_t n, int64_t k, uint64_t p,
+                                const uint64_t *dA, int64_t lda, const uint64_t *dB, int64_t ldb,
+                                uint64_t *dC, int64_t ldc, void *stream);
+
 /* ---- step-level entry points (used to check single steps of the path) ---- */
 
 /* Alg. 4 / INT8 digits: write the words of A (side 0, M is m x k) or of B

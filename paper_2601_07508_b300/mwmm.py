@@ -92,6 +92,7 @@ def lib() -> ctypes.CDLL:
     L.mwmm_split.argtypes = [_vp, ctypes.c_int, _vp, _i64, _vp, _vp]
     L.mwmm_fmod.argtypes = [_vp, _i64, _u64, _vp, _vp]
     L.mwmm_mulmod.argtypes = [_vp, _vp, _i64, _u64, _vp, _vp]
+    L.mwmm_matmul_noalloc.argtypes = [_i64, _i64, _i64, _u64, _vp, _i64, _vp, _i64, _vp, _i64, _vp]
     L.mwmm_plan_set_timing.argtypes = [_vp, ctypes.c_int]
     L.mwmm_plan_timing.argtypes = [_vp, ctypes.POINTER(Timing)]
     L.mwmm_status_str.argtypes = [ctypes.c_int]
@@ -197,6 +198,16 @@ def mwmm_matmul_host(h: int, A: np.ndarray, B: np.ndarray, C: np.ndarray, stream
 
 def mwmm_matmul_host_ptr(h: int, a_ptr: int, lda: int, b_ptr: int, ldb: int, c_ptr: int, ldc: int, stream=None):
     _check(lib().mwmm_matmul_host(h, a_ptr, lda, b_ptr, ldb, c_ptr, ldc, _stream_ptr(stream)), "mwmm_matmul_host")
+
+
+def mwmm_matmul_noalloc(A, B, C, p: int, stream=None) -> int:
+    """INT8-form product with the library's static scratch (no device
+    allocation); synchronous.  Returns the status (0 = ok)."""
+    dt = _u64_dtypes()
+    m, k = A.shape
+    n = B.shape[1]
+    return int(lib().mwmm_matmul_noalloc(m, n, k, p, _dev_ptr(A, dt), _ld(A), _dev_ptr(B, dt), _ld(B),
+                                         _dev_ptr(C, dt), _ld(C), _stream_ptr(stream)))
 
 
 def mwmm_plan_check(h: int, stream=None) -> int:
