@@ -159,6 +159,59 @@ mwmm_status mwmm_plan_check(mwmm_plan_t plan, void *stream);
 
 void mwmm_plan_destroy(mwmm_plan_t plan);
 
+/* ---- batched products (many independent problems, different shapes and primes) ----
+ * A batch is planned once: every problem gets its own plan (FP64: (u,v) by
+ * the cost model, lambda from Prop. 3.3; INT8: fewest digits), their words and
+ * sums share one device workspace owned by the batch, the tcgen05 work items
+ * of all problems are spread over the SMs (longest first, to the least
+ * loaded SM), and the kernel launches (3 for the INT8 form, 2 for the FP64
+ * form, whatever the count) are captured once into a CUDA graph.  The device
+ * pointers of the problems are bound at creation: a run recomputes every C
+ * from the current contents of its A and B.  The paper computes one product
+ * at a time; its first perspective (Sec. 6) suggests batching. */
+typedef struct {
+    int64_t m, n, k;
+    uint64_t p;               /* odd, 5 <= p < 2^52 */
+    const uint64_t *A;        /* device, m x k, row-major, entries in [0, p) */
+    int64_t lda;
+    const uint64_t *B;        /* device, k x n */
+    int64_t ldb;
+    uint64_t *C;              /* device, m x n; must not overlap another problem's C */
+    int64_t ldc;
+} mwmm_problem;
+
+typedef struct mwmm_batch_s *mwmm_batch_t;
+
+typedef struct {
+    int32_t count, form;
+    int32_t ctas;             /* CTAs of the persistent tcgen05 launch (INT8 form) */
+    int64_t items;            /* tcgen05 work items over all problems */
+    int64_t launches;         /* kernel launches per run */
+    uint64_t workspace_bytes, table_bytes;
+    double flops_2mnk;        /* sum over problems of 2 m n k */
+    double word_flops;        /* sum of 2 u v m n k (word-product flops) */
+} mwmm_batch_desc;
+
+/* Plan and capture a batch (allocates the workspace and tables; makes CUDA
+ * calls).  opts applies to every problem (lambda is ignored).  Errors: those of
+ * mwmm_plan for any problem, MWMM_ERR_ARG, MWMM_ERR_NOMEM, MWMM_ERR_CUDA. */
+mwmm_status mwmm_batch_create(mwmm_batch_t *out, const mwmm_problem *probs, int count, mwmm_form form,
+                              const mwmm_plan_opts *opts);
+/* Replay the captured graph on `stream` (asynchronous). */
+mwmm_status mwmm_batch_run(mwmm_batch_t batch, void *stream);
+/* Synchronise `stream`; report and clear device-side errors of the batch. */
+mwmm_status mwmm_batch_check(mwmm_batch_t batch, void *stream);
+mwmm_status mwmm_batch_info(mwmm_batch_t batch, mwmm_batch_desc *out);
+/* The plan of problem `index` (words, block size, digits). */
+mwmm_status mwmm_batch_problem_info(mwmm_batch_t batch, int index, mwmm_plan_desc *out);
+void mwmm_batch_destroy(mwmm_batch_t batch);
+
+/* One call for callers that keep a cache handle: creates (or re-creates, when
+ * the problems differ from the cached ones) the batch in *cache and runs it.
+ * cache == NULL: create, run, synchronise, destroy. */
+mwmm_status mwmm_matmul_batched(const mwmm_problem *probs, int count, mwmm_form form, mwmm_batch_t *cache,
+                                void *stream);
+
 /* The INT8-form product for callers that cannot allocate device memory
  * (their allocator belongs to another framework, or their device footprint
  * must stay fixed after start-up).  The paper has no counterpart: this is a

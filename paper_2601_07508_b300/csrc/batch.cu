@@ -1,0 +1,387 @@
+// Batched products: many independent C_i = A_i B_i mod p_i (different shapes
+// and primes) run by one CUDA-graph replay of three table-driven kernels.
+//
+// The paper computes one product at a time; its first perspective (Sec. 6)
+// suggests batching the block products.  Here a batch is planned once:
+//   - each problem gets its own plan (words, lambda / digits, layout),
+//   - all word matrices and diagonal sums share one device workspace,
+//   - the split kernel walks a table of (problem, side, tile) blocks,
+//   - INT8 form: the persistent tcgen05 kernel walks per-CTA lists of work
+//     items (tile, diagonal, K-range) of all problems, assigned by
+//     longest-processing-time-first so every SM gets the same modelled work;
+//     the recombination kernel walks (problem, 8-row block) jobs,
+//   - FP64 form: the fused kernel walks a table of (problem, 64 x 64 tile),
+// and the launches are captured once into a CUDA graph; a run is one
+// cudaGraphLaunch on the caller's stream.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <functional>
+#include <new>
+#include <queue>
+#include <vector>
+
+#include "mwmm_internal.h"
+
+using mwmm::Plan;
+
+struct mwmm_batch_s {
+    int form = 0;
+    std::vector<mwmm_problem> probs;
+    std::vector<Plan> plans;
+    uint8_t *ws = nullptr;        // words + sums of every problem
+    uint8_t *tables = nullptr;    // kernel tables
+    int *err = nullptr;           // error words
+    uint64_t ws_bytes = 0, table_bytes = 0;
+    int nsplit = 0, ntc_ctas = 0, nrec = 0, nf64 = 0;
+    int64_t nitems = 0;
+    const void *d_split_jobs = nullptr;
+    const int *d_split_blocks = nullptr;
+    const mwmm::TcItem *d_items = nullptr;
+    const int64_t *d_cta_off = nullptr;
+    const void *d_rec = nullptr;
+    const int *d_rec_jobs = nullptr;
+    const void *d_f64 = nullptr;
+    const int *d_f64_jobs = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    double flops_2mnk = 0, word_flops = 0;
+    int64_t launches = 0;
+    int chunk_blocks = mwmm::kTcMaxChunk / mwmm::kTcKB;
+};
+
+namespace {
+
+uint64_t align256(uint64_t x) { return (x + 255) & ~uint64_t(255); }
+
+mwmm_status cuda_st(cudaError_t e) {
+    if (e == cudaSuccess) return MWMM_OK;
+    return e == cudaErrorMemoryAllocation ? MWMM_ERR_NOMEM : MWMM_ERR_CUDA;
+}
+
+void free_batch(mwmm_batch_s *b) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    if (b->ws) cudaFree(b->ws);
+    if (b->tables) cudaFree(b->tables);
+    if (b->err) cudaFree(b->err);
+    delete b;
+}
+
+// Longest-processing-time-first: items sorted by decreasing cost, each to the
+// CTA with the least work so far.  Returns items grouped per CTA and offsets.
+void lpt_schedule(std::vector<mwmm::TcItem> &items, int ctas, std::vector<int64_t> &off) {
+    std::vector<int64_t> cost(items.size());
+    for (size_t i = 0; i < items.size(); ++i) cost[i] = items[i].w * items[i].nkbc + 2;  // +2: drain and store
+    std::vector<size_t> order(items.size());
+    for (size_t i = 0; i < order.size(); ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) { return cost[a] > cost[b]; });
+    typedef std::pair<int64_t, int> Load;  // (work, cta)
+    std::priority_queue<Load, std::vector<Load>, std::greater<Load>> heap;
+    for (int c = 0; c < ctas; ++c) heap.push(Load(0, c));
+    std::vector<std::vector<size_t>> per(ctas);
+    for (size_t i : order) {
+        Load l = heap.top();
+        heap.pop();
+        per[l.second].push_back(i);
+        heap.push(Load(l.first + cost[i], l.second));
+    }
+    std::vector<mwmm::TcItem> out;
+    out.reserve(items.size());
+    off.assign(ctas + 1, 0);
+    for (int c = 0; c < ctas; ++c) {
+        off[c] = (int64_t)out.size();
+        for (size_t i : per[c]) out.push_back(items[i]);
+    }
+    off[ctas] = (int64_t)out.size();
+    items.swap(out);
+}
+
+// Work items of one INT8-form problem whose words start at Aw / Bw and whose
+// sums start at S (see the plan layout).
+void tc_items(const Plan &pl, const uint8_t *Aw, const uint8_t *Bw, int32_t *S, std::vector<mwmm::TcItem> &items) {
+    const int64_t mtc = pl.A_rows / mwmm::kTcBM, ntc = pl.B_rows / mwmm::kTcBN;
+    const int64_t kcb = pl.kc / mwmm::kTcKB;
+    for (int s = 0; s < pl.nsums; ++s) {
+        const int ilo = std::max(0, s - (pl.v - 1)), ihi = std::min(s, pl.u - 1);
+        for (int kc = 0; kc < pl.nkc; ++kc)
+            for (int64_t mt = 0; mt < mtc; ++mt)
+                for (int64_t nt = 0; nt < ntc; ++nt) {
+                    mwmm::TcItem it;
+                    std::memset(&it, 0, sizeof(it));
+                    it.Aw = Aw;
+                    it.Bw = Bw;
+                    it.S = S + (((int64_t)s * pl.nkc + kc) * pl.A_rows + mt * mwmm::kTcBM) * pl.B_rows +
+                           nt * mwmm::kTcBN;
+                    it.A_rows = pl.A_rows;
+                    it.B_rows = pl.B_rows;
+                    it.nkb = pl.nkb;
+                    it.kb0 = (int64_t)kc * kcb;
+                    it.nkbc = std::min(kcb, pl.nkb - it.kb0);
+                    it.mt = mt;
+                    it.nt = nt;
+                    it.s = s;
+                    it.i0 = ilo;
+                    it.w = ihi - ilo + 1;
+                    items.push_back(it);
+                }
+    }
+}
+
+mwmm_status record(mwmm_batch_s *b, cudaStream_t s) {
+    const int fp64 = b->form == MWMM_FORM_FP64;
+    int e = mwmm::launch_split_batched(b->d_split_jobs, b->d_split_blocks, b->nsplit, fp64, s);
+    if (e) return cuda_st((cudaError_t)e);
+    if (fp64) {
+        e = mwmm::launch_gemm_fp64_batched(b->d_f64, b->d_f64_jobs, b->nf64, s);
+        return cuda_st((cudaError_t)e);
+    }
+    e = mwmm::launch_gemm_tc_table(b->d_items, b->d_cta_off, b->ntc_ctas, b->chunk_blocks, b->err, s);
+    if (e) return cuda_st((cudaError_t)e);
+    e = mwmm::launch_recombine_batched(b->d_rec, b->d_rec_jobs, b->nrec, s);
+    return cuda_st((cudaError_t)e);
+}
+
+bool same_problems(const mwmm_batch_s *b, const mwmm_problem *probs, int count, int form) {
+    if (!b || b->form != form || (int)b->probs.size() != count) return false;
+    return std::memcmp(b->probs.data(), probs, sizeof(mwmm_problem) * (size_t)count) == 0;
+}
+
+}  // namespace
+
+extern "C" {
+
+mwmm_status mwmm_batch_create(mwmm_batch_t *out, const mwmm_problem *probs, int count, mwmm_form form,
+                              const mwmm_plan_opts *opts) {
+    if (!out || count < 0 || (count > 0 && !probs)) return MWMM_ERR_ARG;
+    *out = nullptr;
+    if (form == MWMM_FORM_AUTO) form = MWMM_FORM_INT8;
+    if (form != MWMM_FORM_FP64 && form != MWMM_FORM_INT8) return MWMM_ERR_ARG;
+    mwmm_batch_s *b = new (std::nothrow) mwmm_batch_s();
+    if (!b) return MWMM_ERR_NOMEM;
+    b->form = form;
+    if (opts && opts->tc_chunk) b->chunk_blocks = opts->tc_chunk / mwmm::kTcKB;
+    b->probs.assign(probs, probs + count);
+    b->plans.resize(count);
+    // ---- plans and workspace layout
+    std::vector<uint64_t> base(count);
+    uint64_t total = 0;
+    for (int i = 0; i < count; ++i) {
+        const mwmm_problem &q = probs[i];
+        mwmm_plan_opts o;
+        std::memset(&o, 0, sizeof(o));
+        if (opts) o = *opts;
+        o.lambda = 0;  // per-problem block sizes: always the bound
+        mwmm_status st = mwmm::make_plan(&b->plans[i], q.m, q.n, q.k, q.p, 0, 0, (int)form, &o);
+        if (st != MWMM_OK) {
+            delete b;
+            return st;
+        }
+        const Plan &pl = b->plans[i];
+        if (pl.m > 0 && pl.n > 0 && (!q.C || q.ldc < pl.n || (pl.k > 0 && (!q.A || !q.B || q.lda < pl.k ||
+                                                                       q.ldb < pl.n)))) {
+            delete b;
+            return MWMM_ERR_ARG;
+        }
+        base[i] = total;
+        total = align256(total + pl.ws_bytes);
+        b->flops_2mnk += 2.0 * pl.m * pl.n * pl.k;
+        b->word_flops += 2.0 * pl.u * pl.v * pl.m * pl.n * pl.k;
+    }
+    b->ws_bytes = total;
+    cudaError_t ce = cudaMalloc(&b->err, 256);
+    if (ce == cudaSuccess) ce = cudaMemset(b->err, 0, 256);
+    if (ce == cudaSuccess && total) ce = cudaMalloc(&b->ws, total);
+    if (ce != cudaSuccess) {
+        mwmm_status st = cuda_st(ce);
+        free_batch(b);
+        return st;
+    }
+    // ---- tables
+    std::vector<uint8_t> split_jobs(mwmm::split_job_bytes() * 2 * (size_t)count);
+    std::vector<int> split_blocks, f64_jobs, rec_jobs;
+    std::vector<uint8_t> f64_recs, rec_recs;
+    std::vector<mwmm::TcItem> items;
+    int nsj = 0;
+    for (int i = 0; i < count; ++i) {
+        Plan &pl = b->plans[i];
+        pl.err_dev = b->err;
+        const mwmm_problem &q = probs[i];
+        if (pl.m == 0 || pl.n == 0 || pl.k == 0) continue;
+        uint8_t *w = b->ws + base[i];
+        mwmm::split_job(pl, 0, q.A, q.lda, w + pl.A_off, &split_jobs[mwmm::split_job_bytes() * nsj], nsj,
+                        split_blocks);
+        ++nsj;
+        mwmm::split_job(pl, 1, q.B, q.ldb, w + pl.B_off, &split_jobs[mwmm::split_job_bytes() * nsj], nsj,
+                        split_blocks);
+        ++nsj;
+        if (form == MWMM_FORM_FP64) {
+            f64_recs.resize(f64_recs.size() + mwmm::fp64_job_bytes());
+            mwmm::fp64_job(pl, w + pl.A_off, w + pl.B_off, q.C, q.ldc, b->err,
+                           &f64_recs[f64_recs.size() - mwmm::fp64_job_bytes()],
+                           (int)(f64_recs.size() / mwmm::fp64_job_bytes()) - 1, f64_jobs);
+        } else {
+            int32_t *S = reinterpret_cast<int32_t *>(w + pl.S_off);
+            tc_items(pl, w + pl.A_off, w + pl.B_off, S, items);
+            rec_recs.resize(rec_recs.size() + mwmm::recombine_job_bytes());
+            mwmm::recombine_job(pl, S, q.C, q.ldc, &rec_recs[rec_recs.size() - mwmm::recombine_job_bytes()],
+                                (int)(rec_recs.size() / mwmm::recombine_job_bytes()) - 1, rec_jobs);
+        }
+    }
+    std::vector<int64_t> cta_off;
+    if (!items.empty()) {
+        const int ctas = (int)std::min<int64_t>((int64_t)items.size(), mwmm::tc_sm_count());
+        lpt_schedule(items, ctas, cta_off);
+        b->ntc_ctas = ctas;
+    }
+    b->nitems = (int64_t)items.size();
+    b->nsplit = (int)(split_blocks.size() / 4);
+    b->nrec = (int)(rec_jobs.size() / 4);
+    b->nf64 = (int)(f64_jobs.size() / 4);
+    // one device allocation for every table
+    struct Piece { const void *src; uint64_t bytes; uint64_t off; };
+    std::vector<Piece> pieces = {
+        {split_jobs.data(), (uint64_t)mwmm::split_job_bytes() * nsj, 0},
+        {split_blocks.data(), split_blocks.size() * sizeof(int), 0},
+        {items.data(), items.size() * sizeof(mwmm::TcItem), 0},
+        {cta_off.data(), cta_off.size() * sizeof(int64_t), 0},
+        {rec_recs.data(), rec_recs.size(), 0},
+        {rec_jobs.data(), rec_jobs.size() * sizeof(int), 0},
+        {f64_recs.data(), f64_recs.size(), 0},
+        {f64_jobs.data(), f64_jobs.size() * sizeof(int), 0}};
+    uint64_t tb = 0;
+    for (auto &pc : pieces) {
+        pc.off = tb;
+        tb = align256(tb + pc.bytes);
+    }
+    b->table_bytes = tb;
+    if (tb) {
+        ce = cudaMalloc(&b->tables, tb);
+        for (auto &pc : pieces)
+            if (ce == cudaSuccess && pc.bytes)
+                ce = cudaMemcpy(b->tables + pc.off, pc.src, pc.bytes, cudaMemcpyHostToDevice);
+        if (ce != cudaSuccess) {
+            mwmm_status st = cuda_st(ce);
+            free_batch(b);
+            return st;
+        }
+    }
+    b->d_split_jobs = b->tables + pieces[0].off;
+    b->d_split_blocks = reinterpret_cast<const int *>(b->tables + pieces[1].off);
+    b->d_items = reinterpret_cast<const mwmm::TcItem *>(b->tables + pieces[2].off);
+    b->d_cta_off = reinterpret_cast<const int64_t *>(b->tables + pieces[3].off);
+    b->d_rec = b->tables + pieces[4].off;
+    b->d_rec_jobs = reinterpret_cast<const int *>(b->tables + pieces[5].off);
+    b->d_f64 = b->tables + pieces[6].off;
+    b->d_f64_jobs = reinterpret_cast<const int *>(b->tables + pieces[7].off);
+    b->launches = (b->nsplit > 0) + (form == MWMM_FORM_FP64 ? (b->nf64 > 0) : (b->ntc_ctas > 0) + (b->nrec > 0));
+    // ---- capture the launches once; zero outputs of empty-k problems are set per run
+    if (mwmm::prepare_kernel_attributes() != 0) {
+        free_batch(b);
+        return MWMM_ERR_CUDA;
+    }
+    cudaStream_t cs;
+    ce = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (ce != cudaSuccess) {
+        free_batch(b);
+        return MWMM_ERR_CUDA;
+    }
+    ce = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    mwmm_status st = MWMM_OK;
+    if (ce == cudaSuccess) {
+        for (int i = 0; i < count; ++i) {  // k = 0: C = 0
+            const Plan &pl = b->plans[i];
+            if (pl.m > 0 && pl.n > 0 && pl.k == 0)
+                cudaMemset2DAsync(probs[i].C, (size_t)probs[i].ldc * 8, 0, (size_t)pl.n * 8, (size_t)pl.m, cs);
+        }
+        st = record(b, cs);
+        cudaGraph_t g = nullptr;
+        cudaError_t e2 = cudaStreamEndCapture(cs, &g);
+        if (st == MWMM_OK && e2 != cudaSuccess) st = MWMM_ERR_CUDA;
+        b->graph = g;
+        if (st == MWMM_OK && cudaGraphInstantiate(&b->exec, g, 0) != cudaSuccess) st = MWMM_ERR_CUDA;
+    } else {
+        st = MWMM_ERR_CUDA;
+    }
+    cudaStreamDestroy(cs);
+    if (st != MWMM_OK) {
+        free_batch(b);
+        return st;
+    }
+    *out = b;
+    return MWMM_OK;
+}
+
+mwmm_status mwmm_batch_run(mwmm_batch_t b, void *stream) {
+    if (!b) return MWMM_ERR_ARG;
+    if (!b->exec) return MWMM_OK;
+    return cudaGraphLaunch(b->exec, static_cast<cudaStream_t>(stream)) == cudaSuccess ? MWMM_OK : MWMM_ERR_CUDA;
+}
+
+mwmm_status mwmm_batch_check(mwmm_batch_t b, void *stream) {
+    if (!b) return MWMM_ERR_ARG;
+    if (cudaStreamSynchronize(static_cast<cudaStream_t>(stream)) != cudaSuccess) return MWMM_ERR_CUDA;
+    int flags[2] = {0, 0};
+    if (cudaMemcpy(flags, b->err, sizeof(flags), cudaMemcpyDeviceToHost) != cudaSuccess) return MWMM_ERR_CUDA;
+    if (flags[0] || flags[1]) cudaMemset(b->err, 0, sizeof(flags));
+    if (flags[0]) return MWMM_ERR_TIMEOUT;
+    if (flags[1]) return MWMM_ERR_RANGE;
+    return MWMM_OK;
+}
+
+mwmm_status mwmm_batch_info(mwmm_batch_t b, mwmm_batch_desc *d) {
+    if (!b || !d) return MWMM_ERR_ARG;
+    std::memset(d, 0, sizeof(*d));
+    d->count = (int32_t)b->probs.size();
+    d->form = b->form;
+    d->items = b->nitems;
+    d->ctas = b->ntc_ctas;
+    d->launches = b->launches;
+    d->workspace_bytes = b->ws_bytes;
+    d->table_bytes = b->table_bytes;
+    d->flops_2mnk = b->flops_2mnk;
+    d->word_flops = b->word_flops;
+    return MWMM_OK;
+}
+
+mwmm_status mwmm_batch_problem_info(mwmm_batch_t b, int index, mwmm_plan_desc *d) {
+    if (!b || !d || index < 0 || index >= (int)b->plans.size()) return MWMM_ERR_ARG;
+    mwmm_plan_t tmp = nullptr;
+    const Plan &pl = b->plans[index];
+    mwmm_status st = mwmm_plan(&tmp, pl.m, pl.n, pl.k, pl.p, pl.u, pl.v, (mwmm_form)pl.form, nullptr);
+    if (st != MWMM_OK) return st;
+    st = mwmm_plan_info(tmp, d);
+    mwmm_plan_destroy(tmp);
+    return st;
+}
+
+void mwmm_batch_destroy(mwmm_batch_t b) {
+    if (!b) return;
+    free_batch(b);
+}
+
+mwmm_status mwmm_matmul_batched(const mwmm_problem *probs, int count, mwmm_form form, mwmm_batch_t *cache,
+                                void *stream) {
+    if (form == MWMM_FORM_AUTO) form = MWMM_FORM_INT8;
+    mwmm_batch_t b = cache ? *cache : nullptr;
+    if (!same_problems(b, probs, count, (int)form)) {
+        if (b) {
+            cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+            mwmm_batch_destroy(b);
+        }
+        b = nullptr;
+        mwmm_status st = mwmm_batch_create(&b, probs, count, form, nullptr);
+        if (cache) *cache = b;
+        if (st != MWMM_OK) return st;
+    }
+    mwmm_status st = mwmm_batch_run(b, stream);
+    if (!cache) {
+        if (cudaStreamSynchronize(static_cast<cudaStream_t>(stream)) != cudaSuccess && st == MWMM_OK)
+            st = MWMM_ERR_CUDA;
+        mwmm_batch_destroy(b);
+    }
+    return st;
+}
+
+}  // extern "C"

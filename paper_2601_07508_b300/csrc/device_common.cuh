@@ -111,11 +111,20 @@ __device__ __forceinline__ double mulmod_split(double g, double g26, double y, d
 }  // namespace mwmm
 
 namespace mwmm {
-// Raise a kernel's dynamic shared-memory limit once per device.
+// Raise a kernel's dynamic shared-memory limit (once per device and kernel;
+// later calls are free, so a launch inside a stream capture makes no
+// attribute call once the same launch ran outside it).
 inline cudaError_t set_smem_attr(const void *func, int bytes) {
+    struct Done { const void *f; int dev; };
+    static Done done[64];
+    static int ndone = 0;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    for (int i = 0; i < ndone; ++i)
+        if (done[i].f == func && done[i].dev == dev) return cudaSuccess;
+    e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess && ndone < 64) done[ndone++] = Done{func, dev};
+    return e;
 }
 }  // namespace mwmm

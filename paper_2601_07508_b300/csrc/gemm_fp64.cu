@@ -14,6 +14,9 @@
 // form, so the kernel keeps the DFMA issue dense and everything else off the
 // critical path: word tiles (64 rows x 16 k, 8 KB) arrive by bulk TMA copies
 // into a 4-stage shared-memory ring, each thread owns a 4 x 4 output block.
+#include <cstring>
+#include <vector>
+
 #include "device_common.cuh"
 #include "mwmm_internal.h"
 
@@ -44,15 +47,14 @@ __device__ __forceinline__ double lds_word(const uint8_t *tile, int r, int kk) {
                                              ((kk & 1) << 3));
 }
 
-__global__ void __launch_bounds__(THREADS) gemm_fp64_kernel(const __grid_constant__ F64Params P) {
-    extern __shared__ __align__(1024) uint8_t smem[];
-    __shared__ __align__(8) uint64_t full[STAGES];
+// One 64 x 64 output tile (row0, col0) of the product described by P.
+__device__ __forceinline__ void fp64_tile(const F64Params &P, int64_t row0, int64_t col0, uint8_t *smem,
+                                          uint64_t *full) {
     uint8_t *sA = smem;
     uint8_t *sB = smem + STAGES * kTileA;
 
     const int tid = threadIdx.x;
     const int tx = tid & 15, ty = tid >> 4;
-    const int64_t row0 = (int64_t)blockIdx.y * BM, col0 = (int64_t)blockIdx.x * BN;
     const int64_t total = (int64_t)P.u * P.v * P.nkb;  // virtual k-blocks: (pair, kb)
 
     if (tid == 0) {
@@ -152,10 +154,22 @@ __global__ void __launch_bounds__(THREADS) gemm_fp64_kernel(const __grid_constan
     }
 }
 
-}  // namespace
+__global__ void __launch_bounds__(THREADS) gemm_fp64_kernel(const __grid_constant__ F64Params P) {
+    extern __shared__ __align__(1024) uint8_t smem[];
+    __shared__ __align__(8) uint64_t full[STAGES];
+    fp64_tile(P, (int64_t)blockIdx.y * BM, (int64_t)blockIdx.x * BN, smem, full);
+}
 
-int launch_gemm_fp64(const Plan &pl, const void *Aw, const void *Bw, uint64_t *C, int64_t ldc, int *err,
-                     void *stream) {
+// Batched: block b computes tile (row block y, col block x) of problem
+// probs[jobs[b].x] with jobs[b] = (problem, y, x, 0).
+__global__ void __launch_bounds__(THREADS) gemm_fp64_batched_kernel(const F64Params *probs, const int4 *jobs) {
+    extern __shared__ __align__(1024) uint8_t smem[];
+    __shared__ __align__(8) uint64_t full[STAGES];
+    const int4 j = jobs[blockIdx.x];
+    fp64_tile(probs[j.x], (int64_t)j.y * BM, (int64_t)j.z * BN, smem, full);
+}
+
+F64Params make_f64_params(const Plan &pl, const void *Aw, const void *Bw, uint64_t *C, int64_t ldc, int *err) {
     F64Params P;
     P.Aw = static_cast<const uint8_t *>(Aw);
     P.Bw = static_cast<const uint8_t *>(Bw);
@@ -177,6 +191,49 @@ int launch_gemm_fp64(const Plan &pl, const void *Aw, const void *Bw, uint64_t *C
         P.gamma26[i] = pl.gamma26[i];
     }
     P.err = err;
+    return P;
+}
+
+}  // namespace
+
+size_t fp64_job_bytes() { return sizeof(F64Params); }
+
+int prepare_tc_attributes();
+
+int prepare_kernel_attributes() {
+    const int smem = STAGES * (kTileA + kTileB);
+    cudaError_t e = set_smem_attr(reinterpret_cast<const void *>(gemm_fp64_kernel), smem);
+    if (e == cudaSuccess) e = set_smem_attr(reinterpret_cast<const void *>(gemm_fp64_batched_kernel), smem);
+    if (e != cudaSuccess) return (int)e;
+    return prepare_tc_attributes();
+}
+
+void fp64_job(const Plan &pl, const void *Aw, const void *Bw, uint64_t *C, int64_t ldc, int *err, void *rec,
+              int index, std::vector<int> &jobs) {
+    const F64Params P = make_f64_params(pl, Aw, Bw, C, ldc, err);
+    std::memcpy(rec, &P, sizeof(P));
+    for (int64_t y = 0; y < pl.A_rows / BM; ++y)
+        for (int64_t x = 0; x < pl.B_rows / BN; ++x) {
+            jobs.push_back(index);
+            jobs.push_back((int)y);
+            jobs.push_back((int)x);
+            jobs.push_back(0);
+        }
+}
+
+int launch_gemm_fp64_batched(const void *probs, const int *jobs, int njobs, void *stream) {
+    if (njobs == 0) return 0;
+    const int smem = STAGES * (kTileA + kTileB);
+    cudaError_t e = set_smem_attr(reinterpret_cast<const void *>(gemm_fp64_batched_kernel), smem);
+    if (e != cudaSuccess) return (int)e;
+    gemm_fp64_batched_kernel<<<njobs, THREADS, smem, static_cast<cudaStream_t>(stream)>>>(
+        static_cast<const F64Params *>(probs), reinterpret_cast<const int4 *>(jobs));
+    return (int)cudaGetLastError();
+}
+
+int launch_gemm_fp64(const Plan &pl, const void *Aw, const void *Bw, uint64_t *C, int64_t ldc, int *err,
+                     void *stream) {
+    const F64Params P = make_f64_params(pl, Aw, Bw, C, ldc, err);
     const int smem = STAGES * (kTileA + kTileB);
     cudaError_t e = set_smem_attr(reinterpret_cast<const void *>(gemm_fp64_kernel), smem);
     if (e != cudaSuccess) return (int)e;

@@ -33,6 +33,8 @@
 // error flag and all roles leave their loops.
 #include <cuda_bf16.h>
 
+#include <cstring>
+
 #include "device_common.cuh"
 #include "mwmm_internal.h"
 
@@ -51,25 +53,33 @@ constexpr uint32_t kTmemCols = 2 * BN;        // 512: two accumulator buffers
 constexpr int kSmemBytes = STAGES * (kTileA + kTileB) + 1024;
 
 struct TcParams {
+    // computed items (one product)
     const uint8_t *Aw, *Bw;
     int32_t *S;
     int64_t nkb, A_rows, B_rows, kcb, nitems;
-    int u, v, nsums, nkc, chunk_blocks, mt_count, nt_count;
+    int u, v, nsums, nkc, mt_count, nt_count;
     int diag_order[2 * kMaxWords];
+    // table items (batch): CTA c runs items[cta_off[c] .. cta_off[c + 1])
+    const TcItem *items;
+    const int64_t *cta_off;
+    int chunk_blocks;
     int *err;
 };
 
+// One work item with everything the three roles need.
 struct Item {
-    int64_t mt, nt, kb0, nkbc;
-    int s, kc, i0, w;
+    const uint8_t *Aw, *Bw;
+    int32_t *S;  // origin of the item's 128 x 256 output tile, row stride B_rows
+    int64_t A_rows, B_rows, nkb, kb0, nkbc, mt, nt;
+    int s, i0, w;
 };
 
-__device__ __forceinline__ Item get_item(const TcParams &P, int64_t idx) {
+__device__ __forceinline__ Item computed_item(const TcParams &P, int64_t idx) {
     Item it;
     const int64_t ntiles = (int64_t)P.mt_count * P.nt_count;
     const int64_t tile = idx % ntiles;
     const int64_t rest = idx / ntiles;
-    it.kc = (int)(rest % P.nkc);
+    const int kc = (int)(rest % P.nkc);
     it.s = P.diag_order[rest / P.nkc];
     it.mt = tile / P.nt_count;
     it.nt = tile % P.nt_count;
@@ -77,10 +87,56 @@ __device__ __forceinline__ Item get_item(const TcParams &P, int64_t idx) {
     const int ihi = it.s < P.u - 1 ? it.s : P.u - 1;
     it.i0 = ilo;
     it.w = ihi - ilo + 1;
-    it.kb0 = (int64_t)it.kc * P.kcb;
+    it.kb0 = (int64_t)kc * P.kcb;
     const int64_t left = P.nkb - it.kb0;
     it.nkbc = left < P.kcb ? left : P.kcb;
+    it.Aw = P.Aw;
+    it.Bw = P.Bw;
+    it.A_rows = P.A_rows;
+    it.B_rows = P.B_rows;
+    it.nkb = P.nkb;
+    it.S = P.S + (((int64_t)it.s * P.nkc + kc) * P.A_rows + it.mt * BM) * P.B_rows + it.nt * BN;
     return it;
+}
+
+__device__ __forceinline__ Item table_item(const TcParams &P, int64_t pos) {
+    const TcItem &d = P.items[pos];
+    Item it;
+    it.Aw = d.Aw;
+    it.Bw = d.Bw;
+    it.S = d.S;
+    it.A_rows = d.A_rows;
+    it.B_rows = d.B_rows;
+    it.nkb = d.nkb;
+    it.kb0 = d.kb0;
+    it.nkbc = d.nkbc;
+    it.mt = d.mt;
+    it.nt = d.nt;
+    it.s = d.s;
+    it.i0 = d.i0;
+    it.w = d.w;
+    return it;
+}
+
+template <bool kTable>
+struct ItemRange {
+    int64_t begin, end, step;
+    __device__ ItemRange(const TcParams &P) {
+        if (kTable) {
+            begin = P.cta_off[blockIdx.x];
+            end = P.cta_off[blockIdx.x + 1];
+            step = 1;
+        } else {
+            begin = blockIdx.x;
+            end = P.nitems;
+            step = gridDim.x;
+        }
+    }
+};
+
+template <bool kTable>
+__device__ __forceinline__ Item get_item(const TcParams &P, int64_t idx) {
+    return kTable ? table_item(P, idx) : computed_item(P, idx);
 }
 
 // ---- tcgen05 wrappers -------------------------------------------------------
@@ -137,6 +193,7 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+template <bool kTable>
 __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_constant__ TcParams P) {
     extern __shared__ uint8_t smem_raw[];
     __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES], tfull[2], tempty[2], done;
@@ -176,8 +233,9 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_consta
         if (lane == 0) {  // ---------------- TMA producer
             uint64_t g = 0;
             bool alive = true;
-            for (int64_t idx = blockIdx.x; alive && idx < P.nitems; idx += gridDim.x) {
-                const Item it = get_item(P, idx);
+            const ItemRange<kTable> R(P);
+            for (int64_t idx = R.begin; alive && idx < R.end; idx += R.step) {
+                const Item it = get_item<kTable>(P, idx);
                 const int64_t nvb = (int64_t)it.w * it.nkbc;
                 for (int64_t t = 0; t < nvb; ++t, ++g) {
                     const int slot = (int)(g % STAGES);
@@ -188,8 +246,8 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_consta
                     const int i = it.i0 + (int)(t / it.nkbc);
                     const int j = it.s - i;
                     const int64_t kb = it.kb0 + t % it.nkbc;
-                    const uint8_t *a = P.Aw + (((int64_t)i * P.nkb + kb) * P.A_rows + it.mt * BM) * kTileBytes;
-                    const uint8_t *b = P.Bw + (((int64_t)j * P.nkb + kb) * P.B_rows + it.nt * BN) * kTileBytes;
+                    const uint8_t *a = it.Aw + (((int64_t)i * it.nkb + kb) * it.A_rows + it.mt * BM) * kTileBytes;
+                    const uint8_t *b = it.Bw + (((int64_t)j * it.nkb + kb) * it.B_rows + it.nt * BN) * kTileBytes;
                     mbar_arrive_expect_tx(&full[slot], kTileA + kTileB);
                     bulk_g2s(sA + slot * kTileA, a, kTileA, &full[slot]);
                     bulk_g2s(sB + slot * kTileB, b, kTileB, &full[slot]);
@@ -206,8 +264,9 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_consta
             uint64_t g = 0, c = 0;
             bool alive = true;
             const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
-            for (int64_t idx = blockIdx.x; alive && idx < P.nitems; idx += gridDim.x) {
-                const Item it = get_item(P, idx);
+            const ItemRange<kTable> R(P);
+            for (int64_t idx = R.begin; alive && idx < R.end; idx += R.step) {
+                const Item it = get_item<kTable>(P, idx);
                 const int64_t nvb = (int64_t)it.w * it.nkbc;
                 for (int64_t t0 = 0; alive && t0 < nvb; t0 += P.chunk_blocks, ++c) {
                     const int buf = (int)(c & 1);
@@ -244,8 +303,9 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_consta
         const uint32_t tlane = tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(half * 128);
         uint64_t c = 0;
         bool alive = true;
-        for (int64_t idx = blockIdx.x; alive && idx < P.nitems; idx += gridDim.x) {
-            const Item it = get_item(P, idx);
+        const ItemRange<kTable> R(P);
+        for (int64_t idx = R.begin; alive && idx < R.end; idx += R.step) {
+            const Item it = get_item<kTable>(P, idx);
             const int64_t nvb = (int64_t)it.w * it.nkbc;
             const int64_t nch = (nvb + P.chunk_blocks - 1) / P.chunk_blocks;
             int32_t acc[128];
@@ -271,9 +331,7 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_consta
                 if (lane == 0) mbar_arrive(&tempty[buf]);
             }
             if (!alive) break;
-            const int64_t row = it.mt * BM + quarter * 32 + lane;
-            int32_t *dst = P.S + (((int64_t)it.s * P.nkc + it.kc) * P.A_rows + row) * P.B_rows + it.nt * BN +
-                           half * 128;
+            int32_t *dst = it.S + (int64_t)(quarter * 32 + lane) * it.B_rows + half * 128;
 #pragma unroll
             for (int q4 = 0; q4 < 32; ++q4)
                 reinterpret_cast<int4 *>(dst)[q4] =
@@ -321,6 +379,8 @@ int launch_gemm_tc(const Plan &pl, const void *Aw, const void *Bw, int32_t *S, i
     P.nt_count = (int)(pl.B_rows / BN);
     P.nitems = (int64_t)P.mt_count * P.nt_count * pl.nsums * pl.nkc;
     P.err = err;
+    P.items = nullptr;
+    P.cta_off = nullptr;
     // diagonals by decreasing number of word pairs (heaviest items first)
     int order[2 * kMaxWords];
     int w[2 * kMaxWords];
@@ -337,11 +397,34 @@ int launch_gemm_tc(const Plan &pl, const void *Aw, const void *Bw, int32_t *S, i
         }
     for (int s = 0; s < 2 * kMaxWords; ++s) P.diag_order[s] = s < pl.nsums ? order[s] : 0;
     if (P.nitems == 0) return 0;
-    cudaError_t e = set_smem_attr(reinterpret_cast<const void *>(gemm_tc_kernel), kSmemBytes);
+    cudaError_t e = set_smem_attr(reinterpret_cast<const void *>(gemm_tc_kernel<false>), kSmemBytes);
     if (e != cudaSuccess) return (int)e;
     const int64_t sms = sm_count();
     const unsigned grid = (unsigned)(P.nitems < sms ? P.nitems : sms);
-    gemm_tc_kernel<<<grid, THREADS, kSmemBytes, static_cast<cudaStream_t>(stream)>>>(P);
+    gemm_tc_kernel<false><<<grid, THREADS, kSmemBytes, static_cast<cudaStream_t>(stream)>>>(P);
+    return (int)cudaGetLastError();
+}
+
+int tc_sm_count() { return sm_count(); }
+
+int prepare_tc_attributes() {
+    cudaError_t e = set_smem_attr(reinterpret_cast<const void *>(gemm_tc_kernel<false>), kSmemBytes);
+    if (e == cudaSuccess) e = set_smem_attr(reinterpret_cast<const void *>(gemm_tc_kernel<true>), kSmemBytes);
+    return (int)e;
+}
+
+int launch_gemm_tc_table(const TcItem *items, const int64_t *cta_off, int ctas, int chunk_blocks, int *err,
+                         void *stream) {
+    if (ctas <= 0) return 0;
+    TcParams P;
+    std::memset(&P, 0, sizeof(P));
+    P.items = items;
+    P.cta_off = cta_off;
+    P.chunk_blocks = chunk_blocks;
+    P.err = err;
+    cudaError_t e = set_smem_attr(reinterpret_cast<const void *>(gemm_tc_kernel<true>), kSmemBytes);
+    if (e != cudaSuccess) return (int)e;
+    gemm_tc_kernel<true><<<ctas, THREADS, kSmemBytes, static_cast<cudaStream_t>(stream)>>>(P);
     return (int)cudaGetLastError();
 }
 

@@ -3,6 +3,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <vector>
 
 #include "mwmm.h"
 
@@ -20,6 +21,16 @@ constexpr int kTcBM = 128;              // MMA M (one CTA, TMEM lanes)
 constexpr int kTcBN = 256;              // MMA N
 constexpr int kTcMaxChunk = 1024;       // 2^24 / 2^14 digit products per FP32 chunk
 constexpr int64_t kInt32SumLimit = 131071; // floor((2^31 - 1) / 2^14): products per INT32 sum
+
+// One work item of the tcgen05 kernel in table mode (batched products): the
+// u-by-v word products of diagonal s over k-blocks [kb0, kb0 + nkbc) for the
+// 128 x 256 output tile (mt, nt) of one problem.
+struct TcItem {
+    const uint8_t *Aw, *Bw;  // word bases of the problem's A and B
+    int32_t *S;              // origin of the tile's diagonal sum (row stride B_rows)
+    int64_t A_rows, B_rows, nkb, kb0, nkbc, mt, nt;
+    int32_t s, i0, w, pad;
+};
 
 struct Plan {
     int64_t m = 0, n = 0, k = 0;
@@ -63,6 +74,23 @@ int launch_gemm_fp64(const Plan &pl, const void *Aw, const void *Bw, uint64_t *C
                      int *err, void *stream);
 int launch_gemm_tc(const Plan &pl, const void *Aw, const void *Bw, int32_t *S, int *err, void *stream);
 int launch_recombine(const Plan &pl, const int32_t *S, uint64_t *C, int64_t ldc, void *stream);
+// batched split: job records are opaque blobs of split_job_bytes() bytes
+size_t split_job_bytes();
+void split_job(const Plan &pl, int side, const uint64_t *M, int64_t ld, void *words, void *job, int job_index,
+               std::vector<int> &blocks);
+int launch_split_batched(const void *jobs, const int *blocks, int nblocks, int fp64, void *stream);
+size_t recombine_job_bytes();
+void recombine_job(const Plan &pl, const int32_t *S, uint64_t *C, int64_t ldc, void *rec, int index,
+                   std::vector<int> &jobs);
+int launch_recombine_batched(const void *probs, const int *jobs, int njobs, void *stream);
+size_t fp64_job_bytes();
+void fp64_job(const Plan &pl, const void *Aw, const void *Bw, uint64_t *C, int64_t ldc, int *err, void *rec,
+              int index, std::vector<int> &jobs);
+int launch_gemm_fp64_batched(const void *probs, const int *jobs, int njobs, void *stream);
+int prepare_kernel_attributes();  // dynamic shared-memory limits, once per device (call before capturing)
+int tc_sm_count();
+int launch_gemm_tc_table(const TcItem *items, const int64_t *cta_off, int ctas, int chunk_blocks, int *err,
+                         void *stream);
 int launch_fmod(const double *x, int64_t count, uint64_t p, double *out, void *stream);
 int launch_mulmod(const double *x, const double *y, int64_t count, uint64_t p, double *out, void *stream);
 

@@ -10,6 +10,9 @@
 // Bounds: 0 <= R < p < 2^52, so 256 R < 2^60; |S_s| < 2^31 per K-range and at
 // most nkc K-ranges, so y = 256 R + S_s + off with off = p * ceil(2^31 nkc / p)
 // lies in [0, 2^64) and y mod p = (256 R + S_s) mod p.
+#include <cstring>
+#include <vector>
+
 #include "device_common.cuh"
 #include "mwmm_internal.h"
 
@@ -33,12 +36,12 @@ __device__ __forceinline__ uint64_t reduce_u64(uint64_t y, uint64_t p, uint64_t 
     return r;
 }
 
-// Each thread produces 4 consecutive outputs of one row.
-__global__ void __launch_bounds__(256) recombine_kernel(const __grid_constant__ RecParams P) {
-    const int64_t c0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4;
+// Rows row0, row0 + rstep, ... < P.m of C; each thread produces 4
+// consecutive outputs (columns c0 .. c0 + 3) of a row.
+__device__ __forceinline__ void recombine_rows(const RecParams &P, int64_t c0, int64_t row0, int64_t rstep) {
     if (c0 >= P.n) return;
     const int64_t plane = P.A_rows * P.B_rows;
-    for (int64_t row = blockIdx.y; row < P.m; row += gridDim.y) {
+    for (int64_t row = row0; row < P.m; row += rstep) {
     uint64_t R[4] = {0, 0, 0, 0};
     for (int s = P.nsums - 1; s >= 0; --s) {
         int64_t x[4] = {0, 0, 0, 0};
@@ -58,9 +61,20 @@ __global__ void __launch_bounds__(256) recombine_kernel(const __grid_constant__ 
     }
 }
 
-}  // namespace
+__global__ void __launch_bounds__(256) recombine_kernel(const __grid_constant__ RecParams P) {
+    recombine_rows(P, ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4, blockIdx.y, gridDim.y);
+}
 
-int launch_recombine(const Plan &pl, const int32_t *S, uint64_t *C, int64_t ldc, void *stream) {
+// Batched: block b handles 1024 columns of rows [y0, y0 + 8) of problem
+// jobs[b] = (problem, y0, column block, 0).
+__global__ void __launch_bounds__(256) recombine_batched_kernel(const RecParams *probs, const int4 *jobs) {
+    const int4 j = jobs[blockIdx.x];
+    const RecParams &P = probs[j.x];
+    const int64_t c0 = ((int64_t)j.z * blockDim.x + threadIdx.x) * 4;
+    for (int64_t r = j.y; r < j.y + 8 && r < P.m; ++r) recombine_rows(P, c0, r, P.m);
+}
+
+RecParams make_rec_params(const Plan &pl, const int32_t *S, uint64_t *C, int64_t ldc) {
     RecParams P;
     P.S = S;
     P.C = C;
@@ -75,6 +89,36 @@ int launch_recombine(const Plan &pl, const int32_t *S, uint64_t *C, int64_t ldc,
     P.mu = (~uint64_t(0)) / pl.p;
     const unsigned __int128 need = (unsigned __int128)pl.nkc << 31;
     P.off = (uint64_t)((need + pl.p - 1) / pl.p * pl.p);
+    return P;
+}
+
+}  // namespace
+
+size_t recombine_job_bytes() { return sizeof(RecParams); }
+
+void recombine_job(const Plan &pl, const int32_t *S, uint64_t *C, int64_t ldc, void *rec, int index,
+                   std::vector<int> &jobs) {
+    const RecParams P = make_rec_params(pl, S, C, ldc);
+    std::memcpy(rec, &P, sizeof(P));
+    const int64_t cblocks = ((pl.n + 3) / 4 + 255) / 256;
+    for (int64_t y = 0; y < pl.m; y += 8)
+        for (int64_t c = 0; c < cblocks; ++c) {
+            jobs.push_back(index);
+            jobs.push_back((int)y);
+            jobs.push_back((int)c);
+            jobs.push_back(0);
+        }
+}
+
+int launch_recombine_batched(const void *probs, const int *jobs, int njobs, void *stream) {
+    if (njobs == 0) return 0;
+    recombine_batched_kernel<<<njobs, 256, 0, static_cast<cudaStream_t>(stream)>>>(
+        static_cast<const RecParams *>(probs), reinterpret_cast<const int4 *>(jobs));
+    return (int)cudaGetLastError();
+}
+
+int launch_recombine(const Plan &pl, const int32_t *S, uint64_t *C, int64_t ldc, void *stream) {
+    const RecParams P = make_rec_params(pl, S, C, ldc);
     if (pl.m == 0 || pl.n == 0) return 0;
     const int64_t groups = (pl.n + 3) / 4;
     dim3 grid((unsigned)((groups + 255) / 256), (unsigned)(pl.m < 65535 ? pl.m : 65535));

@@ -17,6 +17,9 @@
 // shared-memory reads spread over all banks.
 #include <cuda_bf16.h>
 
+#include <cstring>
+#include <vector>
+
 #include "device_common.cuh"
 #include "mwmm_internal.h"
 
@@ -89,9 +92,9 @@ __device__ __forceinline__ float int8_next(int64_t &s, bool last) {
 }
 
 // FP64 form: a 64 x 64 tile covers 4 k-blocks of 16 doubles, 8 granules each.
-__global__ void __launch_bounds__(256) split_fp64_kernel(const __grid_constant__ SplitParams P) {
-    __shared__ uint64_t tile[kST][kST + 1];
-    const int64_t r0 = (int64_t)blockIdx.y * kST, l0 = (int64_t)blockIdx.x * kST;
+__device__ __forceinline__ void split_fp64_tile(const SplitParams &P, uint64_t (*tile)[kST + 1], int64_t by,
+                                                int64_t bx) {
+    const int64_t r0 = by * kST, l0 = bx * kST;
     load_tile(P, tile, r0, l0);
     // units: (row, granule) with 32 granules (2 doubles) per row of the tile
     for (int unit = threadIdx.x; unit < kST * 32; unit += 256) {
@@ -113,9 +116,9 @@ __global__ void __launch_bounds__(256) split_fp64_kernel(const __grid_constant__
 }
 
 // INT8 form: a 64 x 64 tile is exactly one k-block of 64 bf16, 8 granules.
-__global__ void __launch_bounds__(256) split_int8_kernel(const __grid_constant__ SplitParams P) {
-    __shared__ uint64_t tile[kST][kST + 1];
-    const int64_t r0 = (int64_t)blockIdx.y * kST, l0 = (int64_t)blockIdx.x * kST;
+__device__ __forceinline__ void split_int8_tile(const SplitParams &P, uint64_t (*tile)[kST + 1], int64_t by,
+                                                int64_t bx) {
+    const int64_t r0 = by * kST, l0 = bx * kST;
     load_tile(P, tile, r0, l0);
     const int64_t kb = l0 / kTcKB;
     const uint64_t half = (P.p - 1) / 2;
@@ -140,9 +143,27 @@ __global__ void __launch_bounds__(256) split_int8_kernel(const __grid_constant__
     }
 }
 
-}  // namespace
+__global__ void __launch_bounds__(256) split_fp64_kernel(const __grid_constant__ SplitParams P) {
+    __shared__ uint64_t tile[kST][kST + 1];
+    split_fp64_tile(P, tile, blockIdx.y, blockIdx.x);
+}
 
-int launch_split(const Plan &pl, int side, const uint64_t *M, int64_t ld, void *words, void *stream) {
+__global__ void __launch_bounds__(256) split_int8_kernel(const __grid_constant__ SplitParams P) {
+    __shared__ uint64_t tile[kST][kST + 1];
+    split_int8_tile(P, tile, blockIdx.y, blockIdx.x);
+}
+
+// Batched: block b splits tile blocks[b] = (job, tile row, tile col) of jobs[job].
+__global__ void __launch_bounds__(256) split_batched_kernel(const SplitParams *jobs, const int4 *blocks,
+                                                            int fp64) {
+    __shared__ uint64_t tile[kST][kST + 1];
+    const int4 bl = blocks[blockIdx.x];
+    const SplitParams &P = jobs[bl.x];
+    if (fp64) split_fp64_tile(P, tile, bl.y, bl.z);
+    else split_int8_tile(P, tile, bl.y, bl.z);
+}
+
+SplitParams make_split_params(const Plan &pl, int side, const uint64_t *M, int64_t ld, void *words) {
     SplitParams P;
     P.M = M;
     P.ld = ld;
@@ -158,6 +179,41 @@ int launch_split(const Plan &pl, int side, const uint64_t *M, int64_t ld, void *
     P.mu = P.alpha >= 2 ? (~uint64_t(0)) / P.alpha : 0;
     P.validate = pl.validate;
     P.err = pl.err_dev;
+    return P;
+}
+
+}  // namespace
+
+size_t split_job_bytes() { return sizeof(SplitParams); }
+
+// Host side of the batched split: fill the job record for (plan, side) into
+// `job` (sizeof(SplitParams) bytes) and append its tile blocks to `blocks`
+// as (job index, tile row, tile col, 0).
+void split_job(const Plan &pl, int side, const uint64_t *M, int64_t ld, void *words, void *job, int job_index,
+               std::vector<int> &blocks) {
+    SplitParams P = make_split_params(pl, side, M, ld, words);
+    std::memcpy(job, &P, sizeof(P));
+    if (pl.nkb == 0 || P.rows_pad == 0) return;
+    const int64_t kcols = pl.nkb * pl.kb_elems;
+    const int64_t gx = (kcols + kST - 1) / kST, gy = P.rows_pad / kST;
+    for (int64_t y = 0; y < gy; ++y)
+        for (int64_t x = 0; x < gx; ++x) {
+            blocks.push_back(job_index);
+            blocks.push_back((int)y);
+            blocks.push_back((int)x);
+            blocks.push_back(0);
+        }
+}
+
+int launch_split_batched(const void *jobs, const int *blocks, int nblocks, int fp64, void *stream) {
+    if (nblocks == 0) return 0;
+    split_batched_kernel<<<nblocks, 256, 0, static_cast<cudaStream_t>(stream)>>>(
+        static_cast<const SplitParams *>(jobs), reinterpret_cast<const int4 *>(blocks), fp64);
+    return (int)cudaGetLastError();
+}
+
+int launch_split(const Plan &pl, int side, const uint64_t *M, int64_t ld, void *words, void *stream) {
+    const SplitParams P = make_split_params(pl, side, M, ld, words);
     if (pl.nkb == 0 || P.rows_pad == 0) return 0;
     const int64_t kcols = pl.nkb * pl.kb_elems;
     dim3 grid((unsigned)((kcols + kST - 1) / kST), (unsigned)(P.rows_pad / kST));

@@ -64,6 +64,18 @@ class PlanDesc(ctypes.Structure):
         return d
 
 
+class Problem(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int64), ("n", ctypes.c_int64), ("k", ctypes.c_int64), ("p", ctypes.c_uint64),
+                ("A", ctypes.c_void_p), ("lda", ctypes.c_int64), ("B", ctypes.c_void_p), ("ldb", ctypes.c_int64),
+                ("C", ctypes.c_void_p), ("ldc", ctypes.c_int64)]
+
+
+class BatchDesc(ctypes.Structure):
+    _fields_ = [("count", ctypes.c_int32), ("form", ctypes.c_int32), ("ctas", ctypes.c_int32),
+                ("items", ctypes.c_int64), ("launches", ctypes.c_int64), ("workspace_bytes", ctypes.c_uint64),
+                ("table_bytes", ctypes.c_uint64), ("flops_2mnk", ctypes.c_double), ("word_flops", ctypes.c_double)]
+
+
 _lib: Optional[ctypes.CDLL] = None
 _vp = ctypes.c_void_p
 _i64 = ctypes.c_int64
@@ -93,6 +105,15 @@ def lib() -> ctypes.CDLL:
     L.mwmm_fmod.argtypes = [_vp, _i64, _u64, _vp, _vp]
     L.mwmm_mulmod.argtypes = [_vp, _vp, _i64, _u64, _vp, _vp]
     L.mwmm_matmul_noalloc.argtypes = [_i64, _i64, _i64, _u64, _vp, _i64, _vp, _i64, _vp, _i64, _vp]
+    L.mwmm_batch_create.argtypes = [ctypes.POINTER(_vp), ctypes.POINTER(Problem), ctypes.c_int, ctypes.c_int,
+                                    ctypes.POINTER(PlanOpts)]
+    L.mwmm_batch_run.argtypes = [_vp, _vp]
+    L.mwmm_batch_check.argtypes = [_vp, _vp]
+    L.mwmm_batch_info.argtypes = [_vp, ctypes.POINTER(BatchDesc)]
+    L.mwmm_batch_problem_info.argtypes = [_vp, ctypes.c_int, ctypes.POINTER(PlanDesc)]
+    L.mwmm_batch_destroy.argtypes = [_vp]
+    L.mwmm_batch_destroy.restype = None
+    L.mwmm_matmul_batched.argtypes = [ctypes.POINTER(Problem), ctypes.c_int, ctypes.c_int, ctypes.POINTER(_vp), _vp]
     L.mwmm_plan_set_timing.argtypes = [_vp, ctypes.c_int]
     L.mwmm_plan_timing.argtypes = [_vp, ctypes.POINTER(Timing)]
     L.mwmm_status_str.argtypes = [ctypes.c_int]
@@ -253,6 +274,93 @@ def mwmm_status_str(s: int) -> str:
 
 def mwmm_version() -> str:
     return lib().mwmm_version().decode()
+
+
+def _problems(items):
+    """items: sequence of (A, B, C, p) device tensors (row-major)."""
+    arr = (Problem * len(items))()
+    for i, (A, B, C, p) in enumerate(items):
+        dt = _u64_dtypes()
+        arr[i].m, arr[i].k = A.shape
+        arr[i].n = B.shape[1]
+        arr[i].p = p
+        arr[i].A, arr[i].lda = _dev_ptr(A, dt), _ld(A)
+        arr[i].B, arr[i].ldb = _dev_ptr(B, dt), _ld(B)
+        arr[i].C, arr[i].ldc = _dev_ptr(C, dt), _ld(C)
+    return arr
+
+
+def mwmm_batch_create(items, form="auto", tc_chunk: int = 0, kc: int = 0) -> int:
+    if isinstance(form, str):
+        form = FORMS[form]
+    probs = _problems(items)
+    o = PlanOpts()
+    o.tc_chunk = tc_chunk
+    o.kc = kc
+    h = _vp()
+    _check(lib().mwmm_batch_create(ctypes.byref(h), probs, len(items), form, ctypes.byref(o)), "mwmm_batch_create")
+    return h.value
+
+
+def mwmm_batch_run(h: int, stream=None):
+    _check(lib().mwmm_batch_run(h, _stream_ptr(stream)), "mwmm_batch_run")
+
+
+def mwmm_batch_check(h: int, stream=None) -> int:
+    return int(lib().mwmm_batch_check(h, _stream_ptr(stream)))
+
+
+def mwmm_batch_info(h: int) -> dict:
+    d = BatchDesc()
+    _check(lib().mwmm_batch_info(h, ctypes.byref(d)), "mwmm_batch_info")
+    return {name: getattr(d, name) for name, _ in d._fields_}
+
+
+def mwmm_batch_problem_info(h: int, index: int) -> dict:
+    d = PlanDesc()
+    _check(lib().mwmm_batch_problem_info(h, index, ctypes.byref(d)), "mwmm_batch_problem_info")
+    return d.as_dict()
+
+
+def mwmm_batch_destroy(h: int):
+    lib().mwmm_batch_destroy(h)
+
+
+def mwmm_matmul_batched(items, form="auto", stream=None):
+    """Create, run, synchronise and destroy a batch in one call."""
+    if isinstance(form, str):
+        form = FORMS[form]
+    probs = _problems(items)
+    _check(lib().mwmm_matmul_batched(probs, len(items), form, None, _stream_ptr(stream)), "mwmm_matmul_batched")
+
+
+class Batch:
+    """Owns a batch handle over device tensors [(A, B, C, p), ...]."""
+
+    def __init__(self, items, form="auto", tc_chunk: int = 0, kc: int = 0):
+        self.items = list(items)  # keep the tensors alive
+        self.handle = mwmm_batch_create(self.items, form, tc_chunk, kc)
+        self.info = mwmm_batch_info(self.handle)
+
+    def run(self, stream=None):
+        mwmm_batch_run(self.handle, stream)
+
+    def check(self, stream=None) -> int:
+        return mwmm_batch_check(self.handle, stream)
+
+    def problem_info(self, i: int) -> dict:
+        return mwmm_batch_problem_info(self.handle, i)
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h:
+            try:
+                import torch
+                torch.cuda.synchronize()
+                mwmm_batch_destroy(h)
+            except Exception:
+                pass
+            self.handle = None
 
 
 # --------------------------------------------------------------------------- owner object
