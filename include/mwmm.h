@@ -212,6 +212,61 @@ void mwmm_batch_destroy(mwmm_batch_t batch);
 mwmm_status mwmm_matmul_batched(const mwmm_problem *probs, int count, mwmm_form form, mwmm_batch_t *cache,
                                 void *stream);
 
+/* ---- serving: continuous batching of products as they arrive ----
+ * A server owns a worker thread and a device-memory budget.  Clients submit
+ * problems (device pointers; the operands stay on the device) from any
+ * thread and get a ticket.  The worker admits queued requests, oldest first,
+ * as soon as their workspace fits in what is left of the budget, groups the
+ * admitted ones into a batch (the batched kernels of mwmm_batch_create,
+ * without graph capture) and launches it on the next of max_inflight
+ * streams while earlier batches still run; finished batches return their
+ * memory and wake their waiters.  Latency = completion seen by the worker
+ * minus arrival (submit time, or an earlier scheduled time the client gives).
+ * The budget covers the per-request workspaces plus one 32 MiB table region
+ * per stream; operands and outputs are the client's. */
+typedef struct {
+    int32_t max_batch;   /* requests per batch (0: 64) */
+    int32_t form;        /* MWMM_FORM_AUTO (INT8) or MWMM_FORM_FP64 for every request */
+    int32_t reserved[8];
+} mwmm_serve_opts;
+
+typedef struct {
+    int64_t submitted, completed, rejected, batches;
+    double mean_batch;             /* requests per launched batch */
+    int64_t peak_queue, peak_inflight;
+    uint64_t peak_bytes;           /* most workspace bytes in use at once */
+    uint64_t budget_bytes;
+    double flops_2mnk;             /* sum of 2 m n k over completed requests */
+    double busy_s;                 /* first arrival to last completion */
+    double gops;                   /* flops_2mnk / busy_s / 1e9 */
+    double p50_ms, p99_ms, mean_ms, max_ms;
+} mwmm_serve_report;
+
+typedef struct mwmm_server_s *mwmm_server_t;
+
+/* Errors: MWMM_ERR_BUDGET (budget below max_inflight x 32 MiB + 16 MiB),
+ * MWMM_ERR_NOMEM, MWMM_ERR_CUDA. */
+mwmm_status mwmm_serve_create(mwmm_server_t *out, size_t mem_budget_bytes, int max_inflight,
+                              const mwmm_serve_opts *opts);
+/* Seconds on the server's clock (0 at creation). */
+double mwmm_serve_now(mwmm_server_t server);
+/* Non-blocking.  t_arrival: scheduled arrival on the server clock, or < 0 for
+ * "now".  Errors: those of mwmm_plan, MWMM_ERR_ARG, MWMM_ERR_BUDGET (the
+ * request's workspace exceeds the whole budget; it is counted as rejected). */
+mwmm_status mwmm_serve_submit(mwmm_server_t server, const mwmm_problem *prob, double t_arrival,
+                              uint64_t *ticket);
+/* MWMM_OK (or the request's error) once done, MWMM_ERR_BUSY while pending. */
+mwmm_status mwmm_serve_poll(mwmm_server_t server, uint64_t ticket);
+/* Block until done (timeout_ms < 0: no limit); MWMM_ERR_TIMEOUT on expiry. */
+mwmm_status mwmm_serve_wait(mwmm_server_t server, uint64_t ticket, int timeout_ms);
+/* Latency of a finished request in seconds. */
+mwmm_status mwmm_serve_latency(mwmm_server_t server, uint64_t ticket, double *seconds);
+mwmm_status mwmm_serve_stats(mwmm_server_t server, mwmm_serve_report *out);
+/* Zero the counters and forget finished requests (their tickets). */
+mwmm_status mwmm_serve_reset_stats(mwmm_server_t server);
+/* Finish every submitted request, then release the server. */
+void mwmm_serve_destroy(mwmm_server_t server);
+
 /* The INT8-form product for callers that cannot allocate device memory
  * (their allocator belongs to another framework, or their device footprint
  * must stay fixed after start-up).  The paper has no counterpart: this is a

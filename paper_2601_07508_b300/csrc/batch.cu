@@ -51,27 +51,11 @@ struct mwmm_batch_s {
     int chunk_blocks = mwmm::kTcMaxChunk / mwmm::kTcKB;
 };
 
-namespace {
-
-uint64_t align256(uint64_t x) { return (x + 255) & ~uint64_t(255); }
-
-mwmm_status cuda_st(cudaError_t e) {
-    if (e == cudaSuccess) return MWMM_OK;
-    return e == cudaErrorMemoryAllocation ? MWMM_ERR_NOMEM : MWMM_ERR_CUDA;
-}
-
-void free_batch(mwmm_batch_s *b) {
-    if (b->exec) cudaGraphExecDestroy(b->exec);
-    if (b->graph) cudaGraphDestroy(b->graph);
-    if (b->ws) cudaFree(b->ws);
-    if (b->tables) cudaFree(b->tables);
-    if (b->err) cudaFree(b->err);
-    delete b;
-}
+namespace mwmm {
 
 // Longest-processing-time-first: items sorted by decreasing cost, each to the
 // CTA with the least work so far.  Returns items grouped per CTA and offsets.
-void lpt_schedule(std::vector<mwmm::TcItem> &items, int ctas, std::vector<int64_t> &off) {
+static void lpt_schedule(std::vector<mwmm::TcItem> &items, int ctas, std::vector<int64_t> &off) {
     std::vector<int64_t> cost(items.size());
     for (size_t i = 0; i < items.size(); ++i) cost[i] = items[i].w * items[i].nkbc + 2;  // +2: drain and store
     std::vector<size_t> order(items.size());
@@ -100,7 +84,7 @@ void lpt_schedule(std::vector<mwmm::TcItem> &items, int ctas, std::vector<int64_
 
 // Work items of one INT8-form problem whose words start at Aw / Bw and whose
 // sums start at S (see the plan layout).
-void tc_items(const Plan &pl, const uint8_t *Aw, const uint8_t *Bw, int32_t *S, std::vector<mwmm::TcItem> &items) {
+static void tc_items(const Plan &pl, const uint8_t *Aw, const uint8_t *Bw, int32_t *S, std::vector<mwmm::TcItem> &items) {
     const int64_t mtc = pl.A_rows / mwmm::kTcBM, ntc = pl.B_rows / mwmm::kTcBN;
     const int64_t kcb = pl.kc / mwmm::kTcKB;
     for (int s = 0; s < pl.nsums; ++s) {
@@ -127,6 +111,95 @@ void tc_items(const Plan &pl, const uint8_t *Aw, const uint8_t *Bw, int32_t *S, 
                     items.push_back(it);
                 }
     }
+}
+
+void build_batch_tables(const Plan *plans, const mwmm_problem *probs, uint8_t *const *ws_base, int count, int form,
+                        int *err, BatchTables &T) {
+    T = BatchTables();
+    T.split_jobs.resize(split_job_bytes() * 2 * (size_t)count);
+    int nsj = 0;
+    for (int i = 0; i < count; ++i) {
+        const Plan &pl = plans[i];
+        const mwmm_problem &q = probs[i];
+        if (pl.m == 0 || pl.n == 0 || pl.k == 0) continue;
+        uint8_t *w = ws_base[i];
+        split_job(pl, 0, q.A, q.lda, w + pl.A_off, &T.split_jobs[split_job_bytes() * nsj], nsj, T.split_blocks);
+        ++nsj;
+        split_job(pl, 1, q.B, q.ldb, w + pl.B_off, &T.split_jobs[split_job_bytes() * nsj], nsj, T.split_blocks);
+        ++nsj;
+        if (form == MWMM_FORM_FP64) {
+            T.f64_recs.resize(T.f64_recs.size() + fp64_job_bytes());
+            fp64_job(pl, w + pl.A_off, w + pl.B_off, q.C, q.ldc, err, &T.f64_recs[T.f64_recs.size() - fp64_job_bytes()],
+                     (int)(T.f64_recs.size() / fp64_job_bytes()) - 1, T.f64_jobs);
+        } else {
+            int32_t *S = reinterpret_cast<int32_t *>(w + pl.S_off);
+            tc_items(pl, w + pl.A_off, w + pl.B_off, S, T.items);
+            T.rec_recs.resize(T.rec_recs.size() + recombine_job_bytes());
+            recombine_job(pl, S, q.C, q.ldc, &T.rec_recs[T.rec_recs.size() - recombine_job_bytes()],
+                          (int)(T.rec_recs.size() / recombine_job_bytes()) - 1, T.rec_jobs);
+        }
+    }
+    T.split_jobs.resize(split_job_bytes() * nsj);
+    if (!T.items.empty()) {
+        T.ctas = (int)std::min<int64_t>((int64_t)T.items.size(), tc_sm_count());
+        lpt_schedule(T.items, T.ctas, T.cta_off);
+    }
+    T.nsplit = (int)(T.split_blocks.size() / 4);
+    T.nrec = (int)(T.rec_jobs.size() / 4);
+    T.nf64 = (int)(T.f64_jobs.size() / 4);
+}
+
+uint64_t pack_batch_tables(const BatchTables &T, std::vector<uint8_t> &blob, uint64_t off[8]) {
+    const void *src[8] = {T.split_jobs.data(), T.split_blocks.data(), T.items.data(), T.cta_off.data(),
+                          T.rec_recs.data(), T.rec_jobs.data(), T.f64_recs.data(), T.f64_jobs.data()};
+    const uint64_t bytes[8] = {T.split_jobs.size(), T.split_blocks.size() * sizeof(int),
+                               T.items.size() * sizeof(TcItem), T.cta_off.size() * sizeof(int64_t),
+                               T.rec_recs.size(), T.rec_jobs.size() * sizeof(int), T.f64_recs.size(),
+                               T.f64_jobs.size() * sizeof(int)};
+    uint64_t tb = 0;
+    for (int i = 0; i < 8; ++i) {
+        off[i] = tb;
+        tb = (tb + bytes[i] + 255) & ~uint64_t(255);
+    }
+    blob.assign(tb, 0);
+    for (int i = 0; i < 8; ++i)
+        if (bytes[i]) std::memcpy(blob.data() + off[i], src[i], bytes[i]);
+    return tb;
+}
+
+int launch_batch_tables(const BatchTables &T, const uint8_t *dtables, const uint64_t off[8], int form,
+                        int chunk_blocks, int *err, void *stream) {
+    const int fp64 = form == MWMM_FORM_FP64;
+    int e = launch_split_batched(dtables + off[0], reinterpret_cast<const int *>(dtables + off[1]), T.nsplit, fp64,
+                                 stream);
+    if (e) return e;
+    if (fp64) return launch_gemm_fp64_batched(dtables + off[6], reinterpret_cast<const int *>(dtables + off[7]),
+                                              T.nf64, stream);
+    e = launch_gemm_tc_table(reinterpret_cast<const TcItem *>(dtables + off[2]),
+                             reinterpret_cast<const int64_t *>(dtables + off[3]), T.ctas, chunk_blocks, err, stream);
+    if (e) return e;
+    return launch_recombine_batched(dtables + off[4], reinterpret_cast<const int *>(dtables + off[5]), T.nrec,
+                                    stream);
+}
+
+}  // namespace mwmm
+
+namespace {
+
+uint64_t align256(uint64_t x) { return (x + 255) & ~uint64_t(255); }
+
+mwmm_status cuda_st(cudaError_t e) {
+    if (e == cudaSuccess) return MWMM_OK;
+    return e == cudaErrorMemoryAllocation ? MWMM_ERR_NOMEM : MWMM_ERR_CUDA;
+}
+
+void free_batch(mwmm_batch_s *b) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    if (b->ws) cudaFree(b->ws);
+    if (b->tables) cudaFree(b->tables);
+    if (b->err) cudaFree(b->err);
+    delete b;
 }
 
 mwmm_status record(mwmm_batch_s *b, cudaStream_t s) {
@@ -199,74 +272,33 @@ mwmm_status mwmm_batch_create(mwmm_batch_t *out, const mwmm_problem *probs, int 
         return st;
     }
     // ---- tables
-    std::vector<uint8_t> split_jobs(mwmm::split_job_bytes() * 2 * (size_t)count);
-    std::vector<int> split_blocks, f64_jobs, rec_jobs;
-    std::vector<uint8_t> f64_recs, rec_recs;
-    std::vector<mwmm::TcItem> items;
-    int nsj = 0;
+    std::vector<uint8_t *> wsb(count);
     for (int i = 0; i < count; ++i) {
-        Plan &pl = b->plans[i];
-        pl.err_dev = b->err;
-        const mwmm_problem &q = probs[i];
-        if (pl.m == 0 || pl.n == 0 || pl.k == 0) continue;
-        uint8_t *w = b->ws + base[i];
-        mwmm::split_job(pl, 0, q.A, q.lda, w + pl.A_off, &split_jobs[mwmm::split_job_bytes() * nsj], nsj,
-                        split_blocks);
-        ++nsj;
-        mwmm::split_job(pl, 1, q.B, q.ldb, w + pl.B_off, &split_jobs[mwmm::split_job_bytes() * nsj], nsj,
-                        split_blocks);
-        ++nsj;
-        if (form == MWMM_FORM_FP64) {
-            f64_recs.resize(f64_recs.size() + mwmm::fp64_job_bytes());
-            mwmm::fp64_job(pl, w + pl.A_off, w + pl.B_off, q.C, q.ldc, b->err,
-                           &f64_recs[f64_recs.size() - mwmm::fp64_job_bytes()],
-                           (int)(f64_recs.size() / mwmm::fp64_job_bytes()) - 1, f64_jobs);
-        } else {
-            int32_t *S = reinterpret_cast<int32_t *>(w + pl.S_off);
-            tc_items(pl, w + pl.A_off, w + pl.B_off, S, items);
-            rec_recs.resize(rec_recs.size() + mwmm::recombine_job_bytes());
-            mwmm::recombine_job(pl, S, q.C, q.ldc, &rec_recs[rec_recs.size() - mwmm::recombine_job_bytes()],
-                                (int)(rec_recs.size() / mwmm::recombine_job_bytes()) - 1, rec_jobs);
-        }
+        b->plans[i].err_dev = b->err;
+        wsb[i] = b->ws + base[i];
     }
-    std::vector<int64_t> cta_off;
-    if (!items.empty()) {
-        const int ctas = (int)std::min<int64_t>((int64_t)items.size(), mwmm::tc_sm_count());
-        lpt_schedule(items, ctas, cta_off);
-        b->ntc_ctas = ctas;
-    }
-    b->nitems = (int64_t)items.size();
-    b->nsplit = (int)(split_blocks.size() / 4);
-    b->nrec = (int)(rec_jobs.size() / 4);
-    b->nf64 = (int)(f64_jobs.size() / 4);
-    // one device allocation for every table
-    struct Piece { const void *src; uint64_t bytes; uint64_t off; };
-    std::vector<Piece> pieces = {
-        {split_jobs.data(), (uint64_t)mwmm::split_job_bytes() * nsj, 0},
-        {split_blocks.data(), split_blocks.size() * sizeof(int), 0},
-        {items.data(), items.size() * sizeof(mwmm::TcItem), 0},
-        {cta_off.data(), cta_off.size() * sizeof(int64_t), 0},
-        {rec_recs.data(), rec_recs.size(), 0},
-        {rec_jobs.data(), rec_jobs.size() * sizeof(int), 0},
-        {f64_recs.data(), f64_recs.size(), 0},
-        {f64_jobs.data(), f64_jobs.size() * sizeof(int), 0}};
-    uint64_t tb = 0;
-    for (auto &pc : pieces) {
-        pc.off = tb;
-        tb = align256(tb + pc.bytes);
-    }
+    mwmm::BatchTables T;
+    mwmm::build_batch_tables(b->plans.data(), probs, wsb.data(), count, form, b->err, T);
+    b->nitems = (int64_t)T.items.size();
+    b->nsplit = T.nsplit;
+    b->nrec = T.nrec;
+    b->nf64 = T.nf64;
+    b->ntc_ctas = T.ctas;
+    std::vector<uint8_t> blob;
+    uint64_t off[8];
+    const uint64_t tb = mwmm::pack_batch_tables(T, blob, off);
     b->table_bytes = tb;
     if (tb) {
         ce = cudaMalloc(&b->tables, tb);
-        for (auto &pc : pieces)
-            if (ce == cudaSuccess && pc.bytes)
-                ce = cudaMemcpy(b->tables + pc.off, pc.src, pc.bytes, cudaMemcpyHostToDevice);
+        if (ce == cudaSuccess) ce = cudaMemcpy(b->tables, blob.data(), tb, cudaMemcpyHostToDevice);
         if (ce != cudaSuccess) {
             mwmm_status st = cuda_st(ce);
             free_batch(b);
             return st;
         }
     }
+    struct { uint64_t off; } pieces[8];
+    for (int i = 0; i < 8; ++i) pieces[i].off = off[i];
     b->d_split_jobs = b->tables + pieces[0].off;
     b->d_split_blocks = reinterpret_cast<const int *>(b->tables + pieces[1].off);
     b->d_items = reinterpret_cast<const mwmm::TcItem *>(b->tables + pieces[2].off);

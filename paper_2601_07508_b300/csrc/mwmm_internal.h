@@ -94,4 +94,25 @@ int launch_gemm_tc_table(const TcItem *items, const int64_t *cta_off, int ctas, 
 int launch_fmod(const double *x, int64_t count, uint64_t p, double *out, void *stream);
 int launch_mulmod(const double *x, const double *y, int64_t count, uint64_t p, double *out, void *stream);
 
+// Host-side tables of a batch of products (batch.cu).
+struct BatchTables {
+    std::vector<uint8_t> split_jobs;
+    std::vector<int> split_blocks;
+    std::vector<TcItem> items;
+    std::vector<int64_t> cta_off;
+    std::vector<uint8_t> rec_recs;
+    std::vector<int> rec_jobs;
+    std::vector<uint8_t> f64_recs;
+    std::vector<int> f64_jobs;
+    int nsplit = 0, nrec = 0, nf64 = 0, ctas = 0;
+};
+// Tables for problems[0..count) whose workspaces start at ws_base[i] (device).
+void build_batch_tables(const Plan *plans, const mwmm_problem *probs, uint8_t *const *ws_base, int count, int form,
+                        int *err, BatchTables &T);
+// One 256-byte-aligned blob holding the 8 tables; off[i] = offset of table i.
+uint64_t pack_batch_tables(const BatchTables &T, std::vector<uint8_t> &blob, uint64_t off[8]);
+// Launch the batch's kernels with its tables at dtables (device copy of the blob).
+int launch_batch_tables(const BatchTables &T, const uint8_t *dtables, const uint64_t off[8], int form,
+                        int chunk_blocks, int *err, void *stream);
+
 }  // namespace mwmm

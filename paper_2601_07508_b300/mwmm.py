@@ -76,6 +76,19 @@ class BatchDesc(ctypes.Structure):
                 ("table_bytes", ctypes.c_uint64), ("flops_2mnk", ctypes.c_double), ("word_flops", ctypes.c_double)]
 
 
+class ServeOpts(ctypes.Structure):
+    _fields_ = [("max_batch", ctypes.c_int32), ("form", ctypes.c_int32), ("reserved", ctypes.c_int32 * 8)]
+
+
+class ServeReport(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("rejected", ctypes.c_int64),
+                ("batches", ctypes.c_int64), ("mean_batch", ctypes.c_double), ("peak_queue", ctypes.c_int64),
+                ("peak_inflight", ctypes.c_int64), ("peak_bytes", ctypes.c_uint64), ("budget_bytes", ctypes.c_uint64),
+                ("flops_2mnk", ctypes.c_double), ("busy_s", ctypes.c_double), ("gops", ctypes.c_double),
+                ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double), ("mean_ms", ctypes.c_double),
+                ("max_ms", ctypes.c_double)]
+
+
 _lib: Optional[ctypes.CDLL] = None
 _vp = ctypes.c_void_p
 _i64 = ctypes.c_int64
@@ -114,6 +127,17 @@ def lib() -> ctypes.CDLL:
     L.mwmm_batch_destroy.argtypes = [_vp]
     L.mwmm_batch_destroy.restype = None
     L.mwmm_matmul_batched.argtypes = [ctypes.POINTER(Problem), ctypes.c_int, ctypes.c_int, ctypes.POINTER(_vp), _vp]
+    L.mwmm_serve_create.argtypes = [ctypes.POINTER(_vp), ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(ServeOpts)]
+    L.mwmm_serve_now.argtypes = [_vp]
+    L.mwmm_serve_now.restype = ctypes.c_double
+    L.mwmm_serve_submit.argtypes = [_vp, ctypes.POINTER(Problem), ctypes.c_double, ctypes.POINTER(ctypes.c_uint64)]
+    L.mwmm_serve_poll.argtypes = [_vp, ctypes.c_uint64]
+    L.mwmm_serve_wait.argtypes = [_vp, ctypes.c_uint64, ctypes.c_int]
+    L.mwmm_serve_latency.argtypes = [_vp, ctypes.c_uint64, ctypes.POINTER(ctypes.c_double)]
+    L.mwmm_serve_stats.argtypes = [_vp, ctypes.POINTER(ServeReport)]
+    L.mwmm_serve_reset_stats.argtypes = [_vp]
+    L.mwmm_serve_destroy.argtypes = [_vp]
+    L.mwmm_serve_destroy.restype = None
     L.mwmm_plan_set_timing.argtypes = [_vp, ctypes.c_int]
     L.mwmm_plan_timing.argtypes = [_vp, ctypes.POINTER(Timing)]
     L.mwmm_status_str.argtypes = [ctypes.c_int]
@@ -361,6 +385,103 @@ class Batch:
             except Exception:
                 pass
             self.handle = None
+
+
+def mwmm_serve_create(budget_bytes: int, max_inflight: int = 2, max_batch: int = 0, form="auto") -> int:
+    o = ServeOpts()
+    o.max_batch = max_batch
+    o.form = FORMS[form] if isinstance(form, str) else form
+    h = _vp()
+    _check(lib().mwmm_serve_create(ctypes.byref(h), budget_bytes, max_inflight, ctypes.byref(o)), "mwmm_serve_create")
+    return h.value
+
+
+def mwmm_serve_now(h: int) -> float:
+    return float(lib().mwmm_serve_now(h))
+
+
+def mwmm_serve_submit(h: int, A, B, C, p: int, t_arrival: float = -1.0):
+    """Returns (status, ticket)."""
+    prob = _problems([(A, B, C, p)])
+    t = ctypes.c_uint64(0)
+    st = lib().mwmm_serve_submit(h, prob, t_arrival, ctypes.byref(t))
+    return int(st), int(t.value)
+
+
+def mwmm_serve_submit_ptr(h: int, prob: Problem, t_arrival: float = -1.0):
+    t = ctypes.c_uint64(0)
+    st = lib().mwmm_serve_submit(h, ctypes.byref(prob), t_arrival, ctypes.byref(t))
+    return int(st), int(t.value)
+
+
+def mwmm_serve_poll(h: int, ticket: int) -> int:
+    return int(lib().mwmm_serve_poll(h, ticket))
+
+
+def mwmm_serve_wait(h: int, ticket: int, timeout_ms: int = -1) -> int:
+    return int(lib().mwmm_serve_wait(h, ticket, timeout_ms))
+
+
+def mwmm_serve_latency(h: int, ticket: int) -> float:
+    s = ctypes.c_double(0)
+    _check(lib().mwmm_serve_latency(h, ticket, ctypes.byref(s)), "mwmm_serve_latency")
+    return s.value
+
+
+def mwmm_serve_stats(h: int) -> dict:
+    r = ServeReport()
+    st = lib().mwmm_serve_stats(h, ctypes.byref(r))
+    d = {name: getattr(r, name) for name, _ in r._fields_}
+    d["status"] = int(st)
+    return d
+
+
+def mwmm_serve_reset_stats(h: int):
+    _check(lib().mwmm_serve_reset_stats(h), "mwmm_serve_reset_stats")
+
+
+def mwmm_serve_destroy(h: int):
+    lib().mwmm_serve_destroy(h)
+
+
+class Server:
+    """Owns a serving loop: ``Server(budget_bytes)``, then ``submit`` / ``wait``."""
+
+    def __init__(self, budget_bytes: int, max_inflight: int = 2, max_batch: int = 0, form="auto"):
+        self.handle = mwmm_serve_create(budget_bytes, max_inflight, max_batch, form)
+
+    def now(self) -> float:
+        return mwmm_serve_now(self.handle)
+
+    def submit(self, A, B, C, p: int, t_arrival: float = -1.0):
+        return mwmm_serve_submit(self.handle, A, B, C, p, t_arrival)
+
+    def wait(self, ticket: int, timeout_ms: int = -1) -> int:
+        return mwmm_serve_wait(self.handle, ticket, timeout_ms)
+
+    def poll(self, ticket: int) -> int:
+        return mwmm_serve_poll(self.handle, ticket)
+
+    def latency(self, ticket: int) -> float:
+        return mwmm_serve_latency(self.handle, ticket)
+
+    def stats(self) -> dict:
+        return mwmm_serve_stats(self.handle)
+
+    def reset_stats(self):
+        mwmm_serve_reset_stats(self.handle)
+
+    def close(self):
+        h = getattr(self, "handle", None)
+        if h:
+            mwmm_serve_destroy(h)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 # --------------------------------------------------------------------------- owner object

@@ -1,0 +1,123 @@
+"""Serving loop (continuous batching): every result equals the same product
+computed alone and the oracle's; requests are admitted against the memory
+budget; stats report latency percentiles."""
+import threading
+import time
+
+import numpy as np
+import pytest
+
+from paper_2601_07508_b300 import build, inputs
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def M():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    build.build()
+    from paper_2601_07508_b300 import mwmm
+    mwmm.lib()
+    return mwmm
+
+
+def _dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x).view(np.int64)).cuda()
+
+
+def _requests(seed, count, lo, hi):
+    dims = inputs.loguniform_dims(seed, inputs.STREAM_SHAPES, 3 * count, lo, hi).reshape(count, 3)
+    bz = inputs.draws(seed, inputs.STREAM_PRIMES, np.arange(count, dtype=np.uint64)) % np.uint64(33)
+    out = []
+    for i in range(count):
+        p = inputs.random_prime_of_bitsize(seed, 104, i, 20 + int(bz[i]))
+        m, n, k = (int(x) for x in dims[i])
+        A, B = inputs.problem(seed * 10000 + i, m, n, k, p)
+        out.append((A, B, p))
+    return out
+
+
+def test_serve_results_equal_alone_and_oracle(M, oracle):
+    reqs = _requests(21, 120, 8, 400)
+    dev = [(_dev(A), _dev(B), torch.full((A.shape[0], B.shape[1]), -1, dtype=torch.int64, device="cuda"), p)
+           for A, B, p in reqs]
+    torch.cuda.synchronize()
+    srv = M.Server(2 << 30, max_inflight=2, max_batch=16)
+    tickets = []
+    for dA, dB, C, p in dev:  # a burst: later requests arrive while earlier batches run
+        st, t = srv.submit(dA, dB, C, p)
+        assert st == 0
+        tickets.append(t)
+    for t in tickets:
+        assert srv.wait(t, 60000) == 0
+    s = srv.stats()
+    assert s["completed"] == 120 and s["status"] == 0
+    assert s["batches"] >= 120 // 16 and s["mean_batch"] > 1.0
+    assert s["peak_inflight"] >= 1 and 0 < s["p50_ms"] <= s["p99_ms"] <= s["max_ms"]
+    srv.close()
+    for (A, B, p), (dA, dB, C, _) in zip(reqs, dev):
+        alone = M.Plan(A.shape[0], B.shape[1], A.shape[1], p, form="int8").matmul(dA, dB)
+        assert torch.equal(C, alone)
+        assert np.array_equal(C.cpu().numpy().view(np.uint64), oracle.matmul_mod(A, B, p))
+
+
+def test_serve_poisson_stream_from_two_client_threads(M, oracle):
+    reqs = _requests(22, 80, 16, 300)
+    dev = [(_dev(A), _dev(B), torch.empty((A.shape[0], B.shape[1]), dtype=torch.int64, device="cuda"), p)
+           for A, B, p in reqs]
+    torch.cuda.synchronize()
+    srv = M.Server(1 << 30, max_inflight=3, max_batch=8)
+    arrivals = inputs.poisson_arrivals(22, len(reqs), 2000.0)
+    tickets = [0] * len(reqs)
+    t0 = srv.now()
+
+    def client(idx):
+        for i in idx:
+            while srv.now() - t0 < arrivals[i]:
+                time.sleep(0.0001)
+            st, tk = srv.submit(*dev[i], t_arrival=t0 + arrivals[i])
+            assert st == 0
+            tickets[i] = tk
+
+    th = [threading.Thread(target=client, args=(range(j, len(reqs), 2),)) for j in range(2)]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    for tk in tickets:
+        assert srv.wait(tk, 60000) == 0
+        assert srv.latency(tk) >= 0
+    s = srv.stats()
+    assert s["completed"] == len(reqs)
+    srv.close()
+    for (A, B, p), (_, _, C, _) in zip(reqs, dev):
+        assert np.array_equal(C.cpu().numpy().view(np.uint64), oracle.matmul_mod(A, B, p))
+
+
+def test_serve_admission_against_budget(M, oracle):
+    p = inputs.largest_prime_below_pow2(52)
+    # each 700^3 52-bit request needs ~47 MB of workspace; the arena holds one at a time
+    budget = 2 * (32 << 20) + (60 << 20)
+    srv = M.Server(budget, max_inflight=2, max_batch=4)
+    reqs = [inputs.problem(300 + i, 700, 700, 700, p) for i in range(5)]
+    dev = [(_dev(A), _dev(B), torch.empty((700, 700), dtype=torch.int64, device="cuda")) for A, B in reqs]
+    tickets = []
+    for dA, dB, C in dev:
+        st, t = srv.submit(dA, dB, C, p)
+        assert st == 0
+        tickets.append(t)
+    # a request whose workspace can never fit is rejected at once
+    big = torch.zeros((3000, 3000), dtype=torch.int64, device="cuda")
+    st, _ = srv.submit(big, big, big, p)
+    assert st == 6  # MWMM_ERR_BUDGET
+    for t in tickets:
+        assert srv.wait(t, 60000) == 0
+    s = srv.stats()
+    assert s["completed"] == 5 and s["rejected"] == 1
+    assert s["peak_bytes"] <= budget - 2 * (32 << 20)
+    assert s["mean_batch"] == 1.0  # memory admits one request at a time
+    srv.close()
+    for (A, B), (_, _, C) in zip(reqs, dev):
+        assert np.array_equal(C.cpu().numpy().view(np.uint64), oracle.matmul_mod(A, B, p))
