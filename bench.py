@@ -50,6 +50,10 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
+    ap.add_argument("--no-batched", action="store_true", help="skip the 512-instance multi-prime batch")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving run")
+    ap.add_argument("--serve-requests", type=int, default=20000)
+    ap.add_argument("--serve-pool", type=int, default=256, help="distinct operand sets the requests cycle through")
     return ap.parse_args()
 
 
@@ -232,6 +236,110 @@ def workload_config(args, bits):
             "parallelism": "independent problems per GPU (no collective in the data path)"}
 
 
+# ----------------------------------------------------------------------------- batched and serving workloads
+def run_batched(dev, runs=5):
+    """512 instances over the 64 largest primes below 2^50, m, n, k log-uniform
+    in [128, 2048] (seed 4), INT8 and FP64 forms, one graph replay per run."""
+    import torch
+    from paper_2601_07508_b300 import mwmm
+    spec = inputs.batch_instances()
+    items = []
+    for i, (m, n, k, p) in enumerate(spec):
+        A, B = inputs.problem(4000 + i, m, n, k, p)
+        items.append((torch.from_numpy(A.view(np.int64)).to(dev), torch.from_numpy(B.view(np.int64)).to(dev),
+                      torch.empty((m, n), dtype=torch.int64, device=dev), p))
+    out = {"workload": "512 instances, 64 largest primes below 2^50 (instance i uses prime i mod 64), m, n, k "
+                       "log-uniform in [128, 2048], seed 4; one CUDA-graph replay per run"}
+    ref = None
+    for form in ("int8", "fp64"):
+        fitems = items if form == "int8" else [(a, b, torch.empty_like(c), p) for (a, b, c, p) in items]
+        bt = mwmm.Batch(fitems, form=form)
+        bt.run()
+        torch.cuda.synchronize()
+        nrun = runs if form == "int8" else 1
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(nrun):
+            bt.run()
+        e1.record()
+        torch.cuda.synchronize()
+        assert bt.check() == 0
+        ms = e0.elapsed_time(e1) / nrun
+        info = bt.info
+        out[form] = {"ms_per_run": ms, "gops": info["flops_2mnk"] / ms / 1e6,
+                     "word_tflops": info["word_flops"] / ms / 1e9, "launches_per_run": info["launches"],
+                     "tc_items": info["items"], "ctas": info["ctas"]}
+        if form == "int8":
+            ref = [c.clone() for (_, _, c, _) in fitems]
+        else:
+            out["fp64_equals_int8"] = all(torch.equal(c, r) for (_, _, c, _), r in zip(fitems, ref))
+        del bt
+    out["flops_2mnk_per_run"] = sum(2.0 * m * n * k for (m, n, k, _) in spec)
+    return out
+
+
+def run_serve(dev, nreq, pool, budget=40 << 30):
+    """Poisson stream of requests (m, n, k log-uniform in [64, 4096], bitsize
+    uniform in [20, 52], seed 5) against a 40 GB budget; the rate is 0.8 x the
+    closed-loop saturation throughput measured first."""
+    import torch
+    from paper_2601_07508_b300 import mwmm
+    spec = inputs.serve_requests(count=pool)
+    ents = []
+    for i, (m, n, k, p) in enumerate(spec):
+        A, B = inputs.problem(5000 + i, m, n, k, p)
+        tA = torch.from_numpy(A.view(np.int64)).to(dev)
+        tB = torch.from_numpy(B.view(np.int64)).to(dev)
+        tC = torch.empty((m, n), dtype=torch.int64, device=dev)
+        ents.append((tA, tB, tC, p, mwmm._problems([(tA, tB, tC, p)])[0], 2.0 * m * n * k))
+    torch.cuda.synchronize()
+    srv = mwmm.Server(budget, max_inflight=3, max_batch=64)
+    last = [0] * pool
+
+    def stream(count, arrivals):
+        t0 = srv.now()
+        tickets = []
+        for i in range(count):
+            e = i % pool
+            if last[e]:
+                mwmm.mwmm_serve_wait(srv.handle, last[e], 120000)
+            if arrivals is not None:
+                target = t0 + arrivals[i]
+                while srv.now() < target:
+                    pass
+                ta = target
+            else:
+                ta = -1.0
+            st, tk = mwmm.mwmm_serve_submit_ptr(srv.handle, ents[e][4], ta)
+            assert st == 0, st
+            last[e] = tk
+            tickets.append(tk)
+        for tk in tickets:
+            assert mwmm.mwmm_serve_wait(srv.handle, tk, 300000) == 0
+        return srv.stats()
+
+    # closed loop: everything submitted at once -> saturation throughput
+    nsat = min(nreq, 4 * pool)
+    sat = stream(nsat, None)
+    sat_rps = sat["completed"] / sat["busy_s"]
+    srv.reset_stats()
+    rate = 0.8 * sat_rps
+    arrivals = inputs.poisson_arrivals(5, nreq, rate)
+    rep = stream(nreq, arrivals)
+    srv.close()
+    return {"workload": "%d requests, Poisson arrivals at 0.8 x saturation, m, n, k log-uniform in [64, 4096], "
+                        "p a random prime of bitsize uniform in [20, 52], seed 5; operands cycle through %d "
+                        "device-resident sets; 40 GB budget; INT8-word form; 3 streams, <= 64 requests per batch"
+                        % (nreq, pool),
+            "saturation_requests_per_s": sat_rps, "saturation_gops": sat["gops"],
+            "rate_requests_per_s": rate, "p50_ms": rep["p50_ms"], "p99_ms": rep["p99_ms"],
+            "mean_ms": rep["mean_ms"], "max_ms": rep["max_ms"], "gops": rep["gops"],
+            "completed": rep["completed"], "rejected": rep["rejected"], "batches": rep["batches"],
+            "mean_batch": rep["mean_batch"], "peak_inflight_batches": rep["peak_inflight"],
+            "peak_queue": rep["peak_queue"], "peak_workspace_gb": rep["peak_bytes"] / 1e9,
+            "budget_gb": rep["budget_bytes"] / 1e9}
+
+
 # ----------------------------------------------------------------------------- main arm
 def main():
     args = parse_args()
@@ -408,6 +516,9 @@ def main():
         same = all(torch.equal(hC[i], dC[i].cpu()) for i in range(len(plans)))
         e2e["matches_device_result"] = same
 
+    batched = run_batched(dev) if (rank == 0 and not args.no_batched) else None
+    serve = run_serve(dev, args.serve_requests, args.serve_pool) if (rank == 0 and not args.no_serve) else None
+
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "GOP/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -417,7 +528,8 @@ def main():
                 "data": "synthetic (seeded, entries uniform in [0,p))",
                 "config": workload_config(args, bits),
                 "roofline": roofline, "cpu_baseline": cpu_baseline, "e2e": e2e,
-                "gpu_launches": launches * world, "clocks": clocks, "per_bitsize": per_bits}
+                "gpu_launches": launches * world, "clocks": clocks, "per_bitsize": per_bits,
+                "batched_multi_prime": batched, "serve": serve}
         print(json.dumps(line))
     if dist:
         dist.destroy_process_group()

@@ -163,7 +163,7 @@ void mwmm_plan_destroy(mwmm_plan_t plan);
  * A batch is planned once: every problem gets its own plan (FP64: (u,v) by
  * the cost model, lambda from Prop. 3.3; INT8: fewest digits), their words and
  * sums share one device workspace owned by the batch, the tcgen05 work items
- * of all problems are spread over the SMs (longest first, to the least
+ * of all problems are spread over the SMs (longest first, each to the least
  * loaded SM), and the kernel launches (3 for the INT8 form, 2 for the FP64
  * form, whatever the count) are captured once into a CUDA graph.  The device
  * pointers of the problems are bound at creation: a run recomputes every C

@@ -51,6 +51,7 @@ constexpr uint32_t kTileA = BM * kTileBytes;  // 16 KB
 constexpr uint32_t kTileB = BN * kTileBytes;  // 32 KB
 constexpr uint32_t kTmemCols = 2 * BN;        // 512: two accumulator buffers
 constexpr int kSmemBytes = STAGES * (kTileA + kTileB) + 1024;
+constexpr int64_t kGroupN = 8;  // column tiles per raster group
 
 struct TcParams {
     // computed items (one product)
@@ -81,8 +82,14 @@ __device__ __forceinline__ Item computed_item(const TcParams &P, int64_t idx) {
     const int64_t rest = idx / ntiles;
     const int kc = (int)(rest % P.nkc);
     it.s = P.diag_order[rest / P.nkc];
-    it.mt = tile / P.nt_count;
-    it.nt = tile % P.nt_count;
+    // Raster in groups of kGroupN column tiles, rows inside a group first: the
+    // ~148 tiles running at once cover about 18 row tiles x 8 column tiles, a
+    // squarer region than whole rows, so fewer word tiles are fetched twice.
+    const int64_t gsz = (int64_t)P.mt_count * kGroupN;
+    const int64_t grp = tile / gsz, t = tile % gsz;
+    const int64_t width = P.nt_count - grp * kGroupN < kGroupN ? P.nt_count - grp * kGroupN : kGroupN;
+    it.mt = t / width;
+    it.nt = grp * kGroupN + t % width;
     const int ilo = it.s - (P.v - 1) > 0 ? it.s - (P.v - 1) : 0;
     const int ihi = it.s < P.u - 1 ? it.s : P.u - 1;
     it.i0 = ilo;
@@ -331,11 +338,13 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_consta
                 if (lane == 0) mbar_arrive(&tempty[buf]);
             }
             if (!alive) break;
+            // streaming stores: the sums are read once, by the recombination, so
+            // they should not displace word tiles from L2
             int32_t *dst = it.S + (int64_t)(quarter * 32 + lane) * it.B_rows + half * 128;
 #pragma unroll
             for (int q4 = 0; q4 < 32; ++q4)
-                reinterpret_cast<int4 *>(dst)[q4] =
-                    make_int4(acc[4 * q4], acc[4 * q4 + 1], acc[4 * q4 + 2], acc[4 * q4 + 3]);
+                __stcs(reinterpret_cast<int4 *>(dst) + q4,
+                       make_int4(acc[4 * q4], acc[4 * q4 + 1], acc[4 * q4 + 2], acc[4 * q4 + 3]));
         }
     }
 

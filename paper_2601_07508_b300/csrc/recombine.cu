@@ -1,15 +1,20 @@
 // Recombination of the INT8 form:
-//   C = sum_{s=0}^{u+v-2} 256^s S_s mod p,  S_s = sum_{i+j=s} A_i B_j
-// evaluated by Horner's rule from the top diagonal down,
-//   R <- (256 R + S_s) mod p,
-// in exact 64-bit integer arithmetic.  This is the alpha^i beta^j mod p
-// recombination of Alg. 5 with alpha = beta = 256 and the pairs of equal
-// i + j grouped; B300's FP64 pipe runs at 1/64 of its integer rate, so the
-// reduction uses a Barrett reciprocal instead of Alg. 1 / Alg. 2.
+//   C = sum_{s=0}^{u+v-2} gamma_s S_s mod p,  gamma_s = 256^s mod p,
+//   S_s = sum_{i+j=s} A_i B_j,
+// the alpha^i beta^j mod p recombination of Alg. 5 with alpha = beta = 256
+// and the pairs of equal i + j grouped.  B300's FP64 pipe runs at 1/64 of its
+// integer rate, so the arithmetic is exact integer arithmetic, not Alg. 1 /
+// Alg. 2.
 //
-// Bounds: 0 <= R < p < 2^52, so 256 R < 2^60; |S_s| < 2^31 per K-range and at
-// most nkc K-ranges, so y = 256 R + S_s + off with off = p * ceil(2^31 nkc / p)
-// lies in [0, 2^64) and y mod p = (256 R + S_s) mod p.
+// One K-range (nkc = 1, every product with k <= ~18k): |S_s| < 2^31, so
+// U_s = S_s + 2^31 is in [0, 2^32).  With gamma_s = gl_s + gh_s 2^26
+// (gl_s, gh_s < 2^26) the two sums A0 = sum_s gl_s U_s and A1 = sum_s gh_s U_s
+// are exact in 64 bits (at most 15 terms below 2^58), and
+//   C = (A0 + 2^26 A1 - 2^31 sum_s gamma_s) mod p,
+// which takes three Barrett-type reductions per output instead of one per
+// diagonal.  Several K-ranges: Horner's rule R <- (256 R + S_s) mod p from
+// the top diagonal down (256 R < 2^60, |sum of the ranges| < nkc 2^31, so
+// y = 256 R + S_s + off with off = p ceil(2^31 nkc / p) lies in [0, 2^64)).
 #include <cstring>
 #include <vector>
 
@@ -26,6 +31,9 @@ struct RecParams {
     int64_t ldc, m, n, A_rows, B_rows;
     int nsums, nkc;
     uint64_t p, mu, off;  // mu = floor((2^64 - 1) / p)
+    uint64_t mu90;        // floor(2^90 / p) when p > 2^26, else 0 (then every gh_s = 0)
+    uint64_t K;           // (-2^31 sum_s gamma_s) mod p
+    uint32_t gl[2 * kMaxWords], gh[2 * kMaxWords];
 };
 
 __device__ __forceinline__ uint64_t reduce_u64(uint64_t y, uint64_t p, uint64_t mu) {
@@ -36,11 +44,49 @@ __device__ __forceinline__ uint64_t reduce_u64(uint64_t y, uint64_t p, uint64_t 
     return r;
 }
 
+// (r 2^26) mod p for r < p, p > 2^26: q = floor(r 2^26 / p) < 2^26 is
+// estimated as umulhi(r, floor(2^90 / p)) (too small by at most 1); the
+// remainder is below 2p < 2^53, so 64-bit wrap-around arithmetic gives it exactly.
+__device__ __forceinline__ uint64_t shl26_mod(uint64_t r, uint64_t p, uint64_t mu90) {
+    const uint64_t q = __umul64hi(r, mu90);
+    uint64_t rem = (r << 26) - q * p;
+    if (rem >= p) rem -= p;
+    return rem;
+}
+
 // Rows row0, row0 + rstep, ... < P.m of C; each thread produces 4
 // consecutive outputs (columns c0 .. c0 + 3) of a row.
 __device__ __forceinline__ void recombine_rows(const RecParams &P, int64_t c0, int64_t row0, int64_t rstep) {
     if (c0 >= P.n) return;
     const int64_t plane = P.A_rows * P.B_rows;
+    if (P.nkc == 1) {
+        for (int64_t row = row0; row < P.m; row += rstep) {
+            uint64_t A0[4] = {0, 0, 0, 0}, A1[4] = {0, 0, 0, 0};
+            const int32_t *src = P.S + row * P.B_rows + c0;
+            for (int s = 0; s < P.nsums; ++s) {
+                const int4 v = *reinterpret_cast<const int4 *>(src + (int64_t)s * plane);
+                const uint32_t U[4] = {(uint32_t)v.x + 0x80000000u, (uint32_t)v.y + 0x80000000u,
+                                       (uint32_t)v.z + 0x80000000u, (uint32_t)v.w + 0x80000000u};
+                const uint64_t gl = P.gl[s], gh = P.gh[s];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    A0[e] += gl * U[e];
+                    A1[e] += gh * U[e];
+                }
+            }
+            uint64_t *out = P.C + row * P.ldc + c0;
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                uint64_t r = reduce_u64(A0[e] + P.K, P.p, P.mu);
+                if (P.mu90) {
+                    r += shl26_mod(reduce_u64(A1[e], P.p, P.mu), P.p, P.mu90);
+                    if (r >= P.p) r -= P.p;
+                }
+                if (c0 + e < P.n) out[e] = r;
+            }
+        }
+        return;
+    }
     for (int64_t row = row0; row < P.m; row += rstep) {
     uint64_t R[4] = {0, 0, 0, 0};
     for (int s = P.nsums - 1; s >= 0; --s) {
@@ -68,8 +114,10 @@ __global__ void __launch_bounds__(256) recombine_kernel(const __grid_constant__ 
 // Batched: block b handles 1024 columns of rows [y0, y0 + 8) of problem
 // jobs[b] = (problem, y0, column block, 0).
 __global__ void __launch_bounds__(256) recombine_batched_kernel(const RecParams *probs, const int4 *jobs) {
+    __shared__ RecParams P;  // staged once: the loops read it many times
     const int4 j = jobs[blockIdx.x];
-    const RecParams &P = probs[j.x];
+    if (threadIdx.x == 0) P = probs[j.x];
+    __syncthreads();
     const int64_t c0 = ((int64_t)j.z * blockDim.x + threadIdx.x) * 4;
     for (int64_t r = j.y; r < j.y + 8 && r < P.m; ++r) recombine_rows(P, c0, r, P.m);
 }
@@ -89,6 +137,16 @@ RecParams make_rec_params(const Plan &pl, const int32_t *S, uint64_t *C, int64_t
     P.mu = (~uint64_t(0)) / pl.p;
     const unsigned __int128 need = (unsigned __int128)pl.nkc << 31;
     P.off = (uint64_t)((need + pl.p - 1) / pl.p * pl.p);
+    P.mu90 = pl.p > (uint64_t(1) << 26) ? (uint64_t)(((unsigned __int128)1 << 90) / pl.p) : 0;
+    uint64_t g = 1 % pl.p, gsum = 0;
+    for (int s = 0; s < 2 * kMaxWords; ++s) {
+        P.gl[s] = (uint32_t)(g & ((1u << 26) - 1));
+        P.gh[s] = (uint32_t)(g >> 26);
+        if (s < pl.nsums) gsum = (gsum + g) % pl.p;
+        g = mulmod_u64(g, 256, pl.p);
+    }
+    const uint64_t bias = mulmod_u64(gsum, uint64_t(1) << 31, pl.p);
+    P.K = (pl.p - bias) % pl.p;
     return P;
 }
 

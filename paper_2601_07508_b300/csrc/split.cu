@@ -157,8 +157,10 @@ __global__ void __launch_bounds__(256) split_int8_kernel(const __grid_constant__
 __global__ void __launch_bounds__(256) split_batched_kernel(const SplitParams *jobs, const int4 *blocks,
                                                             int fp64) {
     __shared__ uint64_t tile[kST][kST + 1];
+    __shared__ SplitParams P;  // staged once: the loops read it many times
     const int4 bl = blocks[blockIdx.x];
-    const SplitParams &P = jobs[bl.x];
+    if (threadIdx.x == 0) P = jobs[bl.x];
+    __syncthreads();
     if (fp64) split_fp64_tile(P, tile, bl.y, bl.z);
     else split_int8_tile(P, tile, bl.y, bl.z);
 }
