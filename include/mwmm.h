@@ -87,7 +87,13 @@ typedef struct {
                          64 in [64, 1024] (0: 1024) */
     int64_t kc;       /* INT8 form: k-range of one INT32 sum, a multiple of 64
                          (0: the largest allowed by |S_s| < 2^31) */
-    int32_t reserved[8];
+    int32_t tc_pair;  /* INT8 form, m > 128: nonzero uses the two-CTA tcgen05
+                         kernel (256 x 256 tiles on an SM pair, cta_group::2)
+                         instead of the one-CTA kernel (128 x 256 tiles).
+                         Bit-exact, but currently slower on B300 (its TMA
+                         completions reach the issuing CTA through a
+                         software relay); default 0 */
+    int32_t reserved[7];
 } mwmm_plan_opts;
 
 /* What a plan decided (mwmm_plan_info). */
@@ -101,6 +107,7 @@ typedef struct {
     int64_t lambda_max;     /* FP64: largest block size allowed by Prop. 3.3 */
     int64_t tc_chunk;       /* INT8: digit products per FP32 tensor-memory chunk */
     int64_t kc;             /* INT8: k-range of one INT32 diagonal sum */
+    int32_t tc_pair;        /* INT8: 1 when the two-CTA kernel computes the word products */
     int32_t nkc;            /* INT8: number of k-ranges, ceil(k / kc) */
     int32_t nsums;          /* INT8: number of diagonal sums u + v - 1 */
     double q;               /* fl(1/p) */

@@ -356,6 +356,265 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_consta
                      : "memory");
 }
 
+// ---------------------------------------------------------------------------
+// Pair kernel (opt-in, plan option tc_pair): a cluster of two CTAs on two SMs
+// computes a 256 x 256 tile with tcgen05.mma.cta_group::2 (M = 256 split over
+// the pair, each CTA holding its 128 rows of A and its 128-row half of B).
+// Each SM then streams 32 KB of operands per 64-wide k-block instead of 48 KB,
+// and 6 stages fit in shared memory.  Roles per CTA as above; only the even
+// CTA ("leader") issues MMAs.  The odd CTA's warp 1 relays the completion of
+// its own TMA stages to the leader (remote mbarrier arrive), and its epilogue
+// warps report drained accumulators to the leader the same way; the leader's
+// commits are multicast to both CTAs.  Measured on B300 this relay makes a
+// stage's round trip several times longer than the one-CTA kernel's, so the
+// one-CTA kernel stays the default; the relay would go away if the odd CTA's
+// copies completed on the leader's barrier directly (tensor TMA with
+// .cta_group::2).
+constexpr int P_STAGES = 6;
+constexpr int BM2 = 256;
+constexpr uint32_t kTileA2 = 128 * kTileBytes;  // own 128 rows of A: 16 KB
+constexpr uint32_t kTileB2 = 128 * kTileBytes;  // own half of B: 16 KB
+constexpr int kSmemPair = P_STAGES * (kTileA2 + kTileB2) + 1024;
+constexpr uint32_t kIdescPair = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                                ((uint32_t)(BM2 >> 4) << 24);
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ uint32_t peer_addr(const void *local, uint32_t rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(smem_u32(local)), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t cluster_addr) {
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr) : "memory");
+}
+__device__ __forceinline__ void cluster_sync_all() {
+    asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;" ::: "memory");
+}
+__device__ __forceinline__ void mma_bf16_pair(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
+        "l"(adesc), "l"(bdesc), "r"(kIdescPair), "r"(acc)
+        : "memory");
+}
+// Arrive once on `bar` (same shared-memory offset) in every CTA of `mask`
+// when all MMAs issued so far by this thread have completed.
+__device__ __forceinline__ void mma_commit_pair(uint64_t *bar, uint16_t mask) {
+    asm volatile(
+        "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+            smem_u32(bar)),
+        "h"(mask)
+        : "memory");
+}
+
+__device__ __forceinline__ Item pair_item(const TcParams &P, int64_t idx) {
+    // tiles of 256 rows: mt counts 256-row tiles here; A_rows % 256 == 0
+    Item it;
+    const int64_t mt2 = P.mt_count / 2;
+    const int64_t ntiles = mt2 * P.nt_count;
+    const int64_t tile = idx % ntiles;
+    const int64_t rest = idx / ntiles;
+    const int kc = (int)(rest % P.nkc);
+    it.s = P.diag_order[rest / P.nkc];
+    const int64_t gsz = mt2 * kGroupN;
+    const int64_t grp = tile / gsz, t = tile % gsz;
+    const int64_t width = P.nt_count - grp * kGroupN < kGroupN ? P.nt_count - grp * kGroupN : kGroupN;
+    it.mt = t / width;  // 256-row tile index
+    it.nt = grp * kGroupN + t % width;
+    const int ilo = it.s - (P.v - 1) > 0 ? it.s - (P.v - 1) : 0;
+    const int ihi = it.s < P.u - 1 ? it.s : P.u - 1;
+    it.i0 = ilo;
+    it.w = ihi - ilo + 1;
+    it.kb0 = (int64_t)kc * P.kcb;
+    const int64_t left = P.nkb - it.kb0;
+    it.nkbc = left < P.kcb ? left : P.kcb;
+    it.Aw = P.Aw;
+    it.Bw = P.Bw;
+    it.A_rows = P.A_rows;
+    it.B_rows = P.B_rows;
+    it.nkb = P.nkb;
+    it.S = P.S + (((int64_t)it.s * P.nkc + kc) * P.A_rows + it.mt * BM2) * P.B_rows + it.nt * BN;
+    return it;
+}
+
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS, 1)
+    gemm_tc_pair_kernel(const __grid_constant__ TcParams P) {
+    extern __shared__ uint8_t smem_raw[];
+    __shared__ __align__(8) uint64_t full[P_STAGES], empty[P_STAGES], pfull[P_STAGES], tfull[2], tempty[2], done;
+    __shared__ uint32_t tmem_base_sh;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t rank = cluster_rank();
+    const bool leader = rank == 0;
+    const uint32_t raw = smem_u32(smem_raw);
+    const uint32_t pad = ((raw + 1023u) & ~1023u) - raw;
+    uint8_t *sA = smem_raw + pad;
+    uint8_t *sB = sA + P_STAGES * kTileA2;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < P_STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+            mbar_init(&pfull[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&tfull[b], 1);
+            mbar_init(&tempty[b], 2 * EPI_WARPS);  // both CTAs' epilogue warps (leader's copy)
+        }
+        mbar_init(&done, 1);
+        fence_mbar_init();
+    }
+    if (warp == 1) {  // one warp of each CTA of the pair allocates, collectively
+        asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&tmem_base_sh)),
+                     "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    cluster_sync_all();  // barriers of both CTAs initialised, TMEM allocated
+    tc_fence_after();
+    const uint32_t tmem_base = tmem_base_sh;
+    const int64_t cid = blockIdx.x >> 1, ncl = gridDim.x >> 1;
+
+    if (warp == 0) {
+        if (lane == 0) {  // ---------------- TMA producer (both CTAs)
+            uint64_t g = 0;
+            bool alive = true;
+            for (int64_t idx = cid; alive && idx < P.nitems; idx += ncl) {
+                const Item it = pair_item(P, idx);
+                const int64_t nvb = (int64_t)it.w * it.nkbc;
+                for (int64_t t = 0; t < nvb; ++t, ++g) {
+                    const int slot = (int)(g % P_STAGES);
+                    if (!mbar_wait(&empty[slot], (uint32_t)(((g / P_STAGES) & 1) ^ 1), P.err)) {
+                        alive = false;
+                        break;
+                    }
+                    const int i = it.i0 + (int)(t / it.nkbc);
+                    const int j = it.s - i;
+                    const int64_t kb = it.kb0 + t % it.nkbc;
+                    const uint8_t *a = it.Aw + (((int64_t)i * it.nkb + kb) * it.A_rows + it.mt * BM2 + rank * 128) *
+                                                   kTileBytes;
+                    const uint8_t *b = it.Bw + (((int64_t)j * it.nkb + kb) * it.B_rows + it.nt * BN + rank * 128) *
+                                                   kTileBytes;
+                    mbar_arrive_expect_tx(&full[slot], kTileA2 + kTileB2);
+                    bulk_g2s(sA + slot * kTileA2, a, kTileA2, &full[slot]);
+                    bulk_g2s(sB + slot * kTileB2, b, kTileB2, &full[slot]);
+                }
+            }
+            for (int s = 0; s < P_STAGES; ++s) {  // let every copy land before exit
+                const uint64_t armed = g > (uint64_t)s ? (g - s + P_STAGES - 1) / P_STAGES : 0;
+                if (armed) mbar_wait(&full[s], (uint32_t)((armed - 1) & 1), P.err);
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0 && leader) {  // ---------------- MMA issuer (leader)
+            uint64_t g = 0, c = 0;
+            bool alive = true;
+            const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
+            for (int64_t idx = cid; alive && idx < P.nitems; idx += ncl) {
+                const Item it = pair_item(P, idx);
+                const int64_t nvb = (int64_t)it.w * it.nkbc;
+                for (int64_t t0 = 0; alive && t0 < nvb; t0 += P.chunk_blocks, ++c) {
+                    const int buf = (int)(c & 1);
+                    if (!mbar_wait(&tempty[buf], (uint32_t)(((c >> 1) & 1) ^ 1), P.err)) {
+                        alive = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t dt = tmem_base + (uint32_t)(buf * BN);
+                    const int64_t tend = t0 + P.chunk_blocks < nvb ? t0 + P.chunk_blocks : nvb;
+                    for (int64_t t = t0; t < tend; ++t, ++g) {
+                        const int slot = (int)(g % P_STAGES);
+                        const uint32_t par = (uint32_t)((g / P_STAGES) & 1);
+                        if (!mbar_wait(&full[slot], par, P.err) || !mbar_wait(&pfull[slot], par, P.err)) {
+                            alive = false;
+                            break;
+                        }
+                        tc_fence_after();
+                        const uint64_t ad = sdesc(a0 + slot * kTileA2), bd = sdesc(b0 + slot * kTileB2);
+#pragma unroll
+                        for (int kk = 0; kk < 4; ++kk)
+                            mma_bf16_pair(dt, ad + 2 * kk, bd + 2 * kk, (t > t0 || kk > 0) ? 1u : 0u);
+                        mma_commit_pair(&empty[slot], 3);
+                    }
+                    mma_commit_pair(&tfull[buf], 3);
+                }
+            }
+            mma_commit_pair(&done, 1);
+            mbar_wait(&done, 0, P.err);
+        } else if (lane == 0) {  // ---------------- forwarder (odd CTA)
+            const uint32_t lead_pfull = peer_addr(&pfull[0], 0);
+            uint64_t g = 0;
+            bool alive = true;
+            for (int64_t idx = cid; alive && idx < P.nitems; idx += ncl) {
+                const Item it = pair_item(P, idx);
+                const int64_t nvb = (int64_t)it.w * it.nkbc;
+                for (int64_t t = 0; t < nvb; ++t, ++g) {
+                    const int slot = (int)(g % P_STAGES);
+                    if (!mbar_wait(&full[slot], (uint32_t)((g / P_STAGES) & 1), P.err)) {
+                        alive = false;
+                        break;
+                    }
+                    mbar_arrive_cluster(lead_pfull + (uint32_t)(slot * sizeof(uint64_t)));
+                }
+            }
+        }
+    } else {  // -------------------------------- epilogue warps 2..9 (both CTAs)
+        const int quarter = warp & 3;
+        const int half = (warp - 2) >> 2;
+        const uint32_t tlane = tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(half * 128);
+        const uint32_t lead_tempty = peer_addr(&tempty[0], 0);
+        uint64_t c = 0;
+        bool alive = true;
+        for (int64_t idx = cid; alive && idx < P.nitems; idx += ncl) {
+            const Item it = pair_item(P, idx);
+            const int64_t nvb = (int64_t)it.w * it.nkbc;
+            const int64_t nch = (nvb + P.chunk_blocks - 1) / P.chunk_blocks;
+            int32_t acc[128];
+#pragma unroll
+            for (int e = 0; e < 128; ++e) acc[e] = 0;
+            for (int64_t ch = 0; ch < nch; ++ch, ++c) {
+                const int buf = (int)(c & 1);
+                const bool ok = mbar_wait(&tfull[buf], (uint32_t)((c >> 1) & 1), P.err);
+                if (!__all_sync(0xffffffffu, ok)) {
+                    alive = false;
+                    break;
+                }
+                tc_fence_after();
+#pragma unroll
+                for (int jb = 0; jb < 4; ++jb) {
+                    uint32_t r[32];
+                    tmem_ld32(tlane + (uint32_t)(buf * BN + jb * 32), r);
+#pragma unroll
+                    for (int e = 0; e < 32; ++e) acc[jb * 32 + e] += __float2int_rn(__uint_as_float(r[e]));
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive_cluster(lead_tempty + (uint32_t)(buf * sizeof(uint64_t)));
+            }
+            if (!alive) break;
+            int32_t *dst = it.S + (int64_t)(rank * 128 + quarter * 32 + lane) * it.B_rows + half * 128;
+#pragma unroll
+            for (int q4 = 0; q4 < 32; ++q4)
+                __stcs(reinterpret_cast<int4 *>(dst) + q4,
+                       make_int4(acc[4 * q4], acc[4 * q4 + 1], acc[4 * q4 + 2], acc[4 * q4 + 3]));
+        }
+    }
+
+    tc_fence_before();
+    cluster_sync_all();  // no CTA frees TMEM or exits while its peer may still signal it
+    tc_fence_after();
+    if (warp == 1)
+        asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(kTmemCols)
+                     : "memory");
+}
+
 int sm_count() {
     static int cached[64] = {0};
     int dev = 0;
@@ -363,6 +622,35 @@ int sm_count() {
     if (!cached[dev]) {
         int n = 0;
         if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 148;
+        cached[dev] = n;
+    }
+    return cached[dev];
+}
+
+// Clusters of two that can be resident at once (the pair kernel is
+// persistent: one cluster per SM pair, never more than fit).
+int pair_clusters() {
+    static int cached[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+    if (!cached[dev]) {
+        if (set_smem_attr(reinterpret_cast<const void *>(gemm_tc_pair_kernel), kSmemPair) != cudaSuccess) return 0;
+        cudaLaunchConfig_t cfg;
+        std::memset(&cfg, 0, sizeof(cfg));
+        cfg.gridDim = dim3(2 * (unsigned)(sm_count() / 2), 1, 1);
+        cfg.blockDim = dim3(THREADS, 1, 1);
+        cfg.dynamicSmemBytes = kSmemPair;
+        cudaLaunchAttribute attr;
+        attr.id = cudaLaunchAttributeClusterDimension;
+        attr.val.clusterDim.x = 2;
+        attr.val.clusterDim.y = 1;
+        attr.val.clusterDim.z = 1;
+        cfg.attrs = &attr;
+        cfg.numAttrs = 1;
+        int n = 0;
+        if (cudaOccupancyMaxActiveClusters(&n, reinterpret_cast<const void *>(gemm_tc_pair_kernel), &cfg) !=
+                cudaSuccess || n <= 0)
+            return 0;
         cached[dev] = n;
     }
     return cached[dev];
@@ -406,6 +694,16 @@ int launch_gemm_tc(const Plan &pl, const void *Aw, const void *Bw, int32_t *S, i
         }
     for (int s = 0; s < 2 * kMaxWords; ++s) P.diag_order[s] = s < pl.nsums ? order[s] : 0;
     if (P.nitems == 0) return 0;
+    if (pl.tc_pair) {
+        P.nitems = (int64_t)(P.mt_count / 2) * P.nt_count * pl.nsums * pl.nkc;
+        cudaError_t e = set_smem_attr(reinterpret_cast<const void *>(gemm_tc_pair_kernel), kSmemPair);
+        if (e != cudaSuccess) return (int)e;
+        const int clusters = pair_clusters();
+        if (clusters <= 0) return (int)cudaErrorLaunchOutOfResources;
+        const int64_t ncl = P.nitems < clusters ? P.nitems : clusters;
+        gemm_tc_pair_kernel<<<(unsigned)(2 * ncl), THREADS, kSmemPair, static_cast<cudaStream_t>(stream)>>>(P);
+        return (int)cudaGetLastError();
+    }
     cudaError_t e = set_smem_attr(reinterpret_cast<const void *>(gemm_tc_kernel<false>), kSmemBytes);
     if (e != cudaSuccess) return (int)e;
     const int64_t sms = sm_count();
@@ -419,6 +717,7 @@ int tc_sm_count() { return sm_count(); }
 int prepare_tc_attributes() {
     cudaError_t e = set_smem_attr(reinterpret_cast<const void *>(gemm_tc_kernel<false>), kSmemBytes);
     if (e == cudaSuccess) e = set_smem_attr(reinterpret_cast<const void *>(gemm_tc_kernel<true>), kSmemBytes);
+    if (e == cudaSuccess) (void)pair_clusters();  // cache the cluster count outside any capture
     return (int)e;
 }
 

@@ -47,6 +47,7 @@ struct Plan {
     int big_p = 0;                               // p > 2^52 / 3: split Alg. 2
     // INT8 form
     int64_t tc_chunk = 0, kc = 0;
+    int tc_pair = 0;  // 1: 2-CTA kernel, A rows padded to 256
     int nkc = 0, nsums = 0;
     // layout
     int64_t kb_elems = 0, nkb = 0, A_rows = 0, B_rows = 0;

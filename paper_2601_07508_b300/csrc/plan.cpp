@@ -166,7 +166,9 @@ mwmm_status make_plan(Plan *pl, int64_t m, int64_t n, int64_t k, uint64_t p, int
         P.nkc = k > 0 ? (int)ceil_div(k, kc) : 0;
         P.kb_elems = kTcKB;
         P.nkb = ceil_div(k, kTcKB);
-        P.A_rows = round_up(m > 0 ? m : 1, kTcBM);
+        // the 2-CTA kernel (opt-in) computes 256-row tiles
+        P.tc_pair = (m > kTcBM && o.tc_pair) ? 1 : 0;
+        P.A_rows = round_up(m > 0 ? m : 1, P.tc_pair ? 2 * kTcBM : kTcBM);
         P.B_rows = round_up(n > 0 ? n : 1, kTcBN);
         uint64_t abytes = (uint64_t)u * P.nkb * P.A_rows * kTileBytes;
         uint64_t bbytes = (uint64_t)v * P.nkb * P.B_rows * kTileBytes;

@@ -251,3 +251,18 @@ def test_mulmod_alg2_matches_xy_mod_p(M, oracle, p):
     M.mwmm_mulmod(torch.from_numpy(x.astype(np.float64)).cuda(), torch.from_numpy(y.astype(np.float64)).cuda(),
                   p, out)
     assert np.array_equal(out.cpu().numpy().astype(np.uint64), oracle.mulmod_vec(x, y, p))
+
+
+@pytest.mark.parametrize("shape", [(129, 300, 257), (256, 256, 64), (700, 520, 1100), (1000, 90, 333)])
+@pytest.mark.parametrize("b", [20, 40, 52])
+def test_int8_pair_and_single_cta_kernels(M, oracle, shape, b):
+    """The two-CTA kernel (256-row tiles on an SM pair, tcgen05 cta_group::2)
+    and the one-CTA kernel (128-row tiles) both match the oracle."""
+    m, n, k = shape
+    p = SWEEP[b]
+    A, B = inputs.problem(60 + b, m, n, k, p)
+    ref = oracle.matmul_mod(A, B, p)
+    for pair in (False, True):
+        C, plan = gpu_product(M, A, B, p, form="int8", tc_pair=pair)
+        assert plan.info["tc_pair"] == (1 if pair else 0)
+        assert np.array_equal(C, ref), pair
