@@ -52,6 +52,7 @@ def parse_args():
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
     ap.add_argument("--no-batched", action="store_true", help="skip the 512-instance multi-prime batch")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving run")
+    ap.add_argument("--no-shapes", action="store_true", help="skip the 50-bit shape study")
     ap.add_argument("--serve-requests", type=int, default=20000)
     ap.add_argument("--serve-pool", type=int, default=256, help="distinct operand sets the requests cycle through")
     return ap.parse_args()
@@ -275,6 +276,48 @@ def run_batched(dev, runs=5):
             out["fp64_equals_int8"] = all(torch.equal(c, r) for (_, _, c, _), r in zip(fitems, ref))
         del bt
     out["flops_2mnk_per_run"] = sum(2.0 * m * n * k for (m, n, k, _) in spec)
+    return out
+
+
+def run_shapes(dev):
+    """p = largest prime below 2^50: rank update (8192, 8192, 512), tall-skinny
+    (8192, 64, 8192) and cube (8192, 8192, 8192); INT8-word form vs FP64 (2,2)
+    (and FP64 (2,3), the form the cost model picks at 50 bits)."""
+    import torch
+    from paper_2601_07508_b300 import mwmm
+    p = inputs.largest_prime_below_pow2(50)
+    out = {}
+    for (m, n, k), seed, name in (((8192, 8192, 512), 1, "rank_update"), ((8192, 64, 8192), 2, "tall_skinny"),
+                                  ((8192, 8192, 8192), 3, "cube")):
+        A, B = inputs.problem(seed, m, n, k, p)
+        dA = torch.from_numpy(A.view(np.int64)).to(dev)
+        dB = torch.from_numpy(B.view(np.int64)).to(dev)
+        res = {"m": m, "n": n, "k": k}
+        ref = None
+        for form, uv in (("int8", (0, 0)), ("fp64", (2, 2)), ("fp64", (2, 3))):
+            pl = mwmm.Plan(m, n, k, p, uv[0], uv[1], form=form)
+            pl.alloc_workspace(dev)
+            C = pl.matmul(dA, dB)
+            torch.cuda.synchronize()
+            mwmm.mwmm_plan_set_timing(pl.handle, True)
+            reps = 5 if form == "int8" else 1
+            for _ in range(reps):
+                pl.matmul(dA, dB, C)
+            t = mwmm.mwmm_plan_timing(pl.handle)
+            assert pl.check() == 0
+            ms = t["total_ms"] / t["calls"]
+            key = form if form == "int8" else "fp64_%d%d" % uv
+            d = pl.info
+            res[key] = {"ms": ms, "gops": 2.0 * m * n * k / ms / 1e6, "uv": [d["u"], d["v"]],
+                        "word_product_ms": t["gemm_ms"] / t["calls"]}
+            if ref is None:
+                ref = C
+            else:
+                res[key]["equals_int8"] = bool(torch.equal(C, ref))
+            del pl, C
+            torch.cuda.empty_cache()
+        res["int8_over_fp64_22"] = res["fp64_22"]["ms"] / res["int8"]["ms"]
+        out[name] = res
     return out
 
 
@@ -517,6 +560,7 @@ def main():
         e2e["matches_device_result"] = same
 
     batched = run_batched(dev) if (rank == 0 and not args.no_batched) else None
+    shapes = run_shapes(dev) if (rank == 0 and not args.no_shapes) else None
     serve = run_serve(dev, args.serve_requests, args.serve_pool) if (rank == 0 and not args.no_serve) else None
 
     if rank == 0:
@@ -529,7 +573,7 @@ def main():
                 "config": workload_config(args, bits),
                 "roofline": roofline, "cpu_baseline": cpu_baseline, "e2e": e2e,
                 "gpu_launches": launches * world, "clocks": clocks, "per_bitsize": per_bits,
-                "batched_multi_prime": batched, "serve": serve}
+                "batched_multi_prime": batched, "shapes_50bit": shapes, "serve": serve}
         print(json.dumps(line))
     if dist:
         dist.destroy_process_group()
