@@ -61,7 +61,7 @@ namespace mwmm {
 // and offsets.
 static void lpt_schedule(std::vector<mwmm::TcItem> &items, int ctas, std::vector<int64_t> &off) {
     std::vector<int64_t> cost(items.size());
-    for (size_t i = 0; i < items.size(); ++i) cost[i] = items[i].w * items[i].nkbc + 2;  // +2: drain and store
+    for (size_t i = 0; i < items.size(); ++i) cost[i] = items[i].ni * items[i].nkbc + 2;  // +2: drain and store
     std::vector<size_t> order(items.size());
     for (size_t i = 0; i < order.size(); ++i) order[i] = i;
     std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) { return cost[a] > cost[b]; });
@@ -87,12 +87,15 @@ static void lpt_schedule(std::vector<mwmm::TcItem> &items, int ctas, std::vector
 }
 
 // Work items of one INT8-form problem whose words start at Aw / Bw and whose
-// sums start at S (see the plan layout).
+// sums start at S (see the plan layout and TcItem).
 static void tc_items(const Plan &pl, const uint8_t *Aw, const uint8_t *Bw, int32_t *S, std::vector<mwmm::TcItem> &items) {
-    const int64_t mtc = pl.A_rows / mwmm::kTcBM, ntc = pl.B_rows / mwmm::kTcBN;
+    const int64_t mtc = pl.A_rows / mwmm::kTcBM;
+    const int64_t ntc = pl.tc_nb == mwmm::kTcBN ? pl.B_rows / mwmm::kTcBN : 1;
     const int64_t kcb = pl.kc / mwmm::kTcKB;
-    for (int s = 0; s < pl.nsums; ++s) {
-        const int ilo = std::max(0, s - (pl.v - 1)), ihi = std::min(s, pl.u - 1);
+    const int64_t plane = (int64_t)pl.nkc * pl.A_rows * pl.B_rows;
+    for (int s0 = 0; s0 < pl.nsums; s0 += pl.tc_ndiag) {
+        const int nd = std::min(pl.tc_ndiag, pl.nsums - s0);
+        const int ilo = std::max(0, s0 - (pl.v - 1)), ihi = std::min(s0 + nd - 1, pl.u - 1);
         for (int kc = 0; kc < pl.nkc; ++kc)
             for (int64_t mt = 0; mt < mtc; ++mt)
                 for (int64_t nt = 0; nt < ntc; ++nt) {
@@ -100,7 +103,7 @@ static void tc_items(const Plan &pl, const uint8_t *Aw, const uint8_t *Bw, int32
                     std::memset(&it, 0, sizeof(it));
                     it.Aw = Aw;
                     it.Bw = Bw;
-                    it.S = S + (((int64_t)s * pl.nkc + kc) * pl.A_rows + mt * mwmm::kTcBM) * pl.B_rows +
+                    it.S = S + (((int64_t)s0 * pl.nkc + kc) * pl.A_rows + mt * mwmm::kTcBM) * pl.B_rows +
                            nt * mwmm::kTcBN;
                     it.A_rows = pl.A_rows;
                     it.B_rows = pl.B_rows;
@@ -109,9 +112,13 @@ static void tc_items(const Plan &pl, const uint8_t *Aw, const uint8_t *Bw, int32
                     it.nkbc = std::min(kcb, pl.nkb - it.kb0);
                     it.mt = mt;
                     it.nt = nt;
-                    it.s = s;
+                    it.plane = plane;
+                    it.s0 = s0;
+                    it.ndiag = nd;
+                    it.nb = pl.tc_nb;
                     it.i0 = ilo;
-                    it.w = ihi - ilo + 1;
+                    it.ni = ihi - ilo + 1;
+                    it.v = pl.v;
                     items.push_back(it);
                 }
     }

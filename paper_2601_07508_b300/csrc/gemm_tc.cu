@@ -58,8 +58,10 @@ struct TcParams {
     const uint8_t *Aw, *Bw;
     int32_t *S;
     int64_t nkb, A_rows, B_rows, kcb, nitems;
-    int u, v, nsums, nkc, mt_count, nt_count;
-    int diag_order[2 * kMaxWords];
+    int u, v, nsums, nkc, mt_count, nt_count, nb;
+    // diagonal windows, heaviest first: window g covers diagonals
+    // g_s0[g] .. g_s0[g] + g_nd[g] - 1 and A words g_i0[g] .. + g_ni[g] - 1
+    int g_s0[2 * kMaxWords], g_nd[2 * kMaxWords], g_i0[2 * kMaxWords], g_ni[2 * kMaxWords];
     // table items (batch): CTA c runs items[cta_off[c] .. cta_off[c + 1])
     const TcItem *items;
     const int64_t *cta_off;
@@ -67,13 +69,17 @@ struct TcParams {
     int *err;
 };
 
-// One work item with everything the three roles need.
+// One work item with everything the three roles need (see TcItem).
 struct Item {
     const uint8_t *Aw, *Bw;
-    int32_t *S;  // origin of the item's 128 x 256 output tile, row stride B_rows
-    int64_t A_rows, B_rows, nkb, kb0, nkbc, mt, nt;
-    int s, i0, w;
+    int32_t *S;  // S of diagonal s0 at the item's tile origin, row stride B_rows
+    int64_t A_rows, B_rows, nkb, kb0, nkbc, mt, nt, plane;
+    int s0, ndiag, nb, i0, ni, v;
 };
+
+// A static zero tile stands in for the B slices of pairs (i, j) with j
+// outside [0, v) inside a diagonal window (device globals start zeroed).
+__device__ __align__(128) uint8_t g_zero_slice[BN * kTileBytes];
 
 __device__ __forceinline__ Item computed_item(const TcParams &P, int64_t idx) {
     Item it;
@@ -81,7 +87,13 @@ __device__ __forceinline__ Item computed_item(const TcParams &P, int64_t idx) {
     const int64_t tile = idx % ntiles;
     const int64_t rest = idx / ntiles;
     const int kc = (int)(rest % P.nkc);
-    it.s = P.diag_order[rest / P.nkc];
+    const int grp_w = (int)(rest / P.nkc);
+    it.s0 = P.g_s0[grp_w];
+    it.ndiag = P.g_nd[grp_w];
+    it.i0 = P.g_i0[grp_w];
+    it.ni = P.g_ni[grp_w];
+    it.nb = P.nb;
+    it.v = P.v;
     // Raster in groups of kGroupN column tiles, rows inside a group first: the
     // ~148 tiles running at once cover about 18 row tiles x 8 column tiles, a
     // squarer region than whole rows, so fewer word tiles are fetched twice.
@@ -90,10 +102,6 @@ __device__ __forceinline__ Item computed_item(const TcParams &P, int64_t idx) {
     const int64_t width = P.nt_count - grp * kGroupN < kGroupN ? P.nt_count - grp * kGroupN : kGroupN;
     it.mt = t / width;
     it.nt = grp * kGroupN + t % width;
-    const int ilo = it.s - (P.v - 1) > 0 ? it.s - (P.v - 1) : 0;
-    const int ihi = it.s < P.u - 1 ? it.s : P.u - 1;
-    it.i0 = ilo;
-    it.w = ihi - ilo + 1;
     it.kb0 = (int64_t)kc * P.kcb;
     const int64_t left = P.nkb - it.kb0;
     it.nkbc = left < P.kcb ? left : P.kcb;
@@ -102,7 +110,8 @@ __device__ __forceinline__ Item computed_item(const TcParams &P, int64_t idx) {
     it.A_rows = P.A_rows;
     it.B_rows = P.B_rows;
     it.nkb = P.nkb;
-    it.S = P.S + (((int64_t)it.s * P.nkc + kc) * P.A_rows + it.mt * BM) * P.B_rows + it.nt * BN;
+    it.plane = (int64_t)P.nkc * P.A_rows * P.B_rows;
+    it.S = P.S + (((int64_t)it.s0 * P.nkc + kc) * P.A_rows + it.mt * BM) * P.B_rows + it.nt * BN;
     return it;
 }
 
@@ -119,9 +128,13 @@ __device__ __forceinline__ Item table_item(const TcParams &P, int64_t pos) {
     it.nkbc = d.nkbc;
     it.mt = d.mt;
     it.nt = d.nt;
-    it.s = d.s;
+    it.plane = d.plane;
+    it.s0 = d.s0;
+    it.ndiag = d.ndiag;
+    it.nb = d.nb;
     it.i0 = d.i0;
-    it.w = d.w;
+    it.ni = d.ni;
+    it.v = d.v;
     return it;
 }
 
@@ -159,16 +172,19 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
     return d;
 }
 
-// Instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major.
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
-                            ((uint32_t)(BM >> 4) << 24);
+// Instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major,
+// M = 128, N = n (a multiple of 16, at most 256).
+__device__ __forceinline__ uint32_t idesc_n(int n) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+}
 
-__device__ __forceinline__ void mma_bf16(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t acc) {
+__device__ __forceinline__ void mma_bf16(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t acc) {
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
         "setp.ne.b32 p, %4, 0;\n\t"
         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
-        "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(acc)
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
         : "memory");
 }
 
@@ -243,21 +259,36 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_consta
             const ItemRange<kTable> R(P);
             for (int64_t idx = R.begin; alive && idx < R.end; idx += R.step) {
                 const Item it = get_item<kTable>(P, idx);
-                const int64_t nvb = (int64_t)it.w * it.nkbc;
-                for (int64_t t = 0; t < nvb; ++t, ++g) {
-                    const int slot = (int)(g % STAGES);
-                    if (!mbar_wait(&empty[slot], (uint32_t)(((g / STAGES) & 1) ^ 1), P.err)) {
-                        alive = false;
-                        break;
+                // One thread issues every copy, so the per-stage work is kept to a
+                // few adds: nested (word, k-block) loops and running addresses.
+                const uint32_t slice = (uint32_t)it.nb * kTileBytes;
+                const uint32_t stage_bytes = kTileA + (uint32_t)it.ndiag * slice;
+                const int64_t a_step = it.A_rows * kTileBytes, b_step = it.B_rows * kTileBytes;
+                const int64_t b_word = it.nkb * b_step;  // bytes between consecutive B words
+                for (int ii = 0; alive && ii < it.ni; ++ii) {
+                    const int i = it.i0 + ii;
+                    const uint8_t *a = it.Aw + (((int64_t)i * it.nkb + it.kb0) * it.A_rows + it.mt * BM) * kTileBytes;
+                    const int j0 = it.s0 - i;  // B word of column block 0
+                    const uint8_t *b0 =
+                        it.Bw + ((int64_t)j0 * it.nkb + it.kb0) * b_step + it.nt * it.nb * kTileBytes;
+                    for (int64_t kb = 0; kb < it.nkbc; ++kb, ++g, a += a_step, b0 += b_step) {
+                        const int slot = (int)(g % STAGES);
+                        if (!mbar_wait(&empty[slot], (uint32_t)(((g / STAGES) & 1) ^ 1), P.err)) {
+                            alive = false;
+                            break;
+                        }
+                        mbar_arrive_expect_tx(&full[slot], stage_bytes);
+                        bulk_g2s(sA + slot * kTileA, a, kTileA, &full[slot]);
+                        uint8_t *dst = sB + slot * kTileB;
+                        if (it.ndiag == 1) {
+                            bulk_g2s(dst, b0, slice, &full[slot]);
+                        } else {  // the window's B slices side by side; zeros where j is out of range
+                            for (int d = 0; d < it.ndiag; ++d, dst += slice) {
+                                const int j = j0 + d;
+                                bulk_g2s(dst, (j >= 0 && j < it.v) ? b0 + d * b_word : g_zero_slice, slice, &full[slot]);
+                            }
+                        }
                     }
-                    const int i = it.i0 + (int)(t / it.nkbc);
-                    const int j = it.s - i;
-                    const int64_t kb = it.kb0 + t % it.nkbc;
-                    const uint8_t *a = it.Aw + (((int64_t)i * it.nkb + kb) * it.A_rows + it.mt * BM) * kTileBytes;
-                    const uint8_t *b = it.Bw + (((int64_t)j * it.nkb + kb) * it.B_rows + it.nt * BN) * kTileBytes;
-                    mbar_arrive_expect_tx(&full[slot], kTileA + kTileB);
-                    bulk_g2s(sA + slot * kTileA, a, kTileA, &full[slot]);
-                    bulk_g2s(sB + slot * kTileB, b, kTileB, &full[slot]);
                 }
             }
             // Let every copy this lane started land before the CTA can exit.
@@ -274,7 +305,8 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_consta
             const ItemRange<kTable> R(P);
             for (int64_t idx = R.begin; alive && idx < R.end; idx += R.step) {
                 const Item it = get_item<kTable>(P, idx);
-                const int64_t nvb = (int64_t)it.w * it.nkbc;
+                const int64_t nvb = (int64_t)it.ni * it.nkbc;
+                const uint32_t idesc = idesc_n(it.ndiag * it.nb);
                 for (int64_t t0 = 0; alive && t0 < nvb; t0 += P.chunk_blocks, ++c) {
                     const int buf = (int)(c & 1);
                     if (!mbar_wait(&tempty[buf], (uint32_t)(((c >> 1) & 1) ^ 1), P.err)) {
@@ -294,7 +326,7 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_consta
                         const uint64_t ad = sdesc(a0 + slot * kTileA), bd = sdesc(b0 + slot * kTileB);
 #pragma unroll
                         for (int kk = 0; kk < 4; ++kk)  // K = 16 per MMA: +32 bytes = +2 in the address field
-                            mma_bf16(dt, ad + 2 * kk, bd + 2 * kk, (t > t0 || kk > 0) ? 1u : 0u);
+                            mma_bf16(dt, ad + 2 * kk, bd + 2 * kk, idesc, (t > t0 || kk > 0) ? 1u : 0u);
                         mma_commit(&empty[slot]);
                     }
                     mma_commit(&tfull[buf]);
@@ -313,7 +345,7 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_consta
         const ItemRange<kTable> R(P);
         for (int64_t idx = R.begin; alive && idx < R.end; idx += R.step) {
             const Item it = get_item<kTable>(P, idx);
-            const int64_t nvb = (int64_t)it.w * it.nkbc;
+            const int64_t nvb = (int64_t)it.ni * it.nkbc;
             const int64_t nch = (nvb + P.chunk_blocks - 1) / P.chunk_blocks;
             int32_t acc[128];
 #pragma unroll
@@ -340,11 +372,16 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_consta
             if (!alive) break;
             // streaming stores: the sums are read once, by the recombination, so
             // they should not displace word tiles from L2
-            int32_t *dst = it.S + (int64_t)(quarter * 32 + lane) * it.B_rows + half * 128;
+            // column c of the accumulator is column c mod nb of diagonal s0 + c / nb
+            int32_t *row = it.S + (int64_t)(quarter * 32 + lane) * it.B_rows;
 #pragma unroll
-            for (int q4 = 0; q4 < 32; ++q4)
-                __stcs(reinterpret_cast<int4 *>(dst) + q4,
-                       make_int4(acc[4 * q4], acc[4 * q4 + 1], acc[4 * q4 + 2], acc[4 * q4 + 3]));
+            for (int q4 = 0; q4 < 32; ++q4) {
+                const int c = half * 128 + 4 * q4;
+                const int d = c / it.nb;
+                if (d < it.ndiag)
+                    __stcs(reinterpret_cast<int4 *>(row + d * it.plane + (c - d * it.nb)),
+                           make_int4(acc[4 * q4], acc[4 * q4 + 1], acc[4 * q4 + 2], acc[4 * q4 + 3]));
+            }
         }
     }
 
@@ -420,16 +457,18 @@ __device__ __forceinline__ Item pair_item(const TcParams &P, int64_t idx) {
     const int64_t tile = idx % ntiles;
     const int64_t rest = idx / ntiles;
     const int kc = (int)(rest % P.nkc);
-    it.s = P.diag_order[rest / P.nkc];
+    const int grp_w = (int)(rest / P.nkc);  // nb = 256: one diagonal per window
+    it.s0 = P.g_s0[grp_w];
+    it.ndiag = 1;
+    it.nb = BN;
+    it.i0 = P.g_i0[grp_w];
+    it.ni = P.g_ni[grp_w];
+    it.v = P.v;
     const int64_t gsz = mt2 * kGroupN;
     const int64_t grp = tile / gsz, t = tile % gsz;
     const int64_t width = P.nt_count - grp * kGroupN < kGroupN ? P.nt_count - grp * kGroupN : kGroupN;
     it.mt = t / width;  // 256-row tile index
     it.nt = grp * kGroupN + t % width;
-    const int ilo = it.s - (P.v - 1) > 0 ? it.s - (P.v - 1) : 0;
-    const int ihi = it.s < P.u - 1 ? it.s : P.u - 1;
-    it.i0 = ilo;
-    it.w = ihi - ilo + 1;
     it.kb0 = (int64_t)kc * P.kcb;
     const int64_t left = P.nkb - it.kb0;
     it.nkbc = left < P.kcb ? left : P.kcb;
@@ -438,7 +477,8 @@ __device__ __forceinline__ Item pair_item(const TcParams &P, int64_t idx) {
     it.A_rows = P.A_rows;
     it.B_rows = P.B_rows;
     it.nkb = P.nkb;
-    it.S = P.S + (((int64_t)it.s * P.nkc + kc) * P.A_rows + it.mt * BM2) * P.B_rows + it.nt * BN;
+    it.plane = (int64_t)P.nkc * P.A_rows * P.B_rows;
+    it.S = P.S + (((int64_t)it.s0 * P.nkc + kc) * P.A_rows + it.mt * BM2) * P.B_rows + it.nt * BN;
     return it;
 }
 
@@ -488,23 +528,24 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS, 1)
             bool alive = true;
             for (int64_t idx = cid; alive && idx < P.nitems; idx += ncl) {
                 const Item it = pair_item(P, idx);
-                const int64_t nvb = (int64_t)it.w * it.nkbc;
-                for (int64_t t = 0; t < nvb; ++t, ++g) {
-                    const int slot = (int)(g % P_STAGES);
-                    if (!mbar_wait(&empty[slot], (uint32_t)(((g / P_STAGES) & 1) ^ 1), P.err)) {
-                        alive = false;
-                        break;
+                const int64_t a_step = it.A_rows * kTileBytes, b_step = it.B_rows * kTileBytes;
+                for (int ii = 0; alive && ii < it.ni; ++ii) {
+                    const int i = it.i0 + ii;
+                    const int j = it.s0 - i;
+                    const uint8_t *a = it.Aw + (((int64_t)i * it.nkb + it.kb0) * it.A_rows + it.mt * BM2 + rank * 128) *
+                                                   kTileBytes;
+                    const uint8_t *b = it.Bw + (((int64_t)j * it.nkb + it.kb0) * it.B_rows + it.nt * BN + rank * 128) *
+                                                   kTileBytes;
+                    for (int64_t kb = 0; kb < it.nkbc; ++kb, ++g, a += a_step, b += b_step) {
+                        const int slot = (int)(g % P_STAGES);
+                        if (!mbar_wait(&empty[slot], (uint32_t)(((g / P_STAGES) & 1) ^ 1), P.err)) {
+                            alive = false;
+                            break;
+                        }
+                        mbar_arrive_expect_tx(&full[slot], kTileA2 + kTileB2);
+                        bulk_g2s(sA + slot * kTileA2, a, kTileA2, &full[slot]);
+                        bulk_g2s(sB + slot * kTileB2, b, kTileB2, &full[slot]);
                     }
-                    const int i = it.i0 + (int)(t / it.nkbc);
-                    const int j = it.s - i;
-                    const int64_t kb = it.kb0 + t % it.nkbc;
-                    const uint8_t *a = it.Aw + (((int64_t)i * it.nkb + kb) * it.A_rows + it.mt * BM2 + rank * 128) *
-                                                   kTileBytes;
-                    const uint8_t *b = it.Bw + (((int64_t)j * it.nkb + kb) * it.B_rows + it.nt * BN + rank * 128) *
-                                                   kTileBytes;
-                    mbar_arrive_expect_tx(&full[slot], kTileA2 + kTileB2);
-                    bulk_g2s(sA + slot * kTileA2, a, kTileA2, &full[slot]);
-                    bulk_g2s(sB + slot * kTileB2, b, kTileB2, &full[slot]);
                 }
             }
             for (int s = 0; s < P_STAGES; ++s) {  // let every copy land before exit
@@ -519,7 +560,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS, 1)
             const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
             for (int64_t idx = cid; alive && idx < P.nitems; idx += ncl) {
                 const Item it = pair_item(P, idx);
-                const int64_t nvb = (int64_t)it.w * it.nkbc;
+                const int64_t nvb = (int64_t)it.ni * it.nkbc;
                 for (int64_t t0 = 0; alive && t0 < nvb; t0 += P.chunk_blocks, ++c) {
                     const int buf = (int)(c & 1);
                     if (!mbar_wait(&tempty[buf], (uint32_t)(((c >> 1) & 1) ^ 1), P.err)) {
@@ -554,7 +595,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS, 1)
             bool alive = true;
             for (int64_t idx = cid; alive && idx < P.nitems; idx += ncl) {
                 const Item it = pair_item(P, idx);
-                const int64_t nvb = (int64_t)it.w * it.nkbc;
+                const int64_t nvb = (int64_t)it.ni * it.nkbc;
                 for (int64_t t = 0; t < nvb; ++t, ++g) {
                     const int slot = (int)(g % P_STAGES);
                     if (!mbar_wait(&full[slot], (uint32_t)((g / P_STAGES) & 1), P.err)) {
@@ -574,7 +615,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS, 1)
         bool alive = true;
         for (int64_t idx = cid; alive && idx < P.nitems; idx += ncl) {
             const Item it = pair_item(P, idx);
-            const int64_t nvb = (int64_t)it.w * it.nkbc;
+            const int64_t nvb = (int64_t)it.ni * it.nkbc;
             const int64_t nch = (nvb + P.chunk_blocks - 1) / P.chunk_blocks;
             int32_t acc[128];
 #pragma unroll
@@ -673,29 +714,41 @@ int launch_gemm_tc(const Plan &pl, const void *Aw, const void *Bw, int32_t *S, i
     P.nkc = pl.nkc;
     P.chunk_blocks = (int)(pl.tc_chunk / kTcKB);
     P.mt_count = (int)(pl.A_rows / BM);
-    P.nt_count = (int)(pl.B_rows / BN);
-    P.nitems = (int64_t)P.mt_count * P.nt_count * pl.nsums * pl.nkc;
+    P.nt_count = pl.tc_nb == BN ? (int)(pl.B_rows / BN) : 1;
+    const int nwin = (pl.nsums + pl.tc_ndiag - 1) / pl.tc_ndiag;
+    P.nitems = (int64_t)P.mt_count * P.nt_count * nwin * pl.nkc;
     P.err = err;
     P.items = nullptr;
     P.cta_off = nullptr;
-    // diagonals by decreasing number of word pairs (heaviest items first)
-    int order[2 * kMaxWords];
-    int w[2 * kMaxWords];
-    for (int s = 0; s < pl.nsums; ++s) {
-        const int lo = s - (pl.v - 1) > 0 ? s - (pl.v - 1) : 0, hi = s < pl.u - 1 ? s : pl.u - 1;
-        w[s] = hi - lo + 1;
-        order[s] = s;
+    // diagonal windows of tc_ndiag diagonals, by decreasing number of A words
+    // (heaviest items first)
+    P.nb = pl.tc_nb;
+    int ng = 0;
+    int gs0[2 * kMaxWords], gnd[2 * kMaxWords], gi0[2 * kMaxWords], gni[2 * kMaxWords], order[2 * kMaxWords];
+    for (int s0 = 0; s0 < pl.nsums; s0 += pl.tc_ndiag, ++ng) {
+        gs0[ng] = s0;
+        gnd[ng] = pl.nsums - s0 < pl.tc_ndiag ? pl.nsums - s0 : pl.tc_ndiag;
+        const int lo = s0 - (pl.v - 1) > 0 ? s0 - (pl.v - 1) : 0;
+        const int hi = s0 + gnd[ng] - 1 < pl.u - 1 ? s0 + gnd[ng] - 1 : pl.u - 1;
+        gi0[ng] = lo;
+        gni[ng] = hi - lo + 1;
+        order[ng] = ng;
     }
-    for (int a = 1; a < pl.nsums; ++a)
-        for (int b = a; b > 0 && w[order[b]] > w[order[b - 1]]; --b) {
+    for (int a = 1; a < ng; ++a)
+        for (int b = a; b > 0 && gni[order[b]] > gni[order[b - 1]]; --b) {
             int t = order[b];
             order[b] = order[b - 1];
             order[b - 1] = t;
         }
-    for (int s = 0; s < 2 * kMaxWords; ++s) P.diag_order[s] = s < pl.nsums ? order[s] : 0;
+    for (int g = 0; g < 2 * kMaxWords; ++g) {
+        P.g_s0[g] = g < ng ? gs0[order[g]] : 0;
+        P.g_nd[g] = g < ng ? gnd[order[g]] : 0;
+        P.g_i0[g] = g < ng ? gi0[order[g]] : 0;
+        P.g_ni[g] = g < ng ? gni[order[g]] : 0;
+    }
     if (P.nitems == 0) return 0;
     if (pl.tc_pair) {
-        P.nitems = (int64_t)(P.mt_count / 2) * P.nt_count * pl.nsums * pl.nkc;
+        P.nitems = (int64_t)(P.mt_count / 2) * P.nt_count * nwin * pl.nkc;
         cudaError_t e = set_smem_attr(reinterpret_cast<const void *>(gemm_tc_pair_kernel), kSmemPair);
         if (e != cudaSuccess) return (int)e;
         const int clusters = pair_clusters();

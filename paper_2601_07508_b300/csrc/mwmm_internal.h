@@ -22,14 +22,20 @@ constexpr int kTcBN = 256;              // MMA N
 constexpr int kTcMaxChunk = 1024;       // 2^24 / 2^14 digit products per FP32 chunk
 constexpr int64_t kInt32SumLimit = 131071; // floor((2^31 - 1) / 2^14): products per INT32 sum
 
-// One work item of the tcgen05 kernel in table mode (batched products): the
-// u-by-v word products of diagonal s over k-blocks [kb0, kb0 + nkbc) for the
-// 128 x 256 output tile (mt, nt) of one problem.
+// One work item of the tcgen05 kernel: the word products of the diagonals
+// s0 .. s0 + ndiag - 1 over k-blocks [kb0, kb0 + nkbc) for the 128-row tile mt
+// and column tile nt of one problem.  Column block d (nb columns) of the
+// 128 x (ndiag nb) accumulator holds diagonal s0 + d; A word i contributes to
+// it through B word j = s0 + d - i when 0 <= j < v (the B words of a window
+// are concatenated along N, Alg. 6's concatenation).  nb = 256 (ndiag = 1)
+// when n > 128; otherwise nb is n padded to 16, 32, 64 or 128 and one item
+// covers 256 / nb diagonals.
 struct TcItem {
     const uint8_t *Aw, *Bw;  // word bases of the problem's A and B
-    int32_t *S;              // origin of the tile's diagonal sum (row stride B_rows)
+    int32_t *S;              // S of diagonal s0, K-range kc, at the tile's origin (row stride B_rows)
     int64_t A_rows, B_rows, nkb, kb0, nkbc, mt, nt;
-    int32_t s, i0, w, pad;
+    int64_t plane;           // int32 elements between the S planes of consecutive diagonals
+    int32_t s0, ndiag, nb, i0, ni, v, pad0, pad1;
 };
 
 struct Plan {
@@ -48,6 +54,8 @@ struct Plan {
     // INT8 form
     int64_t tc_chunk = 0, kc = 0;
     int tc_pair = 0;  // 1: 2-CTA kernel, A rows padded to 256
+    int tc_nb = 256;  // B rows per word slice of a tile (256, or n padded to 16/32/64/128)
+    int tc_ndiag = 1; // diagonals per work item (256 / tc_nb, at most nsums)
     int nkc = 0, nsums = 0;
     // layout
     int64_t kb_elems = 0, nkb = 0, A_rows = 0, B_rows = 0;

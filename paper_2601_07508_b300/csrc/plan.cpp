@@ -166,10 +166,18 @@ mwmm_status make_plan(Plan *pl, int64_t m, int64_t n, int64_t k, uint64_t p, int
         P.nkc = k > 0 ? (int)ceil_div(k, kc) : 0;
         P.kb_elems = kTcKB;
         P.nkb = ceil_div(k, kTcKB);
-        // the 2-CTA kernel (opt-in) computes 256-row tiles
-        P.tc_pair = (m > kTcBM && o.tc_pair) ? 1 : 0;
+        // Column tiles: 256 wide when n > 128; narrower n is padded to 16, 32,
+        // 64 or 128 and one tile then carries 256 / nb diagonals side by side.
+        P.tc_nb = kTcBN;
+        if (n <= kTcBN / 2) {
+            P.tc_nb = 16;
+            while (P.tc_nb < n) P.tc_nb *= 2;
+        }
+        P.tc_ndiag = kTcBN / P.tc_nb < P.nsums ? kTcBN / P.tc_nb : P.nsums;
+        // the 2-CTA kernel (opt-in) computes 256 x 256 tiles
+        P.tc_pair = (m > kTcBM && P.tc_nb == kTcBN && o.tc_pair) ? 1 : 0;
         P.A_rows = round_up(m > 0 ? m : 1, P.tc_pair ? 2 * kTcBM : kTcBM);
-        P.B_rows = round_up(n > 0 ? n : 1, kTcBN);
+        P.B_rows = P.tc_nb == kTcBN ? round_up(n > 0 ? n : 1, kTcBN) : P.tc_nb;
         uint64_t abytes = (uint64_t)u * P.nkb * P.A_rows * kTileBytes;
         uint64_t bbytes = (uint64_t)v * P.nkb * P.B_rows * kTileBytes;
         uint64_t sbytes = (uint64_t)P.nsums * P.nkc * P.A_rows * P.B_rows * 4;

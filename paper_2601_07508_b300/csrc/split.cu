@@ -104,6 +104,7 @@ __device__ __forceinline__ void split_fp64_tile(const SplitParams &P, uint64_t (
         const int g = gg % 8;
         uint64_t T0 = tile[rr][2 * gg], T1 = tile[rr][2 * gg + 1];
         const int64_t r = r0 + rr;
+        if (r >= P.rows_pad) continue;  // a last row tile may be partial (rows_pad < 64)
         for (int w = 0; w < P.words; ++w) {
             const bool last = (w == P.words - 1);
             const double w0 = alg4_next(T0, P.alpha, P.mu, last);
@@ -131,6 +132,7 @@ __device__ __forceinline__ void split_int8_tile(const SplitParams &P, uint64_t (
             s[e] = (x <= half) ? (int64_t)x : (int64_t)x - (int64_t)P.p;
         }
         const int64_t r = r0 + rr;
+        if (r >= P.rows_pad) continue;  // a last row tile may be partial (rows_pad 16 or 32)
         for (int w = 0; w < P.words; ++w) {
             const bool last = (w == P.words - 1);
             __align__(16) __nv_bfloat16 h[8];
@@ -197,7 +199,7 @@ void split_job(const Plan &pl, int side, const uint64_t *M, int64_t ld, void *wo
     std::memcpy(job, &P, sizeof(P));
     if (pl.nkb == 0 || P.rows_pad == 0) return;
     const int64_t kcols = pl.nkb * pl.kb_elems;
-    const int64_t gx = (kcols + kST - 1) / kST, gy = P.rows_pad / kST;
+    const int64_t gx = (kcols + kST - 1) / kST, gy = (P.rows_pad + kST - 1) / kST;
     for (int64_t y = 0; y < gy; ++y)
         for (int64_t x = 0; x < gx; ++x) {
             blocks.push_back(job_index);
@@ -218,7 +220,7 @@ int launch_split(const Plan &pl, int side, const uint64_t *M, int64_t ld, void *
     const SplitParams P = make_split_params(pl, side, M, ld, words);
     if (pl.nkb == 0 || P.rows_pad == 0) return 0;
     const int64_t kcols = pl.nkb * pl.kb_elems;
-    dim3 grid((unsigned)((kcols + kST - 1) / kST), (unsigned)(P.rows_pad / kST));
+    dim3 grid((unsigned)((kcols + kST - 1) / kST), (unsigned)((P.rows_pad + kST - 1) / kST));
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (pl.form == MWMM_FORM_FP64) {
         // Words equal to the input when u == 1 (alpha = p): Alg. 4 has no loop.

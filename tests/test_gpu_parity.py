@@ -264,5 +264,42 @@ def test_int8_pair_and_single_cta_kernels(M, oracle, shape, b):
     ref = oracle.matmul_mod(A, B, p)
     for pair in (False, True):
         C, plan = gpu_product(M, A, B, p, form="int8", tc_pair=pair)
-        assert plan.info["tc_pair"] == (1 if pair else 0)
+        assert plan.info["tc_pair"] == (1 if pair and n > 128 else 0)  # pairs need 256-wide column tiles
         assert np.array_equal(C, ref), pair
+
+
+@pytest.mark.parametrize("n", [1, 15, 16, 17, 32, 40, 64, 65, 100, 128])
+@pytest.mark.parametrize("b", [23, 40, 52])
+def test_int8_narrow_n_diagonal_windows(M, oracle, n, b):
+    """n <= 128: one work item carries 256 / nb diagonals, the B words of a
+    window concatenated along N (Alg. 6), zero slices where j is out of range."""
+    p = SWEEP[b]
+    m, k = 300, 777
+    A, B = inputs.problem(70 + n, m, n, k, p)
+    C, plan = gpu_product(M, A, B, p, form="int8")
+    nb = plan.info["B_rows"]
+    assert nb >= n and nb in (16, 32, 64, 128)
+    assert np.array_equal(C, oracle.matmul_mod(A, B, p))
+    C2, _ = gpu_product(M, A, B, p, form="int8", tc_chunk=128, kc=256)  # chunks and K-ranges inside windows
+    assert np.array_equal(C2, C)
+
+
+def test_int8_windowed_diagonal_sums_match_oracle(M, oracle):
+    p = SWEEP[52]
+    m, n, k = 130, 40, 500
+    A, B = inputs.problem(43, m, n, k, p)
+    plan = M.Plan(m, n, k, p, form="int8", kc=192)
+    ws = plan.alloc_workspace()
+    plan.matmul(dev(A), dev(B))
+    assert plan.check() == 0
+    d = plan.info
+    assert d["B_rows"] == 64
+    S = ws[d["S_off"]:d["S_off"] + d["nsums"] * d["nkc"] * d["A_rows"] * d["B_rows"] * 4]
+    S = S.cpu().numpy().view(np.int32).reshape(d["nsums"], d["nkc"], d["A_rows"], d["B_rows"])
+    u = d["u"]
+    Aw = oracle.split_signed8(A, p, u)
+    Bw = oracle.split_signed8(B, p, u)
+    for kc in range(d["nkc"]):
+        sl = slice(kc * d["kc"], min(k, (kc + 1) * d["kc"]))
+        ref = oracle.diag_sums(np.ascontiguousarray(Aw[:, :, sl]), np.ascontiguousarray(Bw[:, sl, :]))
+        assert np.array_equal(S[:, kc, :m, :n].astype(np.int64), ref)
