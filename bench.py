@@ -53,6 +53,7 @@ def parse_args():
     ap.add_argument("--no-batched", action="store_true", help="skip the 512-instance multi-prime batch")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving run")
     ap.add_argument("--no-shapes", action="store_true", help="skip the 50-bit shape study")
+    ap.add_argument("--no-unbalanced", action="store_true", help="skip the block-Wiedemann shape")
     ap.add_argument("--serve-requests", type=int, default=20000)
     ap.add_argument("--serve-pool", type=int, default=256, help="distinct operand sets the requests cycle through")
     return ap.parse_args()
@@ -321,6 +322,51 @@ def run_shapes(dev):
     return out
 
 
+def run_unbalanced(dev, reps=5):
+    """The paper's unbalanced scenario (Sec. 4.1): m = 10923, k = 32768, n = 32,
+    A decomposed once and reused (its split is excluded, as in the paper);
+    each timed product splits B, multiplies and recombines."""
+    import torch
+    from paper_2601_07508_b300 import mwmm
+    m, k, n = 10923, 32768, 32
+    p52 = inputs.largest_prime_below_pow2(52)
+    A52, _ = inputs.problem(7, m, 1, k, p52)
+    dA52 = torch.from_numpy(A52.view(np.int64)).to(dev)
+    del A52
+    out = {"workload": "m = 10923, k = 32768, n = 32 (block-Wiedemann shape); A split once and reused, time "
+                       "= split of B + word products + recombination; A = (52-bit uniform matrix) mod p"}
+    for b, fp64 in ((20, None), (32, (1, 2)), (40, (2, 2)), (48, None), (52, (2, 3))):
+        p = inputs.largest_prime_below_pow2(b)
+        dA = torch.remainder(dA52, p) if b < 52 else dA52
+        B = inputs.matrix(b, inputs.STREAM_B, k, n, p)
+        dB = torch.from_numpy(B.view(np.int64)).to(dev)
+        res = {}
+        forms = [("int8", (0, 0))] + ([("fp64", fp64)] if fp64 else [])
+        ref = None
+        for form, uv in forms:
+            pl = mwmm.Plan(m, n, k, p, uv[0], uv[1], form=form)
+            C = pl.matmul(dA, dB)  # splits A
+            torch.cuda.synchronize()
+            mwmm.mwmm_plan_set_timing(pl.handle, True)
+            r = reps if form == "int8" else 1
+            for _ in range(r):
+                pl.matmul_reuse_a(dB, C)
+            t = mwmm.mwmm_plan_timing(pl.handle)
+            assert pl.check() == 0
+            ms = t["total_ms"] / t["calls"]
+            key = form if form == "int8" else "fp64_%d%d" % uv
+            res[key] = {"ms": ms, "gops": 2.0 * m * n * k / ms / 1e6, "uv": [pl.info["u"], pl.info["v"]]}
+            if ref is None:
+                ref = C
+            else:
+                res[key]["equals_int8"] = bool(torch.equal(C, ref))
+            del pl
+            torch.cuda.empty_cache()
+        out[str(b)] = res
+        del dA
+    return out
+
+
 def run_serve(dev, nreq, pool, budget=40 << 30):
     """Poisson stream of requests (m, n, k log-uniform in [64, 4096], bitsize
     uniform in [20, 52], seed 5) against a 40 GB budget; the rate is 0.8 x the
@@ -561,6 +607,7 @@ def main():
 
     batched = run_batched(dev) if (rank == 0 and not args.no_batched) else None
     shapes = run_shapes(dev) if (rank == 0 and not args.no_shapes) else None
+    unbalanced = run_unbalanced(dev) if (rank == 0 and not args.no_unbalanced) else None
     serve = run_serve(dev, args.serve_requests, args.serve_pool) if (rank == 0 and not args.no_serve) else None
 
     if rank == 0:
@@ -573,7 +620,8 @@ def main():
                 "config": workload_config(args, bits),
                 "roofline": roofline, "cpu_baseline": cpu_baseline, "e2e": e2e,
                 "gpu_launches": launches * world, "clocks": clocks, "per_bitsize": per_bits,
-                "batched_multi_prime": batched, "shapes_50bit": shapes, "serve": serve}
+                "batched_multi_prime": batched, "shapes_50bit": shapes, "unbalanced_block_wiedemann": unbalanced,
+                "serve": serve}
         print(json.dumps(line))
     if dist:
         dist.destroy_process_group()

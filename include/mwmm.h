@@ -116,12 +116,18 @@ typedef struct {
      * K-contiguous) are stored as 128-byte row chunks:
      *   chunk(word w, k-block kb, row r) at X_off + ((w * nkb + kb) * X_rows + r) * 128
      * where nkb = ceil(k / kb_elems) and X_rows = A_rows or B_rows (padded).
+     * INT8 form with n <= 128 only, for B: k-block major with B_wpad zero
+     * words on each side,
+     *   chunk(word w, k-block kb, row r) at
+     *     B_off + ((kb * (v + 2 B_wpad) + w + B_wpad) * B_rows + r) * 128
+     * (words -B_wpad .. -1 and v .. v + B_wpad - 1 are all zero).
      * Inside a chunk the 16-byte granule g (elements g*E .. g*E+E-1 of the
      * k-block, E = 16 / element size) is stored at granule position
      * g ^ (r mod 8).  Element type: double (FP64 form, kb_elems = 16) or
      * bf16 holding an integer digit (INT8 form, kb_elems = 64).  Padding is 0.
      * INT8 form only: S (int32) at S_off, laid out [nsums][nkc][A_rows][B_rows]. */
     int64_t kb_elems, nkb, A_rows, B_rows;
+    int32_t B_wpad, pad0;
     uint64_t A_off, B_off, S_off;
     uint64_t workspace_bytes;
 } mwmm_plan_desc;
@@ -151,6 +157,16 @@ size_t mwmm_workspace_size(mwmm_plan_t plan);
 mwmm_status mwmm_matmul(mwmm_plan_t plan, const uint64_t *dA, int64_t lda,
                         const uint64_t *dB, int64_t ldb, uint64_t *dC, int64_t ldc,
                         void *workspace, size_t workspace_bytes, void *stream);
+
+/* C = A B mod p reusing the words of A left in `workspace` by the most recent
+ * mwmm_matmul (or mwmm_split of side 0 into workspace + A_off) with this
+ * plan: only B is split.  For sequences of products with one fixed A, as in
+ * the block-Wiedemann iterations of Sec. 4.1 where A's decomposition is
+ * computed once.  A itself is not read; the caller keeps the workspace
+ * (NULL: the plan's own) unchanged between the calls.
+ * Errors: as mwmm_matmul. */
+mwmm_status mwmm_matmul_reuse_a(mwmm_plan_t plan, const uint64_t *dB, int64_t ldb, uint64_t *dC, int64_t ldc,
+                                void *workspace, size_t workspace_bytes, void *stream);
 
 /* Same product with HOST matrices: copies A and B to plan-owned device
  * buffers, computes, copies C back and synchronises `stream`.  For the

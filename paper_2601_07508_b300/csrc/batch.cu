@@ -119,6 +119,9 @@ static void tc_items(const Plan &pl, const uint8_t *Aw, const uint8_t *Bw, int32
                     it.i0 = ilo;
                     it.ni = ihi - ilo + 1;
                     it.v = pl.v;
+                    it.b_wpad = pl.B_wpad;
+                    it.b_wstride = pl.B_wstride * mwmm::kTileBytes;
+                    it.b_kstride = pl.B_kstride * mwmm::kTileBytes;
                     items.push_back(it);
                 }
     }

@@ -86,7 +86,8 @@ inline void rec(cudaEvent_t e, cudaStream_t s) {
     if (e) cudaEventRecord(e, s);
 }
 
-// Run the product on device pointers with a given workspace.
+// Run the product on device pointers with a given workspace (dA == NULL:
+// the A words already in the workspace are used).
 mwmm_status run_product(mwmm_plan_s *h, const uint64_t *dA, int64_t lda, const uint64_t *dB, int64_t ldb,
                         uint64_t *dC, int64_t ldc, uint8_t *ws, void *stream) {
     Plan &pl = h->pl;
@@ -98,7 +99,7 @@ mwmm_status run_product(mwmm_plan_s *h, const uint64_t *dA, int64_t lda, const u
     mwmm_status st = take_events(h, pe);
     if (st != MWMM_OK) return st;
     rec(pe.ev[0], s);
-    int e = mwmm::launch_split(pl, 0, dA, lda, ws + pl.A_off, stream);
+    int e = dA ? mwmm::launch_split(pl, 0, dA, lda, ws + pl.A_off, stream) : 0;
     if (e) return cuda_status(e);
     rec(pe.ev[1], s);
     e = mwmm::launch_split(pl, 1, dB, ldb, ws + pl.B_off, stream);
@@ -108,7 +109,7 @@ mwmm_status run_product(mwmm_plan_s *h, const uint64_t *dA, int64_t lda, const u
         e = mwmm::launch_gemm_fp64(pl, ws + pl.A_off, ws + pl.B_off, dC, ldc, pl.err_dev, stream);
         rec(pe.ev[3], s);
         rec(pe.ev[4], s);
-        if (h->timing) h->pending_launches += 3;
+        if (h->timing) h->pending_launches += dA ? 3 : 2;
         return cuda_status(e);
     }
     int32_t *S = reinterpret_cast<int32_t *>(ws + pl.S_off);
@@ -117,7 +118,7 @@ mwmm_status run_product(mwmm_plan_s *h, const uint64_t *dA, int64_t lda, const u
     rec(pe.ev[3], s);
     e = mwmm::launch_recombine(pl, S, dC, ldc, stream);
     rec(pe.ev[4], s);
-    if (h->timing) h->pending_launches += 4;
+    if (h->timing) h->pending_launches += dA ? 4 : 3;
     return cuda_status(e);
 }
 
@@ -170,6 +171,7 @@ mwmm_status mwmm_plan_info(mwmm_plan_t plan, mwmm_plan_desc *d) {
     d->tc_chunk = P.tc_chunk; d->kc = P.kc; d->nkc = P.nkc; d->nsums = P.nsums; d->tc_pair = P.tc_pair;
     d->q = P.q;
     d->kb_elems = P.kb_elems; d->nkb = P.nkb; d->A_rows = P.A_rows; d->B_rows = P.B_rows;
+    d->B_wpad = P.B_wpad;
     d->A_off = P.A_off; d->B_off = P.B_off; d->S_off = P.S_off;
     d->workspace_bytes = P.ws_bytes;
     return MWMM_OK;
@@ -193,6 +195,23 @@ mwmm_status mwmm_matmul(mwmm_plan_t plan, const uint64_t *dA, int64_t lda, const
         workspace = pl.own_ws;
     }
     return run_product(plan, dA, lda, dB, ldb, dC, ldc, static_cast<uint8_t *>(workspace), stream);
+}
+
+mwmm_status mwmm_matmul_reuse_a(mwmm_plan_t plan, const uint64_t *dB, int64_t ldb, uint64_t *dC, int64_t ldc,
+                                void *workspace, size_t workspace_bytes, void *stream) {
+    if (!plan) return MWMM_ERR_ARG;
+    Plan &pl = plan->pl;
+    if (pl.m == 0 || pl.n == 0) return MWMM_OK;
+    if (!dC || (pl.k > 0 && !dB) || !valid_ld(pl, pl.k > 0 ? pl.k : 1, ldb, ldc)) return MWMM_ERR_ARG;
+    if (workspace && (workspace_bytes < pl.ws_bytes || (reinterpret_cast<uintptr_t>(workspace) & 255)))
+        return MWMM_ERR_ARG;
+    mwmm_status st = ensure_device(pl);
+    if (st != MWMM_OK) return st;
+    if (!workspace) {
+        if (!pl.own_ws && pl.ws_bytes) return MWMM_ERR_ARG;  // no words of A to reuse yet
+        workspace = pl.own_ws;
+    }
+    return run_product(plan, nullptr, 0, dB, ldb, dC, ldc, static_cast<uint8_t *>(workspace), stream);
 }
 
 mwmm_status mwmm_plan_check(mwmm_plan_t plan, void *stream) {

@@ -58,7 +58,8 @@ struct TcParams {
     const uint8_t *Aw, *Bw;
     int32_t *S;
     int64_t nkb, A_rows, B_rows, kcb, nitems;
-    int u, v, nsums, nkc, mt_count, nt_count, nb;
+    int u, v, nsums, nkc, mt_count, nt_count, nb, b_wpad;
+    int64_t b_wstride, b_kstride;  // bytes between consecutive B words / k-blocks
     // diagonal windows, heaviest first: window g covers diagonals
     // g_s0[g] .. g_s0[g] + g_nd[g] - 1 and A words g_i0[g] .. + g_ni[g] - 1
     int g_s0[2 * kMaxWords], g_nd[2 * kMaxWords], g_i0[2 * kMaxWords], g_ni[2 * kMaxWords];
@@ -73,13 +74,9 @@ struct TcParams {
 struct Item {
     const uint8_t *Aw, *Bw;
     int32_t *S;  // S of diagonal s0 at the item's tile origin, row stride B_rows
-    int64_t A_rows, B_rows, nkb, kb0, nkbc, mt, nt, plane;
-    int s0, ndiag, nb, i0, ni, v;
+    int64_t A_rows, B_rows, nkb, kb0, nkbc, mt, nt, plane, b_wstride, b_kstride;
+    int s0, ndiag, nb, i0, ni, v, b_wpad;
 };
-
-// A static zero tile stands in for the B slices of pairs (i, j) with j
-// outside [0, v) inside a diagonal window (device globals start zeroed).
-__device__ __align__(128) uint8_t g_zero_slice[BN * kTileBytes];
 
 __device__ __forceinline__ Item computed_item(const TcParams &P, int64_t idx) {
     Item it;
@@ -94,6 +91,9 @@ __device__ __forceinline__ Item computed_item(const TcParams &P, int64_t idx) {
     it.ni = P.g_ni[grp_w];
     it.nb = P.nb;
     it.v = P.v;
+    it.b_wstride = P.b_wstride;
+    it.b_kstride = P.b_kstride;
+    it.b_wpad = P.b_wpad;
     // Raster in groups of kGroupN column tiles, rows inside a group first: the
     // ~148 tiles running at once cover about 18 row tiles x 8 column tiles, a
     // squarer region than whole rows, so fewer word tiles are fetched twice.
@@ -135,6 +135,9 @@ __device__ __forceinline__ Item table_item(const TcParams &P, int64_t pos) {
     it.i0 = d.i0;
     it.ni = d.ni;
     it.v = d.v;
+    it.b_wstride = d.b_wstride;
+    it.b_kstride = d.b_kstride;
+    it.b_wpad = d.b_wpad;
     return it;
 }
 
@@ -261,17 +264,18 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_consta
                 const Item it = get_item<kTable>(P, idx);
                 // One thread issues every copy, so the per-stage work is kept to a
                 // few adds: nested (word, k-block) loops and running addresses.
-                const uint32_t slice = (uint32_t)it.nb * kTileBytes;
-                const uint32_t stage_bytes = kTileA + (uint32_t)it.ndiag * slice;
-                const int64_t a_step = it.A_rows * kTileBytes, b_step = it.B_rows * kTileBytes;
-                const int64_t b_word = it.nkb * b_step;  // bytes between consecutive B words
+                // The window's B words B_{s0-i} .. B_{s0-i+ndiag-1} are contiguous
+                // (k-block-major layout padded with zero words), so each stage is
+                // two copies whatever the window.
+                const uint32_t bbytes = (uint32_t)(it.ndiag * it.nb) * kTileBytes;
+                const uint32_t stage_bytes = kTileA + bbytes;
+                const int64_t a_step = it.A_rows * kTileBytes;
                 for (int ii = 0; alive && ii < it.ni; ++ii) {
                     const int i = it.i0 + ii;
                     const uint8_t *a = it.Aw + (((int64_t)i * it.nkb + it.kb0) * it.A_rows + it.mt * BM) * kTileBytes;
-                    const int j0 = it.s0 - i;  // B word of column block 0
-                    const uint8_t *b0 =
-                        it.Bw + ((int64_t)j0 * it.nkb + it.kb0) * b_step + it.nt * it.nb * kTileBytes;
-                    for (int64_t kb = 0; kb < it.nkbc; ++kb, ++g, a += a_step, b0 += b_step) {
+                    const uint8_t *b = it.Bw + (int64_t)(it.s0 - i + it.b_wpad) * it.b_wstride +
+                                       it.kb0 * it.b_kstride + it.nt * it.nb * kTileBytes;
+                    for (int64_t kb = 0; kb < it.nkbc; ++kb, ++g, a += a_step, b += it.b_kstride) {
                         const int slot = (int)(g % STAGES);
                         if (!mbar_wait(&empty[slot], (uint32_t)(((g / STAGES) & 1) ^ 1), P.err)) {
                             alive = false;
@@ -279,15 +283,7 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_consta
                         }
                         mbar_arrive_expect_tx(&full[slot], stage_bytes);
                         bulk_g2s(sA + slot * kTileA, a, kTileA, &full[slot]);
-                        uint8_t *dst = sB + slot * kTileB;
-                        if (it.ndiag == 1) {
-                            bulk_g2s(dst, b0, slice, &full[slot]);
-                        } else {  // the window's B slices side by side; zeros where j is out of range
-                            for (int d = 0; d < it.ndiag; ++d, dst += slice) {
-                                const int j = j0 + d;
-                                bulk_g2s(dst, (j >= 0 && j < it.v) ? b0 + d * b_word : g_zero_slice, slice, &full[slot]);
-                            }
-                        }
+                        bulk_g2s(sB + slot * kTileB, b, bbytes, &full[slot]);
                     }
                 }
             }
@@ -723,6 +719,9 @@ int launch_gemm_tc(const Plan &pl, const void *Aw, const void *Bw, int32_t *S, i
     // diagonal windows of tc_ndiag diagonals, by decreasing number of A words
     // (heaviest items first)
     P.nb = pl.tc_nb;
+    P.b_wpad = pl.B_wpad;
+    P.b_wstride = pl.B_wstride * kTileBytes;
+    P.b_kstride = pl.B_kstride * kTileBytes;
     int ng = 0;
     int gs0[2 * kMaxWords], gnd[2 * kMaxWords], gi0[2 * kMaxWords], gni[2 * kMaxWords], order[2 * kMaxWords];
     for (int s0 = 0; s0 < pl.nsums; s0 += pl.tc_ndiag, ++ng) {

@@ -35,7 +35,8 @@ struct TcItem {
     int32_t *S;              // S of diagonal s0, K-range kc, at the tile's origin (row stride B_rows)
     int64_t A_rows, B_rows, nkb, kb0, nkbc, mt, nt;
     int64_t plane;           // int32 elements between the S planes of consecutive diagonals
-    int32_t s0, ndiag, nb, i0, ni, v, pad0, pad1;
+    int64_t b_wstride, b_kstride;  // bytes between consecutive B words / k-blocks
+    int32_t s0, ndiag, nb, i0, ni, v, b_wpad, pad0;
 };
 
 struct Plan {
@@ -59,6 +60,13 @@ struct Plan {
     int nkc = 0, nsums = 0;
     // layout
     int64_t kb_elems = 0, nkb = 0, A_rows = 0, B_rows = 0;
+    // B word layout: chunk(word w, k-block kb, row r) at
+    // ((kb * B_kstride + (w + B_wpad) * B_wstride) + r) * 128; plain layout:
+    // B_wstride = nkb * B_rows, B_kstride = B_rows, B_wpad = 0.  Narrow n
+    // (diagonal windows): k-block major with B_wpad zero words on each side,
+    // B_wstride = B_rows, B_kstride = (v + 2 B_wpad) * B_rows.
+    int64_t B_wstride = 0, B_kstride = 0;
+    int B_wpad = 0;
     uint64_t A_off = 0, B_off = 0, S_off = 0, ws_bytes = 0;
     // owned device resources (lazily created)
     int device = -1;

@@ -135,6 +135,8 @@ mwmm_status make_plan(Plan *pl, int64_t m, int64_t n, int64_t k, uint64_t p, int
         P.B_rows = round_up(n > 0 ? n : 1, kF64BN);
         uint64_t abytes = (uint64_t)u * P.nkb * P.A_rows * kTileBytes;
         uint64_t bbytes = (uint64_t)v * P.nkb * P.B_rows * kTileBytes;
+        P.B_wstride = P.nkb * P.B_rows;
+        P.B_kstride = P.B_rows;
         P.A_off = 0;
         P.B_off = align256(abytes);
         P.S_off = align256(P.B_off + bbytes);
@@ -179,7 +181,17 @@ mwmm_status make_plan(Plan *pl, int64_t m, int64_t n, int64_t k, uint64_t p, int
         P.A_rows = round_up(m > 0 ? m : 1, P.tc_pair ? 2 * kTcBM : kTcBM);
         P.B_rows = P.tc_nb == kTcBN ? round_up(n > 0 ? n : 1, kTcBN) : P.tc_nb;
         uint64_t abytes = (uint64_t)u * P.nkb * P.A_rows * kTileBytes;
-        uint64_t bbytes = (uint64_t)v * P.nkb * P.B_rows * kTileBytes;
+        // Narrow n: B's words k-block major with zero words on both sides, so
+        // the words B_{s0-i} .. B_{s0-i+ndiag-1} of any window are contiguous.
+        P.B_wpad = P.tc_nb < kTcBN ? P.tc_ndiag - 1 : 0;
+        if (P.tc_nb < kTcBN) {
+            P.B_wstride = P.B_rows;
+            P.B_kstride = (int64_t)(v + 2 * P.B_wpad) * P.B_rows;
+        } else {
+            P.B_wstride = P.nkb * P.B_rows;
+            P.B_kstride = P.B_rows;
+        }
+        uint64_t bbytes = (uint64_t)(v + 2 * P.B_wpad) * P.nkb * P.B_rows * kTileBytes;
         uint64_t sbytes = (uint64_t)P.nsums * P.nkc * P.A_rows * P.B_rows * 4;
         P.A_off = 0;
         P.B_off = align256(abytes);

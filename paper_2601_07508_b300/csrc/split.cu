@@ -38,6 +38,8 @@ struct SplitParams {
     int64_t rows_pad, nkb;
     uint8_t *out;
     int words;
+    int64_t wstride, kstride;  // rows between consecutive words / k-blocks
+    int wpad;                  // zero words written before and after the words
     uint64_t p;
     uint64_t alpha, mu;  // FP64: radix and floor((2^64 - 1) / alpha)
     int validate;
@@ -109,7 +111,7 @@ __device__ __forceinline__ void split_fp64_tile(const SplitParams &P, uint64_t (
             const bool last = (w == P.words - 1);
             const double w0 = alg4_next(T0, P.alpha, P.mu, last);
             const double w1 = alg4_next(T1, P.alpha, P.mu, last);
-            uint8_t *dst = P.out + (((int64_t)w * P.nkb + kb) * P.rows_pad + r) * kTileBytes +
+            uint8_t *dst = P.out + ((int64_t)w * P.wstride + kb * P.kstride + r) * kTileBytes +
                            ((g ^ (int)(r & 7)) * 16);
             *reinterpret_cast<double2 *>(dst) = make_double2(w0, w1);
         }
@@ -138,9 +140,16 @@ __device__ __forceinline__ void split_int8_tile(const SplitParams &P, uint64_t (
             __align__(16) __nv_bfloat16 h[8];
 #pragma unroll
             for (int e = 0; e < 8; ++e) h[e] = __float2bfloat16_rn(int8_next(s[e], last));
-            uint8_t *dst = P.out + (((int64_t)w * P.nkb + kb) * P.rows_pad + r) * kTileBytes +
+            uint8_t *dst = P.out + ((int64_t)(w + P.wpad) * P.wstride + kb * P.kstride + r) * kTileBytes +
                            ((g ^ (int)(r & 7)) * 16);
             *reinterpret_cast<uint4 *>(dst) = *reinterpret_cast<const uint4 *>(h);
+        }
+        for (int z = 0; z < P.wpad; ++z) {  // the zero words on both sides
+            const int64_t base = kb * P.kstride + r;
+            const uint4 zero = make_uint4(0, 0, 0, 0);
+            *reinterpret_cast<uint4 *>(P.out + ((int64_t)z * P.wstride + base) * kTileBytes + ((g ^ (int)(r & 7)) * 16)) = zero;
+            *reinterpret_cast<uint4 *>(P.out + ((int64_t)(P.wpad + P.words + z) * P.wstride + base) * kTileBytes +
+                                       ((g ^ (int)(r & 7)) * 16)) = zero;
         }
     }
 }
@@ -178,6 +187,9 @@ SplitParams make_split_params(const Plan &pl, int side, const uint64_t *M, int64
     P.nkb = pl.nkb;
     P.out = static_cast<uint8_t *>(words);
     P.words = side == 0 ? pl.u : pl.v;
+    P.wstride = side == 0 ? pl.nkb * pl.A_rows : pl.B_wstride;
+    P.kstride = side == 0 ? pl.A_rows : pl.B_kstride;
+    P.wpad = side == 0 ? 0 : pl.B_wpad;
     P.p = pl.p;
     P.alpha = side == 0 ? pl.alpha : pl.beta;
     P.mu = P.alpha >= 2 ? (~uint64_t(0)) / P.alpha : 0;

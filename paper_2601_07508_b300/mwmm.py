@@ -55,7 +55,8 @@ class PlanDesc(ctypes.Structure):
                 ("kc", ctypes.c_int64), ("tc_pair", ctypes.c_int32), ("nkc", ctypes.c_int32), ("nsums", ctypes.c_int32),
                 ("q", ctypes.c_double),
                 ("kb_elems", ctypes.c_int64), ("nkb", ctypes.c_int64), ("A_rows", ctypes.c_int64),
-                ("B_rows", ctypes.c_int64), ("A_off", ctypes.c_uint64), ("B_off", ctypes.c_uint64),
+                ("B_rows", ctypes.c_int64), ("B_wpad", ctypes.c_int32), ("pad0", ctypes.c_int32),
+                ("A_off", ctypes.c_uint64), ("B_off", ctypes.c_uint64),
                 ("S_off", ctypes.c_uint64), ("workspace_bytes", ctypes.c_uint64)]
 
     def as_dict(self):
@@ -112,6 +113,7 @@ def lib() -> ctypes.CDLL:
     L.mwmm_workspace_size.restype = ctypes.c_size_t
     L.mwmm_matmul.argtypes = [_vp, _vp, _i64, _vp, _i64, _vp, _i64, _vp, ctypes.c_size_t, _vp]
     L.mwmm_matmul_host.argtypes = [_vp, _vp, _i64, _vp, _i64, _vp, _i64, _vp]
+    L.mwmm_matmul_reuse_a.argtypes = [_vp, _vp, _i64, _vp, _i64, _vp, ctypes.c_size_t, _vp]
     L.mwmm_plan_check.argtypes = [_vp, _vp]
     L.mwmm_plan_destroy.argtypes = [_vp]
     L.mwmm_plan_destroy.restype = None
@@ -232,6 +234,16 @@ def mwmm_matmul(h: int, A, B, C, workspace=None, stream=None):
         ws_ptr, ws_bytes = _dev_ptr(workspace), workspace.numel() * workspace.element_size()
     _check(lib().mwmm_matmul(h, _dev_ptr(A, dt), _ld(A), _dev_ptr(B, dt), _ld(B), _dev_ptr(C, dt), _ld(C),
                              ws_ptr, ws_bytes, _stream_ptr(stream)), "mwmm_matmul")
+
+
+def mwmm_matmul_reuse_a(h: int, B, C, workspace=None, stream=None):
+    """C = A B mod p with the A words left in the workspace by the last product."""
+    dt = _u64_dtypes()
+    ws_ptr, ws_bytes = None, 0
+    if workspace is not None:
+        ws_ptr, ws_bytes = _dev_ptr(workspace), workspace.numel() * workspace.element_size()
+    _check(lib().mwmm_matmul_reuse_a(h, _dev_ptr(B, dt), _ld(B), _dev_ptr(C, dt), _ld(C), ws_ptr, ws_bytes,
+                                     _stream_ptr(stream)), "mwmm_matmul_reuse_a")
 
 
 def mwmm_matmul_host(h: int, A: np.ndarray, B: np.ndarray, C: np.ndarray, stream=None):
@@ -521,6 +533,14 @@ class Plan:
         if C is None:
             C = torch.empty((self.info["m"], self.info["n"]), dtype=A.dtype, device=A.device)
         mwmm_matmul(self.handle, A, B, C, self.alloc_workspace(A.device), stream)
+        return C
+
+    def matmul_reuse_a(self, B, C=None, stream=None):
+        """Product with the A words of the previous matmul (only B is split)."""
+        import torch
+        if C is None:
+            C = torch.empty((self.info["m"], self.info["n"]), dtype=B.dtype, device=B.device)
+        mwmm_matmul_reuse_a(self.handle, B, C, self.alloc_workspace(B.device), stream)
         return C
 
     def matmul_host(self, A: np.ndarray, B: np.ndarray) -> np.ndarray:

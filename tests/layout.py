@@ -2,11 +2,18 @@
 import numpy as np
 
 
-def unpack_words(buf: np.ndarray, words: int, nkb: int, rows_pad: int, kind: str) -> np.ndarray:
+def unpack_words(buf: np.ndarray, words: int, nkb: int, rows_pad: int, kind: str, wpad: int = 0) -> np.ndarray:
     """buf: uint8 bytes of one side's word region.  Returns [words][rows_pad][nkb*kb_elems]
-    as float64 (FP64 words) or int32 (INT8 digits stored as bf16)."""
-    n = words * nkb * rows_pad * 128
-    a = np.asarray(buf[:n]).reshape(words, nkb, rows_pad, 8, 16)
+    as float64 (FP64 words) or int32 (INT8 digits stored as bf16).  wpad > 0:
+    the k-block-major layout with wpad zero words on each side (checked zero)."""
+    if wpad:
+        wp = words + 2 * wpad
+        a = np.asarray(buf[:nkb * wp * rows_pad * 128]).reshape(nkb, wp, rows_pad, 8, 16)
+        assert not a[:, :wpad].any() and not a[:, wpad + words:].any(), "padding words must be zero"
+        a = np.ascontiguousarray(a[:, wpad:wpad + words].transpose(1, 0, 2, 3, 4))
+    else:
+        n = words * nkb * rows_pad * 128
+        a = np.asarray(buf[:n]).reshape(words, nkb, rows_pad, 8, 16)
     r = np.arange(rows_pad) & 7
     out = np.empty_like(a)
     for g in range(8):

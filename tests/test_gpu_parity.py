@@ -182,11 +182,12 @@ def test_validation_reports_entries_out_of_range(M):
 
 
 # ------------------------------------------------------------------ single steps
-@pytest.mark.parametrize("form,b,uv", [("fp64", 40, (2, 2)), ("fp64", 52, (2, 3)), ("fp64", 32, (1, 4)),
-                                       ("int8", 52, None), ("int8", 23, None)])
-def test_split_words_match_oracle(M, oracle, form, b, uv):
+@pytest.mark.parametrize("form,b,uv,n", [("fp64", 40, (2, 2), 90), ("fp64", 52, (2, 3), 90), ("fp64", 32, (1, 4), 90),
+                                         ("int8", 52, None, 290), ("int8", 23, None, 290), ("int8", 52, None, 90),
+                                         ("int8", 40, None, 20)])
+def test_split_words_match_oracle(M, oracle, form, b, uv, n):
     p = SWEEP[b]
-    m, n, k = 70, 90, 150
+    m, k = 70, 150
     A, B = inputs.problem(31, m, n, k, p)
     kw = dict(u=uv[0], v=uv[1]) if uv else {}
     plan = M.Plan(m, n, k, p, form=form, **kw)
@@ -194,10 +195,11 @@ def test_split_words_match_oracle(M, oracle, form, b, uv):
     for side, Mx, rows in ((0, A, m), (1, B, n)):
         words = d["u"] if side == 0 else d["v"]
         rows_pad = d["A_rows"] if side == 0 else d["B_rows"]
-        buf = torch.zeros(words * d["nkb"] * rows_pad * 128, dtype=torch.uint8, device="cuda")
+        wpad = d["B_wpad"] if side == 1 else 0
+        buf = torch.full(((words + 2 * wpad) * d["nkb"] * rows_pad * 128,), 0x5A, dtype=torch.uint8, device="cuda")
         M.mwmm_split(plan.handle, side, dev(Mx), buf)
         torch.cuda.synchronize()
-        W = unpack_words(buf.cpu().numpy(), words, d["nkb"], rows_pad, form)
+        W = unpack_words(buf.cpu().numpy(), words, d["nkb"], rows_pad, form, wpad)
         src = Mx if side == 0 else Mx.T.copy()       # rows x k
         if form == "fp64":
             ref = oracle.split_alpha(src, d["alpha"] if side == 0 else d["beta"], words).astype(np.float64)
@@ -303,3 +305,22 @@ def test_int8_windowed_diagonal_sums_match_oracle(M, oracle):
         sl = slice(kc * d["kc"], min(k, (kc + 1) * d["kc"]))
         ref = oracle.diag_sums(np.ascontiguousarray(Aw[:, :, sl]), np.ascontiguousarray(Bw[:, sl, :]))
         assert np.array_equal(S[:, kc, :m, :n].astype(np.int64), ref)
+
+
+@pytest.mark.parametrize("form", ["int8", "fp64"])
+def test_reuse_a_words_across_products(M, oracle, form):
+    """A decomposed once, then products with new B only (Sec. 4.1's unbalanced
+    scenario); each result matches the oracle."""
+    p = SWEEP[40]
+    m, n, k = 300, 32, 2000
+    A, B1 = inputs.problem(81, m, n, k, p)
+    plan = M.Plan(m, n, k, p, form=form)
+    dA = dev(A)
+    C1 = plan.matmul(dA, dev(B1))
+    assert plan.check() == 0
+    assert np.array_equal(host(C1), oracle.matmul_mod(A, B1, p))
+    for t in range(3):
+        _, B2 = inputs.problem(82 + t, m, n, k, p)
+        C2 = plan.matmul_reuse_a(dev(B2))
+        assert plan.check() == 0
+        assert np.array_equal(host(C2), oracle.matmul_mod(A, B2, p))
