@@ -87,13 +87,16 @@ typedef struct {
                          64 in [64, 1024] (0: 1024) */
     int64_t kc;       /* INT8 form: k-range of one INT32 sum, a multiple of 64
                          (0: the largest allowed by |S_s| < 2^31) */
-    int32_t tc_pair;  /* INT8 form, m > 128: nonzero uses the two-CTA tcgen05
-                         kernel (256 x 256 tiles on an SM pair, cta_group::2)
-                         instead of the one-CTA kernel (128 x 256 tiles).
-                         Bit-exact, but currently slower on B300 (its TMA
-                         completions reach the issuing CTA through a
-                         software relay); default 0 */
-    int32_t reserved[7];
+    int32_t tc_pair;  /* INT8 form, m > 128, n > 128: nonzero uses the two-CTA
+                         tcgen05 kernel (256 x 256 tiles on an SM pair,
+                         cta_group::2) instead of the one-CTA kernel (128 x 256
+                         tiles).  Bit-exact; measured on B300 within 3% of the
+                         one-CTA kernel either way; default 0 */
+    int32_t tc_cluster; /* INT8 form, one-CTA kernel, m > 128: 2 = clusters of
+                         two CTAs sharing each B tile through TMA multicast
+                         (bit-exact, measured 2-3% slower on B300);
+                         0 or 1 = lone CTAs (default) */
+    int32_t reserved[6];
 } mwmm_plan_opts;
 
 /* What a plan decided (mwmm_plan_info). */
@@ -127,7 +130,8 @@ typedef struct {
      * bf16 holding an integer digit (INT8 form, kb_elems = 64).  Padding is 0.
      * INT8 form only: S (int32) at S_off, laid out [nsums][nkc][A_rows][B_rows]. */
     int64_t kb_elems, nkb, A_rows, B_rows;
-    int32_t B_wpad, pad0;
+    int32_t B_wpad;
+    int32_t tc_cluster;     /* INT8: CTAs per cluster of the one-CTA kernel (2: A_rows % 256 == 0) */
     uint64_t A_off, B_off, S_off;
     uint64_t workspace_bytes;
 } mwmm_plan_desc;

@@ -259,7 +259,9 @@ mwmm_status mwmm_batch_create(mwmm_batch_t *out, const mwmm_problem *probs, int 
         mwmm_plan_opts o;
         std::memset(&o, 0, sizeof(o));
         if (opts) o = *opts;
-        o.lambda = 0;  // per-problem block sizes: always the bound
+        o.lambda = 0;      // per-problem block sizes: always the bound
+        o.tc_cluster = 1;  // table items run on lone CTAs (no 256-row padding)
+        o.tc_pair = 0;
         mwmm_status st = mwmm::make_plan(&b->plans[i], q.m, q.n, q.k, q.p, 0, 0, (int)form, &o);
         if (st != MWMM_OK) {
             delete b;

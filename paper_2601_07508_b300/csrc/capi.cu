@@ -168,7 +168,7 @@ mwmm_status mwmm_plan_info(mwmm_plan_t plan, mwmm_plan_desc *d) {
     d->form = P.form; d->u = P.u; d->v = P.v;
     d->alpha = P.alpha; d->beta = P.beta;
     d->lambda = P.lambda; d->lambda_max = P.lambda_max;
-    d->tc_chunk = P.tc_chunk; d->kc = P.kc; d->nkc = P.nkc; d->nsums = P.nsums; d->tc_pair = P.tc_pair;
+    d->tc_chunk = P.tc_chunk; d->kc = P.kc; d->nkc = P.nkc; d->nsums = P.nsums; d->tc_pair = P.tc_pair; d->tc_cluster = P.tc_cluster;
     d->q = P.q;
     d->kb_elems = P.kb_elems; d->nkb = P.nkb; d->A_rows = P.A_rows; d->B_rows = P.B_rows;
     d->B_wpad = P.B_wpad;

@@ -21,6 +21,13 @@
 // of Alg. 6's concatenation).  Items go round-robin over a persistent grid of
 // one CTA per SM, heaviest diagonals first.
 //
+// Clusters of two (plan option tc_cluster = 2): the CTAs of a cluster take
+// the two 128-row halves of a 256-row tile against the same B tile.  Each CTA
+// copies half of the B tile and multicasts it to both, and each MMA commit
+// releases the stage in both CTAs, so a CTA pulls 32 KB per stage from L2
+// instead of 48 KB.  Measured on B300 this does not pay (2-3% slower: L2 reads
+// are not what bounds the kernel), so lone CTAs are the default.
+//
 // Warp roles (320 threads):
 //   warp 0      one lane issues bulk TMA copies of the pre-swizzled word tiles
 //               (A 16 KB + B 32 KB per stage, 4 stages);
@@ -31,7 +38,9 @@
 //               sum the chunks of an item, store S_s.
 // Every wait is bounded (device_common.cuh); a timeout raises the plan's
 // error flag and all roles leave their loops.
+#include <cuda.h>  // CUtensorMap (encoded through the runtime's driver entry point)
 #include <cuda_bf16.h>
+#include <cudaTypedefs.h>
 
 #include <cstring>
 
@@ -78,9 +87,13 @@ struct Item {
     int s0, ndiag, nb, i0, ni, v, b_wpad;
 };
 
-__device__ __forceinline__ Item computed_item(const TcParams &P, int64_t idx) {
+// kCl = 2: item idx is a 256-row tile shared by the cluster; `rank` picks
+// its 128-row half.
+template <int kCl>
+__device__ __forceinline__ Item computed_item(const TcParams &P, int64_t idx, int rank) {
     Item it;
-    const int64_t ntiles = (int64_t)P.mt_count * P.nt_count;
+    const int64_t mtc = P.mt_count / kCl;
+    const int64_t ntiles = mtc * P.nt_count;
     const int64_t tile = idx % ntiles;
     const int64_t rest = idx / ntiles;
     const int kc = (int)(rest % P.nkc);
@@ -97,10 +110,10 @@ __device__ __forceinline__ Item computed_item(const TcParams &P, int64_t idx) {
     // Raster in groups of kGroupN column tiles, rows inside a group first: the
     // ~148 tiles running at once cover about 18 row tiles x 8 column tiles, a
     // squarer region than whole rows, so fewer word tiles are fetched twice.
-    const int64_t gsz = (int64_t)P.mt_count * kGroupN;
+    const int64_t gsz = mtc * kGroupN;
     const int64_t grp = tile / gsz, t = tile % gsz;
     const int64_t width = P.nt_count - grp * kGroupN < kGroupN ? P.nt_count - grp * kGroupN : kGroupN;
-    it.mt = t / width;
+    it.mt = (t / width) * kCl + rank;
     it.nt = grp * kGroupN + t % width;
     it.kb0 = (int64_t)kc * P.kcb;
     const int64_t left = P.nkb - it.kb0;
@@ -141,7 +154,7 @@ __device__ __forceinline__ Item table_item(const TcParams &P, int64_t pos) {
     return it;
 }
 
-template <bool kTable>
+template <bool kTable, int kCl>
 struct ItemRange {
     int64_t begin, end, step;
     __device__ ItemRange(const TcParams &P) {
@@ -149,17 +162,17 @@ struct ItemRange {
             begin = P.cta_off[blockIdx.x];
             end = P.cta_off[blockIdx.x + 1];
             step = 1;
-        } else {
-            begin = blockIdx.x;
+        } else {  // clusters are consecutive blocks
+            begin = blockIdx.x / kCl;
             end = P.nitems;
-            step = gridDim.x;
+            step = gridDim.x / kCl;
         }
     }
 };
 
-template <bool kTable>
-__device__ __forceinline__ Item get_item(const TcParams &P, int64_t idx) {
-    return kTable ? table_item(P, idx) : computed_item(P, idx);
+template <bool kTable, int kCl>
+__device__ __forceinline__ Item get_item(const TcParams &P, int64_t idx, int rank) {
+    return kTable ? table_item(P, idx) : computed_item<kCl>(P, idx, rank);
 }
 
 // ---- tcgen05 wrappers -------------------------------------------------------
@@ -204,6 +217,45 @@ __device__ __forceinline__ void tc_fence_after() {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
 
+__device__ __forceinline__ uint32_t cluster_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ uint32_t peer_addr(const void *local, uint32_t rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(smem_u32(local)), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t cluster_addr) {
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr) : "memory");
+}
+__device__ __forceinline__ void cluster_sync_all() {
+    asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;" ::: "memory");
+}
+
+// Bulk copy of `bytes` from global memory to the same shared-memory offset in
+// every CTA of `mask`, completing `bytes` on the barrier at `bar`'s offset in
+// each of them.
+__device__ __forceinline__ void bulk_g2s_mcast(void *dst, const void *src, uint32_t bytes, uint64_t *bar,
+                                               uint16_t mask) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster [%0], [%1], %2, [%3], "
+        "%4;" ::"r"(smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar)), "h"(mask)
+        : "memory");
+}
+
+// Arrive once on `bar` (same offset) in every CTA of `mask` when all MMAs
+// issued so far by this thread have completed.
+__device__ __forceinline__ void mma_commit_mcast(uint64_t *bar, uint16_t mask) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+            smem_u32(bar)),
+        "h"(mask)
+        : "memory");
+}
+
 // 32 consecutive FP32 columns of this thread's TMEM lane.
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
     asm volatile(
@@ -219,13 +271,15 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-template <bool kTable>
+template <bool kTable, int kCl>
 __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_constant__ TcParams P) {
+    static_assert(kCl == 1 || (kCl == 2 && !kTable), "clusters of two run computed items only");
     extern __shared__ uint8_t smem_raw[];
     __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES], tfull[2], tempty[2], done;
     __shared__ uint32_t tmem_base_sh;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int rank = kCl == 1 ? 0 : (int)cluster_rank();
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t pad = ((raw + 1023u) & ~1023u) - raw;
     uint8_t *sA = smem_raw + pad;
@@ -234,7 +288,7 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_consta
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
             mbar_init(&full[s], 1);
-            mbar_init(&empty[s], 1);
+            mbar_init(&empty[s], kCl);  // one MMA commit from each CTA of the cluster
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&tfull[b], 1);
@@ -251,7 +305,10 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_consta
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     tc_fence_before();
-    __syncthreads();
+    if (kCl == 1)
+        __syncthreads();
+    else
+        cluster_sync_all();  // the peer's barriers exist before any multicast reaches them
     tc_fence_after();
     const uint32_t tmem_base = tmem_base_sh;
 
@@ -259,9 +316,9 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_consta
         if (lane == 0) {  // ---------------- TMA producer
             uint64_t g = 0;
             bool alive = true;
-            const ItemRange<kTable> R(P);
+            const ItemRange<kTable, kCl> R(P);
             for (int64_t idx = R.begin; alive && idx < R.end; idx += R.step) {
-                const Item it = get_item<kTable>(P, idx);
+                const Item it = get_item<kTable, kCl>(P, idx, rank);
                 // One thread issues every copy, so the per-stage work is kept to a
                 // few adds: nested (word, k-block) loops and running addresses.
                 // The window's B words B_{s0-i} .. B_{s0-i+ndiag-1} are contiguous
@@ -283,14 +340,21 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_consta
                         }
                         mbar_arrive_expect_tx(&full[slot], stage_bytes);
                         bulk_g2s(sA + slot * kTileA, a, kTileA, &full[slot]);
-                        bulk_g2s(sB + slot * kTileB, b, bbytes, &full[slot]);
+                        if (kCl == 1) {
+                            bulk_g2s(sB + slot * kTileB, b, bbytes, &full[slot]);
+                        } else {  // ndiag * nb is a multiple of 16 rows: halves keep the 1 KB swizzle atoms
+                            const uint32_t h = bbytes / 2;
+                            bulk_g2s_mcast(sB + slot * kTileB + rank * h, b + rank * h, h, &full[slot], 0x3);
+                        }
                     }
                 }
             }
-            // Let every copy this lane started land before the CTA can exit.
+            // Let every copy into this CTA (own and the peer's multicast) land,
+            // and every commit aimed at this CTA's barriers arrive, before exit.
             for (int s = 0; s < STAGES; ++s) {
                 const uint64_t armed = g > (uint64_t)s ? (g - s + STAGES - 1) / STAGES : 0;
                 if (armed) mbar_wait(&full[s], (uint32_t)((armed - 1) & 1), P.err);
+                if (armed && kCl > 1) mbar_wait(&empty[s], (uint32_t)((armed - 1) & 1), P.err);
             }
         }
     } else if (warp == 1) {
@@ -298,9 +362,9 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_consta
             uint64_t g = 0, c = 0;
             bool alive = true;
             const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
-            const ItemRange<kTable> R(P);
+            const ItemRange<kTable, kCl> R(P);
             for (int64_t idx = R.begin; alive && idx < R.end; idx += R.step) {
-                const Item it = get_item<kTable>(P, idx);
+                const Item it = get_item<kTable, kCl>(P, idx, rank);
                 const int64_t nvb = (int64_t)it.ni * it.nkbc;
                 const uint32_t idesc = idesc_n(it.ndiag * it.nb);
                 for (int64_t t0 = 0; alive && t0 < nvb; t0 += P.chunk_blocks, ++c) {
@@ -323,7 +387,10 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_consta
 #pragma unroll
                         for (int kk = 0; kk < 4; ++kk)  // K = 16 per MMA: +32 bytes = +2 in the address field
                             mma_bf16(dt, ad + 2 * kk, bd + 2 * kk, idesc, (t > t0 || kk > 0) ? 1u : 0u);
-                        mma_commit(&empty[slot]);
+                        if (kCl == 1)
+                            mma_commit(&empty[slot]);
+                        else
+                            mma_commit_mcast(&empty[slot], 0x3);  // the slot is free once both CTAs are done
                     }
                     mma_commit(&tfull[buf]);
                 }
@@ -338,9 +405,9 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_consta
         const uint32_t tlane = tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(half * 128);
         uint64_t c = 0;
         bool alive = true;
-        const ItemRange<kTable> R(P);
+        const ItemRange<kTable, kCl> R(P);
         for (int64_t idx = R.begin; alive && idx < R.end; idx += R.step) {
-            const Item it = get_item<kTable>(P, idx);
+            const Item it = get_item<kTable, kCl>(P, idx, rank);
             const int64_t nvb = (int64_t)it.ni * it.nkbc;
             const int64_t nch = (nvb + P.chunk_blocks - 1) / P.chunk_blocks;
             int32_t acc[128];
@@ -382,7 +449,10 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_consta
     }
 
     tc_fence_before();
-    __syncthreads();
+    if (kCl == 1)
+        __syncthreads();
+    else
+        cluster_sync_all();  // neither CTA exits while the other may still signal it
     tc_fence_after();
     if (warp == 1)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(kTmemCols)
@@ -393,16 +463,14 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_consta
 // Pair kernel (opt-in, plan option tc_pair): a cluster of two CTAs on two SMs
 // computes a 256 x 256 tile with tcgen05.mma.cta_group::2 (M = 256 split over
 // the pair, each CTA holding its 128 rows of A and its 128-row half of B).
-// Each SM then streams 32 KB of operands per 64-wide k-block instead of 48 KB,
-// and 6 stages fit in shared memory.  Roles per CTA as above; only the even
-// CTA ("leader") issues MMAs.  The odd CTA's warp 1 relays the completion of
-// its own TMA stages to the leader (remote mbarrier arrive), and its epilogue
-// warps report drained accumulators to the leader the same way; the leader's
-// commits are multicast to both CTAs.  Measured on B300 this relay makes a
-// stage's round trip several times longer than the one-CTA kernel's, so the
-// one-CTA kernel stays the default; the relay would go away if the odd CTA's
-// copies completed on the leader's barrier directly (tensor TMA with
-// .cta_group::2).
+// Each SM then receives 32 KB of operands per 64-wide k-block instead of
+// 48 KB, and 6 stages fit in shared memory.  Roles per CTA as above; only the
+// even CTA ("leader") issues MMAs.  Both CTAs load their halves with tensor
+// TMA (.cta_group::2), whose completion lands directly on the leader's
+// barrier, so the leader waits on one barrier per stage; its commits are
+// multicast to both CTAs.  The word tiles are already in their shared-memory
+// order, so the tensor maps describe them as plain 2-D arrays of 128-byte rows
+// (no TMA swizzle).
 constexpr int P_STAGES = 6;
 constexpr int BM2 = 256;
 constexpr uint32_t kTileA2 = 128 * kTileBytes;  // own 128 rows of A: 16 KB
@@ -411,22 +479,6 @@ constexpr int kSmemPair = P_STAGES * (kTileA2 + kTileB2) + 1024;
 constexpr uint32_t kIdescPair = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
                                 ((uint32_t)(BM2 >> 4) << 24);
 
-__device__ __forceinline__ uint32_t cluster_rank() {
-    uint32_t r;
-    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-    return r;
-}
-__device__ __forceinline__ uint32_t peer_addr(const void *local, uint32_t rank) {
-    uint32_t r;
-    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(smem_u32(local)), "r"(rank));
-    return r;
-}
-__device__ __forceinline__ void mbar_arrive_cluster(uint32_t cluster_addr) {
-    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr) : "memory");
-}
-__device__ __forceinline__ void cluster_sync_all() {
-    asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;" ::: "memory");
-}
 __device__ __forceinline__ void mma_bf16_pair(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t acc) {
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
@@ -478,10 +530,22 @@ __device__ __forceinline__ Item pair_item(const TcParams &P, int64_t idx) {
     return it;
 }
 
+// 2-D tensor TMA of a (64-element x 128-row) box at row y into this CTA's
+// shared memory; the bytes complete on the barrier at cluster address `bar`
+// (the leader's) -- the .cta_group::2 form allows either CTA of the pair.
+__device__ __forceinline__ void tma2_load_pair(void *dst, const CUtensorMap *map, int32_t y, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, "
+        "%3}], [%4];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(0), "r"(y), "r"(bar)
+        : "memory");
+}
+
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS, 1)
-    gemm_tc_pair_kernel(const __grid_constant__ TcParams P) {
+    gemm_tc_pair_kernel(const __grid_constant__ TcParams P, const __grid_constant__ CUtensorMap tmA,
+                        const __grid_constant__ CUtensorMap tmB) {
     extern __shared__ uint8_t smem_raw[];
-    __shared__ __align__(8) uint64_t full[P_STAGES], empty[P_STAGES], pfull[P_STAGES], tfull[2], tempty[2], done;
+    __shared__ __align__(8) uint64_t full[P_STAGES], empty[P_STAGES], tfull[2], tempty[2], done;
     __shared__ uint32_t tmem_base_sh;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -496,7 +560,6 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS, 1)
         for (int s = 0; s < P_STAGES; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
-            mbar_init(&pfull[s], 1);
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&tfull[b], 1);
@@ -520,33 +583,40 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS, 1)
 
     if (warp == 0) {
         if (lane == 0) {  // ---------------- TMA producer (both CTAs)
+            const uint32_t lead_full = peer_addr(&full[0], 0);
             uint64_t g = 0;
             bool alive = true;
             for (int64_t idx = cid; alive && idx < P.nitems; idx += ncl) {
                 const Item it = pair_item(P, idx);
-                const int64_t a_step = it.A_rows * kTileBytes, b_step = it.B_rows * kTileBytes;
                 for (int ii = 0; alive && ii < it.ni; ++ii) {
                     const int i = it.i0 + ii;
                     const int j = it.s0 - i;
-                    const uint8_t *a = it.Aw + (((int64_t)i * it.nkb + it.kb0) * it.A_rows + it.mt * BM2 + rank * 128) *
-                                                   kTileBytes;
-                    const uint8_t *b = it.Bw + (((int64_t)j * it.nkb + it.kb0) * it.B_rows + it.nt * BN + rank * 128) *
-                                                   kTileBytes;
-                    for (int64_t kb = 0; kb < it.nkbc; ++kb, ++g, a += a_step, b += b_step) {
+                    // row coordinates of the tensor maps (the host checks they fit int32)
+                    int32_t ya = (int32_t)(((int64_t)i * it.nkb + it.kb0) * it.A_rows + it.mt * BM2 + rank * 128);
+                    int32_t yb = (int32_t)(((int64_t)j * it.nkb + it.kb0) * it.B_rows + it.nt * BN + rank * 128);
+                    for (int64_t kb = 0; kb < it.nkbc;
+                         ++kb, ++g, ya += (int32_t)it.A_rows, yb += (int32_t)it.B_rows) {
                         const int slot = (int)(g % P_STAGES);
                         if (!mbar_wait(&empty[slot], (uint32_t)(((g / P_STAGES) & 1) ^ 1), P.err)) {
                             alive = false;
                             break;
                         }
-                        mbar_arrive_expect_tx(&full[slot], kTileA2 + kTileB2);
-                        bulk_g2s(sA + slot * kTileA2, a, kTileA2, &full[slot]);
-                        bulk_g2s(sB + slot * kTileB2, b, kTileB2, &full[slot]);
+                        // the leader's barrier counts both CTAs' bytes
+                        if (leader) mbar_arrive_expect_tx(&full[slot], 2 * (kTileA2 + kTileB2));
+                        const uint32_t bar = lead_full + (uint32_t)(slot * sizeof(uint64_t));
+                        tma2_load_pair(sA + slot * kTileA2, &tmA, ya, bar);
+                        tma2_load_pair(sB + slot * kTileB2, &tmB, yb, bar);
                     }
                 }
             }
-            for (int s = 0; s < P_STAGES; ++s) {  // let every copy land before exit
+            // Before exit: the leader sees every byte of both CTAs land; both
+            // wait for the leader's last commit to each slot (after which no
+            // copy into, or signal to, this CTA is outstanding).
+            for (int s = 0; s < P_STAGES; ++s) {
                 const uint64_t armed = g > (uint64_t)s ? (g - s + P_STAGES - 1) / P_STAGES : 0;
-                if (armed) mbar_wait(&full[s], (uint32_t)((armed - 1) & 1), P.err);
+                if (!armed) continue;
+                if (leader) mbar_wait(&full[s], (uint32_t)((armed - 1) & 1), P.err);
+                mbar_wait(&empty[s], (uint32_t)((armed - 1) & 1), P.err);
             }
         }
     } else if (warp == 1) {
@@ -569,7 +639,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS, 1)
                     for (int64_t t = t0; t < tend; ++t, ++g) {
                         const int slot = (int)(g % P_STAGES);
                         const uint32_t par = (uint32_t)((g / P_STAGES) & 1);
-                        if (!mbar_wait(&full[slot], par, P.err) || !mbar_wait(&pfull[slot], par, P.err)) {
+                        if (!mbar_wait(&full[slot], par, P.err)) {
                             alive = false;
                             break;
                         }
@@ -585,22 +655,6 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS, 1)
             }
             mma_commit_pair(&done, 1);
             mbar_wait(&done, 0, P.err);
-        } else if (lane == 0) {  // ---------------- forwarder (odd CTA)
-            const uint32_t lead_pfull = peer_addr(&pfull[0], 0);
-            uint64_t g = 0;
-            bool alive = true;
-            for (int64_t idx = cid; alive && idx < P.nitems; idx += ncl) {
-                const Item it = pair_item(P, idx);
-                const int64_t nvb = (int64_t)it.ni * it.nkbc;
-                for (int64_t t = 0; t < nvb; ++t, ++g) {
-                    const int slot = (int)(g % P_STAGES);
-                    if (!mbar_wait(&full[slot], (uint32_t)((g / P_STAGES) & 1), P.err)) {
-                        alive = false;
-                        break;
-                    }
-                    mbar_arrive_cluster(lead_pfull + (uint32_t)(slot * sizeof(uint64_t)));
-                }
-            }
         }
     } else {  // -------------------------------- epilogue warps 2..9 (both CTAs)
         const int quarter = warp & 3;
@@ -664,19 +718,18 @@ int sm_count() {
     return cached[dev];
 }
 
-// Clusters of two that can be resident at once (the pair kernel is
-// persistent: one cluster per SM pair, never more than fit).
-int pair_clusters() {
-    static int cached[64] = {0};
+// Clusters of two of `kernel` that can be resident at once (the cluster
+// kernels are persistent: one cluster per SM pair, never more than fit).
+int max_clusters2(const void *kernel, int smem, int (&cached)[64]) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
     if (!cached[dev]) {
-        if (set_smem_attr(reinterpret_cast<const void *>(gemm_tc_pair_kernel), kSmemPair) != cudaSuccess) return 0;
+        if (set_smem_attr(kernel, smem) != cudaSuccess) return 0;
         cudaLaunchConfig_t cfg;
         std::memset(&cfg, 0, sizeof(cfg));
         cfg.gridDim = dim3(2 * (unsigned)(sm_count() / 2), 1, 1);
         cfg.blockDim = dim3(THREADS, 1, 1);
-        cfg.dynamicSmemBytes = kSmemPair;
+        cfg.dynamicSmemBytes = smem;
         cudaLaunchAttribute attr;
         attr.id = cudaLaunchAttributeClusterDimension;
         attr.val.clusterDim.x = 2;
@@ -685,12 +738,51 @@ int pair_clusters() {
         cfg.attrs = &attr;
         cfg.numAttrs = 1;
         int n = 0;
-        if (cudaOccupancyMaxActiveClusters(&n, reinterpret_cast<const void *>(gemm_tc_pair_kernel), &cfg) !=
-                cudaSuccess || n <= 0)
-            return 0;
+        if (cudaOccupancyMaxActiveClusters(&n, kernel, &cfg) != cudaSuccess || n <= 0) return 0;
         cached[dev] = n;
     }
     return cached[dev];
+}
+
+// cuTensorMapEncodeTiled, looked up once through the runtime (no link
+// against the driver library).
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static const PFN_cuTensorMapEncodeTiled_v12000 fn = []() -> PFN_cuTensorMapEncodeTiled_v12000 {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            return nullptr;
+        return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+    }();
+    return fn;
+}
+
+// A word region as a 2-D tensor of `rows` 128-byte rows (64 x 16-bit), read
+// in (64 x 128-row) boxes with no swizzle: a box is one contiguous 16 KB tile.
+int encode_rows_map(CUtensorMap *map, const void *base, uint64_t rows) {
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc) return (int)cudaErrorNotSupported;
+    if (rows == 0 || rows > (uint64_t)INT32_MAX) return (int)cudaErrorInvalidValue;  // int32 coordinates
+    const cuuint64_t dims[2] = {64, rows};
+    const cuuint64_t strides[1] = {kTileBytes};
+    const cuuint32_t box[2] = {64, 128};
+    const cuuint32_t estr[2] = {1, 1};
+    CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, const_cast<void *>(base), dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? 0 : (int)cudaErrorInvalidValue;
+}
+
+int pair_clusters() {
+    static int cached[64] = {0};
+    return max_clusters2(reinterpret_cast<const void *>(gemm_tc_pair_kernel), kSmemPair, cached);
+}
+
+int mcast_clusters() {
+    static int cached[64] = {0};
+    return max_clusters2(reinterpret_cast<const void *>(gemm_tc_kernel<false, 2>), kSmemBytes, cached);
 }
 
 }  // namespace
@@ -753,23 +845,55 @@ int launch_gemm_tc(const Plan &pl, const void *Aw, const void *Bw, int32_t *S, i
         const int clusters = pair_clusters();
         if (clusters <= 0) return (int)cudaErrorLaunchOutOfResources;
         const int64_t ncl = P.nitems < clusters ? P.nitems : clusters;
-        gemm_tc_pair_kernel<<<(unsigned)(2 * ncl), THREADS, kSmemPair, static_cast<cudaStream_t>(stream)>>>(P);
+        CUtensorMap tmA, tmB;
+        int r = encode_rows_map(&tmA, Aw, (uint64_t)pl.u * pl.nkb * pl.A_rows);
+        if (r == 0) r = encode_rows_map(&tmB, Bw, (uint64_t)pl.v * pl.nkb * pl.B_rows);
+        if (r != 0) return r;
+        gemm_tc_pair_kernel<<<(unsigned)(2 * ncl), THREADS, kSmemPair, static_cast<cudaStream_t>(stream)>>>(P, tmA,
+                                                                                                            tmB);
         return (int)cudaGetLastError();
     }
-    cudaError_t e = set_smem_attr(reinterpret_cast<const void *>(gemm_tc_kernel<false>), kSmemBytes);
+    if (pl.tc_cluster == 2) {
+        P.nitems /= 2;  // items are 256-row tiles; A_rows % 256 == 0
+        const void *kern = reinterpret_cast<const void *>(gemm_tc_kernel<false, 2>);
+        cudaError_t e = set_smem_attr(kern, kSmemBytes);
+        if (e != cudaSuccess) return (int)e;
+        const int clusters = mcast_clusters();
+        if (clusters <= 0) return (int)cudaErrorLaunchOutOfResources;
+        const int64_t ncl = P.nitems < clusters ? P.nitems : clusters;
+        cudaLaunchConfig_t cfg;
+        std::memset(&cfg, 0, sizeof(cfg));
+        cfg.gridDim = dim3((unsigned)(2 * ncl), 1, 1);
+        cfg.blockDim = dim3(THREADS, 1, 1);
+        cfg.dynamicSmemBytes = kSmemBytes;
+        cfg.stream = static_cast<cudaStream_t>(stream);
+        cudaLaunchAttribute attr;
+        attr.id = cudaLaunchAttributeClusterDimension;
+        attr.val.clusterDim.x = 2;
+        attr.val.clusterDim.y = 1;
+        attr.val.clusterDim.z = 1;
+        cfg.attrs = &attr;
+        cfg.numAttrs = 1;
+        return (int)cudaLaunchKernelEx(&cfg, gemm_tc_kernel<false, 2>, P);
+    }
+    cudaError_t e = set_smem_attr(reinterpret_cast<const void *>(gemm_tc_kernel<false, 1>), kSmemBytes);
     if (e != cudaSuccess) return (int)e;
     const int64_t sms = sm_count();
     const unsigned grid = (unsigned)(P.nitems < sms ? P.nitems : sms);
-    gemm_tc_kernel<false><<<grid, THREADS, kSmemBytes, static_cast<cudaStream_t>(stream)>>>(P);
+    gemm_tc_kernel<false, 1><<<grid, THREADS, kSmemBytes, static_cast<cudaStream_t>(stream)>>>(P);
     return (int)cudaGetLastError();
 }
 
 int tc_sm_count() { return sm_count(); }
 
 int prepare_tc_attributes() {
-    cudaError_t e = set_smem_attr(reinterpret_cast<const void *>(gemm_tc_kernel<false>), kSmemBytes);
-    if (e == cudaSuccess) e = set_smem_attr(reinterpret_cast<const void *>(gemm_tc_kernel<true>), kSmemBytes);
-    if (e == cudaSuccess) (void)pair_clusters();  // cache the cluster count outside any capture
+    cudaError_t e = set_smem_attr(reinterpret_cast<const void *>(gemm_tc_kernel<false, 1>), kSmemBytes);
+    if (e == cudaSuccess) e = set_smem_attr(reinterpret_cast<const void *>(gemm_tc_kernel<true, 1>), kSmemBytes);
+    if (e == cudaSuccess) {  // cache the cluster counts outside any capture
+        (void)pair_clusters();
+        (void)mcast_clusters();
+        (void)tensor_map_encoder();
+    }
     return (int)e;
 }
 
@@ -782,9 +906,9 @@ int launch_gemm_tc_table(const TcItem *items, const int64_t *cta_off, int ctas, 
     P.cta_off = cta_off;
     P.chunk_blocks = chunk_blocks;
     P.err = err;
-    cudaError_t e = set_smem_attr(reinterpret_cast<const void *>(gemm_tc_kernel<true>), kSmemBytes);
+    cudaError_t e = set_smem_attr(reinterpret_cast<const void *>(gemm_tc_kernel<true, 1>), kSmemBytes);
     if (e != cudaSuccess) return (int)e;
-    gemm_tc_kernel<true><<<ctas, THREADS, kSmemBytes, static_cast<cudaStream_t>(stream)>>>(P);
+    gemm_tc_kernel<true, 1><<<ctas, THREADS, kSmemBytes, static_cast<cudaStream_t>(stream)>>>(P);
     return (int)cudaGetLastError();
 }
 

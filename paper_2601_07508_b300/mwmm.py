@@ -38,7 +38,8 @@ class MwmmError(RuntimeError):
 
 class PlanOpts(ctypes.Structure):
     _fields_ = [("lambda_", ctypes.c_int64), ("validate", ctypes.c_int32), ("tc_chunk", ctypes.c_int32),
-                ("kc", ctypes.c_int64), ("tc_pair", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
+                ("kc", ctypes.c_int64), ("tc_pair", ctypes.c_int32), ("tc_cluster", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 6)]
 
 
 class Timing(ctypes.Structure):
@@ -55,7 +56,7 @@ class PlanDesc(ctypes.Structure):
                 ("kc", ctypes.c_int64), ("tc_pair", ctypes.c_int32), ("nkc", ctypes.c_int32), ("nsums", ctypes.c_int32),
                 ("q", ctypes.c_double),
                 ("kb_elems", ctypes.c_int64), ("nkb", ctypes.c_int64), ("A_rows", ctypes.c_int64),
-                ("B_rows", ctypes.c_int64), ("B_wpad", ctypes.c_int32), ("pad0", ctypes.c_int32),
+                ("B_rows", ctypes.c_int64), ("B_wpad", ctypes.c_int32), ("tc_cluster", ctypes.c_int32),
                 ("A_off", ctypes.c_uint64), ("B_off", ctypes.c_uint64),
                 ("S_off", ctypes.c_uint64), ("workspace_bytes", ctypes.c_uint64)]
 
@@ -202,7 +203,8 @@ def _ld(t) -> int:
 
 # --------------------------------------------------------------------------- C-named calls
 def mwmm_plan(m: int, n: int, k: int, p: int, u: int = 0, v: int = 0, form="auto", lam: int = 0,
-              validate: bool = False, tc_chunk: int = 0, kc: int = 0, tc_pair: bool = False) -> int:
+              validate: bool = False, tc_chunk: int = 0, kc: int = 0, tc_pair: bool = False,
+              tc_cluster: int = 0) -> int:
     if isinstance(form, str):
         form = FORMS[form]
     h = _vp()
@@ -212,6 +214,7 @@ def mwmm_plan(m: int, n: int, k: int, p: int, u: int = 0, v: int = 0, form="auto
     o.tc_chunk = tc_chunk
     o.kc = kc
     o.tc_pair = 1 if tc_pair else 0
+    o.tc_cluster = tc_cluster
     _check(lib().mwmm_plan(ctypes.byref(h), m, n, k, p, u, v, form, ctypes.byref(o)), "mwmm_plan")
     return h.value
 
@@ -503,8 +506,9 @@ class Plan:
     """Owns a plan handle: ``Plan(m, n, k, p, form="int8")``, then ``.matmul(A, B)``."""
 
     def __init__(self, m: int, n: int, k: int, p: int, u: int = 0, v: int = 0, form="auto", lam: int = 0,
-                 validate: bool = False, tc_chunk: int = 0, kc: int = 0, tc_pair: bool = False):
-        self.handle = mwmm_plan(m, n, k, p, u, v, form, lam, validate, tc_chunk, kc, tc_pair)
+                 validate: bool = False, tc_chunk: int = 0, kc: int = 0, tc_pair: bool = False,
+                 tc_cluster: int = 0):
+        self.handle = mwmm_plan(m, n, k, p, u, v, form, lam, validate, tc_chunk, kc, tc_pair, tc_cluster)
         self.info = mwmm_plan_info(self.handle)
         self.workspace = None
 

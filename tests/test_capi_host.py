@@ -86,7 +86,7 @@ def test_int8_plan_digits_match_oracle(M, oracle, p):
     assert d["kc"] % 64 == 0 and d["kc"] * min(u, u) * 2 ** 14 < 2 ** 31
     assert d["nkc"] == -(-5000 // d["kc"])
     assert d["tc_chunk"] == 1024 and d["tc_chunk"] * 2 ** 14 <= 2 ** 24
-    assert d["A_rows"] == 128 and d["B_rows"] == 512
+    assert d["A_rows"] == 128 and d["B_rows"] == 512  # m = 100: one row tile, no cluster
 
 
 def test_plan_errors(M):
@@ -120,3 +120,30 @@ def test_workspace_layout_sizes(M):
     h = M.mwmm_plan(0, 200, 100, p, 2, 2, "fp64")
     assert M.mwmm_workspace_size(h) == 0
     M.mwmm_plan_destroy(h)
+
+
+@pytest.mark.parametrize("m,n,cl,want_cl,want_rows", [
+    (100, 300, 0, 1, 128),    # default: lone CTAs
+    (700, 300, 0, 1, 768),
+    (129, 300, 2, 2, 256),    # clusters of two need 256-row tiles
+    (700, 20, 2, 2, 768),     # narrow n (diagonal windows) clusters too
+    (700, 300, 1, 1, 768),
+    (100, 300, 2, 1, 128),    # a single row tile cannot be shared
+])
+def test_int8_plan_cluster_choice(M, m, n, cl, want_cl, want_rows):
+    h = M.mwmm_plan(m, n, 1000, SWEEP[52], 0, 0, "int8", tc_cluster=cl)
+    d = M.mwmm_plan_info(h)
+    M.mwmm_plan_destroy(h)
+    assert d["tc_cluster"] == want_cl and d["A_rows"] == want_rows and d["tc_pair"] == 0
+    assert d["workspace_bytes"] >= d["S_off"] + d["nsums"] * d["nkc"] * d["A_rows"] * d["B_rows"] * 4
+
+
+def test_int8_plan_cluster_option_range(M):
+    for cl in (-1, 3):
+        with pytest.raises(M.MwmmError) as e:
+            M.mwmm_plan(300, 300, 64, SWEEP[40], 0, 0, "int8", tc_cluster=cl)
+        assert e.value.status == 1
+    h = M.mwmm_plan(300, 300, 64, SWEEP[40], 0, 0, "int8", tc_pair=True)  # the pair kernel excludes clusters
+    d = M.mwmm_plan_info(h)
+    M.mwmm_plan_destroy(h)
+    assert d["tc_pair"] == 1 and d["tc_cluster"] == 1
