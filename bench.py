@@ -54,6 +54,8 @@ def parse_args():
     ap.add_argument("--no-serve", action="store_true", help="skip the serving run")
     ap.add_argument("--no-shapes", action="store_true", help="skip the 50-bit shape study")
     ap.add_argument("--no-unbalanced", action="store_true", help="skip the block-Wiedemann shape")
+    ap.add_argument("--variant-sweep", action="store_true",
+                    help="also time every FP64 variant at every bitsize 20..52 (Table 4 crossovers; minutes)")
     ap.add_argument("--serve-requests", type=int, default=20000)
     ap.add_argument("--serve-pool", type=int, default=256, help="distinct operand sets the requests cycle through")
     return ap.parse_args()
@@ -322,48 +324,138 @@ def run_shapes(dev):
     return out
 
 
-def run_unbalanced(dev, reps=5):
-    """The paper's unbalanced scenario (Sec. 4.1): m = 10923, k = 32768, n = 32,
-    A decomposed once and reused (its split is excluded, as in the paper);
-    each timed product splits B, multiplies and recombines."""
+UNBALANCED = (10923, 32, 32768)  # m, n, k of the block-Wiedemann products (Sec. 4.1)
+
+# One bitsize per FP64 variant inside the range where its block size covers
+# the whole k (one reduction per product): the variant's rate plateau.
+PLATEAU_BITS = {(1, 2): 20, (1, 3): 26, (1, 4): 26, (2, 2): 32, (2, 3): 40}
+
+
+_A52 = {}
+
+
+def _unbalanced_operands(dev, b):
+    """A (m x k) and B (k x n) of the unbalanced shape for the largest prime
+    below 2^b; A is the 52-bit matrix of seed 7 (drawn once) reduced mod p."""
+    import torch
+    m, n, k = UNBALANCED
+    p = inputs.largest_prime_below_pow2(b)
+    if dev not in _A52:
+        A52, _ = inputs.problem(7, m, 1, k, inputs.largest_prime_below_pow2(52))
+        _A52[dev] = torch.from_numpy(A52.view(np.int64)).to(dev)
+    dA = torch.remainder(_A52[dev], p)
+    B = inputs.matrix(b, inputs.STREAM_B, k, n, p)
+    return p, dA, torch.from_numpy(B.view(np.int64)).to(dev)
+
+
+def _time_reuse_a(pl, dA, dB, reps):
+    """Split A once, then time `reps` products that split B, multiply and
+    recombine (the paper excludes A's decomposition in this scenario)."""
     import torch
     from paper_2601_07508_b300 import mwmm
-    m, k, n = 10923, 32768, 32
-    p52 = inputs.largest_prime_below_pow2(52)
-    A52, _ = inputs.problem(7, m, 1, k, p52)
-    dA52 = torch.from_numpy(A52.view(np.int64)).to(dev)
-    del A52
+    C = pl.matmul(dA, dB)
+    torch.cuda.synchronize()
+    mwmm.mwmm_plan_set_timing(pl.handle, True)
+    for _ in range(reps):
+        pl.matmul_reuse_a(dB, C)
+    t = mwmm.mwmm_plan_timing(pl.handle)
+    assert pl.check() == 0
+    return t["total_ms"] / t["calls"], C
+
+
+def run_unbalanced(dev, reps=5):
+    """The paper's unbalanced scenario (Sec. 4.1): m = 10923, k = 32768, n = 32,
+    A decomposed once and reused.  INT8-word form per bitsize, and the FP64
+    variants without and with concatenation of B's words (Alg. 6) at their
+    plateau bitsizes (the layout of Table 3)."""
+    import torch
+    from paper_2601_07508_b300 import mwmm
+    m, n, k = UNBALANCED
+    flops = 2.0 * m * n * k
     out = {"workload": "m = 10923, k = 32768, n = 32 (block-Wiedemann shape); A split once and reused, time "
                        "= split of B + word products + recombination; A = (52-bit uniform matrix) mod p"}
-    for b, fp64 in ((20, None), (32, (1, 2)), (40, (2, 2)), (48, None), (52, (2, 3))):
+    int8_ref = {}
+    for b in (20, 26, 32, 40, 48, 52):
+        p, dA, dB = _unbalanced_operands(dev, b)
+        pl = mwmm.Plan(m, n, k, p, form="int8")
+        ms, C = _time_reuse_a(pl, dA, dB, reps)
+        out[str(b)] = {"int8": {"ms": ms, "gops": flops / ms / 1e6, "uv": [pl.info["u"], pl.info["v"]]}}
+        int8_ref[b] = C
+        del pl, dA, dB
+    table = {}
+    for uv, b in PLATEAU_BITS.items():
+        p, dA, dB = _unbalanced_operands(dev, b)
+        row = {"bits": b}
+        for name, cat in (("plain", 1), ("concat", 2)):
+            pl = mwmm.Plan(m, n, k, p, uv[0], uv[1], form="fp64", f64_concat=cat)
+            ms, C = _time_reuse_a(pl, dA, dB, 1)
+            row[name] = {"ms": ms, "gops": flops / ms / 1e6, "ksplit": pl.info["ksplit"],
+                         "equals_int8": bool(torch.equal(C, int8_ref[b]))}
+            del pl, C
+        row["increase_pct"] = 100.0 * (row["plain"]["ms"] / row["concat"]["ms"] - 1.0)
+        table["%d,%d" % uv] = row
+        del dA, dB
+        torch.cuda.empty_cache()
+    out["fp64_concat_table"] = table
+    return out
+
+
+def run_variant_sweep(dev, size=2048):
+    """Every FP64 variant the block-size bound allows at every bitsize 20..52,
+    on a size^3 square product and on the unbalanced shape (concatenated
+    variant, A reused): the best variant per bitsize gives the crossover
+    ranges of Table 4 measured on this GPU."""
+    import torch
+    from paper_2601_07508_b300 import mwmm
+    variants = [(1, 1), (1, 2), (1, 3), (1, 4), (2, 2), (2, 3)]
+    out = {"square": {"m": size, "n": size, "k": size}, "unbalanced_concat": {}}
+    sq = {}
+    for b in range(20, 53):
         p = inputs.largest_prime_below_pow2(b)
-        dA = torch.remainder(dA52, p) if b < 52 else dA52
-        B = inputs.matrix(b, inputs.STREAM_B, k, n, p)
+        A, B = inputs.problem(b, size, size, size, p)
+        dA = torch.from_numpy(A.view(np.int64)).to(dev)
         dB = torch.from_numpy(B.view(np.int64)).to(dev)
-        res = {}
-        forms = [("int8", (0, 0))] + ([("fp64", fp64)] if fp64 else [])
-        ref = None
-        for form, uv in forms:
-            pl = mwmm.Plan(m, n, k, p, uv[0], uv[1], form=form)
-            C = pl.matmul(dA, dB)  # splits A
+        row = {}
+        for uv in variants:
+            try:
+                pl = mwmm.Plan(size, size, size, p, uv[0], uv[1], form="fp64")
+            except mwmm.MwmmError:
+                continue
+            C = pl.matmul(dA, dB)
             torch.cuda.synchronize()
             mwmm.mwmm_plan_set_timing(pl.handle, True)
-            r = reps if form == "int8" else 1
-            for _ in range(r):
-                pl.matmul_reuse_a(dB, C)
+            pl.matmul(dA, dB, C)
             t = mwmm.mwmm_plan_timing(pl.handle)
             assert pl.check() == 0
-            ms = t["total_ms"] / t["calls"]
-            key = form if form == "int8" else "fp64_%d%d" % uv
-            res[key] = {"ms": ms, "gops": 2.0 * m * n * k / ms / 1e6, "uv": [pl.info["u"], pl.info["v"]]}
-            if ref is None:
-                ref = C
-            else:
-                res[key]["equals_int8"] = bool(torch.equal(C, ref))
-            del pl
-            torch.cuda.empty_cache()
-        out[str(b)] = res
-        del dA
+            row["%d,%d" % uv] = 2.0 * size ** 3 / (t["total_ms"] / t["calls"]) / 1e6
+            del pl, C
+        sq[str(b)] = row
+    out["square"]["gops"] = sq
+    m, n, k = UNBALANCED
+    ub = {}
+    for b in range(20, 53):
+        p, dA, dB = _unbalanced_operands(dev, b)
+        row = {}
+        for uv in variants:
+            try:
+                pl = mwmm.Plan(m, n, k, p, uv[0], uv[1], form="fp64")
+            except mwmm.MwmmError:
+                continue
+            ms, C = _time_reuse_a(pl, dA, dB, 1)
+            row["%d,%d" % uv] = 2.0 * m * n * k / ms / 1e6
+            del pl, C
+        ub[str(b)] = row
+        del dA, dB
+    out["unbalanced_concat"]["gops"] = ub
+
+    def ranges(tab):
+        best = {b: max(r, key=r.get) for b, r in tab.items() if r}
+        res = {}
+        for b in sorted(best, key=int):
+            res.setdefault(best[b], []).append(int(b))
+        return {v: [min(bs), max(bs)] for v, bs in res.items()}
+    out["square"]["best_ranges"] = ranges(sq)
+    out["unbalanced_concat"]["best_ranges"] = ranges(ub)
     return out
 
 
@@ -608,6 +700,7 @@ def main():
     batched = run_batched(dev) if (rank == 0 and not args.no_batched) else None
     shapes = run_shapes(dev) if (rank == 0 and not args.no_shapes) else None
     unbalanced = run_unbalanced(dev) if (rank == 0 and not args.no_unbalanced) else None
+    sweep = run_variant_sweep(dev) if (rank == 0 and args.variant_sweep) else None
     serve = run_serve(dev, args.serve_requests, args.serve_pool) if (rank == 0 and not args.no_serve) else None
 
     if rank == 0:
@@ -621,6 +714,7 @@ def main():
                 "roofline": roofline, "cpu_baseline": cpu_baseline, "e2e": e2e,
                 "gpu_launches": launches * world, "clocks": clocks, "per_bitsize": per_bits,
                 "batched_multi_prime": batched, "shapes_50bit": shapes, "unbalanced_block_wiedemann": unbalanced,
+                "variant_sweep": sweep,
                 "serve": serve}
         print(json.dumps(line))
     if dist:

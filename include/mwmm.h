@@ -96,7 +96,13 @@ typedef struct {
                          two CTAs sharing each B tile through TMA multicast
                          (bit-exact, measured 2-3% slower on B300);
                          0 or 1 = lone CTAs (default) */
-    int32_t reserved[6];
+    int32_t f64_concat; /* FP64 form: 0 = concatenate B's words along n (Alg. 6)
+                         when 2 <= v <= 4 and n < 64, 1 = never, 2 = always
+                         (needs 2 <= v <= 4) */
+    int32_t ksplit;     /* FP64 form: K ranges computed by separate CTAs and
+                         added mod p afterwards, 1..64 (0: chosen so that the
+                         last wave of CTAs is nearly full) */
+    int32_t reserved[4];
 } mwmm_plan_opts;
 
 /* What a plan decided (mwmm_plan_info). */
@@ -124,16 +130,22 @@ typedef struct {
      *   chunk(word w, k-block kb, row r) at
      *     B_off + ((kb * (v + 2 B_wpad) + w + B_wpad) * B_rows + r) * 128
      * (words -B_wpad .. -1 and v .. v + B_wpad - 1 are all zero).
+     * FP64 form with f64_concat = 1, for B: k-block major without padding,
+     *   chunk(word w, k-block kb, row r) at B_off + ((kb * v + w) * B_rows + r) * 128.
      * Inside a chunk the 16-byte granule g (elements g*E .. g*E+E-1 of the
      * k-block, E = 16 / element size) is stored at granule position
      * g ^ (r mod 8).  Element type: double (FP64 form, kb_elems = 16) or
      * bf16 holding an integer digit (INT8 form, kb_elems = 64).  Padding is 0.
-     * INT8 form only: S (int32) at S_off, laid out [nsums][nkc][A_rows][B_rows]. */
+     * INT8 form: S (int32) at S_off, laid out [nsums][nkc][A_rows][B_rows].
+     * FP64 form with ksplit > 1: the partial results of the K ranges
+     * (uint64 residues) at S_off, laid out [ksplit][m][n]. */
     int64_t kb_elems, nkb, A_rows, B_rows;
     int32_t B_wpad;
     int32_t tc_cluster;     /* INT8: CTAs per cluster of the one-CTA kernel (2: A_rows % 256 == 0) */
     uint64_t A_off, B_off, S_off;
     uint64_t workspace_bytes;
+    int32_t f64_concat;     /* FP64: 1 when B's words are concatenated along n (Alg. 6) */
+    int32_t ksplit;         /* FP64: K ranges (1: none) */
 } mwmm_plan_desc;
 
 /* Plan a product of an m x k by a k x n matrix mod p.

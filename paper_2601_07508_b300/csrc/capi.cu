@@ -106,10 +106,11 @@ mwmm_status run_product(mwmm_plan_s *h, const uint64_t *dA, int64_t lda, const u
     if (e) return cuda_status(e);
     rec(pe.ev[2], s);
     if (pl.form == MWMM_FORM_FP64) {
-        e = mwmm::launch_gemm_fp64(pl, ws + pl.A_off, ws + pl.B_off, dC, ldc, pl.err_dev, stream);
+        e = mwmm::launch_gemm_fp64(pl, ws + pl.A_off, ws + pl.B_off, dC, ldc,
+                                   reinterpret_cast<uint64_t *>(ws + pl.S_off), pl.err_dev, stream);
         rec(pe.ev[3], s);
         rec(pe.ev[4], s);
-        if (h->timing) h->pending_launches += dA ? 3 : 2;
+        if (h->timing) h->pending_launches += (dA ? 3 : 2) + (pl.ksplit > 1 ? 1 : 0);
         return cuda_status(e);
     }
     int32_t *S = reinterpret_cast<int32_t *>(ws + pl.S_off);
@@ -169,6 +170,7 @@ mwmm_status mwmm_plan_info(mwmm_plan_t plan, mwmm_plan_desc *d) {
     d->alpha = P.alpha; d->beta = P.beta;
     d->lambda = P.lambda; d->lambda_max = P.lambda_max;
     d->tc_chunk = P.tc_chunk; d->kc = P.kc; d->nkc = P.nkc; d->nsums = P.nsums; d->tc_pair = P.tc_pair; d->tc_cluster = P.tc_cluster;
+    d->f64_concat = P.f64_concat; d->ksplit = P.ksplit;
     d->q = P.q;
     d->kb_elems = P.kb_elems; d->nkb = P.nkb; d->A_rows = P.A_rows; d->B_rows = P.B_rows;
     d->B_wpad = P.B_wpad;

@@ -52,6 +52,11 @@ struct Plan {
     double gamma[kMaxWords * kMaxWords] = {};
     double gamma26[kMaxWords * kMaxWords] = {};  // gamma * 2^26 mod p
     int big_p = 0;                               // p > 2^52 / 3: split Alg. 2
+    int f64_concat = 0;  // 1: B words concatenated along n (Alg. 6)
+    int f64_vs = 1;      // word slots per 64-column tile (2 or 4 when concatenated)
+    int f64_w = 64;      // output columns per tile (64 / f64_vs)
+    int ksplit = 1;      // K ranges of the FP64 kernel (partial results summed mod p)
+    int64_t kbr = 0;     // k-blocks per K range
     // INT8 form
     int64_t tc_chunk = 0, kc = 0;
     int tc_pair = 0;  // 1: 2-CTA kernel, A rows padded to 256
@@ -88,7 +93,8 @@ uint64_t mulmod_u64(uint64_t a, uint64_t b, uint64_t p);
 
 // launches (return cudaError_t as int)
 int launch_split(const Plan &pl, int side, const uint64_t *M, int64_t ld, void *words, void *stream);
-int launch_gemm_fp64(const Plan &pl, const void *Aw, const void *Bw, uint64_t *C, int64_t ldc,
+// part: ksplit x m x n partial results (workspace at S_off) when pl.ksplit > 1
+int launch_gemm_fp64(const Plan &pl, const void *Aw, const void *Bw, uint64_t *C, int64_t ldc, uint64_t *part,
                      int *err, void *stream);
 int launch_gemm_tc(const Plan &pl, const void *Aw, const void *Bw, int32_t *S, int *err, void *stream);
 int launch_recombine(const Plan &pl, const int32_t *S, uint64_t *C, int64_t ldc, void *stream);

@@ -2,6 +2,7 @@
 //
 // Pure host logic (no CUDA calls), so plans can be made and inspected on a
 // machine without a GPU.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 
@@ -132,15 +133,52 @@ mwmm_status make_plan(Plan *pl, int64_t m, int64_t n, int64_t k, uint64_t p, int
         P.kb_elems = kF64KB;
         P.nkb = ceil_div(k, kF64KB);
         P.A_rows = round_up(m > 0 ? m : 1, kF64BM);
-        P.B_rows = round_up(n > 0 ? n : 1, kF64BN);
+        // Alg. 6: concatenate B's words along n when n is narrow (a 64-column
+        // tile then holds v word slots of 64 / f64_vs columns instead of one
+        // mostly empty word); at most 4 slots.
+        if (o.f64_concat < 0 || o.f64_concat > 2) return MWMM_ERR_ARG;
+        bool concat = o.f64_concat == 2 || (o.f64_concat == 0 && v >= 2 && n < kF64BN);
+        if (concat && (v > 4 || v < 2)) {
+            if (o.f64_concat == 2) return MWMM_ERR_ARG;
+            concat = false;
+        }
+        P.f64_concat = concat ? 1 : 0;
+        P.f64_vs = concat ? (v <= 2 ? 2 : 4) : 1;
+        P.f64_w = kF64BN / P.f64_vs;
+        P.B_rows = round_up(n > 0 ? n : 1, P.f64_w);
+        if (concat) {  // k-block major: the word slots of one k-block are adjacent
+            P.B_wstride = P.B_rows;
+            P.B_kstride = (int64_t)v * P.B_rows;
+        } else {
+            P.B_wstride = P.nkb * P.B_rows;
+            P.B_kstride = P.B_rows;
+        }
+        // K ranges: enough CTAs that the last wave is nearly full.  The
+        // planner is device independent and assumes 148 SMs x 2 resident CTAs.
+        const int64_t tiles = (P.A_rows / kF64BM) * (P.B_rows / P.f64_w);
+        const int64_t smax = std::max<int64_t>(1, std::min<int64_t>(64, P.nkb / 8));
+        int64_t ks = 1;
+        if (o.ksplit != 0) {
+            if (o.ksplit < 1 || o.ksplit > 64) return MWMM_ERR_ARG;
+            ks = std::min<int64_t>(o.ksplit, std::max<int64_t>(P.nkb, 1));
+        } else {
+            const int64_t cap = 2 * 148;
+            double best = -1.0;
+            for (int64_t s = 1; s <= smax; ++s) {
+                const int64_t ctas = tiles * s;
+                const double eff = (double)ctas / (double)(ceil_div(ctas, cap) * cap);
+                if (eff > best + 1e-9) { best = eff; ks = s; }
+                if (eff >= 0.9) break;  // smallest split that fills 90% of the last wave
+            }
+        }
+        P.kbr = ceil_div(std::max<int64_t>(P.nkb, 1), ks);
+        P.ksplit = (int)ceil_div(std::max<int64_t>(P.nkb, 1), P.kbr);  // no empty range
         uint64_t abytes = (uint64_t)u * P.nkb * P.A_rows * kTileBytes;
         uint64_t bbytes = (uint64_t)v * P.nkb * P.B_rows * kTileBytes;
-        P.B_wstride = P.nkb * P.B_rows;
-        P.B_kstride = P.B_rows;
         P.A_off = 0;
         P.B_off = align256(abytes);
         P.S_off = align256(P.B_off + bbytes);
-        P.ws_bytes = P.S_off;
+        P.ws_bytes = P.ksplit > 1 ? align256(P.S_off + (uint64_t)P.ksplit * m * n * 8) : P.S_off;
     } else {
         const int need = int8_digits(p);
         if (u == 0) { u = need; v = need; }

@@ -338,7 +338,10 @@ mwmm_status mwmm_serve_submit(mwmm_server_t S, const mwmm_problem *prob, double 
     *ticket = 0;
     std::unique_ptr<Request> r(new (std::nothrow) Request());
     if (!r) return MWMM_ERR_NOMEM;
-    mwmm_status st = mwmm::make_plan(&r->plan, prob->m, prob->n, prob->k, prob->p, 0, 0, S->form, nullptr);
+    mwmm_plan_opts o;
+    std::memset(&o, 0, sizeof(o));
+    o.ksplit = 1;  // requests run as batched tiles over the whole K range
+    mwmm_status st = mwmm::make_plan(&r->plan, prob->m, prob->n, prob->k, prob->p, 0, 0, S->form, &o);
     if (st != MWMM_OK) return st;
     const Plan &pl = r->plan;
     if (pl.m > 0 && pl.n > 0 &&

@@ -39,7 +39,7 @@ class MwmmError(RuntimeError):
 class PlanOpts(ctypes.Structure):
     _fields_ = [("lambda_", ctypes.c_int64), ("validate", ctypes.c_int32), ("tc_chunk", ctypes.c_int32),
                 ("kc", ctypes.c_int64), ("tc_pair", ctypes.c_int32), ("tc_cluster", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 6)]
+                ("f64_concat", ctypes.c_int32), ("ksplit", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
 
 
 class Timing(ctypes.Structure):
@@ -58,7 +58,8 @@ class PlanDesc(ctypes.Structure):
                 ("kb_elems", ctypes.c_int64), ("nkb", ctypes.c_int64), ("A_rows", ctypes.c_int64),
                 ("B_rows", ctypes.c_int64), ("B_wpad", ctypes.c_int32), ("tc_cluster", ctypes.c_int32),
                 ("A_off", ctypes.c_uint64), ("B_off", ctypes.c_uint64),
-                ("S_off", ctypes.c_uint64), ("workspace_bytes", ctypes.c_uint64)]
+                ("S_off", ctypes.c_uint64), ("workspace_bytes", ctypes.c_uint64),
+                ("f64_concat", ctypes.c_int32), ("ksplit", ctypes.c_int32)]
 
     def as_dict(self):
         d = {}
@@ -204,7 +205,7 @@ def _ld(t) -> int:
 # --------------------------------------------------------------------------- C-named calls
 def mwmm_plan(m: int, n: int, k: int, p: int, u: int = 0, v: int = 0, form="auto", lam: int = 0,
               validate: bool = False, tc_chunk: int = 0, kc: int = 0, tc_pair: bool = False,
-              tc_cluster: int = 0) -> int:
+              tc_cluster: int = 0, f64_concat: int = 0, ksplit: int = 0) -> int:
     if isinstance(form, str):
         form = FORMS[form]
     h = _vp()
@@ -215,6 +216,8 @@ def mwmm_plan(m: int, n: int, k: int, p: int, u: int = 0, v: int = 0, form="auto
     o.kc = kc
     o.tc_pair = 1 if tc_pair else 0
     o.tc_cluster = tc_cluster
+    o.f64_concat = f64_concat
+    o.ksplit = ksplit
     _check(lib().mwmm_plan(ctypes.byref(h), m, n, k, p, u, v, form, ctypes.byref(o)), "mwmm_plan")
     return h.value
 
@@ -507,8 +510,9 @@ class Plan:
 
     def __init__(self, m: int, n: int, k: int, p: int, u: int = 0, v: int = 0, form="auto", lam: int = 0,
                  validate: bool = False, tc_chunk: int = 0, kc: int = 0, tc_pair: bool = False,
-                 tc_cluster: int = 0):
-        self.handle = mwmm_plan(m, n, k, p, u, v, form, lam, validate, tc_chunk, kc, tc_pair, tc_cluster)
+                 tc_cluster: int = 0, f64_concat: int = 0, ksplit: int = 0):
+        self.handle = mwmm_plan(m, n, k, p, u, v, form, lam, validate, tc_chunk, kc, tc_pair, tc_cluster,
+                                f64_concat, ksplit)
         self.info = mwmm_plan_info(self.handle)
         self.workspace = None
 

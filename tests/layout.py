@@ -2,11 +2,12 @@
 import numpy as np
 
 
-def unpack_words(buf: np.ndarray, words: int, nkb: int, rows_pad: int, kind: str, wpad: int = 0) -> np.ndarray:
+def unpack_words(buf: np.ndarray, words: int, nkb: int, rows_pad: int, kind: str, wpad: int = 0,
+                 kmajor: bool = False) -> np.ndarray:
     """buf: uint8 bytes of one side's word region.  Returns [words][rows_pad][nkb*kb_elems]
-    as float64 (FP64 words) or int32 (INT8 digits stored as bf16).  wpad > 0:
-    the k-block-major layout with wpad zero words on each side (checked zero)."""
-    if wpad:
+    as float64 (FP64 words) or int32 (INT8 digits stored as bf16).  wpad > 0 or
+    kmajor: the k-block-major layout with wpad zero words on each side (checked zero)."""
+    if wpad or kmajor:
         wp = words + 2 * wpad
         a = np.asarray(buf[:nkb * wp * rows_pad * 128]).reshape(nkb, wp, rows_pad, 8, 16)
         assert not a[:, :wpad].any() and not a[:, wpad + words:].any(), "padding words must be zero"

@@ -147,3 +147,45 @@ def test_int8_plan_cluster_option_range(M):
     d = M.mwmm_plan_info(h)
     M.mwmm_plan_destroy(h)
     assert d["tc_pair"] == 1 and d["tc_cluster"] == 1
+
+
+@pytest.mark.parametrize("n,v,opt,want,slots", [
+    (32, 2, 0, 1, 2), (20, 3, 0, 1, 4), (63, 4, 0, 1, 4), (64, 2, 0, 0, 1),   # auto: narrow n, 2 <= v <= 4
+    (32, 1, 0, 0, 1), (32, 2, 1, 0, 1), (200, 2, 2, 1, 2),
+])
+def test_fp64_plan_concatenation(M, n, v, opt, want, slots):
+    p = {1: SWEEP[20], 2: SWEEP[32], 3: SWEEP[32], 4: SWEEP[40]}[v]  # bitsizes each (1, v) handles
+    h = M.mwmm_plan(1000, n, 4096, p, 1, v, "fp64", f64_concat=opt)
+    d = M.mwmm_plan_info(h)
+    M.mwmm_plan_destroy(h)
+    assert d["f64_concat"] == want
+    w = 64 // slots
+    assert d["B_rows"] == -(-n // w) * w
+    assert d["workspace_bytes"] >= d["B_off"] + v * d["nkb"] * d["B_rows"] * 128
+
+
+def test_fp64_plan_concatenation_errors(M):
+    for v, p in ((1, SWEEP[20]), (5, SWEEP[20])):
+        with pytest.raises(M.MwmmError) as e:
+            M.mwmm_plan(100, 20, 100, p, 1, v, "fp64", f64_concat=2)
+        assert e.value.status == 1
+    with pytest.raises(M.MwmmError) as e:
+        M.mwmm_plan(100, 20, 100, SWEEP[32], 1, 2, "fp64", f64_concat=3)
+    assert e.value.status == 1
+
+
+@pytest.mark.parametrize("m,n,k,want", [
+    (4096, 4096, 4096, 1),     # 4096 tiles: the last wave is already 99% full
+    (10923, 32, 32768, 5),     # 171 tiles (concatenated (1,2)): 5 ranges fill 96% of 3 waves
+    (8192, 64, 8192, 9),       # 128 tiles: 9 ranges
+    (64, 64, 64, 1),           # 4 k-blocks: ranges of at least 8 k-blocks
+])
+def test_fp64_plan_k_ranges(M, m, n, k, want):
+    h = M.mwmm_plan(m, n, k, SWEEP[32], 1, 2, "fp64")
+    d = M.mwmm_plan_info(h)
+    M.mwmm_plan_destroy(h)
+    assert d["ksplit"] == want
+    if want > 1:
+        assert d["workspace_bytes"] >= d["S_off"] + want * m * n * 8
+    with pytest.raises(M.MwmmError):
+        M.mwmm_plan(m, n, k, SWEEP[32], 1, 2, "fp64", ksplit=65)

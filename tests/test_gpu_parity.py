@@ -70,6 +70,46 @@ def test_fp64_variants_ragged(M, oracle, b, uv):
         assert np.array_equal(C, oracle.matmul_mod(A, B, p)), (m, n, k)
 
 
+@pytest.mark.parametrize("uv", [(1, 2), (1, 3), (1, 4), (2, 2), (2, 3)])
+@pytest.mark.parametrize("b", [23, 32, 40, 52])
+def test_fp64_concatenated_words_narrow_n(M, oracle, uv, b):
+    """Alg. 6: B's words concatenated along n (64-column tiles of 2 or 4 word
+    slots), for n across the slot widths 16 and 32 and beyond one tile, with
+    and without K ranges; equals the non-concatenated product and the oracle."""
+    p = SWEEP[b]
+    if oracle.lam(p, *uv) < 1:
+        pytest.skip("variant cannot handle this bitsize")
+    for seed, (m, n, k) in enumerate([(70, 1, 50), (130, 15, 333), (65, 16, 100), (200, 17, 257),
+                                      (129, 32, 500), (100, 33, 64), (64, 63, 1000)]):
+        A, B = inputs.problem(300 * b + seed, m, n, k, p)
+        ref = oracle.matmul_mod(A, B, p)
+        C, plan = gpu_product(M, A, B, p, form="fp64", u=uv[0], v=uv[1])
+        assert plan.info["f64_concat"] == 1 and plan.info["B_rows"] % (32 if uv[1] == 2 else 16) == 0
+        assert np.array_equal(C, ref), (m, n, k)
+        C1, plan1 = gpu_product(M, A, B, p, form="fp64", u=uv[0], v=uv[1], f64_concat=1, ksplit=3)
+        nkb = -(-k // 16)
+        assert plan1.info["f64_concat"] == 0 and plan1.info["ksplit"] == -(-nkb // -(-nkb // min(3, nkb)))
+        assert np.array_equal(C1, ref), (m, n, k)
+        C2, plan2 = gpu_product(M, A, B, p, form="fp64", u=uv[0], v=uv[1], ksplit=5)
+        assert plan2.info["f64_concat"] == 1
+        assert np.array_equal(C2, ref), (m, n, k)
+
+
+@pytest.mark.parametrize("ks", [1, 2, 3, 7, 64])
+def test_fp64_k_ranges(M, oracle, ks):
+    """K ranges (grid z) with their partial results added mod p by a second
+    kernel: ragged last range, ranges of one k-block, more ranges than asked
+    when k is short; lambda boundaries inside ranges."""
+    p = SWEEP[48]
+    for seed, (m, n, k, lam) in enumerate([(70, 90, 1000, 0), (129, 65, 33, 0), (64, 64, 16 * 64, 3),
+                                           (300, 130, 777, 31)]):
+        A, B = inputs.problem(500 + seed, m, n, k, p)
+        C, plan = gpu_product(M, A, B, p, form="fp64", u=2, v=2, lam=lam, ksplit=ks)
+        nkb = -(-k // 16)
+        assert plan.info["ksplit"] == -(-nkb // -(-nkb // min(ks, nkb)))
+        assert np.array_equal(C, oracle.matmul_mod(A, B, p)), (m, n, k, ks)
+
+
 @pytest.mark.parametrize("lam", [1, 2, 3, 7, 16, 17])
 def test_fp64_block_size_boundaries(M, oracle, lam):
     """Reductions at every lambda-th k-step (including inside a 16-wide k-block)."""
@@ -183,6 +223,7 @@ def test_validation_reports_entries_out_of_range(M):
 
 # ------------------------------------------------------------------ single steps
 @pytest.mark.parametrize("form,b,uv,n", [("fp64", 40, (2, 2), 90), ("fp64", 52, (2, 3), 90), ("fp64", 32, (1, 4), 90),
+                                         ("fp64", 32, (1, 2), 40), ("fp64", 40, (1, 4), 20), ("fp64", 52, (2, 3), 33),
                                          ("int8", 52, None, 290), ("int8", 23, None, 290), ("int8", 52, None, 90),
                                          ("int8", 40, None, 20)])
 def test_split_words_match_oracle(M, oracle, form, b, uv, n):
@@ -199,7 +240,8 @@ def test_split_words_match_oracle(M, oracle, form, b, uv, n):
         buf = torch.full(((words + 2 * wpad) * d["nkb"] * rows_pad * 128,), 0x5A, dtype=torch.uint8, device="cuda")
         M.mwmm_split(plan.handle, side, dev(Mx), buf)
         torch.cuda.synchronize()
-        W = unpack_words(buf.cpu().numpy(), words, d["nkb"], rows_pad, form, wpad)
+        W = unpack_words(buf.cpu().numpy(), words, d["nkb"], rows_pad, form, wpad,
+                         kmajor=side == 1 and d["f64_concat"] == 1)
         src = Mx if side == 0 else Mx.T.copy()       # rows x k
         if form == "fp64":
             ref = oracle.split_alpha(src, d["alpha"] if side == 0 else d["beta"], words).astype(np.float64)
