@@ -345,6 +345,19 @@ mwmm_status mwmm_fmod(const double *dx, int64_t count, uint64_t p, double *dout,
 mwmm_status mwmm_mulmod(const double *dx, const double *dy, int64_t count, uint64_t p,
                         double *dout, void *stream);
 
+/* Self-test of the bounded device waits (no counterpart in the paper).
+ * Every wait of the product kernels on a shared-memory barrier gives up
+ * after a fixed number of SM cycles (about two seconds), sets the plan's
+ * error flag and lets the kernel return, so a stalled pipeline ends as
+ * MWMM_ERR_TIMEOUT from mwmm_plan_check instead of a hung context.  This call
+ * runs that same wait routine in a one-thread kernel on a barrier phase that
+ * nothing completes, with a limit of `cycles` (1 .. 2^34), synchronises
+ * `stream`, and returns MWMM_ERR_TIMEOUT when the wait gave up (the expected
+ * outcome), MWMM_OK if it did not, MWMM_ERR_ARG for a limit out of range,
+ * MWMM_ERR_NOMEM / MWMM_ERR_CUDA on a runtime failure.  It allocates and
+ * frees a 4-byte flag; the device stays usable afterwards. */
+mwmm_status mwmm_selftest_wait_timeout(int64_t cycles, void *stream);
+
 /* ---- per-phase timing (CUDA events on the call's stream) ----
  * When timing is on, every mwmm_matmul / mwmm_matmul_host call records events
  * around its phases: the split of A, the split of B (Alg. 4 or INT8 digits),

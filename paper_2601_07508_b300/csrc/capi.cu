@@ -129,6 +129,22 @@ extern "C" {
 
 const char *mwmm_version(void) { return "mwmm 0.1 (sm_103a)"; }
 
+mwmm_status mwmm_selftest_wait_timeout(int64_t cycles, void *stream) {
+    if (cycles < 1 || cycles > ((int64_t)1 << 34)) return MWMM_ERR_ARG;  // at most ~9 s
+    int *flag = nullptr;
+    cudaError_t e = cudaMalloc(&flag, sizeof(int));
+    if (e != cudaSuccess) return cuda_status((int)e);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int host = 0;
+    e = cudaMemsetAsync(flag, 0, sizeof(int), s);
+    if (e == cudaSuccess) e = (cudaError_t)mwmm::launch_wait_probe(cycles, flag, stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&host, flag, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(flag);
+    if (e != cudaSuccess) return cuda_status((int)e);
+    return host ? MWMM_ERR_TIMEOUT : MWMM_OK;
+}
+
 const char *mwmm_status_str(mwmm_status s) {
     switch (s) {
         case MWMM_OK: return "ok";

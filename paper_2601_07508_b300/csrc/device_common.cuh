@@ -44,17 +44,22 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
 }
 
 // Wait for the phase with the given parity to complete.  Returns false, and
-// sets err[0], if it has not completed within kWaitCycles.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *err) {
+// sets err[0], if it has not completed within `limit` SM clock cycles.
+__device__ __forceinline__ bool mbar_wait_for(uint64_t *bar, uint32_t parity, int *err, long long limit) {
     if (mbar_try_wait(bar, parity)) return true;
     const long long t0 = clock64();
     while (!mbar_try_wait(bar, parity)) {
-        if (clock64() - t0 > kWaitCycles) {
+        if (clock64() - t0 > limit) {
             atomicExch(err, 1);
             return false;
         }
     }
     return true;
+}
+
+// The product kernels' waits: limit kWaitCycles.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *err) {
+    return mbar_wait_for(bar, parity, err, kWaitCycles);
 }
 
 // One bulk (TMA) copy of `bytes` contiguous bytes global -> shared, completing

@@ -117,6 +117,7 @@ int launch_gemm_tc_table(const TcItem *items, const int64_t *cta_off, int ctas, 
                          void *stream);
 int launch_fmod(const double *x, int64_t count, uint64_t p, double *out, void *stream);
 int launch_mulmod(const double *x, const double *y, int64_t count, uint64_t p, double *out, void *stream);
+int launch_wait_probe(int64_t cycles, int *err, void *stream);
 
 // Host-side tables of a batch of products (batch.cu).
 struct BatchTables {

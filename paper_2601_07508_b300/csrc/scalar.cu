@@ -27,6 +27,17 @@ __global__ void mulmod_kernel(const double *x, const double *y, int64_t count, d
     }
 }
 
+// One thread waits, through the product kernels' bounded-wait routine, on a
+// barrier phase that nothing completes; the wait gives up after `limit`
+// cycles and raises err[0].
+__global__ void wait_probe_kernel(long long limit, int *err) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x != 0) return;
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+    (void)mbar_wait_for(&bar, 0, err, limit);
+}
+
 int grid_for(int64_t count) {
     int64_t b = (count + 255) / 256;
     if (b > 148 * 16) b = 148 * 16;
@@ -39,6 +50,11 @@ int launch_fmod(const double *x, int64_t count, uint64_t p, double *out, void *s
     if (count == 0) return 0;
     const double pd = (double)p;
     fmod_kernel<<<grid_for(count), 256, 0, static_cast<cudaStream_t>(stream)>>>(x, count, pd, 1.0 / pd, out);
+    return (int)cudaGetLastError();
+}
+
+int launch_wait_probe(int64_t cycles, int *err, void *stream) {
+    wait_probe_kernel<<<1, 32, 0, static_cast<cudaStream_t>(stream)>>>((long long)cycles, err);
     return (int)cudaGetLastError();
 }
 

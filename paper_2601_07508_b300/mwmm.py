@@ -121,6 +121,7 @@ def lib() -> ctypes.CDLL:
     L.mwmm_plan_destroy.restype = None
     L.mwmm_split.argtypes = [_vp, ctypes.c_int, _vp, _i64, _vp, _vp]
     L.mwmm_fmod.argtypes = [_vp, _i64, _u64, _vp, _vp]
+    L.mwmm_selftest_wait_timeout.argtypes = [_i64, _vp]
     L.mwmm_mulmod.argtypes = [_vp, _vp, _i64, _u64, _vp, _vp]
     L.mwmm_matmul_noalloc.argtypes = [_i64, _i64, _i64, _u64, _vp, _i64, _vp, _i64, _vp, _i64, _vp]
     L.mwmm_batch_create.argtypes = [ctypes.POINTER(_vp), ctypes.POINTER(Problem), ctypes.c_int, ctypes.c_int,
@@ -300,6 +301,12 @@ def mwmm_mulmod(x, y, p: int, out, stream=None):
     f = (torch.float64,)
     _check(lib().mwmm_mulmod(_dev_ptr(x, f), _dev_ptr(y, f), x.numel(), p, _dev_ptr(out, f), _stream_ptr(stream)),
            "mwmm_mulmod")
+
+
+def mwmm_selftest_wait_timeout(cycles: int, stream=None) -> int:
+    """Run the bounded-wait routine on a barrier nothing completes; returns the
+    status code (MWMM_ERR_TIMEOUT = 8 is the expected outcome)."""
+    return int(lib().mwmm_selftest_wait_timeout(cycles, _stream_ptr(stream)))
 
 
 def mwmm_plan_set_timing(h: int, on: bool = True):

@@ -189,3 +189,9 @@ def test_fp64_plan_k_ranges(M, m, n, k, want):
         assert d["workspace_bytes"] >= d["S_off"] + want * m * n * 8
     with pytest.raises(M.MwmmError):
         M.mwmm_plan(m, n, k, SWEEP[32], 1, 2, "fp64", ksplit=65)
+
+
+def test_selftest_wait_rejects_limits_out_of_range(M):
+    """Argument checks happen before any device call (runs without a GPU)."""
+    for cycles in (0, -5, (1 << 34) + 1):
+        assert M.mwmm_selftest_wait_timeout(cycles, stream=0) == 1  # 0: the legacy default stream
