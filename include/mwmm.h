@@ -185,12 +185,29 @@ mwmm_status mwmm_matmul_reuse_a(mwmm_plan_t plan, const uint64_t *dB, int64_t ld
                                 void *workspace, size_t workspace_bytes, void *stream);
 
 /* Same product with HOST matrices: copies A and B to plan-owned device
- * buffers, computes, copies C back and synchronises `stream`.  For the
- * copies to overlap nothing else, pass page-locked host memory.
- * Device-side errors are checked before returning. */
+ * buffers, computes, copies C back and synchronises `stream`.  Device-side
+ * errors are checked before returning.  When m >= 1024 (and per-phase timing
+ * is off) the rows are processed in 2..8 blocks of at least 512 rows on
+ * three plan-owned streams, so that copying the next block of A in and the
+ * previous block of C out overlaps the current block's split, products and
+ * recombination (the copies overlap only with page-locked host memory); the
+ * plan then also owns a workspace for one block.  The work starts after
+ * everything enqueued earlier on `stream`. */
 mwmm_status mwmm_matmul_host(mwmm_plan_t plan, const uint64_t *hA, int64_t lda,
                              const uint64_t *hB, int64_t ldb, uint64_t *hC, int64_t ldc,
                              void *stream);
+
+/* mwmm_matmul_host without the final synchronisation and error check: the
+ * work is enqueued (ordered after earlier work on `stream`; `stream` is
+ * ordered after its end) and the call returns.  hC is complete once `stream`
+ * has been synchronised; mwmm_plan_check reports device-side errors.  Host
+ * buffers must stay valid until then and must be page-locked for the copies
+ * to be asynchronous.  Calls on different plans with different streams
+ * overlap (copies of one product with the products of another); calls on one
+ * plan must be ordered (the same stream, or synchronised between). */
+mwmm_status mwmm_matmul_host_async(mwmm_plan_t plan, const uint64_t *hA, int64_t lda,
+                                   const uint64_t *hB, int64_t ldb, uint64_t *hC, int64_t ldc,
+                                   void *stream);
 
 /* Synchronise `stream` and report device-side errors raised by this plan's
  * earlier calls (MWMM_ERR_RANGE, MWMM_ERR_TIMEOUT); clears them. */

@@ -1,7 +1,9 @@
 // C ABI of libmwmm (declared in include/mwmm.h).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstring>
+#include <memory>
 #include <new>
 #include <vector>
 
@@ -9,8 +11,29 @@
 
 using mwmm::Plan;
 
+// Row-block pipeline of mwmm_matmul_host: rows of C depend only on the same
+// rows of A, so the product runs as R row blocks (sub-plans sharing B's
+// words) while copies stream on their own engines.
+struct HostPipe {
+    int R = 0;        // row blocks
+    int64_t mb = 0;   // rows per block (the last one may be shorter)
+    Plan sub, tail;   // plans of an mb-row block and of the last block
+    cudaStream_t s_in = nullptr, s_comp = nullptr, s_out = nullptr;
+    std::vector<cudaEvent_t> ev;  // start, B in, end, then A-in / C-ready per block
+    void *ws = nullptr;
+    uint64_t A_off = 0, B_off = 0, S_off = 0, ws_bytes = 0;
+    ~HostPipe() {
+        for (cudaEvent_t e : ev) cudaEventDestroy(e);
+        if (s_in) cudaStreamDestroy(s_in);
+        if (s_comp) cudaStreamDestroy(s_comp);
+        if (s_out) cudaStreamDestroy(s_out);
+        if (ws) cudaFree(ws);
+    }
+};
+
 struct mwmm_plan_s {
     Plan pl;
+    HostPipe *pipe = nullptr;  // created by the first pipelined mwmm_matmul_host
     // per-phase timing: one set of 5 events per timed call
     bool timing = false;
     std::vector<cudaEvent_t> pool;     // free events
@@ -121,6 +144,126 @@ mwmm_status run_product(mwmm_plan_s *h, const uint64_t *dA, int64_t lda, const u
     rec(pe.ev[4], s);
     if (h->timing) h->pending_launches += dA ? 4 : 3;
     return cuda_status(e);
+}
+
+uint64_t align256u(uint64_t x) { return (x + 255) & ~uint64_t(255); }
+
+// Rows per block: at least 512 (several waves of the word-product kernels
+// per block), at most 8 blocks; R = 1 means no pipeline.
+void choose_blocks(const Plan &pl, int *R, int64_t *mb) {
+    const int64_t quantum = pl.form == MWMM_FORM_FP64 ? 64 : 256;
+    int r = (int)std::min<int64_t>(8, pl.m / 512);
+    if (r < 2 || pl.k == 0) {
+        *R = 1;
+        *mb = pl.m;
+        return;
+    }
+    int64_t b = (pl.m + r - 1) / r;
+    b = (b + quantum - 1) / quantum * quantum;
+    *R = (int)((pl.m + b - 1) / b);
+    *mb = b;
+}
+
+mwmm_status make_sub_plan(const Plan &pl, int64_t rows, Plan *out) {
+    mwmm_plan_opts o;
+    std::memset(&o, 0, sizeof(o));
+    o.validate = pl.validate;
+    if (pl.form == MWMM_FORM_FP64) {
+        o.lambda = pl.lambda;
+        o.f64_concat = pl.f64_concat ? 2 : 1;
+    } else {
+        o.tc_chunk = (int32_t)pl.tc_chunk;
+        o.kc = pl.kc;
+        o.tc_cluster = pl.tc_cluster == 2 ? 2 : 1;
+    }
+    mwmm_status st = mwmm::make_plan(out, rows, pl.n, pl.k, pl.p, pl.u, pl.v, pl.form, &o);
+    if (st != MWMM_OK) return st;
+    out->err_dev = pl.err_dev;  // shared flags (owned by the full plan)
+    out->device = pl.device;
+    return MWMM_OK;
+}
+
+mwmm_status ensure_pipe(mwmm_plan_s *h) {
+    if (h->pipe) return MWMM_OK;
+    Plan &pl = h->pl;
+    std::unique_ptr<HostPipe> hp(new (std::nothrow) HostPipe());
+    if (!hp) return MWMM_ERR_NOMEM;
+    choose_blocks(pl, &hp->R, &hp->mb);
+    mwmm_status st = make_sub_plan(pl, hp->mb, &hp->sub);
+    if (st == MWMM_OK) st = make_sub_plan(pl, pl.m - (int64_t)(hp->R - 1) * hp->mb, &hp->tail);
+    if (st != MWMM_OK) return st;
+    // one workspace for every block: A words (mb rows), B words, then the
+    // larger of the two plans' sums / partial results
+    const Plan &a = hp->sub, &t = hp->tail;
+    const uint64_t sreg = std::max(a.ws_bytes - a.S_off, t.ws_bytes > t.S_off ? t.ws_bytes - t.S_off : 0);
+    hp->A_off = 0;
+    hp->B_off = align256u(a.B_off);
+    hp->S_off = align256u(hp->B_off + (a.S_off - a.B_off));
+    hp->ws_bytes = align256u(hp->S_off + sreg);
+    cudaError_t e = cudaMalloc(&hp->ws, hp->ws_bytes);
+    if (e != cudaSuccess) return cuda_status((int)e);
+    for (cudaStream_t *sp : {&hp->s_in, &hp->s_comp, &hp->s_out})
+        if (cudaStreamCreateWithFlags(sp, cudaStreamNonBlocking) != cudaSuccess) return MWMM_ERR_CUDA;
+    hp->ev.resize(3 + 2 * (size_t)hp->R, nullptr);
+    for (cudaEvent_t &ev : hp->ev)
+        if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) return MWMM_ERR_CUDA;
+    h->pipe = hp.release();
+    return MWMM_OK;
+}
+
+// One row block: split its A rows, multiply by B's words, recombine into C.
+int run_rows(const Plan &sub, const uint64_t *dA, int64_t lda, uint8_t *ws, const HostPipe &hp, uint64_t *dC,
+             int64_t ldc, cudaStream_t s) {
+    uint8_t *Aw = ws + hp.A_off, *Bw = ws + hp.B_off, *Sr = ws + hp.S_off;
+    int e = mwmm::launch_split(sub, 0, dA, lda, Aw, s);
+    if (e) return e;
+    if (sub.form == MWMM_FORM_FP64)
+        return mwmm::launch_gemm_fp64(sub, Aw, Bw, dC, ldc, reinterpret_cast<uint64_t *>(Sr), sub.err_dev, s);
+    e = mwmm::launch_gemm_tc(sub, Aw, Bw, reinterpret_cast<int32_t *>(Sr), sub.err_dev, s);
+    if (e) return e;
+    return mwmm::launch_recombine(sub, reinterpret_cast<int32_t *>(Sr), dC, ldc, s);
+}
+
+// Pipelined host product: B in, then per row block A_r in (copy stream) ->
+// split, products, recombination (compute stream) -> C_r out (copy stream).
+mwmm_status host_pipelined(mwmm_plan_s *h, const uint64_t *hA, int64_t lda, const uint64_t *hB, int64_t ldb,
+                           uint64_t *hC, int64_t ldc, uint64_t *dA, uint64_t *dB, uint64_t *dC, cudaStream_t s) {
+    Plan &pl = h->pl;
+    HostPipe &hp = *h->pipe;
+    cudaEvent_t *ev = hp.ev.data();
+    uint8_t *ws = static_cast<uint8_t *>(hp.ws);
+    cudaError_t e = cudaEventRecord(ev[0], s);  // after the caller's earlier work on `s`
+    for (cudaStream_t q : {hp.s_in, hp.s_comp, hp.s_out})
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(q, ev[0], 0);
+    if (e == cudaSuccess)
+        e = cudaMemcpy2DAsync(dB, (size_t)pl.n * 8, hB, (size_t)ldb * 8, (size_t)pl.n * 8, (size_t)pl.k,
+                              cudaMemcpyHostToDevice, hp.s_in);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[1], hp.s_in);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(hp.s_comp, ev[1], 0);
+    if (e != cudaSuccess) return MWMM_ERR_CUDA;
+    int ke = mwmm::launch_split(hp.sub, 1, dB, pl.n, ws + hp.B_off, hp.s_comp);
+    if (ke) return cuda_status(ke);
+    for (int r = 0; r < hp.R; ++r) {
+        const int64_t r0 = (int64_t)r * hp.mb;
+        const Plan &sub = r + 1 < hp.R ? hp.sub : hp.tail;
+        cudaEvent_t a_in = ev[3 + 2 * r], c_ready = ev[4 + 2 * r];
+        e = cudaMemcpy2DAsync(dA + r0 * pl.k, (size_t)pl.k * 8, hA + r0 * lda, (size_t)lda * 8, (size_t)pl.k * 8,
+                              (size_t)sub.m, cudaMemcpyHostToDevice, hp.s_in);
+        if (e == cudaSuccess) e = cudaEventRecord(a_in, hp.s_in);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(hp.s_comp, a_in, 0);
+        if (e != cudaSuccess) return MWMM_ERR_CUDA;
+        ke = run_rows(sub, dA + r0 * pl.k, pl.k, ws, hp, dC + r0 * pl.n, pl.n, hp.s_comp);
+        if (ke) return cuda_status(ke);
+        e = cudaEventRecord(c_ready, hp.s_comp);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(hp.s_out, c_ready, 0);
+        if (e == cudaSuccess)
+            e = cudaMemcpy2DAsync(hC + r0 * ldc, (size_t)ldc * 8, dC + r0 * pl.n, (size_t)pl.n * 8,
+                                  (size_t)pl.n * 8, (size_t)sub.m, cudaMemcpyDeviceToHost, hp.s_out);
+        if (e != cudaSuccess) return MWMM_ERR_CUDA;
+    }
+    e = cudaEventRecord(ev[2], hp.s_out);  // the last copy out follows every block
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev[2], 0);
+    return e == cudaSuccess ? MWMM_OK : MWMM_ERR_CUDA;
 }
 
 }  // namespace
@@ -250,15 +393,13 @@ mwmm_status mwmm_plan_check(mwmm_plan_t plan, void *stream) {
     return MWMM_OK;
 }
 
-mwmm_status mwmm_matmul_host(mwmm_plan_t plan, const uint64_t *hA, int64_t lda, const uint64_t *hB, int64_t ldb,
-                             uint64_t *hC, int64_t ldc, void *stream) {
+mwmm_status mwmm_matmul_host_async(mwmm_plan_t plan, const uint64_t *hA, int64_t lda, const uint64_t *hB,
+                                   int64_t ldb, uint64_t *hC, int64_t ldc, void *stream) {
     if (!plan) return MWMM_ERR_ARG;
     Plan &pl = plan->pl;
     if (pl.m == 0 || pl.n == 0) return MWMM_OK;
     if (!hC || (pl.k > 0 && (!hA || !hB)) || !valid_ld(pl, lda, ldb, ldc)) return MWMM_ERR_ARG;
     mwmm_status st = ensure_device(pl);
-    if (st != MWMM_OK) return st;
-    st = ensure_own_ws(pl);
     if (st != MWMM_OK) return st;
     const uint64_t abytes = (uint64_t)pl.m * pl.k * 8, bbytes = (uint64_t)pl.k * pl.n * 8,
                    cbytes = (uint64_t)pl.m * pl.n * 8;
@@ -279,6 +420,14 @@ mwmm_status mwmm_matmul_host(mwmm_plan_t plan, const uint64_t *hA, int64_t lda, 
     uint64_t *dC = reinterpret_cast<uint64_t *>(base + ((abytes + 255) & ~uint64_t(255)) +
                                                 ((bbytes + 255) & ~uint64_t(255)));
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int R = 1;
+    int64_t mb = pl.m;
+    choose_blocks(pl, &R, &mb);
+    if (R > 1 && !plan->timing) {  // per-phase timing needs the one-stream order
+        st = ensure_pipe(plan);
+        if (st == MWMM_OK) st = host_pipelined(plan, hA, lda, hB, ldb, hC, ldc, dA, dB, dC, s);
+        return st;
+    }
     cudaError_t e = cudaSuccess;
     if (pl.k > 0) {
         e = cudaMemcpy2DAsync(dA, (size_t)pl.k * 8, hA, (size_t)lda * 8, (size_t)pl.k * 8, (size_t)pl.m,
@@ -288,11 +437,20 @@ mwmm_status mwmm_matmul_host(mwmm_plan_t plan, const uint64_t *hA, int64_t lda, 
                                   cudaMemcpyHostToDevice, s);
         if (e != cudaSuccess) return MWMM_ERR_CUDA;
     }
+    st = ensure_own_ws(pl);
+    if (st != MWMM_OK) return st;
     st = run_product(plan, dA, pl.k > 0 ? pl.k : 1, dB, pl.n, dC, pl.n, static_cast<uint8_t *>(pl.own_ws), stream);
     if (st != MWMM_OK) return st;
     e = cudaMemcpy2DAsync(hC, (size_t)ldc * 8, dC, (size_t)pl.n * 8, (size_t)pl.n * 8, (size_t)pl.m,
                           cudaMemcpyDeviceToHost, s);
     if (e != cudaSuccess) return MWMM_ERR_CUDA;
+    return MWMM_OK;
+}
+
+mwmm_status mwmm_matmul_host(mwmm_plan_t plan, const uint64_t *hA, int64_t lda, const uint64_t *hB, int64_t ldb,
+                             uint64_t *hC, int64_t ldc, void *stream) {
+    mwmm_status st = mwmm_matmul_host_async(plan, hA, lda, hB, ldb, hC, ldc, stream);
+    if (st != MWMM_OK || !plan || plan->pl.m == 0 || plan->pl.n == 0) return st;
     return mwmm_plan_check(plan, stream);
 }
 
@@ -330,6 +488,7 @@ void mwmm_plan_destroy(mwmm_plan_t plan) {
     if (!plan) return;
     for (cudaEvent_t e : plan->pool) cudaEventDestroy(e);
     for (cudaEvent_t e : plan->pending) cudaEventDestroy(e);
+    delete plan->pipe;
     Plan &pl = plan->pl;
     if (pl.own_ws) cudaFree(pl.own_ws);
     if (pl.hostbuf_dev) cudaFree(pl.hostbuf_dev);

@@ -115,6 +115,7 @@ def lib() -> ctypes.CDLL:
     L.mwmm_workspace_size.restype = ctypes.c_size_t
     L.mwmm_matmul.argtypes = [_vp, _vp, _i64, _vp, _i64, _vp, _i64, _vp, ctypes.c_size_t, _vp]
     L.mwmm_matmul_host.argtypes = [_vp, _vp, _i64, _vp, _i64, _vp, _i64, _vp]
+    L.mwmm_matmul_host_async.argtypes = [_vp, _vp, _i64, _vp, _i64, _vp, _i64, _vp]
     L.mwmm_matmul_reuse_a.argtypes = [_vp, _vp, _i64, _vp, _i64, _vp, ctypes.c_size_t, _vp]
     L.mwmm_plan_check.argtypes = [_vp, _vp]
     L.mwmm_plan_destroy.argtypes = [_vp]
@@ -264,6 +265,13 @@ def mwmm_matmul_host(h: int, A: np.ndarray, B: np.ndarray, C: np.ndarray, stream
 
 def mwmm_matmul_host_ptr(h: int, a_ptr: int, lda: int, b_ptr: int, ldb: int, c_ptr: int, ldc: int, stream=None):
     _check(lib().mwmm_matmul_host(h, a_ptr, lda, b_ptr, ldb, c_ptr, ldc, _stream_ptr(stream)), "mwmm_matmul_host")
+
+
+def mwmm_matmul_host_async_ptr(h: int, a_ptr: int, lda: int, b_ptr: int, ldb: int, c_ptr: int, ldc: int,
+                               stream=None):
+    """Enqueue a host-buffer product (page-locked buffers) without waiting."""
+    _check(lib().mwmm_matmul_host_async(h, a_ptr, lda, b_ptr, ldb, c_ptr, ldc, _stream_ptr(stream)),
+           "mwmm_matmul_host_async")
 
 
 def mwmm_matmul_noalloc(A, B, C, p: int, stream=None) -> int:

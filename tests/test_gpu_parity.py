@@ -209,6 +209,62 @@ def test_host_entry_point(M, oracle, form):
     assert np.array_equal(C, oracle.matmul_mod(A, B, p))
 
 
+@pytest.mark.parametrize("form", ["fp64", "int8"])
+@pytest.mark.parametrize("shape", [(1100, 70, 300), (4100, 33, 200), (2048, 260, 129)])
+def test_host_entry_point_row_block_pipeline(M, oracle, form, shape):
+    """m >= 1024: row blocks on three streams (A in, compute, C out); strided
+    host matrices; equal to the one-stream order (taken when timing is on)."""
+    m, n, k = shape
+    p = SWEEP[52] if form == "int8" else SWEEP[32]
+    A, B = inputs.problem(23 + m, m, n, k, p)
+    ref = oracle.matmul_mod(A, B, p)
+    plan = M.Plan(m, n, k, p, form=form)
+    assert np.array_equal(plan.matmul_host(A, B), ref)
+    # leading dimensions larger than the rows
+    Ap = np.zeros((m, k + 3), np.uint64)
+    Ap[:, :k] = A
+    Bp = np.zeros((k, n + 5), np.uint64)
+    Bp[:, :n] = B
+    Cp = np.full((m, n + 2), 7, np.uint64)
+    M.mwmm_matmul_host_ptr(plan.handle, Ap.ctypes.data, k + 3, Bp.ctypes.data, n + 5, Cp.ctypes.data, n + 2)
+    assert np.array_equal(Cp[:, :n], ref) and np.all(Cp[:, n:] == 7)
+    M.mwmm_plan_set_timing(plan.handle, True)  # one-stream path
+    assert np.array_equal(plan.matmul_host(A, B), ref)
+
+
+def test_host_async_products_on_separate_streams(M, oracle):
+    """Enqueued host-buffer products of several plans on several streams
+    (page-locked buffers) all complete with the oracle's results."""
+    p = SWEEP[48]
+    shapes = [(1500, 300, 200), (700, 64, 333), (2100, 20, 100)]
+    jobs = []
+    for i, (m, n, k) in enumerate(shapes):
+        A, B = inputs.problem(60 + i, m, n, k, p)
+        hA = torch.from_numpy(A.view(np.int64)).pin_memory()
+        hB = torch.from_numpy(B.view(np.int64)).pin_memory()
+        hC = torch.empty((m, n), dtype=torch.int64).pin_memory()
+        plan = M.Plan(m, n, k, p, form="int8" if i != 1 else "fp64")
+        st = torch.cuda.Stream()
+        M.mwmm_matmul_host_async_ptr(plan.handle, hA.data_ptr(), k, hB.data_ptr(), n, hC.data_ptr(), n, stream=st)
+        jobs.append((plan, st, hC, A, B))
+    for plan, st, hC, A, B in jobs:
+        assert plan.check(st) == 0
+        assert np.array_equal(hC.numpy().view(np.uint64), oracle.matmul_mod(A, B, p))
+
+
+def test_host_pipeline_reports_out_of_range_entries(M, oracle):
+    p = SWEEP[40]
+    m, n, k = 2000, 40, 100
+    A, B = inputs.problem(5, m, n, k, p)
+    A[1500, 7] = p  # in the second row block
+    plan = M.Plan(m, n, k, p, form="int8", validate=True)
+    with pytest.raises(M.MwmmError) as e:
+        plan.matmul_host(A, B)
+    assert e.value.status == 4  # MWMM_ERR_RANGE
+    A[1500, 7] = 0
+    assert np.array_equal(plan.matmul_host(A, B), oracle.matmul_mod(A, B, p))
+
+
 def test_validation_reports_entries_out_of_range(M):
     p = SWEEP[40]
     A, B = inputs.problem(3, 64, 64, 64, p)
