@@ -102,7 +102,10 @@ typedef struct {
     int32_t ksplit;     /* FP64 form: K ranges computed by separate CTAs and
                          added mod p afterwards, 1..64 (0: chosen so that the
                          last wave of CTAs is nearly full) */
-    int32_t reserved[4];
+    int32_t autotune;   /* mwmm_batch_create / mwmm_matmul_batched only:
+                         nonzero picks (u,v) and the K-range per bitsize
+                         group by timing candidates (see mwmm_plan_autotuned) */
+    int32_t reserved[3];
 } mwmm_plan_opts;
 
 /* What a plan decided (mwmm_plan_info). */
@@ -146,6 +149,9 @@ typedef struct {
     uint64_t workspace_bytes;
     int32_t f64_concat;     /* FP64: 1 when B's words are concatenated along n (Alg. 6) */
     int32_t ksplit;         /* FP64: K ranges (1: none) */
+    double tuned_ms;        /* mwmm_plan_autotuned: measured time of the chosen configuration (0: not tuned) */
+    int32_t tuned_tried;    /* candidates timed (0 when the choice came from the cache) */
+    int32_t pad1;
 } mwmm_plan_desc;
 
 /* Plan a product of an m x k by a k x n matrix mod p.
@@ -161,6 +167,33 @@ mwmm_status mwmm_plan(mwmm_plan_t *out, int64_t m, int64_t n, int64_t k, uint64_
                       int u, int v, mwmm_form form, const mwmm_plan_opts *opts);
 
 mwmm_status mwmm_plan_info(mwmm_plan_t plan, mwmm_plan_desc *out);
+
+/* Autotuned plan (no counterpart in the paper's code; the paper picks (u,v)
+ * from its cost model and measured crossovers, Sec. 3.3 and Table 4).
+ * Times candidate configurations of this product on the current device and
+ * returns a plan with the fastest: the form (when form = MWMM_FORM_AUTO;
+ * otherwise the given one), (u,v) among the FP64 variants whose block size
+ * is >= 1 with concatenation on and off where it applies, the tcgen05 tile
+ * variant (one CTA, clusters of two, CTA pairs) and the INT32 K-range.  Each
+ * candidate runs once to warm up and twice timed (CUDA events on `stream`,
+ * synchronised); candidates whose flop model exceeds 3x the best measured
+ * time are skipped.  dA / dB (device, row-major, leading dimensions lda /
+ * ldb) may be NULL: zero operands are used (run times do not depend on the
+ * values).  Allocates scratch for C and one workspace for the call.
+ * Results are cached per (form, bitsize of p, log2 buckets of m, n, k, SM
+ * count); environment variable MWMM_AUTOTUNE_CACHE names a file that is read
+ * at the first lookup and rewritten (one JSON object per line) after each
+ * new entry.  mwmm_plan_info reports tuned_ms and tuned_tried.
+ * Errors: those of mwmm_plan, MWMM_ERR_NOMEM, MWMM_ERR_CUDA. */
+mwmm_status mwmm_plan_autotuned(mwmm_plan_t *out, int64_t m, int64_t n, int64_t k, uint64_t p,
+                                mwmm_form form, const uint64_t *dA, int64_t lda, const uint64_t *dB,
+                                int64_t ldb, void *stream);
+/* The autotuner's cache: entries held in memory, clear, save to / load from
+ * a file (JSON lines; load adds to the entries held). */
+int64_t mwmm_autotune_cache_entries(void);
+void mwmm_autotune_cache_clear(void);
+mwmm_status mwmm_autotune_cache_save(const char *path);
+mwmm_status mwmm_autotune_cache_load(const char *path);
 
 /* Bytes of device workspace one mwmm_matmul call needs (0 for a NULL plan). */
 size_t mwmm_workspace_size(mwmm_plan_t plan);
@@ -246,10 +279,19 @@ typedef struct {
     uint64_t workspace_bytes, table_bytes;
     double flops_2mnk;        /* sum over problems of 2 m n k */
     double word_flops;        /* sum of 2 u v m n k (word-product flops) */
+    int32_t tuned_groups;     /* opts.autotune: bitsize groups whose configuration was timed or cached */
+    int32_t pad0;
+    double tuned_ms;          /* sum over groups of the probe products' measured times */
 } mwmm_batch_desc;
 
 /* Plan and capture a batch (allocates the workspace and tables; makes CUDA
- * calls).  opts applies to every problem (lambda is ignored).  Errors: those of
+ * calls).  opts applies to every problem (lambda is ignored).  With
+ * opts->autotune set, the problems are grouped by the bit length of p and
+ * each group's (u,v), INT32 K-range and concatenation are those
+ * mwmm_plan_autotuned picks for the group's median-size problem among the
+ * configurations the batched kernels run (one-CTA tcgen05 tiles, one FP64 K
+ * range); the choice is timed on zero operands of that size, or taken from
+ * the autotuner's cache.  Errors: those of
  * mwmm_plan for any problem, MWMM_ERR_ARG, MWMM_ERR_NOMEM, MWMM_ERR_CUDA. */
 mwmm_status mwmm_batch_create(mwmm_batch_t *out, const mwmm_problem *probs, int count, mwmm_form form,
                               const mwmm_plan_opts *opts);

@@ -48,6 +48,8 @@ struct mwmm_batch_s {
     cudaGraphExec_t exec = nullptr;
     double flops_2mnk = 0, word_flops = 0;
     int64_t launches = 0;
+    int tuned_groups = 0;
+    double tuned_ms = 0;
     int chunk_blocks = mwmm::kTcMaxChunk / mwmm::kTcKB;
 };
 
@@ -251,6 +253,43 @@ mwmm_status mwmm_batch_create(mwmm_batch_t *out, const mwmm_problem *probs, int 
     if (opts && opts->tc_chunk) b->chunk_blocks = opts->tc_chunk / mwmm::kTcKB;
     b->probs.assign(probs, probs + count);
     b->plans.resize(count);
+    // ---- autotuning: one configuration per bitsize group, timed on the
+    // group's median-size problem (or taken from the autotuner's cache)
+    struct Tuned { bool ok = false; int u = 0, v = 0; mwmm_plan_opts o{}; };
+    std::vector<Tuned> tuned(65);
+    if (opts && opts->autotune) {
+        std::vector<std::vector<int>> groups(65);
+        for (int i = 0; i < count; ++i) {
+            int bits = 0;
+            for (uint64_t x = probs[i].p; x; x >>= 1) ++bits;
+            if (probs[i].m > 0 && probs[i].n > 0 && probs[i].k > 0 && bits <= 64) groups[bits].push_back(i);
+        }
+        cudaStream_t ts = nullptr;
+        if (cudaStreamCreateWithFlags(&ts, cudaStreamNonBlocking) != cudaSuccess) {
+            delete b;
+            return MWMM_ERR_CUDA;
+        }
+        for (int bits = 0; bits <= 64; ++bits) {
+            std::vector<int> &g = groups[bits];
+            if (g.empty()) continue;
+            std::sort(g.begin(), g.end(), [&](int a, int c) {
+                return (double)probs[a].m * probs[a].n * probs[a].k < (double)probs[c].m * probs[c].n * probs[c].k;
+            });
+            const mwmm_problem &q = probs[g[g.size() / 2]];
+            int f = 0, tried = 0;
+            double ms = 0;
+            Tuned t;
+            if (mwmm::autotune((int)form, q.m, q.n, q.k, q.p, nullptr, 0, nullptr, 0, true, ts, &f, &t.u, &t.v, &t.o,
+                               &ms, &tried) == MWMM_OK) {
+                t.ok = true;
+                tuned[bits] = t;
+                b->tuned_groups += 1;
+                b->tuned_ms += ms;
+            }
+        }
+        cudaStreamSynchronize(ts);
+        cudaStreamDestroy(ts);
+    }
     // ---- plans and workspace layout
     std::vector<uint64_t> base(count);
     uint64_t total = 0;
@@ -259,11 +298,27 @@ mwmm_status mwmm_batch_create(mwmm_batch_t *out, const mwmm_problem *probs, int 
         mwmm_plan_opts o;
         std::memset(&o, 0, sizeof(o));
         if (opts) o = *opts;
+        int u = 0, v = 0;
+        int bits = 0;
+        for (uint64_t x = q.p; x; x >>= 1) ++bits;
+        if (bits <= 64 && tuned[bits].ok) {  // the group's configuration; the caller's checks and chunk stay
+            const mwmm_plan_opts user = o;
+            o = tuned[bits].o;
+            o.validate = user.validate;
+            if (user.tc_chunk) o.tc_chunk = user.tc_chunk;
+            u = tuned[bits].u;
+            v = tuned[bits].v;
+        }
         o.lambda = 0;      // per-problem block sizes: always the bound
         o.tc_cluster = 1;  // table items run on lone CTAs (no 256-row padding)
         o.tc_pair = 0;
         o.ksplit = 1;      // batched FP64 tiles run the whole K range
-        mwmm_status st = mwmm::make_plan(&b->plans[i], q.m, q.n, q.k, q.p, 0, 0, (int)form, &o);
+        mwmm_status st = mwmm::make_plan(&b->plans[i], q.m, q.n, q.k, q.p, u, v, (int)form, &o);
+        if (st != MWMM_OK && (u || v)) {  // the group's words do not fit this prime: plan it alone
+            o.kc = 0;
+            o.f64_concat = 0;
+            st = mwmm::make_plan(&b->plans[i], q.m, q.n, q.k, q.p, 0, 0, (int)form, &o);
+        }
         if (st != MWMM_OK) {
             delete b;
             return st;
@@ -391,18 +446,15 @@ mwmm_status mwmm_batch_info(mwmm_batch_t b, mwmm_batch_desc *d) {
     d->table_bytes = b->table_bytes;
     d->flops_2mnk = b->flops_2mnk;
     d->word_flops = b->word_flops;
+    d->tuned_groups = b->tuned_groups;
+    d->tuned_ms = b->tuned_ms;
     return MWMM_OK;
 }
 
 mwmm_status mwmm_batch_problem_info(mwmm_batch_t b, int index, mwmm_plan_desc *d) {
     if (!b || !d || index < 0 || index >= (int)b->plans.size()) return MWMM_ERR_ARG;
-    mwmm_plan_t tmp = nullptr;
-    const Plan &pl = b->plans[index];
-    mwmm_status st = mwmm_plan(&tmp, pl.m, pl.n, pl.k, pl.p, pl.u, pl.v, (mwmm_form)pl.form, nullptr);
-    if (st != MWMM_OK) return st;
-    st = mwmm_plan_info(tmp, d);
-    mwmm_plan_destroy(tmp);
-    return st;
+    mwmm::describe_plan(b->plans[index], d);
+    return MWMM_OK;
 }
 
 void mwmm_batch_destroy(mwmm_batch_t b) {

@@ -322,7 +322,39 @@ mwmm_status mwmm_plan(mwmm_plan_t *out, int64_t m, int64_t n, int64_t k, uint64_
 
 mwmm_status mwmm_plan_info(mwmm_plan_t plan, mwmm_plan_desc *d) {
     if (!plan || !d) return MWMM_ERR_ARG;
-    const Plan &P = plan->pl;
+    mwmm::describe_plan(plan->pl, d);
+    return MWMM_OK;
+}
+
+mwmm_status mwmm_plan_autotuned(mwmm_plan_t *out, int64_t m, int64_t n, int64_t k, uint64_t p, mwmm_form form,
+                                const uint64_t *dA, int64_t lda, const uint64_t *dB, int64_t ldb, void *stream) {
+    if (!out) return MWMM_ERR_ARG;
+    *out = nullptr;
+    if ((dA && lda < std::max<int64_t>(k, 1)) || (dB && ldb < n)) return MWMM_ERR_ARG;
+    // validate p and the shape first (same errors as mwmm_plan)
+    Plan probe;
+    mwmm_status st = mwmm::make_plan(&probe, m, n, k, p, 0, 0, form == MWMM_FORM_FP64 ? MWMM_FORM_FP64 : MWMM_FORM_INT8,
+                                     nullptr);
+    if (st != MWMM_OK && form != MWMM_FORM_AUTO) return st;
+    if (m == 0 || n == 0 || k == 0) return mwmm_plan(out, m, n, k, p, 0, 0, form, nullptr);  // nothing to time
+    int f = 0, u = 0, v = 0, tried = 0;
+    double ms = 0;
+    mwmm_plan_opts o;
+    std::memset(&o, 0, sizeof(o));
+    st = mwmm::autotune((int)form, m, n, k, p, dA, lda, dB, ldb, false, stream, &f, &u, &v, &o, &ms, &tried);
+    if (st != MWMM_OK) return st;
+    st = mwmm_plan(out, m, n, k, p, u, v, (mwmm_form)f, &o);
+    if (st != MWMM_OK) return st;
+    (*out)->pl.tuned_ms = ms;
+    (*out)->pl.tuned_tried = tried;
+    return MWMM_OK;
+}
+
+}  // extern "C"
+
+namespace mwmm {
+
+void describe_plan(const Plan &P, mwmm_plan_desc *d) {
     std::memset(d, 0, sizeof(*d));
     d->m = P.m; d->n = P.n; d->k = P.k; d->p = P.p;
     d->form = P.form; d->u = P.u; d->v = P.v;
@@ -335,8 +367,13 @@ mwmm_status mwmm_plan_info(mwmm_plan_t plan, mwmm_plan_desc *d) {
     d->B_wpad = P.B_wpad;
     d->A_off = P.A_off; d->B_off = P.B_off; d->S_off = P.S_off;
     d->workspace_bytes = P.ws_bytes;
-    return MWMM_OK;
+    d->tuned_ms = P.tuned_ms;
+    d->tuned_tried = P.tuned_tried;
 }
+
+}  // namespace mwmm
+
+extern "C" {
 
 size_t mwmm_workspace_size(mwmm_plan_t plan) { return plan ? (size_t)plan->pl.ws_bytes : 0; }
 

@@ -57,6 +57,9 @@ struct Plan {
     int f64_w = 64;      // output columns per tile (64 / f64_vs)
     int ksplit = 1;      // K ranges of the FP64 kernel (partial results summed mod p)
     int64_t kbr = 0;     // k-blocks per K range
+    // autotuner outcome (0 when the plan was not tuned)
+    double tuned_ms = 0;
+    int tuned_tried = 0;
     // INT8 form
     int64_t tc_chunk = 0, kc = 0;
     int tc_pair = 0;  // 1: 2-CTA kernel, A rows padded to 256
@@ -118,6 +121,14 @@ int launch_gemm_tc_table(const TcItem *items, const int64_t *cta_off, int ctas, 
 int launch_fmod(const double *x, int64_t count, uint64_t p, double *out, void *stream);
 int launch_mulmod(const double *x, const double *y, int64_t count, uint64_t p, double *out, void *stream);
 int launch_wait_probe(int64_t cycles, int *err, void *stream);
+
+// autotune.cpp: the fastest configuration measured on the device (or cached)
+// for this problem; batch = only configurations the batched kernels run.
+mwmm_status autotune(int form_req, int64_t m, int64_t n, int64_t k, uint64_t p, const uint64_t *dA, int64_t lda,
+                     const uint64_t *dB, int64_t ldb, bool batch, void *stream, int *form, int *u, int *v,
+                     mwmm_plan_opts *opts, double *ms, int *tried);
+// capi.cu
+void describe_plan(const Plan &P, mwmm_plan_desc *d);
 
 // Host-side tables of a batch of products (batch.cu).
 struct BatchTables {

@@ -39,7 +39,8 @@ class MwmmError(RuntimeError):
 class PlanOpts(ctypes.Structure):
     _fields_ = [("lambda_", ctypes.c_int64), ("validate", ctypes.c_int32), ("tc_chunk", ctypes.c_int32),
                 ("kc", ctypes.c_int64), ("tc_pair", ctypes.c_int32), ("tc_cluster", ctypes.c_int32),
-                ("f64_concat", ctypes.c_int32), ("ksplit", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
+                ("f64_concat", ctypes.c_int32), ("ksplit", ctypes.c_int32), ("autotune", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 3)]
 
 
 class Timing(ctypes.Structure):
@@ -59,7 +60,8 @@ class PlanDesc(ctypes.Structure):
                 ("B_rows", ctypes.c_int64), ("B_wpad", ctypes.c_int32), ("tc_cluster", ctypes.c_int32),
                 ("A_off", ctypes.c_uint64), ("B_off", ctypes.c_uint64),
                 ("S_off", ctypes.c_uint64), ("workspace_bytes", ctypes.c_uint64),
-                ("f64_concat", ctypes.c_int32), ("ksplit", ctypes.c_int32)]
+                ("f64_concat", ctypes.c_int32), ("ksplit", ctypes.c_int32),
+                ("tuned_ms", ctypes.c_double), ("tuned_tried", ctypes.c_int32), ("pad1", ctypes.c_int32)]
 
     def as_dict(self):
         d = {}
@@ -77,7 +79,8 @@ class Problem(ctypes.Structure):
 class BatchDesc(ctypes.Structure):
     _fields_ = [("count", ctypes.c_int32), ("form", ctypes.c_int32), ("ctas", ctypes.c_int32),
                 ("items", ctypes.c_int64), ("launches", ctypes.c_int64), ("workspace_bytes", ctypes.c_uint64),
-                ("table_bytes", ctypes.c_uint64), ("flops_2mnk", ctypes.c_double), ("word_flops", ctypes.c_double)]
+                ("table_bytes", ctypes.c_uint64), ("flops_2mnk", ctypes.c_double), ("word_flops", ctypes.c_double),
+                ("tuned_groups", ctypes.c_int32), ("pad0", ctypes.c_int32), ("tuned_ms", ctypes.c_double)]
 
 
 class ServeOpts(ctypes.Structure):
@@ -123,6 +126,12 @@ def lib() -> ctypes.CDLL:
     L.mwmm_split.argtypes = [_vp, ctypes.c_int, _vp, _i64, _vp, _vp]
     L.mwmm_fmod.argtypes = [_vp, _i64, _u64, _vp, _vp]
     L.mwmm_selftest_wait_timeout.argtypes = [_i64, _vp]
+    L.mwmm_plan_autotuned.argtypes = [ctypes.POINTER(_vp), _i64, _i64, _i64, _u64, ctypes.c_int, _vp, _i64, _vp,
+                                      _i64, _vp]
+    L.mwmm_autotune_cache_entries.restype = ctypes.c_int64
+    L.mwmm_autotune_cache_clear.restype = None
+    L.mwmm_autotune_cache_save.argtypes = [ctypes.c_char_p]
+    L.mwmm_autotune_cache_load.argtypes = [ctypes.c_char_p]
     L.mwmm_mulmod.argtypes = [_vp, _vp, _i64, _u64, _vp, _vp]
     L.mwmm_matmul_noalloc.argtypes = [_i64, _i64, _i64, _u64, _vp, _i64, _vp, _i64, _vp, _i64, _vp]
     L.mwmm_batch_create.argtypes = [ctypes.POINTER(_vp), ctypes.POINTER(Problem), ctypes.c_int, ctypes.c_int,
@@ -222,6 +231,36 @@ def mwmm_plan(m: int, n: int, k: int, p: int, u: int = 0, v: int = 0, form="auto
     o.ksplit = ksplit
     _check(lib().mwmm_plan(ctypes.byref(h), m, n, k, p, u, v, form, ctypes.byref(o)), "mwmm_plan")
     return h.value
+
+
+def mwmm_plan_autotuned(m: int, n: int, k: int, p: int, form="auto", A=None, B=None, stream=None) -> int:
+    """Plan whose configuration was timed on the device (A, B: optional
+    device tensors of the product; zeros are used when omitted)."""
+    if isinstance(form, str):
+        form = FORMS[form]
+    dt = _u64_dtypes()
+    a = _dev_ptr(A, dt) if A is not None else None
+    b = _dev_ptr(B, dt) if B is not None else None
+    h = _vp()
+    _check(lib().mwmm_plan_autotuned(ctypes.byref(h), m, n, k, p, form, a, _ld(A) if A is not None else 0, b,
+                                     _ld(B) if B is not None else 0, _stream_ptr(stream)), "mwmm_plan_autotuned")
+    return h.value
+
+
+def mwmm_autotune_cache_entries() -> int:
+    return int(lib().mwmm_autotune_cache_entries())
+
+
+def mwmm_autotune_cache_clear():
+    lib().mwmm_autotune_cache_clear()
+
+
+def mwmm_autotune_cache_save(path: str):
+    _check(lib().mwmm_autotune_cache_save(path.encode()), "mwmm_autotune_cache_save")
+
+
+def mwmm_autotune_cache_load(path: str):
+    _check(lib().mwmm_autotune_cache_load(path.encode()), "mwmm_autotune_cache_load")
 
 
 def mwmm_plan_info(h: int) -> dict:
@@ -349,13 +388,14 @@ def _problems(items):
     return arr
 
 
-def mwmm_batch_create(items, form="auto", tc_chunk: int = 0, kc: int = 0) -> int:
+def mwmm_batch_create(items, form="auto", tc_chunk: int = 0, kc: int = 0, autotune: bool = False) -> int:
     if isinstance(form, str):
         form = FORMS[form]
     probs = _problems(items)
     o = PlanOpts()
     o.tc_chunk = tc_chunk
     o.kc = kc
+    o.autotune = 1 if autotune else 0
     h = _vp()
     _check(lib().mwmm_batch_create(ctypes.byref(h), probs, len(items), form, ctypes.byref(o)), "mwmm_batch_create")
     return h.value
@@ -396,9 +436,9 @@ def mwmm_matmul_batched(items, form="auto", stream=None):
 class Batch:
     """Owns a batch handle over device tensors [(A, B, C, p), ...]."""
 
-    def __init__(self, items, form="auto", tc_chunk: int = 0, kc: int = 0):
+    def __init__(self, items, form="auto", tc_chunk: int = 0, kc: int = 0, autotune: bool = False):
         self.items = list(items)  # keep the tensors alive
-        self.handle = mwmm_batch_create(self.items, form, tc_chunk, kc)
+        self.handle = mwmm_batch_create(self.items, form, tc_chunk, kc, autotune)
         self.info = mwmm_batch_info(self.handle)
 
     def run(self, stream=None):
@@ -530,6 +570,15 @@ class Plan:
                                 f64_concat, ksplit)
         self.info = mwmm_plan_info(self.handle)
         self.workspace = None
+
+    @classmethod
+    def autotuned(cls, m: int, n: int, k: int, p: int, form="auto", A=None, B=None, stream=None):
+        """Plan with the configuration the autotuner measured fastest."""
+        self = cls.__new__(cls)
+        self.handle = mwmm_plan_autotuned(m, n, k, p, form, A, B, stream)
+        self.info = mwmm_plan_info(self.handle)
+        self.workspace = None
+        return self
 
     def __del__(self):
         h = getattr(self, "handle", None)

@@ -195,3 +195,36 @@ def test_selftest_wait_rejects_limits_out_of_range(M):
     """Argument checks happen before any device call (runs without a GPU)."""
     for cycles in (0, -5, (1 << 34) + 1):
         assert M.mwmm_selftest_wait_timeout(cycles, stream=0) == 1  # 0: the legacy default stream
+
+
+def test_autotune_cache_file_round_trip(M, tmp_path):
+    """The autotuner's cache is host state: JSON lines load, count, save and
+    clear without a GPU."""
+    M.mwmm_autotune_cache_clear()
+    assert M.mwmm_autotune_cache_entries() == 0
+    src = tmp_path / "cache.jsonl"
+    src.write_text(
+        '{"key": "f2.b52.m12.n12.k12.single.sm148", "form": 2, "u": 7, "v": 7, "tc_chunk": 0, "kc": 0, '
+        '"tc_pair": 0, "tc_cluster": 1, "f64_concat": 0, "ksplit": 0, "ms": 4.250000, "tried": 3}\n'
+        '{"key": "f1.b40.m11.n11.k11.batch.sm148", "form": 1, "u": 2, "v": 2, "tc_chunk": 0, "kc": 0, '
+        '"tc_pair": 0, "tc_cluster": 0, "f64_concat": 1, "ksplit": 1, "ms": 59.400000, "tried": 4}\n'
+        'not a cache line\n')
+    M.mwmm_autotune_cache_load(str(src))
+    assert M.mwmm_autotune_cache_entries() == 2
+    out = tmp_path / "saved.jsonl"
+    M.mwmm_autotune_cache_save(str(out))
+    lines = out.read_text().splitlines()
+    assert len(lines) == 2 and all(l.startswith('{"key": "f') for l in lines)
+    assert '"u": 2, "v": 2' in lines[0] and '"ksplit": 1' in lines[0]  # keys sorted: f1... before f2...
+    M.mwmm_autotune_cache_clear()
+    M.mwmm_autotune_cache_load(str(out))
+    assert M.mwmm_autotune_cache_entries() == 2
+    M.mwmm_autotune_cache_clear()
+    with pytest.raises(M.MwmmError):
+        M.mwmm_autotune_cache_load(str(tmp_path / "missing.jsonl"))
+
+
+def test_autotuned_plan_rejects_bad_arguments_before_any_device_call(M):
+    for args in ((-1, 8, 8, SWEEP[40]), (8, 8, 8, 4), (8, 8, 8, 1 << 52)):
+        with pytest.raises(M.MwmmError):
+            M.mwmm_plan_autotuned(*args, form="fp64", stream=0)
