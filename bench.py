@@ -18,6 +18,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import math
 import os
 import re
 import statistics
@@ -48,6 +49,7 @@ def parse_args():
     ap.add_argument("--bits", default=",".join(str(b) for b in inputs.SWEEP_BITS))
     ap.add_argument("--no-fp64", action="store_true", help="skip the per-bitsize FP64-form timing")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-crt", action="store_true", help="skip the per-bitsize CRT (multimodular) comparison form")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
     ap.add_argument("--no-batched", action="store_true", help="skip the 512-instance multi-prime batch")
@@ -253,11 +255,12 @@ def run_batched(dev, runs=5):
         items.append((torch.from_numpy(A.view(np.int64)).to(dev), torch.from_numpy(B.view(np.int64)).to(dev),
                       torch.empty((m, n), dtype=torch.int64, device=dev), p))
     out = {"workload": "512 instances, 64 largest primes below 2^50 (instance i uses prime i mod 64), m, n, k "
-                       "log-uniform in [128, 2048], seed 4; one CUDA-graph replay per run"}
+                       "log-uniform in [128, 2048], seed 4; one CUDA-graph replay per run; (u,v) and K-range "
+                       "per bitsize group chosen by the autotuner (timed at batch creation)"}
     ref = None
     for form in ("int8", "fp64"):
         fitems = items if form == "int8" else [(a, b, torch.empty_like(c), p) for (a, b, c, p) in items]
-        bt = mwmm.Batch(fitems, form=form)
+        bt = mwmm.Batch(fitems, form=form, autotune=True)
         bt.run()
         torch.cuda.synchronize()
         nrun = runs if form == "int8" else 1
@@ -270,9 +273,12 @@ def run_batched(dev, runs=5):
         assert bt.check() == 0
         ms = e0.elapsed_time(e1) / nrun
         info = bt.info
+        d0 = bt.problem_info(0)
         out[form] = {"ms_per_run": ms, "gops": info["flops_2mnk"] / ms / 1e6,
                      "word_tflops": info["word_flops"] / ms / 1e9, "launches_per_run": info["launches"],
-                     "tc_items": info["items"], "ctas": info["ctas"]}
+                     "tc_items": info["items"], "ctas": info["ctas"],
+                     "autotuned": {"groups": info["tuned_groups"], "probe_ms": info["tuned_ms"],
+                                   "uv": [d0["u"], d0["v"]], "kc": d0["kc"], "f64_concat": d0["f64_concat"]}}
         if form == "int8":
             ref = [c.clone() for (_, _, c, _) in fitems]
         else:
@@ -663,6 +669,40 @@ def main():
                       "int8_over_fp64": t["total_ms"] / e["int8_ms"],
                       "fp64_equals_int8": same})
             del pl, Cf
+            torch.cuda.empty_cache()
+
+    # CRT (multimodular) comparison form per bitsize (Sec. 5.2), rank 0 only:
+    # residues modulo s primes below 256, s tcgen05 products, reconstruction
+    if not args.no_crt and rank == 0:
+        for i, (b, p, _, _) in enumerate(probs):
+            pl = mwmm.Plan(n, n, n, p, form="crt8")
+            pl.alloc_workspace(dev)
+            Cc = torch.empty((n, n), dtype=torch.int64, device=dev)
+            pl.matmul(dA[i], dB[i], Cc)  # warm-up
+            torch.cuda.synchronize()
+            mwmm.mwmm_plan_set_timing(pl.handle, True)
+            for _ in range(3):
+                pl.matmul(dA[i], dB[i], Cc)
+            t = mwmm.mwmm_plan_timing(pl.handle)
+            assert pl.check() == 0
+            d = pl.info
+            calls = max(t["calls"], 1)
+            e = per_bits[str(b)]
+            lg = math.log2(p)
+            e.update({"crt8_moduli": d["u"], "crt8_ms": t["total_ms"] / calls,
+                      "crt8_gops": 2.0 * n ** 3 / (t["total_ms"] / calls) / 1e6,
+                      "crt8_phase_ms": {"split_a": t["split_a_ms"] / calls, "split_b": t["split_b_ms"] / calls,
+                                        "word_products": t["gemm_ms"] / calls,
+                                        "reconstruct": t["recombine_ms"] / calls},
+                      "crt8_tensor_tflops": 2.0 * d["u"] * n ** 3 / (t["gemm_ms"] / calls) / 1e9,
+                      "crt8_equals_int8": bool(torch.equal(Cc, dC[i])),
+                      # products per result: multiword u v vs multimodular s, and the
+                      # paper's counts (numprodMW, numprodMM) for 8-bit words: t - log2(lambda)
+                      # = 24 - 10 bits per exact FP32 chunk of 1024 products
+                      "products": {"multiword_int8": e["int8_words"][0] * e["int8_words"][1], "crt8": d["u"],
+                                   "paper_multiword": math.ceil(2 * e["int8_words"][0] * lg / 14),
+                                   "paper_multimodular": math.ceil((4 * lg + 2 * math.log2(n)) / 14)}})
+            del pl, Cc
             torch.cuda.empty_cache()
 
     # end to end through the host entry point (pinned buffers, copies timed)

@@ -74,7 +74,14 @@ typedef enum {
 typedef enum {
     MWMM_FORM_AUTO = 0, /* INT8 form (the faster form on B300 at every bitsize) */
     MWMM_FORM_FP64 = 1,
-    MWMM_FORM_INT8 = 2
+    MWMM_FORM_INT8 = 2,
+    MWMM_FORM_CRT8 = 3  /* multimodular comparison form (Sec. 5.2): residues of A
+                           and B modulo the s largest primes below 256 (s the
+                           fewest whose product exceeds 2 k (p-1)^2), one
+                           tcgen05 product per modulus (signed residues exact
+                           in bf16, FP32 chunks of 1024, INT32 sums), and CRT
+                           reconstruction of the integer product, reduced mod p.
+                           u = v = nsums = s in the plan description. */
 } mwmm_form;
 
 typedef struct mwmm_plan_s *mwmm_plan_t;
@@ -152,6 +159,8 @@ typedef struct {
     double tuned_ms;        /* mwmm_plan_autotuned: measured time of the chosen configuration (0: not tuned) */
     int32_t tuned_tried;    /* candidates timed (0 when the choice came from the cache) */
     int32_t pad1;
+    uint32_t crt_m[24];     /* CRT form: the moduli m_0 > m_1 > ... (u of them); word i of A and of B
+                               holds the signed residues modulo m_i, sum plane i their product */
 } mwmm_plan_desc;
 
 /* Plan a product of an m x k by a k x n matrix mod p.

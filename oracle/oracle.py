@@ -194,3 +194,49 @@ def int8_words(p: int) -> int:
     while 127 * (256 ** u - 1) // 255 < (p - 1) // 2:
         u += 1
     return u
+
+
+# ---- multimodular (CRT) comparison form, Sec. 5.2 ------------------------
+# Plain big-integer definitions: the moduli, the signed residues each side is
+# split into, and the Chinese-remainder reconstruction of an integer.
+
+def crt_moduli(p: int, k: int) -> list:
+    """Moduli of the CRT form: the largest primes below 256 (largest first),
+    the fewest whose product M exceeds 2 k (p-1)^2.  Sec. 5.2 needs
+    M > k (p-1)^2 for the integer product; the factor 2 keeps that product
+    below M / 2, the margin the reconstruction's quotient estimate uses."""
+    primes = [c for c in range(255, 2, -1) if all(c % d for d in range(2, int(c ** 0.5) + 1))]
+    target = 2 * max(k, 1) * (p - 1) ** 2
+    out, prod = [], 1
+    for q in primes:
+        if prod > target:
+            break
+        out.append(q)
+        prod *= q
+    if prod <= target:
+        raise ValueError("not enough primes below 256 for p=%d, k=%d" % (p, k))
+    return out
+
+
+def crt_residues(M: np.ndarray, moduli) -> np.ndarray:
+    """Signed residues of every entry modulo each m_i, in
+    [-(m_i-1)/2, (m_i-1)/2]; shape (s,) + M.shape, int32."""
+    M = _c(M, np.uint64)
+    out = np.empty((len(moduli),) + M.shape, dtype=np.int32)
+    for i, m in enumerate(moduli):
+        r = (M % np.uint64(m)).astype(np.int64)
+        out[i] = np.where(r > (m - 1) // 2, r - m, r)
+    return out
+
+
+def crt_reconstruct(residues, moduli) -> int:
+    """The unique x in [0, M), M = prod(moduli), with x = residues[i] mod
+    moduli[i] (pairwise coprime moduli; textbook formula with big integers)."""
+    M = 1
+    for m in moduli:
+        M *= m
+    x = 0
+    for r, m in zip(residues, moduli):
+        Mi = M // m
+        x += (int(r) % m) * Mi * pow(Mi, -1, m)
+    return x % M

@@ -369,6 +369,7 @@ void describe_plan(const Plan &P, mwmm_plan_desc *d) {
     d->workspace_bytes = P.ws_bytes;
     d->tuned_ms = P.tuned_ms;
     d->tuned_tried = P.tuned_tried;
+    for (int i = 0; i < P.crt_s && i < 24; ++i) d->crt_m[i] = P.crt_m[i];
 }
 
 }  // namespace mwmm

@@ -70,8 +70,10 @@ struct TcParams {
     int u, v, nsums, nkc, mt_count, nt_count, nb, b_wpad;
     int64_t b_wstride, b_kstride;  // bytes between consecutive B words / k-blocks
     // diagonal windows, heaviest first: window g covers diagonals
-    // g_s0[g] .. g_s0[g] + g_nd[g] - 1 and A words g_i0[g] .. + g_ni[g] - 1
-    int g_s0[2 * kMaxWords], g_nd[2 * kMaxWords], g_i0[2 * kMaxWords], g_ni[2 * kMaxWords];
+    // g_s0[g] .. g_s0[g] + g_nd[g] - 1 and A words g_i0[g] .. + g_ni[g] - 1;
+    // its sums start at S plane g_plane[g] (the diagonal s0; the modulus i of
+    // the CRT form, whose window is the single pair (i, i) with s0 = 2 i)
+    int g_s0[kMaxWindows], g_nd[kMaxWindows], g_i0[kMaxWindows], g_ni[kMaxWindows], g_plane[kMaxWindows];
     // table items (batch): CTA c runs items[cta_off[c] .. cta_off[c + 1])
     const TcItem *items;
     const int64_t *cta_off;
@@ -124,7 +126,7 @@ __device__ __forceinline__ Item computed_item(const TcParams &P, int64_t idx, in
     it.B_rows = P.B_rows;
     it.nkb = P.nkb;
     it.plane = (int64_t)P.nkc * P.A_rows * P.B_rows;
-    it.S = P.S + (((int64_t)it.s0 * P.nkc + kc) * P.A_rows + it.mt * BM) * P.B_rows + it.nt * BN;
+    it.S = P.S + (((int64_t)P.g_plane[grp_w] * P.nkc + kc) * P.A_rows + it.mt * BM) * P.B_rows + it.nt * BN;
     return it;
 }
 
@@ -526,7 +528,7 @@ __device__ __forceinline__ Item pair_item(const TcParams &P, int64_t idx) {
     it.B_rows = P.B_rows;
     it.nkb = P.nkb;
     it.plane = (int64_t)P.nkc * P.A_rows * P.B_rows;
-    it.S = P.S + (((int64_t)it.s0 * P.nkc + kc) * P.A_rows + it.mt * BM2) * P.B_rows + it.nt * BN;
+    it.S = P.S + (((int64_t)P.g_plane[grp_w] * P.nkc + kc) * P.A_rows + it.mt * BM2) * P.B_rows + it.nt * BN;
     return it;
 }
 
@@ -815,15 +817,28 @@ int launch_gemm_tc(const Plan &pl, const void *Aw, const void *Bw, int32_t *S, i
     P.b_wstride = pl.B_wstride * kTileBytes;
     P.b_kstride = pl.B_kstride * kTileBytes;
     int ng = 0;
-    int gs0[2 * kMaxWords], gnd[2 * kMaxWords], gi0[2 * kMaxWords], gni[2 * kMaxWords], order[2 * kMaxWords];
-    for (int s0 = 0; s0 < pl.nsums; s0 += pl.tc_ndiag, ++ng) {
-        gs0[ng] = s0;
-        gnd[ng] = pl.nsums - s0 < pl.tc_ndiag ? pl.nsums - s0 : pl.tc_ndiag;
-        const int lo = s0 - (pl.v - 1) > 0 ? s0 - (pl.v - 1) : 0;
-        const int hi = s0 + gnd[ng] - 1 < pl.u - 1 ? s0 + gnd[ng] - 1 : pl.u - 1;
-        gi0[ng] = lo;
-        gni[ng] = hi - lo + 1;
-        order[ng] = ng;
+    int gs0[kMaxWindows], gnd[kMaxWindows], gi0[kMaxWindows], gni[kMaxWindows], gpl[kMaxWindows],
+        order[kMaxWindows];
+    if (pl.form == MWMM_FORM_CRT8) {  // one window per modulus: the pair (i, i)
+        for (; ng < pl.crt_s; ++ng) {
+            gs0[ng] = 2 * ng;
+            gnd[ng] = 1;
+            gi0[ng] = ng;
+            gni[ng] = 1;
+            gpl[ng] = ng;
+            order[ng] = ng;
+        }
+    } else {
+        for (int s0 = 0; s0 < pl.nsums; s0 += pl.tc_ndiag, ++ng) {
+            gs0[ng] = s0;
+            gnd[ng] = pl.nsums - s0 < pl.tc_ndiag ? pl.nsums - s0 : pl.tc_ndiag;
+            const int lo = s0 - (pl.v - 1) > 0 ? s0 - (pl.v - 1) : 0;
+            const int hi = s0 + gnd[ng] - 1 < pl.u - 1 ? s0 + gnd[ng] - 1 : pl.u - 1;
+            gi0[ng] = lo;
+            gni[ng] = hi - lo + 1;
+            gpl[ng] = s0;
+            order[ng] = ng;
+        }
     }
     for (int a = 1; a < ng; ++a)
         for (int b = a; b > 0 && gni[order[b]] > gni[order[b - 1]]; --b) {
@@ -831,11 +846,12 @@ int launch_gemm_tc(const Plan &pl, const void *Aw, const void *Bw, int32_t *S, i
             order[b] = order[b - 1];
             order[b - 1] = t;
         }
-    for (int g = 0; g < 2 * kMaxWords; ++g) {
+    for (int g = 0; g < kMaxWindows; ++g) {
         P.g_s0[g] = g < ng ? gs0[order[g]] : 0;
         P.g_nd[g] = g < ng ? gnd[order[g]] : 0;
         P.g_i0[g] = g < ng ? gi0[order[g]] : 0;
         P.g_ni[g] = g < ng ? gni[order[g]] : 0;
+        P.g_plane[g] = g < ng ? gpl[order[g]] : 0;
     }
     if (P.nitems == 0) return 0;
     if (pl.tc_pair) {

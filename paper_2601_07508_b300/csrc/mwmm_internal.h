@@ -9,7 +9,9 @@
 
 namespace mwmm {
 
-constexpr int kMaxWords = 8;            // u, v <= 8 in either form
+constexpr int kMaxWords = 8;            // u, v <= 8 in the multiword forms
+constexpr int kMaxCrt = 24;             // moduli of the CRT form
+constexpr int kMaxWindows = 32;         // tcgen05 item groups (diagonal windows or moduli)
 constexpr int kTileBytes = 128;         // one k-block row chunk of the word layout
 // FP64 form tiling
 constexpr int kF64KB = 16;              // doubles per k-block (128 B)
@@ -57,6 +59,12 @@ struct Plan {
     int f64_w = 64;      // output columns per tile (64 / f64_vs)
     int ksplit = 1;      // K ranges of the FP64 kernel (partial results summed mod p)
     int64_t kbr = 0;     // k-blocks per K range
+    // CRT form (MWMM_FORM_CRT8): moduli m_i, y_i = (M / m_i)^-1 mod m_i,
+    // w_i = (M / m_i) mod p, W = M mod p, two64 = 2^64 mod p
+    int crt_s = 0;
+    uint32_t crt_m[kMaxCrt] = {}, crt_y[kMaxCrt] = {};
+    uint64_t crt_w[kMaxCrt] = {};
+    uint64_t crt_W = 0, crt_two64 = 0;
     // autotuner outcome (0 when the plan was not tuned)
     double tuned_ms = 0;
     int tuned_tried = 0;

@@ -69,6 +69,69 @@ int int8_digits(uint64_t p) {
 
 static int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
+// Primes below 256, largest first (moduli of the CRT form).
+static int small_primes_desc(uint32_t *out, int cap) {
+    int n = 0;
+    for (uint32_t c = 255; c >= 3 && n < cap; --c) {
+        bool prime = true;
+        for (uint32_t d = 2; d * d <= c; ++d)
+            if (c % d == 0) { prime = false; break; }
+        if (prime) out[n++] = c;
+    }
+    return n;
+}
+
+static uint64_t inv_mod_small(uint64_t a, uint64_t m) {  // a^-1 mod m for gcd(a, m) = 1, m < 2^16
+    int64_t t = 0, nt = 1, r = (int64_t)m, nr = (int64_t)(a % m);
+    while (nr) {
+        const int64_t q = r / nr;
+        int64_t x = t - q * nt; t = nt; nt = x;
+        x = r - q * nr; r = nr; nr = x;
+    }
+    return (uint64_t)(t < 0 ? t + (int64_t)m : t);
+}
+
+// Moduli of the CRT form: the fewest largest primes below 256 whose product
+// M exceeds 2 k (p-1)^2 (then C = AB over the integers is below M / 2, which
+// the reconstruction needs), with the constants of the reconstruction.
+static mwmm_status crt_moduli(Plan &P, int64_t k, uint64_t p) {
+    uint32_t primes[64];
+    const int np = small_primes_desc(primes, 64);
+    const u128 kk = (u128)(k > 0 ? k : 1);
+    if (kk > ((u128)1 << 22)) return MWMM_ERR_ARG;  // 2 k (p-1)^2 must stay below 2^127
+    const u128 target = 2 * kk * (u128)(p - 1) * (p - 1);
+    u128 prod = 1;
+    int s = 0;
+    while (prod <= target) {
+        if (s >= kMaxCrt || s >= np) return MWMM_ERR_ARG;
+        const uint32_t mi = primes[s];
+        if (prod > target / mi) {  // prod * mi > target: the last modulus needed
+            P.crt_m[s++] = mi;
+            break;
+        }
+        prod *= mi;
+        P.crt_m[s++] = mi;
+    }
+    P.crt_s = s;
+    // M mod p and (M / m_i) mod p by products of the other moduli; y_i by
+    // products mod m_i
+    uint64_t W = 1 % p;
+    for (int i = 0; i < s; ++i) W = mulmod_u64(W, P.crt_m[i], p);
+    P.crt_W = W;
+    for (int i = 0; i < s; ++i) {
+        uint64_t wi = 1 % p, mi_mod = 1;
+        for (int j = 0; j < s; ++j) {
+            if (j == i) continue;
+            wi = mulmod_u64(wi, P.crt_m[j], p);
+            mi_mod = mi_mod * P.crt_m[j] % P.crt_m[i];
+        }
+        P.crt_w[i] = wi;
+        P.crt_y[i] = (uint32_t)inv_mod_small(mi_mod, P.crt_m[i]);
+    }
+    P.crt_two64 = (uint64_t)(((u128)1 << 64) % p);
+    return MWMM_OK;
+}
+
 mwmm_status make_plan(Plan *pl, int64_t m, int64_t n, int64_t k, uint64_t p, int u, int v,
                       int form, const mwmm_plan_opts *opts) {
     if (m < 0 || n < 0 || k < 0 || u < 0 || v < 0 || u > kMaxWords || v > kMaxWords)
@@ -77,7 +140,7 @@ mwmm_status make_plan(Plan *pl, int64_t m, int64_t n, int64_t k, uint64_t p, int
     // Alg. 1 needs p < 2^(t-1) (Prop. 2.1); the paper also assumes p >= 5.
     if (p < 5 || (p & 1) == 0 || p >= (uint64_t(1) << 52)) return MWMM_ERR_PRIME;
     if (form == MWMM_FORM_AUTO) form = MWMM_FORM_INT8;
-    if (form != MWMM_FORM_FP64 && form != MWMM_FORM_INT8) return MWMM_ERR_ARG;
+    if (form != MWMM_FORM_FP64 && form != MWMM_FORM_INT8 && form != MWMM_FORM_CRT8) return MWMM_ERR_ARG;
     mwmm_plan_opts o;
     std::memset(&o, 0, sizeof(o));
     if (opts) o = *opts;
@@ -180,20 +243,29 @@ mwmm_status make_plan(Plan *pl, int64_t m, int64_t n, int64_t k, uint64_t p, int
         P.S_off = align256(P.B_off + bbytes);
         P.ws_bytes = P.ksplit > 1 ? align256(P.S_off + (uint64_t)P.ksplit * m * n * 8) : P.S_off;
     } else {
-        const int need = int8_digits(p);
-        if (u == 0) { u = need; v = need; }
-        if (u < need || v < need) return MWMM_ERR_BOUND;
+        if (form == MWMM_FORM_CRT8) {  // one word (residue) per modulus on each side
+            if (u != 0 || v != 0) return MWMM_ERR_ARG;
+            mwmm_status cs = crt_moduli(P, k, p);
+            if (cs != MWMM_OK) return cs;
+            u = v = P.crt_s;
+        } else {
+            const int need = int8_digits(p);
+            if (u == 0) { u = need; v = need; }
+            if (u < need || v < need) return MWMM_ERR_BOUND;
+        }
         P.u = u; P.v = v;
-        P.alpha = 256; P.beta = 256;
-        P.nsums = u + v - 1;
+        P.alpha = form == MWMM_FORM_CRT8 ? 0 : 256;
+        P.beta = P.alpha;
+        P.nsums = form == MWMM_FORM_CRT8 ? P.crt_s : u + v - 1;  // one sum per modulus / per diagonal
         P.tc_chunk = kTcMaxChunk;
         if (o.tc_chunk != 0) {
             if (o.tc_chunk < 64 || o.tc_chunk > kTcMaxChunk || o.tc_chunk % 64) return MWMM_ERR_ARG;
             P.tc_chunk = o.tc_chunk;
         }
-        // One INT32 sum S_s collects w = min(u,v) pairs (at most) over kc
-        // k-steps, each product |d_a d_b| <= 2^14: need kc * w <= 131071.
-        const int w = u < v ? u : v;
+        // One INT32 sum S_s collects w = min(u,v) pairs (at most; one for the
+        // CRT form) over kc k-steps, each product |d_a d_b| <= 2^14: need
+        // kc * w <= 131071.
+        const int w = form == MWMM_FORM_CRT8 ? 1 : (u < v ? u : v);
         int64_t kcmax = (kInt32SumLimit / w) / kTcKB * kTcKB;
         int64_t kc = kcmax;
         if (o.kc != 0) {
@@ -214,6 +286,7 @@ mwmm_status make_plan(Plan *pl, int64_t m, int64_t n, int64_t k, uint64_t p, int
             while (P.tc_nb < n) P.tc_nb *= 2;
         }
         P.tc_ndiag = kTcBN / P.tc_nb < P.nsums ? kTcBN / P.tc_nb : P.nsums;
+        if (form == MWMM_FORM_CRT8) P.tc_ndiag = 1;  // each modulus pairs A_i with B_i only: no windows
         // the 2-CTA kernel (opt-in) computes 256 x 256 tiles
         P.tc_pair = (m > kTcBM && P.tc_nb == kTcBN && o.tc_pair) ? 1 : 0;
         // on request the one-CTA kernel runs in clusters of two sharing each B tile

@@ -175,7 +175,153 @@ int launch_recombine_batched(const void *probs, const int *jobs, int njobs, void
     return (int)cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// CRT form (multimodular comparison, Sec. 5.2): from the exact sums
+// S_i = sum_l a_l b_l over signed residues mod m_i (S_i = C mod m_i, where C
+// is the integer product, 0 <= C < M / 2, M = prod m_i), rebuild C mod p:
+//   x_i = (S_i mod m_i) y_i  (< m_i^2, not reduced),  y_i = (M / m_i)^-1 mod m_i,
+//   C = sum_i x_i (M / m_i) - q M,   q = floor(sum_i x_i / m_i)
+// (the textbook CRT formula with unreduced x_i: C / M = sum_i x_i / m_i - q
+// lies in [0, 1/2)).  q < 2^13 is evaluated in FP32 as
+// floor(0.25 + sum_i x_i fl(1/m_i)): the rounding error stays below 0.01 <<
+// 1/4, so the offset makes the floor exact.  Then
+//   C mod p = (sum_i x_i w_i - q W) mod p,  w_i = (M / m_i) mod p, W = M mod p,
+// with w_i = wh_i 2^26 + wl_i: the sums of x_i wl_i and x_i wh_i (< 2^42
+// each) are exact in 64 bits and are combined mod p once per output.  Remainders by the small moduli use the division-free method of
+// Lemire, Kaser and Kurz ("Faster remainder by direct computation", 2019):
+// for 32-bit a, a mod m = umulhi64((ceil(2^64 / m) a) mod 2^64, m).
+namespace {
+
+struct CrtParams {
+    const int32_t *S;
+    uint64_t *C;
+    int64_t ldc, m, n, A_rows, B_rows;
+    int s, nkc;
+    uint64_t p, mu, mu90, W;  // mu90 = floor(2^90 / p) when p > 2^26, else 0
+    uint32_t cm[kMaxCrt], cy[kMaxCrt];
+    uint32_t c31[kMaxCrt];    // 2^31 mod m_i
+    uint32_t wl[kMaxCrt], wh[kMaxCrt];  // w_i = wh_i 2^26 + wl_i
+    float rinv[kMaxCrt];
+    uint64_t cmag[kMaxCrt];   // ceil(2^64 / m_i)
+};
+
+// a mod m for any 32-bit a (division-free, see above).
+__device__ __forceinline__ uint32_t fastmod(uint32_t a, uint32_t m, uint64_t mag) {
+    return (uint32_t)__umul64hi(mag * a, m);
+}
+
+__global__ void __launch_bounds__(256) crt_kernel(const __grid_constant__ CrtParams P) {
+    const int64_t c0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4;
+    if (c0 >= P.n) return;
+    const int64_t plane = P.A_rows * P.B_rows;
+    for (int64_t row = blockIdx.y; row < P.m; row += gridDim.y) {
+        uint64_t a0[4] = {0, 0, 0, 0}, a1[4] = {0, 0, 0, 0};
+        float qf[4] = {0.25f, 0.25f, 0.25f, 0.25f};
+        if (P.nkc == 1) {
+            // four moduli per round: their loads are issued together
+            for (int i0 = 0; i0 < P.s; i0 += 4) {
+                int4 v[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    if (i0 + j < P.s)
+                        v[j] = __ldcs(reinterpret_cast<const int4 *>(P.S + (int64_t)(i0 + j) * plane + row * P.B_rows + c0));
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int i = i0 + j;
+                    if (i >= P.s) break;
+                    const uint32_t mi = P.cm[i], yi = P.cy[i], c = P.c31[i];
+                    const uint64_t mag = P.cmag[i];
+                    const float ri = P.rinv[i];
+                    const uint64_t wl = P.wl[i], wh = P.wh[i];
+                    const int32_t vv[4] = {v[j].x, v[j].y, v[j].z, v[j].w};
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        // S + 2^31 is in [0, 2^32): its residue, minus 2^31 mod m_i
+                        const uint32_t t = fastmod((uint32_t)vv[e] + 0x80000000u, mi, mag);
+                        const uint32_t r = t >= c ? t - c : t + mi - c;
+                        const uint32_t xi = r * yi;  // < m_i^2 < 2^16
+                        qf[e] = __fmaf_rn((float)xi, ri, qf[e]);
+                        a0[e] += xi * wl;
+                        a1[e] += xi * wh;
+                    }
+                }
+            }
+        } else {  // several K-ranges: exact 64-bit sums, then the residues
+            for (int i = 0; i < P.s; ++i) {
+                const uint32_t mi = P.cm[i], yi = P.cy[i];
+                int64_t x[4] = {0, 0, 0, 0};
+                for (int kc = 0; kc < P.nkc; ++kc) {
+                    const int4 v = *reinterpret_cast<const int4 *>(P.S + ((int64_t)i * P.nkc + kc) * plane +
+                                                                   row * P.B_rows + c0);
+                    x[0] += v.x; x[1] += v.y; x[2] += v.z; x[3] += v.w;
+                }
+                const float ri = P.rinv[i];
+                const uint64_t wl = P.wl[i], wh = P.wh[i];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int64_t t = x[e] % (int64_t)mi;
+                    const uint32_t xi = (uint32_t)(t < 0 ? t + mi : t) * yi;
+                    qf[e] = __fmaf_rn((float)xi, ri, qf[e]);
+                    a0[e] += xi * wl;
+                    a1[e] += xi * wh;
+                }
+            }
+        }
+        uint64_t *out = P.C + row * P.ldc + c0;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const uint64_t q = (uint64_t)floorf(qf[e]);  // < 2^13
+            // sum_i x_i w_i = a0 + 2^26 a1, and q W = q Wl + 2^26 q Wh
+            uint64_t lo = reduce_u64(a0[e], P.p, P.mu), hi = reduce_u64(a1[e], P.p, P.mu);
+            const uint64_t qlo = reduce_u64(q * (P.W & ((1u << 26) - 1)), P.p, P.mu);
+            const uint64_t qhi = reduce_u64(q * (P.W >> 26), P.p, P.mu);
+            lo = lo >= qlo ? lo - qlo : lo + P.p - qlo;
+            hi = hi >= qhi ? hi - qhi : hi + P.p - qhi;
+            uint64_t v = lo;
+            if (P.mu90) {
+                v += shl26_mod(hi, P.p, P.mu90);
+                if (v >= P.p) v -= P.p;
+            }
+            if (c0 + e < P.n) out[e] = v;
+        }
+    }
+}
+
+}  // namespace
+
+static int launch_crt(const Plan &pl, const int32_t *S, uint64_t *C, int64_t ldc, void *stream) {
+    CrtParams P;
+    std::memset(&P, 0, sizeof(P));
+    P.S = S;
+    P.C = C;
+    P.ldc = ldc;
+    P.m = pl.m;
+    P.n = pl.n;
+    P.A_rows = pl.A_rows;
+    P.B_rows = pl.B_rows;
+    P.s = pl.crt_s;
+    P.nkc = pl.nkc;
+    P.p = pl.p;
+    P.mu = (~uint64_t(0)) / pl.p;
+    P.mu90 = pl.p > (uint64_t(1) << 26) ? (uint64_t)(((unsigned __int128)1 << 90) / pl.p) : 0;
+    P.W = pl.crt_W;
+    for (int i = 0; i < pl.crt_s; ++i) {
+        P.cm[i] = pl.crt_m[i];
+        P.cy[i] = pl.crt_y[i];
+        P.rinv[i] = 1.0f / (float)pl.crt_m[i];
+        P.wl[i] = (uint32_t)(pl.crt_w[i] & ((1u << 26) - 1));
+        P.wh[i] = (uint32_t)(pl.crt_w[i] >> 26);
+        P.cmag[i] = (~uint64_t(0)) / pl.crt_m[i] + 1;
+        P.c31[i] = (uint32_t)((uint64_t(1) << 31) % pl.crt_m[i]);
+    }
+    const int64_t groups = (pl.n + 3) / 4;
+    dim3 grid((unsigned)((groups + 255) / 256), (unsigned)(pl.m < 65535 ? pl.m : 65535));
+    crt_kernel<<<grid, 256, 0, static_cast<cudaStream_t>(stream)>>>(P);
+    return (int)cudaGetLastError();
+}
+
 int launch_recombine(const Plan &pl, const int32_t *S, uint64_t *C, int64_t ldc, void *stream) {
+    if (pl.form == MWMM_FORM_CRT8) return pl.m == 0 || pl.n == 0 ? 0 : launch_crt(pl, S, C, ldc, stream);
     const RecParams P = make_rec_params(pl, S, C, ldc);
     if (pl.m == 0 || pl.n == 0) return 0;
     const int64_t groups = (pl.n + 3) / 4;

@@ -10,6 +10,10 @@
 // M > (p-1)/2) is written as balanced base-2^8 digits in [-128, 127],
 // s = sum_i 256^i d_i; the digits are stored exactly as bf16.
 //
+// CRT form (multimodular comparison, Sec. 5.2): word i is the signed
+// residue of M modulo the i-th modulus m_i < 256 (in [-(m_i-1)/2, (m_i-1)/2]),
+// stored exactly as bf16 in the same layout.
+//
 // Output layout (see mwmm_plan_desc): word w, k-block kb, row r occupies the
 // 128-byte chunk ((w * nkb + kb) * rows_pad + r); inside it the 16-byte
 // granule g sits at position g ^ (r & 7), which is the 128-byte swizzle the
@@ -44,7 +48,17 @@ struct SplitParams {
     uint64_t alpha, mu;  // FP64: radix and floor((2^64 - 1) / alpha)
     int validate;
     int *err;
+    int crt;                    // CRT form: residues instead of digits
+    uint32_t cm[kMaxCrt];       // moduli
+    uint64_t cmu[kMaxCrt];      // floor((2^64 - 1) / m_i)
 };
+
+// Signed residue of x modulo m < 2^16: x - m umulhi(x, mu) is below 2m.
+__device__ __forceinline__ float signed_residue(uint64_t x, uint32_t m, uint64_t mu) {
+    uint32_t r = (uint32_t)(x - __umul64hi(x, mu) * m);
+    if (r >= m) r -= m;
+    return (float)(r > (m - 1) / 2 ? (int)r - (int)m : (int)r);
+}
 
 __device__ __forceinline__ uint64_t load_tile_elem(const SplitParams &P, int64_t r, int64_t l) {
     if (r >= P.rows || l >= P.K) return 0;
@@ -127,19 +141,25 @@ __device__ __forceinline__ void split_int8_tile(const SplitParams &P, uint64_t (
     const uint64_t half = (P.p - 1) / 2;
     for (int unit = threadIdx.x; unit < kST * 8; unit += 256) {
         const int rr = unit / 8, g = unit % 8;
+        uint64_t x[8];
         int64_t s[8];
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
-            const uint64_t x = tile[rr][8 * g + e];
-            s[e] = (x <= half) ? (int64_t)x : (int64_t)x - (int64_t)P.p;
+            x[e] = tile[rr][8 * g + e];
+            s[e] = (x[e] <= half) ? (int64_t)x[e] : (int64_t)x[e] - (int64_t)P.p;
         }
         const int64_t r = r0 + rr;
         if (r >= P.rows_pad) continue;  // a last row tile may be partial (rows_pad 16 or 32)
         for (int w = 0; w < P.words; ++w) {
             const bool last = (w == P.words - 1);
             __align__(16) __nv_bfloat16 h[8];
+            if (P.crt) {
 #pragma unroll
-            for (int e = 0; e < 8; ++e) h[e] = __float2bfloat16_rn(int8_next(s[e], last));
+                for (int e = 0; e < 8; ++e) h[e] = __float2bfloat16_rn(signed_residue(x[e], P.cm[w], P.cmu[w]));
+            } else {
+#pragma unroll
+                for (int e = 0; e < 8; ++e) h[e] = __float2bfloat16_rn(int8_next(s[e], last));
+            }
             uint8_t *dst = P.out + ((int64_t)(w + P.wpad) * P.wstride + kb * P.kstride + r) * kTileBytes +
                            ((g ^ (int)(r & 7)) * 16);
             *reinterpret_cast<uint4 *>(dst) = *reinterpret_cast<const uint4 *>(h);
@@ -195,6 +215,11 @@ SplitParams make_split_params(const Plan &pl, int side, const uint64_t *M, int64
     P.mu = P.alpha >= 2 ? (~uint64_t(0)) / P.alpha : 0;
     P.validate = pl.validate;
     P.err = pl.err_dev;
+    P.crt = pl.form == MWMM_FORM_CRT8;
+    for (int i = 0; i < kMaxCrt; ++i) {
+        P.cm[i] = i < pl.crt_s ? pl.crt_m[i] : 1;
+        P.cmu[i] = i < pl.crt_s ? (~uint64_t(0)) / pl.crt_m[i] : 0;
+    }
     return P;
 }
 

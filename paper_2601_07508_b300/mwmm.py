@@ -25,8 +25,8 @@ MWMM_OK = 0
 STATUS = {0: "MWMM_OK", 1: "MWMM_ERR_ARG", 2: "MWMM_ERR_PRIME", 3: "MWMM_ERR_BOUND", 4: "MWMM_ERR_RANGE",
           5: "MWMM_ERR_NOMEM", 6: "MWMM_ERR_BUDGET", 7: "MWMM_ERR_CUDA", 8: "MWMM_ERR_TIMEOUT",
           9: "MWMM_ERR_BUSY", 10: "MWMM_ERR_UNSUPPORTED"}
-FORM_AUTO, FORM_FP64, FORM_INT8 = 0, 1, 2
-FORMS = {"auto": FORM_AUTO, "fp64": FORM_FP64, "int8": FORM_INT8}
+FORM_AUTO, FORM_FP64, FORM_INT8, FORM_CRT8 = 0, 1, 2, 3
+FORMS = {"auto": FORM_AUTO, "fp64": FORM_FP64, "int8": FORM_INT8, "crt8": FORM_CRT8}
 
 
 class MwmmError(RuntimeError):
@@ -61,12 +61,14 @@ class PlanDesc(ctypes.Structure):
                 ("A_off", ctypes.c_uint64), ("B_off", ctypes.c_uint64),
                 ("S_off", ctypes.c_uint64), ("workspace_bytes", ctypes.c_uint64),
                 ("f64_concat", ctypes.c_int32), ("ksplit", ctypes.c_int32),
-                ("tuned_ms", ctypes.c_double), ("tuned_tried", ctypes.c_int32), ("pad1", ctypes.c_int32)]
+                ("tuned_ms", ctypes.c_double), ("tuned_tried", ctypes.c_int32), ("pad1", ctypes.c_int32),
+                ("crt_m", ctypes.c_uint32 * 24)]
 
     def as_dict(self):
         d = {}
         for name, _ in self._fields_:
-            d[name.rstrip("_")] = getattr(self, name)
+            val = getattr(self, name)
+            d[name.rstrip("_")] = list(val) if isinstance(val, ctypes.Array) else val
         return d
 
 

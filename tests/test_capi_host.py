@@ -228,3 +228,26 @@ def test_autotuned_plan_rejects_bad_arguments_before_any_device_call(M):
     for args in ((-1, 8, 8, SWEEP[40]), (8, 8, 8, 4), (8, 8, 8, 1 << 52)):
         with pytest.raises(M.MwmmError):
             M.mwmm_plan_autotuned(*args, form="fp64", stream=0)
+
+
+@pytest.mark.parametrize("b", [20, 26, 32, 40, 48, 52])
+@pytest.mark.parametrize("k", [1, 100, 4096, 40000])
+def test_crt_plan_moduli_match_oracle(M, oracle, b, k):
+    p = SWEEP[b]
+    h = M.mwmm_plan(300, 200, k, p, 0, 0, "crt8")
+    d = M.mwmm_plan_info(h)
+    M.mwmm_plan_destroy(h)
+    ms = oracle.crt_moduli(p, k)
+    assert d["form"] == 3 and d["u"] == d["v"] == d["nsums"] == len(ms)
+    assert d["crt_m"][:len(ms)] == ms and all(x == 0 for x in d["crt_m"][len(ms):])
+    assert d["kc"] * 2 ** 14 < 2 ** 31  # one residue product per INT32 sum
+    assert d["workspace_bytes"] >= d["S_off"] + len(ms) * d["nkc"] * d["A_rows"] * d["B_rows"] * 4
+
+
+def test_crt_plan_errors(M):
+    with pytest.raises(M.MwmmError) as e:  # words are fixed by the moduli
+        M.mwmm_plan(8, 8, 8, SWEEP[40], 2, 2, "crt8")
+    assert e.value.status == 1
+    with pytest.raises(M.MwmmError) as e:  # 2 k (p-1)^2 beyond what 24 moduli below 256 cover
+        M.mwmm_plan(8, 8, 1 << 23, SWEEP[52], 0, 0, "crt8")
+    assert e.value.status == 1

@@ -110,6 +110,76 @@ def test_fp64_k_ranges(M, oracle, ks):
         assert np.array_equal(C, oracle.matmul_mod(A, B, p)), (m, n, k, ks)
 
 
+@pytest.mark.parametrize("b", [20, 23, 26, 32, 40, 48, 50, 52])
+def test_crt_form_ragged(M, oracle, b):
+    """Multimodular comparison form (Sec. 5.2): residues modulo the primes
+    below 256, one tcgen05 product per modulus, CRT reconstruction mod p."""
+    p = SWEEP.get(b, P50)
+    for seed, (m, n, k) in enumerate(SHAPES + [(300, 520, 1000), (129, 20, 777), (260, 130, 64)]):
+        A, B = inputs.problem(2000 + 10 * b + seed, m, n, k, p)
+        C, plan = gpu_product(M, A, B, p, form="crt8")
+        assert plan.info["u"] == len(oracle.crt_moduli(p, k))
+        assert np.array_equal(C, oracle.matmul_mod(A, B, p)), (m, n, k)
+
+
+@pytest.mark.parametrize("b", [26, 52])
+def test_crt_form_extremes_and_k_ranges(M, oracle, b):
+    """All entries p - 1 (the largest integer product k (p-1)^2 the moduli
+    must cover) and INT32 K-ranges of 64 / 320 steps (several sums per
+    modulus added in 64 bits before the residue is taken)."""
+    p = SWEEP[b]
+    A = np.full((130, 700), p - 1, dtype=np.uint64)
+    B = np.full((700, 260), p - 1, dtype=np.uint64)
+    for kc in (0, 64, 320):
+        C, plan = gpu_product(M, A, B, p, form="crt8", kc=kc)
+        assert np.all(C == (700 * (p - 1) ** 2) % p), kc
+    A, B = inputs.problem(77, 200, 300, 1500, p)
+    C, plan = gpu_product(M, A, B, p, form="crt8", kc=192)
+    assert plan.info["nkc"] == -(-1500 // 192)
+    assert np.array_equal(C, oracle.matmul_mod(A, B, p))
+
+
+@pytest.mark.parametrize("b", [20, 52])
+def test_crt_form_int32_sums_at_their_bound(M, oracle, b):
+    """k at the INT32 K-range limit with constant columns, so each sum
+    S_i = k d_a d_b sits near +-2^31 (|d| up to 125): the residues of the
+    sums are taken over the whole 32-bit range."""
+    p = SWEEP[b]
+    k = 131008
+    plan = M.Plan(2, 3, k, p, form="crt8")
+    assert plan.info["nkc"] == 1
+    m0 = plan.info["crt_m"][0]
+    cols = np.array([p - 1, (m0 + 1) // 2, (m0 - 1) // 2], dtype=np.uint64)  # d = -1, -(m0-1)/2, (m0-1)/2 mod m0
+    A = np.full((2, k), p - 1, dtype=np.uint64)
+    B = np.tile(cols, (k, 1))
+    C = host(plan.matmul(dev(A), dev(B)))
+    assert plan.check() == 0
+    ref = np.array([[k * (p - 1) * int(c) % p for c in cols]] * 2, dtype=np.uint64)
+    assert np.array_equal(C, ref)
+
+
+def test_crt_residue_words_and_sums_match_oracle(M, oracle):
+    p = SWEEP[48]
+    m, n, k = 130, 260, 300
+    A, B = inputs.problem(79, m, n, k, p)
+    plan = M.Plan(m, n, k, p, form="crt8")
+    ws = plan.alloc_workspace()
+    plan.matmul(dev(A), dev(B))
+    assert plan.check() == 0
+    d = plan.info
+    ms = d["crt_m"][:d["u"]]
+    assert ms == oracle.crt_moduli(p, k)
+    WA = unpack_words(ws[d["A_off"]:].cpu().numpy(), d["u"], d["nkb"], d["A_rows"], "int8")
+    WB = unpack_words(ws[d["B_off"]:].cpu().numpy(), d["v"], d["nkb"], d["B_rows"], "int8")
+    RA, RB = oracle.crt_residues(A, ms), oracle.crt_residues(B.T.copy(), ms)
+    assert np.array_equal(WA[:, :m, :k], RA) and np.array_equal(WB[:, :n, :k], RB)
+    S = ws[d["S_off"]:d["S_off"] + d["nsums"] * d["nkc"] * d["A_rows"] * d["B_rows"] * 4]
+    S = S.cpu().numpy().view(np.int32).reshape(d["nsums"], d["nkc"], d["A_rows"], d["B_rows"])
+    for i in range(len(ms)):
+        ref = RA[i].astype(np.int64) @ RB[i].astype(np.int64).T
+        assert np.array_equal(S[i, 0, :m, :n], ref), i
+
+
 @pytest.mark.parametrize("lam", [1, 2, 3, 7, 16, 17])
 def test_fp64_block_size_boundaries(M, oracle, lam):
     """Reductions at every lambda-th k-step (including inside a 16-wide k-block)."""

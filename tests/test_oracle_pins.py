@@ -375,3 +375,55 @@ def test_alg2_reading_returns_xy_mod_p(b):
     ys = [int(v) for v in inputs.uniform_mod(b, 5, 200, p)] + [p - 1, p - 1, p - 1, p - 1]
     for x, y in zip(xs, ys):
         assert alg2(float(x), float(y), float(p), q) == float(x * y % p)
+
+
+# ---- CRT (multimodular) comparison form, Sec. 5.2 ----
+from math import gcd, prod
+
+
+@pytest.mark.parametrize("b", [20, 23, 26, 32, 40, 48, 52])
+@pytest.mark.parametrize("k", [1, 64, 4096, 32768])
+def test_crt_moduli_are_minimal_coprime_and_cover_the_product(oracle, b, k):
+    p = inputs.largest_prime_below_pow2(b)
+    ms = oracle.crt_moduli(p, k)
+    assert all(3 <= m < 256 for m in ms) and ms == sorted(ms, reverse=True)
+    assert all(gcd(a, c) == 1 for i, a in enumerate(ms) for c in ms[i + 1:])
+    target = 2 * k * (p - 1) ** 2
+    assert prod(ms) > target >= prod(ms[:-1])  # enough, and one fewer is not
+    # Sec. 5.2: M > k (p-1)^2 needs at least (2 log2(p-1) + log2 k) / 8 moduli below 2^8
+    assert len(ms) >= (2 * (p - 1).bit_length() - 2 + k.bit_length() - 1) / 8
+
+
+def test_crt_reconstruction_against_brute_force(oracle):
+    ms = [3, 5, 7]
+    for x in range(105):  # every residue triple comes from exactly one x < 105
+        r = [((x % m) + m // 2) % m - m // 2 for m in ms]  # signed residues
+        assert oracle.crt_reconstruct(r, ms) == x
+    rng = np.random.default_rng(3)
+    ms = oracle.crt_moduli(inputs.largest_prime_below_pow2(52), 4096)
+    M = prod(ms)
+    for _ in range(200):
+        x = int(rng.integers(0, 1 << 62)) * int(rng.integers(0, 1 << 62)) % M
+        assert oracle.crt_reconstruct([x % m for m in ms], ms) == x
+
+
+@pytest.mark.parametrize("b", [20, 40, 52])
+def test_crt_pipeline_reaches_the_exact_product(oracle, b):
+    """Residues of A and B, one integer product per modulus, reconstruction:
+    the integer product AB itself (checked with Python integers), hence AB mod
+    p as the oracle computes it."""
+    p = inputs.largest_prime_below_pow2(b)
+    A, B = inputs.problem(70 + b, 5, 4, 6, p)
+    ms = oracle.crt_moduli(p, 6)
+    RA, RB = oracle.crt_residues(A, ms), oracle.crt_residues(B, ms)
+    for i, m in enumerate(ms):
+        assert np.all(np.abs(RA[i]) <= (m - 1) // 2) and np.all((RA[i].astype(np.int64) - A.astype(object) % m) % m == 0)
+    S = [RA[i].astype(np.int64) @ RB[i].astype(np.int64) for i in range(len(ms))]
+    exact = [[sum(int(A[r, l]) * int(B[l, c]) for l in range(6)) for c in range(4)] for r in range(5)]
+    for r in range(5):
+        for c in range(4):
+            x = oracle.crt_reconstruct([S[i][r, c] for i in range(len(ms))], ms)
+            assert x == exact[r][c]
+    C = np.array([[oracle.crt_reconstruct([S[i][r, c] for i in range(len(ms))], ms) % p for c in range(4)]
+                  for r in range(5)], dtype=np.uint64)
+    assert np.array_equal(C, oracle.matmul_mod(A, B, p))
