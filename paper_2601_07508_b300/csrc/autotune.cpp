@@ -11,7 +11,8 @@
 //     two sharing B, 256 x 256 CTA pairs; one-CTA only in batch mode) and the
 //     INT32 K-range kc (the largest the bound allows, and half of k when that
 //     splits the k loop), within twice the default workspace;
-//   - both forms when the caller asks for MWMM_FORM_AUTO.
+//   - for MWMM_FORM_AUTO, both forms and (single products only) the
+//     multimodular CRT form of Sec. 5.2 with the same tile variants.
 // Candidates are ordered by a flop model; each is run once to warm up and
 // timed twice (CUDA events, the faster run counts); a candidate whose model
 // time exceeds 3x the best measured time is skipped.  The kernels' run time
@@ -151,7 +152,8 @@ void add(std::vector<Cand> &out, int form, int u, int v, const mwmm_plan_opts &o
         const double lam = (double)std::min<int64_t>(c.pl.lambda, std::max<int64_t>(k, 1));
         c.model_ms = uv * mnk2 * (1.0 + 3.0 / lam) / 1.0e12 * 1e3;  // FP64 pipe ~1 TFLOP/s
     } else {
-        c.model_ms = uv * mnk2 / 1.4e15 * 1e3 + (double)c.pl.ws_bytes / 5.0e12 * 1e3;
+        const double prods = form == MWMM_FORM_CRT8 ? (double)c.pl.crt_s : uv;  // one product per modulus
+        c.model_ms = prods * mnk2 / 1.4e15 * 1e3 + (double)c.pl.ws_bytes / 5.0e12 * 1e3;
     }
     out.push_back(c);
 }
@@ -161,6 +163,17 @@ void candidates(int form_req, int64_t m, int64_t n, int64_t k, uint64_t p, bool 
     const bool want_fp64 = form_req == MWMM_FORM_AUTO || form_req == MWMM_FORM_FP64;
     mwmm_plan_opts z;
     std::memset(&z, 0, sizeof(z));
+    if (form_req == MWMM_FORM_AUTO && !batch) {  // the batched kernels run the multiword forms only
+        Plan crt;
+        if (make_plan(&crt, m, n, k, p, 0, 0, MWMM_FORM_CRT8, &z) == MWMM_OK) {
+            mwmm_plan_opts o = z;
+            add(out, MWMM_FORM_CRT8, 0, 0, o, m, n, k, p);
+            if (m > kTcBM && n > kTcBN / 2) {
+                o.tc_pair = 1;
+                add(out, MWMM_FORM_CRT8, 0, 0, o, m, n, k, p);
+            }
+        }
+    }
     if (want_int8) {
         Plan base;
         if (make_plan(&base, m, n, k, p, 0, 0, MWMM_FORM_INT8, &z) == MWMM_OK) {

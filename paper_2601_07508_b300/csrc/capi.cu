@@ -176,7 +176,8 @@ mwmm_status make_sub_plan(const Plan &pl, int64_t rows, Plan *out) {
         o.kc = pl.kc;
         o.tc_cluster = pl.tc_cluster == 2 ? 2 : 1;
     }
-    mwmm_status st = mwmm::make_plan(out, rows, pl.n, pl.k, pl.p, pl.u, pl.v, pl.form, &o);
+    const bool crt = pl.form == MWMM_FORM_CRT8;  // its words follow from p and k
+    mwmm_status st = mwmm::make_plan(out, rows, pl.n, pl.k, pl.p, crt ? 0 : pl.u, crt ? 0 : pl.v, pl.form, &o);
     if (st != MWMM_OK) return st;
     out->err_dev = pl.err_dev;  // shared flags (owned by the full plan)
     out->device = pl.device;

@@ -279,13 +279,13 @@ def test_host_entry_point(M, oracle, form):
     assert np.array_equal(C, oracle.matmul_mod(A, B, p))
 
 
-@pytest.mark.parametrize("form", ["fp64", "int8"])
+@pytest.mark.parametrize("form", ["fp64", "int8", "crt8"])
 @pytest.mark.parametrize("shape", [(1100, 70, 300), (4100, 33, 200), (2048, 260, 129)])
 def test_host_entry_point_row_block_pipeline(M, oracle, form, shape):
     """m >= 1024: row blocks on three streams (A in, compute, C out); strided
     host matrices; equal to the one-stream order (taken when timing is on)."""
     m, n, k = shape
-    p = SWEEP[52] if form == "int8" else SWEEP[32]
+    p = SWEEP[32] if form == "fp64" else SWEEP[52]
     A, B = inputs.problem(23 + m, m, n, k, p)
     ref = oracle.matmul_mod(A, B, p)
     plan = M.Plan(m, n, k, p, form=form)
