@@ -205,9 +205,13 @@ struct CrtParams {
     uint64_t cmag[kMaxCrt];   // ceil(2^64 / m_i)
 };
 
-// a mod m for any 32-bit a (division-free, see above).
+// a mod m for any 32-bit a (division-free, see above); the high word of the
+// 96-bit product (mag a mod 2^64) m is formed from two 32 x 32 -> 64 products.
 __device__ __forceinline__ uint32_t fastmod(uint32_t a, uint32_t m, uint64_t mag) {
-    return (uint32_t)__umul64hi(mag * a, m);
+    const uint64_t low = mag * a;
+    const uint64_t t = (uint64_t)(uint32_t)low * m;
+    const uint64_t u = (low >> 32) * (uint64_t)m + (t >> 32);
+    return (uint32_t)(u >> 32);
 }
 
 __global__ void __launch_bounds__(256) crt_kernel(const __grid_constant__ CrtParams P) {
@@ -232,7 +236,7 @@ __global__ void __launch_bounds__(256) crt_kernel(const __grid_constant__ CrtPar
                     const uint32_t mi = P.cm[i], yi = P.cy[i], c = P.c31[i];
                     const uint64_t mag = P.cmag[i];
                     const float ri = P.rinv[i];
-                    const uint64_t wl = P.wl[i], wh = P.wh[i];
+                    const uint32_t wl = P.wl[i], wh = P.wh[i];
                     const int32_t vv[4] = {v[j].x, v[j].y, v[j].z, v[j].w};
 #pragma unroll
                     for (int e = 0; e < 4; ++e) {
@@ -241,8 +245,8 @@ __global__ void __launch_bounds__(256) crt_kernel(const __grid_constant__ CrtPar
                         const uint32_t r = t >= c ? t - c : t + mi - c;
                         const uint32_t xi = r * yi;  // < m_i^2 < 2^16
                         qf[e] = __fmaf_rn((float)xi, ri, qf[e]);
-                        a0[e] += xi * wl;
-                        a1[e] += xi * wh;
+                        a0[e] += (uint64_t)xi * wl;  // 32 x 32 -> 64
+                        a1[e] += (uint64_t)xi * wh;
                     }
                 }
             }
