@@ -122,6 +122,8 @@ static void tc_items(const Plan &pl, const uint8_t *Aw, const uint8_t *Bw, int32
                     it.ni = ihi - ilo + 1;
                     it.v = pl.v;
                     it.b_wpad = pl.B_wpad;
+                    it.rv = (int32_t)std::min<int64_t>(mwmm::kTcBM, pl.m - mt * mwmm::kTcBM);
+                    it.cv = (int32_t)std::min<int64_t>(pl.tc_nb, pl.n - nt * pl.tc_nb);
                     it.b_wstride = pl.B_wstride * mwmm::kTileBytes;
                     it.b_kstride = pl.B_kstride * mwmm::kTileBytes;
                     items.push_back(it);

@@ -68,6 +68,7 @@ struct TcParams {
     int32_t *S;
     int64_t nkb, A_rows, B_rows, kcb, nitems;
     int u, v, nsums, nkc, mt_count, nt_count, nb, b_wpad;
+    int64_t m, n;  // valid rows and columns (sums outside are not stored)
     int64_t b_wstride, b_kstride;  // bytes between consecutive B words / k-blocks
     // diagonal windows, heaviest first: window g covers diagonals
     // g_s0[g] .. g_s0[g] + g_nd[g] - 1 and A words g_i0[g] .. + g_ni[g] - 1;
@@ -87,7 +88,17 @@ struct Item {
     int32_t *S;  // S of diagonal s0 at the item's tile origin, row stride B_rows
     int64_t A_rows, B_rows, nkb, kb0, nkbc, mt, nt, plane, b_wstride, b_kstride;
     int s0, ndiag, nb, i0, ni, v, b_wpad;
+    int rv, cv;  // rows of the tile inside m (from its first row), columns of each diagonal block inside n
+    int nn;      // MMA N: ndiag nb
 };
+
+// MMA N of an item.  Fitting N of a last column tile to its valid columns
+// (rounded up to 16) was measured: it made the 512-instance batch 33% slower
+// on B300, so every tile runs its full width.
+__device__ __forceinline__ int item_n(int ndiag, int nb, int cv) {
+    (void)cv;
+    return ndiag * nb;
+}
 
 // kCl = 2: item idx is a 256-row tile shared by the cluster; `rank` picks
 // its 128-row half.
@@ -127,6 +138,10 @@ __device__ __forceinline__ Item computed_item(const TcParams &P, int64_t idx, in
     it.nkb = P.nkb;
     it.plane = (int64_t)P.nkc * P.A_rows * P.B_rows;
     it.S = P.S + (((int64_t)P.g_plane[grp_w] * P.nkc + kc) * P.A_rows + it.mt * BM) * P.B_rows + it.nt * BN;
+    const int64_t rv = P.m - it.mt * BM, cv = P.n - it.nt * P.nb;
+    it.rv = (int)(rv < BM ? rv : BM);
+    it.cv = (int)(cv < P.nb ? cv : P.nb);
+    it.nn = item_n(it.ndiag, it.nb, it.cv);
     return it;
 }
 
@@ -153,6 +168,9 @@ __device__ __forceinline__ Item table_item(const TcParams &P, int64_t pos) {
     it.b_wstride = d.b_wstride;
     it.b_kstride = d.b_kstride;
     it.b_wpad = d.b_wpad;
+    it.rv = d.rv;
+    it.cv = d.cv;
+    it.nn = item_n(it.ndiag, it.nb, it.cv);
     return it;
 }
 
@@ -326,7 +344,7 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_consta
                 // The window's B words B_{s0-i} .. B_{s0-i+ndiag-1} are contiguous
                 // (k-block-major layout padded with zero words), so each stage is
                 // two copies whatever the window.
-                const uint32_t bbytes = (uint32_t)(it.ndiag * it.nb) * kTileBytes;
+                const uint32_t bbytes = (uint32_t)it.nn * kTileBytes;
                 const uint32_t stage_bytes = kTileA + bbytes;
                 const int64_t a_step = it.A_rows * kTileBytes;
                 for (int ii = 0; alive && ii < it.ni; ++ii) {
@@ -368,7 +386,7 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_consta
             for (int64_t idx = R.begin; alive && idx < R.end; idx += R.step) {
                 const Item it = get_item<kTable, kCl>(P, idx, rank);
                 const int64_t nvb = (int64_t)it.ni * it.nkbc;
-                const uint32_t idesc = idesc_n(it.ndiag * it.nb);
+                const uint32_t idesc = idesc_n(it.nn);
                 for (int64_t t0 = 0; alive && t0 < nvb; t0 += P.chunk_blocks, ++c) {
                     const int buf = (int)(c & 1);
                     if (!mbar_wait(&tempty[buf], (uint32_t)(((c >> 1) & 1) ^ 1), P.err)) {
@@ -423,12 +441,14 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_consta
                     break;
                 }
                 tc_fence_after();
+                if (half * 128 < it.nn) {  // this warp's columns hold products (warp-uniform)
 #pragma unroll
-                for (int jb = 0; jb < 4; ++jb) {
-                    uint32_t r[32];
-                    tmem_ld32(tlane + (uint32_t)(buf * BN + jb * 32), r);
+                    for (int jb = 0; jb < 4; ++jb) {
+                        uint32_t r[32];
+                        tmem_ld32(tlane + (uint32_t)(buf * BN + jb * 32), r);
 #pragma unroll
-                    for (int e = 0; e < 32; ++e) acc[jb * 32 + e] += __float2int_rn(__uint_as_float(r[e]));
+                        for (int e = 0; e < 32; ++e) acc[jb * 32 + e] += __float2int_rn(__uint_as_float(r[e]));
+                    }
                 }
                 tc_fence_before();
                 __syncwarp();
@@ -436,16 +456,19 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_consta
             }
             if (!alive) break;
             // streaming stores: the sums are read once, by the recombination, so
-            // they should not displace word tiles from L2
+            // they should not displace word tiles from L2; rows and columns
+            // outside the matrix (tile padding) are never read and not stored
             // column c of the accumulator is column c mod nb of diagonal s0 + c / nb
             int32_t *row = it.S + (int64_t)(quarter * 32 + lane) * it.B_rows;
+            if (quarter * 32 + lane < it.rv) {
 #pragma unroll
-            for (int q4 = 0; q4 < 32; ++q4) {
-                const int c = half * 128 + 4 * q4;
-                const int d = c / it.nb;
-                if (d < it.ndiag)
-                    __stcs(reinterpret_cast<int4 *>(row + d * it.plane + (c - d * it.nb)),
-                           make_int4(acc[4 * q4], acc[4 * q4 + 1], acc[4 * q4 + 2], acc[4 * q4 + 3]));
+                for (int q4 = 0; q4 < 32; ++q4) {
+                    const int c = half * 128 + 4 * q4;
+                    const int d = c / it.nb;
+                    if (d < it.ndiag && c - d * it.nb < it.cv)
+                        __stcs(reinterpret_cast<int4 *>(row + d * it.plane + (c - d * it.nb)),
+                               make_int4(acc[4 * q4], acc[4 * q4 + 1], acc[4 * q4 + 2], acc[4 * q4 + 3]));
+                }
             }
         }
     }
@@ -529,6 +552,9 @@ __device__ __forceinline__ Item pair_item(const TcParams &P, int64_t idx) {
     it.nkb = P.nkb;
     it.plane = (int64_t)P.nkc * P.A_rows * P.B_rows;
     it.S = P.S + (((int64_t)P.g_plane[grp_w] * P.nkc + kc) * P.A_rows + it.mt * BM2) * P.B_rows + it.nt * BN;
+    const int64_t rv = P.m - it.mt * BM2, cv = P.n - it.nt * BN;  // clipped to the 256 x 256 tile
+    it.rv = (int)(rv < BM2 ? rv : BM2);
+    it.cv = (int)(cv < BN ? cv : BN);
     return it;
 }
 
@@ -693,10 +719,13 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS, 1)
             }
             if (!alive) break;
             int32_t *dst = it.S + (int64_t)(rank * 128 + quarter * 32 + lane) * it.B_rows + half * 128;
+            if (rank * 128 + quarter * 32 + lane < it.rv) {  // padding rows and columns are not stored
 #pragma unroll
-            for (int q4 = 0; q4 < 32; ++q4)
-                __stcs(reinterpret_cast<int4 *>(dst) + q4,
-                       make_int4(acc[4 * q4], acc[4 * q4 + 1], acc[4 * q4 + 2], acc[4 * q4 + 3]));
+                for (int q4 = 0; q4 < 32; ++q4)
+                    if (half * 128 + 4 * q4 < it.cv)
+                        __stcs(reinterpret_cast<int4 *>(dst) + q4,
+                               make_int4(acc[4 * q4], acc[4 * q4 + 1], acc[4 * q4 + 2], acc[4 * q4 + 3]));
+            }
         }
     }
 
@@ -813,6 +842,8 @@ int launch_gemm_tc(const Plan &pl, const void *Aw, const void *Bw, int32_t *S, i
     // diagonal windows of tc_ndiag diagonals, by decreasing number of A words
     // (heaviest items first)
     P.nb = pl.tc_nb;
+    P.m = pl.m;
+    P.n = pl.n;
     P.b_wpad = pl.B_wpad;
     P.b_wstride = pl.B_wstride * kTileBytes;
     P.b_kstride = pl.B_kstride * kTileBytes;

@@ -38,7 +38,9 @@ struct TcItem {
     int64_t A_rows, B_rows, nkb, kb0, nkbc, mt, nt;
     int64_t plane;           // int32 elements between the S planes of consecutive diagonals
     int64_t b_wstride, b_kstride;  // bytes between consecutive B words / k-blocks
-    int32_t s0, ndiag, nb, i0, ni, v, b_wpad, pad0;
+    int32_t s0, ndiag, nb, i0, ni, v, b_wpad;
+    int32_t rv, cv;          // rows of the tile inside m, columns of each diagonal block inside n
+    int32_t pad0;
 };
 
 struct Plan {

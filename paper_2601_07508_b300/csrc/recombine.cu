@@ -111,15 +111,25 @@ __global__ void __launch_bounds__(256) recombine_kernel(const __grid_constant__ 
     recombine_rows(P, ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4, blockIdx.y, gridDim.y);
 }
 
-// Batched: block b handles 1024 columns of rows [y0, y0 + 8) of problem
-// jobs[b] = (problem, y0, column block, 0).
+// Batched: block b handles columns [1024 z, 1024 z + 1024) of rows
+// [y0, y0 + 8) of problem jobs[b] = (problem, y0, z, 0); its threads take the
+// (row, 4-column group) units of that block in turn, so narrow problems keep
+// every thread busy.
 __global__ void __launch_bounds__(256) recombine_batched_kernel(const RecParams *probs, const int4 *jobs) {
-    __shared__ RecParams P;  // staged once: the loops read it many times
+    __shared__ __align__(16) RecParams P;  // staged once (all threads copy): the loops read it many times
     const int4 j = jobs[blockIdx.x];
-    if (threadIdx.x == 0) P = probs[j.x];
+    {
+        const uint32_t *src = reinterpret_cast<const uint32_t *>(probs + j.x);
+        uint32_t *dst = reinterpret_cast<uint32_t *>(&P);
+        for (int w = threadIdx.x; w < (int)(sizeof(RecParams) / 4); w += blockDim.x) dst[w] = src[w];
+    }
     __syncthreads();
-    const int64_t c0 = ((int64_t)j.z * blockDim.x + threadIdx.x) * 4;
-    for (int64_t r = j.y; r < j.y + 8 && r < P.m; ++r) recombine_rows(P, c0, r, P.m);
+    const int64_t cb = (int64_t)j.z * 1024;
+    const int64_t width = P.n - cb < 1024 ? P.n - cb : 1024;
+    const int64_t rows = P.m - j.y < 8 ? P.m - j.y : 8;
+    const int64_t groups = (width + 3) / 4;
+    for (int64_t u = threadIdx.x; u < rows * groups; u += blockDim.x)
+        recombine_rows(P, cb + (u % groups) * 4, j.y + u / groups, P.m);
 }
 
 RecParams make_rec_params(const Plan &pl, const int32_t *S, uint64_t *C, int64_t ldc) {

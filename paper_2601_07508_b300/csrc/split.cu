@@ -188,9 +188,13 @@ __global__ void __launch_bounds__(256) split_int8_kernel(const __grid_constant__
 __global__ void __launch_bounds__(256) split_batched_kernel(const SplitParams *jobs, const int4 *blocks,
                                                             int fp64) {
     __shared__ uint64_t tile[kST][kST + 1];
-    __shared__ SplitParams P;  // staged once: the loops read it many times
+    __shared__ __align__(16) SplitParams P;  // staged once (all threads copy): the loops read it many times
     const int4 bl = blocks[blockIdx.x];
-    if (threadIdx.x == 0) P = jobs[bl.x];
+    {
+        const uint32_t *src = reinterpret_cast<const uint32_t *>(jobs + bl.x);
+        uint32_t *dst = reinterpret_cast<uint32_t *>(&P);
+        for (int w = threadIdx.x; w < (int)(sizeof(SplitParams) / 4); w += blockDim.x) dst[w] = src[w];
+    }
     __syncthreads();
     if (fp64) split_fp64_tile(P, tile, bl.y, bl.z);
     else split_int8_tile(P, tile, bl.y, bl.z);
