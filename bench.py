@@ -465,10 +465,12 @@ def run_variant_sweep(dev, size=2048):
     return out
 
 
-def run_serve(dev, nreq, pool, budget=40 << 30):
+def run_serve(dev, nreq, pool, budget=40 << 30, ring=4):
     """Poisson stream of requests (m, n, k log-uniform in [64, 4096], bitsize
-    uniform in [20, 52], seed 5) against a 40 GB budget; the rate is 0.8 x the
-    closed-loop saturation throughput measured first."""
+    uniform in [20, 52], seed 5) against a 40 GB budget, at 0.8 x and 0.5 x the
+    closed-loop saturation throughput measured first.  Requests cycle through
+    `pool` operand sets; each set has `ring` output buffers, so a request waits
+    for an earlier one only when it reuses that output buffer."""
     import torch
     from paper_2601_07508_b300 import mwmm
     spec = inputs.serve_requests(count=pool)
@@ -477,19 +479,19 @@ def run_serve(dev, nreq, pool, budget=40 << 30):
         A, B = inputs.problem(5000 + i, m, n, k, p)
         tA = torch.from_numpy(A.view(np.int64)).to(dev)
         tB = torch.from_numpy(B.view(np.int64)).to(dev)
-        tC = torch.empty((m, n), dtype=torch.int64, device=dev)
-        ents.append((tA, tB, tC, p, mwmm._problems([(tA, tB, tC, p)])[0], 2.0 * m * n * k))
+        outs = [torch.empty((m, n), dtype=torch.int64, device=dev) for _ in range(ring)]
+        ents.append((tA, tB, outs, [mwmm._problems([(tA, tB, c, p)])[0] for c in outs]))
     torch.cuda.synchronize()
     srv = mwmm.Server(budget, max_inflight=3, max_batch=64)
-    last = [0] * pool
+    last = {}
 
     def stream(count, arrivals):
         t0 = srv.now()
         tickets = []
         for i in range(count):
-            e = i % pool
-            if last[e]:
-                mwmm.mwmm_serve_wait(srv.handle, last[e], 120000)
+            e, slot = i % pool, (i // pool) % ring
+            if last.get((e, slot)):
+                mwmm.mwmm_serve_wait(srv.handle, last[(e, slot)], 120000)
             if arrivals is not None:
                 target = t0 + arrivals[i]
                 while srv.now() < target:
@@ -497,9 +499,9 @@ def run_serve(dev, nreq, pool, budget=40 << 30):
                 ta = target
             else:
                 ta = -1.0
-            st, tk = mwmm.mwmm_serve_submit_ptr(srv.handle, ents[e][4], ta)
+            st, tk = mwmm.mwmm_serve_submit_ptr(srv.handle, ents[e][3][slot], ta)
             assert st == 0, st
-            last[e] = tk
+            last[(e, slot)] = tk
             tickets.append(tk)
         for tk in tickets:
             assert mwmm.mwmm_serve_wait(srv.handle, tk, 300000) == 0
@@ -509,22 +511,26 @@ def run_serve(dev, nreq, pool, budget=40 << 30):
     nsat = min(nreq, 4 * pool)
     sat = stream(nsat, None)
     sat_rps = sat["completed"] / sat["busy_s"]
-    srv.reset_stats()
-    rate = 0.8 * sat_rps
-    arrivals = inputs.poisson_arrivals(5, nreq, rate)
-    rep = stream(nreq, arrivals)
+    out = {"workload": "%d requests per rate, Poisson arrivals at 0.8 x and 0.5 x saturation, m, n, k log-uniform "
+                       "in [64, 4096], p a random prime of bitsize uniform in [20, 52], seed 5; operands cycle "
+                       "through %d device-resident sets with %d output buffers each; 40 GB budget; INT8-word "
+                       "form; 3 streams, <= 64 requests per batch" % (nreq, pool, ring),
+           "saturation_requests_per_s": sat_rps, "saturation_gops": sat["gops"]}
+    for frac, key in ((0.8, "at_0.8"), (0.5, "at_0.5")):
+        srv.reset_stats()
+        rate = frac * sat_rps
+        arrivals = inputs.poisson_arrivals(5 if frac == 0.8 else 6, nreq, rate)
+        rep = stream(nreq, arrivals)
+        out[key] = {"rate_requests_per_s": rate, "p50_ms": rep["p50_ms"], "p99_ms": rep["p99_ms"],
+                    "mean_ms": rep["mean_ms"], "max_ms": rep["max_ms"], "gops": rep["gops"],
+                    "completed": rep["completed"], "rejected": rep["rejected"], "batches": rep["batches"],
+                    "mean_batch": rep["mean_batch"], "peak_inflight_batches": rep["peak_inflight"],
+                    "peak_queue": rep["peak_queue"], "peak_workspace_gb": rep["peak_bytes"] / 1e9,
+                    "budget_gb": rep["budget_bytes"] / 1e9}
     srv.close()
-    return {"workload": "%d requests, Poisson arrivals at 0.8 x saturation, m, n, k log-uniform in [64, 4096], "
-                        "p a random prime of bitsize uniform in [20, 52], seed 5; operands cycle through %d "
-                        "device-resident sets; 40 GB budget; INT8-word form; 3 streams, <= 64 requests per batch"
-                        % (nreq, pool),
-            "saturation_requests_per_s": sat_rps, "saturation_gops": sat["gops"],
-            "rate_requests_per_s": rate, "p50_ms": rep["p50_ms"], "p99_ms": rep["p99_ms"],
-            "mean_ms": rep["mean_ms"], "max_ms": rep["max_ms"], "gops": rep["gops"],
-            "completed": rep["completed"], "rejected": rep["rejected"], "batches": rep["batches"],
-            "mean_batch": rep["mean_batch"], "peak_inflight_batches": rep["peak_inflight"],
-            "peak_queue": rep["peak_queue"], "peak_workspace_gb": rep["peak_bytes"] / 1e9,
-            "budget_gb": rep["budget_bytes"] / 1e9}
+    # the headline serve figures: the 0.8 x rate
+    out.update({k: out["at_0.8"][k] for k in ("p50_ms", "p99_ms", "gops", "rate_requests_per_s")})
+    return out
 
 
 # ----------------------------------------------------------------------------- main arm

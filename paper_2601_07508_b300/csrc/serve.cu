@@ -6,8 +6,13 @@
 //   1. retires finished batches (event query): their requests complete, their
 //      workspace returns to the arena, waiters are woken;
 //   2. while fewer than max_inflight batches are on the GPU, forms a batch from
-//      the head of the FIFO queue: a request joins if its workspace fits in the
-//      arena now (admission against the memory budget) and the batch has room,
+//      the head of the FIFO queue: the head request always, then later queued
+//      requests (in arrival order, within the first kScan) whose word-product
+//      work is at most kCostRatio times the head's -- all requests of a batch
+//      complete together, so a small request is not held back by a much larger
+//      batch-mate; a skipped large request heads a batch of its own next.  A
+//      request joins if its workspace fits in the arena now (admission against
+//      the memory budget) and the batch has room,
 //      then builds the batch's tables, copies them to the device and launches
 //      the batched kernels on the next of its streams -- so requests that
 //      arrive while other batches run are admitted as memory frees up, and
@@ -36,6 +41,8 @@ using mwmm::Plan;
 namespace {
 
 constexpr uint64_t kStagingBytes = 32ull << 20;  // pinned table staging per stream
+constexpr int kScan = 512;                         // queued requests a batch formation looks at
+constexpr double kCostRatio = 4.0;                 // batch-mates do at most this much more work than the head
 
 uint64_t align256(uint64_t x) { return (x + 255) & ~uint64_t(255); }
 
@@ -181,11 +188,18 @@ bool launch_one(mwmm_server_s *S, std::unique_lock<std::mutex> &lock) {
             break;
         }
     if (slot < 0) return false;
-    // admission: FIFO head first, while the workspace fits the arena
+    // admission: FIFO head first, then similar-sized requests, while the
+    // workspace fits the arena
     std::vector<uint64_t> tickets;
     uint64_t table_est = 0;
-    while (!S->queue.empty() && (int)tickets.size() < S->max_batch) {
-        Request &r = *S->reqs[S->queue.front()];
+    auto work = [](const Request &r) { return (double)r.plan.u * r.plan.v * r.flops; };
+    const double cap = kCostRatio * work(*S->reqs[S->queue.front()]);
+    for (size_t qi = 0; qi < S->queue.size() && (int)qi < kScan && (int)tickets.size() < S->max_batch;) {
+        Request &r = *S->reqs[S->queue[qi]];
+        if (!tickets.empty() && work(r) > cap) {  // too large for this batch: it waits for its own
+            ++qi;
+            continue;
+        }
         const uint64_t est = 4096 + 96 * (uint64_t)(r.plan.A_rows / 64 + 1) * (r.plan.nkb + 1) * 2 +
                              128 * (uint64_t)r.plan.nsums * r.plan.nkc * (r.plan.A_rows / 128 + 1) *
                                  (r.plan.B_rows / 256 + 1);
@@ -195,8 +209,8 @@ bool launch_one(mwmm_server_s *S, std::unique_lock<std::mutex> &lock) {
         r.ws_off = off;
         r.ws_bytes = r.plan.ws_bytes;
         r.state = 1;
-        tickets.push_back(S->queue.front());
-        S->queue.pop_front();
+        tickets.push_back(S->queue[qi]);
+        S->queue.erase(S->queue.begin() + (long)qi);
         table_est += est;
     }
     if (tickets.empty()) return false;
