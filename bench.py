@@ -193,6 +193,32 @@ def oracle_sample(bits, size, seconds, rank_seed=0):
             "seconds": t}, rows
 
 
+# ----------------------------------------------------------------------------- ranks
+# The path shards by independent problems: every rank runs the whole sweep on
+# its own GPU with its own seeds; the only collectives are the timing
+# barrier and the maximum of the elapsed times (harness, not data path).
+
+def rank_seed(rank: int) -> int:
+    """Seed offset of a rank's problems (independent problems per rank)."""
+    return 1000 * rank
+
+
+def max_over_ranks(x: float, dist, device) -> float:
+    """The largest of the ranks' values (the job's elapsed time)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(ops_per_rank_step: float, steps: int, world: int, seconds: float) -> float:
+    """Whole-job rate in G-units per second: every rank did `steps` steps of
+    `ops_per_rank_step` units within `seconds` (the slowest rank's time)."""
+    return ops_per_rank_step * steps * world / seconds / 1e9
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -553,7 +579,7 @@ def main():
     dev = torch.device("cuda", torch.cuda.current_device())
     bits = [int(x) for x in args.bits.split(",")]
     n = args.size
-    seed_off = 1000 * rank
+    seed_off = rank_seed(rank)
 
     # CPU baseline first (before any GPU work; rank 0 at N = 1 only)
     cpu_baseline = None
@@ -605,16 +631,12 @@ def main():
     if dist:
         dist.barrier()
     clocks = sampler.stop()
-    ms = e0.elapsed_time(e1)
-    if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(e0.elapsed_time(e1), dist, dev)
     for pl in plans:
         assert pl.check() == 0, "device-side error in the timed region"
 
     flop_per_step = 2.0 * n * n * n * len(bits)
-    value = flop_per_step * args.steps * world / (ms / 1e3) / 1e9
+    value = job_rate(flop_per_step, args.steps, world, ms / 1e3)
 
     # per-bitsize phases of the INT8 form (CUDA events on the launching stream)
     per_bits, launches = {}, 0
@@ -739,12 +761,8 @@ def main():
         t0 = time.perf_counter()
         for _ in range(esteps):
             host_step()
-        dt = time.perf_counter() - t0
-        if dist:
-            t = torch.tensor([dt], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            dt = float(t.item())
-        e2e = {"value": flop_per_step * esteps * world / dt / 1e9, "unit": "GOP/s",
+        dt = max_over_ranks(time.perf_counter() - t0, dist, dev)
+        e2e = {"value": job_rate(flop_per_step, esteps, world, dt), "unit": "GOP/s",
                "h2d_bytes_per_step": 2 * n * n * 8 * len(bits), "d2h_bytes_per_step": n * n * 8 * len(bits),
                "steps": esteps,
                "api": "mwmm_matmul_host_async on one stream per product, then mwmm_plan_check (pinned host buffers)"}
