@@ -103,9 +103,11 @@ typedef struct {
                          two CTAs sharing each B tile through TMA multicast
                          (bit-exact, measured 2-3% slower on B300);
                          0 or 1 = lone CTAs (default) */
-    int32_t f64_concat; /* FP64 form: 0 = concatenate B's words along n (Alg. 6)
-                         when 2 <= v <= 4 and n < 64, 1 = never, 2 = always
-                         (needs 2 <= v <= 4) */
+    int32_t f64_concat; /* FP64 form, Alg. 6: 0 = automatic (when min(m, n) < 64,
+                         concatenate the words of the narrower side: B's
+                         along n when n <= m and 2 <= v <= 4, else A's along m
+                         when 2 <= u <= 4), 1 = never, 2 = B's words
+                         (needs 2 <= v <= 4), 3 = A's words (2 <= u <= 4) */
     int32_t ksplit;     /* FP64 form: K ranges computed by separate CTAs and
                          added mod p afterwards, 1..64 (0: chosen so that the
                          last wave of CTAs is nearly full) */
@@ -141,7 +143,8 @@ typedef struct {
      *     B_off + ((kb * (v + 2 B_wpad) + w + B_wpad) * B_rows + r) * 128
      * (words -B_wpad .. -1 and v .. v + B_wpad - 1 are all zero).
      * FP64 form with f64_concat = 1, for B: k-block major without padding,
-     *   chunk(word w, k-block kb, row r) at B_off + ((kb * v + w) * B_rows + r) * 128.
+     *   chunk(word w, k-block kb, row r) at B_off + ((kb * v + w) * B_rows + r) * 128;
+     * with f64_concat = 2 the same for A: A_off + ((kb * u + w) * A_rows + r) * 128.
      * Inside a chunk the 16-byte granule g (elements g*E .. g*E+E-1 of the
      * k-block, E = 16 / element size) is stored at granule position
      * g ^ (r mod 8).  Element type: double (FP64 form, kb_elems = 16) or
@@ -154,7 +157,7 @@ typedef struct {
     int32_t tc_cluster;     /* INT8: CTAs per cluster of the one-CTA kernel (2: A_rows % 256 == 0) */
     uint64_t A_off, B_off, S_off;
     uint64_t workspace_bytes;
-    int32_t f64_concat;     /* FP64: 1 when B's words are concatenated along n (Alg. 6) */
+    int32_t f64_concat;     /* FP64: 1 when B's words are concatenated along n, 2 when A's along m (Alg. 6) */
     int32_t ksplit;         /* FP64: K ranges (1: none) */
     double tuned_ms;        /* mwmm_plan_autotuned: measured time of the chosen configuration (0: not tuned) */
     int32_t tuned_tried;    /* candidates timed (0 when the choice came from the cache) */

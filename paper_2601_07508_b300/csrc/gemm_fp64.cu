@@ -21,7 +21,10 @@
 // when n is 32 or 16.  B's words are then stored k-block major so the slots of
 // one k-block are adjacent.  A thread owns columns tx + 16 c, i.e. word slot
 // (tx + 16 c) / w; after scaling each T_ij by gamma_ij it adds up its own
-// columns of the same output column (no data exchange).
+// columns of the same output column (no data exchange).  When m is the narrow
+// side, the A words are concatenated instead ([A_0; ...; A_{u-1}] B_j, Sec.
+// 3.2): the 64 rows of a tile hold u slots of w rows, and a thread adds up its
+// rows ty + 16 r of the same output row.
 //
 // K ranges (plan ksplit > 1): grid z splits the k-blocks so that narrow or
 // small products still fill the GPU; each range writes its partial C (already
@@ -48,8 +51,9 @@ struct F64Params {
     int64_t ldc, m, n, nkb, A_rows, B_rows, lambda;
     int64_t kbr;                   // k-blocks per K range
     int64_t b_wstride, b_kstride;  // B layout: rows between consecutive words / k-blocks
+    int64_t a_wstride, a_kstride;  // A layout: the same for A
     uint64_t *part;                // ksplit > 1: partial C of range z at part + z m n (row stride n)
-    int u, v, big_p, concat, w;
+    int u, v, big_p, concat, w;  // concat: 0 none, 1 B words, 2 A words (slots of w)
     double p, q;
     double gamma[kMaxWords * kMaxWords];
     double gamma26[kMaxWords * kMaxWords];
@@ -62,9 +66,9 @@ __device__ __forceinline__ double lds_word(const uint8_t *tile, int r, int kk) {
                                              ((kk & 1) << 3));
 }
 
-// One output tile (row tile `row0`, column tile `ct`) over K range z of the
+// One output tile (row tile `rt`, column tile `ct`) over K range z of the
 // product described by P.
-__device__ __forceinline__ void fp64_tile(const F64Params &P, int64_t row0, int64_t ct, int64_t z, uint8_t *smem,
+__device__ __forceinline__ void fp64_tile(const F64Params &P, int64_t rt, int64_t ct, int64_t z, uint8_t *smem,
                                           uint64_t *full) {
     uint8_t *sA = smem;
     uint8_t *sB = smem + STAGES * kTileA;
@@ -73,9 +77,12 @@ __device__ __forceinline__ void fp64_tile(const F64Params &P, int64_t row0, int6
     const int tx = tid & 15, ty = tid >> 4;
     const int64_t kb0 = z * P.kbr;
     const int64_t kbn = P.nkb - kb0 < P.kbr ? P.nkb - kb0 : P.kbr;
-    const int npairs = P.concat ? P.u : P.u * P.v;  // concatenated: one product per A word
-    const int64_t total = (int64_t)npairs * kbn;      // virtual k-blocks: (pair, kb)
-    const int64_t col0 = P.concat ? ct * P.w : ct * BN;  // first output column
+    const bool catB = P.concat == 1, catA = P.concat == 2;
+    // concatenated: one product per A word (B concatenated) or per B word (A concatenated)
+    const int npairs = catB ? P.u : catA ? P.v : P.u * P.v;
+    const int64_t total = (int64_t)npairs * kbn;  // virtual k-blocks: (pair, kb)
+    const int64_t col0 = catB ? ct * P.w : ct * BN;  // first output column
+    const int64_t row0 = catA ? rt * P.w : rt * BM;  // first output row
 
     if (tid == 0) {
         for (int s = 0; s < STAGES; ++s) mbar_init(&full[s], 1);
@@ -87,10 +94,24 @@ __device__ __forceinline__ void fp64_tile(const F64Params &P, int64_t row0, int6
         const int slot = (int)(vb % STAGES);
         const int pair = (int)(vb / kbn);
         const int64_t kb = kb0 + vb % kbn;
-        const int i = P.concat ? pair : pair / P.v;
-        const uint8_t *a = P.Aw + (((int64_t)i * P.nkb + kb) * P.A_rows + row0) * kTileBytes;
         uint8_t *dst = sB + slot * kTileB;
-        if (!P.concat) {
+        if (catA) {  // A slots i = 0 .. u-1 of w rows each, then the B word j = pair
+            const uint32_t wbytes = (uint32_t)P.w * kTileBytes;
+            const uint8_t *a = P.Aw + (kb * P.a_kstride + row0) * kTileBytes;
+            const uint8_t *b = P.Bw + (pair * P.b_wstride + kb * P.b_kstride + col0) * kTileBytes;
+            mbar_arrive_expect_tx(&full[slot], (uint32_t)P.u * wbytes + kTileB);
+            uint8_t *da = sA + slot * kTileA;
+            if (P.A_rows == P.w) {  // one row tile: the u slots are adjacent
+                bulk_g2s(da, a, (uint32_t)P.u * wbytes, &full[slot]);
+            } else {
+                for (int i = 0; i < P.u; ++i) bulk_g2s(da + i * wbytes, a + i * P.a_wstride * kTileBytes, wbytes, &full[slot]);
+            }
+            bulk_g2s(dst, b, kTileB, &full[slot]);
+            return;
+        }
+        const int i = catB ? pair : pair / P.v;
+        const uint8_t *a = P.Aw + (i * P.a_wstride + kb * P.a_kstride + row0) * kTileBytes;
+        if (!catB) {
             const int j = pair % P.v;
             const uint8_t *b = P.Bw + (j * P.b_wstride + kb * P.b_kstride + col0) * kTileBytes;
             mbar_arrive_expect_tx(&full[slot], kTileA + kTileB);
@@ -161,14 +182,15 @@ __device__ __forceinline__ void fp64_tile(const F64Params &P, int64_t row0, int6
         if (kb == kbn - 1) {  // word pair(s) complete: recombine (Alg. 5 / Alg. 6 with Alg. 2)
             const int pair = (int)(vb / kbn);
 #pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                // gamma index i v + j: j from the column's word slot when concatenated
-                const int j = P.concat ? (tx + 16 * c) / P.w : 0;
-                if (j >= P.v) continue;  // unused slot
-                const int gi = P.concat ? pair * P.v + j : pair;
-                const double g = P.gamma[gi], g26 = P.gamma26[gi];
+            for (int r = 0; r < 4; ++r) {
 #pragma unroll
-                for (int r = 0; r < 4; ++r) {
+                for (int c = 0; c < 4; ++c) {
+                    // gamma index i v + j: i or j from the row's / column's word slot when concatenated
+                    const int i = catA ? (ty + 16 * r) / P.w : catB ? pair : pair / P.v;
+                    const int j = catB ? (tx + 16 * c) / P.w : catA ? pair : pair % P.v;
+                    if (i >= P.u || j >= P.v) continue;  // unused slot
+                    const int gi = i * P.v + j;
+                    const double g = P.gamma[gi], g26 = P.gamma26[gi];
                     const double T = fmod_alg1(acc[r][c], p, q);
                     double e;
                     if (gi == 0) e = T;  // gamma_00 = 1
@@ -189,7 +211,33 @@ __device__ __forceinline__ void fp64_tile(const F64Params &P, int64_t row0, int6
         out = P.part + z * P.m * P.n;
         ld = P.n;
     }
-    if (P.concat) {
+    if (catA) {
+        // row ty + 16 r is output row (ty + 16 r) mod w of word slot
+        // (ty + 16 r) / w; add the slots of each output row (w = 32: r and
+        // r + 2; w = 16: all four)
+        const bool two = P.w == 32;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int64_t col = col0 + tx + 16 * c;
+            if (col >= P.n) continue;
+            double s0 = 0.0, s1 = 0.0;
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                if ((ty + 16 * r) / P.w >= P.u) continue;
+                if (two && (r & 1)) {
+                    s1 = __dadd_rn(s1, cres[r][c]);
+                    if (s1 >= p) s1 = __dsub_rn(s1, p);
+                } else {
+                    s0 = __dadd_rn(s0, cres[r][c]);
+                    if (s0 >= p) s0 = __dsub_rn(s0, p);
+                }
+            }
+            if (row0 + ty < P.m) out[(row0 + ty) * ld + col] = (uint64_t)s0;
+            if (two && row0 + ty + 16 < P.m) out[(row0 + ty + 16) * ld + col] = (uint64_t)s1;
+        }
+        return;
+    }
+    if (catB) {
         // column tx + 16 c is output column (tx + 16 c) mod w of word slot
         // (tx + 16 c) / w; add the slots of each output column (w = 32: c and
         // c + 2; w = 16: all four)
@@ -246,7 +294,7 @@ __global__ void fp64_range_sum_kernel(const uint64_t *part, int ranges, int64_t 
 __global__ void __launch_bounds__(THREADS) gemm_fp64_kernel(const __grid_constant__ F64Params P) {
     extern __shared__ __align__(1024) uint8_t smem[];
     __shared__ __align__(8) uint64_t full[STAGES];
-    fp64_tile(P, (int64_t)blockIdx.y * BM, blockIdx.x, blockIdx.z, smem, full);
+    fp64_tile(P, blockIdx.y, blockIdx.x, blockIdx.z, smem, full);
 }
 
 // Batched: block b computes tile (row block y, col tile x) over K range z of
@@ -255,7 +303,7 @@ __global__ void __launch_bounds__(THREADS) gemm_fp64_batched_kernel(const F64Par
     extern __shared__ __align__(1024) uint8_t smem[];
     __shared__ __align__(8) uint64_t full[STAGES];
     const int4 j = jobs[blockIdx.x];
-    fp64_tile(probs[j.x], (int64_t)j.y * BM, j.z, j.w, smem, full);
+    fp64_tile(probs[j.x], j.y, j.z, j.w, smem, full);
 }
 
 F64Params make_f64_params(const Plan &pl, const void *Aw, const void *Bw, uint64_t *C, int64_t ldc, int *err) {
@@ -273,6 +321,8 @@ F64Params make_f64_params(const Plan &pl, const void *Aw, const void *Bw, uint64
     P.kbr = pl.kbr;
     P.b_wstride = pl.B_wstride;
     P.b_kstride = pl.B_kstride;
+    P.a_wstride = pl.A_wstride;
+    P.a_kstride = pl.A_kstride;
     P.part = nullptr;
     P.u = pl.u;
     P.v = pl.v;
@@ -289,7 +339,8 @@ F64Params make_f64_params(const Plan &pl, const void *Aw, const void *Bw, uint64
     return P;
 }
 
-int64_t col_tiles(const Plan &pl) { return pl.f64_concat ? pl.B_rows / pl.f64_w : pl.B_rows / BN; }
+int64_t col_tiles(const Plan &pl) { return pl.f64_concat == 1 ? pl.B_rows / pl.f64_w : pl.B_rows / BN; }
+int64_t row_tiles(const Plan &pl) { return pl.f64_concat == 2 ? pl.A_rows / pl.f64_w : pl.A_rows / BM; }
 
 }  // namespace
 
@@ -310,7 +361,7 @@ void fp64_job(const Plan &pl, const void *Aw, const void *Bw, uint64_t *C, int64
               int index, std::vector<int> &jobs) {
     const F64Params P = make_f64_params(pl, Aw, Bw, C, ldc, err);
     std::memcpy(rec, &P, sizeof(P));
-    for (int64_t y = 0; y < pl.A_rows / BM; ++y)
+    for (int64_t y = 0; y < row_tiles(pl); ++y)
         for (int64_t x = 0; x < col_tiles(pl); ++x) {
             jobs.push_back(index);
             jobs.push_back((int)y);
@@ -340,8 +391,8 @@ int launch_gemm_fp64(const Plan &pl, const void *Aw, const void *Bw, uint64_t *C
     const int smem = STAGES * (kTileA + kTileB);
     cudaError_t e = set_smem_attr(reinterpret_cast<const void *>(gemm_fp64_kernel), smem);
     if (e != cudaSuccess) return (int)e;
-    if (pl.A_rows / BM > 65535) return (int)cudaErrorInvalidConfiguration;  // grid y limit: m <= 4194240
-    dim3 grid((unsigned)col_tiles(pl), (unsigned)(pl.A_rows / BM), (unsigned)pl.ksplit);
+    if (row_tiles(pl) > 65535) return (int)cudaErrorInvalidConfiguration;  // grid y limit: m <= 4194240
+    dim3 grid((unsigned)col_tiles(pl), (unsigned)row_tiles(pl), (unsigned)pl.ksplit);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     gemm_fp64_kernel<<<grid, THREADS, smem, s>>>(P);
     e = cudaGetLastError();

@@ -56,9 +56,9 @@ struct Plan {
     double gamma[kMaxWords * kMaxWords] = {};
     double gamma26[kMaxWords * kMaxWords] = {};  // gamma * 2^26 mod p
     int big_p = 0;                               // p > 2^52 / 3: split Alg. 2
-    int f64_concat = 0;  // 1: B words concatenated along n (Alg. 6)
-    int f64_vs = 1;      // word slots per 64-column tile (2 or 4 when concatenated)
-    int f64_w = 64;      // output columns per tile (64 / f64_vs)
+    int f64_concat = 0;  // 1: B words concatenated along n, 2: A words along m (Alg. 6)
+    int f64_vs = 1;      // word slots per 64-wide tile side (2 or 4 when concatenated)
+    int f64_w = 64;      // output columns (B) or rows (A) per tile: 64 / f64_vs
     int ksplit = 1;      // K ranges of the FP64 kernel (partial results summed mod p)
     int64_t kbr = 0;     // k-blocks per K range
     // CRT form (MWMM_FORM_CRT8): moduli m_i, y_i = (M / m_i)^-1 mod m_i,
@@ -86,6 +86,10 @@ struct Plan {
     // B_wstride = B_rows, B_kstride = (v + 2 B_wpad) * B_rows.
     int64_t B_wstride = 0, B_kstride = 0;
     int B_wpad = 0;
+    // A word layout: chunk(word w, k-block kb, row r) at
+    // (w A_wstride + kb A_kstride + r) * 128; k-block major (A_wstride =
+    // A_rows, A_kstride = u A_rows) only for the FP64 form with A concatenated
+    int64_t A_wstride = 0, A_kstride = 0;
     uint64_t A_off = 0, B_off = 0, S_off = 0, ws_bytes = 0;
     // owned device resources (lazily created)
     int device = -1;

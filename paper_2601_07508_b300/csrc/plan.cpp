@@ -195,30 +195,43 @@ mwmm_status make_plan(Plan *pl, int64_t m, int64_t n, int64_t k, uint64_t p, int
         P.big_p = (u128)3 * (p - 1) * (p - 1) > ((u128)p << 52);
         P.kb_elems = kF64KB;
         P.nkb = ceil_div(k, kF64KB);
-        P.A_rows = round_up(m > 0 ? m : 1, kF64BM);
         // Alg. 6: concatenate B's words along n when n is narrow (a 64-column
         // tile then holds v word slots of 64 / f64_vs columns instead of one
-        // mostly empty word); at most 4 slots.
-        if (o.f64_concat < 0 || o.f64_concat > 2) return MWMM_ERR_ARG;
-        bool concat = o.f64_concat == 2 || (o.f64_concat == 0 && v >= 2 && n < kF64BN);
-        if (concat && (v > 4 || v < 2)) {
-            if (o.f64_concat == 2) return MWMM_ERR_ARG;
-            concat = false;
+        // mostly empty word), or A's words along m when m is the narrow side
+        // (Sec. 3.2: concatenate the side whose outer dimension is smaller);
+        // at most 4 slots.
+        if (o.f64_concat < 0 || o.f64_concat > 3) return MWMM_ERR_ARG;
+        int side = 0;  // 1: B, 2: A
+        if (o.f64_concat == 2) side = 1;
+        if (o.f64_concat == 3) side = 2;
+        if (o.f64_concat == 0 && (m < kF64BM || n < kF64BN)) {
+            if (n <= m && v >= 2 && v <= 4) side = 1;
+            else if (m < n && u >= 2 && u <= 4) side = 2;
         }
-        P.f64_concat = concat ? 1 : 0;
-        P.f64_vs = concat ? (v <= 2 ? 2 : 4) : 1;
+        const int words = side == 1 ? v : u;
+        if (side && (words < 2 || words > 4)) return MWMM_ERR_ARG;
+        P.f64_concat = side;
+        P.f64_vs = side ? (words <= 2 ? 2 : 4) : 1;
         P.f64_w = kF64BN / P.f64_vs;
-        P.B_rows = round_up(n > 0 ? n : 1, P.f64_w);
-        if (concat) {  // k-block major: the word slots of one k-block are adjacent
+        P.A_rows = round_up(m > 0 ? m : 1, side == 2 ? P.f64_w : kF64BM);
+        P.B_rows = round_up(n > 0 ? n : 1, side == 1 ? P.f64_w : kF64BN);
+        if (side == 1) {  // k-block major: the word slots of one k-block are adjacent
             P.B_wstride = P.B_rows;
             P.B_kstride = (int64_t)v * P.B_rows;
         } else {
             P.B_wstride = P.nkb * P.B_rows;
             P.B_kstride = P.B_rows;
         }
+        if (side == 2) {
+            P.A_wstride = P.A_rows;
+            P.A_kstride = (int64_t)u * P.A_rows;
+        } else {
+            P.A_wstride = P.nkb * P.A_rows;
+            P.A_kstride = P.A_rows;
+        }
         // K ranges: enough CTAs that the last wave is nearly full.  The
         // planner is device independent and assumes 148 SMs x 2 resident CTAs.
-        const int64_t tiles = (P.A_rows / kF64BM) * (P.B_rows / P.f64_w);
+        const int64_t tiles = (P.A_rows / (side == 2 ? P.f64_w : kF64BM)) * (P.B_rows / (side == 1 ? P.f64_w : kF64BN));
         const int64_t smax = std::max<int64_t>(1, std::min<int64_t>(64, P.nkb / 8));
         int64_t ks = 1;
         if (o.ksplit != 0) {
@@ -293,6 +306,8 @@ mwmm_status make_plan(Plan *pl, int64_t m, int64_t n, int64_t k, uint64_t p, int
         if (o.tc_cluster < 0 || o.tc_cluster > 2) return MWMM_ERR_ARG;
         P.tc_cluster = (!P.tc_pair && m > kTcBM && o.tc_cluster == 2) ? 2 : 1;
         P.A_rows = round_up(m > 0 ? m : 1, (P.tc_pair || P.tc_cluster == 2) ? 2 * kTcBM : kTcBM);
+        P.A_wstride = P.nkb * P.A_rows;
+        P.A_kstride = P.A_rows;
         P.B_rows = P.tc_nb == kTcBN ? round_up(n > 0 ? n : 1, kTcBN) : P.tc_nb;
         uint64_t abytes = (uint64_t)u * P.nkb * P.A_rows * kTileBytes;
         // Narrow n: B's words k-block major with zero words on both sides, so

@@ -211,8 +211,8 @@ SplitParams make_split_params(const Plan &pl, int side, const uint64_t *M, int64
     P.nkb = pl.nkb;
     P.out = static_cast<uint8_t *>(words);
     P.words = side == 0 ? pl.u : pl.v;
-    P.wstride = side == 0 ? pl.nkb * pl.A_rows : pl.B_wstride;
-    P.kstride = side == 0 ? pl.A_rows : pl.B_kstride;
+    P.wstride = side == 0 ? pl.A_wstride : pl.B_wstride;
+    P.kstride = side == 0 ? pl.A_kstride : pl.B_kstride;
     P.wpad = side == 0 ? 0 : pl.B_wpad;
     P.p = pl.p;
     P.alpha = side == 0 ? pl.alpha : pl.beta;

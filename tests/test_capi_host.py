@@ -164,13 +164,35 @@ def test_fp64_plan_concatenation(M, n, v, opt, want, slots):
     assert d["workspace_bytes"] >= d["B_off"] + v * d["nkb"] * d["B_rows"] * 128
 
 
+@pytest.mark.parametrize("m,n,u,v,opt,want", [
+    (20, 3000, 2, 2, 0, 2),    # m is the narrow side: A's words
+    (20, 3000, 2, 3, 0, 2),
+    (3000, 20, 2, 3, 0, 1),    # n is: B's words
+    (20, 30, 2, 2, 0, 2),      # both narrow: the smaller outer dimension, m
+    (20, 3000, 1, 2, 0, 0),    # one A word: nothing to concatenate on the narrow side
+    (500, 500, 2, 2, 3, 2),    # forced
+])
+def test_fp64_plan_concatenation_side(M, m, n, u, v, opt, want):
+    h = M.mwmm_plan(m, n, 1000, SWEEP[32] if u == 1 else SWEEP[40], u, v, "fp64", f64_concat=opt)
+    d = M.mwmm_plan_info(h)
+    M.mwmm_plan_destroy(h)
+    assert d["f64_concat"] == want
+    if want == 2:
+        w = 64 // (2 if u == 2 else 4)
+        assert d["A_rows"] == -(-m // w) * w
+        assert d["B_off"] >= u * d["nkb"] * d["A_rows"] * 128
+
+
 def test_fp64_plan_concatenation_errors(M):
     for v, p in ((1, SWEEP[20]), (5, SWEEP[20])):
         with pytest.raises(M.MwmmError) as e:
             M.mwmm_plan(100, 20, 100, p, 1, v, "fp64", f64_concat=2)
         assert e.value.status == 1
-    with pytest.raises(M.MwmmError) as e:
+    with pytest.raises(M.MwmmError) as e:  # A concatenation needs 2 <= u <= 4
         M.mwmm_plan(100, 20, 100, SWEEP[32], 1, 2, "fp64", f64_concat=3)
+    assert e.value.status == 1
+    with pytest.raises(M.MwmmError) as e:
+        M.mwmm_plan(100, 20, 100, SWEEP[32], 1, 2, "fp64", f64_concat=4)
     assert e.value.status == 1
 
 

@@ -95,6 +95,28 @@ def test_fp64_concatenated_words_narrow_n(M, oracle, uv, b):
         assert np.array_equal(C2, ref), (m, n, k)
 
 
+@pytest.mark.parametrize("uv", [(2, 2), (2, 3)])
+@pytest.mark.parametrize("b", [32, 40, 52])
+def test_fp64_concatenated_a_words_narrow_m(M, oracle, uv, b):
+    """Alg. 6 with the A words concatenated (the narrow side is m, Sec. 3.2):
+    64-row tiles of 2 word slots, with and without K ranges; equals the
+    plain product and the oracle."""
+    p = SWEEP[b]
+    if oracle.lam(p, *uv) < 1:
+        pytest.skip("variant cannot handle this bitsize")
+    for seed, (m, n, k) in enumerate([(1, 70, 50), (15, 130, 333), (32, 257, 100), (33, 100, 257), (63, 64, 1000)]):
+        A, B = inputs.problem(400 * b + seed, m, n, k, p)
+        ref = oracle.matmul_mod(A, B, p)
+        C, plan = gpu_product(M, A, B, p, form="fp64", u=uv[0], v=uv[1])
+        assert plan.info["f64_concat"] == 2 and plan.info["A_rows"] % 32 == 0
+        assert np.array_equal(C, ref), (m, n, k)
+        C2, plan2 = gpu_product(M, A, B, p, form="fp64", u=uv[0], v=uv[1], ksplit=4)
+        assert plan2.info["f64_concat"] == 2
+        assert np.array_equal(C2, ref), (m, n, k)
+        C3, _ = gpu_product(M, A, B, p, form="fp64", u=uv[0], v=uv[1], f64_concat=1)
+        assert np.array_equal(C3, ref), (m, n, k)
+
+
 @pytest.mark.parametrize("ks", [1, 2, 3, 7, 64])
 def test_fp64_k_ranges(M, oracle, ks):
     """K ranges (grid z) with their partial results added mod p by a second
@@ -350,11 +372,14 @@ def test_validation_reports_entries_out_of_range(M):
 # ------------------------------------------------------------------ single steps
 @pytest.mark.parametrize("form,b,uv,n", [("fp64", 40, (2, 2), 90), ("fp64", 52, (2, 3), 90), ("fp64", 32, (1, 4), 90),
                                          ("fp64", 32, (1, 2), 40), ("fp64", 40, (1, 4), 20), ("fp64", 52, (2, 3), 33),
+                                         ("fp64", 40, (2, 2), 300),
                                          ("int8", 52, None, 290), ("int8", 23, None, 290), ("int8", 52, None, 90),
                                          ("int8", 40, None, 20)])
 def test_split_words_match_oracle(M, oracle, form, b, uv, n):
     p = SWEEP[b]
     m, k = 70, 150
+    if form == "fp64" and n == 300:
+        m = 20  # narrow m: the A words are concatenated (k-block major)
     A, B = inputs.problem(31, m, n, k, p)
     kw = dict(u=uv[0], v=uv[1]) if uv else {}
     plan = M.Plan(m, n, k, p, form=form, **kw)
@@ -366,8 +391,8 @@ def test_split_words_match_oracle(M, oracle, form, b, uv, n):
         buf = torch.full(((words + 2 * wpad) * d["nkb"] * rows_pad * 128,), 0x5A, dtype=torch.uint8, device="cuda")
         M.mwmm_split(plan.handle, side, dev(Mx), buf)
         torch.cuda.synchronize()
-        W = unpack_words(buf.cpu().numpy(), words, d["nkb"], rows_pad, form, wpad,
-                         kmajor=side == 1 and d["f64_concat"] == 1)
+        kmajor = (side == 1 and d["f64_concat"] == 1) or (side == 0 and d["f64_concat"] == 2)
+        W = unpack_words(buf.cpu().numpy(), words, d["nkb"], rows_pad, form, wpad, kmajor=kmajor)
         src = Mx if side == 0 else Mx.T.copy()       # rows x k
         if form == "fp64":
             ref = oracle.split_alpha(src, d["alpha"] if side == 0 else d["beta"], words).astype(np.float64)
