@@ -63,15 +63,23 @@ __device__ __forceinline__ void recombine_rows(const RecParams &P, int64_t c0, i
         for (int64_t row = row0; row < P.m; row += rstep) {
             uint64_t A0[4] = {0, 0, 0, 0}, A1[4] = {0, 0, 0, 0};
             const int32_t *src = P.S + row * P.B_rows + c0;
-            for (int s = 0; s < P.nsums; ++s) {
-                const int4 v = *reinterpret_cast<const int4 *>(src + (int64_t)s * plane);
-                const uint32_t U[4] = {(uint32_t)v.x + 0x80000000u, (uint32_t)v.y + 0x80000000u,
-                                       (uint32_t)v.z + 0x80000000u, (uint32_t)v.w + 0x80000000u};
-                const uint64_t gl = P.gl[s], gh = P.gh[s];
+            // four planes per round: their loads are issued together
+            for (int s0 = 0; s0 < P.nsums; s0 += 4) {
+                int4 v[4];
 #pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    A0[e] += gl * U[e];
-                    A1[e] += gh * U[e];
+                for (int j = 0; j < 4; ++j)
+                    if (s0 + j < P.nsums) v[j] = __ldcs(reinterpret_cast<const int4 *>(src + (int64_t)(s0 + j) * plane));
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    if (s0 + j >= P.nsums) break;
+                    const uint32_t U[4] = {(uint32_t)v[j].x + 0x80000000u, (uint32_t)v[j].y + 0x80000000u,
+                                           (uint32_t)v[j].z + 0x80000000u, (uint32_t)v[j].w + 0x80000000u};
+                    const uint32_t gl = P.gl[s0 + j], gh = P.gh[s0 + j];
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        A0[e] += (uint64_t)gl * U[e];  // 32 x 32 -> 64
+                        A1[e] += (uint64_t)gh * U[e];
+                    }
                 }
             }
             uint64_t *out = P.C + row * P.ldc + c0;
