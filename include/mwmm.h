@@ -10,7 +10,7 @@
  * (Alg. 3, Prop. 2.3, Prop. 3.3), each chunk is reduced mod p (Alg. 1), and
  * the products are recombined with alpha^i beta^j mod p (Alg. 2, Alg. 5).
  *
- * Two forms compute the same, unique result (every output in [0, p)):
+ * Three forms compute the same, unique result (every output in [0, p)):
  *
  *   MWMM_FORM_FP64  the paper's method as stated: FP64 words from Alg. 4
  *                   with alpha = ceil(p^(1/u)), FP64 (DFMA) accumulation with
@@ -31,6 +31,11 @@
  *                   INT32 sums S_s = sum_{i+j=s} A_i B_j, K-chunked so that
  *                   |S_s| < 2^31, and C = sum_s 256^s S_s mod p is
  *                   recombined with exact 64-bit integer arithmetic.
+ *
+ *   MWMM_FORM_CRT8  the multimodular approach the paper compares against
+ *                   (Sec. 5.2), run on the same tensor pipe: residues modulo
+ *                   s primes below 256 instead of digits, one product per
+ *                   modulus, and CRT reconstruction of the integer product.
  *
  * Conventions for every entry point:
  *   - Matrices are row-major uint64 with a leading dimension (in elements)
@@ -170,9 +175,10 @@ typedef struct {
  * u = v = 0 picks the words automatically: FP64 form, the (u,v) of least
  * modelled cost u*v*(1 + 6/lambda) among (1,1),(1,2),(1,3),(1,4),(2,2),(2,3)
  * with lambda >= 1 (Sec. 3.3, Table 1); INT8 form, the fewest digits that
- * represent (p-1)/2.  Explicit (u,v) are validated (FP64: Prop. 3.3 must give
- * lambda >= 1, else MWMM_ERR_BOUND; INT8: u and v must be at least the
- * fewest digits).  Pure host logic: makes no CUDA call and allocates no
+ * represent (p-1)/2; CRT form, the fewest moduli (u = v must be 0 there;
+ * k <= 2^22).  MWMM_FORM_AUTO plans the INT8 form.  Explicit (u,v) are
+ * validated (FP64: Prop. 3.3 must give lambda >= 1, else MWMM_ERR_BOUND;
+ * INT8: u and v must be at least the fewest digits).  Pure host logic: makes no CUDA call and allocates no
  * device memory.  m, n, k >= 0; k may be 0 (C = 0).
  * Errors: MWMM_ERR_ARG, MWMM_ERR_PRIME, MWMM_ERR_BOUND. */
 mwmm_status mwmm_plan(mwmm_plan_t *out, int64_t m, int64_t n, int64_t k, uint64_t p,
@@ -183,8 +189,8 @@ mwmm_status mwmm_plan_info(mwmm_plan_t plan, mwmm_plan_desc *out);
 /* Autotuned plan (no counterpart in the paper's code; the paper picks (u,v)
  * from its cost model and measured crossovers, Sec. 3.3 and Table 4).
  * Times candidate configurations of this product on the current device and
- * returns a plan with the fastest: the form (when form = MWMM_FORM_AUTO;
- * otherwise the given one), (u,v) among the FP64 variants whose block size
+ * returns a plan with the fastest: the form (when form = MWMM_FORM_AUTO:
+ * FP64, INT8 or CRT; otherwise the given one), (u,v) among the FP64 variants whose block size
  * is >= 1 with concatenation on and off where it applies, the tcgen05 tile
  * variant (one CTA, clusters of two, CTA pairs) and the INT32 K-range.  Each
  * candidate runs once to warm up and twice timed (CUDA events on `stream`,

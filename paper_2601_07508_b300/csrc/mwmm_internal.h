@@ -62,11 +62,11 @@ struct Plan {
     int ksplit = 1;      // K ranges of the FP64 kernel (partial results summed mod p)
     int64_t kbr = 0;     // k-blocks per K range
     // CRT form (MWMM_FORM_CRT8): moduli m_i, y_i = (M / m_i)^-1 mod m_i,
-    // w_i = (M / m_i) mod p, W = M mod p, two64 = 2^64 mod p
+    // w_i = (M / m_i) mod p, W = M mod p
     int crt_s = 0;
     uint32_t crt_m[kMaxCrt] = {}, crt_y[kMaxCrt] = {};
     uint64_t crt_w[kMaxCrt] = {};
-    uint64_t crt_W = 0, crt_two64 = 0;
+    uint64_t crt_W = 0;
     // autotuner outcome (0 when the plan was not tuned)
     double tuned_ms = 0;
     int tuned_tried = 0;

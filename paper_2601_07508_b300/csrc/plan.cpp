@@ -128,7 +128,6 @@ static mwmm_status crt_moduli(Plan &P, int64_t k, uint64_t p) {
         P.crt_w[i] = wi;
         P.crt_y[i] = (uint32_t)inv_mod_small(mi_mod, P.crt_m[i]);
     }
-    P.crt_two64 = (uint64_t)(((u128)1 << 64) % p);
     return MWMM_OK;
 }
 
