@@ -10,7 +10,7 @@
 namespace mwmm {
 
 constexpr int kMaxWords = 8;            // u, v <= 8 in the multiword forms
-constexpr int kMaxCrt = 24;             // moduli of the CRT form
+constexpr int kMaxCrt = 24;             // moduli of the CRT form (recombine.cu instantiates 1..24)
 constexpr int kMaxWindows = 32;         // tcgen05 item groups (diagonal windows or moduli)
 constexpr int kTileBytes = 128;         // one k-block row chunk of the word layout
 // FP64 form tiling

@@ -232,6 +232,67 @@ __device__ __forceinline__ uint32_t fastmod(uint32_t a, uint32_t m, uint64_t mag
     return (uint32_t)(u >> 32);
 }
 
+// C mod p from the per-output sums a0 + 2^26 a1 = sum_i x_i w_i and the
+// quotient estimate qf (see above).
+__device__ __forceinline__ void crt_store(const CrtParams &P, const uint64_t (&a0)[4], const uint64_t (&a1)[4],
+                                          const float (&qf)[4], uint64_t *out, int64_t c0) {
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        const uint64_t q = (uint64_t)floorf(qf[e]);  // < 2^13
+        // sum_i x_i w_i = a0 + 2^26 a1, and q W = q Wl + 2^26 q Wh
+        uint64_t lo = reduce_u64(a0[e], P.p, P.mu), hi = reduce_u64(a1[e], P.p, P.mu);
+        const uint64_t qlo = reduce_u64(q * (P.W & ((1u << 26) - 1)), P.p, P.mu);
+        const uint64_t qhi = reduce_u64(q * (P.W >> 26), P.p, P.mu);
+        lo = lo >= qlo ? lo - qlo : lo + P.p - qlo;
+        hi = hi >= qhi ? hi - qhi : hi + P.p - qhi;
+        uint64_t v = lo;
+        if (P.mu90) {
+            v += shl26_mod(hi, P.p, P.mu90);
+            if (v >= P.p) v -= P.p;
+        }
+        if (c0 + e < P.n) out[e] = v;
+    }
+}
+
+// One K-range, S moduli known at compile time: the modulus loop unrolls and
+// the per-modulus constants become immediate kernel-parameter operands.
+template <int S>
+__global__ void __launch_bounds__(256) crt_kernel_s(const __grid_constant__ CrtParams P) {
+    const int64_t c0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4;
+    if (c0 >= P.n) return;
+    const int64_t plane = P.A_rows * P.B_rows;
+    for (int64_t row = blockIdx.y; row < P.m; row += gridDim.y) {
+        uint64_t a0[4] = {0, 0, 0, 0}, a1[4] = {0, 0, 0, 0};
+        float qf[4] = {0.25f, 0.25f, 0.25f, 0.25f};
+        const int32_t *src = P.S + row * P.B_rows + c0;
+#pragma unroll
+        for (int i0 = 0; i0 < S; i0 += 4) {  // four moduli per round: their loads are issued together
+            int4 v[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (i0 + j < S) v[j] = __ldcs(reinterpret_cast<const int4 *>(src + (int64_t)(i0 + j) * plane));
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                if (i0 + j >= S) break;
+                const int i = i0 + j;
+                const int32_t vv[4] = {v[j].x, v[j].y, v[j].z, v[j].w};
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    // S + 2^31 is in [0, 2^32): its residue, minus 2^31 mod m_i
+                    const uint32_t t = fastmod((uint32_t)vv[e] + 0x80000000u, P.cm[i], P.cmag[i]);
+                    const uint32_t r = t >= P.c31[i] ? t - P.c31[i] : t + P.cm[i] - P.c31[i];
+                    const uint32_t xi = r * P.cy[i];  // < m_i^2 < 2^16
+                    qf[e] = __fmaf_rn((float)xi, P.rinv[i], qf[e]);
+                    a0[e] += (uint64_t)xi * P.wl[i];  // 32 x 32 -> 64
+                    a1[e] += (uint64_t)xi * P.wh[i];
+                }
+            }
+        }
+        crt_store(P, a0, a1, qf, P.C + row * P.ldc + c0, c0);
+    }
+}
+
+// Several K-ranges (k beyond one INT32 sum): exact 64-bit sums, then the residues.
 __global__ void __launch_bounds__(256) crt_kernel(const __grid_constant__ CrtParams P) {
     const int64_t c0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4;
     if (c0 >= P.n) return;
@@ -239,73 +300,26 @@ __global__ void __launch_bounds__(256) crt_kernel(const __grid_constant__ CrtPar
     for (int64_t row = blockIdx.y; row < P.m; row += gridDim.y) {
         uint64_t a0[4] = {0, 0, 0, 0}, a1[4] = {0, 0, 0, 0};
         float qf[4] = {0.25f, 0.25f, 0.25f, 0.25f};
-        if (P.nkc == 1) {
-            // four moduli per round: their loads are issued together
-            for (int i0 = 0; i0 < P.s; i0 += 4) {
-                int4 v[4];
-#pragma unroll
-                for (int j = 0; j < 4; ++j)
-                    if (i0 + j < P.s)
-                        v[j] = __ldcs(reinterpret_cast<const int4 *>(P.S + (int64_t)(i0 + j) * plane + row * P.B_rows + c0));
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const int i = i0 + j;
-                    if (i >= P.s) break;
-                    const uint32_t mi = P.cm[i], yi = P.cy[i], c = P.c31[i];
-                    const uint64_t mag = P.cmag[i];
-                    const float ri = P.rinv[i];
-                    const uint32_t wl = P.wl[i], wh = P.wh[i];
-                    const int32_t vv[4] = {v[j].x, v[j].y, v[j].z, v[j].w};
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        // S + 2^31 is in [0, 2^32): its residue, minus 2^31 mod m_i
-                        const uint32_t t = fastmod((uint32_t)vv[e] + 0x80000000u, mi, mag);
-                        const uint32_t r = t >= c ? t - c : t + mi - c;
-                        const uint32_t xi = r * yi;  // < m_i^2 < 2^16
-                        qf[e] = __fmaf_rn((float)xi, ri, qf[e]);
-                        a0[e] += (uint64_t)xi * wl;  // 32 x 32 -> 64
-                        a1[e] += (uint64_t)xi * wh;
-                    }
-                }
+        for (int i = 0; i < P.s; ++i) {
+            const uint32_t mi = P.cm[i], yi = P.cy[i];
+            int64_t x[4] = {0, 0, 0, 0};
+            for (int kc = 0; kc < P.nkc; ++kc) {
+                const int4 v = *reinterpret_cast<const int4 *>(P.S + ((int64_t)i * P.nkc + kc) * plane +
+                                                               row * P.B_rows + c0);
+                x[0] += v.x; x[1] += v.y; x[2] += v.z; x[3] += v.w;
             }
-        } else {  // several K-ranges: exact 64-bit sums, then the residues
-            for (int i = 0; i < P.s; ++i) {
-                const uint32_t mi = P.cm[i], yi = P.cy[i];
-                int64_t x[4] = {0, 0, 0, 0};
-                for (int kc = 0; kc < P.nkc; ++kc) {
-                    const int4 v = *reinterpret_cast<const int4 *>(P.S + ((int64_t)i * P.nkc + kc) * plane +
-                                                                   row * P.B_rows + c0);
-                    x[0] += v.x; x[1] += v.y; x[2] += v.z; x[3] += v.w;
-                }
-                const float ri = P.rinv[i];
-                const uint64_t wl = P.wl[i], wh = P.wh[i];
+            const float ri = P.rinv[i];
+            const uint32_t wl = P.wl[i], wh = P.wh[i];
 #pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    const int64_t t = x[e] % (int64_t)mi;
-                    const uint32_t xi = (uint32_t)(t < 0 ? t + mi : t) * yi;
-                    qf[e] = __fmaf_rn((float)xi, ri, qf[e]);
-                    a0[e] += xi * wl;
-                    a1[e] += xi * wh;
-                }
+            for (int e = 0; e < 4; ++e) {
+                const int64_t t = x[e] % (int64_t)mi;
+                const uint32_t xi = (uint32_t)(t < 0 ? t + mi : t) * yi;
+                qf[e] = __fmaf_rn((float)xi, ri, qf[e]);
+                a0[e] += (uint64_t)xi * wl;
+                a1[e] += (uint64_t)xi * wh;
             }
         }
-        uint64_t *out = P.C + row * P.ldc + c0;
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            const uint64_t q = (uint64_t)floorf(qf[e]);  // < 2^13
-            // sum_i x_i w_i = a0 + 2^26 a1, and q W = q Wl + 2^26 q Wh
-            uint64_t lo = reduce_u64(a0[e], P.p, P.mu), hi = reduce_u64(a1[e], P.p, P.mu);
-            const uint64_t qlo = reduce_u64(q * (P.W & ((1u << 26) - 1)), P.p, P.mu);
-            const uint64_t qhi = reduce_u64(q * (P.W >> 26), P.p, P.mu);
-            lo = lo >= qlo ? lo - qlo : lo + P.p - qlo;
-            hi = hi >= qhi ? hi - qhi : hi + P.p - qhi;
-            uint64_t v = lo;
-            if (P.mu90) {
-                v += shl26_mod(hi, P.p, P.mu90);
-                if (v >= P.p) v -= P.p;
-            }
-            if (c0 + e < P.n) out[e] = v;
-        }
+        crt_store(P, a0, a1, qf, P.C + row * P.ldc + c0, c0);
     }
 }
 
@@ -338,7 +352,38 @@ static int launch_crt(const Plan &pl, const int32_t *S, uint64_t *C, int64_t ldc
     }
     const int64_t groups = (pl.n + 3) / 4;
     dim3 grid((unsigned)((groups + 255) / 256), (unsigned)(pl.m < 65535 ? pl.m : 65535));
-    crt_kernel<<<grid, 256, 0, static_cast<cudaStream_t>(stream)>>>(P);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (pl.nkc != 1 || pl.crt_s < 1 || pl.crt_s > kMaxCrt) {
+        crt_kernel<<<grid, 256, 0, st>>>(P);
+        return (int)cudaGetLastError();
+    }
+    switch (pl.crt_s) {
+        case 1: crt_kernel_s<1><<<grid, 256, 0, st>>>(P); break;
+        case 2: crt_kernel_s<2><<<grid, 256, 0, st>>>(P); break;
+        case 3: crt_kernel_s<3><<<grid, 256, 0, st>>>(P); break;
+        case 4: crt_kernel_s<4><<<grid, 256, 0, st>>>(P); break;
+        case 5: crt_kernel_s<5><<<grid, 256, 0, st>>>(P); break;
+        case 6: crt_kernel_s<6><<<grid, 256, 0, st>>>(P); break;
+        case 7: crt_kernel_s<7><<<grid, 256, 0, st>>>(P); break;
+        case 8: crt_kernel_s<8><<<grid, 256, 0, st>>>(P); break;
+        case 9: crt_kernel_s<9><<<grid, 256, 0, st>>>(P); break;
+        case 10: crt_kernel_s<10><<<grid, 256, 0, st>>>(P); break;
+        case 11: crt_kernel_s<11><<<grid, 256, 0, st>>>(P); break;
+        case 12: crt_kernel_s<12><<<grid, 256, 0, st>>>(P); break;
+        case 13: crt_kernel_s<13><<<grid, 256, 0, st>>>(P); break;
+        case 14: crt_kernel_s<14><<<grid, 256, 0, st>>>(P); break;
+        case 15: crt_kernel_s<15><<<grid, 256, 0, st>>>(P); break;
+        case 16: crt_kernel_s<16><<<grid, 256, 0, st>>>(P); break;
+        case 17: crt_kernel_s<17><<<grid, 256, 0, st>>>(P); break;
+        case 18: crt_kernel_s<18><<<grid, 256, 0, st>>>(P); break;
+        case 19: crt_kernel_s<19><<<grid, 256, 0, st>>>(P); break;
+        case 20: crt_kernel_s<20><<<grid, 256, 0, st>>>(P); break;
+        case 21: crt_kernel_s<21><<<grid, 256, 0, st>>>(P); break;
+        case 22: crt_kernel_s<22><<<grid, 256, 0, st>>>(P); break;
+        case 23: crt_kernel_s<23><<<grid, 256, 0, st>>>(P); break;
+        case 24: crt_kernel_s<24><<<grid, 256, 0, st>>>(P); break;
+        default: crt_kernel<<<grid, 256, 0, st>>>(P); break;
+    }
     return (int)cudaGetLastError();
 }
 
