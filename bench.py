@@ -356,6 +356,50 @@ def run_shapes(dev):
     return out
 
 
+def _ceil_root(p: int, u: int) -> int:
+    lo, hi = 1, 1
+    while hi ** u < p:
+        hi *= 2
+    lo = hi // 2
+    while lo < hi:
+        mid = (lo + hi) // 2
+        if mid ** u >= p:
+            hi = mid
+        else:
+            lo = mid + 1
+    return lo
+
+
+def product_counts(k: int = 4096, lams=(1, 512), t: int = 53):
+    """Fig. 7 of the paper recomputed exactly for FP64 words: per bitsize, the
+    fewest word products of a multiword variant (u, v <= 8) whose block size
+    lambda satisfies lambda max|A_i| max|B_j| + p - 1 <= 2^t (Prop. 3.3, Sec.
+    2.2), against the fewest products of the multimodular approach: distinct
+    primes m_i with lambda (m_i - 1)^2 <= 2^t whose product exceeds k (p-1)^2
+    (eqs. CRT1, CRT2), largest primes first."""
+    out = {}
+    for b in range(20, 53):
+        p = inputs.largest_prime_below_pow2(b)
+        row = {}
+        for lam in lams:
+            best = None
+            for u in range(1, 9):
+                for v in range(u, 9):
+                    amax = p - 1 if u == 1 else _ceil_root(p, u)
+                    bmax = p - 1 if v == 1 else _ceil_root(p, v)
+                    if lam * amax * bmax + p - 1 <= 2 ** t and (best is None or u * v < best[0]):
+                        best = (u * v, u, v)
+            bound = math.isqrt((2 ** t) // lam) + 1  # (m - 1)^2 <= 2^t / lambda
+            target, prod, s, q = k * (p - 1) ** 2, 1, 0, bound + 1
+            while prod <= target:
+                q = inputs.prev_prime(q)
+                prod *= q
+                s += 1
+            row[str(lam)] = {"multiword": best[0], "uv": [best[1], best[2]], "multimodular": s}
+        out[str(b)] = row
+    return out
+
+
 UNBALANCED = (10923, 32, 32768)  # m, n, k of the block-Wiedemann products (Sec. 4.1)
 
 # One bitsize per FP64 variant inside the range where its block size covers
@@ -787,6 +831,7 @@ def main():
                 "gpu_launches": launches * world, "clocks": clocks, "per_bitsize": per_bits,
                 "batched_multi_prime": batched, "shapes_50bit": shapes, "unbalanced_block_wiedemann": unbalanced,
                 "variant_sweep": sweep,
+                "product_counts_fp64_words": product_counts(n),
                 "serve": serve}
         print(json.dumps(line))
     if dist:
