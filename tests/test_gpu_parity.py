@@ -269,7 +269,7 @@ def test_int8_extreme_digits_fill_the_fp32_chunk(M, oracle, b, da, db):
     assert np.all(C == (a * bb * (1024 + 64)) % p)
 
 
-@pytest.mark.parametrize("form", ["fp64", "int8"])
+@pytest.mark.parametrize("form", ["fp64", "int8", "crt8"])
 def test_leading_dimensions_and_degenerate_shapes(M, oracle, form):
     p = SWEEP[32]
     A, B = inputs.problem(5, 40, 30, 20, p)
@@ -290,9 +290,16 @@ def test_leading_dimensions_and_degenerate_shapes(M, oracle, form):
                       torch.zeros((1, 9), dtype=torch.int64, device="cuda"),
                       torch.full((7, 9), 5, dtype=torch.int64, device="cuda"))
     assert plan0.check() == 0 and int(C0.abs().sum()) == 0
+    # m = 0 or n = 0: nothing to compute, nothing written, no workspace
+    for m, n in ((0, 9), (7, 0), (0, 0)):
+        pe = M.Plan(m, n, 5, p, form=form)
+        assert pe.workspace_bytes == 0
+        Ce = pe.matmul(torch.zeros((max(m, 1), 5), dtype=torch.int64, device="cuda")[:m],
+                       torch.zeros((5, max(n, 1)), dtype=torch.int64, device="cuda")[:, :n])
+        assert pe.check() == 0 and tuple(Ce.shape) == (m, n)
 
 
-@pytest.mark.parametrize("form", ["fp64", "int8"])
+@pytest.mark.parametrize("form", ["fp64", "int8", "crt8"])
 def test_host_entry_point(M, oracle, form):
     p = SWEEP[48]
     A, B = inputs.problem(21, 150, 140, 130, p)
