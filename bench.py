@@ -769,10 +769,12 @@ def main():
                       "crt8_tensor_tflops": 2.0 * d["u"] * n ** 3 / (t["gemm_ms"] / calls) / 1e9,
                       "crt8_equals_int8": bool(torch.equal(Cc, dC[i])),
                       # products per result: multiword u v vs multimodular s, and the
-                      # paper's counts (numprodMW, numprodMM) for 8-bit words: t - log2(lambda)
-                      # = 24 - 10 bits per exact FP32 chunk of 1024 products
+                      # paper's counts (numprodMW, numprodMM) for t - log2(lambda) = 24 - 10
+                      # bits per exact FP32 chunk of 1024 products; numprodMW at the
+                      # paper's own word count, unsigned words below 2^7 (u = v =
+                      # ceil(log2 p / 7)), where the balanced digits here carry 8 bits
                       "products": {"multiword_int8": e["int8_words"][0] * e["int8_words"][1], "crt8": d["u"],
-                                   "paper_multiword": math.ceil(2 * e["int8_words"][0] * lg / 14),
+                                   "paper_multiword": math.ceil(2 * math.ceil(lg / 7) * lg / 14),
                                    "paper_multimodular": math.ceil((4 * lg + 2 * math.log2(n)) / 14)}})
             del pl, Cc
             torch.cuda.empty_cache()

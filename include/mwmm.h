@@ -20,8 +20,9 @@
  *                   into the epilogue (the workspace variant of Sec. 3.2).
  *
  *   MWMM_FORM_INT8  the narrower-word form of the paper's second
- *                   perspective (Sec. 6): words are balanced base-2^8 digits
- *                   in [-128, 127] of the signed representative of each
+ *                   perspective (Sec. 6): words are base-2^8 digits of
+ *                   magnitude <= 128 (balanced, the top one in [-128, 128])
+ *                   of the signed representative of each
  *                   entry (so alpha = beta = 256), multiplied on the tcgen05
  *                   tensor pipe.  On sm_103a the tensor pipe has no INT8
  *                   kind, so the INT8 digits are carried exactly in bf16 and

@@ -167,10 +167,11 @@ int oracle_split_alpha(const uint64_t *M, int64_t count, uint64_t alpha, int u, 
 
 /* INT8 words.  The signed representative s of M mod p is M when
  * M <= (p-1)/2 and M - p otherwise (|s| <= (p-1)/2).  Its balanced base-2^8
- * digits d_0..d_{u-1}, each in [-128, 127], satisfy s = sum_i 256^i d_i:
- * d_i = ((s + 128) mod 256) - 128, s <- (s - d_i) / 256, and the last digit
- * is what remains.  Returns 2 if that last digit leaves [-128, 127] (u too
- * small for p).  words is [u][count]. */
+ * digits satisfy s = sum_i 256^i d_i: d_0..d_{u-2} are balanced,
+ * d_i = ((s + 128) mod 256) - 128 in [-128, 127], s <- (s - d_i) / 256, and
+ * the last digit is what remains, allowed in [-128, 128] (magnitude <= 2^7,
+ * like every other digit).  Returns 2 if that last digit leaves [-128, 128]
+ * (u too small for p).  words is [u][count]. */
 int oracle_split_signed8(const uint64_t *M, int64_t count, uint64_t p, int u, int32_t *words) {
     if (u < 1) return 1;
     for (int64_t e = 0; e < count; ++e) {
@@ -182,7 +183,7 @@ int oracle_split_signed8(const uint64_t *M, int64_t count, uint64_t p, int u, in
             words[(int64_t)i * count + e] = (int32_t)d;
             s = (s - d) / 256;
         }
-        if (s < -128 || s > 127) return 2;
+        if (s < -128 || s > 128) return 2;
         words[(int64_t)(u - 1) * count + e] = (int32_t)s;
     }
     return 0;

@@ -187,11 +187,12 @@ def lam(p: int, u: int, v: int, t: int = 53) -> int:
 
 
 def int8_words(p: int) -> int:
-    """Fewest balanced base-2^8 digits in [-128, 127] that represent every
-    signed representative in [-(p-1)/2, (p-1)/2]: the largest such value is
-    127 (256^u - 1) / 255."""
+    """Fewest base-2^8 digits that represent every signed representative in
+    [-(p-1)/2, (p-1)/2] with u - 1 balanced digits in [-128, 127] and a top
+    digit in [-128, 128]: with B = 256^(u-1) the largest such value is
+    128 B + 127 (B - 1) / 255."""
     u = 1
-    while 127 * (256 ** u - 1) // 255 < (p - 1) // 2:
+    while 128 * 256 ** (u - 1) + 127 * (256 ** (u - 1) - 1) // 255 < (p - 1) // 2:
         u += 1
     return u
 

@@ -5,8 +5,8 @@
 // C = sum_s 256^s S_s mod p.  This is the paper's second perspective (Sec. 6):
 // narrower words, more of them, multiplied on tensor cores.
 //
-// Exactness.  sm_103a's tcgen05 has no INT8 kind, so the digits (integers in
-// [-128, 127]) are carried exactly in bf16 and multiplied with
+// Exactness.  sm_103a's tcgen05 has no INT8 kind, so the digits (integers of
+// magnitude <= 128) are carried exactly in bf16 and multiplied with
 // tcgen05.mma.kind::f16 into FP32 tensor memory.  Every product is an integer
 // of magnitude <= 2^14, so as long as a chunk sums at most 1024 of them every
 // partial sum is an integer of magnitude <= 2^24, which FP32 represents

@@ -54,15 +54,18 @@ uint64_t block_size(uint64_t p, int u, int v) {
     return lam > (u128)UINT64_MAX ? UINT64_MAX : (uint64_t)lam;
 }
 
-// Fewest balanced base-2^8 digits in [-128, 127] that represent every signed
-// representative in [-(p-1)/2, (p-1)/2]; u digits reach 127 (256^u - 1) / 255.
+// Fewest base-2^8 digits for every signed representative in
+// [-(p-1)/2, (p-1)/2]: u - 1 balanced digits in [-128, 127] and a top digit
+// in [-128, 128], so every digit product stays <= 2^14 in magnitude.  With
+// B = 256^(u-1) the largest value reached is 128 B + 127 (B - 1) / 255: u
+// digits cover every prime below 2^(8u).
 int int8_digits(uint64_t p) {
     const u128 half = (p - 1) / 2;
     int u = 1;
-    u128 pw = 256;
-    while ((u128)127 * (pw - 1) / 255 < half) {
+    u128 B = 1;
+    while ((u128)128 * B + (u128)127 * (B - 1) / 255 < half) {
         ++u;
-        pw *= 256;
+        B *= 256;
     }
     return u;
 }

@@ -7,8 +7,9 @@
 // floor(fl(T / alpha)) is the same integer, so the words are identical.
 //
 // INT8 form: the signed representative s of M mod p (M, or M - p when
-// M > (p-1)/2) is written as balanced base-2^8 digits in [-128, 127],
-// s = sum_i 256^i d_i; the digits are stored exactly as bf16.
+// M > (p-1)/2) is written as base-2^8 digits, s = sum_i 256^i d_i: balanced
+// digits in [-128, 127] and a top digit in [-128, 128] (the remainder); the
+// digits are stored exactly as bf16.
 //
 // CRT form (multimodular comparison, Sec. 5.2): word i is the signed
 // residue of M modulo the i-th modulus m_i < 256 (in [-(m_i-1)/2, (m_i-1)/2]),

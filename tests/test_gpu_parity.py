@@ -269,6 +269,32 @@ def test_int8_extreme_digits_fill_the_fp32_chunk(M, oracle, b, da, db):
     assert np.all(C == (a * bb * (1024 + 64)) % p)
 
 
+@pytest.mark.parametrize("b", [32, 40, 48])
+@pytest.mark.parametrize("sa,sb", [(1, 1), (-1, -1), (1, -1)])
+def test_int8_top_digit_128_fills_the_fp32_chunk(M, oracle, b, sa, sb):
+    """For the largest prime below 2^(8u), +-(p-1)/2 has top digit +-128:
+    u digits suffice, and top x top products of +-2^14 fill a 1024-product
+    chunk to |sum| = 2^24."""
+    p = SWEEP[b]
+    u = oracle.int8_words(p)
+    assert u == b // 8
+    half = (p - 1) // 2
+    a, bb = (half if sa > 0 else p - half), (half if sb > 0 else p - half)
+    Aw = oracle.split_signed8(np.array([a], np.uint64), p, u)[:, 0]
+    Bw = oracle.split_signed8(np.array([bb], np.uint64), p, u)[:, 0]
+    assert Aw[-1] == 128 * sa and Bw[-1] == 128 * sb
+    A = np.full((130, 1024 + 64), a, dtype=np.uint64)
+    B = np.full((1024 + 64, 260), bb, dtype=np.uint64)
+    C, _ = gpu_product(M, A, B, p, form="int8")
+    assert np.all(C == (a * bb * (1024 + 64)) % p)
+    # every entry at +-(p-1)/2 or 0, mixed, against the oracle
+    rng = np.random.default_rng(b)
+    A = rng.choice(np.array([0, half, p - half], np.uint64), size=(200, 1500))
+    B = rng.choice(np.array([0, half, p - half], np.uint64), size=(1500, 300))
+    C, _ = gpu_product(M, A, B, p, form="int8")
+    assert np.array_equal(C, oracle.matmul_mod(A, B, p))
+
+
 @pytest.mark.parametrize("form", ["fp64", "int8", "crt8"])
 def test_leading_dimensions_and_degenerate_shapes(M, oracle, form):
     p = SWEEP[32]

@@ -164,7 +164,7 @@ def test_split_signed8(oracle, p):
     M = np.concatenate([inputs.uniform_mod(11, 7, 400, p),
                         np.array([0, 1, p - 1, (p - 1) // 2, (p + 1) // 2], dtype=np.uint64)])
     W = oracle.split_signed8(M, p, u)
-    assert W.min() >= -128 and W.max() <= 127
+    assert W.min() >= -128 and W[:u - 1].max(initial=0) <= 127 and W[u - 1].max() <= 128
     for e, x in enumerate(M):
         x = int(x)
         s = x if x <= (p - 1) // 2 else x - p
@@ -179,12 +179,37 @@ def test_int8_words_table():
     # digits per side for the sweep primes (largest prime below 2^b)
     from oracle import oracle as O
     got = {b: O.int8_words(SWEEP_PRIMES[b]) for b in inputs.SWEEP_BITS}
-    # closed form: (p-1)/2 <= 127 (256^u - 1) / 255, checked independently with floats
+    # u - 1 balanced digits and a top digit of magnitude <= 128 reach
+    # 128 B + 127 (B - 1) / 255 with B = 256^(u-1), about 2^(8u-1): every
+    # prime below 2^(8u) needs at most u digits (checked with floats)
     for b, u in got.items():
         p = SWEEP_PRIMES[b]
-        assert (p - 1) / 2 <= 127 * (256.0 ** u - 1) / 255 * (1 + 1e-12)
-        assert (p - 1) / 2 > 127 * (256.0 ** (u - 1) - 1) / 255
-    assert got == {20: 3, 23: 3, 26: 4, 32: 5, 40: 6, 48: 7, 52: 7}
+        B = 256.0 ** (u - 1)
+        assert (p - 1) / 2 <= (128 * B + 127 * (B - 1) / 255) * (1 + 1e-12)
+        assert (p - 1) / 2 > 128 * B / 256 + 127 * (B / 256 - 1) / 255
+        assert u == -(-b // 8)
+    assert got == {20: 3, 23: 3, 26: 4, 32: 4, 40: 5, 48: 6, 52: 7}
+
+
+def test_split_signed8_top_digit_128(oracle):
+    # (p-1)/2 for p = 2^32 - 5 is 2^31 - 3 = 128 * 2^24 - 3: digits (-3, 0, 0, 128)
+    p = SWEEP_PRIMES[32]
+    W = oracle.split_signed8(np.array([(p - 1) // 2, (p + 1) // 2], dtype=np.uint64), p, 4)
+    assert W[:, 0].tolist() == [-3, 0, 0, 128] and W[:, 1].tolist() == [3, 0, 0, -128]
+    # brute force over every signed value of a 2-digit split: the covered
+    # range is [-128 * 257, 128 * 256 + 127], the top digit reaching -128 and
+    # +128 at its ends, and one more on either side needs a third digit
+    top = 128 * 256 + 127
+    s = np.arange(-top - 2, top + 2, dtype=np.int64)
+    pp = 2 * (top + 2) + 1          # odd modulus with (pp - 1) / 2 = top + 2
+    M = np.where(s >= 0, s, s + pp).astype(np.uint64)
+    for bad in (0, len(s) - 1):
+        with pytest.raises(ValueError):
+            oracle.split_signed8(M[bad:bad + 1], pp, 2)
+    ok = (s >= -top - 1) & (s <= top)
+    W = oracle.split_signed8(M[ok], pp, 2)
+    assert np.array_equal(W[0] + 256 * W[1], s[ok])
+    assert W[1].min() == -128 and W[1].max() == 128 and W[0].min() == -128 and W[0].max() == 127
 
 
 def test_diag_sums_and_recombine_reproduce_product(oracle):

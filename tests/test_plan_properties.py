@@ -60,7 +60,12 @@ def test_int8_plans_keep_fp32_chunks_and_int32_sums_exact(M, oracle, p, m, n, k)
     M.mwmm_plan_destroy(h)
     u = d["u"]
     assert u == d["v"] == oracle.int8_words(p)
-    assert 127 * (256 ** u - 1) // 255 >= (p - 1) // 2  # the digits reach every signed representative
+    B = 256 ** (u - 1)  # u - 1 balanced digits, top digit in [-128, 128]
+    assert 128 * B + 127 * (B - 1) // 255 >= (p - 1) // 2  # every signed representative is reached
+    assert u <= -(-(p.bit_length()) // 8)  # at most ceil(b / 8) digits for a b-bit prime
+    if u > 1:  # and the fewest: u - 1 digits miss the largest signed representative
+        B //= 256
+        assert 128 * B + 127 * (B - 1) // 255 < (p - 1) // 2
     assert d["tc_chunk"] * 128 * 128 <= 2 ** 24  # FP32 chunk: every partial sum exact
     assert d["kc"] * min(u, u) * 128 * 128 <= 2 ** 31 - 1 or k == 0  # INT32 sum of one K-range
     assert d["nkc"] == (-(-k // d["kc"]) if k else 0)
