@@ -49,16 +49,34 @@ struct SplitParams {
     uint64_t alpha, mu;  // FP64: radix and floor((2^64 - 1) / alpha)
     int validate;
     int *err;
+    int64_t cbias;              // INT8 form: 128 (1 + 256 + ... + 256^(words-2))
     int crt;                    // CRT form: residues instead of digits
     uint32_t cm[kMaxCrt];       // moduli
     uint64_t cmu[kMaxCrt];      // floor((2^64 - 1) / m_i)
 };
 
+// Small integers to bf16 without the conversion pipe.  For |v| < 2^22 the
+// FP32 number with bit pattern 0x4B400000 + v is 1.5 * 2^23 + v exactly, and
+// subtracting 1.5 * 2^23 leaves v exactly.  A value of magnitude <= 256 has
+// at most 8 significant bits, so its bf16 is the upper half of that FP32
+// pattern (no rounding): two of them pack into one word with one byte
+// permutation.
+constexpr float kMagic = 12582912.0f;  // 1.5 * 2^23
+__device__ __forceinline__ float small_int_float(int v) { return __int_as_float(0x4B400000 + v) - kMagic; }
+// FP32 value byte_i(x) - 128 (i in 0..3): the byte is placed under the
+// exponent of 1.5 * 2^23 by a byte permutation.
+__device__ __forceinline__ float byte_digit_float(uint32_t x, int i) {
+    return __int_as_float((int)__byte_perm(x, 0x4B400000u, 0x7650u | (uint32_t)i)) - (kMagic + 128.0f);
+}
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
+    return __byte_perm(__float_as_uint(lo), __float_as_uint(hi), 0x7632u);
+}
+
 // Signed residue of x modulo m < 2^16: x - m umulhi(x, mu) is below 2m.
 __device__ __forceinline__ float signed_residue(uint64_t x, uint32_t m, uint64_t mu) {
     uint32_t r = (uint32_t)(x - __umul64hi(x, mu) * m);
     if (r >= m) r -= m;
-    return (float)(r > (m - 1) / 2 ? (int)r - (int)m : (int)r);
+    return small_int_float(r > (m - 1) / 2 ? (int)r - (int)m : (int)r);
 }
 
 __device__ __forceinline__ uint64_t load_tile_elem(const SplitParams &P, int64_t r, int64_t l) {
@@ -71,15 +89,22 @@ __device__ __forceinline__ uint64_t load_tile_elem(const SplitParams &P, int64_t
 __device__ __forceinline__ void load_tile(const SplitParams &P, uint64_t (*tile)[kST + 1], int64_t r0,
                                           int64_t l0) {
     const int t = threadIdx.x;
+    constexpr int kPer = (kST * kST) / 256;
     bool bad = false;
-#pragma unroll 4
-    for (int it = 0; it < (kST * kST) / 256; ++it) {
+    uint64_t x[kPer];  // every load of the thread in flight before the first store
+#pragma unroll
+    for (int it = 0; it < kPer; ++it) {
         const int a = t / kST + it * (256 / kST), b = t % kST;
         // side 0: a = row offset, b = k offset (contiguous);  side 1: a = k, b = row
         const int rr = P.side == 0 ? a : b, ll = P.side == 0 ? b : a;
-        const uint64_t x = load_tile_elem(P, r0 + rr, l0 + ll);
-        bad |= (x >= P.p);
-        tile[rr][ll] = x;
+        x[it] = load_tile_elem(P, r0 + rr, l0 + ll);
+    }
+#pragma unroll
+    for (int it = 0; it < kPer; ++it) {
+        const int a = t / kST + it * (256 / kST), b = t % kST;
+        const int rr = P.side == 0 ? a : b, ll = P.side == 0 ? b : a;
+        bad |= (x[it] >= P.p);
+        tile[rr][ll] = x[it];
     }
     if (P.validate && bad) atomicExch(P.err + 1, 1);
     __syncthreads();
@@ -99,13 +124,14 @@ __device__ __forceinline__ double alg4_next(uint64_t &T, uint64_t alpha, uint64_
     return (double)rem;
 }
 
-// Next balanced base-2^8 digit of the running signed value s; the last digit
-// is s itself.
-__device__ __forceinline__ float int8_next(int64_t &s, bool last) {
-    if (last) return (float)s;
-    const int64_t d = ((s + 128) & 255) - 128;
-    s = (s - d) >> 8;  // exact: s - d is a multiple of 256
-    return (float)d;
+// INT8 digits through bytes: with c = 128 (1 + 256 + ... + 256^(u-2)),
+// t = s + c = sum_{i<u-1} (d_i + 128) 256^i + d_{u-1} 256^(u-1), and every
+// d_i + 128 lies in [0, 255], so the lower digits are the bytes of t minus
+// 128 and the top digit is t >> 8 (u-1) (arithmetic shift).
+__device__ __forceinline__ float int8_digit(int64_t t, int w, bool last) {
+    if (last) return small_int_float((int)(t >> (8 * w)));
+    const uint32_t half = w < 4 ? (uint32_t)t : (uint32_t)((uint64_t)t >> 32);
+    return byte_digit_float(half, w & 3);
 }
 
 // FP64 form: a 64 x 64 tile covers 4 k-blocks of 16 doubles, 8 granules each.
@@ -143,27 +169,28 @@ __device__ __forceinline__ void split_int8_tile(const SplitParams &P, uint64_t (
     for (int unit = threadIdx.x; unit < kST * 8; unit += 256) {
         const int rr = unit / 8, g = unit % 8;
         uint64_t x[8];
-        int64_t s[8];
+        int64_t t[8];  // signed representative + digit bias
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
             x[e] = tile[rr][8 * g + e];
-            s[e] = (x[e] <= half) ? (int64_t)x[e] : (int64_t)x[e] - (int64_t)P.p;
+            t[e] = ((x[e] <= half) ? (int64_t)x[e] : (int64_t)x[e] - (int64_t)P.p) + P.cbias;
         }
         const int64_t r = r0 + rr;
         if (r >= P.rows_pad) continue;  // a last row tile may be partial (rows_pad 16 or 32)
         for (int w = 0; w < P.words; ++w) {
             const bool last = (w == P.words - 1);
-            __align__(16) __nv_bfloat16 h[8];
+            float f[8];
             if (P.crt) {
 #pragma unroll
-                for (int e = 0; e < 8; ++e) h[e] = __float2bfloat16_rn(signed_residue(x[e], P.cm[w], P.cmu[w]));
+                for (int e = 0; e < 8; ++e) f[e] = signed_residue(x[e], P.cm[w], P.cmu[w]);
             } else {
 #pragma unroll
-                for (int e = 0; e < 8; ++e) h[e] = __float2bfloat16_rn(int8_next(s[e], last));
+                for (int e = 0; e < 8; ++e) f[e] = int8_digit(t[e], w, last);
             }
             uint8_t *dst = P.out + ((int64_t)(w + P.wpad) * P.wstride + kb * P.kstride + r) * kTileBytes +
                            ((g ^ (int)(r & 7)) * 16);
-            *reinterpret_cast<uint4 *>(dst) = *reinterpret_cast<const uint4 *>(h);
+            *reinterpret_cast<uint4 *>(dst) = make_uint4(pack_bf16x2(f[0], f[1]), pack_bf16x2(f[2], f[3]),
+                                                         pack_bf16x2(f[4], f[5]), pack_bf16x2(f[6], f[7]));
         }
         for (int z = 0; z < P.wpad; ++z) {  // the zero words on both sides
             const int64_t base = kb * P.kstride + r;
@@ -221,6 +248,8 @@ SplitParams make_split_params(const Plan &pl, int side, const uint64_t *M, int64
     P.validate = pl.validate;
     P.err = pl.err_dev;
     P.crt = pl.form == MWMM_FORM_CRT8;
+    P.cbias = 0;
+    for (int i = 0; i + 1 < P.words && !P.crt && pl.form != MWMM_FORM_FP64; ++i) P.cbias += (int64_t)128 << (8 * i);
     for (int i = 0; i < kMaxCrt; ++i) {
         P.cm[i] = i < pl.crt_s ? pl.crt_m[i] : 1;
         P.cmu[i] = i < pl.crt_s ? (~uint64_t(0)) / pl.crt_m[i] : 0;
