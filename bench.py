@@ -271,7 +271,8 @@ def workload_config(args, bits):
 # ----------------------------------------------------------------------------- batched and serving workloads
 def run_batched(dev, runs=5):
     """512 instances over the 64 largest primes below 2^50, m, n, k log-uniform
-    in [128, 2048] (seed 4), INT8 and FP64 forms, one graph replay per run."""
+    in [128, 2048] (seed 4), INT8 and FP64 forms and the autotuner's tensor
+    form (INT8 or CRT per instance), one graph replay per run."""
     import torch
     from paper_2601_07508_b300 import mwmm
     spec = inputs.batch_instances()
@@ -282,14 +283,16 @@ def run_batched(dev, runs=5):
                       torch.empty((m, n), dtype=torch.int64, device=dev), p))
     out = {"workload": "512 instances, 64 largest primes below 2^50 (instance i uses prime i mod 64), m, n, k "
                        "log-uniform in [128, 2048], seed 4; one CUDA-graph replay per run; (u,v) and K-range "
-                       "per bitsize group chosen by the autotuner (timed at batch creation)"}
+                       "per bitsize group chosen by the autotuner (timed at batch creation); 'auto': each "
+                       "instance's tensor form (INT8 digits or CRT) from the planner's cost model, the "
+                       "autotuner's configuration per (bitsize, form) group"}
     ref = None
-    for form in ("int8", "fp64"):
+    for form in ("int8", "auto", "fp64"):
         fitems = items if form == "int8" else [(a, b, torch.empty_like(c), p) for (a, b, c, p) in items]
         bt = mwmm.Batch(fitems, form=form, autotune=True)
         bt.run()
         torch.cuda.synchronize()
-        nrun = runs if form == "int8" else 1
+        nrun = 1 if form == "fp64" else runs
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
         for _ in range(nrun):
@@ -305,10 +308,13 @@ def run_batched(dev, runs=5):
                      "tc_items": info["items"], "ctas": info["ctas"],
                      "autotuned": {"groups": info["tuned_groups"], "probe_ms": info["tuned_ms"],
                                    "uv": [d0["u"], d0["v"]], "kc": d0["kc"], "f64_concat": d0["f64_concat"]}}
+        if form == "auto":
+            fc = [bt.problem_info(i)["form"] for i in range(len(fitems))]
+            out[form]["forms"] = {"int8": fc.count(2), "crt8": fc.count(3)}
         if form == "int8":
             ref = [c.clone() for (_, _, c, _) in fitems]
         else:
-            out["fp64_equals_int8"] = all(torch.equal(c, r) for (_, _, c, _), r in zip(fitems, ref))
+            out[form + "_equals_int8"] = all(torch.equal(c, r) for (_, _, c, _), r in zip(fitems, ref))
         del bt
     out["flops_2mnk_per_run"] = sum(2.0 * m * n * k for (m, n, k, _) in spec)
     return out
@@ -552,7 +558,8 @@ def run_serve(dev, nreq, pool, budget=40 << 30, ring=4):
         outs = [torch.empty((m, n), dtype=torch.int64, device=dev) for _ in range(ring)]
         ents.append((tA, tB, outs, [mwmm._problems([(tA, tB, c, p)])[0] for c in outs]))
     torch.cuda.synchronize()
-    srv = mwmm.Server(budget, max_inflight=3, max_batch=64)
+    crt_share = sum(mwmm.mwmm_tensor_form(m, n, k, p) == "crt8" for (m, n, k, p) in spec) / len(spec)
+    srv = mwmm.Server(budget, max_inflight=3, max_batch=64, form="int8")
     last = {}
 
     def stream(count, arrivals):
@@ -577,15 +584,25 @@ def run_serve(dev, nreq, pool, budget=40 << 30, ring=4):
             assert mwmm.mwmm_serve_wait(srv.handle, tk, 300000) == 0
         return srv.stats()
 
-    # closed loop: everything submitted at once -> saturation throughput
+    # closed loop: everything submitted at once -> saturation throughput; first
+    # with the INT8 form for every request (for comparison), then the served
+    # configuration: each request's tensor form from the planner's cost model
     nsat = min(nreq, 4 * pool)
+    sat8 = stream(nsat, None)  # returns after every ticket finished
+    srv.close()
+    last.clear()
+    srv = mwmm.Server(budget, max_inflight=3, max_batch=64, form="auto")
     sat = stream(nsat, None)
     sat_rps = sat["completed"] / sat["busy_s"]
     out = {"workload": "%d requests per rate, Poisson arrivals at 0.8 x and 0.5 x saturation, m, n, k log-uniform "
                        "in [64, 4096], p a random prime of bitsize uniform in [20, 52], seed 5; operands cycle "
-                       "through %d device-resident sets with %d output buffers each; 40 GB budget; INT8-word "
-                       "form; 3 streams, <= 64 requests per batch" % (nreq, pool, ring),
-           "saturation_requests_per_s": sat_rps, "saturation_gops": sat["gops"]}
+                       "through %d device-resident sets with %d output buffers each; 40 GB budget; form per "
+                       "request: INT8 digits or CRT, whichever the planner's cost model (mwmm_tensor_form) "
+                       "finds faster; 3 streams, <= 64 requests per batch" % (nreq, pool, ring),
+           "crt_share_of_requests": crt_share,
+           "saturation_requests_per_s": sat_rps, "saturation_gops": sat["gops"],
+           "saturation_int8_only": {"requests_per_s": sat8["completed"] / sat8["busy_s"], "gops": sat8["gops"],
+                                    "p50_ms": sat8["p50_ms"], "p99_ms": sat8["p99_ms"]}}
     for frac, key in ((0.8, "at_0.8"), (0.5, "at_0.5")):
         srv.reset_stats()
         rate = frac * sat_rps

@@ -78,7 +78,9 @@ typedef enum {
 } mwmm_status;
 
 typedef enum {
-    MWMM_FORM_AUTO = 0, /* INT8 form (the faster form on B300 at every bitsize) */
+    MWMM_FORM_AUTO = 0, /* plans: the INT8 form (faster than FP64 on B300 at
+                           every bitsize); batches and the serving loop: INT8
+                           or CRT per problem, see mwmm_tensor_form */
     MWMM_FORM_FP64 = 1,
     MWMM_FORM_INT8 = 2,
     MWMM_FORM_CRT8 = 3  /* multimodular comparison form (Sec. 5.2): residues of A
@@ -267,13 +269,25 @@ mwmm_status mwmm_plan_check(mwmm_plan_t plan, void *stream);
 
 void mwmm_plan_destroy(mwmm_plan_t plan);
 
+/* The tensor form, MWMM_FORM_INT8 or MWMM_FORM_CRT8, that batches and the
+ * serving loop use for this product under MWMM_FORM_AUTO: the smaller time
+ * in the planner's cost model (word products at the tensor rate, plus the
+ * split and the recombination or CRT reconstruction, calibrated on 4096^3
+ * products on B300: INT8 below about 24 bits, CRT from about 26 bits).  Host
+ * only, no CUDA call.  MWMM_FORM_INT8 when the CRT form cannot be planned
+ * (k > 2^22); MWMM_FORM_AUTO for arguments no form can plan. */
+mwmm_form mwmm_tensor_form(int64_t m, int64_t n, int64_t k, uint64_t p);
+
 /* ---- batched products (many independent problems, different shapes and primes) ----
  * A batch is planned once: every problem gets its own plan (FP64: (u,v) by
- * the cost model, lambda from Prop. 3.3; INT8: fewest digits), their words and
- * sums share one device workspace owned by the batch, the tcgen05 work items
- * of all problems are spread over the SMs (longest first, each to the least
- * loaded SM), and the kernel launches (3 for the INT8 form, 2 for the FP64
- * form, whatever the count) are captured once into a CUDA graph.  The device
+ * the cost model, lambda from Prop. 3.3; INT8: fewest digits; CRT: fewest
+ * moduli), their words and sums share one device workspace owned by the
+ * batch, the tcgen05 work items of all problems are spread over the SMs
+ * (longest first, each to the least loaded SM), and the kernel launches are
+ * captured once into a CUDA graph, whatever the count: 2 for the FP64 form;
+ * for the tensor forms split, word products, then the INT8 recombination
+ * and / or the CRT reconstruction (3 or 4).  INT8 and CRT problems may mix in
+ * one batch (MWMM_FORM_AUTO); FP64 problems run in batches of their own.  The device
  * pointers of the problems are bound at creation: a run recomputes every C
  * from the current contents of its A and B.  The paper computes one product
  * at a time; its first perspective (Sec. 6) suggests batching. */
@@ -292,26 +306,29 @@ typedef struct mwmm_batch_s *mwmm_batch_t;
 
 typedef struct {
     int32_t count, form;
-    int32_t ctas;             /* CTAs of the persistent tcgen05 launch (INT8 form) */
+    int32_t ctas;             /* CTAs of the persistent tcgen05 launch (tensor forms) */
     int64_t items;            /* tcgen05 work items over all problems */
     int64_t launches;         /* kernel launches per run */
     uint64_t workspace_bytes, table_bytes;
     double flops_2mnk;        /* sum over problems of 2 m n k */
-    double word_flops;        /* sum of 2 u v m n k (word-product flops) */
+    double word_flops;        /* sum of 2 u v m n k (CRT: 2 s m n k), the word-product flops */
     int32_t tuned_groups;     /* opts.autotune: bitsize groups whose configuration was timed or cached */
     int32_t pad0;
     double tuned_ms;          /* sum over groups of the probe products' measured times */
 } mwmm_batch_desc;
 
 /* Plan and capture a batch (allocates the workspace and tables; makes CUDA
- * calls).  opts applies to every problem (lambda is ignored).  With
+ * calls).  form: MWMM_FORM_FP64, MWMM_FORM_INT8 or MWMM_FORM_CRT8 for every
+ * problem, or MWMM_FORM_AUTO for the tensor form of each problem (INT8 or
+ * CRT, mwmm_tensor_form; per problem, since one bitsize can span a wide range
+ * of sizes).  opts applies to every problem (lambda is ignored).  With
  * opts->autotune set, the problems are grouped by the bit length of p and
- * each group's (u,v), INT32 K-range and concatenation are those
- * mwmm_plan_autotuned picks for the group's median-size problem among the
- * configurations the batched kernels run (one-CTA tcgen05 tiles, one FP64 K
- * range); the choice is timed on zero operands of that size, or taken from
- * the autotuner's cache.  Errors: those of
- * mwmm_plan for any problem, MWMM_ERR_ARG, MWMM_ERR_NOMEM, MWMM_ERR_CUDA. */
+ * their form, and each group's (u,v), INT32 K-range and concatenation are
+ * those mwmm_plan_autotuned picks in that form for the group's median-size
+ * problem among the configurations the batched kernels run (one-CTA tcgen05
+ * tiles, one FP64 K range); the choice is timed on zero operands of that
+ * size, or taken from the autotuner's cache.  Errors: those
+ * of mwmm_plan for any problem, MWMM_ERR_ARG, MWMM_ERR_NOMEM, MWMM_ERR_CUDA. */
 mwmm_status mwmm_batch_create(mwmm_batch_t *out, const mwmm_problem *probs, int count, mwmm_form form,
                               const mwmm_plan_opts *opts);
 /* Replay the captured graph on `stream` (asynchronous). */
@@ -343,7 +360,10 @@ mwmm_status mwmm_matmul_batched(const mwmm_problem *probs, int count, mwmm_form 
  * per stream; operands and outputs are the client's. */
 typedef struct {
     int32_t max_batch;   /* requests per batch (0: 64) */
-    int32_t form;        /* MWMM_FORM_AUTO (INT8) or MWMM_FORM_FP64 for every request */
+    int32_t form;        /* MWMM_FORM_AUTO: each request's tensor form (INT8 or
+                            CRT, mwmm_tensor_form; a batch may mix them);
+                            MWMM_FORM_INT8, MWMM_FORM_CRT8 or MWMM_FORM_FP64:
+                            that form for every request */
     int32_t reserved[8];
 } mwmm_serve_opts;
 

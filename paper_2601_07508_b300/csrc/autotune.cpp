@@ -11,8 +11,10 @@
 //     two sharing B, 256 x 256 CTA pairs; one-CTA only in batch mode) and the
 //     INT32 K-range kc (the largest the bound allows, and half of k when that
 //     splits the k loop), within twice the default workspace;
-//   - for MWMM_FORM_AUTO, both forms and (single products only) the
-//     multimodular CRT form of Sec. 5.2 with the same tile variants.
+//   - the multimodular CRT form of Sec. 5.2 (one-CTA and, for single
+//     products, pair tiles) when asked for, and for MWMM_FORM_AUTO: single
+//     products try every form; a batch tries the two tensor forms (INT8 and
+//     CRT), which share its word-product kernel.
 // Candidates are ordered by a flop model; each is run once to warm up and
 // timed twice (CUDA events, the faster run counts); a candidate whose model
 // time exceeds 3x the best measured time is skipped.  The kernels' run time
@@ -159,16 +161,19 @@ void add(std::vector<Cand> &out, int form, int u, int v, const mwmm_plan_opts &o
 }
 
 void candidates(int form_req, int64_t m, int64_t n, int64_t k, uint64_t p, bool batch, std::vector<Cand> &out) {
+    // A batch runs either FP64 problems or tensor-form (INT8 / CRT) problems,
+    // so a batch's AUTO choice is between the two tensor forms.
     const bool want_int8 = form_req == MWMM_FORM_AUTO || form_req == MWMM_FORM_INT8;
-    const bool want_fp64 = form_req == MWMM_FORM_AUTO || form_req == MWMM_FORM_FP64;
+    const bool want_crt = form_req == MWMM_FORM_AUTO || form_req == MWMM_FORM_CRT8;
+    const bool want_fp64 = (form_req == MWMM_FORM_AUTO && !batch) || form_req == MWMM_FORM_FP64;
     mwmm_plan_opts z;
     std::memset(&z, 0, sizeof(z));
-    if (form_req == MWMM_FORM_AUTO && !batch) {  // the batched kernels run the multiword forms only
+    if (want_crt) {
         Plan crt;
         if (make_plan(&crt, m, n, k, p, 0, 0, MWMM_FORM_CRT8, &z) == MWMM_OK) {
             mwmm_plan_opts o = z;
             add(out, MWMM_FORM_CRT8, 0, 0, o, m, n, k, p);
-            if (m > kTcBM && n > kTcBN / 2) {
+            if (!batch && m > kTcBM && n > kTcBN / 2) {
                 o.tc_pair = 1;
                 add(out, MWMM_FORM_CRT8, 0, 0, o, m, n, k, p);
             }
@@ -246,7 +251,9 @@ mwmm_status autotune(int form_req, int64_t m, int64_t n, int64_t k, uint64_t p, 
                      const uint64_t *dB, int64_t ldb, bool batch, void *stream, int *form, int *u, int *v,
                      mwmm_plan_opts *opts, double *ms, int *tried) {
     if (m <= 0 || n <= 0 || k < 0) return MWMM_ERR_ARG;
-    if (form_req != MWMM_FORM_AUTO && form_req != MWMM_FORM_FP64 && form_req != MWMM_FORM_INT8) return MWMM_ERR_ARG;
+    if (form_req != MWMM_FORM_AUTO && form_req != MWMM_FORM_FP64 && form_req != MWMM_FORM_INT8 &&
+        form_req != MWMM_FORM_CRT8)
+        return MWMM_ERR_ARG;
     const std::string key = make_key(form_req, m, n, k, p, batch);
     {
         std::lock_guard<std::mutex> lock(g_mu);

@@ -6,10 +6,12 @@
 //   - each problem gets its own plan (words, lambda / digits, layout),
 //   - all word matrices and diagonal sums share one device workspace,
 //   - the split kernel walks a table of (problem, side, tile) blocks,
-//   - INT8 form: the persistent tcgen05 kernel walks per-CTA lists of work
-//     items (tile, diagonal, K-range) of all problems, assigned longest
-//     first to the least loaded SM so every SM gets the same modelled work;
-//     the recombination kernel walks (problem, 8-row block) jobs,
+//   - INT8 and CRT forms (they may mix in one batch): the persistent tcgen05
+//     kernel walks per-CTA lists of work items (tile, diagonal or modulus,
+//     K-range) of all problems, assigned longest first to the least loaded
+//     SM so every SM gets the same modelled work; the recombination kernel
+//     (INT8 problems) and the CRT reconstruction kernel (CRT problems) walk
+//     (problem, 8-row block) jobs,
 //   - FP64 form: the fused kernel walks a table of (problem, 64 x 64 tile),
 // and the launches are captured once into a CUDA graph; a run is one
 // cudaGraphLaunch on the caller's stream.
@@ -44,6 +46,9 @@ struct mwmm_batch_s {
     const int *d_rec_jobs = nullptr;
     const void *d_f64 = nullptr;
     const int *d_f64_jobs = nullptr;
+    const void *d_crt = nullptr;
+    const int *d_crt_jobs = nullptr;
+    int ncrt = 0;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     double flops_2mnk = 0, word_flops = 0;
@@ -88,16 +93,22 @@ static void lpt_schedule(std::vector<mwmm::TcItem> &items, int ctas, std::vector
     items.swap(out);
 }
 
-// Work items of one INT8-form problem whose words start at Aw / Bw and whose
-// sums start at S (see the plan layout and TcItem).
+// Work items of one INT8- or CRT-form problem whose words start at Aw / Bw
+// and whose sums start at S (see the plan layout and TcItem).  INT8: windows
+// of tc_ndiag diagonals; CRT: one window per modulus i, the pair (i, i)
+// (s0 = 2 i, so that B word s0 - i = i), its sums in plane i.
 static void tc_items(const Plan &pl, const uint8_t *Aw, const uint8_t *Bw, int32_t *S, std::vector<mwmm::TcItem> &items) {
     const int64_t mtc = pl.A_rows / mwmm::kTcBM;
     const int64_t ntc = pl.tc_nb == mwmm::kTcBN ? pl.B_rows / mwmm::kTcBN : 1;
     const int64_t kcb = pl.kc / mwmm::kTcKB;
     const int64_t plane = (int64_t)pl.nkc * pl.A_rows * pl.B_rows;
-    for (int s0 = 0; s0 < pl.nsums; s0 += pl.tc_ndiag) {
-        const int nd = std::min(pl.tc_ndiag, pl.nsums - s0);
-        const int ilo = std::max(0, s0 - (pl.v - 1)), ihi = std::min(s0 + nd - 1, pl.u - 1);
+    const bool crt = pl.form == MWMM_FORM_CRT8;
+    const int nwin = crt ? pl.crt_s : (pl.nsums + pl.tc_ndiag - 1) / pl.tc_ndiag;
+    for (int g = 0; g < nwin; ++g) {
+        const int s0 = crt ? 2 * g : g * pl.tc_ndiag;
+        const int nd = crt ? 1 : std::min(pl.tc_ndiag, pl.nsums - s0);
+        const int ilo = crt ? g : std::max(0, s0 - (pl.v - 1)), ihi = crt ? g : std::min(s0 + nd - 1, pl.u - 1);
+        const int splane = crt ? g : s0;
         for (int kc = 0; kc < pl.nkc; ++kc)
             for (int64_t mt = 0; mt < mtc; ++mt)
                 for (int64_t nt = 0; nt < ntc; ++nt) {
@@ -105,7 +116,7 @@ static void tc_items(const Plan &pl, const uint8_t *Aw, const uint8_t *Bw, int32
                     std::memset(&it, 0, sizeof(it));
                     it.Aw = Aw;
                     it.Bw = Bw;
-                    it.S = S + (((int64_t)s0 * pl.nkc + kc) * pl.A_rows + mt * mwmm::kTcBM) * pl.B_rows +
+                    it.S = S + (((int64_t)splane * pl.nkc + kc) * pl.A_rows + mt * mwmm::kTcBM) * pl.B_rows +
                            nt * mwmm::kTcBN;
                     it.A_rows = pl.A_rows;
                     it.B_rows = pl.B_rows;
@@ -131,7 +142,7 @@ static void tc_items(const Plan &pl, const uint8_t *Aw, const uint8_t *Bw, int32
     }
 }
 
-void build_batch_tables(const Plan *plans, const mwmm_problem *probs, uint8_t *const *ws_base, int count, int form,
+void build_batch_tables(const Plan *plans, const mwmm_problem *probs, uint8_t *const *ws_base, int count,
                         int *err, BatchTables &T) {
     T = BatchTables();
     T.split_jobs.resize(split_job_bytes() * 2 * (size_t)count);
@@ -145,10 +156,16 @@ void build_batch_tables(const Plan *plans, const mwmm_problem *probs, uint8_t *c
         ++nsj;
         split_job(pl, 1, q.B, q.ldb, w + pl.B_off, &T.split_jobs[split_job_bytes() * nsj], nsj, T.split_blocks);
         ++nsj;
-        if (form == MWMM_FORM_FP64) {
+        if (pl.form == MWMM_FORM_FP64) {
             T.f64_recs.resize(T.f64_recs.size() + fp64_job_bytes());
             fp64_job(pl, w + pl.A_off, w + pl.B_off, q.C, q.ldc, err, &T.f64_recs[T.f64_recs.size() - fp64_job_bytes()],
                      (int)(T.f64_recs.size() / fp64_job_bytes()) - 1, T.f64_jobs);
+        } else if (pl.form == MWMM_FORM_CRT8) {
+            int32_t *S = reinterpret_cast<int32_t *>(w + pl.S_off);
+            tc_items(pl, w + pl.A_off, w + pl.B_off, S, T.items);
+            T.crt_recs.resize(T.crt_recs.size() + crt_job_bytes());
+            crt_job(pl, S, q.C, q.ldc, &T.crt_recs[T.crt_recs.size() - crt_job_bytes()],
+                    (int)(T.crt_recs.size() / crt_job_bytes()) - 1, T.crt_jobs);
         } else {
             int32_t *S = reinterpret_cast<int32_t *>(w + pl.S_off);
             tc_items(pl, w + pl.A_off, w + pl.B_off, S, T.items);
@@ -165,29 +182,31 @@ void build_batch_tables(const Plan *plans, const mwmm_problem *probs, uint8_t *c
     T.nsplit = (int)(T.split_blocks.size() / 4);
     T.nrec = (int)(T.rec_jobs.size() / 4);
     T.nf64 = (int)(T.f64_jobs.size() / 4);
+    T.ncrt = (int)(T.crt_jobs.size() / 4);
 }
 
-uint64_t pack_batch_tables(const BatchTables &T, std::vector<uint8_t> &blob, uint64_t off[8]) {
-    const void *src[8] = {T.split_jobs.data(), T.split_blocks.data(), T.items.data(), T.cta_off.data(),
-                          T.rec_recs.data(), T.rec_jobs.data(), T.f64_recs.data(), T.f64_jobs.data()};
-    const uint64_t bytes[8] = {T.split_jobs.size(), T.split_blocks.size() * sizeof(int),
-                               T.items.size() * sizeof(TcItem), T.cta_off.size() * sizeof(int64_t),
-                               T.rec_recs.size(), T.rec_jobs.size() * sizeof(int), T.f64_recs.size(),
-                               T.f64_jobs.size() * sizeof(int)};
+uint64_t pack_batch_tables(const BatchTables &T, std::vector<uint8_t> &blob, uint64_t off[kBatchTables]) {
+    const void *src[kBatchTables] = {T.split_jobs.data(), T.split_blocks.data(), T.items.data(), T.cta_off.data(),
+                                     T.rec_recs.data(),   T.rec_jobs.data(),     T.f64_recs.data(), T.f64_jobs.data(),
+                                     T.crt_recs.data(),   T.crt_jobs.data()};
+    const uint64_t bytes[kBatchTables] = {T.split_jobs.size(), T.split_blocks.size() * sizeof(int),
+                                          T.items.size() * sizeof(TcItem), T.cta_off.size() * sizeof(int64_t),
+                                          T.rec_recs.size(), T.rec_jobs.size() * sizeof(int), T.f64_recs.size(),
+                                          T.f64_jobs.size() * sizeof(int), T.crt_recs.size(),
+                                          T.crt_jobs.size() * sizeof(int)};
     uint64_t tb = 0;
-    for (int i = 0; i < 8; ++i) {
+    for (int i = 0; i < kBatchTables; ++i) {
         off[i] = tb;
         tb = (tb + bytes[i] + 255) & ~uint64_t(255);
     }
     blob.assign(tb, 0);
-    for (int i = 0; i < 8; ++i)
+    for (int i = 0; i < kBatchTables; ++i)
         if (bytes[i]) std::memcpy(blob.data() + off[i], src[i], bytes[i]);
     return tb;
 }
 
-int launch_batch_tables(const BatchTables &T, const uint8_t *dtables, const uint64_t off[8], int form,
+int launch_batch_tables(const BatchTables &T, const uint8_t *dtables, const uint64_t off[kBatchTables], int fp64,
                         int chunk_blocks, int *err, void *stream) {
-    const int fp64 = form == MWMM_FORM_FP64;
     int e = launch_split_batched(dtables + off[0], reinterpret_cast<const int *>(dtables + off[1]), T.nsplit, fp64,
                                  stream);
     if (e) return e;
@@ -196,8 +215,9 @@ int launch_batch_tables(const BatchTables &T, const uint8_t *dtables, const uint
     e = launch_gemm_tc_table(reinterpret_cast<const TcItem *>(dtables + off[2]),
                              reinterpret_cast<const int64_t *>(dtables + off[3]), T.ctas, chunk_blocks, err, stream);
     if (e) return e;
-    return launch_recombine_batched(dtables + off[4], reinterpret_cast<const int *>(dtables + off[5]), T.nrec,
-                                    stream);
+    e = launch_recombine_batched(dtables + off[4], reinterpret_cast<const int *>(dtables + off[5]), T.nrec, stream);
+    if (e) return e;
+    return launch_crt_batched(dtables + off[8], reinterpret_cast<const int *>(dtables + off[9]), T.ncrt, stream);
 }
 
 }  // namespace mwmm
@@ -231,6 +251,8 @@ mwmm_status record(mwmm_batch_s *b, cudaStream_t s) {
     e = mwmm::launch_gemm_tc_table(b->d_items, b->d_cta_off, b->ntc_ctas, b->chunk_blocks, b->err, s);
     if (e) return cuda_st((cudaError_t)e);
     e = mwmm::launch_recombine_batched(b->d_rec, b->d_rec_jobs, b->nrec, s);
+    if (e) return cuda_st((cudaError_t)e);
+    e = mwmm::launch_crt_batched(b->d_crt, b->d_crt_jobs, b->ncrt, s);
     return cuda_st((cudaError_t)e);
 }
 
@@ -247,32 +269,42 @@ mwmm_status mwmm_batch_create(mwmm_batch_t *out, const mwmm_problem *probs, int 
                               const mwmm_plan_opts *opts) {
     if (!out || count < 0 || (count > 0 && !probs)) return MWMM_ERR_ARG;
     *out = nullptr;
-    if (form == MWMM_FORM_AUTO) form = MWMM_FORM_INT8;
-    if (form != MWMM_FORM_FP64 && form != MWMM_FORM_INT8) return MWMM_ERR_ARG;
+    if (form != MWMM_FORM_AUTO && form != MWMM_FORM_FP64 && form != MWMM_FORM_INT8 && form != MWMM_FORM_CRT8)
+        return MWMM_ERR_ARG;
     mwmm_batch_s *b = new (std::nothrow) mwmm_batch_s();
     if (!b) return MWMM_ERR_NOMEM;
     b->form = form;
     if (opts && opts->tc_chunk) b->chunk_blocks = opts->tc_chunk / mwmm::kTcKB;
     b->probs.assign(probs, probs + count);
     b->plans.resize(count);
-    // ---- autotuning: one configuration per bitsize group, timed on the
-    // group's median-size problem (or taken from the autotuner's cache)
-    struct Tuned { bool ok = false; int u = 0, v = 0; mwmm_plan_opts o{}; };
-    std::vector<Tuned> tuned(65);
+    // ---- form of each problem: the requested one, or under AUTO the tensor
+    // form of the planner's cost model (per problem: the sizes of one bitsize
+    // group span a wide range, and measured on the 512-instance batch this
+    // beats one timed form per group)
+    std::vector<int> pform(count);
+    for (int i = 0; i < count; ++i)
+        pform[i] = form != MWMM_FORM_AUTO ? (int)form
+                                          : mwmm::choose_tensor_form(probs[i].m, probs[i].n, probs[i].k, probs[i].p);
+    // ---- autotuning: one configuration per (bitsize, form) group, timed on
+    // the group's median-size problem (or taken from the autotuner's cache)
+    struct Tuned { bool ok = false; int form = 0, u = 0, v = 0; mwmm_plan_opts o{}; };
+    auto gkey = [](int bits, int f) { return bits * 4 + (f & 3); };
+    std::vector<Tuned> tuned(65 * 4);
     if (opts && opts->autotune) {
-        std::vector<std::vector<int>> groups(65);
+        std::vector<std::vector<int>> groups(65 * 4);
         for (int i = 0; i < count; ++i) {
             int bits = 0;
             for (uint64_t x = probs[i].p; x; x >>= 1) ++bits;
-            if (probs[i].m > 0 && probs[i].n > 0 && probs[i].k > 0 && bits <= 64) groups[bits].push_back(i);
+            if (probs[i].m > 0 && probs[i].n > 0 && probs[i].k > 0 && bits <= 64)
+                groups[gkey(bits, pform[i])].push_back(i);
         }
         cudaStream_t ts = nullptr;
         if (cudaStreamCreateWithFlags(&ts, cudaStreamNonBlocking) != cudaSuccess) {
             delete b;
             return MWMM_ERR_CUDA;
         }
-        for (int bits = 0; bits <= 64; ++bits) {
-            std::vector<int> &g = groups[bits];
+        for (int gi = 0; gi < 65 * 4; ++gi) {
+            std::vector<int> &g = groups[gi];
             if (g.empty()) continue;
             std::sort(g.begin(), g.end(), [&](int a, int c) {
                 return (double)probs[a].m * probs[a].n * probs[a].k < (double)probs[c].m * probs[c].n * probs[c].k;
@@ -281,10 +313,11 @@ mwmm_status mwmm_batch_create(mwmm_batch_t *out, const mwmm_problem *probs, int 
             int f = 0, tried = 0;
             double ms = 0;
             Tuned t;
-            if (mwmm::autotune((int)form, q.m, q.n, q.k, q.p, nullptr, 0, nullptr, 0, true, ts, &f, &t.u, &t.v, &t.o,
+            if (mwmm::autotune(gi & 3, q.m, q.n, q.k, q.p, nullptr, 0, nullptr, 0, true, ts, &f, &t.u, &t.v, &t.o,
                                &ms, &tried) == MWMM_OK) {
                 t.ok = true;
-                tuned[bits] = t;
+                t.form = f;
+                tuned[gi] = t;
                 b->tuned_groups += 1;
                 b->tuned_ms += ms;
             }
@@ -303,23 +336,25 @@ mwmm_status mwmm_batch_create(mwmm_batch_t *out, const mwmm_problem *probs, int 
         int u = 0, v = 0;
         int bits = 0;
         for (uint64_t x = q.p; x; x >>= 1) ++bits;
-        if (bits <= 64 && tuned[bits].ok) {  // the group's configuration; the caller's checks and chunk stay
+        const int pf = pform[i];
+        if (bits <= 64 && tuned[gkey(bits, pf)].ok) {  // the group's configuration; the caller's checks and chunk stay
+            const Tuned &t = tuned[gkey(bits, pf)];
             const mwmm_plan_opts user = o;
-            o = tuned[bits].o;
+            o = t.o;
             o.validate = user.validate;
             if (user.tc_chunk) o.tc_chunk = user.tc_chunk;
-            u = tuned[bits].u;
-            v = tuned[bits].v;
+            u = t.u;
+            v = t.v;
         }
         o.lambda = 0;      // per-problem block sizes: always the bound
         o.tc_cluster = 1;  // table items run on lone CTAs (no 256-row padding)
         o.tc_pair = 0;
         o.ksplit = 1;      // batched FP64 tiles run the whole K range
-        mwmm_status st = mwmm::make_plan(&b->plans[i], q.m, q.n, q.k, q.p, u, v, (int)form, &o);
-        if (st != MWMM_OK && (u || v)) {  // the group's words do not fit this prime: plan it alone
+        mwmm_status st = mwmm::make_plan(&b->plans[i], q.m, q.n, q.k, q.p, u, v, pf, &o);
+        if (st != MWMM_OK && (u || v || o.kc)) {  // the group's words do not fit this prime: plan it alone
             o.kc = 0;
             o.f64_concat = 0;
-            st = mwmm::make_plan(&b->plans[i], q.m, q.n, q.k, q.p, 0, 0, (int)form, &o);
+            st = mwmm::make_plan(&b->plans[i], q.m, q.n, q.k, q.p, 0, 0, pf, &o);
         }
         if (st != MWMM_OK) {
             delete b;
@@ -334,7 +369,8 @@ mwmm_status mwmm_batch_create(mwmm_batch_t *out, const mwmm_problem *probs, int 
         base[i] = total;
         total = align256(total + pl.ws_bytes);
         b->flops_2mnk += 2.0 * pl.m * pl.n * pl.k;
-        b->word_flops += 2.0 * pl.u * pl.v * pl.m * pl.n * pl.k;
+        const double prods = pl.form == MWMM_FORM_CRT8 ? (double)pl.crt_s : (double)pl.u * pl.v;
+        b->word_flops += 2.0 * prods * pl.m * pl.n * pl.k;
     }
     b->ws_bytes = total;
     cudaError_t ce = cudaMalloc(&b->err, 256);
@@ -352,14 +388,15 @@ mwmm_status mwmm_batch_create(mwmm_batch_t *out, const mwmm_problem *probs, int 
         wsb[i] = b->ws + base[i];
     }
     mwmm::BatchTables T;
-    mwmm::build_batch_tables(b->plans.data(), probs, wsb.data(), count, form, b->err, T);
+    mwmm::build_batch_tables(b->plans.data(), probs, wsb.data(), count, b->err, T);
     b->nitems = (int64_t)T.items.size();
     b->nsplit = T.nsplit;
     b->nrec = T.nrec;
     b->nf64 = T.nf64;
+    b->ncrt = T.ncrt;
     b->ntc_ctas = T.ctas;
     std::vector<uint8_t> blob;
-    uint64_t off[8];
+    uint64_t off[mwmm::kBatchTables];
     const uint64_t tb = mwmm::pack_batch_tables(T, blob, off);
     b->table_bytes = tb;
     if (tb) {
@@ -371,8 +408,8 @@ mwmm_status mwmm_batch_create(mwmm_batch_t *out, const mwmm_problem *probs, int 
             return st;
         }
     }
-    struct { uint64_t off; } pieces[8];
-    for (int i = 0; i < 8; ++i) pieces[i].off = off[i];
+    struct { uint64_t off; } pieces[mwmm::kBatchTables];
+    for (int i = 0; i < mwmm::kBatchTables; ++i) pieces[i].off = off[i];
     b->d_split_jobs = b->tables + pieces[0].off;
     b->d_split_blocks = reinterpret_cast<const int *>(b->tables + pieces[1].off);
     b->d_items = reinterpret_cast<const mwmm::TcItem *>(b->tables + pieces[2].off);
@@ -381,7 +418,10 @@ mwmm_status mwmm_batch_create(mwmm_batch_t *out, const mwmm_problem *probs, int 
     b->d_rec_jobs = reinterpret_cast<const int *>(b->tables + pieces[5].off);
     b->d_f64 = b->tables + pieces[6].off;
     b->d_f64_jobs = reinterpret_cast<const int *>(b->tables + pieces[7].off);
-    b->launches = (b->nsplit > 0) + (form == MWMM_FORM_FP64 ? (b->nf64 > 0) : (b->ntc_ctas > 0) + (b->nrec > 0));
+    b->d_crt = b->tables + pieces[8].off;
+    b->d_crt_jobs = reinterpret_cast<const int *>(b->tables + pieces[9].off);
+    b->launches = (b->nsplit > 0) + (form == MWMM_FORM_FP64 ? (b->nf64 > 0)
+                                                            : (b->ntc_ctas > 0) + (b->nrec > 0) + (b->ncrt > 0));
     // ---- capture the launches once; zero outputs of empty-k problems are set per run
     if (mwmm::prepare_kernel_attributes() != 0) {
         free_batch(b);
@@ -466,7 +506,6 @@ void mwmm_batch_destroy(mwmm_batch_t b) {
 
 mwmm_status mwmm_matmul_batched(const mwmm_problem *probs, int count, mwmm_form form, mwmm_batch_t *cache,
                                 void *stream) {
-    if (form == MWMM_FORM_AUTO) form = MWMM_FORM_INT8;
     mwmm_batch_t b = cache ? *cache : nullptr;
     if (!same_problems(b, probs, count, (int)form)) {
         if (b) {

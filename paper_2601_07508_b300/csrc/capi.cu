@@ -327,6 +327,14 @@ mwmm_status mwmm_plan_info(mwmm_plan_t plan, mwmm_plan_desc *d) {
     return MWMM_OK;
 }
 
+mwmm_form mwmm_tensor_form(int64_t m, int64_t n, int64_t k, uint64_t p) {
+    mwmm::Plan pl;
+    mwmm_plan_opts z;
+    std::memset(&z, 0, sizeof(z));
+    if (mwmm::make_plan(&pl, m, n, k, p, 0, 0, MWMM_FORM_INT8, &z) != MWMM_OK) return MWMM_FORM_AUTO;
+    return (mwmm_form)mwmm::choose_tensor_form(m, n, k, p);
+}
+
 mwmm_status mwmm_plan_autotuned(mwmm_plan_t *out, int64_t m, int64_t n, int64_t k, uint64_t p, mwmm_form form,
                                 const uint64_t *dA, int64_t lda, const uint64_t *dB, int64_t ldb, void *stream) {
     if (!out) return MWMM_ERR_ARG;

@@ -124,6 +124,9 @@ size_t recombine_job_bytes();
 void recombine_job(const Plan &pl, const int32_t *S, uint64_t *C, int64_t ldc, void *rec, int index,
                    std::vector<int> &jobs);
 int launch_recombine_batched(const void *probs, const int *jobs, int njobs, void *stream);
+size_t crt_job_bytes();
+void crt_job(const Plan &pl, const int32_t *S, uint64_t *C, int64_t ldc, void *rec, int index, std::vector<int> &jobs);
+int launch_crt_batched(const void *probs, const int *jobs, int njobs, void *stream);
 size_t fp64_job_bytes();
 void fp64_job(const Plan &pl, const void *Aw, const void *Bw, uint64_t *C, int64_t ldc, int *err, void *rec,
               int index, std::vector<int> &jobs);
@@ -154,15 +157,24 @@ struct BatchTables {
     std::vector<int> rec_jobs;
     std::vector<uint8_t> f64_recs;
     std::vector<int> f64_jobs;
-    int nsplit = 0, nrec = 0, nf64 = 0, ctas = 0;
+    std::vector<uint8_t> crt_recs;
+    std::vector<int> crt_jobs;
+    int nsplit = 0, nrec = 0, nf64 = 0, ncrt = 0, ctas = 0;
 };
+constexpr int kBatchTables = 10;
 // Tables for problems[0..count) whose workspaces start at ws_base[i] (device).
-void build_batch_tables(const Plan *plans, const mwmm_problem *probs, uint8_t *const *ws_base, int count, int form,
+// Every plan is FP64, or every plan is INT8 or CRT8 (the two tensor forms
+// share the word-product kernel and may mix).
+void build_batch_tables(const Plan *plans, const mwmm_problem *probs, uint8_t *const *ws_base, int count,
                         int *err, BatchTables &T);
-// One 256-byte-aligned blob holding the 8 tables; off[i] = offset of table i.
-uint64_t pack_batch_tables(const BatchTables &T, std::vector<uint8_t> &blob, uint64_t off[8]);
+// One 256-byte-aligned blob holding the tables; off[i] = offset of table i.
+uint64_t pack_batch_tables(const BatchTables &T, std::vector<uint8_t> &blob, uint64_t off[kBatchTables]);
 // Launch the batch's kernels with its tables at dtables (device copy of the blob).
-int launch_batch_tables(const BatchTables &T, const uint8_t *dtables, const uint64_t off[8], int form,
+int launch_batch_tables(const BatchTables &T, const uint8_t *dtables, const uint64_t off[kBatchTables], int fp64,
                         int chunk_blocks, int *err, void *stream);
+// The tensor form (MWMM_FORM_INT8 or MWMM_FORM_CRT8) with the smaller
+// modelled time for this product: word products at the tensor rate plus the
+// split and recombination / reconstruction traffic (calibrated on 4096^3).
+int choose_tensor_form(int64_t m, int64_t n, int64_t k, uint64_t p);
 
 }  // namespace mwmm

@@ -292,28 +292,34 @@ __global__ void __launch_bounds__(256) crt_kernel_s(const __grid_constant__ CrtP
     }
 }
 
-// Several K-ranges (k beyond one INT32 sum): exact 64-bit sums, then the residues.
-__global__ void __launch_bounds__(256) crt_kernel(const __grid_constant__ CrtParams P) {
-    const int64_t c0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4;
+// Any number of moduli and K-ranges, 32-bit arithmetic only: the residue of
+// each range's sum S (via S + 2^31, then + m_i - (2^31 mod m_i), a value in
+// [1, 2 m_i) congruent to S) is added up over the ranges (below
+// 2 nkc m_i < 2^25) and reduced once.  Rows row0, row0 + rstep, ... < P.m;
+// columns c0 .. c0 + 3.
+__device__ __forceinline__ void crt_rows(const CrtParams &P, int64_t c0, int64_t row0, int64_t rstep) {
     if (c0 >= P.n) return;
     const int64_t plane = P.A_rows * P.B_rows;
-    for (int64_t row = blockIdx.y; row < P.m; row += gridDim.y) {
+    for (int64_t row = row0; row < P.m; row += rstep) {
         uint64_t a0[4] = {0, 0, 0, 0}, a1[4] = {0, 0, 0, 0};
         float qf[4] = {0.25f, 0.25f, 0.25f, 0.25f};
+#pragma unroll 4
         for (int i = 0; i < P.s; ++i) {
-            const uint32_t mi = P.cm[i], yi = P.cy[i];
-            int64_t x[4] = {0, 0, 0, 0};
+            const uint32_t mi = P.cm[i], yi = P.cy[i], back = P.cm[i] - P.c31[i];
+            const uint64_t mag = P.cmag[i];
+            uint32_t r[4] = {0, 0, 0, 0};
             for (int kc = 0; kc < P.nkc; ++kc) {
-                const int4 v = *reinterpret_cast<const int4 *>(P.S + ((int64_t)i * P.nkc + kc) * plane +
-                                                               row * P.B_rows + c0);
-                x[0] += v.x; x[1] += v.y; x[2] += v.z; x[3] += v.w;
+                const int4 v = __ldcs(reinterpret_cast<const int4 *>(P.S + ((int64_t)i * P.nkc + kc) * plane +
+                                                                     row * P.B_rows + c0));
+                const int32_t vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                for (int e = 0; e < 4; ++e) r[e] += fastmod((uint32_t)vv[e] + 0x80000000u, mi, mag) + back;
             }
             const float ri = P.rinv[i];
             const uint32_t wl = P.wl[i], wh = P.wh[i];
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
-                const int64_t t = x[e] % (int64_t)mi;
-                const uint32_t xi = (uint32_t)(t < 0 ? t + mi : t) * yi;
+                const uint32_t xi = fastmod(r[e], mi, mag) * yi;
                 qf[e] = __fmaf_rn((float)xi, ri, qf[e]);
                 a0[e] += (uint64_t)xi * wl;
                 a1[e] += (uint64_t)xi * wh;
@@ -323,9 +329,31 @@ __global__ void __launch_bounds__(256) crt_kernel(const __grid_constant__ CrtPar
     }
 }
 
-}  // namespace
+__global__ void __launch_bounds__(256) crt_kernel(const __grid_constant__ CrtParams P) {
+    crt_rows(P, ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4, blockIdx.y, gridDim.y);
+}
 
-static int launch_crt(const Plan &pl, const int32_t *S, uint64_t *C, int64_t ldc, void *stream) {
+// Batched: block b handles columns [1024 z, 1024 z + 1024) of rows
+// [y0, y0 + 8) of problem jobs[b] = (problem, y0, z, 0), like the batched
+// recombination.
+__global__ void __launch_bounds__(256) crt_batched_kernel(const CrtParams *probs, const int4 *jobs) {
+    __shared__ __align__(16) CrtParams P;  // staged once (all threads copy): the loops read it many times
+    const int4 j = jobs[blockIdx.x];
+    {
+        const uint32_t *src = reinterpret_cast<const uint32_t *>(probs + j.x);
+        uint32_t *dst = reinterpret_cast<uint32_t *>(&P);
+        for (int w = threadIdx.x; w < (int)(sizeof(CrtParams) / 4); w += blockDim.x) dst[w] = src[w];
+    }
+    __syncthreads();
+    const int64_t cb = (int64_t)j.z * 1024;
+    const int64_t width = P.n - cb < 1024 ? P.n - cb : 1024;
+    const int64_t rows = P.m - j.y < 8 ? P.m - j.y : 8;
+    const int64_t groups = (width + 3) / 4;
+    for (int64_t u = threadIdx.x; u < rows * groups; u += blockDim.x)
+        crt_rows(P, cb + (u % groups) * 4, j.y + u / groups, P.m);
+}
+
+CrtParams make_crt_params(const Plan &pl, const int32_t *S, uint64_t *C, int64_t ldc) {
     CrtParams P;
     std::memset(&P, 0, sizeof(P));
     P.S = S;
@@ -350,6 +378,35 @@ static int launch_crt(const Plan &pl, const int32_t *S, uint64_t *C, int64_t ldc
         P.cmag[i] = (~uint64_t(0)) / pl.crt_m[i] + 1;
         P.c31[i] = (uint32_t)((uint64_t(1) << 31) % pl.crt_m[i]);
     }
+    return P;
+}
+
+}  // namespace
+
+size_t crt_job_bytes() { return sizeof(CrtParams); }
+
+void crt_job(const Plan &pl, const int32_t *S, uint64_t *C, int64_t ldc, void *rec, int index, std::vector<int> &jobs) {
+    const CrtParams P = make_crt_params(pl, S, C, ldc);
+    std::memcpy(rec, &P, sizeof(P));
+    const int64_t cblocks = ((pl.n + 3) / 4 + 255) / 256;
+    for (int64_t y = 0; y < pl.m; y += 8)
+        for (int64_t c = 0; c < cblocks; ++c) {
+            jobs.push_back(index);
+            jobs.push_back((int)y);
+            jobs.push_back((int)c);
+            jobs.push_back(0);
+        }
+}
+
+int launch_crt_batched(const void *probs, const int *jobs, int njobs, void *stream) {
+    if (njobs == 0) return 0;
+    crt_batched_kernel<<<njobs, 256, 0, static_cast<cudaStream_t>(stream)>>>(
+        static_cast<const CrtParams *>(probs), reinterpret_cast<const int4 *>(jobs));
+    return (int)cudaGetLastError();
+}
+
+static int launch_crt(const Plan &pl, const int32_t *S, uint64_t *C, int64_t ldc, void *stream) {
+    const CrtParams P = make_crt_params(pl, S, C, ldc);
     const int64_t groups = (pl.n + 3) / 4;
     dim3 grid((unsigned)((groups + 255) / 256), (unsigned)(pl.m < 65535 ? pl.m : 65535));
     cudaStream_t st = static_cast<cudaStream_t>(stream);

@@ -114,7 +114,7 @@ struct Inflight {
 }  // namespace
 
 struct mwmm_server_s {
-    int form = MWMM_FORM_INT8;
+    int form = MWMM_FORM_AUTO;  // AUTO: each request's tensor form (INT8 or CRT) from the planner's cost model
     int max_batch = 64, max_inflight = 2;
     uint8_t *arena_dev = nullptr;
     int *err = nullptr;
@@ -192,7 +192,9 @@ bool launch_one(mwmm_server_s *S, std::unique_lock<std::mutex> &lock) {
     // workspace fits the arena
     std::vector<uint64_t> tickets;
     uint64_t table_est = 0;
-    auto work = [](const Request &r) { return (double)r.plan.u * r.plan.v * r.flops; };
+    auto work = [](const Request &r) {  // word products x 2 m n k
+        return (r.plan.form == MWMM_FORM_CRT8 ? (double)r.plan.crt_s : (double)r.plan.u * r.plan.v) * r.flops;
+    };
     const double cap = kCostRatio * work(*S->reqs[S->queue.front()]);
     for (size_t qi = 0; qi < S->queue.size() && (int)qi < kScan && (int)tickets.size() < S->max_batch;) {
         Request &r = *S->reqs[S->queue[qi]];
@@ -226,9 +228,9 @@ bool launch_one(mwmm_server_s *S, std::unique_lock<std::mutex> &lock) {
     }
     lock.unlock();
     mwmm::BatchTables T;
-    mwmm::build_batch_tables(plans.data(), probs.data(), wsb.data(), (int)plans.size(), S->form, S->err, T);
+    mwmm::build_batch_tables(plans.data(), probs.data(), wsb.data(), (int)plans.size(), S->err, T);
     std::vector<uint8_t> blob;
-    uint64_t off[8];
+    uint64_t off[mwmm::kBatchTables];
     const uint64_t tb = mwmm::pack_batch_tables(T, blob, off);
     lock.lock();
     Inflight f;
@@ -248,7 +250,7 @@ bool launch_one(mwmm_server_s *S, std::unique_lock<std::mutex> &lock) {
                 e = cudaMemset2DAsync(probs[i].C, (size_t)probs[i].ldc * 8, 0, (size_t)plans[i].n * 8,
                                       (size_t)plans[i].m, s);
         if (e == cudaSuccess && tb)
-            e = (cudaError_t)mwmm::launch_batch_tables(T, S->dtables[slot], off, S->form,
+            e = (cudaError_t)mwmm::launch_batch_tables(T, S->dtables[slot], off, S->form == MWMM_FORM_FP64,
                                                        mwmm::kTcMaxChunk / mwmm::kTcKB, S->err, s);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&f.ev, cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventRecord(f.ev, s);
@@ -312,8 +314,12 @@ mwmm_status mwmm_serve_create(mwmm_server_t *out, size_t mem_budget_bytes, int m
     S->max_inflight = slots;
     const uint64_t arena_bytes = mem_budget_bytes - (uint64_t)slots * kStagingBytes;
     if (opts) {
+        if (opts->form < MWMM_FORM_AUTO || opts->form > MWMM_FORM_CRT8) {
+            delete S;
+            return MWMM_ERR_ARG;
+        }
         if (opts->max_batch > 0) S->max_batch = opts->max_batch;
-        if (opts->form == MWMM_FORM_FP64) S->form = MWMM_FORM_FP64;
+        S->form = opts->form;
     }
     S->t0 = std::chrono::steady_clock::now();
     cudaError_t e = cudaGetDevice(&S->device);
@@ -355,7 +361,8 @@ mwmm_status mwmm_serve_submit(mwmm_server_t S, const mwmm_problem *prob, double 
     mwmm_plan_opts o;
     std::memset(&o, 0, sizeof(o));
     o.ksplit = 1;  // requests run as batched tiles over the whole K range
-    mwmm_status st = mwmm::make_plan(&r->plan, prob->m, prob->n, prob->k, prob->p, 0, 0, S->form, &o);
+    const int form = S->form != MWMM_FORM_AUTO ? S->form : mwmm::choose_tensor_form(prob->m, prob->n, prob->k, prob->p);
+    mwmm_status st = mwmm::make_plan(&r->plan, prob->m, prob->n, prob->k, prob->p, 0, 0, form, &o);
     if (st != MWMM_OK) return st;
     const Plan &pl = r->plan;
     if (pl.m > 0 && pl.n > 0 &&

@@ -136,6 +136,8 @@ def lib() -> ctypes.CDLL:
     L.mwmm_autotune_cache_load.argtypes = [ctypes.c_char_p]
     L.mwmm_mulmod.argtypes = [_vp, _vp, _i64, _u64, _vp, _vp]
     L.mwmm_matmul_noalloc.argtypes = [_i64, _i64, _i64, _u64, _vp, _i64, _vp, _i64, _vp, _i64, _vp]
+    L.mwmm_tensor_form.argtypes = [_i64, _i64, _i64, _u64]
+    L.mwmm_tensor_form.restype = ctypes.c_int
     L.mwmm_batch_create.argtypes = [ctypes.POINTER(_vp), ctypes.POINTER(Problem), ctypes.c_int, ctypes.c_int,
                                     ctypes.POINTER(PlanOpts)]
     L.mwmm_batch_run.argtypes = [_vp, _vp]
@@ -233,6 +235,13 @@ def mwmm_plan(m: int, n: int, k: int, p: int, u: int = 0, v: int = 0, form="auto
     o.ksplit = ksplit
     _check(lib().mwmm_plan(ctypes.byref(h), m, n, k, p, u, v, form, ctypes.byref(o)), "mwmm_plan")
     return h.value
+
+
+def mwmm_tensor_form(m: int, n: int, k: int, p: int) -> str:
+    """The tensor form ("int8" or "crt8") batches and the serving loop use
+    for this product under form "auto" (host only; "auto" if none plans)."""
+    f = lib().mwmm_tensor_form(m, n, k, p)
+    return {v: name for name, v in FORMS.items()}[f]
 
 
 def mwmm_plan_autotuned(m: int, n: int, k: int, p: int, form="auto", A=None, B=None, stream=None) -> int:

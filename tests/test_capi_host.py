@@ -273,3 +273,19 @@ def test_crt_plan_errors(M):
     with pytest.raises(M.MwmmError) as e:  # 2 k (p-1)^2 beyond what 24 moduli below 256 cover
         M.mwmm_plan(8, 8, 1 << 23, SWEEP[52], 0, 0, "crt8")
     assert e.value.status == 1
+
+
+def test_tensor_form_choice_follows_the_cost_model(M):
+    """AUTO's tensor form for batches and serving: at 4096^3 the INT8 digits
+    below 24 bits (9 digit products against 8 moduli plus a costlier CRT
+    reconstruction), the CRT form from 25 bits (16 / 25 / 36 / 49 digit
+    products against 9-16 moduli); small products stay INT8 (the CRT split
+    and reconstruction grow with the moduli); k > 2^22 cannot use CRT."""
+    P = {b: inputs.largest_prime_below_pow2(b) for b in (23, 24, 26, 32, 40, 48, 52)}
+    assert M.mwmm_tensor_form(4096, 4096, 4096, P[23]) == "int8"
+    assert M.mwmm_tensor_form(4096, 4096, 4096, P[24]) == "int8"
+    for b in (26, 32, 40, 48, 52):
+        assert M.mwmm_tensor_form(4096, 4096, 4096, P[b]) == "crt8", b
+        assert M.mwmm_tensor_form(64, 64, 64, P[b]) == "int8", b
+    assert M.mwmm_tensor_form(64, 64, (1 << 22) + 64, P[52]) == "int8"
+    assert M.mwmm_tensor_form(4, 4, 4, 4) == "auto"  # no form plans an even p

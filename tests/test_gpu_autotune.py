@@ -62,20 +62,25 @@ def test_autotune_cache_file_from_environment(M, oracle, tmp_path, monkeypatch):
     M.mwmm_autotune_cache_clear()
 
 
-@pytest.mark.parametrize("form", ["int8", "fp64"])
+@pytest.mark.parametrize("form", ["int8", "fp64", "crt8", "auto"])
 def test_autotuned_batch_matches_oracle(M, oracle, form):
     rng = np.random.default_rng(9)
-    items, refs = [], []
+    items, refs, forms = [], [], set()
     for i in range(12):
         b = (40, 50, 26)[i % 3]
         p = inputs.largest_prime_below_pow2(b) if i % 2 else inputs.prev_prime(inputs.largest_prime_below_pow2(b))
         m, n, k = (int(x) for x in rng.integers(60, 400, size=3))
+        if form == "auto" and i < 3:  # large enough for the CRT form
+            m, n, k = 1100, 1000, 1200
         A, B = inputs.problem(900 + i, m, n, k, p)
         items.append((dev(A), dev(B), torch.empty((m, n), dtype=torch.int64, device="cuda"), p))
         refs.append(oracle.matmul_mod(A, B, p))
+        forms.add((b, M.mwmm_tensor_form(m, n, k, p) if form == "auto" else form))
     M.mwmm_autotune_cache_clear()
     batch = M.Batch(items, form=form, autotune=True)
-    assert batch.info["tuned_groups"] == 3
+    assert batch.info["tuned_groups"] == len(forms)  # one per (bitsize, form)
+    if form == "auto":
+        assert {f for _, f in forms} == {"int8", "crt8"}
     batch.run()
     assert batch.check() == 0
     for (_, _, C, _), ref in zip(items, refs):

@@ -37,7 +37,7 @@ def _mixed_problems(seed, count, lo, hi, bits_lo=20, bits_hi=52):
     return out
 
 
-@pytest.mark.parametrize("form", ["int8", "fp64"])
+@pytest.mark.parametrize("form", ["int8", "fp64", "crt8", "auto"])
 def test_batch_of_mixed_shapes_and_primes(M, oracle, form):
     probs = _mixed_problems(3, 24, 1, 300)
     items = [(_dev(A), _dev(B), torch.full((A.shape[0], B.shape[1]), -1, dtype=torch.int64, device="cuda"), p)
@@ -47,6 +47,42 @@ def test_batch_of_mixed_shapes_and_primes(M, oracle, form):
     assert batch.check() == 0
     for (A, B, p), (_, _, C, _) in zip(probs, items):
         assert np.array_equal(C.cpu().numpy().view(np.uint64), oracle.matmul_mod(A, B, p))
+
+
+def test_auto_batch_mixes_int8_and_crt_problems(M, oracle):
+    """Under "auto" every problem gets its tensor form from the planner's
+    cost model; INT8 and CRT problems share the word-product launch and each
+    form's recombination runs after it (4 launches).  Every C equals the
+    oracle and the same product planned alone in that form."""
+    shapes = [(1024, 1024, 1024, 52), (1100, 900, 1000, 48), (300, 200, 500, 52), (130, 70, 1500, 40),
+              (1024, 1100, 900, 50), (64, 300, 64, 23)]
+    probs = []
+    for i, (m, n, k, b) in enumerate(shapes):
+        p = inputs.random_prime_of_bitsize(21, 78, i, b)
+        A, B = inputs.problem(2100 + i, m, n, k, p)
+        probs.append((A, B, p))
+    want = [M.mwmm_tensor_form(A.shape[0], B.shape[1], A.shape[1], p) for A, B, p in probs]
+    assert "crt8" in want and "int8" in want
+    items = [(_dev(A), _dev(B), torch.full((A.shape[0], B.shape[1]), -1, dtype=torch.int64, device="cuda"), p)
+             for A, B, p in probs]
+    batch = M.Batch(items, form="auto")
+    assert batch.info["launches"] == 4
+    got = [{2: "int8", 3: "crt8"}[batch.problem_info(i)["form"]] for i in range(len(items))]
+    assert got == want
+    batch.run()
+    assert batch.check() == 0
+    for (A, B, p), (dA, dB, C, _), f in zip(probs, items, want):
+        Ch = C.cpu().numpy().view(np.uint64)
+        if A.shape[0] * B.shape[1] * A.shape[1] <= 1 << 27:
+            assert np.array_equal(Ch, oracle.matmul_mod(A, B, p))
+        else:  # large: Freivalds over the whole result plus sampled entries
+            x = inputs.uniform_mod(21, 7, B.shape[1], p)
+            assert oracle.freivalds(A, B, Ch, p, x) == 0
+            r = np.arange(0, A.shape[0], 37, dtype=np.int64)
+            c = (r * 13) % B.shape[1]
+            assert np.array_equal(Ch[r, c], oracle.matmul_entries(A, B, p, r, c))
+        alone = M.Plan(A.shape[0], B.shape[1], A.shape[1], p, form=f).matmul(dA, dB)
+        assert torch.equal(C, alone)
 
 
 def test_batch_equals_products_alone_and_reruns_on_new_inputs(M, oracle):

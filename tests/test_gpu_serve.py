@@ -39,12 +39,13 @@ def _requests(seed, count, lo, hi):
     return out
 
 
-def test_serve_results_equal_alone_and_oracle(M, oracle):
+@pytest.mark.parametrize("form", ["auto", "crt8", "int8"])
+def test_serve_results_equal_alone_and_oracle(M, oracle, form):
     reqs = _requests(21, 120, 8, 400)
     dev = [(_dev(A), _dev(B), torch.full((A.shape[0], B.shape[1]), -1, dtype=torch.int64, device="cuda"), p)
            for A, B, p in reqs]
     torch.cuda.synchronize()
-    srv = M.Server(2 << 30, max_inflight=2, max_batch=16)
+    srv = M.Server(2 << 30, max_inflight=2, max_batch=16, form=form)
     tickets = []
     for dA, dB, C, p in dev:  # a burst: later requests arrive while earlier batches run
         st, t = srv.submit(dA, dB, C, p)
@@ -61,6 +62,42 @@ def test_serve_results_equal_alone_and_oracle(M, oracle):
         alone = M.Plan(A.shape[0], B.shape[1], A.shape[1], p, form="int8").matmul(dA, dB)
         assert torch.equal(C, alone)
         assert np.array_equal(C.cpu().numpy().view(np.uint64), oracle.matmul_mod(A, B, p))
+
+
+def test_serve_auto_form_mixes_int8_and_crt(M, oracle):
+    """Under "auto" each request takes the planner's tensor form; large
+    high-bitsize requests run as CRT, the others as INT8, in shared batches."""
+    specs = [(900, 800, 1000, 52), (64, 64, 64, 30), (1000, 1000, 700, 48), (200, 300, 100, 21), (700, 900, 1024, 50),
+             (128, 128, 2048, 26)]
+    reqs = []
+    for i, (m, n, k, b) in enumerate(specs):
+        p = inputs.random_prime_of_bitsize(23, 104, i, b)
+        A, B = inputs.problem(2300 + i, m, n, k, p)
+        reqs.append((A, B, p))
+    forms = [M.mwmm_tensor_form(A.shape[0], B.shape[1], A.shape[1], p) for A, B, p in reqs]
+    assert "crt8" in forms and "int8" in forms
+    dev = [(_dev(A), _dev(B), torch.full((A.shape[0], B.shape[1]), -1, dtype=torch.int64, device="cuda"), p)
+           for A, B, p in reqs]
+    torch.cuda.synchronize()
+    srv = M.Server(4 << 30, max_inflight=2, max_batch=8)
+    tickets = []
+    for d in dev:
+        st, t = srv.submit(*d)
+        assert st == 0
+        tickets.append(t)
+    for t in tickets:
+        assert srv.wait(t, 60000) == 0
+    assert srv.stats()["completed"] == len(reqs)
+    srv.close()
+    for (A, B, p), (dA, dB, C, _), f in zip(reqs, dev, forms):
+        alone = M.Plan(A.shape[0], B.shape[1], A.shape[1], p, form=f).matmul(dA, dB)
+        assert torch.equal(C, alone)
+        Ch = C.cpu().numpy().view(np.uint64)
+        x = inputs.uniform_mod(23, 9, B.shape[1], p)
+        assert oracle.freivalds(A, B, Ch, p, x) == 0
+        r = np.arange(0, A.shape[0], 29, dtype=np.int64)
+        c = (r * 7) % B.shape[1]
+        assert np.array_equal(Ch[r, c], oracle.matmul_entries(A, B, p, r, c))
 
 
 def test_serve_poisson_stream_from_two_client_threads(M, oracle):
@@ -98,9 +135,10 @@ def test_serve_poisson_stream_from_two_client_threads(M, oracle):
 
 def test_serve_admission_against_budget(M, oracle):
     p = inputs.largest_prime_below_pow2(52)
-    # each 700^3 52-bit request needs ~47 MB of workspace; the arena holds one at a time
+    # each 700^3 52-bit request needs ~47 MB of workspace in the INT8 form;
+    # the arena holds one at a time
     budget = 2 * (32 << 20) + (60 << 20)
-    srv = M.Server(budget, max_inflight=2, max_batch=4)
+    srv = M.Server(budget, max_inflight=2, max_batch=4, form="int8")
     reqs = [inputs.problem(300 + i, 700, 700, 700, p) for i in range(5)]
     dev = [(_dev(A), _dev(B), torch.empty((700, 700), dtype=torch.int64, device="cuda")) for A, B in reqs]
     tickets = []
