@@ -58,6 +58,11 @@ def parse_args():
     ap.add_argument("--no-unbalanced", action="store_true", help="skip the block-Wiedemann shape")
     ap.add_argument("--variant-sweep", action="store_true",
                     help="also time every FP64 variant at every bitsize 20..52 (Table 4 crossovers; minutes)")
+    ap.add_argument("--batched-only", action="store_true",
+                    help="profiling aid: run only the batched workload and print its results as the JSON line")
+    ap.add_argument("--batch-instances", type=int, default=512, help="first N instances of the batched workload")
+    ap.add_argument("--batch-forms", default="int8,auto,fp64", help="forms of the batched workload")
+    ap.add_argument("--no-batch-autotune", action="store_true", help="batched workload without the autotuner")
     ap.add_argument("--serve-requests", type=int, default=20000)
     ap.add_argument("--serve-pool", type=int, default=256, help="distinct operand sets the requests cycle through")
     return ap.parse_args()
@@ -269,13 +274,13 @@ def workload_config(args, bits):
 
 
 # ----------------------------------------------------------------------------- batched and serving workloads
-def run_batched(dev, runs=5):
+def run_batched(dev, runs=5, count=512, forms=("int8", "auto", "fp64"), autotune=True):
     """512 instances over the 64 largest primes below 2^50, m, n, k log-uniform
     in [128, 2048] (seed 4), INT8 and FP64 forms and the autotuner's tensor
     form (INT8 or CRT per instance), one graph replay per run."""
     import torch
     from paper_2601_07508_b300 import mwmm
-    spec = inputs.batch_instances()
+    spec = inputs.batch_instances()[:count]
     items = []
     for i, (m, n, k, p) in enumerate(spec):
         A, B = inputs.problem(4000 + i, m, n, k, p)
@@ -287,9 +292,9 @@ def run_batched(dev, runs=5):
                        "instance's tensor form (INT8 digits or CRT) from the planner's cost model, the "
                        "autotuner's configuration per (bitsize, form) group"}
     ref = None
-    for form in ("int8", "auto", "fp64"):
-        fitems = items if form == "int8" else [(a, b, torch.empty_like(c), p) for (a, b, c, p) in items]
-        bt = mwmm.Batch(fitems, form=form, autotune=True)
+    for form in forms:
+        fitems = items if ref is None else [(a, b, torch.empty_like(c), p) for (a, b, c, p) in items]
+        bt = mwmm.Batch(fitems, form=form, autotune=autotune)
         bt.run()
         torch.cuda.synchronize()
         nrun = 1 if form == "fp64" else runs
@@ -311,10 +316,10 @@ def run_batched(dev, runs=5):
         if form == "auto":
             fc = [bt.problem_info(i)["form"] for i in range(len(fitems))]
             out[form]["forms"] = {"int8": fc.count(2), "crt8": fc.count(3)}
-        if form == "int8":
-            ref = [c.clone() for (_, _, c, _) in fitems]
+        if ref is None:
+            ref, ref_form = [c.clone() for (_, _, c, _) in fitems], form
         else:
-            out[form + "_equals_int8"] = all(torch.equal(c, r) for (_, _, c, _), r in zip(fitems, ref))
+            out[form + "_equals_" + ref_form] = all(torch.equal(c, r) for (_, _, c, _), r in zip(fitems, ref))
         del bt
     out["flops_2mnk_per_run"] = sum(2.0 * m * n * k for (m, n, k, _) in spec)
     return out
@@ -641,6 +646,14 @@ def main():
     bits = [int(x) for x in args.bits.split(",")]
     n = args.size
     seed_off = rank_seed(rank)
+    if args.batched_only:  # profiling aid: the batched workload alone
+        mwmm.lib()
+        forms = tuple(f for f in args.batch_forms.split(",") if f)
+        b = run_batched(dev, count=args.batch_instances, forms=forms, autotune=not args.no_batch_autotune)
+        if rank == 0:
+            print(json.dumps({"metric": "batched modular 2mnk GOP/s", "value": b[forms[0]]["gops"], "unit": "GOP/s",
+                              "higher_is_better": True, "batched_multi_prime": b}))
+        return 0
 
     # CPU baseline first (before any GPU work; rank 0 at N = 1 only)
     cpu_baseline = None

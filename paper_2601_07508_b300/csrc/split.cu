@@ -51,8 +51,10 @@ struct SplitParams {
     int *err;
     int64_t cbias;              // INT8 form: 128 (1 + 256 + ... + 256^(words-2))
     int crt;                    // CRT form: residues instead of digits
-    uint32_t cm[kMaxCrt];       // moduli
-    uint64_t cmu[kMaxCrt];      // floor((2^64 - 1) / m_i)
+    uint32_t cm[kMaxCrt];       // moduli (odd primes below 256)
+    uint32_t cM[kMaxCrt];       // floor(2^32 / m_i) + 1
+    uint32_t c18[kMaxCrt], c36[kMaxCrt];  // 2^18 mod m_i, 2^36 mod m_i
+    float cmh[kMaxCrt];         // 1.5 * 2^23 + (m_i - 1) / 2
 };
 
 // Small integers to bf16 without the conversion pipe.  For |v| < 2^22 the
@@ -72,11 +74,20 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
     return __byte_perm(__float_as_uint(lo), __float_as_uint(hi), 0x7632u);
 }
 
-// Signed residue of x modulo m < 2^16: x - m umulhi(x, mu) is below 2m.
-__device__ __forceinline__ float signed_residue(uint64_t x, uint32_t m, uint64_t mu) {
-    uint32_t r = (uint32_t)(x - __umul64hi(x, mu) * m);
-    if (r >= m) r -= m;
-    return small_int_float(r > (m - 1) / 2 ? (int)r - (int)m : (int)r);
+// Signed residue of x < 2^52 modulo an odd m < 256, in [-(m-1)/2, (m-1)/2],
+// with 32-bit operations only: from the 18-bit limbs x = x2 2^36 + x1 2^18
+// + x0, z = x2 (2^36 mod m) + x1 (2^18 mod m) + x0 + (m-1)/2 < 2^27 is
+// congruent to x + (m-1)/2.  q = umulhi(z, floor(2^32 / m) + 1) is floor(z / m)
+// or one more (the multiplier exceeds 2^32 / m by less than 1, and
+// z / 2^32 < 1/32), so z - q m is z mod m, or that minus m (then m is added
+// back).  The residue minus (m-1)/2 is the signed one; its FP32 value comes
+// from the magic exponent with the offset folded into the constant cmh.
+__device__ __forceinline__ float signed_residue(uint32_t x0, uint32_t x1, uint32_t x2, uint32_t m, uint32_t M,
+                                                uint32_t c18, uint32_t c36, float cmh) {
+    const uint32_t z = x2 * c36 + x1 * c18 + x0 + (m >> 1);
+    int r = (int)(z - __umulhi(z, M) * m);
+    r += (r >> 31) & (int)m;
+    return __int_as_float(0x4B400000 + r) - cmh;
 }
 
 __device__ __forceinline__ uint64_t load_tile_elem(const SplitParams &P, int64_t r, int64_t l) {
@@ -168,29 +179,46 @@ __device__ __forceinline__ void split_int8_tile(const SplitParams &P, uint64_t (
     const uint64_t half = (P.p - 1) / 2;
     for (int unit = threadIdx.x; unit < kST * 8; unit += 256) {
         const int rr = unit / 8, g = unit % 8;
-        uint64_t x[8];
-        int64_t t[8];  // signed representative + digit bias
-#pragma unroll
-        for (int e = 0; e < 8; ++e) {
-            x[e] = tile[rr][8 * g + e];
-            t[e] = ((x[e] <= half) ? (int64_t)x[e] : (int64_t)x[e] - (int64_t)P.p) + P.cbias;
-        }
         const int64_t r = r0 + rr;
         if (r >= P.rows_pad) continue;  // a last row tile may be partial (rows_pad 16 or 32)
-        for (int w = 0; w < P.words; ++w) {
-            const bool last = (w == P.words - 1);
-            float f[8];
-            if (P.crt) {
-#pragma unroll
-                for (int e = 0; e < 8; ++e) f[e] = signed_residue(x[e], P.cm[w], P.cmu[w]);
-            } else {
-#pragma unroll
-                for (int e = 0; e < 8; ++e) f[e] = int8_digit(t[e], w, last);
-            }
+        // word w of the unit's 8 entries, packed bf16, to its swizzled 16-byte granule
+        auto store = [&](int w, const float (&f)[8]) {
             uint8_t *dst = P.out + ((int64_t)(w + P.wpad) * P.wstride + kb * P.kstride + r) * kTileBytes +
                            ((g ^ (int)(r & 7)) * 16);
             *reinterpret_cast<uint4 *>(dst) = make_uint4(pack_bf16x2(f[0], f[1]), pack_bf16x2(f[2], f[3]),
                                                          pack_bf16x2(f[4], f[5]), pack_bf16x2(f[6], f[7]));
+        };
+        if (P.crt) {
+            uint32_t x0[8], x1[8], x2[8];  // 18-bit limbs
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                const uint64_t x = tile[rr][8 * g + e];
+                x0[e] = (uint32_t)x & 0x3FFFFu;
+                x1[e] = (uint32_t)(x >> 18) & 0x3FFFFu;
+                x2[e] = (uint32_t)(x >> 36);
+            }
+            for (int w = 0; w < P.words; ++w) {
+                const uint32_t m = P.cm[w], M = P.cM[w], c18 = P.c18[w], c36 = P.c36[w];
+                const float cmh = P.cmh[w];
+                float f[8];
+#pragma unroll
+                for (int e = 0; e < 8; ++e) f[e] = signed_residue(x0[e], x1[e], x2[e], m, M, c18, c36, cmh);
+                store(w, f);
+            }
+        } else {
+            int64_t t[8];  // signed representative + digit bias
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                const uint64_t x = tile[rr][8 * g + e];
+                t[e] = ((x <= half) ? (int64_t)x : (int64_t)x - (int64_t)P.p) + P.cbias;
+            }
+            for (int w = 0; w < P.words; ++w) {
+                const bool last = (w == P.words - 1);
+                float f[8];
+#pragma unroll
+                for (int e = 0; e < 8; ++e) f[e] = int8_digit(t[e], w, last);
+                store(w, f);
+            }
         }
         for (int z = 0; z < P.wpad; ++z) {  // the zero words on both sides
             const int64_t base = kb * P.kstride + r;
@@ -251,8 +279,12 @@ SplitParams make_split_params(const Plan &pl, int side, const uint64_t *M, int64
     P.cbias = 0;
     for (int i = 0; i + 1 < P.words && !P.crt && pl.form != MWMM_FORM_FP64; ++i) P.cbias += (int64_t)128 << (8 * i);
     for (int i = 0; i < kMaxCrt; ++i) {
-        P.cm[i] = i < pl.crt_s ? pl.crt_m[i] : 1;
-        P.cmu[i] = i < pl.crt_s ? (~uint64_t(0)) / pl.crt_m[i] : 0;
+        const uint32_t m = i < pl.crt_s ? pl.crt_m[i] : 3;
+        P.cm[i] = m;
+        P.cM[i] = (uint32_t)((uint64_t(1) << 32) / m + 1);
+        P.c18[i] = (uint32_t)((uint64_t(1) << 18) % m);
+        P.c36[i] = (uint32_t)((uint64_t(1) << 36) % m);
+        P.cmh[i] = 12582912.0f + (float)(m >> 1);
     }
     return P;
 }
