@@ -77,14 +77,14 @@ static int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 // split (8 B read + 2 B per digit written per entry) and recombination
 // (4 B per sum read + 8 B written per output) at ~5 TB/s; the CRT split and
 // reconstruction are issue-bound at ~0.6 ps per (entry, modulus) and
-// ~1.6 ps per (output, modulus).
+// ~1.35 ps per (output, modulus).
 static double tensor_form_cost(const Plan &pl) {
     const double mnk2 = 2.0 * pl.m * pl.n * pl.k, mk_kn = (double)pl.m * pl.k + (double)pl.k * pl.n,
                  mn = (double)pl.m * pl.n;
     constexpr double kTensor = 1.5e15, kHbm = 5.0e12;
     if (pl.form == MWMM_FORM_CRT8) {
         const double s = pl.crt_s;
-        return s * mnk2 / kTensor + mk_kn * s * 0.6e-12 + mn * s * (1.6e-12 + 4.0 * (pl.nkc - 1) / kHbm);
+        return s * mnk2 / kTensor + mk_kn * s * 0.6e-12 + mn * s * (1.35e-12 + 4.0 * (pl.nkc - 1) / kHbm);
     }
     return (double)pl.u * pl.v * mnk2 / kTensor + mk_kn * (8.0 + 2.0 * pl.u) / kHbm +
            mn * (4.0 * pl.nsums * pl.nkc + 8.0) / kHbm;

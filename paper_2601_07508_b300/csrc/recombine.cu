@@ -205,9 +205,14 @@ int launch_recombine_batched(const void *probs, const int *jobs, int njobs, void
 // 1/4, so the offset makes the floor exact.  Then
 //   C mod p = (sum_i x_i w_i - q W) mod p,  w_i = (M / m_i) mod p, W = M mod p,
 // with w_i = wh_i 2^26 + wl_i: the sums of x_i wl_i and x_i wh_i (< 2^42
-// each) are exact in 64 bits and are combined mod p once per output.  Remainders by the small moduli use the division-free method of
-// Lemire, Kaser and Kurz ("Faster remainder by direct computation", 2019):
-// for 32-bit a, a mod m = umulhi64((ceil(2^64 / m) a) mod 2^64, m).
+// each) are exact in 64 bits and are combined mod p once per output.
+// Remainders by the small moduli take one 32-bit multiply-high: for
+// 0 <= a < 2^32, q = umulhi(a, floor(2^32 / m) + 1) is floor(a / m) or one
+// more (the multiplier exceeds 2^32 / m by less than 1), so a - q m is
+// a mod m or that minus m, and m is added back when it is negative.  A sum
+// S (|S| <= 131071 * 2^14 < 2^31 - 2^14) enters as S + O_i with
+// O_i = m_i ceil((2^31 - 1) / m_i), which keeps it in [0, 2^32) and
+// congruent to S.
 namespace {
 
 struct CrtParams {
@@ -217,19 +222,23 @@ struct CrtParams {
     int s, nkc;
     uint64_t p, mu, mu90, W;  // mu90 = floor(2^90 / p) when p > 2^26, else 0
     uint32_t cm[kMaxCrt], cy[kMaxCrt];
-    uint32_t c31[kMaxCrt];    // 2^31 mod m_i
+    uint32_t cB[kMaxCrt];     // floor(2^32 / m_i) + 1
+    uint32_t cO[kMaxCrt];     // m_i ceil((2^31 - 1) / m_i)
     uint32_t wl[kMaxCrt], wh[kMaxCrt];  // w_i = wh_i 2^26 + wl_i
     float rinv[kMaxCrt];
-    uint64_t cmag[kMaxCrt];   // ceil(2^64 / m_i)
 };
 
-// a mod m for any 32-bit a (division-free, see above); the high word of the
-// 96-bit product (mag a mod 2^64) m is formed from two 32 x 32 -> 64 products.
-__device__ __forceinline__ uint32_t fastmod(uint32_t a, uint32_t m, uint64_t mag) {
-    const uint64_t low = mag * a;
-    const uint64_t t = (uint64_t)(uint32_t)low * m;
-    const uint64_t u = (low >> 32) * (uint64_t)m + (t >> 32);
-    return (uint32_t)(u >> 32);
+// a mod m for 0 <= a < 2^32 (see above); B = floor(2^32 / m) + 1.
+__device__ __forceinline__ uint32_t mod_small(uint32_t a, uint32_t m, uint32_t B) {
+    int r = (int)(a - __umulhi(a, B) * m);
+    r += (r >> 31) & (int)m;
+    return (uint32_t)r;
+}
+
+// FP32 value of an integer 0 <= x < 2^22 without the conversion pipe: the
+// bit pattern 0x4B400000 + x is 1.5 * 2^23 + x.
+__device__ __forceinline__ float small_uint_float(uint32_t x) {
+    return __int_as_float(0x4B400000 + (int)x) - 12582912.0f;
 }
 
 // C mod p from the per-output sums a0 + 2^26 a1 = sum_i x_i w_i and the
@@ -278,11 +287,9 @@ __global__ void __launch_bounds__(256) crt_kernel_s(const __grid_constant__ CrtP
                 const int32_t vv[4] = {v[j].x, v[j].y, v[j].z, v[j].w};
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
-                    // S + 2^31 is in [0, 2^32): its residue, minus 2^31 mod m_i
-                    const uint32_t t = fastmod((uint32_t)vv[e] + 0x80000000u, P.cm[i], P.cmag[i]);
-                    const uint32_t r = t >= P.c31[i] ? t - P.c31[i] : t + P.cm[i] - P.c31[i];
+                    const uint32_t r = mod_small((uint32_t)vv[e] + P.cO[i], P.cm[i], P.cB[i]);
                     const uint32_t xi = r * P.cy[i];  // < m_i^2 < 2^16
-                    qf[e] = __fmaf_rn((float)xi, P.rinv[i], qf[e]);
+                    qf[e] = __fmaf_rn(small_uint_float(xi), P.rinv[i], qf[e]);
                     a0[e] += (uint64_t)xi * P.wl[i];  // 32 x 32 -> 64
                     a1[e] += (uint64_t)xi * P.wh[i];
                 }
@@ -292,10 +299,9 @@ __global__ void __launch_bounds__(256) crt_kernel_s(const __grid_constant__ CrtP
     }
 }
 
-// Any number of moduli and K-ranges, 32-bit arithmetic only: the residue of
-// each range's sum S (via S + 2^31, then + m_i - (2^31 mod m_i), a value in
-// [1, 2 m_i) congruent to S) is added up over the ranges (below
-// 2 nkc m_i < 2^25) and reduced once.  Rows row0, row0 + rstep, ... < P.m;
+// Any number of moduli and K-ranges, 32-bit arithmetic only: the residues
+// of the ranges' sums (each below m_i) are added up (below nkc m_i < 2^24)
+// and reduced once.  Rows row0, row0 + rstep, ... < P.m;
 // columns c0 .. c0 + 3.
 __device__ __forceinline__ void crt_rows(const CrtParams &P, int64_t c0, int64_t row0, int64_t rstep) {
     if (c0 >= P.n) return;
@@ -305,22 +311,21 @@ __device__ __forceinline__ void crt_rows(const CrtParams &P, int64_t c0, int64_t
         float qf[4] = {0.25f, 0.25f, 0.25f, 0.25f};
 #pragma unroll 4
         for (int i = 0; i < P.s; ++i) {
-            const uint32_t mi = P.cm[i], yi = P.cy[i], back = P.cm[i] - P.c31[i];
-            const uint64_t mag = P.cmag[i];
+            const uint32_t mi = P.cm[i], yi = P.cy[i], Bi = P.cB[i], Oi = P.cO[i];
             uint32_t r[4] = {0, 0, 0, 0};
             for (int kc = 0; kc < P.nkc; ++kc) {
                 const int4 v = __ldcs(reinterpret_cast<const int4 *>(P.S + ((int64_t)i * P.nkc + kc) * plane +
                                                                      row * P.B_rows + c0));
                 const int32_t vv[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-                for (int e = 0; e < 4; ++e) r[e] += fastmod((uint32_t)vv[e] + 0x80000000u, mi, mag) + back;
+                for (int e = 0; e < 4; ++e) r[e] += mod_small((uint32_t)vv[e] + Oi, mi, Bi);
             }
             const float ri = P.rinv[i];
             const uint32_t wl = P.wl[i], wh = P.wh[i];
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
-                const uint32_t xi = fastmod(r[e], mi, mag) * yi;
-                qf[e] = __fmaf_rn((float)xi, ri, qf[e]);
+                const uint32_t xi = mod_small(r[e], mi, Bi) * yi;
+                qf[e] = __fmaf_rn(small_uint_float(xi), ri, qf[e]);
                 a0[e] += (uint64_t)xi * wl;
                 a1[e] += (uint64_t)xi * wh;
             }
@@ -375,8 +380,9 @@ CrtParams make_crt_params(const Plan &pl, const int32_t *S, uint64_t *C, int64_t
         P.rinv[i] = 1.0f / (float)pl.crt_m[i];
         P.wl[i] = (uint32_t)(pl.crt_w[i] & ((1u << 26) - 1));
         P.wh[i] = (uint32_t)(pl.crt_w[i] >> 26);
-        P.cmag[i] = (~uint64_t(0)) / pl.crt_m[i] + 1;
-        P.c31[i] = (uint32_t)((uint64_t(1) << 31) % pl.crt_m[i]);
+        const uint64_t mi = pl.crt_m[i];
+        P.cB[i] = (uint32_t)((uint64_t(1) << 32) / mi + 1);
+        P.cO[i] = (uint32_t)(mi * ((((uint64_t)1 << 31) - 1 + mi - 1) / mi));
     }
     return P;
 }
