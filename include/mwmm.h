@@ -52,6 +52,9 @@
  *   - Every call returns a status; nothing exits, traps or prints.
  *   - A plan is not thread-safe: calls on one plan must be serialised and
  *     the plan's own workspace is shared by its calls on one stream.
+ *   - A plan's device-side state is allocated on the device current at its
+ *     first device call; a later call made with another device current
+ *     returns MWMM_ERR_ARG.
  */
 #ifndef MWMM_H
 #define MWMM_H

@@ -52,9 +52,9 @@ mwmm_status cuda_status(int e) {
 // Device resources every call needs: the error flags (allocated on the first
 // device call, on the device current at that time).
 mwmm_status ensure_device(Plan &pl) {
-    if (pl.err_dev) return MWMM_OK;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return MWMM_ERR_CUDA;
+    if (pl.err_dev) return dev == pl.device ? MWMM_OK : MWMM_ERR_ARG;  // the plan's state lives on pl.device
     void *p = nullptr;
     cudaError_t e = cudaMalloc(&p, 256);
     if (e != cudaSuccess) return cuda_status((int)e);
