@@ -352,11 +352,13 @@ mwmm_status mwmm_matmul_batched(const mwmm_problem *probs, int count, mwmm_form 
 /* ---- serving: continuous batching of products as they arrive ----
  * A server owns a worker thread and a device-memory budget.  Clients submit
  * problems (device pointers; the operands stay on the device) from any
- * thread and get a ticket.  The worker admits queued requests, oldest first,
- * as soon as their workspace fits in what is left of the budget, groups the
- * admitted ones into a batch (the batched kernels of mwmm_batch_create,
- * without graph capture) and launches it on the next of max_inflight
- * streams while earlier batches still run; finished batches return their
+ * thread and get a ticket.  The worker forms a batch around the queued
+ * request with the least work (or the oldest one, once it has waited several
+ * times its estimated run time), adds queued requests of similar work in
+ * arrival order as soon as their workspace fits in what is left of the
+ * budget, and launches the batch (the batched kernels of mwmm_batch_create,
+ * without graph capture) on the next of max_inflight streams while earlier
+ * batches still run; finished batches return their
  * memory and wake their waiters.  Latency = completion seen by the worker
  * minus arrival (submit time, or an earlier scheduled time the client gives).
  * The budget covers the per-request workspaces plus one 32 MiB table region

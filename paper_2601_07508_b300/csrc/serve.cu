@@ -5,14 +5,17 @@
 // worker
 //   1. retires finished batches (event query): their requests complete, their
 //      workspace returns to the arena, waiters are woken;
-//   2. while fewer than max_inflight batches are on the GPU, forms a batch from
-//      the head of the FIFO queue: the head request always, then later queued
-//      requests (in arrival order, within the first kScan) whose word-product
-//      work is at most kCostRatio times the head's -- all requests of a batch
-//      complete together, so a small request is not held back by a much larger
-//      batch-mate; a skipped large request heads a batch of its own next.  A
-//      request joins if its workspace fits in the arena now (admission against
-//      the memory budget) and the batch has room,
+//   2. while fewer than max_inflight batches are on the GPU, forms a batch:
+//      its head is the queued request with the least word-product work
+//      (within the first kScan), or the oldest one once it has waited more
+//      than kAgeFactor times its estimated run time (shortest work first
+//      with aging: a medium request does not wait behind several large ones,
+//      and a large one cannot starve); then later queued requests (in arrival
+//      order) whose work is at most kCostRatio times the head's -- all
+//      requests of a batch complete together, so a small request is not held
+//      back by a much larger batch-mate.  A request joins if its workspace
+//      fits in the arena now (admission against the memory budget) and the
+//      batch has room,
 //      then builds the batch's tables, copies them to the device and launches
 //      the batched kernels on the next of its streams -- so requests that
 //      arrive while other batches run are admitted as memory frees up, and
@@ -43,6 +46,8 @@ namespace {
 constexpr uint64_t kStagingBytes = 32ull << 20;  // pinned table staging per stream
 constexpr int kScan = 512;                         // queued requests a batch formation looks at
 constexpr double kCostRatio = 4.0;                 // batch-mates do at most this much more work than the head
+constexpr double kAgeFactor = 3.0;                 // a request waiting this many times its run time goes next
+constexpr double kAgeFloor = 1e-3;                 // ... plus this many seconds
 
 uint64_t align256(uint64_t x) { return (x + 255) & ~uint64_t(255); }
 
@@ -188,13 +193,36 @@ bool launch_one(mwmm_server_s *S, std::unique_lock<std::mutex> &lock) {
             break;
         }
     if (slot < 0) return false;
-    // admission: FIFO head first, then similar-sized requests, while the
-    // workspace fits the arena
+    // admission: the head, then similar-sized requests in arrival order,
+    // while the workspace fits the arena.  The head is the queued request
+    // with the least work (among the first kScan), unless the oldest one has
+    // waited more than kAgeFactor times its estimated run time: short
+    // requests pass long ones, and a long one cannot starve.
     std::vector<uint64_t> tickets;
     uint64_t table_est = 0;
     auto work = [](const Request &r) {  // word products x 2 m n k
         return (r.plan.form == MWMM_FORM_CRT8 ? (double)r.plan.crt_s : (double)r.plan.u * r.plan.v) * r.flops;
     };
+    size_t head = 0;
+    {
+        const Request &old = *S->reqs[S->queue.front()];
+        const double run_s = work(old) / 1.0e15 + 5e-5;  // ~1 PFLOP/s of word products plus launch overhead
+        if (S->now() - old.t_arrival <= kAgeFactor * run_s + kAgeFloor) {
+            double best = work(old);
+            for (size_t qi = 1; qi < S->queue.size() && (int)qi < kScan; ++qi) {
+                const double w = work(*S->reqs[S->queue[qi]]);
+                if (w < best) {
+                    best = w;
+                    head = qi;
+                }
+            }
+        }
+    }
+    if (head != 0) {  // move the head to the front; the others keep their order
+        const uint64_t tk = S->queue[head];
+        S->queue.erase(S->queue.begin() + (long)head);
+        S->queue.push_front(tk);
+    }
     const double cap = kCostRatio * work(*S->reqs[S->queue.front()]);
     for (size_t qi = 0; qi < S->queue.size() && (int)qi < kScan && (int)tickets.size() < S->max_batch;) {
         Request &r = *S->reqs[S->queue[qi]];
