@@ -266,11 +266,10 @@ __device__ __forceinline__ void crt_store(const CrtParams &P, const uint64_t (&a
 // One K-range, S moduli known at compile time: the modulus loop unrolls and
 // the per-modulus constants become immediate kernel-parameter operands.
 template <int S>
-__global__ void __launch_bounds__(256) crt_kernel_s(const __grid_constant__ CrtParams P) {
-    const int64_t c0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4;
+__device__ __forceinline__ void crt_rows_s(const CrtParams &P, int64_t c0, int64_t row0, int64_t rstep) {
     if (c0 >= P.n) return;
     const int64_t plane = P.A_rows * P.B_rows;
-    for (int64_t row = blockIdx.y; row < P.m; row += gridDim.y) {
+    for (int64_t row = row0; row < P.m; row += rstep) {
         uint64_t a0[4] = {0, 0, 0, 0}, a1[4] = {0, 0, 0, 0};
         float qf[4] = {0.25f, 0.25f, 0.25f, 0.25f};
         const int32_t *src = P.S + row * P.B_rows + c0;
@@ -299,6 +298,26 @@ __global__ void __launch_bounds__(256) crt_kernel_s(const __grid_constant__ CrtP
     }
 }
 
+template <int S>
+__global__ void __launch_bounds__(256) crt_kernel_s(const __grid_constant__ CrtParams P) {
+    crt_rows_s<S>(P, ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4, blockIdx.y, gridDim.y);
+}
+
+// One K-range and S moduli: the unrolled rows above, chosen at run time.
+__device__ __forceinline__ bool crt_rows_dispatch(const CrtParams &P, int64_t c0, int64_t row0, int64_t rstep) {
+    if (P.nkc != 1) return false;
+    switch (P.s) {
+#define MWMM_CRT_CASE(k) \
+    case k: crt_rows_s<k>(P, c0, row0, rstep); return true;
+        MWMM_CRT_CASE(1) MWMM_CRT_CASE(2) MWMM_CRT_CASE(3) MWMM_CRT_CASE(4) MWMM_CRT_CASE(5) MWMM_CRT_CASE(6)
+        MWMM_CRT_CASE(7) MWMM_CRT_CASE(8) MWMM_CRT_CASE(9) MWMM_CRT_CASE(10) MWMM_CRT_CASE(11) MWMM_CRT_CASE(12)
+        MWMM_CRT_CASE(13) MWMM_CRT_CASE(14) MWMM_CRT_CASE(15) MWMM_CRT_CASE(16) MWMM_CRT_CASE(17) MWMM_CRT_CASE(18)
+        MWMM_CRT_CASE(19) MWMM_CRT_CASE(20) MWMM_CRT_CASE(21) MWMM_CRT_CASE(22) MWMM_CRT_CASE(23) MWMM_CRT_CASE(24)
+#undef MWMM_CRT_CASE
+        default: return false;
+    }
+}
+
 // Any number of moduli and K-ranges, 32-bit arithmetic only: the residues
 // of the ranges' sums (each below m_i) are added up (below nkc m_i < 2^24)
 // and reduced once.  Rows row0, row0 + rstep, ... < P.m;
@@ -324,7 +343,7 @@ __device__ __forceinline__ void crt_rows(const CrtParams &P, int64_t c0, int64_t
             const uint32_t wl = P.wl[i], wh = P.wh[i];
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
-                const uint32_t xi = mod_small(r[e], mi, Bi) * yi;
+                const uint32_t xi = (P.nkc == 1 ? r[e] : mod_small(r[e], mi, Bi)) * yi;  // one range: r < m_i
                 qf[e] = __fmaf_rn(small_uint_float(xi), ri, qf[e]);
                 a0[e] += (uint64_t)xi * wl;
                 a1[e] += (uint64_t)xi * wh;
@@ -354,8 +373,10 @@ __global__ void __launch_bounds__(256) crt_batched_kernel(const CrtParams *probs
     const int64_t width = P.n - cb < 1024 ? P.n - cb : 1024;
     const int64_t rows = P.m - j.y < 8 ? P.m - j.y : 8;
     const int64_t groups = (width + 3) / 4;
-    for (int64_t u = threadIdx.x; u < rows * groups; u += blockDim.x)
-        crt_rows(P, cb + (u % groups) * 4, j.y + u / groups, P.m);
+    for (int64_t u = threadIdx.x; u < rows * groups; u += blockDim.x) {
+        const int64_t c0 = cb + (u % groups) * 4, row = j.y + u / groups;
+        if (!crt_rows_dispatch(P, c0, row, P.m)) crt_rows(P, c0, row, P.m);
+    }
 }
 
 CrtParams make_crt_params(const Plan &pl, const int32_t *S, uint64_t *C, int64_t ldc) {
