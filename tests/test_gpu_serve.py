@@ -39,7 +39,7 @@ def _requests(seed, count, lo, hi):
     return out
 
 
-@pytest.mark.parametrize("form", ["auto", "crt8", "int8"])
+@pytest.mark.parametrize("form", ["auto", "crt8", "int8", "fp64"])
 def test_serve_results_equal_alone_and_oracle(M, oracle, form):
     reqs = _requests(21, 120, 8, 400)
     dev = [(_dev(A), _dev(B), torch.full((A.shape[0], B.shape[1]), -1, dtype=torch.int64, device="cuda"), p)
@@ -60,7 +60,7 @@ def test_serve_results_equal_alone_and_oracle(M, oracle, form):
     srv.close()
     for (A, B, p), (dA, dB, C, _) in zip(reqs, dev):
         alone = M.Plan(A.shape[0], B.shape[1], A.shape[1], p, form="int8").matmul(dA, dB)
-        assert torch.equal(C, alone)
+        assert torch.equal(C, alone)  # the result is unique: any form alone gives it
         assert np.array_equal(C.cpu().numpy().view(np.uint64), oracle.matmul_mod(A, B, p))
 
 
