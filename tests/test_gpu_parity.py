@@ -555,3 +555,28 @@ def test_reuse_a_words_across_products(M, oracle, form):
         C2 = plan.matmul_reuse_a(dev(B2))
         assert plan.check() == 0
         assert np.array_equal(host(C2), oracle.matmul_mod(A, B2, p))
+
+
+def test_concurrent_plans_on_separate_streams(M, oracle):
+    """Plans of every form, each with its own workspace, launched together on
+    separate streams (their kernels overlap on the device): every result
+    equals the oracle, and rerunning them one at a time gives the same bits."""
+    cases = [(300, 260, 700, 52, "int8"), (257, 300, 513, 40, "crt8"), (190, 70, 1000, 26, "int8"),
+             (128, 129, 300, 32, "fp64"), (400, 64, 260, 48, "crt8"), (333, 111, 222, 20, "fp64")]
+    plans, data, outs = [], [], []
+    for i, (m, n, k, b, form) in enumerate(cases):
+        p = inputs.largest_prime_below_pow2(b)
+        A, B = inputs.problem(7700 + i, m, n, k, p)
+        plans.append(M.Plan(m, n, k, p, form=form))
+        data.append((A, B, p, dev(A), dev(B)))
+        outs.append(torch.full((m, n), -1, dtype=torch.int64, device="cuda"))
+    streams = [torch.cuda.Stream() for _ in cases]
+    torch.cuda.synchronize()
+    for rep in range(3):
+        for pl, (_, _, _, dA, dB), C, st in zip(plans, data, outs, streams):
+            pl.matmul(dA, dB, C, stream=st)
+    torch.cuda.synchronize()
+    for pl, (A, B, p, dA, dB), C in zip(plans, data, outs):
+        assert pl.check() == 0
+        assert np.array_equal(host(C), oracle.matmul_mod(A, B, p))
+        assert torch.equal(pl.matmul(dA, dB), C)
