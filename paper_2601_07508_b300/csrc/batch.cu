@@ -65,31 +65,41 @@ namespace mwmm {
 // run side by side), each to the CTA with the least work so far.  Measured on
 // the 512-instance batch this beats list scheduling in problem order, whose
 // tail is set by whichever problems come last.  Returns items grouped per CTA
-// and offsets.
+// and offsets.  Costs are small integers, so the stable sort is a bucket sort
+// and the items are placed by counting: the serving loop builds these tables
+// for every batch while it also retires finished ones, so they must be cheap.
 static void lpt_schedule(std::vector<mwmm::TcItem> &items, int ctas, std::vector<int64_t> &off) {
-    std::vector<int64_t> cost(items.size());
-    for (size_t i = 0; i < items.size(); ++i) cost[i] = items[i].ni * items[i].nkbc + 2;  // +2: drain and store
-    std::vector<size_t> order(items.size());
-    for (size_t i = 0; i < order.size(); ++i) order[i] = i;
-    std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) { return cost[a] > cost[b]; });
+    const size_t N = items.size();
+    std::vector<int64_t> cost(N);
+    int64_t cmax = 0;
+    for (size_t i = 0; i < N; ++i) {
+        cost[i] = items[i].ni * items[i].nkbc + 2;  // +2: drain and store
+        cmax = std::max(cmax, cost[i]);
+    }
+    // stable order by decreasing cost
+    std::vector<int64_t> start((size_t)cmax + 2, 0);
+    for (size_t i = 0; i < N; ++i) ++start[(size_t)(cmax - cost[i]) + 1];
+    for (size_t c = 1; c < start.size(); ++c) start[c] += start[c - 1];
+    std::vector<size_t> order(N);
+    for (size_t i = 0; i < N; ++i) order[(size_t)start[(size_t)(cmax - cost[i])]++] = i;
+    // each item to the least loaded CTA
     typedef std::pair<int64_t, int> Load;  // (work, cta)
     std::priority_queue<Load, std::vector<Load>, std::greater<Load>> heap;
     for (int c = 0; c < ctas; ++c) heap.push(Load(0, c));
-    std::vector<std::vector<size_t>> per(ctas);
+    std::vector<int> cta_of(N);
+    off.assign(ctas + 1, 0);
     for (size_t i : order) {
         Load l = heap.top();
         heap.pop();
-        per[l.second].push_back(i);
+        cta_of[i] = l.second;
+        ++off[l.second + 1];
         heap.push(Load(l.first + cost[i], l.second));
     }
-    std::vector<mwmm::TcItem> out;
-    out.reserve(items.size());
-    off.assign(ctas + 1, 0);
-    for (int c = 0; c < ctas; ++c) {
-        off[c] = (int64_t)out.size();
-        for (size_t i : per[c]) out.push_back(items[i]);
-    }
-    off[ctas] = (int64_t)out.size();
+    for (int c = 0; c < ctas; ++c) off[c + 1] += off[c];
+    // place the items CTA by CTA, each CTA's in schedule order
+    std::vector<int64_t> pos(off.begin(), off.end() - 1);
+    std::vector<mwmm::TcItem> out(N);
+    for (size_t i : order) out[(size_t)pos[cta_of[i]]++] = items[i];
     items.swap(out);
 }
 
@@ -185,7 +195,32 @@ void build_batch_tables(const Plan *plans, const mwmm_problem *probs, uint8_t *c
     T.ncrt = (int)(T.crt_jobs.size() / 4);
 }
 
-uint64_t pack_batch_tables(const BatchTables &T, std::vector<uint8_t> &blob, uint64_t off[kBatchTables]) {
+int launch_product(const Plan &pl, const uint64_t *dA, int64_t lda, const uint64_t *dB, int64_t ldb, uint64_t *dC,
+                   int64_t ldc, uint8_t *ws, void *stream) {
+    if (pl.m == 0 || pl.n == 0 || pl.k == 0) return 0;
+    int e = launch_split(pl, 0, dA, lda, ws + pl.A_off, stream);
+    if (!e) e = launch_split(pl, 1, dB, ldb, ws + pl.B_off, stream);
+    if (e) return e;
+    if (pl.form == MWMM_FORM_FP64)
+        return launch_gemm_fp64(pl, ws + pl.A_off, ws + pl.B_off, dC, ldc, reinterpret_cast<uint64_t *>(ws + pl.S_off),
+                                pl.err_dev, stream);
+    int32_t *S = reinterpret_cast<int32_t *>(ws + pl.S_off);
+    e = launch_gemm_tc(pl, ws + pl.A_off, ws + pl.B_off, S, pl.err_dev, stream);
+    if (!e) e = launch_recombine(pl, S, dC, ldc, stream);
+    return e;
+}
+
+int64_t batch_items(const Plan &pl) {
+    if (pl.m == 0 || pl.n == 0 || pl.k == 0) return 0;
+    if (pl.form == MWMM_FORM_FP64) return ((pl.m + 63) / 64) * ((pl.n + 63) / 64);
+    const int64_t mtc = pl.A_rows / kTcBM, ntc = pl.tc_nb == kTcBN ? pl.B_rows / kTcBN : 1;
+    const int64_t nwin = pl.form == MWMM_FORM_CRT8 ? pl.crt_s : (pl.nsums + pl.tc_ndiag - 1) / pl.tc_ndiag;
+    return mtc * ntc * nwin * pl.nkc;
+}
+
+// Offsets and total size of the packed tables; with dst != nullptr (and the
+// total <= capacity) the tables are copied there.
+uint64_t pack_batch_tables_to(const BatchTables &T, uint8_t *dst, uint64_t capacity, uint64_t off[kBatchTables]) {
     const void *src[kBatchTables] = {T.split_jobs.data(), T.split_blocks.data(), T.items.data(), T.cta_off.data(),
                                      T.rec_recs.data(),   T.rec_jobs.data(),     T.f64_recs.data(), T.f64_jobs.data(),
                                      T.crt_recs.data(),   T.crt_jobs.data()};
@@ -199,10 +234,16 @@ uint64_t pack_batch_tables(const BatchTables &T, std::vector<uint8_t> &blob, uin
         off[i] = tb;
         tb = (tb + bytes[i] + 255) & ~uint64_t(255);
     }
-    blob.assign(tb, 0);
-    for (int i = 0; i < kBatchTables; ++i)
-        if (bytes[i]) std::memcpy(blob.data() + off[i], src[i], bytes[i]);
+    if (dst && tb <= capacity)
+        for (int i = 0; i < kBatchTables; ++i)
+            if (bytes[i]) std::memcpy(dst + off[i], src[i], bytes[i]);
     return tb;
+}
+
+uint64_t pack_batch_tables(const BatchTables &T, std::vector<uint8_t> &blob, uint64_t off[kBatchTables]) {
+    const uint64_t tb = pack_batch_tables_to(T, nullptr, 0, off);
+    blob.assign(tb, 0);
+    return pack_batch_tables_to(T, blob.data(), tb, off);
 }
 
 int launch_batch_tables(const BatchTables &T, const uint8_t *dtables, const uint64_t off[kBatchTables], int fp64,

@@ -169,6 +169,16 @@ void build_batch_tables(const Plan *plans, const mwmm_problem *probs, uint8_t *c
                         int *err, BatchTables &T);
 // One 256-byte-aligned blob holding the tables; off[i] = offset of table i.
 uint64_t pack_batch_tables(const BatchTables &T, std::vector<uint8_t> &blob, uint64_t off[kBatchTables]);
+// One product with the plan's own (computed-item) kernels on `stream`:
+// split A and B, word products, recombination / reconstruction; ws is the
+// plan's workspace.  k = 0 launches nothing (the caller zeroes C).
+int launch_product(const Plan &pl, const uint64_t *dA, int64_t lda, const uint64_t *dB, int64_t ldb, uint64_t *dC,
+                   int64_t ldc, uint8_t *ws, void *stream);
+// Work items a batch's tables would hold for this plan (tcgen05 items, or
+// FP64 tiles).
+int64_t batch_items(const Plan &pl);
+// The same layout written into dst when it fits in capacity; returns the size either way.
+uint64_t pack_batch_tables_to(const BatchTables &T, uint8_t *dst, uint64_t capacity, uint64_t off[kBatchTables]);
 // Launch the batch's kernels with its tables at dtables (device copy of the blob).
 int launch_batch_tables(const BatchTables &T, const uint8_t *dtables, const uint64_t off[kBatchTables], int fp64,
                         int chunk_blocks, int *err, void *stream);

@@ -48,6 +48,7 @@ constexpr int kScan = 512;                         // queued requests a batch fo
 constexpr double kCostRatio = 4.0;                 // batch-mates do at most this much more work than the head
 constexpr double kAgeFactor = 3.0;                 // a request waiting this many times its run time goes next
 constexpr double kAgeFloor = 1e-3;                 // ... plus this many seconds
+constexpr int64_t kDirectItems = 1024;             // requests with more work items run their own kernels
 
 uint64_t align256(uint64_t x) { return (x + 255) & ~uint64_t(255); }
 
@@ -245,21 +246,29 @@ bool launch_one(mwmm_server_s *S, std::unique_lock<std::mutex> &lock) {
     }
     if (tickets.empty()) return false;
     S->slot_busy[slot] = 1;
-    std::vector<Plan> plans;
-    std::vector<mwmm_problem> probs;
-    std::vector<uint8_t *> wsb;
+    // Large requests (many work items) run the single-product kernels, whose
+    // items are computed on the device; the others share the batch's tables,
+    // which the worker builds on the host.
+    std::vector<Plan> plans, direct;
+    std::vector<mwmm_problem> probs, dprobs;
+    std::vector<uint8_t *> wsb, dws;
+    std::vector<Plan> all_plans;
+    std::vector<mwmm_problem> all_probs;
     for (uint64_t tk : tickets) {
         Request &r = *S->reqs[tk];
-        plans.push_back(r.plan);
-        probs.push_back(r.prob);
-        wsb.push_back(S->arena_dev + r.ws_off);
+        const bool dir = mwmm::batch_items(r.plan) > kDirectItems;
+        (dir ? direct : plans).push_back(r.plan);
+        (dir ? dprobs : probs).push_back(r.prob);
+        (dir ? dws : wsb).push_back(S->arena_dev + r.ws_off);
+        all_plans.push_back(r.plan);
+        all_probs.push_back(r.prob);
     }
     lock.unlock();
     mwmm::BatchTables T;
     mwmm::build_batch_tables(plans.data(), probs.data(), wsb.data(), (int)plans.size(), S->err, T);
-    std::vector<uint8_t> blob;
     uint64_t off[mwmm::kBatchTables];
-    const uint64_t tb = mwmm::pack_batch_tables(T, blob, off);
+    // straight into the slot's pinned staging buffer (free: the slot's previous batch has retired)
+    const uint64_t tb = mwmm::pack_batch_tables_to(T, S->staging[slot], kStagingBytes, off);
     lock.lock();
     Inflight f;
     f.tickets = tickets;
@@ -269,14 +278,16 @@ bool launch_one(mwmm_server_s *S, std::unique_lock<std::mutex> &lock) {
         cudaStream_t s = S->streams[slot];
         lock.unlock();
         cudaError_t e = cudaSuccess;
-        if (tb) {
-            std::memcpy(S->staging[slot], blob.data(), tb);
-            e = cudaMemcpyAsync(S->dtables[slot], S->staging[slot], tb, cudaMemcpyHostToDevice, s);
+        if (tb) e = cudaMemcpyAsync(S->dtables[slot], S->staging[slot], tb, cudaMemcpyHostToDevice, s);
+        for (size_t i = 0; e == cudaSuccess && i < all_plans.size(); ++i)  // k = 0: C = 0
+            if (all_plans[i].m > 0 && all_plans[i].n > 0 && all_plans[i].k == 0)
+                e = cudaMemset2DAsync(all_probs[i].C, (size_t)all_probs[i].ldc * 8, 0, (size_t)all_plans[i].n * 8,
+                                      (size_t)all_plans[i].m, s);
+        for (size_t i = 0; e == cudaSuccess && i < direct.size(); ++i) {
+            direct[i].err_dev = S->err;
+            e = (cudaError_t)mwmm::launch_product(direct[i], dprobs[i].A, dprobs[i].lda, dprobs[i].B, dprobs[i].ldb,
+                                                  dprobs[i].C, dprobs[i].ldc, dws[i], s);
         }
-        for (size_t i = 0; e == cudaSuccess && i < plans.size(); ++i)  // k = 0: C = 0
-            if (plans[i].m > 0 && plans[i].n > 0 && plans[i].k == 0)
-                e = cudaMemset2DAsync(probs[i].C, (size_t)probs[i].ldc * 8, 0, (size_t)plans[i].n * 8,
-                                      (size_t)plans[i].m, s);
         if (e == cudaSuccess && tb)
             e = (cudaError_t)mwmm::launch_batch_tables(T, S->dtables[slot], off, S->form == MWMM_FORM_FP64,
                                                        mwmm::kTcMaxChunk / mwmm::kTcKB, S->err, s);
