@@ -48,7 +48,8 @@ constexpr int kScan = 512;                         // queued requests a batch fo
 constexpr double kCostRatio = 4.0;                 // batch-mates do at most this much more work than the head
 constexpr double kAgeFactor = 3.0;                 // a request waiting this many times its run time goes next
 constexpr double kAgeFloor = 1e-3;                 // ... plus this many seconds
-constexpr int64_t kDirectItems = 1024;             // requests with more work items run their own kernels
+constexpr int64_t kDirectItems = 32;                // requests with more work items run their own kernels
+constexpr int64_t kMaxTableItems = 8192;            // table items per batch (bounds the host's table building)
 
 uint64_t align256(uint64_t x) { return (x + 255) & ~uint64_t(255); }
 
@@ -201,6 +202,7 @@ bool launch_one(mwmm_server_s *S, std::unique_lock<std::mutex> &lock) {
     // requests pass long ones, and a long one cannot starve.
     std::vector<uint64_t> tickets;
     uint64_t table_est = 0;
+    int64_t table_items = 0;
     auto work = [](const Request &r) {  // word products x 2 m n k
         return (r.plan.form == MWMM_FORM_CRT8 ? (double)r.plan.crt_s : (double)r.plan.u * r.plan.v) * r.flops;
     };
@@ -235,6 +237,12 @@ bool launch_one(mwmm_server_s *S, std::unique_lock<std::mutex> &lock) {
                              128 * (uint64_t)r.plan.nsums * r.plan.nkc * (r.plan.A_rows / 128 + 1) *
                                  (r.plan.B_rows / 256 + 1);
         if (table_est + est > kStagingBytes / 2 && !tickets.empty()) break;
+        const int64_t ti = mwmm::batch_items(r.plan) > kDirectItems ? 0 : mwmm::batch_items(r.plan);
+        if (!tickets.empty() && table_items + ti > kMaxTableItems) {  // keeps the host's table building short
+            ++qi;
+            continue;
+        }
+        table_items += ti;
         uint64_t off = 0;
         if (!S->arena.alloc(r.plan.ws_bytes, off)) break;
         r.ws_off = off;
