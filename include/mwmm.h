@@ -356,10 +356,12 @@ mwmm_status mwmm_matmul_batched(const mwmm_problem *probs, int count, mwmm_form 
  * request with the least work (or the oldest one, once it has waited several
  * times its estimated run time), adds queued requests of similar work in
  * arrival order as soon as their workspace fits in what is left of the
- * budget, and launches the batch (the batched kernels of mwmm_batch_create,
- * without graph capture) on the next of max_inflight streams while earlier
- * batches still run; finished batches return their
- * memory and wake their waiters.  Latency = completion seen by the worker
+ * budget, and launches the batch on the next of max_inflight streams while
+ * earlier batches still run.  Requests of at most 32 work items (output
+ * tiles x word windows x K chunks) share the batched kernels of
+ * mwmm_batch_create (without graph capture; at most 8192 items per batch);
+ * larger ones run the single-product kernels of a plan on the same stream.
+ * Finished batches return their memory and wake their waiters.  Latency = completion seen by the worker
  * minus arrival (submit time, or an earlier scheduled time the client gives).
  * The budget covers the per-request workspaces plus one 32 MiB table region
  * per stream; operands and outputs are the client's. */
