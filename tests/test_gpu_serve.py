@@ -100,6 +100,41 @@ def test_serve_auto_form_mixes_int8_and_crt(M, oracle):
         assert np.array_equal(Ch[r, c], oracle.matmul_entries(A, B, p, r, c))
 
 
+@pytest.mark.parametrize("form", ["int8", "crt8"])
+def test_serve_batch_holds_table_and_direct_requests(M, oracle, form):
+    """Requests of at most 32 tcgen05 work items go through the batched
+    tables, larger ones through the single-product kernels of a plan.  The
+    shapes straddle that line with work within 4x of each other, so a burst
+    puts both kinds in one batch; every result equals the oracle's."""
+    shapes = [(64, 64, 64), (128, 256, 1000), (256, 256, 512), (256, 512, 512), (200, 300, 600), (512, 768, 1024)]
+    reqs = []
+    for i in range(2 * len(shapes)):
+        m, n, k = shapes[i % len(shapes)]
+        p = inputs.random_prime_of_bitsize(31, 104, i, 52 - (i % 3))
+        A, B = inputs.problem(3100 + i, m, n, k, p)
+        reqs.append((A, B, p))
+    dev = [(_dev(A), _dev(B), torch.full((A.shape[0], B.shape[1]), -1, dtype=torch.int64, device="cuda"), p)
+           for A, B, p in reqs]
+    torch.cuda.synchronize()
+    items = [M.Batch([d], form=form).info["items"] for d in dev]
+    table = [(A.shape[0] * B.shape[1] * A.shape[1], it) for (A, B, _), it in zip(reqs, items)]
+    assert min(items) <= 32 < max(items)
+    assert any(w1 <= w2 <= 4 * w1 for w1, i1 in table if i1 <= 32 for w2, i2 in table if i2 > 32)
+    srv = M.Server(4 << 30, max_inflight=2, max_batch=16, form=form)
+    tickets = []
+    for d in dev:
+        st, t = srv.submit(*d)
+        assert st == 0
+        tickets.append(t)
+    for t in tickets:
+        assert srv.wait(t, 60000) == 0
+    s = srv.stats()
+    assert s["completed"] == len(reqs) and s["status"] == 0 and s["mean_batch"] > 1.0
+    srv.close()
+    for (A, B, p), (_, _, C, _) in zip(reqs, dev):
+        assert np.array_equal(C.cpu().numpy().view(np.uint64), oracle.matmul_mod(A, B, p))
+
+
 def test_serve_poisson_stream_from_two_client_threads(M, oracle):
     reqs = _requests(22, 80, 16, 300)
     dev = [(_dev(A), _dev(B), torch.empty((A.shape[0], B.shape[1]), dtype=torch.int64, device="cuda"), p)
