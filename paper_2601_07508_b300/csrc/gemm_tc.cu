@@ -776,8 +776,7 @@ int max_clusters2(const void *kernel, int smem, int (&cached)[64]) {
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
     if (!cached[dev]) {
         if (set_smem_attr(kernel, smem) != cudaSuccess) return 0;
-        cudaLaunchConfig_t cfg;
-        std::memset(&cfg, 0, sizeof(cfg));
+        cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(2 * (unsigned)(sm_count() / 2), 1, 1);
         cfg.blockDim = dim3(THREADS, 1, 1);
         cfg.dynamicSmemBytes = smem;
@@ -928,8 +927,7 @@ int launch_gemm_tc(const Plan &pl, const void *Aw, const void *Bw, int32_t *S, i
         const int clusters = mcast_clusters();
         if (clusters <= 0) return (int)cudaErrorLaunchOutOfResources;
         const int64_t ncl = P.nitems < clusters ? P.nitems : clusters;
-        cudaLaunchConfig_t cfg;
-        std::memset(&cfg, 0, sizeof(cfg));
+        cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3((unsigned)(2 * ncl), 1, 1);
         cfg.blockDim = dim3(THREADS, 1, 1);
         cfg.dynamicSmemBytes = kSmemBytes;
