@@ -51,10 +51,9 @@ struct SplitParams {
     int *err;
     int64_t cbias;              // INT8 form: 128 (1 + 256 + ... + 256^(words-2))
     int crt;                    // CRT form: residues instead of digits
-    uint32_t cm[kMaxCrt];       // moduli (odd primes below 256)
-    uint32_t cM[kMaxCrt];       // floor(2^32 / m_i) + 1
-    uint32_t c18[kMaxCrt], c36[kMaxCrt];  // 2^18 mod m_i, 2^36 mod m_i
-    float cmh[kMaxCrt];         // 1.5 * 2^23 + (m_i - 1) / 2
+    float cmf[kMaxCrt];         // moduli m_i (odd primes below 256)
+    float cinv[kMaxCrt];        // fl(1 / m_i), correctly rounded
+    float c11[kMaxCrt], c22[kMaxCrt], c33[kMaxCrt], c44[kMaxCrt];  // 2^(11 j) mod m_i
 };
 
 // Small integers to bf16 without the conversion pipe.  For |v| < 2^22 the
@@ -75,19 +74,29 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
 }
 
 // Signed residue of x < 2^52 modulo an odd m < 256, in [-(m-1)/2, (m-1)/2],
-// with 32-bit operations only: from the 18-bit limbs x = x2 2^36 + x1 2^18
-// + x0, z = x2 (2^36 mod m) + x1 (2^18 mod m) + x0 + (m-1)/2 < 2^27 is
-// congruent to x + (m-1)/2.  q = umulhi(z, floor(2^32 / m) + 1) is floor(z / m)
-// or one more (the multiplier exceeds 2^32 / m by less than 1, and
-// z / 2^32 < 1/32), so z - q m is z mod m, or that minus m (then m is added
-// back).  The residue minus (m-1)/2 is the signed one; its FP32 value comes
-// from the magic exponent with the offset folded into the constant cmh.
-__device__ __forceinline__ float signed_residue(uint32_t x0, uint32_t x1, uint32_t x2, uint32_t m, uint32_t M,
-                                                uint32_t c18, uint32_t c36, float cmh) {
-    const uint32_t z = x2 * c36 + x1 * c18 + x0 + (m >> 1);
-    int r = (int)(z - __umulhi(z, M) * m);
-    r += (r >> 31) & (int)m;
-    return __int_as_float(0x4B400000 + r) - cmh;
+// on the FP32 pipe.  From the 11-bit limbs x = sum_{j<5} x_j 2^(11 j),
+// z = x_0 + sum_{j>=1} x_j (2^(11 j) mod m) <= 2047 + 3 * 2047 * 250 + 255 * 250
+// < 2^21 is congruent to x, and every partial sum is an integer that FP32
+// holds exactly.  q = rint(z fl(1/m)) equals rint(z / m): fl(1/m) is within a
+// relative 2^-24 of 1/m, so the product is within 2^21 2^-24 / m = 0.125 / m
+// of z / m, while z / m (m odd) lies at least 0.5 / m from every
+// half-integer.  r = z - q m is then exact in one FMA, and it is the residue
+// of x nearest to zero, i.e. the balanced one.
+__device__ __forceinline__ float signed_residue(const float (&xl)[5], float m, float inv, float c11, float c22,
+                                                float c33, float c44) {
+    const float z = __fmaf_rn(xl[4], c44, __fmaf_rn(xl[3], c33, __fmaf_rn(xl[2], c22, __fmaf_rn(xl[1], c11, xl[0]))));
+    const float q = __fsub_rn(__fmaf_rn(z, inv, kMagic), kMagic);
+    return __fmaf_rn(-q, m, z);
+}
+// The five 11-bit limbs of x as FP32 integers (2^23 + limb through the
+// exponent pattern, minus 2^23).  The top limb takes every bit from 44 up, so
+// an entry >= 2^52 (outside the preconditions) still yields finite values.
+__device__ __forceinline__ void limbs11(uint64_t x, float (&xl)[5]) {
+    const uint32_t lo = (uint32_t)x, hi = (uint32_t)(x >> 32);
+    const uint32_t l[5] = {lo & 0x7FFu, (lo >> 11) & 0x7FFu, __funnelshift_r(lo, hi, 22) & 0x7FFu, (hi >> 1) & 0x7FFu,
+                           hi >> 12};
+#pragma unroll
+    for (int j = 0; j < 5; ++j) xl[j] = __int_as_float(0x4B000000 | (int)l[j]) - 8388608.0f;
 }
 
 __device__ __forceinline__ uint64_t load_tile_elem(const SplitParams &P, int64_t r, int64_t l) {
@@ -189,20 +198,15 @@ __device__ __forceinline__ void split_int8_tile(const SplitParams &P, uint64_t (
                                                          pack_bf16x2(f[4], f[5]), pack_bf16x2(f[6], f[7]));
         };
         if (P.crt) {
-            uint32_t x0[8], x1[8], x2[8];  // 18-bit limbs
+            float xl[8][5];  // 11-bit limbs
 #pragma unroll
-            for (int e = 0; e < 8; ++e) {
-                const uint64_t x = tile[rr][8 * g + e];
-                x0[e] = (uint32_t)x & 0x3FFFFu;
-                x1[e] = (uint32_t)(x >> 18) & 0x3FFFFu;
-                x2[e] = (uint32_t)(x >> 36);
-            }
+            for (int e = 0; e < 8; ++e) limbs11(tile[rr][8 * g + e], xl[e]);
             for (int w = 0; w < P.words; ++w) {
-                const uint32_t m = P.cm[w], M = P.cM[w], c18 = P.c18[w], c36 = P.c36[w];
-                const float cmh = P.cmh[w];
+                const float m = P.cmf[w], inv = P.cinv[w], c11 = P.c11[w], c22 = P.c22[w], c33 = P.c33[w],
+                            c44 = P.c44[w];
                 float f[8];
 #pragma unroll
-                for (int e = 0; e < 8; ++e) f[e] = signed_residue(x0[e], x1[e], x2[e], m, M, c18, c36, cmh);
+                for (int e = 0; e < 8; ++e) f[e] = signed_residue(xl[e], m, inv, c11, c22, c33, c44);
                 store(w, f);
             }
         } else {
@@ -241,7 +245,7 @@ __global__ void __launch_bounds__(256) split_int8_kernel(const __grid_constant__
 }
 
 // Batched: block b splits tile blocks[b] = (job, tile row, tile col) of jobs[job].
-__global__ void __launch_bounds__(256) split_batched_kernel(const SplitParams *jobs, const int4 *blocks,
+__global__ void __launch_bounds__(256, 4) split_batched_kernel(const SplitParams *jobs, const int4 *blocks,
                                                             int fp64) {
     __shared__ uint64_t tile[kST][kST + 1];
     __shared__ __align__(16) SplitParams P;  // staged once (all threads copy): the loops read it many times
@@ -280,11 +284,12 @@ SplitParams make_split_params(const Plan &pl, int side, const uint64_t *M, int64
     for (int i = 0; i + 1 < P.words && !P.crt && pl.form != MWMM_FORM_FP64; ++i) P.cbias += (int64_t)128 << (8 * i);
     for (int i = 0; i < kMaxCrt; ++i) {
         const uint32_t m = i < pl.crt_s ? pl.crt_m[i] : 3;
-        P.cm[i] = m;
-        P.cM[i] = (uint32_t)((uint64_t(1) << 32) / m + 1);
-        P.c18[i] = (uint32_t)((uint64_t(1) << 18) % m);
-        P.c36[i] = (uint32_t)((uint64_t(1) << 36) % m);
-        P.cmh[i] = 12582912.0f + (float)(m >> 1);
+        P.cmf[i] = (float)m;
+        P.cinv[i] = 1.0f / (float)m;  // IEEE single division: correctly rounded
+        P.c11[i] = (float)((uint64_t(1) << 11) % m);
+        P.c22[i] = (float)((uint64_t(1) << 22) % m);
+        P.c33[i] = (float)((uint64_t(1) << 33) % m);
+        P.c44[i] = (float)((uint64_t(1) << 44) % m);
     }
     return P;
 }
