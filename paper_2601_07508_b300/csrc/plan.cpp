@@ -73,21 +73,23 @@ int int8_digits(uint64_t p) {
 static int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
 // Cost model of the two tensor forms (seconds), calibrated on 4096^3 products
-// on B300: word products at ~1.5 PFLOP/s of 2 m n k per product; the INT8
-// split (8 B read + 2 B per digit written per entry) and recombination
-// (4 B per sum read + 8 B written per output) at ~5 TB/s; the CRT split and
-// reconstruction are issue-bound at ~0.6 ps per (entry, modulus) and
-// ~1.35 ps per (output, modulus).
+// on B300 (7 to 16 moduli, 3 to 7 digits a side): word products at ~1.5
+// PFLOP/s of 2 m n k per product; the INT8 split (8 B read + 2 B per digit
+// written per entry) at ~5 TB/s and recombination (4 B per sum read + 8 B
+// written per output) at ~6 TB/s; the CRT split at 8 B per entry plus
+// ~0.38 ps per (entry, modulus), the CRT reconstruction at 8 B per output
+// plus ~1.0 ps per (output, modulus).
 static double tensor_form_cost(const Plan &pl) {
     const double mnk2 = 2.0 * pl.m * pl.n * pl.k, mk_kn = (double)pl.m * pl.k + (double)pl.k * pl.n,
                  mn = (double)pl.m * pl.n;
-    constexpr double kTensor = 1.5e15, kHbm = 5.0e12;
+    constexpr double kTensor = 1.5e15, kHbm = 5.0e12, kHbmRec = 6.0e12;
     if (pl.form == MWMM_FORM_CRT8) {
         const double s = pl.crt_s;
-        return s * mnk2 / kTensor + mk_kn * s * 0.6e-12 + mn * s * (1.35e-12 + 4.0 * (pl.nkc - 1) / kHbm);
+        return s * mnk2 / kTensor + mk_kn * (8.0 / kHbm + s * 0.38e-12) +
+               mn * (8.0 / kHbm + s * (1.0e-12 + 4.0 * (pl.nkc - 1) / kHbm));
     }
     return (double)pl.u * pl.v * mnk2 / kTensor + mk_kn * (8.0 + 2.0 * pl.u) / kHbm +
-           mn * (4.0 * pl.nsums * pl.nkc + 8.0) / kHbm;
+           mn * (4.0 * pl.nsums * pl.nkc + 8.0) / kHbmRec;
 }
 
 // Primes below 256, largest first (moduli of the CRT form).

@@ -277,7 +277,7 @@ def test_crt_plan_errors(M):
 
 def test_tensor_form_choice_follows_the_cost_model(M):
     """AUTO's tensor form for batches and serving: at 4096^3 the INT8 digits
-    below 24 bits (9 digit products against 8 moduli plus a costlier CRT
+    at 23-24 bits (9 digit products against 8 moduli plus a costlier CRT
     reconstruction), the CRT form from 25 bits (16 / 25 / 36 / 49 digit
     products against 9-16 moduli); small products stay INT8 (the CRT split
     and reconstruction grow with the moduli); k > 2^22 cannot use CRT."""
