@@ -276,7 +276,8 @@ void mwmm_plan_destroy(mwmm_plan_t plan);
  * serving loop use for this product under MWMM_FORM_AUTO: the smaller time
  * in the planner's cost model (word products at the tensor rate, plus the
  * split and the recombination or CRT reconstruction, calibrated on 4096^3
- * products on B300: INT8 below about 24 bits, CRT from about 26 bits).  Host
+ * products on B300: at that size INT8 at 22-24 bits, CRT at 20-21 bits and
+ * from 25 bits; small products INT8).  Host
  * only, no CUDA call.  MWMM_FORM_INT8 when the CRT form cannot be planned
  * (k > 2^22); MWMM_FORM_AUTO for arguments no form can plan. */
 mwmm_form mwmm_tensor_form(int64_t m, int64_t n, int64_t k, uint64_t p);
