@@ -110,10 +110,6 @@ typedef struct {
                          cta_group::2) instead of the one-CTA kernel (128 x 256
                          tiles).  Bit-exact; measured on B300 within 3% of the
                          one-CTA kernel either way; default 0 */
-    int32_t tc_cluster; /* INT8 form, one-CTA kernel, m > 128: 2 = clusters of
-                         two CTAs sharing each B tile through TMA multicast
-                         (bit-exact, measured 2-3% slower on B300);
-                         0 or 1 = lone CTAs (default) */
     int32_t f64_concat; /* FP64 form, Alg. 6: 0 = automatic (when min(m, n) < 64,
                          concatenate the words of the narrower side: B's
                          along n when n <= m and 2 <= v <= 4, else A's along m
@@ -125,7 +121,7 @@ typedef struct {
     int32_t autotune;   /* mwmm_batch_create / mwmm_matmul_batched only:
                          nonzero picks (u,v) and the K-range per bitsize
                          group by timing candidates (see mwmm_plan_autotuned) */
-    int32_t reserved[3];
+    int32_t reserved[4];
 } mwmm_plan_opts;
 
 /* What a plan decided (mwmm_plan_info). */
@@ -165,7 +161,7 @@ typedef struct {
      * (uint64 residues) at S_off, laid out [ksplit][m][n]. */
     int64_t kb_elems, nkb, A_rows, B_rows;
     int32_t B_wpad;
-    int32_t tc_cluster;     /* INT8: CTAs per cluster of the one-CTA kernel (2: A_rows % 256 == 0) */
+    int32_t pad0;
     uint64_t A_off, B_off, S_off;
     uint64_t workspace_bytes;
     int32_t f64_concat;     /* FP64: 1 when B's words are concatenated along n, 2 when A's along m (Alg. 6) */
@@ -198,7 +194,7 @@ mwmm_status mwmm_plan_info(mwmm_plan_t plan, mwmm_plan_desc *out);
  * returns a plan with the fastest: the form (when form = MWMM_FORM_AUTO:
  * FP64, INT8 or CRT; otherwise the given one), (u,v) among the FP64 variants whose block size
  * is >= 1 with concatenation on and off where it applies, the tcgen05 tile
- * variant (one CTA, clusters of two, CTA pairs) and the INT32 K-range.  Each
+ * variant (one CTA or CTA pairs) and the INT32 K-range.  Each
  * candidate runs once to warm up and twice timed (CUDA events on `stream`,
  * synchronised); candidates whose flop model exceeds 3x the best measured
  * time are skipped.  dA / dB (device, row-major, leading dimensions lda /

@@ -388,7 +388,6 @@ mwmm_status mwmm_batch_create(mwmm_batch_t *out, const mwmm_problem *probs, int 
             v = t.v;
         }
         o.lambda = 0;      // per-problem block sizes: always the bound
-        o.tc_cluster = 1;  // table items run on lone CTAs (no 256-row padding)
         o.tc_pair = 0;
         o.ksplit = 1;      // batched FP64 tiles run the whole K range
         mwmm_status st = mwmm::make_plan(&b->plans[i], q.m, q.n, q.k, q.p, u, v, pf, &o);

@@ -174,7 +174,6 @@ mwmm_status make_sub_plan(const Plan &pl, int64_t rows, Plan *out) {
     } else {
         o.tc_chunk = (int32_t)pl.tc_chunk;
         o.kc = pl.kc;
-        o.tc_cluster = pl.tc_cluster == 2 ? 2 : 1;
     }
     const bool crt = pl.form == MWMM_FORM_CRT8;  // its words follow from p and k
     mwmm_status st = mwmm::make_plan(out, rows, pl.n, pl.k, pl.p, crt ? 0 : pl.u, crt ? 0 : pl.v, pl.form, &o);
@@ -369,7 +368,7 @@ void describe_plan(const Plan &P, mwmm_plan_desc *d) {
     d->form = P.form; d->u = P.u; d->v = P.v;
     d->alpha = P.alpha; d->beta = P.beta;
     d->lambda = P.lambda; d->lambda_max = P.lambda_max;
-    d->tc_chunk = P.tc_chunk; d->kc = P.kc; d->nkc = P.nkc; d->nsums = P.nsums; d->tc_pair = P.tc_pair; d->tc_cluster = P.tc_cluster;
+    d->tc_chunk = P.tc_chunk; d->kc = P.kc; d->nkc = P.nkc; d->nsums = P.nsums; d->tc_pair = P.tc_pair;
     d->f64_concat = P.f64_concat; d->ksplit = P.ksplit;
     d->q = P.q;
     d->kb_elems = P.kb_elems; d->nkb = P.nkb; d->A_rows = P.A_rows; d->B_rows = P.B_rows;

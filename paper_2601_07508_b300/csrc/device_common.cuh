@@ -115,7 +115,16 @@ __device__ __forceinline__ double mulmod_split(double g, double g26, double y, d
 
 }  // namespace mwmm
 
+#include <mutex>
+
 namespace mwmm {
+// Host-side caches of the launchers (attributes set, SM and cluster counts)
+// are filled under this lock: plans on different threads may launch at once.
+inline std::mutex &launch_cache_mutex() {
+    static std::mutex mu;
+    return mu;
+}
+
 // Raise a kernel's dynamic shared-memory limit (once per device and kernel;
 // later calls are free, so a launch inside a stream capture makes no
 // attribute call once the same launch ran outside it).
@@ -126,6 +135,7 @@ inline cudaError_t set_smem_attr(const void *func, int bytes) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(launch_cache_mutex());
     for (int i = 0; i < ndone; ++i)
         if (done[i].f == func && done[i].dev == dev) return cudaSuccess;
     e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);

@@ -21,13 +21,6 @@
 // of Alg. 6's concatenation).  Items go round-robin over a persistent grid of
 // one CTA per SM, heaviest diagonals first.
 //
-// Clusters of two (plan option tc_cluster = 2): the CTAs of a cluster take
-// the two 128-row halves of a 256-row tile against the same B tile.  Each CTA
-// copies half of the B tile and multicasts it to both, and each MMA commit
-// releases the stage in both CTAs, so a CTA pulls 32 KB per stage from L2
-// instead of 48 KB.  Measured on B300 this does not pay (2-3% slower: L2 reads
-// are not what bounds the kernel), so lone CTAs are the default.
-//
 // Warp roles (320 threads):
 //   warp 0      one lane issues bulk TMA copies of the pre-swizzled word tiles
 //               (A 16 KB + B 32 KB per stage, 4 stages);
@@ -105,12 +98,9 @@ __device__ __forceinline__ int item_n(int ndiag, int nb, int cv) {
     return ndiag * nb;
 }
 
-// kCl = 2: item idx is a 256-row tile shared by the cluster; `rank` picks
-// its 128-row half.
-template <int kCl>
-__device__ __forceinline__ Item computed_item(const TcParams &P, int64_t idx, int rank) {
+__device__ __forceinline__ Item computed_item(const TcParams &P, int64_t idx) {
     Item it;
-    const int64_t mtc = P.mt_count / kCl;
+    const int64_t mtc = P.mt_count;
     const int64_t ntiles = mtc * P.nt_count;
     const int64_t tile = idx % ntiles;
     const int64_t rest = idx / ntiles;
@@ -131,7 +121,7 @@ __device__ __forceinline__ Item computed_item(const TcParams &P, int64_t idx, in
     const int64_t gsz = mtc * kGroupN;
     const int64_t grp = tile / gsz, t = tile % gsz;
     const int64_t width = P.nt_count - grp * kGroupN < kGroupN ? P.nt_count - grp * kGroupN : kGroupN;
-    it.mt = (t / width) * kCl + rank;
+    it.mt = t / width;
     it.nt = grp * kGroupN + t % width;
     it.kb0 = (int64_t)kc * P.kcb;
     const int64_t left = P.nkb - it.kb0;
@@ -179,7 +169,7 @@ __device__ __forceinline__ Item table_item(const TcParams &P, int64_t pos) {
     return it;
 }
 
-template <bool kTable, int kCl>
+template <bool kTable>
 struct ItemRange {
     int64_t begin, end, step;
     __device__ ItemRange(const TcParams &P) {
@@ -187,17 +177,17 @@ struct ItemRange {
             begin = P.cta_off[blockIdx.x];
             end = P.cta_off[blockIdx.x + 1];
             step = 1;
-        } else {  // clusters are consecutive blocks
-            begin = blockIdx.x / kCl;
+        } else {
+            begin = blockIdx.x;
             end = P.nitems;
-            step = gridDim.x / kCl;
+            step = gridDim.x;
         }
     }
 };
 
-template <bool kTable, int kCl>
-__device__ __forceinline__ Item get_item(const TcParams &P, int64_t idx, int rank) {
-    return kTable ? table_item(P, idx) : computed_item<kCl>(P, idx, rank);
+template <bool kTable>
+__device__ __forceinline__ Item get_item(const TcParams &P, int64_t idx) {
+    return kTable ? table_item(P, idx) : computed_item(P, idx);
 }
 
 // ---- tcgen05 wrappers -------------------------------------------------------
@@ -259,28 +249,6 @@ __device__ __forceinline__ void cluster_sync_all() {
     asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;" ::: "memory");
 }
 
-// Bulk copy of `bytes` from global memory to the same shared-memory offset in
-// every CTA of `mask`, completing `bytes` on the barrier at `bar`'s offset in
-// each of them.
-__device__ __forceinline__ void bulk_g2s_mcast(void *dst, const void *src, uint32_t bytes, uint64_t *bar,
-                                               uint16_t mask) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster [%0], [%1], %2, [%3], "
-        "%4;" ::"r"(smem_u32(dst)),
-        "l"(src), "r"(bytes), "r"(smem_u32(bar)), "h"(mask)
-        : "memory");
-}
-
-// Arrive once on `bar` (same offset) in every CTA of `mask` when all MMAs
-// issued so far by this thread have completed.
-__device__ __forceinline__ void mma_commit_mcast(uint64_t *bar, uint16_t mask) {
-    asm volatile(
-        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
-            smem_u32(bar)),
-        "h"(mask)
-        : "memory");
-}
-
 // 32 consecutive FP32 columns of this thread's TMEM lane.
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
     asm volatile(
@@ -329,15 +297,13 @@ __device__ __forceinline__ void store_sums(const Item &it, const int32_t (&acc)[
     }
 }
 
-template <bool kTable, int kCl>
+template <bool kTable>
 __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_constant__ TcParams P) {
-    static_assert(kCl == 1 || (kCl == 2 && !kTable), "clusters of two run computed items only");
     extern __shared__ uint8_t smem_raw[];
     __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES], tfull[2], tempty[2], done;
     __shared__ uint32_t tmem_base_sh;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int rank = kCl == 1 ? 0 : (int)cluster_rank();
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t pad = ((raw + 1023u) & ~1023u) - raw;
     uint8_t *sA = smem_raw + pad;
@@ -347,7 +313,7 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_consta
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
             mbar_init(&full[s], 1);
-            mbar_init(&empty[s], kCl);  // one MMA commit from each CTA of the cluster
+            mbar_init(&empty[s], 1);
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&tfull[b], 1);
@@ -364,10 +330,7 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_consta
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     tc_fence_before();
-    if (kCl == 1)
-        __syncthreads();
-    else
-        cluster_sync_all();  // the peer's barriers exist before any multicast reaches them
+    __syncthreads();
     tc_fence_after();
     const uint32_t tmem_base = tmem_base_sh;
 
@@ -375,9 +338,9 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_consta
         if (lane == 0) {  // ---------------- TMA producer
             uint64_t g = 0;
             bool alive = true;
-            const ItemRange<kTable, kCl> R(P);
+            const ItemRange<kTable> R(P);
             for (int64_t idx = R.begin; alive && idx < R.end; idx += R.step) {
-                const Item it = get_item<kTable, kCl>(P, idx, rank);
+                const Item it = get_item<kTable>(P, idx);
                 // One thread issues every copy, so the per-stage work is kept to a
                 // few adds: nested (word, k-block) loops and running addresses.
                 // The window's B words B_{s0-i} .. B_{s0-i+ndiag-1} are contiguous
@@ -399,21 +362,14 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_consta
                         }
                         mbar_arrive_expect_tx(&full[slot], stage_bytes);
                         bulk_g2s(sA + slot * kTileA, a, kTileA, &full[slot]);
-                        if (kCl == 1) {
-                            bulk_g2s(sB + slot * kTileB, b, bbytes, &full[slot]);
-                        } else {  // ndiag * nb is a multiple of 16 rows: halves keep the 1 KB swizzle atoms
-                            const uint32_t h = bbytes / 2;
-                            bulk_g2s_mcast(sB + slot * kTileB + rank * h, b + rank * h, h, &full[slot], 0x3);
-                        }
+                        bulk_g2s(sB + slot * kTileB, b, bbytes, &full[slot]);
                     }
                 }
             }
-            // Let every copy into this CTA (own and the peer's multicast) land,
-            // and every commit aimed at this CTA's barriers arrive, before exit.
+            // Let every copy into this CTA land before exit.
             for (int s = 0; s < STAGES; ++s) {
                 const uint64_t armed = g > (uint64_t)s ? (g - s + STAGES - 1) / STAGES : 0;
                 if (armed) mbar_wait(&full[s], (uint32_t)((armed - 1) & 1), P.err);
-                if (armed && kCl > 1) mbar_wait(&empty[s], (uint32_t)((armed - 1) & 1), P.err);
             }
         }
     } else if (warp == 1) {
@@ -421,9 +377,9 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_consta
             uint64_t g = 0, c = 0;
             bool alive = true;
             const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
-            const ItemRange<kTable, kCl> R(P);
+            const ItemRange<kTable> R(P);
             for (int64_t idx = R.begin; alive && idx < R.end; idx += R.step) {
-                const Item it = get_item<kTable, kCl>(P, idx, rank);
+                const Item it = get_item<kTable>(P, idx);
                 const int64_t nvb = (int64_t)it.ni * it.nkbc;
                 const uint32_t idesc = idesc_n(it.nn);
                 for (int64_t t0 = 0; alive && t0 < nvb; t0 += P.chunk_blocks, ++c) {
@@ -446,10 +402,7 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_consta
 #pragma unroll
                         for (int kk = 0; kk < 4; ++kk)  // K = 16 per MMA: +32 bytes = +2 in the address field
                             mma_bf16(dt, ad + 2 * kk, bd + 2 * kk, idesc, (t > t0 || kk > 0) ? 1u : 0u);
-                        if (kCl == 1)
-                            mma_commit(&empty[slot]);
-                        else
-                            mma_commit_mcast(&empty[slot], 0x3);  // the slot is free once both CTAs are done
+                        mma_commit(&empty[slot]);
                     }
                     mma_commit(&tfull[buf]);
                 }
@@ -464,9 +417,9 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_consta
         const uint32_t tlane = tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(half * 128);
         uint64_t c = 0;
         bool alive = true;
-        const ItemRange<kTable, kCl> R(P);
+        const ItemRange<kTable> R(P);
         for (int64_t idx = R.begin; alive && idx < R.end; idx += R.step) {
-            const Item it = get_item<kTable, kCl>(P, idx, rank);
+            const Item it = get_item<kTable>(P, idx);
             const int64_t nvb = (int64_t)it.ni * it.nkbc;
             const int64_t nch = (nvb + P.chunk_blocks - 1) / P.chunk_blocks;
             int32_t acc[128];
@@ -499,10 +452,7 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_consta
     }
 
     tc_fence_before();
-    if (kCl == 1)
-        __syncthreads();
-    else
-        cluster_sync_all();  // neither CTA exits while the other may still signal it
+    __syncthreads();
     tc_fence_after();
     if (warp == 1)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(kTmemCols)
@@ -761,6 +711,7 @@ int sm_count() {
     static int cached[64] = {0};
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 148;
+    std::lock_guard<std::mutex> lock(launch_cache_mutex());
     if (!cached[dev]) {
         int n = 0;
         if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 148;
@@ -774,10 +725,12 @@ int sm_count() {
 int max_clusters2(const void *kernel, int smem, int (&cached)[64]) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+    if (set_smem_attr(kernel, smem) != cudaSuccess) return 0;
+    const int sms = sm_count();
+    std::lock_guard<std::mutex> lock(launch_cache_mutex());
     if (!cached[dev]) {
-        if (set_smem_attr(kernel, smem) != cudaSuccess) return 0;
         cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = dim3(2 * (unsigned)(sm_count() / 2), 1, 1);
+        cfg.gridDim = dim3(2 * (unsigned)(sms / 2), 1, 1);
         cfg.blockDim = dim3(THREADS, 1, 1);
         cfg.dynamicSmemBytes = smem;
         cudaLaunchAttribute attr;
@@ -828,11 +781,6 @@ int encode_rows_map(CUtensorMap *map, const void *base, uint64_t rows) {
 int pair_clusters() {
     static int cached[64] = {0};
     return max_clusters2(reinterpret_cast<const void *>(gemm_tc_pair_kernel), kSmemPair, cached);
-}
-
-int mcast_clusters() {
-    static int cached[64] = {0};
-    return max_clusters2(reinterpret_cast<const void *>(gemm_tc_kernel<false, 2>), kSmemBytes, cached);
 }
 
 }  // namespace
@@ -919,44 +867,21 @@ int launch_gemm_tc(const Plan &pl, const void *Aw, const void *Bw, int32_t *S, i
                                                                                                             tmB);
         return (int)cudaGetLastError();
     }
-    if (pl.tc_cluster == 2) {
-        P.nitems /= 2;  // items are 256-row tiles; A_rows % 256 == 0
-        const void *kern = reinterpret_cast<const void *>(gemm_tc_kernel<false, 2>);
-        cudaError_t e = set_smem_attr(kern, kSmemBytes);
-        if (e != cudaSuccess) return (int)e;
-        const int clusters = mcast_clusters();
-        if (clusters <= 0) return (int)cudaErrorLaunchOutOfResources;
-        const int64_t ncl = P.nitems < clusters ? P.nitems : clusters;
-        cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = dim3((unsigned)(2 * ncl), 1, 1);
-        cfg.blockDim = dim3(THREADS, 1, 1);
-        cfg.dynamicSmemBytes = kSmemBytes;
-        cfg.stream = static_cast<cudaStream_t>(stream);
-        cudaLaunchAttribute attr;
-        attr.id = cudaLaunchAttributeClusterDimension;
-        attr.val.clusterDim.x = 2;
-        attr.val.clusterDim.y = 1;
-        attr.val.clusterDim.z = 1;
-        cfg.attrs = &attr;
-        cfg.numAttrs = 1;
-        return (int)cudaLaunchKernelEx(&cfg, gemm_tc_kernel<false, 2>, P);
-    }
-    cudaError_t e = set_smem_attr(reinterpret_cast<const void *>(gemm_tc_kernel<false, 1>), kSmemBytes);
+    cudaError_t e = set_smem_attr(reinterpret_cast<const void *>(gemm_tc_kernel<false>), kSmemBytes);
     if (e != cudaSuccess) return (int)e;
     const int64_t sms = sm_count();
     const unsigned grid = (unsigned)(P.nitems < sms ? P.nitems : sms);
-    gemm_tc_kernel<false, 1><<<grid, THREADS, kSmemBytes, static_cast<cudaStream_t>(stream)>>>(P);
+    gemm_tc_kernel<false><<<grid, THREADS, kSmemBytes, static_cast<cudaStream_t>(stream)>>>(P);
     return (int)cudaGetLastError();
 }
 
 int tc_sm_count() { return sm_count(); }
 
 int prepare_tc_attributes() {
-    cudaError_t e = set_smem_attr(reinterpret_cast<const void *>(gemm_tc_kernel<false, 1>), kSmemBytes);
-    if (e == cudaSuccess) e = set_smem_attr(reinterpret_cast<const void *>(gemm_tc_kernel<true, 1>), kSmemBytes);
+    cudaError_t e = set_smem_attr(reinterpret_cast<const void *>(gemm_tc_kernel<false>), kSmemBytes);
+    if (e == cudaSuccess) e = set_smem_attr(reinterpret_cast<const void *>(gemm_tc_kernel<true>), kSmemBytes);
     if (e == cudaSuccess) {  // cache the cluster counts outside any capture
         (void)pair_clusters();
-        (void)mcast_clusters();
         (void)tensor_map_encoder();
     }
     return (int)e;
@@ -971,9 +896,9 @@ int launch_gemm_tc_table(const TcItem *items, const int64_t *cta_off, int ctas, 
     P.cta_off = cta_off;
     P.chunk_blocks = chunk_blocks;
     P.err = err;
-    cudaError_t e = set_smem_attr(reinterpret_cast<const void *>(gemm_tc_kernel<true, 1>), kSmemBytes);
+    cudaError_t e = set_smem_attr(reinterpret_cast<const void *>(gemm_tc_kernel<true>), kSmemBytes);
     if (e != cudaSuccess) return (int)e;
-    gemm_tc_kernel<true, 1><<<ctas, THREADS, kSmemBytes, static_cast<cudaStream_t>(stream)>>>(P);
+    gemm_tc_kernel<true><<<ctas, THREADS, kSmemBytes, static_cast<cudaStream_t>(stream)>>>(P);
     return (int)cudaGetLastError();
 }
 

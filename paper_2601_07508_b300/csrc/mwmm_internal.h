@@ -73,7 +73,6 @@ struct Plan {
     // INT8 form
     int64_t tc_chunk = 0, kc = 0;
     int tc_pair = 0;  // 1: 2-CTA kernel, A rows padded to 256
-    int tc_cluster = 1;  // 2: one-CTA kernel in clusters of two (B multicast), A rows padded to 256
     int tc_nb = 256;  // B rows per word slice of a tile (256, or n padded to 16/32/64/128)
     int tc_ndiag = 1; // diagonals per work item (256 / tc_nb, at most nsums)
     int nkc = 0, nsums = 0;

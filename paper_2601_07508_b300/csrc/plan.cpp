@@ -324,10 +324,7 @@ mwmm_status make_plan(Plan *pl, int64_t m, int64_t n, int64_t k, uint64_t p, int
         if (form == MWMM_FORM_CRT8) P.tc_ndiag = 1;  // each modulus pairs A_i with B_i only: no windows
         // the 2-CTA kernel (opt-in) computes 256 x 256 tiles
         P.tc_pair = (m > kTcBM && P.tc_nb == kTcBN && o.tc_pair) ? 1 : 0;
-        // on request the one-CTA kernel runs in clusters of two sharing each B tile
-        if (o.tc_cluster < 0 || o.tc_cluster > 2) return MWMM_ERR_ARG;
-        P.tc_cluster = (!P.tc_pair && m > kTcBM && o.tc_cluster == 2) ? 2 : 1;
-        P.A_rows = round_up(m > 0 ? m : 1, (P.tc_pair || P.tc_cluster == 2) ? 2 * kTcBM : kTcBM);
+        P.A_rows = round_up(m > 0 ? m : 1, P.tc_pair ? 2 * kTcBM : kTcBM);
         P.A_wstride = P.nkb * P.A_rows;
         P.A_kstride = P.A_rows;
         P.B_rows = P.tc_nb == kTcBN ? round_up(n > 0 ? n : 1, kTcBN) : P.tc_nb;

@@ -38,9 +38,9 @@ class MwmmError(RuntimeError):
 
 class PlanOpts(ctypes.Structure):
     _fields_ = [("lambda_", ctypes.c_int64), ("validate", ctypes.c_int32), ("tc_chunk", ctypes.c_int32),
-                ("kc", ctypes.c_int64), ("tc_pair", ctypes.c_int32), ("tc_cluster", ctypes.c_int32),
+                ("kc", ctypes.c_int64), ("tc_pair", ctypes.c_int32),
                 ("f64_concat", ctypes.c_int32), ("ksplit", ctypes.c_int32), ("autotune", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 3)]
+                ("reserved", ctypes.c_int32 * 4)]
 
 
 class Timing(ctypes.Structure):
@@ -57,7 +57,7 @@ class PlanDesc(ctypes.Structure):
                 ("kc", ctypes.c_int64), ("tc_pair", ctypes.c_int32), ("nkc", ctypes.c_int32), ("nsums", ctypes.c_int32),
                 ("q", ctypes.c_double),
                 ("kb_elems", ctypes.c_int64), ("nkb", ctypes.c_int64), ("A_rows", ctypes.c_int64),
-                ("B_rows", ctypes.c_int64), ("B_wpad", ctypes.c_int32), ("tc_cluster", ctypes.c_int32),
+                ("B_rows", ctypes.c_int64), ("B_wpad", ctypes.c_int32), ("pad0", ctypes.c_int32),
                 ("A_off", ctypes.c_uint64), ("B_off", ctypes.c_uint64),
                 ("S_off", ctypes.c_uint64), ("workspace_bytes", ctypes.c_uint64),
                 ("f64_concat", ctypes.c_int32), ("ksplit", ctypes.c_int32),
@@ -220,7 +220,7 @@ def _ld(t) -> int:
 # --------------------------------------------------------------------------- C-named calls
 def mwmm_plan(m: int, n: int, k: int, p: int, u: int = 0, v: int = 0, form="auto", lam: int = 0,
               validate: bool = False, tc_chunk: int = 0, kc: int = 0, tc_pair: bool = False,
-              tc_cluster: int = 0, f64_concat: int = 0, ksplit: int = 0) -> int:
+              f64_concat: int = 0, ksplit: int = 0) -> int:
     if isinstance(form, str):
         form = FORMS[form]
     h = _vp()
@@ -230,7 +230,6 @@ def mwmm_plan(m: int, n: int, k: int, p: int, u: int = 0, v: int = 0, form="auto
     o.tc_chunk = tc_chunk
     o.kc = kc
     o.tc_pair = 1 if tc_pair else 0
-    o.tc_cluster = tc_cluster
     o.f64_concat = f64_concat
     o.ksplit = ksplit
     _check(lib().mwmm_plan(ctypes.byref(h), m, n, k, p, u, v, form, ctypes.byref(o)), "mwmm_plan")
@@ -326,12 +325,27 @@ def mwmm_matmul_host_async_ptr(h: int, a_ptr: int, lda: int, b_ptr: int, ldb: in
 
 def mwmm_matmul_noalloc(A, B, C, p: int, stream=None) -> int:
     """INT8-form product with the library's static scratch (no device
-    allocation); synchronous.  Returns the status (0 = ok)."""
+    allocation); synchronous.  Returns the status (0 = ok).
+
+    The C entry point sees only pointers and sizes, so the shapes and the
+    device are checked here: B must be k x n for A of shape m x k, C must be
+    m x n, and all three must sit on one CUDA device, which is made current
+    for the call (the scratch array used is that device's)."""
+    import torch
     dt = _u64_dtypes()
+    if A.dim() != 2 or B.dim() != 2 or C.dim() != 2:
+        raise ValueError("A, B and C must be 2-D matrices")
     m, k = A.shape
+    if B.shape[0] != k:
+        raise ValueError("B has %d rows; A (%d x %d) needs %d" % (B.shape[0], m, k, k))
     n = B.shape[1]
-    return int(lib().mwmm_matmul_noalloc(m, n, k, p, _dev_ptr(A, dt), _ld(A), _dev_ptr(B, dt), _ld(B),
-                                         _dev_ptr(C, dt), _ld(C), _stream_ptr(stream)))
+    if tuple(C.shape) != (m, n):
+        raise ValueError("C is %s; the product is %d x %d" % (tuple(C.shape), m, n))
+    if not (A.is_cuda and B.is_cuda and C.is_cuda) or not (A.device == B.device == C.device):
+        raise ValueError("A, B and C must be on one CUDA device")
+    with torch.cuda.device(A.device):
+        return int(lib().mwmm_matmul_noalloc(m, n, k, p, _dev_ptr(A, dt), _ld(A), _dev_ptr(B, dt), _ld(B),
+                                             _dev_ptr(C, dt), _ld(C), _stream_ptr(stream)))
 
 
 def mwmm_plan_check(h: int, stream=None) -> int:
@@ -576,9 +590,8 @@ class Plan:
 
     def __init__(self, m: int, n: int, k: int, p: int, u: int = 0, v: int = 0, form="auto", lam: int = 0,
                  validate: bool = False, tc_chunk: int = 0, kc: int = 0, tc_pair: bool = False,
-                 tc_cluster: int = 0, f64_concat: int = 0, ksplit: int = 0):
-        self.handle = mwmm_plan(m, n, k, p, u, v, form, lam, validate, tc_chunk, kc, tc_pair, tc_cluster,
-                                f64_concat, ksplit)
+                 f64_concat: int = 0, ksplit: int = 0):
+        self.handle = mwmm_plan(m, n, k, p, u, v, form, lam, validate, tc_chunk, kc, tc_pair, f64_concat, ksplit)
         self.info = mwmm_plan_info(self.handle)
         self.workspace = None
 

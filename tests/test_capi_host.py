@@ -122,31 +122,19 @@ def test_workspace_layout_sizes(M):
     M.mwmm_plan_destroy(h)
 
 
-@pytest.mark.parametrize("m,n,cl,want_cl,want_rows", [
-    (100, 300, 0, 1, 128),    # default: lone CTAs
-    (700, 300, 0, 1, 768),
-    (129, 300, 2, 2, 256),    # clusters of two need 256-row tiles
-    (700, 20, 2, 2, 768),     # narrow n (diagonal windows) clusters too
-    (700, 300, 1, 1, 768),
-    (100, 300, 2, 1, 128),    # a single row tile cannot be shared
+@pytest.mark.parametrize("m,n,pair,want_pair,want_rows", [
+    (100, 300, False, 0, 128),   # default: one-CTA kernel, 128-row tiles
+    (700, 300, False, 0, 768),
+    (129, 300, True, 1, 256),    # the pair kernel needs 256-row tiles
+    (700, 20, True, 0, 768),     # narrow n (diagonal windows): one-CTA kernel only
+    (100, 300, True, 0, 128),    # a single row tile cannot be shared by a pair
 ])
-def test_int8_plan_cluster_choice(M, m, n, cl, want_cl, want_rows):
-    h = M.mwmm_plan(m, n, 1000, SWEEP[52], 0, 0, "int8", tc_cluster=cl)
+def test_int8_plan_tile_kernel_choice(M, m, n, pair, want_pair, want_rows):
+    h = M.mwmm_plan(m, n, 1000, SWEEP[52], 0, 0, "int8", tc_pair=pair)
     d = M.mwmm_plan_info(h)
     M.mwmm_plan_destroy(h)
-    assert d["tc_cluster"] == want_cl and d["A_rows"] == want_rows and d["tc_pair"] == 0
+    assert d["tc_pair"] == want_pair and d["A_rows"] == want_rows
     assert d["workspace_bytes"] >= d["S_off"] + d["nsums"] * d["nkc"] * d["A_rows"] * d["B_rows"] * 4
-
-
-def test_int8_plan_cluster_option_range(M):
-    for cl in (-1, 3):
-        with pytest.raises(M.MwmmError) as e:
-            M.mwmm_plan(300, 300, 64, SWEEP[40], 0, 0, "int8", tc_cluster=cl)
-        assert e.value.status == 1
-    h = M.mwmm_plan(300, 300, 64, SWEEP[40], 0, 0, "int8", tc_pair=True)  # the pair kernel excludes clusters
-    d = M.mwmm_plan_info(h)
-    M.mwmm_plan_destroy(h)
-    assert d["tc_pair"] == 1 and d["tc_cluster"] == 1
 
 
 @pytest.mark.parametrize("n,v,opt,want,slots", [
@@ -227,9 +215,9 @@ def test_autotune_cache_file_round_trip(M, tmp_path):
     src = tmp_path / "cache.jsonl"
     src.write_text(
         '{"key": "f2.b52.m12.n12.k12.single.sm148", "form": 2, "u": 7, "v": 7, "tc_chunk": 0, "kc": 0, '
-        '"tc_pair": 0, "tc_cluster": 1, "f64_concat": 0, "ksplit": 0, "ms": 4.250000, "tried": 3}\n'
+        '"tc_pair": 0, "f64_concat": 0, "ksplit": 0, "ms": 4.250000, "tried": 3}\n'
         '{"key": "f1.b40.m11.n11.k11.batch.sm148", "form": 1, "u": 2, "v": 2, "tc_chunk": 0, "kc": 0, '
-        '"tc_pair": 0, "tc_cluster": 0, "f64_concat": 1, "ksplit": 1, "ms": 59.400000, "tried": 4}\n'
+        '"tc_pair": 0, "f64_concat": 1, "ksplit": 1, "ms": 59.400000, "tried": 4}\n'
         'not a cache line\n')
     M.mwmm_autotune_cache_load(str(src))
     assert M.mwmm_autotune_cache_entries() == 2
@@ -289,3 +277,22 @@ def test_tensor_form_choice_follows_the_cost_model(M):
         assert M.mwmm_tensor_form(64, 64, 64, P[b]) == "int8", b
     assert M.mwmm_tensor_form(64, 64, (1 << 22) + 64, P[52]) == "int8"
     assert M.mwmm_tensor_form(4, 4, 4, 4) == "auto"  # no form plans an even p
+
+
+def test_noalloc_wrapper_rejects_mismatched_operands_before_any_launch(M):
+    """mwmm_matmul_noalloc's C entry point sees only pointers and sizes, so
+    its binding checks the shapes and the device first: a B with the wrong
+    number of rows, a C of the wrong shape, or operands off the GPU raise
+    ValueError without reaching the library (no kernel could then read or
+    write outside the tensors)."""
+    torch = pytest.importorskip("torch")
+    p = SWEEP[40]
+    A = torch.zeros((8, 6), dtype=torch.int64)
+    with pytest.raises(ValueError, match="rows"):
+        M.mwmm_matmul_noalloc(A, torch.zeros((5, 4), dtype=torch.int64), torch.zeros((8, 4), dtype=torch.int64), p)
+    with pytest.raises(ValueError, match="product is 8 x 4"):
+        M.mwmm_matmul_noalloc(A, torch.zeros((6, 4), dtype=torch.int64), torch.zeros((4, 8), dtype=torch.int64), p)
+    with pytest.raises(ValueError, match="2-D"):
+        M.mwmm_matmul_noalloc(A, torch.zeros(6, dtype=torch.int64), torch.zeros((8, 4), dtype=torch.int64), p)
+    with pytest.raises(ValueError, match="CUDA device"):
+        M.mwmm_matmul_noalloc(A, torch.zeros((6, 4), dtype=torch.int64), torch.zeros((8, 4), dtype=torch.int64), p)

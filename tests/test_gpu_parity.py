@@ -484,21 +484,19 @@ def test_mulmod_alg2_matches_xy_mod_p(M, oracle, p):
 @pytest.mark.parametrize("shape", [(129, 300, 257), (256, 256, 64), (700, 520, 1100), (1000, 90, 333),
                                    (100, 300, 200), (385, 20, 900)])
 @pytest.mark.parametrize("b", [20, 40, 52])
-def test_int8_pair_cluster_and_single_cta_kernels(M, oracle, shape, b):
+def test_int8_pair_and_single_cta_kernels(M, oracle, shape, b):
     """The two-CTA kernel (256-row tiles on an SM pair, tcgen05 cta_group::2,
-    tensor TMA completing on the leader's barrier), the one-CTA kernel in
-    clusters of two sharing B by TMA multicast, and lone one-CTA kernels (the
-    default) all match the oracle."""
+    tensor TMA completing on the leader's barrier) and the one-CTA kernel (the
+    default) both match the oracle."""
     m, n, k = shape
     p = SWEEP[b]
     A, B = inputs.problem(60 + b, m, n, k, p)
     ref = oracle.matmul_mod(A, B, p)
-    for pair, cl in ((False, 0), (False, 1), (False, 2), (True, 0)):
-        C, plan = gpu_product(M, A, B, p, form="int8", tc_pair=pair, tc_cluster=cl)
+    for pair in (False, True):
+        C, plan = gpu_product(M, A, B, p, form="int8", tc_pair=pair)
         assert plan.info["tc_pair"] == (1 if pair and n > 128 and m > 128 else 0)  # pairs need 256-wide tiles
-        assert plan.info["tc_cluster"] == (2 if m > 128 and not plan.info["tc_pair"] and cl == 2 else 1)
-        assert plan.info["A_rows"] % (256 if plan.info["tc_cluster"] == 2 or plan.info["tc_pair"] else 128) == 0
-        assert np.array_equal(C, ref), (pair, cl)
+        assert plan.info["A_rows"] % (256 if plan.info["tc_pair"] else 128) == 0
+        assert np.array_equal(C, ref), pair
 
 
 @pytest.mark.parametrize("n", [1, 15, 16, 17, 32, 40, 64, 65, 100, 128])

@@ -1,7 +1,8 @@
 """mwmm_matmul_noalloc: the product for callers that cannot allocate device
 memory (scratch in the library's static device array).  Checked through the
-C ABI against mwmm_matmul on the same inputs, on two calls in a row so the
-second call runs over what the first left in the shared array.
+C ABI against mwmm_matmul and against the CPU oracle on the same inputs, on
+two calls in a row so the second call runs over what the first left in the
+shared array.
 
 Kept in its own file, collected last, so a run that stops at the first
 failure has already run every other test."""
@@ -28,7 +29,7 @@ def _dev(x):
     return torch.from_numpy(np.ascontiguousarray(x).view(np.int64)).cuda()
 
 
-def test_noalloc_matches_matmul_on_two_calls_in_a_row(M):
+def test_noalloc_matches_matmul_on_two_calls_in_a_row(M, oracle):
     # first a larger problem with a wide prime, then a smaller ragged one with
     # a narrow prime: the second call's words and sums land on the first's.
     cases = [(700, 760, 730, inputs.largest_prime_below_pow2(52), 1),
@@ -42,6 +43,10 @@ def test_noalloc_matches_matmul_on_two_calls_in_a_row(M):
         st = M.mwmm_matmul_noalloc(dA, dB, C, p)
         assert st == 0, M.mwmm_status_str(st)
         assert torch.equal(C, ref), (m, n, k)
+        # and bit for bit against the CPU oracle (a fault the two library
+        # paths shared would pass the first comparison)
+        got = C.cpu().numpy().view(np.uint64)
+        assert np.array_equal(got, oracle.matmul_mod(A, B, p)), (m, n, k)
 
 
 def test_noalloc_rejects_products_larger_than_its_scratch(M):
