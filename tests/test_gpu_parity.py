@@ -295,6 +295,163 @@ def test_int8_top_digit_128_fills_the_fp32_chunk(M, oracle, b, sa, sb):
     assert np.array_equal(C, oracle.matmul_mod(A, B, p))
 
 
+# ------------------------------------------------------------------ FP32 chunk at its bound, odd low bits
+# The tensor form's exactness rests on one property of the device: FP32
+# tensor-memory accumulation of integer digit products is exact while every
+# partial sum stays within 2^24 (Prop. 2.3's block condition with a 24-bit
+# significand; a chunk holds at most 1024 products of magnitude <= 2^14).
+# The patterns below make each MMA (K = 16) add an odd integer, or a small one
+# far below the running sum, while that sum climbs past 2^23.8: an
+# accumulator that dropped even one low bit near 2^24 would change the
+# result.  The expected values come from the oracle only.
+CHUNK = 1024            # digit products per FP32 chunk (default plan)
+KDIM = CHUNK + 64       # two chunks: one full, one k-block
+
+
+def _chunk_partials(a_dig: np.ndarray, b_dig: np.ndarray) -> np.ndarray:
+    """Running sum after each K = 16 slice, restarted every CHUNK positions,
+    of sum_k a_dig[k] b_dig[k] (one diagonal with one word pair)."""
+    prod = (a_dig.astype(np.int64) * b_dig.astype(np.int64)).reshape(-1, 16).sum(axis=1)
+    return np.concatenate([np.cumsum(prod[i:i + CHUNK // 16]) for i in range(0, prod.size, CHUNK // 16)])
+
+
+def _odd_slices_patterns(pos: int, neg: int, rows: int, cols: int):
+    """A (rows x KDIM) and B (KDIM x cols) over {0, pos, neg}: A row r has
+    the value at 15 of every 16 k positions (0 at k % 16 == 15), with sign +
+    for the first r % 65 slices of each chunk and - after, so rows range from
+    all +, through a zero crossing at every slice, to all -; B columns are all
+    + or all - (by column parity)."""
+    k = np.arange(KDIM)
+    A = np.zeros((rows, KDIM), np.uint64)
+    for r in range(rows):
+        t = r % 65
+        plus = ((k % CHUNK) // 16) < t
+        A[r] = np.where(k % 16 == 15, 0, np.where(plus, pos, neg))
+    B = np.empty((KDIM, cols), np.uint64)
+    B[:, 0::2] = pos
+    B[:, 1::2] = neg
+    return A, B
+
+
+@pytest.mark.parametrize("b", [20, 40, 52])
+def test_int8_fp32_chunk_odd_increments_near_2_24(M, oracle, b):
+    """Digits +-127 at 15 of every 16 k positions against B digits +-127: every
+    MMA adds +-15 x 16129 (odd), and a chunk's running sum walks up to
+    +-64 x 241935 = +-15,483,840 (2^23.88), with zero crossings at every
+    slice across the rows."""
+    p = SWEEP[b]
+    u = oracle.int8_words(p)
+    A, B = _odd_slices_patterns(127, p - 127, 130, 260)
+    Ad = oracle.split_signed8(A, p, u)
+    Bd = oracle.split_signed8(B, p, u)
+    assert np.all(Ad[1:] == 0) and np.all(Bd[1:] == 0)  # only digit 0: one diagonal, one pair
+    peak = 0
+    for r in (0, 1, 32, 64):
+        for c in (0, 1):
+            part = _chunk_partials(Ad[0, r], Bd[0, :, c])
+            assert np.all(np.diff(part[:CHUNK // 16]) % 2 == 1) and np.all(np.abs(part) <= 2 ** 24)
+            peak = max(peak, int(np.abs(part).max()))
+    assert peak > 2 ** 23.85
+    C, _ = gpu_product(M, A, B, p, form="int8")
+    assert np.array_equal(C, oracle.matmul_mod(A, B, p))
+
+
+def _small_addend_patterns(big_pos, big_neg, one_pos, one_neg, sign):
+    """A (129 x KDIM), B (KDIM x 257): in each chunk the first 960 k positions
+    (60 slices) hold the large value, then each of the last 4 slices holds a
+    single small value (positions 960, 976, 992, 1008) and zeros; B holds the
+    large value, then the small one, with + and - columns.  Odd rows of A are
+    the pattern one slice later (the last small value moves into the next
+    chunk).  `sign` picks the sign of A's values."""
+    k = np.arange(KDIM)
+    pos = k % CHUNK
+    big, one = (big_pos, one_pos) if sign > 0 else (big_neg, one_neg)
+    row = np.where(pos < 960, big, 0).astype(np.uint64)
+    row[(pos >= 960) & (pos % 16 == 0)] = one
+    A = np.tile(row, (129, 1))
+    A[1::2] = np.roll(row, 16)
+    B = np.empty((KDIM, 257), np.uint64)
+    B[:, 0::2] = np.where(pos < 960, big_pos, one_pos)[:, None]
+    B[:, 1::2] = np.where(pos < 960, big_neg, one_neg)[:, None]
+    return A, B
+
+
+@pytest.mark.parametrize("b", [20, 52])
+@pytest.mark.parametrize("sign", [1, -1])
+def test_int8_fp32_chunk_small_addend_below_large_sum(M, oracle, b, sign):
+    """A chunk first sums 960 products of +-16129 (reaching +-15,483,840,
+    2^23.88), then four MMAs that each add +-1 (one product 1 x 1 in 16): the
+    small addends sit 24 bits below the accumulator."""
+    p = SWEEP[b]
+    u = oracle.int8_words(p)
+    A, B = _small_addend_patterns(127, p - 127, 1, p - 1, sign)
+    Ad = oracle.split_signed8(A, p, u)
+    Bd = oracle.split_signed8(B, p, u)
+    assert np.all(Ad[1:] == 0) and np.all(Bd[1:] == 0)
+    part = _chunk_partials(Ad[0, 0], Bd[0, :, 0])
+    last = part[CHUNK // 16 - 5:CHUNK // 16]
+    assert list(np.diff(last)) == [sign] * 4 and abs(int(last[0])) == 960 * 16129
+    assert np.all(np.abs(part) <= 2 ** 24) and np.abs(part).max() > 2 ** 23.85
+    C, _ = gpu_product(M, A, B, p, form="int8")
+    assert np.array_equal(C, oracle.matmul_mod(A, B, p))
+
+
+@pytest.mark.parametrize("b", [20, 40, 52])
+def test_int8_fp32_chunk_odd_increments_in_a_two_pair_diagonal(M, oracle, b):
+    """Digits 0 and 1 both at +-127 (entries +-(127 + 127 x 256)): diagonal 1
+    concatenates the pairs (0,1) and (1,0) along K, so its chunks span both
+    pairs; every slice still adds an odd multiple of 16129."""
+    p = SWEEP[b]
+    u = oracle.int8_words(p)
+    e = 127 + 127 * 256
+    A, B = _odd_slices_patterns(e, p - e, 130, 260)
+    Ad = oracle.split_signed8(A, p, u)
+    assert np.all(np.abs(Ad[:2]) <= 127) and np.all(Ad[2:] == 0) and int(Ad[1, 64, 0]) == 127
+    C, _ = gpu_product(M, A, B, p, form="int8")
+    assert np.array_equal(C, oracle.matmul_mod(A, B, p))
+
+
+@pytest.mark.parametrize("b", [20, 40, 52])
+def test_crt_fp32_chunk_odd_increments_near_2_24(M, oracle, b):
+    """The CRT form's chunks: entries with residue +-125 modulo 251 (the
+    first modulus; 125 and 126 = 251 - 125) at 15 of every 16 k positions,
+    so the modulus-251 product adds +-15 x 15625 (odd) per slice and climbs
+    to +-15,000,000 (2^23.84); the other moduli see other odd-heavy
+    residues."""
+    p = SWEEP[b]
+    moduli = oracle.crt_moduli(p, KDIM)
+    assert moduli[0] == 251
+    A, B = _odd_slices_patterns(125, 126, 130, 260)
+    R = oracle.crt_residues(A, moduli)
+    Rb = oracle.crt_residues(B, moduli)
+    part = _chunk_partials(R[0, 64], Rb[0, :, 0])
+    assert np.all(np.diff(part[:CHUNK // 16]) % 2 == 1) and np.abs(part).max() > 2 ** 23.8
+    assert np.all(np.abs(part) <= 2 ** 24)
+    C, plan = gpu_product(M, A, B, p, form="crt8")
+    assert plan.info["crt_m"][0] == 251 and plan.info["tc_chunk"] == CHUNK
+    assert np.array_equal(C, oracle.matmul_mod(A, B, p))
+
+
+@pytest.mark.parametrize("b", [20, 52])
+@pytest.mark.parametrize("sign", [1, -1])
+def test_crt_fp32_chunk_small_addend_below_large_sum(M, oracle, b, sign):
+    """CRT residues modulo 251: 960 products of +-125 x 125 (15,000,000,
+    2^23.84), then four MMAs adding +-1 (residues 1 x 1) in the same chunk;
+    126 and 250 are the residues -125 and -1."""
+    p = SWEEP[b]
+    moduli = oracle.crt_moduli(p, KDIM)
+    assert moduli[0] == 251
+    A, B = _small_addend_patterns(125, 126, 1, 250, sign)
+    R = oracle.crt_residues(A, moduli)
+    Rb = oracle.crt_residues(B, moduli)
+    part = _chunk_partials(R[0, 0], Rb[0, :, 0])
+    last = part[CHUNK // 16 - 5:CHUNK // 16]
+    assert list(np.diff(last)) == [sign] * 4 and abs(int(last[0])) == 960 * 15625
+    assert np.all(np.abs(part) <= 2 ** 24)
+    C, _ = gpu_product(M, A, B, p, form="crt8")
+    assert np.array_equal(C, oracle.matmul_mod(A, B, p))
+
+
 @pytest.mark.parametrize("form", ["fp64", "int8", "crt8"])
 def test_leading_dimensions_and_degenerate_shapes(M, oracle, form):
     p = SWEEP[32]
@@ -578,3 +735,63 @@ def test_concurrent_plans_on_separate_streams(M, oracle):
         assert pl.check() == 0
         assert np.array_equal(host(C), oracle.matmul_mod(A, B, p))
         assert torch.equal(pl.matmul(dA, dB), C)
+
+
+_THREADS_SCRIPT = r'''
+import sys, threading
+import numpy as np
+import torch
+sys.path.insert(0, sys.argv[1])
+from paper_2601_07508_b300 import inputs, mwmm
+out = sys.argv[2]
+mwmm.lib()
+cases = [(300, 260, 700, 52, "int8", False), (257, 300, 513, 40, "crt8", False), (400, 300, 500, 48, "int8", True),
+         (128, 129, 300, 32, "fp64", False)]
+go = threading.Barrier(len(cases))
+errors = []
+
+def run(i):
+    try:
+        m, n, k, b, form, pair = cases[i]
+        p = inputs.largest_prime_below_pow2(b)
+        A, B = inputs.problem(7800 + i, m, n, k, p)
+        dA = torch.from_numpy(A.view(np.int64)).cuda()
+        dB = torch.from_numpy(B.view(np.int64)).cuda()
+        st = torch.cuda.Stream()
+        plan = mwmm.Plan(m, n, k, p, form=form, tc_pair=pair)
+        go.wait()  # the first launches (and the launchers' cache fills) start together
+        with torch.cuda.stream(st):
+            C = plan.matmul(dA, dB, stream=st)
+            for _ in range(3):
+                plan.matmul(dA, dB, C, stream=st)
+        assert plan.check(st) == 0
+        np.save("%s/c%d.npy" % (out, i), C.cpu().numpy().view(np.uint64))
+    except Exception as e:  # reported by the parent
+        errors.append(repr(e))
+
+th = [threading.Thread(target=run, args=(i,)) for i in range(len(cases))]
+for t in th: t.start()
+for t in th: t.join()
+if errors:
+    print(errors); sys.exit(1)
+'''
+
+
+def test_plans_on_host_threads_launching_together_in_a_fresh_process(M, oracle, tmp_path):
+    """Four host threads, each with its own plan (one-CTA and pair tcgen05
+    kernels, CRT, FP64) and stream, make their first calls at the same
+    moment in a fresh process, so the launchers' host-side caches (kernel
+    attributes, SM and cluster counts) are filled concurrently; every result
+    equals the oracle."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "-c", _THREADS_SCRIPT, root, str(tmp_path)], capture_output=True,
+                       text=True, timeout=600)
+    assert r.returncode == 0, r.stdout + r.stderr
+    cases = [(300, 260, 700, 52), (257, 300, 513, 40), (400, 300, 500, 48), (128, 129, 300, 32)]
+    for i, (m, n, k, b) in enumerate(cases):
+        p = inputs.largest_prime_below_pow2(b)
+        A, B = inputs.problem(7800 + i, m, n, k, p)
+        assert np.array_equal(np.load(tmp_path / ("c%d.npy" % i)), oracle.matmul_mod(A, B, p)), i
