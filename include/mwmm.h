@@ -115,13 +115,25 @@ typedef struct {
                          along n when n <= m and 2 <= v <= 4, else A's along m
                          when 2 <= u <= 4), 1 = never, 2 = B's words
                          (needs 2 <= v <= 4), 3 = A's words (2 <= u <= 4) */
-    int32_t ksplit;     /* FP64 form: K ranges computed by separate CTAs and
-                         added mod p afterwards, 1..64 (0: chosen so that the
-                         last wave of CTAs is nearly full) */
+    int32_t ksplit;     /* FP64 form and INT8 fused form: K ranges computed by
+                         separate CTAs (pairs) and added mod p afterwards,
+                         1..64 (0: chosen so that the last wave is nearly
+                         full) */
     int32_t autotune;   /* mwmm_batch_create / mwmm_matmul_batched only:
                          nonzero picks (u,v) and the K-range per bitsize
                          group by timing candidates (see mwmm_plan_autotuned) */
-    int32_t reserved[4];
+    int32_t tc_fused;   /* INT8 form: 2 = fuse the reduction and recombination
+                         into the word-product kernel's epilogue when n > 128
+                         (256 x 128 tiles on CTA pairs, residues in tensor
+                         memory, no diagonal sums in memory: the workspace is
+                         the words only, plus K-part planes when ksplit > 1);
+                         0 (default) or 1 = diagonal sums to the workspace,
+                         then the recombination kernel -- the faster form on
+                         B300 (the fused tiles are half as wide) */
+    int32_t tc_seg;     /* INT8 fused form: k-blocks of 64 per segment, the
+                         k-range of one INT32 sum (0: 64, or fewer when the
+                         INT32 bound requires) */
+    int32_t reserved[2];
 } mwmm_plan_opts;
 
 /* What a plan decided (mwmm_plan_info). */
@@ -156,19 +168,23 @@ typedef struct {
      * k-block, E = 16 / element size) is stored at granule position
      * g ^ (r mod 8).  Element type: double (FP64 form, kb_elems = 16) or
      * bf16 holding an integer digit (INT8 form, kb_elems = 64).  Padding is 0.
-     * INT8 form: S (int32) at S_off, laid out [nsums][nkc][A_rows][B_rows].
+     * INT8 form: S (int32) at S_off, laid out [nsums][nkc][A_rows][B_rows];
+     * fused (tc_fused = 1): nothing at S_off unless ksplit > 1, then the K
+     * parts' residues (uint64) laid out [ksplit][m][n rounded up to even].
      * FP64 form with ksplit > 1: the partial results of the K ranges
      * (uint64 residues) at S_off, laid out [ksplit][m][n]. */
     int64_t kb_elems, nkb, A_rows, B_rows;
     int32_t B_wpad;
-    int32_t pad0;
+    int32_t tc_fused;       /* INT8: 1 when the reduction and recombination run in the word-product
+                               kernel's epilogue (then kc = 64 tc_seg is the k-range of one INT32 sum,
+                               nkc = ceil(k / kc), and ksplit K parts each write a partial plane) */
     uint64_t A_off, B_off, S_off;
     uint64_t workspace_bytes;
     int32_t f64_concat;     /* FP64: 1 when B's words are concatenated along n, 2 when A's along m (Alg. 6) */
-    int32_t ksplit;         /* FP64: K ranges (1: none) */
+    int32_t ksplit;         /* FP64 and INT8 fused: K ranges (1: none) */
     double tuned_ms;        /* mwmm_plan_autotuned: measured time of the chosen configuration (0: not tuned) */
     int32_t tuned_tried;    /* candidates timed (0 when the choice came from the cache) */
-    int32_t pad1;
+    int32_t tc_seg;         /* INT8 fused: k-blocks per segment */
     uint32_t crt_m[24];     /* CRT form: the moduli m_0 > m_1 > ... (u of them); word i of A and of B
                                holds the signed residues modulo m_i, sum plane i their product */
 } mwmm_plan_desc;
@@ -420,9 +436,12 @@ void mwmm_serve_destroy(mwmm_server_t server);
  * Every call shares the one array, so calls that overlap on the GPU race:
  * issue them one at a time per device.  Synchronous: returns once C is
  * written.  Calls no cudaMalloc/cudaFree or other allocating routine.
- * Errors: MWMM_ERR_BUDGET when the product's workspace exceeds the array
- * (about m = n = k = 768 at 52 bits; more for smaller primes), plus the
- * errors of mwmm_plan and mwmm_matmul, and MWMM_ERR_TIMEOUT. */
+ * A product whose words and diagonal sums exceed the array runs the fused
+ * form instead (tc_fused = 2 of mwmm_plan_opts, when n > 128: the sums stay
+ * on the SM, so the scratch holds the words only).
+ * Errors: MWMM_ERR_BUDGET when even the words exceed the array (about
+ * m = n = k = 1500 at 52 bits; more for smaller primes), plus the errors of
+ * mwmm_plan and mwmm_matmul, and MWMM_ERR_TIMEOUT. */
 mwmm_status mwmm_matmul_noalloc(int64_t m, int64_t n, int64_t k, uint64_t p,
                                 const uint64_t *dA, int64_t lda, const uint64_t *dB, int64_t ldb,
                                 uint64_t *dC, int64_t ldc, void *stream);

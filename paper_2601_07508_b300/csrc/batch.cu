@@ -204,9 +204,16 @@ int launch_product(const Plan &pl, const uint64_t *dA, int64_t lda, const uint64
     if (pl.form == MWMM_FORM_FP64)
         return launch_gemm_fp64(pl, ws + pl.A_off, ws + pl.B_off, dC, ldc, reinterpret_cast<uint64_t *>(ws + pl.S_off),
                                 pl.err_dev, stream);
+    return launch_tensor_products(pl, ws, dC, ldc, pl.err_dev, stream);
+}
+
+int launch_tensor_products(const Plan &pl, uint8_t *ws, uint64_t *C, int64_t ldc, int *err, void *stream) {
+    if (pl.tc_fused)
+        return launch_gemm_tc_fused(pl, ws + pl.A_off, ws + pl.B_off, C, ldc, reinterpret_cast<uint64_t *>(ws + pl.S_off),
+                                    err, stream);
     int32_t *S = reinterpret_cast<int32_t *>(ws + pl.S_off);
-    e = launch_gemm_tc(pl, ws + pl.A_off, ws + pl.B_off, S, pl.err_dev, stream);
-    if (!e) e = launch_recombine(pl, S, dC, ldc, stream);
+    int e = launch_gemm_tc(pl, ws + pl.A_off, ws + pl.B_off, S, err, stream);
+    if (!e) e = launch_recombine(pl, S, C, ldc, stream);
     return e;
 }
 
@@ -389,6 +396,7 @@ mwmm_status mwmm_batch_create(mwmm_batch_t *out, const mwmm_problem *probs, int 
         }
         o.lambda = 0;      // per-problem block sizes: always the bound
         o.tc_pair = 0;
+        o.tc_fused = 1;    // table items write diagonal sums for the batched recombination
         o.ksplit = 1;      // batched FP64 tiles run the whole K range
         mwmm_status st = mwmm::make_plan(&b->plans[i], q.m, q.n, q.k, q.p, u, v, pf, &o);
         if (st != MWMM_OK && (u || v || o.kc)) {  // the group's words do not fit this prime: plan it alone

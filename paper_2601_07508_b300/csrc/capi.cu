@@ -136,6 +136,14 @@ mwmm_status run_product(mwmm_plan_s *h, const uint64_t *dA, int64_t lda, const u
         if (h->timing) h->pending_launches += (dA ? 3 : 2) + (pl.ksplit > 1 ? 1 : 0);
         return cuda_status(e);
     }
+    if (pl.tc_fused) {  // products, reduction and recombination in one kernel (+ the K-part sum)
+        e = mwmm::launch_gemm_tc_fused(pl, ws + pl.A_off, ws + pl.B_off, dC, ldc,
+                                       reinterpret_cast<uint64_t *>(ws + pl.S_off), pl.err_dev, stream);
+        rec(pe.ev[3], s);
+        rec(pe.ev[4], s);
+        if (h->timing) h->pending_launches += (dA ? 3 : 2) + (pl.ksplit > 1 ? 1 : 0);
+        return cuda_status(e);
+    }
     int32_t *S = reinterpret_cast<int32_t *>(ws + pl.S_off);
     e = mwmm::launch_gemm_tc(pl, ws + pl.A_off, ws + pl.B_off, S, pl.err_dev, stream);
     if (e) return cuda_status(e);
@@ -173,7 +181,10 @@ mwmm_status make_sub_plan(const Plan &pl, int64_t rows, Plan *out) {
         o.f64_concat = pl.f64_concat ? 2 : 1;
     } else {
         o.tc_chunk = (int32_t)pl.tc_chunk;
-        o.kc = pl.kc;
+        o.kc = pl.tc_fused ? 0 : pl.kc;
+        o.tc_pair = pl.tc_pair;
+        o.tc_fused = pl.tc_fused ? 2 : 1;  // every row block in the parent's layout of B's words
+        o.tc_seg = pl.tc_seg;
     }
     const bool crt = pl.form == MWMM_FORM_CRT8;  // its words follow from p and k
     mwmm_status st = mwmm::make_plan(out, rows, pl.n, pl.k, pl.p, crt ? 0 : pl.u, crt ? 0 : pl.v, pl.form, &o);
@@ -219,6 +230,8 @@ int run_rows(const Plan &sub, const uint64_t *dA, int64_t lda, uint8_t *ws, cons
     if (e) return e;
     if (sub.form == MWMM_FORM_FP64)
         return mwmm::launch_gemm_fp64(sub, Aw, Bw, dC, ldc, reinterpret_cast<uint64_t *>(Sr), sub.err_dev, s);
+    if (sub.tc_fused)
+        return mwmm::launch_gemm_tc_fused(sub, Aw, Bw, dC, ldc, reinterpret_cast<uint64_t *>(Sr), sub.err_dev, s);
     e = mwmm::launch_gemm_tc(sub, Aw, Bw, reinterpret_cast<int32_t *>(Sr), sub.err_dev, s);
     if (e) return e;
     return mwmm::launch_recombine(sub, reinterpret_cast<int32_t *>(Sr), dC, ldc, s);
@@ -373,6 +386,8 @@ void describe_plan(const Plan &P, mwmm_plan_desc *d) {
     d->q = P.q;
     d->kb_elems = P.kb_elems; d->nkb = P.nkb; d->A_rows = P.A_rows; d->B_rows = P.B_rows;
     d->B_wpad = P.B_wpad;
+    d->tc_fused = P.tc_fused;
+    d->tc_seg = P.tc_seg;
     d->A_off = P.A_off; d->B_off = P.B_off; d->S_off = P.S_off;
     d->workspace_bytes = P.ws_bytes;
     d->tuned_ms = P.tuned_ms;

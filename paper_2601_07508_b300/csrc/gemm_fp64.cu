@@ -353,6 +353,8 @@ int prepare_kernel_attributes() {
     cudaError_t e = set_smem_attr(reinterpret_cast<const void *>(gemm_fp64_kernel), smem);
     if (e == cudaSuccess) e = set_smem_attr(reinterpret_cast<const void *>(gemm_fp64_batched_kernel), smem);
     if (e != cudaSuccess) return (int)e;
+    e = (cudaError_t)prepare_tc_fused_attributes();
+    if (e != cudaSuccess) return (int)e;
     return prepare_tc_attributes();
 }
 

@@ -31,14 +31,12 @@
 //               sum the chunks of an item, store S_s.
 // Every wait is bounded (device_common.cuh); a timeout raises the plan's
 // error flag and all roles leave their loops.
-#include <cuda.h>  // CUtensorMap (encoded through the runtime's driver entry point)
 #include <cuda_bf16.h>
-#include <cudaTypedefs.h>
 
 #include <cstring>
 
-#include "device_common.cuh"
 #include "mwmm_internal.h"
+#include "tcgen05.cuh"
 
 namespace mwmm {
 
@@ -190,24 +188,9 @@ __device__ __forceinline__ Item get_item(const TcParams &P, int64_t idx) {
     return kTable ? table_item(P, idx) : computed_item(P, idx);
 }
 
-// ---- tcgen05 wrappers -------------------------------------------------------
-// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
-// 1024 bytes apart (SBO), descriptor version 1.
-__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
-    uint64_t d = 0;
-    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
-    d |= (uint64_t)1 << 16;             // LBO (unused for swizzled K-major)
-    d |= (uint64_t)(1024 >> 4) << 32;   // SBO
-    d |= (uint64_t)1 << 46;             // version
-    d |= (uint64_t)2 << 61;             // SWIZZLE_128B
-    return d;
-}
-
-// Instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major,
-// M = 128, N = n (a multiple of 16, at most 256).
-__device__ __forceinline__ uint32_t idesc_n(int n) {
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
-}
+// Instruction descriptor of a one-CTA MMA: M = 128, N = n (a multiple of 16,
+// at most 256).
+__device__ __forceinline__ uint32_t idesc_n(int n) { return idesc_bf16(BM, n); }
 
 __device__ __forceinline__ void mma_bf16(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
                                          uint32_t acc) {
@@ -217,51 +200,6 @@ __device__ __forceinline__ void mma_bf16(uint32_t dtmem, uint64_t adesc, uint64_
         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
         "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
         : "memory");
-}
-
-__device__ __forceinline__ void mma_commit(uint64_t *bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                     smem_u32(bar))
-                 : "memory");
-}
-
-__device__ __forceinline__ void tc_fence_before() {
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void tc_fence_after() {
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-}
-
-__device__ __forceinline__ uint32_t cluster_rank() {
-    uint32_t r;
-    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-    return r;
-}
-__device__ __forceinline__ uint32_t peer_addr(const void *local, uint32_t rank) {
-    uint32_t r;
-    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(smem_u32(local)), "r"(rank));
-    return r;
-}
-__device__ __forceinline__ void mbar_arrive_cluster(uint32_t cluster_addr) {
-    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr) : "memory");
-}
-__device__ __forceinline__ void cluster_sync_all() {
-    asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;" ::: "memory");
-}
-
-// 32 consecutive FP32 columns of this thread's TMEM lane.
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
-          "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
-          "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
-          "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
 // Store this warp's 32 x 128 block of sums (row r held by lane r in acc)
@@ -476,26 +414,7 @@ constexpr int BM2 = 256;
 constexpr uint32_t kTileA2 = 128 * kTileBytes;  // own 128 rows of A: 16 KB
 constexpr uint32_t kTileB2 = 128 * kTileBytes;  // own half of B: 16 KB
 constexpr int kSmemPair = P_STAGES * (kTileA2 + kTileB2) + kStageBytes + 1024;
-constexpr uint32_t kIdescPair = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
-                                ((uint32_t)(BM2 >> 4) << 24);
-
-__device__ __forceinline__ void mma_bf16_pair(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t acc) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
-        "l"(adesc), "l"(bdesc), "r"(kIdescPair), "r"(acc)
-        : "memory");
-}
-// Arrive once on `bar` (same shared-memory offset) in every CTA of `mask`
-// when all MMAs issued so far by this thread have completed.
-__device__ __forceinline__ void mma_commit_pair(uint64_t *bar, uint16_t mask) {
-    asm volatile(
-        "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
-            smem_u32(bar)),
-        "h"(mask)
-        : "memory");
-}
+constexpr uint32_t kIdescPair = idesc_bf16(BM2, BN);
 
 __device__ __forceinline__ Item pair_item(const TcParams &P, int64_t idx) {
     // tiles of 256 rows: mt counts 256-row tiles here; A_rows % 256 == 0
@@ -531,17 +450,6 @@ __device__ __forceinline__ Item pair_item(const TcParams &P, int64_t idx) {
     it.rv = (int)(rv < BM2 ? rv : BM2);
     it.cv = (int)(cv < BN ? cv : BN);
     return it;
-}
-
-// 2-D tensor TMA of a (64-element x 128-row) box at row y into this CTA's
-// shared memory; the bytes complete on the barrier at cluster address `bar`
-// (the leader's) -- the .cta_group::2 form allows either CTA of the pair.
-__device__ __forceinline__ void tma2_load_pair(void *dst, const CUtensorMap *map, int32_t y, uint32_t bar) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, "
-        "%3}], [%4];" ::"r"(smem_u32(dst)),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(0), "r"(y), "r"(bar)
-        : "memory");
 }
 
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS, 1)
@@ -651,7 +559,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS, 1)
                         const uint64_t ad = sdesc(a0 + slot * kTileA2), bd = sdesc(b0 + slot * kTileB2);
 #pragma unroll
                         for (int kk = 0; kk < 4; ++kk)
-                            mma_bf16_pair(dt, ad + 2 * kk, bd + 2 * kk, (t > t0 || kk > 0) ? 1u : 0u);
+                            mma_bf16_pair(dt, ad + 2 * kk, bd + 2 * kk, kIdescPair, (t > t0 || kk > 0) ? 1u : 0u);
                         mma_commit_pair(&empty[slot], 3);
                     }
                     mma_commit_pair(&tfull[buf], 3);
@@ -707,6 +615,13 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS, 1)
                      : "memory");
 }
 
+int pair_clusters() {
+    static int cached[64] = {0};
+    return max_clusters2(reinterpret_cast<const void *>(gemm_tc_pair_kernel), THREADS, kSmemPair, cached);
+}
+
+}  // namespace
+
 int sm_count() {
     static int cached[64] = {0};
     int dev = 0;
@@ -720,9 +635,7 @@ int sm_count() {
     return cached[dev];
 }
 
-// Clusters of two of `kernel` that can be resident at once (the cluster
-// kernels are persistent: one cluster per SM pair, never more than fit).
-int max_clusters2(const void *kernel, int smem, int (&cached)[64]) {
+int max_clusters2(const void *kernel, int threads, int smem, int (&cached)[64]) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
     if (set_smem_attr(kernel, smem) != cudaSuccess) return 0;
@@ -731,7 +644,7 @@ int max_clusters2(const void *kernel, int smem, int (&cached)[64]) {
     if (!cached[dev]) {
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(2 * (unsigned)(sms / 2), 1, 1);
-        cfg.blockDim = dim3(THREADS, 1, 1);
+        cfg.blockDim = dim3((unsigned)threads, 1, 1);
         cfg.dynamicSmemBytes = smem;
         cudaLaunchAttribute attr;
         attr.id = cudaLaunchAttributeClusterDimension;
@@ -762,15 +675,13 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
     return fn;
 }
 
-// A word region as a 2-D tensor of `rows` 128-byte rows (64 x 16-bit), read
-// in (64 x 128-row) boxes with no swizzle: a box is one contiguous 16 KB tile.
-int encode_rows_map(CUtensorMap *map, const void *base, uint64_t rows) {
+int encode_rows_map(CUtensorMap *map, const void *base, uint64_t rows, uint32_t box_rows) {
     PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
     if (!enc) return (int)cudaErrorNotSupported;
     if (rows == 0 || rows > (uint64_t)INT32_MAX) return (int)cudaErrorInvalidValue;  // int32 coordinates
     const cuuint64_t dims[2] = {64, rows};
     const cuuint64_t strides[1] = {kTileBytes};
-    const cuuint32_t box[2] = {64, 128};
+    const cuuint32_t box[2] = {64, box_rows};
     const cuuint32_t estr[2] = {1, 1};
     CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, const_cast<void *>(base), dims, strides, box, estr,
                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -778,12 +689,6 @@ int encode_rows_map(CUtensorMap *map, const void *base, uint64_t rows) {
     return r == CUDA_SUCCESS ? 0 : (int)cudaErrorInvalidValue;
 }
 
-int pair_clusters() {
-    static int cached[64] = {0};
-    return max_clusters2(reinterpret_cast<const void *>(gemm_tc_pair_kernel), kSmemPair, cached);
-}
-
-}  // namespace
 
 int launch_gemm_tc(const Plan &pl, const void *Aw, const void *Bw, int32_t *S, int *err, void *stream) {
     TcParams P;
@@ -860,8 +765,8 @@ int launch_gemm_tc(const Plan &pl, const void *Aw, const void *Bw, int32_t *S, i
         if (clusters <= 0) return (int)cudaErrorLaunchOutOfResources;
         const int64_t ncl = P.nitems < clusters ? P.nitems : clusters;
         CUtensorMap tmA, tmB;
-        int r = encode_rows_map(&tmA, Aw, (uint64_t)pl.u * pl.nkb * pl.A_rows);
-        if (r == 0) r = encode_rows_map(&tmB, Bw, (uint64_t)pl.v * pl.nkb * pl.B_rows);
+        int r = encode_rows_map(&tmA, Aw, (uint64_t)pl.u * pl.nkb * pl.A_rows, 128);
+        if (r == 0) r = encode_rows_map(&tmB, Bw, (uint64_t)pl.v * pl.nkb * pl.B_rows, 128);
         if (r != 0) return r;
         gemm_tc_pair_kernel<<<(unsigned)(2 * ncl), THREADS, kSmemPair, static_cast<cudaStream_t>(stream)>>>(P, tmA,
                                                                                                             tmB);

@@ -23,6 +23,8 @@ constexpr int kTcBM = 128;              // MMA M (one CTA, TMEM lanes)
 constexpr int kTcBN = 256;              // MMA N
 constexpr int kTcMaxChunk = 1024;       // 2^24 / 2^14 digit products per FP32 chunk
 constexpr int64_t kInt32SumLimit = 131071; // floor((2^31 - 1) / 2^14): products per INT32 sum
+constexpr int kFusedSeg = 64;           // fused form: default k-blocks per segment (4096 k)
+constexpr int kFusedPairs = 74;         // fused form: CTA pairs the planner assumes (148 SMs)
 
 // One work item of the tcgen05 kernel: the word products of the diagonals
 // s0 .. s0 + ndiag - 1 over k-blocks [kb0, kb0 + nkbc) for the 128-row tile mt
@@ -73,6 +75,13 @@ struct Plan {
     // INT8 form
     int64_t tc_chunk = 0, kc = 0;
     int tc_pair = 0;  // 1: 2-CTA kernel, A rows padded to 256
+    // Fused recombination (gemm_tc_fused.cu): 256 x 128 tiles on CTA pairs,
+    // A rows padded to 256 and B rows to 128; segments of tc_seg k-blocks;
+    // K parts = ksplit (of kbr k-blocks), their residues in ksplit planes of
+    // m x tc_ldr uint64 at S_off when ksplit > 1
+    int tc_fused = 0;
+    int tc_seg = 0;
+    int64_t tc_ldr = 0;
     int tc_nb = 256;  // B rows per word slice of a tile (256, or n padded to 16/32/64/128)
     int tc_ndiag = 1; // diagonals per work item (256 / tc_nb, at most nsums)
     int nkc = 0, nsums = 0;
@@ -114,6 +123,14 @@ int launch_gemm_fp64(const Plan &pl, const void *Aw, const void *Bw, uint64_t *C
                      int *err, void *stream);
 int launch_gemm_tc(const Plan &pl, const void *Aw, const void *Bw, int32_t *S, int *err, void *stream);
 int launch_recombine(const Plan &pl, const int32_t *S, uint64_t *C, int64_t ldc, void *stream);
+// Fused form (pl.tc_fused): word products, reduction and recombination in one
+// kernel, plus the K-part sum when pl.ksplit > 1 (R = workspace at S_off).
+int launch_gemm_tc_fused(const Plan &pl, const void *Aw, const void *Bw, uint64_t *C, int64_t ldc, uint64_t *R,
+                         int *err, void *stream);
+int prepare_tc_fused_attributes();
+// The word products and recombination of a tensor-form plan (fused or not),
+// on the words in ws, writing C; one or two launches (three with K parts).
+int launch_tensor_products(const Plan &pl, uint8_t *ws, uint64_t *C, int64_t ldc, int *err, void *stream);
 // batched split: job records are opaque blobs of split_job_bytes() bytes
 size_t split_job_bytes();
 void split_job(const Plan &pl, int side, const uint64_t *M, int64_t ld, void *words, void *job, int job_index,

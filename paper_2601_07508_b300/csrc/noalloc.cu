@@ -11,9 +11,11 @@
 // g_scratch below.
 //
 // Properties the caller must know:
-//   - The scratch is kNoAllocScratchBytes (64 MiB).  A product whose
-//     workspace does not fit (roughly m = n = k = 768 at 52 bits, larger
-//     for smaller primes) is rejected with MWMM_ERR_BUDGET before any work.
+//   - The scratch is kNoAllocScratchBytes (64 MiB).  A product whose words
+//     and diagonal sums do not fit runs the fused form (sums kept on the
+//     SM, n > 128), whose scratch is the words alone; one that does not fit
+//     either (roughly m = n = k = 1500 at 52 bits, larger for smaller
+//     primes) is rejected with MWMM_ERR_BUDGET before any work.
 //   - The array belongs to this library's device code: once this code is
 //     loaded on a GPU (at the latest on the first call on that GPU), the GPU
 //     holds the 64 MiB until the process exits.
@@ -31,6 +33,7 @@
 //   - It calls no cudaMalloc, cudaFree or other allocating routine.
 #include <cuda_runtime.h>
 
+#include <cstring>
 #include <mutex>
 
 #include "mwmm_internal.h"
@@ -76,6 +79,16 @@ extern "C" mwmm_status mwmm_matmul_noalloc(int64_t m, int64_t n, int64_t k, uint
     if (m == 0 || n == 0) return MWMM_OK;
     if (!dC || (k > 0 && (!dA || !dB)) || lda < (k > 0 ? k : 1) || ldb < (n > 0 ? n : 1) || ldc < n)
         return MWMM_ERR_ARG;
+    if (pl.ws_bytes > kNoAllocScratchBytes - kErrBytes && n > kTcBN / 2) {
+        // Too large with the diagonal sums in the scratch: the fused form
+        // keeps them on the SM and needs the words only (one K part, so no
+        // partial planes either).
+        mwmm_plan_opts o;
+        std::memset(&o, 0, sizeof(o));
+        o.tc_fused = 2;
+        o.ksplit = 1;
+        if ((st = make_plan(&pl, m, n, k, p, 0, 0, MWMM_FORM_INT8, &o)) != MWMM_OK) return st;
+    }
     if (pl.ws_bytes > kNoAllocScratchBytes - kErrBytes) return MWMM_ERR_BUDGET;
     uint8_t *base = nullptr;
     st = scratch_ptr(&base);
@@ -92,9 +105,7 @@ extern "C" mwmm_status mwmm_matmul_noalloc(int64_t m, int64_t n, int64_t k, uint
     if (cudaMemsetAsync(err, 0, kErrBytes, s) != cudaSuccess) return MWMM_ERR_CUDA;
     if ((st = from_cuda(launch_split(pl, 0, dA, lda, ws + pl.A_off, stream))) != MWMM_OK) return st;
     if ((st = from_cuda(launch_split(pl, 1, dB, ldb, ws + pl.B_off, stream))) != MWMM_OK) return st;
-    int32_t *S = reinterpret_cast<int32_t *>(ws + pl.S_off);
-    if ((st = from_cuda(launch_gemm_tc(pl, ws + pl.A_off, ws + pl.B_off, S, err, stream))) != MWMM_OK) return st;
-    if ((st = from_cuda(launch_recombine(pl, S, dC, ldc, stream))) != MWMM_OK) return st;
+    if ((st = from_cuda(launch_tensor_products(pl, ws, dC, ldc, err, stream))) != MWMM_OK) return st;
     int flags[2] = {0, 0};
     if (cudaMemcpyAsync(flags, err, sizeof(flags), cudaMemcpyDeviceToHost, s) != cudaSuccess) return MWMM_ERR_CUDA;
     if (cudaStreamSynchronize(s) != cudaSuccess) return MWMM_ERR_CUDA;

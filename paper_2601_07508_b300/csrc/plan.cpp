@@ -324,10 +324,22 @@ mwmm_status make_plan(Plan *pl, int64_t m, int64_t n, int64_t k, uint64_t p, int
         if (form == MWMM_FORM_CRT8) P.tc_ndiag = 1;  // each modulus pairs A_i with B_i only: no windows
         // the 2-CTA kernel (opt-in) computes 256 x 256 tiles
         P.tc_pair = (m > kTcBM && P.tc_nb == kTcBN && o.tc_pair) ? 1 : 0;
-        P.A_rows = round_up(m > 0 ? m : 1, P.tc_pair ? 2 * kTcBM : kTcBM);
+        // Fused recombination (INT8 form, n > 128) on request (tc_fused = 2):
+        // its 256 x 128 pair tiles run the word products at about 60% of the
+        // one-CTA 128 x 256 kernel's rate on B300, so the default keeps the
+        // diagonal sums in the workspace; it needs no sum planes, which is
+        // what memory-bound callers want.
+        if (o.tc_fused < 0 || o.tc_fused > 2 || o.tc_seg < 0) return MWMM_ERR_ARG;
+        if (form == MWMM_FORM_INT8 && n > kTcBN / 2 && o.tc_fused == 2) {
+            P.tc_fused = 1;
+            P.tc_pair = 0;
+            P.tc_nb = kTcBN;
+            P.tc_ndiag = 1;
+        }
+        P.A_rows = round_up(m > 0 ? m : 1, (P.tc_pair || P.tc_fused) ? 2 * kTcBM : kTcBM);
         P.A_wstride = P.nkb * P.A_rows;
         P.A_kstride = P.A_rows;
-        P.B_rows = P.tc_nb == kTcBN ? round_up(n > 0 ? n : 1, kTcBN) : P.tc_nb;
+        P.B_rows = P.tc_nb == kTcBN ? round_up(n > 0 ? n : 1, P.tc_fused ? kTcBN / 2 : kTcBN) : P.tc_nb;
         uint64_t abytes = (uint64_t)u * P.nkb * P.A_rows * kTileBytes;
         // Narrow n: B's words k-block major with zero words on both sides, so
         // the words B_{s0-i} .. B_{s0-i+ndiag-1} of any window are contiguous.
@@ -341,6 +353,41 @@ mwmm_status make_plan(Plan *pl, int64_t m, int64_t n, int64_t k, uint64_t p, int
         }
         uint64_t bbytes = (uint64_t)(v + 2 * P.B_wpad) * P.nkb * P.B_rows * kTileBytes;
         uint64_t sbytes = (uint64_t)P.nsums * P.nkc * P.A_rows * P.B_rows * 4;
+        if (P.tc_fused) {
+            // Segments: k-blocks per INT32 sum (ni <= w pairs of seg * 64
+            // products each: seg * 64 <= kcmax); 64 by default (measured:
+            // 16-block segments, whose words stay in L2, saved less DRAM
+            // time than their extra residue folds cost).
+            int64_t seg = o.tc_seg ? o.tc_seg : kFusedSeg;
+            if (seg * kTcKB > kcmax && !o.tc_seg) seg = kcmax / kTcKB;
+            if (seg * kTcKB > kcmax) return MWMM_ERR_ARG;
+            if (seg > P.nkb && P.nkb > 0) seg = P.nkb;
+            P.tc_seg = (int)(seg > 0 ? seg : 1);
+            P.kc = (int64_t)P.tc_seg * kTcKB;
+            P.nkc = k > 0 ? (int)ceil_div(k, P.kc) : 0;
+            // K parts: enough units (tiles x parts) that the last wave of CTA
+            // pairs is nearly full; the planner assumes 74 pairs (148 SMs).
+            const int64_t tiles = (P.A_rows / (2 * kTcBM)) * (P.B_rows / (kTcBN / 2));
+            const int64_t nkb1 = std::max<int64_t>(P.nkb, 1);
+            int64_t ks = 1;
+            if (o.ksplit != 0) {
+                if (o.ksplit < 1 || o.ksplit > 64) return MWMM_ERR_ARG;
+                ks = std::min<int64_t>(o.ksplit, nkb1);
+            } else {
+                const int64_t cap = kFusedPairs;
+                double best = -1.0;
+                for (int64_t s = 1; s <= std::min<int64_t>(8, nkb1); ++s) {
+                    const int64_t units = tiles * s;
+                    const double eff = (double)units / (double)(ceil_div(units, cap) * cap);
+                    if (eff > best + 1e-9) { best = eff; ks = s; }
+                    if (eff >= 0.9) break;  // the fewest parts that fill 90% of the last wave
+                }
+            }
+            P.kbr = ceil_div(nkb1, ks);
+            P.ksplit = (int)ceil_div(nkb1, P.kbr);  // no empty part
+            P.tc_ldr = round_up(n > 0 ? n : 1, 2);
+            sbytes = P.ksplit > 1 ? (uint64_t)P.ksplit * m * P.tc_ldr * 8 : 0;
+        }
         P.A_off = 0;
         P.B_off = align256(abytes);
         P.S_off = align256(P.B_off + bbytes);
@@ -354,6 +401,7 @@ mwmm_status make_plan(Plan *pl, int64_t m, int64_t n, int64_t k, uint64_t p, int
 int choose_tensor_form(int64_t m, int64_t n, int64_t k, uint64_t p) {
     mwmm_plan_opts z;
     std::memset(&z, 0, sizeof(z));
+    z.tc_fused = 1;  // batches and the serving loop run the diagonal sums through the workspace
     Plan a, c;
     if (make_plan(&a, m, n, k, p, 0, 0, MWMM_FORM_INT8, &z) != MWMM_OK) return MWMM_FORM_INT8;
     if (make_plan(&c, m, n, k, p, 0, 0, MWMM_FORM_CRT8, &z) != MWMM_OK) return MWMM_FORM_INT8;

@@ -407,7 +407,8 @@ mwmm_status mwmm_serve_submit(mwmm_server_t S, const mwmm_problem *prob, double 
     if (!r) return MWMM_ERR_NOMEM;
     mwmm_plan_opts o;
     std::memset(&o, 0, sizeof(o));
-    o.ksplit = 1;  // requests run as batched tiles over the whole K range
+    o.ksplit = 1;    // requests run as batched tiles over the whole K range
+    o.tc_fused = 1;  // and write diagonal sums for the batched recombination
     const int form = S->form != MWMM_FORM_AUTO ? S->form : mwmm::choose_tensor_form(prob->m, prob->n, prob->k, prob->p);
     mwmm_status st = mwmm::make_plan(&r->plan, prob->m, prob->n, prob->k, prob->p, 0, 0, form, &o);
     if (st != MWMM_OK) return st;

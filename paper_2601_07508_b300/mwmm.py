@@ -40,7 +40,7 @@ class PlanOpts(ctypes.Structure):
     _fields_ = [("lambda_", ctypes.c_int64), ("validate", ctypes.c_int32), ("tc_chunk", ctypes.c_int32),
                 ("kc", ctypes.c_int64), ("tc_pair", ctypes.c_int32),
                 ("f64_concat", ctypes.c_int32), ("ksplit", ctypes.c_int32), ("autotune", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 4)]
+                ("tc_fused", ctypes.c_int32), ("tc_seg", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
 
 
 class Timing(ctypes.Structure):
@@ -57,11 +57,11 @@ class PlanDesc(ctypes.Structure):
                 ("kc", ctypes.c_int64), ("tc_pair", ctypes.c_int32), ("nkc", ctypes.c_int32), ("nsums", ctypes.c_int32),
                 ("q", ctypes.c_double),
                 ("kb_elems", ctypes.c_int64), ("nkb", ctypes.c_int64), ("A_rows", ctypes.c_int64),
-                ("B_rows", ctypes.c_int64), ("B_wpad", ctypes.c_int32), ("pad0", ctypes.c_int32),
+                ("B_rows", ctypes.c_int64), ("B_wpad", ctypes.c_int32), ("tc_fused", ctypes.c_int32),
                 ("A_off", ctypes.c_uint64), ("B_off", ctypes.c_uint64),
                 ("S_off", ctypes.c_uint64), ("workspace_bytes", ctypes.c_uint64),
                 ("f64_concat", ctypes.c_int32), ("ksplit", ctypes.c_int32),
-                ("tuned_ms", ctypes.c_double), ("tuned_tried", ctypes.c_int32), ("pad1", ctypes.c_int32),
+                ("tuned_ms", ctypes.c_double), ("tuned_tried", ctypes.c_int32), ("tc_seg", ctypes.c_int32),
                 ("crt_m", ctypes.c_uint32 * 24)]
 
     def as_dict(self):
@@ -220,7 +220,7 @@ def _ld(t) -> int:
 # --------------------------------------------------------------------------- C-named calls
 def mwmm_plan(m: int, n: int, k: int, p: int, u: int = 0, v: int = 0, form="auto", lam: int = 0,
               validate: bool = False, tc_chunk: int = 0, kc: int = 0, tc_pair: bool = False,
-              f64_concat: int = 0, ksplit: int = 0) -> int:
+              f64_concat: int = 0, ksplit: int = 0, tc_fused: int = 0, tc_seg: int = 0) -> int:
     if isinstance(form, str):
         form = FORMS[form]
     h = _vp()
@@ -232,6 +232,8 @@ def mwmm_plan(m: int, n: int, k: int, p: int, u: int = 0, v: int = 0, form="auto
     o.tc_pair = 1 if tc_pair else 0
     o.f64_concat = f64_concat
     o.ksplit = ksplit
+    o.tc_fused = tc_fused
+    o.tc_seg = tc_seg
     _check(lib().mwmm_plan(ctypes.byref(h), m, n, k, p, u, v, form, ctypes.byref(o)), "mwmm_plan")
     return h.value
 
@@ -590,8 +592,9 @@ class Plan:
 
     def __init__(self, m: int, n: int, k: int, p: int, u: int = 0, v: int = 0, form="auto", lam: int = 0,
                  validate: bool = False, tc_chunk: int = 0, kc: int = 0, tc_pair: bool = False,
-                 f64_concat: int = 0, ksplit: int = 0):
-        self.handle = mwmm_plan(m, n, k, p, u, v, form, lam, validate, tc_chunk, kc, tc_pair, f64_concat, ksplit)
+                 f64_concat: int = 0, ksplit: int = 0, tc_fused: int = 0, tc_seg: int = 0):
+        self.handle = mwmm_plan(m, n, k, p, u, v, form, lam, validate, tc_chunk, kc, tc_pair, f64_concat, ksplit,
+                                tc_fused, tc_seg)
         self.info = mwmm_plan_info(self.handle)
         self.workspace = None
 

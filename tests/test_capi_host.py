@@ -123,18 +123,73 @@ def test_workspace_layout_sizes(M):
 
 
 @pytest.mark.parametrize("m,n,pair,want_pair,want_rows", [
-    (100, 300, False, 0, 128),   # default: one-CTA kernel, 128-row tiles
+    (100, 300, False, 0, 128),   # unfused: one-CTA kernel, 128-row tiles
     (700, 300, False, 0, 768),
     (129, 300, True, 1, 256),    # the pair kernel needs 256-row tiles
     (700, 20, True, 0, 768),     # narrow n (diagonal windows): one-CTA kernel only
     (100, 300, True, 0, 128),    # a single row tile cannot be shared by a pair
 ])
-def test_int8_plan_tile_kernel_choice(M, m, n, pair, want_pair, want_rows):
-    h = M.mwmm_plan(m, n, 1000, SWEEP[52], 0, 0, "int8", tc_pair=pair)
+def test_int8_unfused_plan_tile_kernel_choice(M, m, n, pair, want_pair, want_rows):
+    h = M.mwmm_plan(m, n, 1000, SWEEP[52], 0, 0, "int8", tc_pair=pair, tc_fused=1)
     d = M.mwmm_plan_info(h)
     M.mwmm_plan_destroy(h)
-    assert d["tc_pair"] == want_pair and d["A_rows"] == want_rows
+    assert d["tc_fused"] == 0 and d["tc_pair"] == want_pair and d["A_rows"] == want_rows
     assert d["workspace_bytes"] >= d["S_off"] + d["nsums"] * d["nkc"] * d["A_rows"] * d["B_rows"] * 4
+
+
+@pytest.mark.parametrize("m,n,opt,want", [
+    (700, 300, 0, 0), (700, 300, 1, 0),   # default and 1: diagonal sums in the workspace
+    (700, 300, 2, 1), (129, 129, 2, 1),   # 2: fused whenever n > 128
+    (100, 300, 2, 1), (1, 129, 2, 1),
+    (700, 128, 2, 0),                     # narrow n (diagonal windows): unfused
+])
+def test_int8_fused_plan_choice_and_layout(M, m, n, opt, want):
+    h = M.mwmm_plan(m, n, 1000, SWEEP[52], 0, 0, "int8", tc_fused=opt, tc_pair=True)
+    d = M.mwmm_plan_info(h)
+    M.mwmm_plan_destroy(h)
+    assert d["tc_fused"] == want
+    if not want:
+        return
+    # 256 x 128 tiles on CTA pairs; INT32 sums over one segment; no sums in the workspace
+    assert d["tc_pair"] == 0 and d["A_rows"] == -(-m // 256) * 256 and d["B_rows"] == -(-n // 128) * 128
+    assert d["tc_seg"] == 16 and d["kc"] == 1024 and d["nkc"] == 1  # k = 1000: one segment of 16 k-blocks
+    assert d["kc"] * d["u"] * 2 ** 14 < 2 ** 31
+    parts = d["ksplit"]
+    assert d["workspace_bytes"] == (d["S_off"] + (parts * m * (n + n % 2) * 8 if parts > 1 else 0) + 255) // 256 * 256
+
+
+@pytest.mark.parametrize("m,n,k,want", [
+    (4096, 4096, 4096, 1),   # 16 x 32 = 512 tiles: 6.9 waves of 74 pairs, no parts
+    (512, 512, 4096, 8),     # 8 tiles: the most parts (8) give 64 units
+    (2048, 2048, 4096, 4),   # 128 tiles: 1-3 parts fill 86% of the last wave, 4 parts (512 units) 99%
+    (2048, 2048, 64, 1),     # one k-block: one part
+])
+def test_int8_fused_plan_k_parts(M, m, n, k, want):
+    h = M.mwmm_plan(m, n, k, SWEEP[40], 0, 0, "int8", tc_fused=2)
+    d = M.mwmm_plan_info(h)
+    M.mwmm_plan_destroy(h)
+    tiles = (d["A_rows"] // 256) * (d["B_rows"] // 128)
+    units = tiles * d["ksplit"]
+    assert d["tc_fused"] == 1 and d["ksplit"] == want, (tiles, d["ksplit"])
+    # the fewest parts whose units fill >= 90% of the last wave, else the best filling
+    eff = units / (-(-units // 74) * 74)
+    assert eff >= 0.9 or d["ksplit"] == min(8, d["nkb"])
+
+
+def test_int8_fused_plan_options(M):
+    p = SWEEP[52]
+    h = M.mwmm_plan(700, 300, 5000, p, 0, 0, "int8", tc_fused=2, tc_seg=3, ksplit=5)
+    d = M.mwmm_plan_info(h)
+    M.mwmm_plan_destroy(h)
+    assert d["tc_seg"] == 3 and d["kc"] == 192 and d["nkc"] == -(-5000 // 192) and d["ksplit"] == 5
+    h = M.mwmm_plan(700, 300, 50000, p, 0, 0, "int8", tc_fused=2)
+    d = M.mwmm_plan_info(h)
+    M.mwmm_plan_destroy(h)
+    assert d["tc_seg"] == 64 and d["kc"] * d["u"] * 2 ** 14 < 2 ** 31  # default segment: 64 k-blocks
+    for kw in ({"tc_fused": 3}, {"tc_fused": -1}, {"tc_seg": -1}, {"tc_seg": 1 << 20}, {"ksplit": 65}):
+        with pytest.raises(M.MwmmError) as e:
+            M.mwmm_plan(700, 300, 5000, p, 0, 0, "int8", **dict({"tc_fused": 2}, **kw))
+        assert e.value.status == 1, kw
 
 
 @pytest.mark.parametrize("n,v,opt,want,slots", [

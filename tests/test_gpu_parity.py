@@ -334,7 +334,8 @@ def _odd_slices_patterns(pos: int, neg: int, rows: int, cols: int):
 
 
 @pytest.mark.parametrize("b", [20, 40, 52])
-def test_int8_fp32_chunk_odd_increments_near_2_24(M, oracle, b):
+@pytest.mark.parametrize("fused", [1, 2])
+def test_int8_fp32_chunk_odd_increments_near_2_24(M, oracle, b, fused):
     """Digits +-127 at 15 of every 16 k positions against B digits +-127: every
     MMA adds +-15 x 16129 (odd), and a chunk's running sum walks up to
     +-64 x 241935 = +-15,483,840 (2^23.88), with zero crossings at every
@@ -352,7 +353,8 @@ def test_int8_fp32_chunk_odd_increments_near_2_24(M, oracle, b):
             assert np.all(np.diff(part[:CHUNK // 16]) % 2 == 1) and np.all(np.abs(part) <= 2 ** 24)
             peak = max(peak, int(np.abs(part).max()))
     assert peak > 2 ** 23.85
-    C, _ = gpu_product(M, A, B, p, form="int8")
+    C, plan = gpu_product(M, A, B, p, form="int8", tc_fused=fused)
+    assert plan.info["tc_fused"] == (fused == 2)
     assert np.array_equal(C, oracle.matmul_mod(A, B, p))
 
 
@@ -378,7 +380,8 @@ def _small_addend_patterns(big_pos, big_neg, one_pos, one_neg, sign):
 
 @pytest.mark.parametrize("b", [20, 52])
 @pytest.mark.parametrize("sign", [1, -1])
-def test_int8_fp32_chunk_small_addend_below_large_sum(M, oracle, b, sign):
+@pytest.mark.parametrize("fused", [1, 2])
+def test_int8_fp32_chunk_small_addend_below_large_sum(M, oracle, b, sign, fused):
     """A chunk first sums 960 products of +-16129 (reaching +-15,483,840,
     2^23.88), then four MMAs that each add +-1 (one product 1 x 1 in 16): the
     small addends sit 24 bits below the accumulator."""
@@ -392,12 +395,14 @@ def test_int8_fp32_chunk_small_addend_below_large_sum(M, oracle, b, sign):
     last = part[CHUNK // 16 - 5:CHUNK // 16]
     assert list(np.diff(last)) == [sign] * 4 and abs(int(last[0])) == 960 * 16129
     assert np.all(np.abs(part) <= 2 ** 24) and np.abs(part).max() > 2 ** 23.85
-    C, _ = gpu_product(M, A, B, p, form="int8")
+    C, plan = gpu_product(M, A, B, p, form="int8", tc_fused=fused)
+    assert plan.info["tc_fused"] == (fused == 2)
     assert np.array_equal(C, oracle.matmul_mod(A, B, p))
 
 
 @pytest.mark.parametrize("b", [20, 40, 52])
-def test_int8_fp32_chunk_odd_increments_in_a_two_pair_diagonal(M, oracle, b):
+@pytest.mark.parametrize("fused", [1, 2])
+def test_int8_fp32_chunk_odd_increments_in_a_two_pair_diagonal(M, oracle, b, fused):
     """Digits 0 and 1 both at +-127 (entries +-(127 + 127 x 256)): diagonal 1
     concatenates the pairs (0,1) and (1,0) along K, so its chunks span both
     pairs; every slice still adds an odd multiple of 16129."""
@@ -407,7 +412,8 @@ def test_int8_fp32_chunk_odd_increments_in_a_two_pair_diagonal(M, oracle, b):
     A, B = _odd_slices_patterns(e, p - e, 130, 260)
     Ad = oracle.split_signed8(A, p, u)
     assert np.all(np.abs(Ad[:2]) <= 127) and np.all(Ad[2:] == 0) and int(Ad[1, 64, 0]) == 127
-    C, _ = gpu_product(M, A, B, p, form="int8")
+    C, plan = gpu_product(M, A, B, p, form="int8", tc_fused=fused)
+    assert plan.info["tc_fused"] == (fused == 2)
     assert np.array_equal(C, oracle.matmul_mod(A, B, p))
 
 
@@ -654,6 +660,109 @@ def test_int8_pair_and_single_cta_kernels(M, oracle, shape, b):
         assert plan.info["tc_pair"] == (1 if pair and n > 128 and m > 128 else 0)  # pairs need 256-wide tiles
         assert plan.info["A_rows"] % (256 if plan.info["tc_pair"] else 128) == 0
         assert np.array_equal(C, ref), pair
+
+
+# ------------------------------------------------------------------ fused recombination (INT8 form)
+FUSED_SHAPES = [(129, 129, 65), (257, 300, 777), (700, 520, 1100), (513, 385, 64), (300, 1000, 2000)]
+
+
+@pytest.mark.parametrize("b", [20, 23, 40, 52])
+def test_int8_fused_matches_oracle(M, oracle, b):
+    """Word products, reduction and the Horner recombination in one kernel
+    (256 x 128 tiles on CTA pairs), on ragged shapes spanning several tiles,
+    one or several segments and K parts; equals the oracle and the unfused
+    kernels bit for bit."""
+    p = SWEEP[b]
+    for seed, (m, n, k) in enumerate(FUSED_SHAPES):
+        A, B = inputs.problem(900 + 10 * b + seed, m, n, k, p)
+        ref = oracle.matmul_mod(A, B, p)
+        C, plan = gpu_product(M, A, B, p, form="int8", tc_fused=2)
+        d = plan.info
+        assert d["tc_fused"] == 1 and d["A_rows"] % 256 == 0 and d["B_rows"] % 128 == 0
+        assert np.array_equal(C, ref), (m, n, k, d["ksplit"])
+        C1, plan1 = gpu_product(M, A, B, p, form="int8", tc_seg=16, tc_fused=2)  # several segments
+        assert plan1.info["tc_fused"] == 1 and np.array_equal(C1, ref), (m, n, k)
+
+
+@pytest.mark.parametrize("seg,parts", [(1, 1), (3, 1), (16, 1), (2, 3), (5, 2), (1, 7), (64, 4)])
+@pytest.mark.parametrize("b", [20, 52])
+def test_int8_fused_segments_and_k_parts(M, oracle, b, seg, parts):
+    """Segment lengths of 1..64 k-blocks (between segments the residue is
+    divided by 2^(8 nsums) mod p) and 1..7 K parts (residue planes added mod
+    p by a second kernel), with k not a multiple of 64."""
+    p = SWEEP[b]
+    m, n, k = 300, 260, 1500
+    A, B = inputs.problem(950 + seg + 10 * parts, m, n, k, p)
+    C, plan = gpu_product(M, A, B, p, form="int8", tc_fused=2, tc_seg=seg, ksplit=parts)
+    d = plan.info
+    nkb = d["nkb"]
+    assert d["tc_fused"] == 1 and d["tc_seg"] == min(seg, nkb)
+    assert d["ksplit"] == -(-nkb // -(-nkb // parts))  # parts of ceil(nkb / parts) k-blocks, none empty
+    assert np.array_equal(C, oracle.matmul_mod(A, B, p))
+
+
+@pytest.mark.parametrize("p", [5, 7, 251, 257, 65521, 65537, (1 << 31) - 1])
+def test_int8_fused_small_and_odd_primes(M, oracle, p):
+    """Primes with one digit (nsums = 1: every Horner pass is one step, the
+    segment hop divides by 2^8) and two or four digits."""
+    m, n, k = 260, 200, 1100
+    A, B = inputs.problem(p % 1000, m, n, k, p)
+    for seg in (16, 3):
+        C, plan = gpu_product(M, A, B, p, form="int8", tc_fused=2, tc_seg=seg)
+        assert plan.info["tc_fused"] == 1
+        assert np.array_equal(C, oracle.matmul_mod(A, B, p)), seg
+
+
+@pytest.mark.parametrize("b", [26, 48])
+def test_int8_fused_narrow_m_and_leading_dimensions(M, oracle, b):
+    """tc_fused = 2 fuses m <= 128 too (a 256-row tile with padding); C with
+    an odd leading dimension and a C that starts 8 bytes past a 16-byte
+    boundary take the single-output stores; entries outside C stay untouched."""
+    p = SWEEP[b]
+    for m, n, k in ((1, 129, 70), (100, 300, 300), (129, 257, 500)):
+        A, B = inputs.problem(960 + m, m, n, k, p)
+        ref = oracle.matmul_mod(A, B, p)
+        plan = M.Plan(m, n, k, p, form="int8", tc_fused=2)
+        assert plan.info["tc_fused"] == 1
+        for ldc, off in ((n, 0), (n + 1, 0), (n + 3, 1)):
+            buf = torch.full((m * ldc + off + 8,), 7, dtype=torch.int64, device="cuda")
+            Cv = buf[off:off + m * ldc].view(m, ldc)[:, :n]
+            M.mwmm_matmul(plan.handle, dev(A), dev(B), Cv, stream=None)
+            assert plan.check() == 0
+            got = buf.cpu().numpy().view(np.uint64)
+            body = got[off:off + m * ldc].reshape(m, ldc)
+            assert np.array_equal(body[:, :n], ref), (m, n, k, ldc, off)
+            assert np.all(body[:, n:] == 7) and np.all(got[:off] == 7) and np.all(got[off + m * ldc:] == 7)
+
+
+@pytest.mark.parametrize("shape", [(1100, 300, 300), (2048, 260, 1500), (1537, 129, 64)])
+def test_int8_fused_host_row_block_pipeline(M, oracle, shape):
+    """Host entry point with the fused form: row blocks (sub-plans sharing B's
+    words, every block fused, the last one down to one row) on three streams,
+    and the one-stream order."""
+    m, n, k = shape
+    p = SWEEP[52]
+    A, B = inputs.problem(990 + m, m, n, k, p)
+    ref = oracle.matmul_mod(A, B, p)
+    plan = M.Plan(m, n, k, p, form="int8", tc_fused=2)
+    assert plan.info["tc_fused"] == 1
+    assert np.array_equal(plan.matmul_host(A, B), ref)
+    M.mwmm_plan_set_timing(plan.handle, True)  # one-stream path
+    assert np.array_equal(plan.matmul_host(A, B), ref)
+
+
+def test_int8_fused_extreme_digits_and_all_max_entries(M, oracle):
+    """Every entry p - 1 (the largest residues) and every entry (p-1)/2 (top
+    digit 128), through several segments and K parts at 40 and 52 bits."""
+    for b in (40, 52):
+        p = SWEEP[b]
+        for val in (p - 1, (p - 1) // 2, (p + 1) // 2):
+            A = np.full((260, 2100), val, dtype=np.uint64)
+            B = np.full((2100, 300), val, dtype=np.uint64)
+            for parts in (0, 3):
+                C, plan = gpu_product(M, A, B, p, form="int8", tc_fused=2, tc_seg=16, ksplit=parts)
+                assert plan.info["tc_fused"] == 1
+                assert np.all(C == (val * val * 2100) % p), (b, val, parts)
 
 
 @pytest.mark.parametrize("n", [1, 15, 16, 17, 32, 40, 64, 65, 100, 128])
