@@ -35,7 +35,7 @@ sys.path.insert(0, ROOT)
 from paper_2601_07508_b300 import inputs  # noqa: E402
 
 METRIC = "modular 2mnk GOP/s vs prime bitsize, INT8-word vs FP64 form; serve p50/p99"
-FP64_NOMINAL_GFLOPS = 1250.0  # B300 FP64 (DFMA) nominal, 148 SMs at 2032 MHz
+FP64_NOMINAL_GFLOPS = 1250.0  # B300 FP64 (DFMA) nominal, 148 SMs at 2032 MHz (only if the measurement fails)
 FALLBACK_PEAKS = {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0}
 
 
@@ -57,7 +57,10 @@ def parse_args():
     ap.add_argument("--no-shapes", action="store_true", help="skip the 50-bit shape study")
     ap.add_argument("--no-unbalanced", action="store_true", help="skip the block-Wiedemann shape")
     ap.add_argument("--variant-sweep", action="store_true",
-                    help="also time every FP64 variant at every bitsize 20..52 (Table 4 crossovers; minutes)")
+                    help="time every FP64 variant at every bitsize 20..52, square and unbalanced (Table 4; minutes)")
+    ap.add_argument("--no-variant-grid", action="store_true",
+                    help="skip the default coarse Table 4 grid (FP64 variants, 2048^3, every 2 bits from 20 to 52)")
+    ap.add_argument("--no-pipe-peaks", action="store_true", help="skip the FP64 pipe-rate measurement")
     ap.add_argument("--batched-only", action="store_true",
                     help="profiling aid: run only the batched workload and print its results as the JSON line")
     ap.add_argument("--batch-instances", type=int, default=512, help="first N instances of the batched workload")
@@ -218,6 +221,22 @@ def max_over_ranks(x: float, dist, device) -> float:
     return float(t.item())
 
 
+def sum_over_ranks(x: float, dist, device) -> float:
+    """The sum of the ranks' values (e.g. the work of every shard)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def batch_shard(count: int, rank: int, world: int):
+    """Instances of the batched workload that a rank runs: i mod world ==
+    rank (the instances are independent, so ranks share no data)."""
+    return [i for i in range(count) if i % world == rank]
+
+
 def job_rate(ops_per_rank_step: float, steps: int, world: int, seconds: float) -> float:
     """Whole-job rate in G-units per second: every rank did `steps` steps of
     `ops_per_rank_step` units within `seconds` (the slowest rank's time)."""
@@ -274,15 +293,19 @@ def workload_config(args, bits):
 
 
 # ----------------------------------------------------------------------------- batched and serving workloads
-def run_batched(dev, runs=5, count=512, forms=("int8", "auto", "fp64"), autotune=True):
+def run_batched(dev, runs=5, count=512, forms=("int8", "auto", "fp64"), autotune=True, rank=0, world=1, dist=None):
     """512 instances over the 64 largest primes below 2^50, m, n, k log-uniform
     in [128, 2048] (seed 4), INT8 and FP64 forms and the autotuner's tensor
-    form (INT8 or CRT per instance), one graph replay per run."""
+    form (INT8 or CRT per instance), one graph replay per run.  Under
+    torchrun each rank runs its shard of the instances (batch_shard) as one
+    batch; the time of a run is the slowest rank's."""
     import torch
     from paper_2601_07508_b300 import mwmm
-    spec = inputs.batch_instances()[:count]
+    full = inputs.batch_instances()[:count]
+    mine = batch_shard(len(full), rank, world)
+    spec = [full[i] for i in mine]
     items = []
-    for i, (m, n, k, p) in enumerate(spec):
+    for i, (m, n, k, p) in zip(mine, spec):
         A, B = inputs.problem(4000 + i, m, n, k, p)
         items.append((torch.from_numpy(A.view(np.int64)).to(dev), torch.from_numpy(B.view(np.int64)).to(dev),
                       torch.empty((m, n), dtype=torch.int64, device=dev), p))
@@ -305,11 +328,14 @@ def run_batched(dev, runs=5, count=512, forms=("int8", "auto", "fp64"), autotune
         e1.record()
         torch.cuda.synchronize()
         assert bt.check() == 0
-        ms = e0.elapsed_time(e1) / nrun
+        ms = max_over_ranks(e0.elapsed_time(e1) / nrun, dist, dev)
         info = bt.info
         d0 = bt.problem_info(0)
-        out[form] = {"ms_per_run": ms, "gops": info["flops_2mnk"] / ms / 1e6,
-                     "word_tflops": info["word_flops"] / ms / 1e9, "launches_per_run": info["launches"],
+        flops_all = sum(2.0 * m * n * k for (m, n, k, _) in full)  # every rank's shard
+        out[form] = {"ms_per_run": ms, "gops": flops_all / ms / 1e6,
+                     "word_tflops": sum_over_ranks(info["word_flops"], dist, dev) / ms / 1e9,
+                     "launches_per_run": info["launches"],
+                     "instances_this_rank": len(spec),
                      "tc_items": info["items"], "ctas": info["ctas"],
                      "autotuned": {"groups": info["tuned_groups"], "probe_ms": info["tuned_ms"],
                                    "uv": [d0["u"], d0["v"]], "kc": d0["kc"], "f64_concat": d0["f64_concat"]}}
@@ -321,7 +347,8 @@ def run_batched(dev, runs=5, count=512, forms=("int8", "auto", "fp64"), autotune
         else:
             out[form + "_equals_" + ref_form] = all(torch.equal(c, r) for (_, _, c, _), r in zip(fitems, ref))
         del bt
-    out["flops_2mnk_per_run"] = sum(2.0 * m * n * k for (m, n, k, _) in spec)
+    out["flops_2mnk_per_run"] = sum(2.0 * m * n * k for (m, n, k, _) in full)
+    out["ranks"] = world
     return out
 
 
@@ -487,17 +514,17 @@ def run_unbalanced(dev, reps=5):
     return out
 
 
-def run_variant_sweep(dev, size=2048):
-    """Every FP64 variant the block-size bound allows at every bitsize 20..52,
-    on a size^3 square product and on the unbalanced shape (concatenated
-    variant, A reused): the best variant per bitsize gives the crossover
-    ranges of Table 4 measured on this GPU."""
+def run_variant_sweep(dev, size=2048, bits=range(20, 53), unbalanced=True):
+    """Every FP64 variant the block-size bound allows at every bitsize in
+    `bits`, on a size^3 square product and (unbalanced=True) on the
+    unbalanced shape (concatenated variant, A reused): the best variant per
+    bitsize gives the crossover ranges of Table 4 measured on this GPU."""
     import torch
     from paper_2601_07508_b300 import mwmm
     variants = [(1, 1), (1, 2), (1, 3), (1, 4), (2, 2), (2, 3)]
-    out = {"square": {"m": size, "n": size, "k": size}, "unbalanced_concat": {}}
+    out = {"square": {"m": size, "n": size, "k": size, "bits": list(bits)}}
     sq = {}
-    for b in range(20, 53):
+    for b in bits:
         p = inputs.largest_prime_below_pow2(b)
         A, B = inputs.problem(b, size, size, size, p)
         dA = torch.from_numpy(A.view(np.int64)).to(dev)
@@ -518,9 +545,20 @@ def run_variant_sweep(dev, size=2048):
             del pl, C
         sq[str(b)] = row
     out["square"]["gops"] = sq
+
+    def ranges(tab):
+        best = {b: max(r, key=r.get) for b, r in tab.items() if r}
+        res = {}
+        for b in sorted(best, key=int):
+            res.setdefault(best[b], []).append(int(b))
+        return {v: [min(bs), max(bs)] for v, bs in res.items()}
+    out["square"]["best_ranges"] = ranges(sq)
+    if not unbalanced:
+        return out
+    out["unbalanced_concat"] = {}
     m, n, k = UNBALANCED
     ub = {}
-    for b in range(20, 53):
+    for b in bits:
         p, dA, dB = _unbalanced_operands(dev, b)
         row = {}
         for uv in variants:
@@ -534,14 +572,6 @@ def run_variant_sweep(dev, size=2048):
         ub[str(b)] = row
         del dA, dB
     out["unbalanced_concat"]["gops"] = ub
-
-    def ranges(tab):
-        best = {b: max(r, key=r.get) for b, r in tab.items() if r}
-        res = {}
-        for b in sorted(best, key=int):
-            res.setdefault(best[b], []).append(int(b))
-        return {v: [min(bs), max(bs)] for v, bs in res.items()}
-    out["square"]["best_ranges"] = ranges(sq)
     out["unbalanced_concat"]["best_ranges"] = ranges(ub)
     return out
 
@@ -666,6 +696,13 @@ def main():
         cpu_baseline.pop("seconds", None)
 
     mwmm.lib()
+    fp64_peak, fp64_peak_kind = FP64_NOMINAL_GFLOPS, "nominal"
+    if not args.no_pipe_peaks:
+        try:
+            fp64_peak = max(mwmm.mwmm_measure_fp64_rate(1 << 16) for _ in range(3))
+            fp64_peak_kind = "measured (DFMA loop, mwmm_measure_fp64_rate, best of 3)"
+        except mwmm.MwmmError:
+            pass
     probs = []
     for b in bits:
         p = inputs.largest_prime_below_pow2(b)
@@ -771,7 +808,7 @@ def main():
             e.update({"fp64_uv": list(uv), "fp64_lambda": d["lambda"], "fp64_ms": t["total_ms"],
                       "fp64_gops": 2.0 * n ** 3 / t["total_ms"] / 1e6,
                       "fp64_pipe_gflops": fl / t["gemm_ms"] / 1e6,
-                      "fp64_pipe_frac": fl / t["gemm_ms"] / 1e6 / FP64_NOMINAL_GFLOPS,
+                      "fp64_pipe_frac": fl / t["gemm_ms"] / 1e6 / fp64_peak,
                       "int8_over_fp64": t["total_ms"] / e["int8_ms"],
                       "fp64_equals_int8": same})
             del pl, Cf
@@ -849,24 +886,31 @@ def main():
         same = all(torch.equal(hC[i], dC[i].cpu()) for i in range(len(plans)))
         e2e["matches_device_result"] = same
 
-    batched = run_batched(dev) if (rank == 0 and not args.no_batched) else None
+    batched = run_batched(dev, rank=rank, world=world, dist=dist) if not args.no_batched else None
     shapes = run_shapes(dev) if (rank == 0 and not args.no_shapes) else None
     unbalanced = run_unbalanced(dev) if (rank == 0 and not args.no_unbalanced) else None
-    sweep = run_variant_sweep(dev) if (rank == 0 and args.variant_sweep) else None
+    if rank == 0 and args.variant_sweep:
+        sweep = run_variant_sweep(dev)
+    elif rank == 0 and not args.no_variant_grid:
+        sweep = run_variant_sweep(dev, size=2048, bits=range(20, 53, 2), unbalanced=False)
+    else:
+        sweep = None
     serve = run_serve(dev, args.serve_requests, args.serve_pool) if (rank == 0 and not args.no_serve) else None
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "GOP/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
-                "dtype_detail": "INT8 digits (exact in bf16) x bf16 -> FP32 tensor memory (exact, <= 2^24) -> "
-                                "INT32 sums -> 64-bit integer recombination mod p",
+                "scaling": "weak", "vs_baseline": None, "dtype": "int8-in-bf16",
+                "dtype_detail": "exact integer arithmetic throughout: 8-bit digits carried exactly in bf16 x bf16 -> "
+                                "FP32 tensor memory (exact, every partial sum <= 2^24) -> INT32 sums -> 64-bit "
+                                "integer recombination mod p; results bit-exact mod p",
                 "data": "synthetic (seeded, entries uniform in [0,p))",
                 "config": workload_config(args, bits),
                 "roofline": roofline, "cpu_baseline": cpu_baseline, "e2e": e2e,
                 "gpu_launches": launches * world, "clocks": clocks, "per_bitsize": per_bits,
                 "batched_multi_prime": batched, "shapes_50bit": shapes, "unbalanced_block_wiedemann": unbalanced,
                 "variant_sweep": sweep,
+                "fp64_pipe_peak_gflops": fp64_peak, "fp64_pipe_peak_kind": fp64_peak_kind,
                 "product_counts_fp64_words": product_counts(n),
                 "serve": serve}
         print(json.dumps(line))

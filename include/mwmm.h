@@ -479,6 +479,15 @@ mwmm_status mwmm_mulmod(const double *dx, const double *dy, int64_t count, uint6
  * frees a 4-byte flag; the device stays usable afterwards. */
 mwmm_status mwmm_selftest_wait_timeout(int64_t cycles, void *stream);
 
+/* Pipe-rate diagnostic (no counterpart in the paper): the FP64 fused
+ * multiply-add rate of the current device, the roofline denominator of the
+ * FP64 form.  Runs a kernel of eight independent DFMA chains per thread
+ * (4 x 256 threads per SM) for `iters` (1 .. 2^24) iterations after a short
+ * warm-up, times it with CUDA events on `stream`, synchronises, and writes
+ * 2 x 8 x iters x threads / time in GFLOP/s to *gflops.  Allocates nothing.
+ * Errors: MWMM_ERR_ARG, MWMM_ERR_CUDA. */
+mwmm_status mwmm_measure_fp64_rate(int64_t iters, double *gflops, void *stream);
+
 /* ---- per-phase timing (CUDA events on the call's stream) ----
  * When timing is on, every mwmm_matmul / mwmm_matmul_host call records events
  * around its phases: the split of A, the split of B (Alg. 4 or INT8 digits),

@@ -128,6 +128,7 @@ def lib() -> ctypes.CDLL:
     L.mwmm_split.argtypes = [_vp, ctypes.c_int, _vp, _i64, _vp, _vp]
     L.mwmm_fmod.argtypes = [_vp, _i64, _u64, _vp, _vp]
     L.mwmm_selftest_wait_timeout.argtypes = [_i64, _vp]
+    L.mwmm_measure_fp64_rate.argtypes = [_i64, ctypes.POINTER(ctypes.c_double), _vp]
     L.mwmm_plan_autotuned.argtypes = [ctypes.POINTER(_vp), _i64, _i64, _i64, _u64, ctypes.c_int, _vp, _i64, _vp,
                                       _i64, _vp]
     L.mwmm_autotune_cache_entries.restype = ctypes.c_int64
@@ -375,6 +376,14 @@ def mwmm_mulmod(x, y, p: int, out, stream=None):
     f = (torch.float64,)
     _check(lib().mwmm_mulmod(_dev_ptr(x, f), _dev_ptr(y, f), x.numel(), p, _dev_ptr(out, f), _stream_ptr(stream)),
            "mwmm_mulmod")
+
+
+def mwmm_measure_fp64_rate(iters: int = 1 << 16, stream=None) -> float:
+    """The device's FP64 fused multiply-add rate in GFLOP/s (a DFMA loop
+    timed with CUDA events)."""
+    g = ctypes.c_double(0)
+    _check(lib().mwmm_measure_fp64_rate(iters, ctypes.byref(g), _stream_ptr(stream)), "mwmm_measure_fp64_rate")
+    return g.value
 
 
 def mwmm_selftest_wait_timeout(cycles: int, stream=None) -> int:

@@ -1,8 +1,9 @@
 """The multi-rank harness on CPU: two gloo ranks exercise the pieces
 bench.py uses under torchrun -- per-rank problem seeds (independent problems,
-no data-path collective), the barrier, the maximum of the ranks' elapsed
-times and the whole-job rate -- and the reference arm's rank rule (rank 0
-alone prints; other ranks exit 0 without work)."""
+no data-path collective), the batched workload's shards (every instance on
+exactly one rank), the barrier, the maximum of the ranks' elapsed times, the
+sum of their work and the whole-job rate -- and the reference arm's rank
+rule (rank 0 alone prints; other ranks exit 0 without work)."""
 import json
 import os
 import socket
@@ -31,11 +32,17 @@ def _worker(rank: int, world: int, port: int, out_dir: str):
     p = inputs.largest_prime_below_pow2(40)
     A, B = inputs.problem(40 + bench.rank_seed(rank), 8, 8, 8, p)
     dist.barrier()
+    # the batched workload: each rank's shard of the 512 instances
+    shard = bench.batch_shard(512, rank, world)
+    everyone = [None] * world
+    dist.all_gather_object(everyone, shard)
+    work = bench.sum_over_ranks(float(len(shard)), dist, "cpu")
     elapsed = 1.5 + rank  # this rank's "time"
     slowest = bench.max_over_ranks(elapsed, dist, "cpu")
     rate = bench.job_rate(2.0 * 8 ** 3, 3, world, slowest)
     with open(os.path.join(out_dir, "rank%d.json" % rank), "w") as f:
-        json.dump({"slowest": slowest, "rate": rate, "a00": int(A[0, 0]), "sum": int(A.sum() % p)}, f)
+        json.dump({"slowest": slowest, "rate": rate, "a00": int(A[0, 0]), "sum": int(A.sum() % p),
+                   "shards": everyone, "work": work}, f)
     dist.barrier()
     dist.destroy_process_group()
 
@@ -49,6 +56,10 @@ def test_two_gloo_ranks_share_timing_but_not_data(tmp_path):
     assert r0["slowest"] == r1["slowest"] == 2.5  # the job's time is the slowest rank's
     assert r0["rate"] == r1["rate"] == pytest.approx(2.0 * 8 ** 3 * 3 * 2 / 2.5 / 1e9)
     assert (r0["a00"], r0["sum"]) != (r1["a00"], r1["sum"])  # independent problems per rank
+    # the batched workload's shards cover every instance exactly once
+    s0, s1 = r0["shards"]
+    assert r1["shards"] == r0["shards"] and sorted(s0 + s1) == list(range(512)) and not set(s0) & set(s1)
+    assert r0["work"] == r1["work"] == 512.0
 
 
 def test_reference_arm_runs_on_rank_zero_only():

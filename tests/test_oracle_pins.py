@@ -268,6 +268,26 @@ def test_lambda_reproduces_table1_bitsize_limits(oracle):
         assert ok == list(range(4, limit + 1))
 
 
+def test_theory_variant_ranges_follow_from_the_block_sizes(oracle):
+    """Sec. 3.3's predicted best variants (the bullet list after Table 1):
+    for each bitsize, the variants of fewest word products u v among those
+    with a block size lambda >= 1 for the largest prime below 2^b, out of
+    (1,1), (1,2), (1,3), (1,4), (2,2) -- (2,3) is not in that list."""
+    rows = load_rows("variant_ranges.txt")
+    want = {}
+    for row in rows:
+        lo, hi, u, v = (int(x) for x in row[:4])
+        for b in range(lo, hi + 1):
+            want.setdefault(b, set()).add((u, v))
+    assert sorted(want) == list(range(1, 53))
+    variants = [(1, 1), (1, 2), (1, 3), (1, 4), (2, 2)]
+    for b in range(4, 53):
+        p = inputs.prev_prime(1 << b)
+        ok = [uv for uv in variants if oracle.lam(p, *uv) >= 1]
+        fewest = min(u * v for u, v in ok)
+        assert {uv for uv in ok if uv[0] * uv[1] == fewest} == want[b], b
+
+
 def test_lambda_single_word_corollary(oracle):
     """Sec. 2.2 corollary: the (1,1) block size is >= 1 exactly when
     p (p - 1) <= 2^t, and it equals floor((2^t - p + 1) / (p-1)^2)."""
