@@ -18,8 +18,15 @@
 // Schedule.  Work item = (128-row tile, 256-col tile, diagonal s, K-range kc);
 // its k-loop runs over the virtual k-blocks (pair (i, s-i), 64-wide k-block):
 // the pairs of one diagonal are concatenated along K (the K-dimension analogue
-// of Alg. 6's concatenation).  Items go round-robin over a persistent grid of
-// one CTA per SM, heaviest diagonals first.
+// of Alg. 6's concatenation).  A persistent grid of one CTA per SM claims
+// items in order from a counter in the workspace (the producer warp claims
+// and hands the index to the MMA and epilogue warps through a small ring in
+// shared memory), so uneven item costs balance themselves.  Items go window
+// by window, heaviest first (the kernel ends on its lightest items), every
+// tile of a window in a raster of kGroupN column tiles; inside an item the
+// k-block is the outer loop and the diagonal's pairs the inner one, so a
+// wave of items walks through k in step and shares each k-slab of words in
+// L2.
 //
 // Warp roles (320 threads):
 //   warp 0      one lane issues bulk TMA copies of the pre-swizzled word tiles
@@ -57,6 +64,7 @@ constexpr int kStgStride = 20;
 constexpr uint32_t kStageBytes = EPI_WARPS * 32 * kStgStride * 4;  // 20 KB
 constexpr int kSmemBytes = STAGES * (kTileA + kTileB) + kStageBytes + 1024;
 constexpr int64_t kGroupN = 8;  // column tiles per raster group
+constexpr int kRing = 4;  // claimed item indices in flight (producer -> MMA and epilogue warps)
 
 struct TcParams {
     // computed items (one product)
@@ -66,6 +74,7 @@ struct TcParams {
     int u, v, nsums, nkc, mt_count, nt_count, nb, b_wpad;
     int64_t m, n;  // valid rows and columns (sums outside are not stored)
     int64_t b_wstride, b_kstride;  // bytes between consecutive B words / k-blocks
+    uint32_t *sched;  // item counter of the computed items, zero at launch
     // diagonal windows, heaviest first: window g covers diagonals
     // g_s0[g] .. g_s0[g] + g_nd[g] - 1 and A words g_i0[g] .. + g_ni[g] - 1;
     // its sums start at S plane g_plane[g] (the diagonal s0; the modulus i of
@@ -99,6 +108,8 @@ __device__ __forceinline__ int item_n(int ndiag, int nb, int cv) {
 __device__ __forceinline__ Item computed_item(const TcParams &P, int64_t idx) {
     Item it;
     const int64_t mtc = P.mt_count;
+    // item idx -> (tile, K-range kc, window grp_w): windows heaviest first,
+    // every tile of a window before the next window
     const int64_t ntiles = mtc * P.nt_count;
     const int64_t tile = idx % ntiles;
     const int64_t rest = idx / ntiles;
@@ -114,8 +125,9 @@ __device__ __forceinline__ Item computed_item(const TcParams &P, int64_t idx) {
     it.b_kstride = P.b_kstride;
     it.b_wpad = P.b_wpad;
     // Raster in groups of kGroupN column tiles, rows inside a group first: the
-    // ~148 tiles running at once cover about 18 row tiles x 8 column tiles, a
-    // squarer region than whole rows, so fewer word tiles are fetched twice.
+    // ~148 tiles running at once cover about 18 row tiles x 8 column tiles,
+    // the aspect that minimises the words they read (a B column tile is twice
+    // the bytes of an A row tile), so fewer word tiles are fetched twice.
     const int64_t gsz = mtc * kGroupN;
     const int64_t grp = tile / gsz, t = tile % gsz;
     const int64_t width = P.nt_count - grp * kGroupN < kGroupN ? P.nt_count - grp * kGroupN : kGroupN;
@@ -168,24 +180,60 @@ __device__ __forceinline__ Item table_item(const TcParams &P, int64_t pos) {
 }
 
 template <bool kTable>
-struct ItemRange {
-    int64_t begin, end, step;
-    __device__ ItemRange(const TcParams &P) {
-        if (kTable) {
-            begin = P.cta_off[blockIdx.x];
-            end = P.cta_off[blockIdx.x + 1];
-            step = 1;
-        } else {
-            begin = blockIdx.x;
-            end = P.nitems;
-            step = gridDim.x;
-        }
-    }
+__device__ __forceinline__ Item get_item(const TcParams &P, int64_t idx) {
+    return kTable ? table_item(P, idx) : computed_item(P, idx);
+}
+
+// The item sequence of one CTA, seen identically by its three roles: table
+// items run the CTA's range of the table; computed items are claimed one at
+// a time from the counter by the producer lane, which publishes each index
+// in a ring of kRing slots (full: 1 arrival, the producer; empty: 1 + 8
+// arrivals, the MMA lane and every epilogue warp).  -1 ends the sequence.
+struct ItemRing {
+    int64_t *idx;
+    uint64_t *full, *empty;
 };
 
 template <bool kTable>
-__device__ __forceinline__ Item get_item(const TcParams &P, int64_t idx) {
-    return kTable ? table_item(P, idx) : computed_item(P, idx);
+__device__ __forceinline__ int64_t produce_item(const TcParams &P, const ItemRing &R, int64_t j, bool &alive) {
+    if (kTable) {
+        const int64_t idx = P.cta_off[blockIdx.x] + j;
+        return idx < P.cta_off[blockIdx.x + 1] ? idx : -1;
+    }
+    const int slot = (int)(j % kRing);
+    if (!mbar_wait(&R.empty[slot], (uint32_t)(((j / kRing) & 1) ^ 1), P.err)) {
+        alive = false;
+        return -1;
+    }
+    int64_t idx = (int64_t)atomicAdd(P.sched, 1u);
+    if (idx >= P.nitems) idx = -1;
+    R.idx[slot] = idx;
+    mbar_arrive(&R.full[slot]);  // release: the index is visible to the waiters of this phase
+    return idx;
+}
+
+// kWarp: the whole warp waits and reads; one lane releases the slot.
+template <bool kTable, bool kWarp>
+__device__ __forceinline__ int64_t consume_item(const TcParams &P, const ItemRing &R, int64_t j, bool &alive) {
+    if (kTable) {
+        const int64_t idx = P.cta_off[blockIdx.x] + j;
+        return idx < P.cta_off[blockIdx.x + 1] ? idx : -1;
+    }
+    const int slot = (int)(j % kRing);
+    bool ok = mbar_wait(&R.full[slot], (uint32_t)((j / kRing) & 1), P.err);
+    if (kWarp) ok = __all_sync(0xffffffffu, ok);
+    if (!ok) {
+        alive = false;
+        return -1;
+    }
+    const int64_t idx = R.idx[slot];
+    if (kWarp) {
+        __syncwarp();
+        if ((threadIdx.x & 31) == 0) mbar_arrive(&R.empty[slot]);
+    } else {
+        mbar_arrive(&R.empty[slot]);
+    }
+    return idx;
 }
 
 // Instruction descriptor of a one-CTA MMA: M = 128, N = n (a multiple of 16,
@@ -239,6 +287,8 @@ template <bool kTable>
 __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_constant__ TcParams P) {
     extern __shared__ uint8_t smem_raw[];
     __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES], tfull[2], tempty[2], done;
+    __shared__ __align__(8) uint64_t rfull[kRing], rempty[kRing];
+    __shared__ int64_t ring_idx[kRing];
     __shared__ uint32_t tmem_base_sh;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -247,6 +297,7 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_consta
     uint8_t *sA = smem_raw + pad;
     uint8_t *sB = sA + STAGES * kTileA;
     int32_t *sStage = reinterpret_cast<int32_t *>(sB + STAGES * kTileB);
+    const ItemRing ring{ring_idx, rfull, rempty};
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
@@ -256,6 +307,10 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_consta
         for (int b = 0; b < 2; ++b) {
             mbar_init(&tfull[b], 1);
             mbar_init(&tempty[b], EPI_WARPS);
+        }
+        for (int r = 0; r < kRing; ++r) {
+            mbar_init(&rfull[r], 1);
+            mbar_init(&rempty[r], 1 + EPI_WARPS);
         }
         mbar_init(&done, 1);
         fence_mbar_init();
@@ -276,23 +331,27 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_consta
         if (lane == 0) {  // ---------------- TMA producer
             uint64_t g = 0;
             bool alive = true;
-            const ItemRange<kTable> R(P);
-            for (int64_t idx = R.begin; alive && idx < R.end; idx += R.step) {
+            for (int64_t j = 0; alive; ++j) {
+                const int64_t idx = produce_item<kTable>(P, ring, j, alive);
+                if (idx < 0) break;
                 const Item it = get_item<kTable>(P, idx);
                 // One thread issues every copy, so the per-stage work is kept to a
-                // few adds: nested (word, k-block) loops and running addresses.
+                // few adds: nested (k-block, word) loops and running addresses.
                 // The window's B words B_{s0-i} .. B_{s0-i+ndiag-1} are contiguous
                 // (k-block-major layout padded with zero words), so each stage is
-                // two copies whatever the window.
+                // two copies whatever the window.  The k-block is the outer loop
+                // (every pair of the diagonal at k-block kb, then kb + 1): the
+                // ~148 items of one wave then walk through k together and share
+                // each k-slab of the words in L2 while it is needed.
                 const uint32_t bbytes = (uint32_t)it.nn * kTileBytes;
                 const uint32_t stage_bytes = kTileA + bbytes;
-                const int64_t a_step = it.A_rows * kTileBytes;
-                for (int ii = 0; alive && ii < it.ni; ++ii) {
-                    const int i = it.i0 + ii;
-                    const uint8_t *a = it.Aw + (((int64_t)i * it.nkb + it.kb0) * it.A_rows + it.mt * BM) * kTileBytes;
-                    const uint8_t *b = it.Bw + (int64_t)(it.s0 - i + it.b_wpad) * it.b_wstride +
-                                       it.kb0 * it.b_kstride + it.nt * it.nb * kTileBytes;
-                    for (int64_t kb = 0; kb < it.nkbc; ++kb, ++g, a += a_step, b += it.b_kstride) {
+                const int64_t a_wstep = it.nkb * it.A_rows * kTileBytes;  // next A word, same k-block
+                for (int64_t kb = 0; alive && kb < it.nkbc; ++kb) {
+                    const uint8_t *a =
+                        it.Aw + (((int64_t)it.i0 * it.nkb + it.kb0 + kb) * it.A_rows + it.mt * BM) * kTileBytes;
+                    const uint8_t *b = it.Bw + (int64_t)(it.s0 - it.i0 + it.b_wpad) * it.b_wstride +
+                                       (it.kb0 + kb) * it.b_kstride + it.nt * it.nb * kTileBytes;
+                    for (int ii = 0; ii < it.ni; ++ii, ++g, a += a_wstep, b -= it.b_wstride) {
                         const int slot = (int)(g % STAGES);
                         if (!mbar_wait(&empty[slot], (uint32_t)(((g / STAGES) & 1) ^ 1), P.err)) {
                             alive = false;
@@ -315,8 +374,9 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_consta
             uint64_t g = 0, c = 0;
             bool alive = true;
             const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
-            const ItemRange<kTable> R(P);
-            for (int64_t idx = R.begin; alive && idx < R.end; idx += R.step) {
+            for (int64_t j = 0; alive; ++j) {
+                const int64_t idx = consume_item<kTable, false>(P, ring, j, alive);
+                if (idx < 0) break;
                 const Item it = get_item<kTable>(P, idx);
                 const int64_t nvb = (int64_t)it.ni * it.nkbc;
                 const uint32_t idesc = idesc_n(it.nn);
@@ -355,8 +415,9 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_consta
         const uint32_t tlane = tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(half * 128);
         uint64_t c = 0;
         bool alive = true;
-        const ItemRange<kTable> R(P);
-        for (int64_t idx = R.begin; alive && idx < R.end; idx += R.step) {
+        for (int64_t j = 0; alive; ++j) {
+            const int64_t idx = consume_item<kTable, true>(P, ring, j, alive);
+            if (idx < 0) break;
             const Item it = get_item<kTable>(P, idx);
             const int64_t nvb = (int64_t)it.ni * it.nkbc;
             const int64_t nch = (nvb + P.chunk_blocks - 1) / P.chunk_blocks;
@@ -692,6 +753,7 @@ int encode_rows_map(CUtensorMap *map, const void *base, uint64_t rows, uint32_t 
 
 int launch_gemm_tc(const Plan &pl, const void *Aw, const void *Bw, int32_t *S, int *err, void *stream) {
     TcParams P;
+    std::memset(&P, 0, sizeof(P));
     P.Aw = static_cast<const uint8_t *>(Aw);
     P.Bw = static_cast<const uint8_t *>(Bw);
     P.S = S;
@@ -775,8 +837,12 @@ int launch_gemm_tc(const Plan &pl, const void *Aw, const void *Bw, int32_t *S, i
     cudaError_t e = set_smem_attr(reinterpret_cast<const void *>(gemm_tc_kernel<false>), kSmemBytes);
     if (e != cudaSuccess) return (int)e;
     const int64_t sms = sm_count();
+    P.sched = reinterpret_cast<uint32_t *>(reinterpret_cast<uint8_t *>(S) + (pl.sched_off - pl.S_off));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    e = cudaMemsetAsync(P.sched, 0, sizeof(uint32_t), s);
+    if (e != cudaSuccess) return (int)e;
     const unsigned grid = (unsigned)(P.nitems < sms ? P.nitems : sms);
-    gemm_tc_kernel<false><<<grid, THREADS, kSmemBytes, static_cast<cudaStream_t>(stream)>>>(P);
+    gemm_tc_kernel<false><<<grid, THREADS, kSmemBytes, s>>>(P);
     return (int)cudaGetLastError();
 }
 

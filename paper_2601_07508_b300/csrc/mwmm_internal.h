@@ -99,6 +99,7 @@ struct Plan {
     // A_rows, A_kstride = u A_rows) only for the FP64 form with A concatenated
     int64_t A_wstride = 0, A_kstride = 0;
     uint64_t A_off = 0, B_off = 0, S_off = 0, ws_bytes = 0;
+    uint64_t sched_off = 0;  // tensor forms (unfused): the word-product kernel's item counter (256 bytes)
     // owned device resources (lazily created)
     int device = -1;
     void *own_ws = nullptr;

@@ -392,6 +392,10 @@ mwmm_status make_plan(Plan *pl, int64_t m, int64_t n, int64_t k, uint64_t p, int
         P.B_off = align256(abytes);
         P.S_off = align256(P.B_off + bbytes);
         P.ws_bytes = align256(P.S_off + sbytes);
+        if (!P.tc_fused) {  // the one-CTA kernel claims its items from a counter after the sums
+            P.sched_off = P.ws_bytes;
+            P.ws_bytes += 256;
+        }
     }
     if (m == 0 || n == 0) P.ws_bytes = 0;
     *pl = P;
