@@ -21,7 +21,6 @@
 #include <cstring>
 #include <functional>
 #include <new>
-#include <queue>
 #include <vector>
 
 #include "mwmm_internal.h"
@@ -60,47 +59,33 @@ struct mwmm_batch_s {
 
 namespace mwmm {
 
-// Longest-processing-time-first: items sorted by decreasing modelled cost
-// (stable, so equal-cost items of one problem and diagonal stay together and
-// run side by side), each to the CTA with the least work so far.  Measured on
-// the 512-instance batch this beats list scheduling in problem order, whose
-// tail is set by whichever problems come last.  Returns items grouped per CTA
-// and offsets.  Costs are small integers, so the stable sort is a bucket sort
-// and the items are placed by counting: the serving loop builds these tables
-// for every batch while it also retires finished ones, so they must be cheap.
-static void lpt_schedule(std::vector<mwmm::TcItem> &items, int ctas, std::vector<int64_t> &off) {
-    const size_t N = items.size();
-    std::vector<int64_t> cost(N);
-    int64_t cmax = 0;
-    for (size_t i = 0; i < N; ++i) {
-        cost[i] = items[i].ni * items[i].nkbc + 2;  // +2: drain and store
-        cmax = std::max(cmax, cost[i]);
+// Claim order of the batch's items: the word-product kernel's CTAs take the
+// items one by one from a counter in this order (list scheduling on the
+// actual finish times).  Problems go largest first (by modelled cost), so the
+// batch ends on the smallest; inside a problem the windows go heaviest first,
+// every tile of a window in row order, so the ~148 items running at once
+// mostly share one problem's word tiles in L2.  T.cta_off holds {0, N, 0}:
+// the item range and the counter (zero; the launch clears it again).
+static void claim_order(std::vector<mwmm::TcItem> &items, const std::vector<size_t> &prob_start,
+                        std::vector<int64_t> &off) {
+    const size_t P = prob_start.size();
+    std::vector<int64_t> cost(P, 0);
+    for (size_t p = 0; p < P; ++p) {
+        const size_t e = p + 1 < P ? prob_start[p + 1] : items.size();
+        for (size_t i = prob_start[p]; i < e; ++i) cost[p] += items[i].ni * items[i].nkbc + 2;  // +2: drain, store
     }
-    // stable order by decreasing cost
-    std::vector<int64_t> start((size_t)cmax + 2, 0);
-    for (size_t i = 0; i < N; ++i) ++start[(size_t)(cmax - cost[i]) + 1];
-    for (size_t c = 1; c < start.size(); ++c) start[c] += start[c - 1];
-    std::vector<size_t> order(N);
-    for (size_t i = 0; i < N; ++i) order[(size_t)start[(size_t)(cmax - cost[i])]++] = i;
-    // each item to the least loaded CTA
-    typedef std::pair<int64_t, int> Load;  // (work, cta)
-    std::priority_queue<Load, std::vector<Load>, std::greater<Load>> heap;
-    for (int c = 0; c < ctas; ++c) heap.push(Load(0, c));
-    std::vector<int> cta_of(N);
-    off.assign(ctas + 1, 0);
-    for (size_t i : order) {
-        Load l = heap.top();
-        heap.pop();
-        cta_of[i] = l.second;
-        ++off[l.second + 1];
-        heap.push(Load(l.first + cost[i], l.second));
+    std::vector<size_t> order(P);
+    for (size_t p = 0; p < P; ++p) order[p] = p;
+    std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) { return cost[a] > cost[b]; });
+    std::vector<mwmm::TcItem> out;
+    out.reserve(items.size());
+    for (size_t p : order) {
+        const size_t e = p + 1 < P ? prob_start[p + 1] : items.size();
+        out.insert(out.end(), items.begin() + (long)prob_start[p], items.begin() + (long)e);
     }
-    for (int c = 0; c < ctas; ++c) off[c + 1] += off[c];
-    // place the items CTA by CTA, each CTA's in schedule order
-    std::vector<int64_t> pos(off.begin(), off.end() - 1);
-    std::vector<mwmm::TcItem> out(N);
-    for (size_t i : order) out[(size_t)pos[cta_of[i]]++] = items[i];
     items.swap(out);
+    off.assign(3, 0);
+    off[1] = (int64_t)items.size();
 }
 
 // Work items of one INT8- or CRT-form problem whose words start at Aw / Bw
@@ -114,7 +99,17 @@ static void tc_items(const Plan &pl, const uint8_t *Aw, const uint8_t *Bw, int32
     const int64_t plane = (int64_t)pl.nkc * pl.A_rows * pl.B_rows;
     const bool crt = pl.form == MWMM_FORM_CRT8;
     const int nwin = crt ? pl.crt_s : (pl.nsums + pl.tc_ndiag - 1) / pl.tc_ndiag;
+    // windows by decreasing number of word pairs (stable)
+    std::vector<int> worder(nwin);
+    std::vector<int> wni(nwin);
     for (int g = 0; g < nwin; ++g) {
+        const int s0 = crt ? 2 * g : g * pl.tc_ndiag;
+        const int nd = crt ? 1 : std::min(pl.tc_ndiag, pl.nsums - s0);
+        wni[g] = crt ? 1 : std::min(s0 + nd - 1, pl.u - 1) - std::max(0, s0 - (pl.v - 1)) + 1;
+        worder[g] = g;
+    }
+    std::stable_sort(worder.begin(), worder.end(), [&](int a, int b) { return wni[a] > wni[b]; });
+    for (int g : worder) {
         const int s0 = crt ? 2 * g : g * pl.tc_ndiag;
         const int nd = crt ? 1 : std::min(pl.tc_ndiag, pl.nsums - s0);
         const int ilo = crt ? g : std::max(0, s0 - (pl.v - 1)), ihi = crt ? g : std::min(s0 + nd - 1, pl.u - 1);
@@ -157,10 +152,12 @@ void build_batch_tables(const Plan *plans, const mwmm_problem *probs, uint8_t *c
     T = BatchTables();
     T.split_jobs.resize(split_job_bytes() * 2 * (size_t)count);
     int nsj = 0;
+    std::vector<size_t> prob_start;  // first item of each tensor-form problem
     for (int i = 0; i < count; ++i) {
         const Plan &pl = plans[i];
         const mwmm_problem &q = probs[i];
         if (pl.m == 0 || pl.n == 0 || pl.k == 0) continue;
+        if (pl.form != MWMM_FORM_FP64) prob_start.push_back(T.items.size());
         uint8_t *w = ws_base[i];
         split_job(pl, 0, q.A, q.lda, w + pl.A_off, &T.split_jobs[split_job_bytes() * nsj], nsj, T.split_blocks);
         ++nsj;
@@ -187,7 +184,7 @@ void build_batch_tables(const Plan *plans, const mwmm_problem *probs, uint8_t *c
     T.split_jobs.resize(split_job_bytes() * nsj);
     if (!T.items.empty()) {
         T.ctas = (int)std::min<int64_t>((int64_t)T.items.size(), tc_sm_count());
-        lpt_schedule(T.items, T.ctas, T.cta_off);
+        claim_order(T.items, prob_start, T.cta_off);
     }
     T.nsplit = (int)(T.split_blocks.size() / 4);
     T.nrec = (int)(T.rec_jobs.size() / 4);
@@ -261,7 +258,8 @@ int launch_batch_tables(const BatchTables &T, const uint8_t *dtables, const uint
     if (fp64) return launch_gemm_fp64_batched(dtables + off[6], reinterpret_cast<const int *>(dtables + off[7]),
                                               T.nf64, stream);
     e = launch_gemm_tc_table(reinterpret_cast<const TcItem *>(dtables + off[2]),
-                             reinterpret_cast<const int64_t *>(dtables + off[3]), T.ctas, chunk_blocks, err, stream);
+                             const_cast<int64_t *>(reinterpret_cast<const int64_t *>(dtables + off[3])),
+                             (int64_t)T.items.size(), T.ctas, chunk_blocks, err, stream);
     if (e) return e;
     e = launch_recombine_batched(dtables + off[4], reinterpret_cast<const int *>(dtables + off[5]), T.nrec, stream);
     if (e) return e;
@@ -296,7 +294,8 @@ mwmm_status record(mwmm_batch_s *b, cudaStream_t s) {
         e = mwmm::launch_gemm_fp64_batched(b->d_f64, b->d_f64_jobs, b->nf64, s);
         return cuda_st((cudaError_t)e);
     }
-    e = mwmm::launch_gemm_tc_table(b->d_items, b->d_cta_off, b->ntc_ctas, b->chunk_blocks, b->err, s);
+    e = mwmm::launch_gemm_tc_table(b->d_items, const_cast<int64_t *>(b->d_cta_off), b->nitems, b->ntc_ctas,
+                                   b->chunk_blocks, b->err, s);
     if (e) return cuda_st((cudaError_t)e);
     e = mwmm::launch_recombine_batched(b->d_rec, b->d_rec_jobs, b->nrec, s);
     if (e) return cuda_st((cudaError_t)e);

@@ -80,7 +80,7 @@ struct TcParams {
     // its sums start at S plane g_plane[g] (the diagonal s0; the modulus i of
     // the CRT form, whose window is the single pair (i, i) with s0 = 2 i)
     int g_s0[kMaxWindows], g_nd[kMaxWindows], g_i0[kMaxWindows], g_ni[kMaxWindows], g_plane[kMaxWindows];
-    // table items (batch): CTA c runs items[cta_off[c] .. cta_off[c + 1])
+    // table items (batch): items[0 .. nitems), claimed in table order
     const TcItem *items;
     const int64_t *cta_off;
     int chunk_blocks;
@@ -184,22 +184,17 @@ __device__ __forceinline__ Item get_item(const TcParams &P, int64_t idx) {
     return kTable ? table_item(P, idx) : computed_item(P, idx);
 }
 
-// The item sequence of one CTA, seen identically by its three roles: table
-// items run the CTA's range of the table; computed items are claimed one at
-// a time from the counter by the producer lane, which publishes each index
-// in a ring of kRing slots (full: 1 arrival, the producer; empty: 1 + 8
-// arrivals, the MMA lane and every epilogue warp).  -1 ends the sequence.
+// The item sequence of one CTA, seen identically by its three roles: items
+// (computed, or rows of a batch's table) are claimed one at a time from the
+// counter by the producer lane, which publishes each index in a ring of
+// kRing slots (full: 1 arrival, the producer; empty: 1 + 8 arrivals, the MMA
+// lane and every epilogue warp).  -1 ends the sequence.
 struct ItemRing {
     int64_t *idx;
     uint64_t *full, *empty;
 };
 
-template <bool kTable>
 __device__ __forceinline__ int64_t produce_item(const TcParams &P, const ItemRing &R, int64_t j, bool &alive) {
-    if (kTable) {
-        const int64_t idx = P.cta_off[blockIdx.x] + j;
-        return idx < P.cta_off[blockIdx.x + 1] ? idx : -1;
-    }
     const int slot = (int)(j % kRing);
     if (!mbar_wait(&R.empty[slot], (uint32_t)(((j / kRing) & 1) ^ 1), P.err)) {
         alive = false;
@@ -213,12 +208,8 @@ __device__ __forceinline__ int64_t produce_item(const TcParams &P, const ItemRin
 }
 
 // kWarp: the whole warp waits and reads; one lane releases the slot.
-template <bool kTable, bool kWarp>
+template <bool kWarp>
 __device__ __forceinline__ int64_t consume_item(const TcParams &P, const ItemRing &R, int64_t j, bool &alive) {
-    if (kTable) {
-        const int64_t idx = P.cta_off[blockIdx.x] + j;
-        return idx < P.cta_off[blockIdx.x + 1] ? idx : -1;
-    }
     const int slot = (int)(j % kRing);
     bool ok = mbar_wait(&R.full[slot], (uint32_t)((j / kRing) & 1), P.err);
     if (kWarp) ok = __all_sync(0xffffffffu, ok);
@@ -332,7 +323,7 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_consta
             uint64_t g = 0;
             bool alive = true;
             for (int64_t j = 0; alive; ++j) {
-                const int64_t idx = produce_item<kTable>(P, ring, j, alive);
+                const int64_t idx = produce_item(P, ring, j, alive);
                 if (idx < 0) break;
                 const Item it = get_item<kTable>(P, idx);
                 // One thread issues every copy, so the per-stage work is kept to a
@@ -375,7 +366,7 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_consta
             bool alive = true;
             const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
             for (int64_t j = 0; alive; ++j) {
-                const int64_t idx = consume_item<kTable, false>(P, ring, j, alive);
+                const int64_t idx = consume_item<false>(P, ring, j, alive);
                 if (idx < 0) break;
                 const Item it = get_item<kTable>(P, idx);
                 const int64_t nvb = (int64_t)it.ni * it.nkbc;
@@ -416,7 +407,7 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_consta
         uint64_t c = 0;
         bool alive = true;
         for (int64_t j = 0; alive; ++j) {
-            const int64_t idx = consume_item<kTable, true>(P, ring, j, alive);
+            const int64_t idx = consume_item<true>(P, ring, j, alive);
             if (idx < 0) break;
             const Item it = get_item<kTable>(P, idx);
             const int64_t nvb = (int64_t)it.ni * it.nkbc;
@@ -858,18 +849,23 @@ int prepare_tc_attributes() {
     return (int)e;
 }
 
-int launch_gemm_tc_table(const TcItem *items, const int64_t *cta_off, int ctas, int chunk_blocks, int *err,
+int launch_gemm_tc_table(const TcItem *items, int64_t *cta_off, int64_t nitems, int ctas, int chunk_blocks, int *err,
                          void *stream) {
-    if (ctas <= 0) return 0;
+    if (ctas <= 0 || nitems <= 0) return 0;
     TcParams P;
     std::memset(&P, 0, sizeof(P));
     P.items = items;
     P.cta_off = cta_off;
+    P.nitems = nitems;
+    P.sched = reinterpret_cast<uint32_t *>(cta_off + 2);
     P.chunk_blocks = chunk_blocks;
     P.err = err;
     cudaError_t e = set_smem_attr(reinterpret_cast<const void *>(gemm_tc_kernel<true>), kSmemBytes);
     if (e != cudaSuccess) return (int)e;
-    gemm_tc_kernel<true><<<ctas, THREADS, kSmemBytes, static_cast<cudaStream_t>(stream)>>>(P);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    e = cudaMemsetAsync(P.sched, 0, sizeof(uint32_t), s);
+    if (e != cudaSuccess) return (int)e;
+    gemm_tc_kernel<true><<<ctas, THREADS, kSmemBytes, s>>>(P);
     return (int)cudaGetLastError();
 }
 

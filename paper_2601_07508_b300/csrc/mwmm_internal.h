@@ -150,7 +150,9 @@ void fp64_job(const Plan &pl, const void *Aw, const void *Bw, uint64_t *C, int64
 int launch_gemm_fp64_batched(const void *probs, const int *jobs, int njobs, void *stream);
 int prepare_kernel_attributes();  // dynamic shared-memory limits, once per device (call before capturing)
 int tc_sm_count();
-int launch_gemm_tc_table(const TcItem *items, const int64_t *cta_off, int ctas, int chunk_blocks, int *err,
+// Items claimed in table order from the counter at cta_off[2] (cleared by
+// the launch): cta_off = {0, nitems, counter}.
+int launch_gemm_tc_table(const TcItem *items, int64_t *cta_off, int64_t nitems, int ctas, int chunk_blocks, int *err,
                          void *stream);
 int launch_fmod(const double *x, int64_t count, uint64_t p, double *out, void *stream);
 int launch_mulmod(const double *x, const double *y, int64_t count, uint64_t p, double *out, void *stream);
