@@ -61,6 +61,8 @@ def parse_args():
     ap.add_argument("--no-variant-grid", action="store_true",
                     help="skip the default coarse Table 4 grid (FP64 variants, 2048^3, every 2 bits from 20 to 52)")
     ap.add_argument("--no-pipe-peaks", action="store_true", help="skip the FP64 pipe-rate measurement")
+    ap.add_argument("--tc-fused", action="store_true",
+                    help="profiling aid: the sweep's INT8 products with the recombination fused (tc_fused = 2)")
     ap.add_argument("--batched-only", action="store_true",
                     help="profiling aid: run only the batched workload and print its results as the JSON line")
     ap.add_argument("--batch-instances", type=int, default=512, help="first N instances of the batched workload")
@@ -714,7 +716,7 @@ def main():
     dA = [to_dev(A) for (_, _, A, _) in probs]
     dB = [to_dev(B) for (_, _, _, B) in probs]
     dC = [torch.empty((n, n), dtype=torch.int64, device=dev) for _ in probs]
-    plans = [mwmm.Plan(n, n, n, p, form="int8") for (_, p, _, _) in probs]
+    plans = [mwmm.Plan(n, n, n, p, form="int8", tc_fused=2 if args.tc_fused else 0) for (_, p, _, _) in probs]
     for pl in plans:
         pl.alloc_workspace(dev)
         mwmm.mwmm_plan_set_timing(pl.handle, True)

@@ -481,10 +481,11 @@ mwmm_status mwmm_selftest_wait_timeout(int64_t cycles, void *stream);
 
 /* Pipe-rate diagnostic (no counterpart in the paper): the FP64 fused
  * multiply-add rate of the current device, the roofline denominator of the
- * FP64 form.  Runs a kernel of eight independent DFMA chains per thread
- * (4 x 256 threads per SM) for `iters` (1 .. 2^24) iterations after a short
+ * FP64 form.  Runs a kernel of sixteen independent DFMA chains per thread
+ * (the FP64 word-product kernel's 4 x 4 accumulator block; one block of
+ * 1024 threads per SM) for `iters` (1 .. 2^24) iterations after a short
  * warm-up, times it with CUDA events on `stream`, synchronises, and writes
- * 2 x 8 x iters x threads / time in GFLOP/s to *gflops.  Allocates nothing.
+ * 2 x 16 x iters x threads / time in GFLOP/s to *gflops.  Allocates nothing.
  * Errors: MWMM_ERR_ARG, MWMM_ERR_CUDA. */
 mwmm_status mwmm_measure_fp64_rate(int64_t iters, double *gflops, void *stream);
 
