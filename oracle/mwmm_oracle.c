@@ -17,6 +17,7 @@
  *   oracle_split_signed8  INT8 words: balanced base-2^8 digits of the
  *                         signed representative of M mod p  (Sec. 6, second
  *                         perspective: narrower words for low-precision units)
+ *   oracle_split_signed_bits  the same with base-2^bits digits (8 or 9 bits)
  *   oracle_diag_sums      S_s = sum_{i+j=s} A_i B_j, exact integers (Sec. 3.2)
  *   oracle_recombine_pow  sum_s r^s S_s mod p                (Sec. 1, product of decompositions)
  *   oracle_mod_vec        x mod p            (the value Alg. 1 must return)
@@ -172,21 +173,32 @@ int oracle_split_alpha(const uint64_t *M, int64_t count, uint64_t alpha, int u, 
  * the last digit is what remains, allowed in [-128, 128] (magnitude <= 2^7,
  * like every other digit).  Returns 2 if that last digit leaves [-128, 128]
  * (u too small for p).  words is [u][count]. */
-int oracle_split_signed8(const uint64_t *M, int64_t count, uint64_t p, int u, int32_t *words) {
-    if (u < 1) return 1;
+/* Balanced base-R digits (R = 2^bits, h = R / 2) of the signed
+ * representative s of each entry (s = M or M - p, |s| <= (p-1)/2): the lower
+ * u - 1 digits d = ((s + h) mod R) - h in [-h, h - 1], each followed by
+ * s <- (s - d) / R (exact), and the top digit the remainder, which must lie
+ * in [-h, h].  Then s = sum_i R^i d_i.  Returns 2 if u digits do not
+ * suffice. */
+int oracle_split_signed_bits(const uint64_t *M, int64_t count, uint64_t p, int u, int bits, int32_t *words) {
+    if (u < 1 || bits < 2 || bits > 16) return 1;
+    const int64_t R = (int64_t)1 << bits, h = R / 2;
     for (int64_t e = 0; e < count; ++e) {
         int64_t s = (M[e] <= (p - 1) / 2) ? (int64_t)M[e] : (int64_t)M[e] - (int64_t)p;
         for (int i = 0; i < u - 1; ++i) {
-            int64_t r = (s + 128) % 256;
-            if (r < 0) r += 256;
-            const int64_t d = r - 128;
+            int64_t r = (s + h) % R;
+            if (r < 0) r += R;
+            const int64_t d = r - h;
             words[(int64_t)i * count + e] = (int32_t)d;
-            s = (s - d) / 256;
+            s = (s - d) / R;
         }
-        if (s < -128 || s > 128) return 2;
+        if (s < -h || s > h) return 2;
         words[(int64_t)(u - 1) * count + e] = (int32_t)s;
     }
     return 0;
+}
+
+int oracle_split_signed8(const uint64_t *M, int64_t count, uint64_t p, int u, int32_t *words) {
+    return oracle_split_signed_bits(M, count, p, u, 8, words);
 }
 
 /* S_s[r][c] = sum_{i+j=s} sum_l A_i[r][l] B_j[l][c] (exact, int64) for the

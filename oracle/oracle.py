@@ -35,6 +35,7 @@ def lib() -> ctypes.CDLL:
         L.oracle_freivalds.restype = ctypes.c_int64
         L.oracle_split_alpha.argtypes = [_u64p, _i64, _u64, ctypes.c_int, _u64p]
         L.oracle_split_signed8.argtypes = [_u64p, _i64, _u64, ctypes.c_int, _i32p]
+        L.oracle_split_signed_bits.argtypes = [_u64p, _i64, _u64, ctypes.c_int, ctypes.c_int, _i32p]
         L.oracle_diag_sums.argtypes = [_i64, _i64, _i64, ctypes.c_int, ctypes.c_int, _i32p, _i32p, _i64p, ctypes.c_int]
         L.oracle_recombine_pow.argtypes = [_i64p, ctypes.c_int, _i64, _u64, _u64, _u64p]
         L.oracle_mod_vec.argtypes = [_f64p, _i64, _u64, _u64p]
@@ -138,6 +139,17 @@ def split_signed8(M: np.ndarray, p: int, u: int) -> np.ndarray:
     return W
 
 
+def split_signed(M: np.ndarray, p: int, u: int, bits: int) -> np.ndarray:
+    """Balanced base-2^bits digits of the signed representative: u - 1 in
+    [-2^(bits-1), 2^(bits-1) - 1], the top one in [-2^(bits-1), 2^(bits-1)]."""
+    M = _c(M, np.uint64)
+    W = np.zeros((u,) + M.shape, dtype=np.int32)
+    rc = lib().oracle_split_signed_bits(_p(M, _u64p), M.size, p, u, bits, _p(W, _i32p))
+    if rc:
+        raise ValueError("oracle_split_signed_bits: u=%d too small for p=%d (bits %d)" % (u, p, bits))
+    return W
+
+
 def diag_sums(Aw: np.ndarray, Bw: np.ndarray, nthreads: int = 0) -> np.ndarray:
     """S_s = sum_{i+j=s} A_i B_j (exact int64); Aw [u][m][k], Bw [v][k][n]."""
     Aw = _c(Aw, np.int32)
@@ -184,6 +196,18 @@ def ceil_root(p: int, u: int) -> int:
 def lam(p: int, u: int, v: int, t: int = 53) -> int:
     """Largest block size allowed by Prop. 3.3 ((1,1): Sec. 2.2); 0 if none."""
     return int(lib().oracle_lambda(p, u, v, t))
+
+
+def digit_words(p: int, bits: int) -> int:
+    """Fewest balanced base-2^bits digits (u - 1 in [-h, h - 1], the top one
+    in [-h, h], h = 2^(bits-1)) that represent every signed representative
+    in [-(p-1)/2, (p-1)/2]: with R = 2^bits and B = R^(u-1) the largest such
+    value is h B + (h - 1) (B - 1) / (R - 1)."""
+    R, h = 1 << bits, 1 << (bits - 1)
+    u = 1
+    while h * R ** (u - 1) + (h - 1) * (R ** (u - 1) - 1) // (R - 1) < (p - 1) // 2:
+        u += 1
+    return u
 
 
 def int8_words(p: int) -> int:

@@ -212,6 +212,53 @@ def test_split_signed8_top_digit_128(oracle):
     assert W[1].min() == -128 and W[1].max() == 128 and W[0].min() == -128 and W[0].max() == 127
 
 
+@pytest.mark.parametrize("p", EDGE_PRIMES + list(SWEEP_PRIMES.values()))
+def test_split_signed_9bit_digits(oracle, p):
+    """Balanced base-2^9 digits (the fp16-carried digits of the tensor form):
+    lower digits in [-256, 255], the top one in [-256, 256], exact
+    reconstruction of the signed representative, and the fewest digits."""
+    u = oracle.digit_words(p, 9)
+    M = np.concatenate([inputs.uniform_mod(12, 7, 400, p),
+                        np.array([0, 1, p - 1, (p - 1) // 2, (p + 1) // 2], dtype=np.uint64)])
+    W = oracle.split_signed(M, p, u, 9)
+    assert W.min() >= -256 and W[:u - 1].max(initial=0) <= 255 and W[u - 1].max() <= 256
+    for e, x in enumerate(M):
+        x = int(x)
+        s = x if x <= (p - 1) // 2 else x - p
+        assert sum(512 ** i * int(W[i, e]) for i in range(u)) == s
+    if u > 1:
+        with pytest.raises(ValueError):
+            oracle.split_signed(np.array([(p - 1) // 2], dtype=np.uint64), p, u - 1, 9)
+    # the 8-bit path through the same routine is the INT8 split
+    W8 = oracle.split_signed(M, p, oracle.int8_words(p), 8)
+    assert np.array_equal(W8, oracle.split_signed8(M, p, oracle.int8_words(p)))
+
+
+def test_9bit_digit_counts():
+    """Digits per side for the sweep primes: u 9-bit digits reach about
+    2^(9u-1), so a b-bit prime needs ceil(b / 9) of them (or one fewer when
+    (p-1)/2 still fits); they save a digit over 8-bit ones at 26 and 52 bits."""
+    from oracle import oracle as O
+    got = {b: O.digit_words(SWEEP_PRIMES[b], 9) for b in inputs.SWEEP_BITS}
+    assert got == {20: 3, 23: 3, 26: 3, 32: 4, 40: 5, 48: 6, 52: 6}
+    for b, u in got.items():
+        assert u == -(-b // 9)
+    # brute force over every signed value of a 2-digit split: the covered
+    # range is [-256 * 513, 256 * 512 + 255]; one more on either side needs a
+    # third digit
+    top = 256 * 512 + 255
+    s = np.arange(-top - 2, top + 2, dtype=np.int64)
+    pp = 2 * (top + 2) + 1
+    M = np.where(s >= 0, s, s + pp).astype(np.uint64)
+    for bad in (0, len(s) - 1):
+        with pytest.raises(ValueError):
+            O.split_signed(M[bad:bad + 1], pp, 2, 9)
+    ok = (s >= -top - 1) & (s <= top)
+    W = O.split_signed(M[ok], pp, 2, 9)
+    assert np.array_equal(W[0] + 512 * W[1], s[ok])
+    assert W[1].min() == -256 and W[1].max() == 256 and W[0].min() == -256 and W[0].max() == 255
+
+
 def test_diag_sums_and_recombine_reproduce_product(oracle):
     """sum_s 256^s S_s mod p with S_s = sum_{i+j=s} A_i B_j equals A B mod p
     (the product of the two decompositions, Sec. 1 / Sec. 3.2)."""
@@ -233,6 +280,10 @@ def test_diag_sums_and_recombine_reproduce_product(oracle):
             assert np.array_equal(S[s].astype(object), ref)
         C = oracle.recombine_pow(S, 256, p)
         assert np.array_equal(C, oracle.matmul_mod(A, B, p))
+        # the same with 9-bit digits and radix 512
+        u9 = oracle.digit_words(p, 9)
+        S9 = oracle.diag_sums(oracle.split_signed(A, p, u9, 9), oracle.split_signed(B, p, u9, 9))
+        assert np.array_equal(oracle.recombine_pow(S9, 512, p), oracle.matmul_mod(A, B, p))
 
 
 def test_recombine_pow_bruteforce(oracle):
