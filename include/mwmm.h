@@ -133,7 +133,13 @@ typedef struct {
     int32_t tc_seg;     /* INT8 fused form: k-blocks of 64 per segment, the
                          k-range of one INT32 sum (0: 64, or fewer when the
                          INT32 bound requires) */
-    int32_t reserved[2];
+    int32_t tc_digit_bits; /* INT8 form, digit width: 8 = digits in [-128, 128]
+                         carried in bf16 (FP32 chunks of <= 1024 products);
+                         9 = digits in [-256, 256] carried in fp16 (chunks of
+                         <= 256 products, INT32 sums of <= 32767 products);
+                         0 = 9 when that needs fewer digits (u, v = 0 only),
+                         else 8 */
+    int32_t reserved[1];
 } mwmm_plan_opts;
 
 /* What a plan decided (mwmm_plan_info). */
@@ -187,6 +193,8 @@ typedef struct {
     int32_t tc_seg;         /* INT8 fused: k-blocks per segment */
     uint32_t crt_m[24];     /* CRT form: the moduli m_0 > m_1 > ... (u of them); word i of A and of B
                                holds the signed residues modulo m_i, sum plane i their product */
+    int32_t tc_digit_bits;  /* INT8: 8 (bf16 words) or 9 (fp16 words); alpha = beta = 2^tc_digit_bits */
+    int32_t pad2;
 } mwmm_plan_desc;
 
 /* Plan a product of an m x k by a k x n matrix mod p.

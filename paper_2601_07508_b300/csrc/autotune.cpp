@@ -81,14 +81,14 @@ std::string make_key(int form, int64_t m, int64_t n, int64_t k, uint64_t p, bool
 // One JSON object per line; the fields are written and read in this order.
 const char *kLineFmt =
     "{\"key\": \"%[^\"]\", \"form\": %d, \"u\": %d, \"v\": %d, \"tc_chunk\": %d, \"kc\": %lld, \"tc_pair\": %d, "
-    "\"f64_concat\": %d, \"ksplit\": %d, \"ms\": %lf, \"tried\": %d}";
+    "\"tc_digit_bits\": %d, \"f64_concat\": %d, \"ksplit\": %d, \"ms\": %lf, \"tried\": %d}";
 
 bool parse_line(const char *line, std::string *key, Entry *e) {
     char k[160];
     long long kc = 0;
     int n = std::sscanf(line, kLineFmt, k, &e->form, &e->u, &e->v, &e->o.tc_chunk, &kc, &e->o.tc_pair,
-                        &e->o.f64_concat, &e->o.ksplit, &e->ms, &e->tried);
-    if (n != 11) return false;
+                        &e->o.tc_digit_bits, &e->o.f64_concat, &e->o.ksplit, &e->ms, &e->tried);
+    if (n != 12) return false;
     e->o.kc = kc;
     *key = k;
     return true;
@@ -119,10 +119,10 @@ int save_file(const char *path) {
         const Entry &e = kv.second;
         std::fprintf(f,
                      "{\"key\": \"%s\", \"form\": %d, \"u\": %d, \"v\": %d, \"tc_chunk\": %d, \"kc\": %lld, "
-                     "\"tc_pair\": %d, \"f64_concat\": %d, \"ksplit\": %d, \"ms\": %.6f, "
+                     "\"tc_pair\": %d, \"tc_digit_bits\": %d, \"f64_concat\": %d, \"ksplit\": %d, \"ms\": %.6f, "
                      "\"tried\": %d}\n",
                      kv.first.c_str(), e.form, e.u, e.v, e.o.tc_chunk, (long long)e.o.kc, e.o.tc_pair,
-                     e.o.f64_concat, e.o.ksplit, e.ms, e.tried);
+                     e.o.tc_digit_bits, e.o.f64_concat, e.o.ksplit, e.ms, e.tried);
     }
     return std::fclose(f) == 0 ? 0 : -1;
 }
@@ -192,6 +192,7 @@ void candidates(int form_req, int64_t m, int64_t n, int64_t k, uint64_t p, bool 
                     mwmm_plan_opts o = z;
                     o.kc = kc;
                     o.tc_pair = pair;
+                    o.tc_digit_bits = base.digit_bits;  // the words base.u, base.v are of this width
                     const size_t before = out.size();
                     add(out, MWMM_FORM_INT8, base.u, base.v, o, m, n, k, p);
                     if (out.size() > before && out.back().pl.ws_bytes > 2 * base.ws_bytes + (64u << 20))

@@ -142,6 +142,7 @@ static void tc_items(const Plan &pl, const uint8_t *Aw, const uint8_t *Bw, int32
                     it.cv = (int32_t)std::min<int64_t>(pl.tc_nb, pl.n - nt * pl.tc_nb);
                     it.b_wstride = pl.B_wstride * mwmm::kTileBytes;
                     it.b_kstride = pl.B_kstride * mwmm::kTileBytes;
+                    it.f16 = pl.form == MWMM_FORM_INT8 && pl.digit_bits == 9;
                     items.push_back(it);
                 }
     }

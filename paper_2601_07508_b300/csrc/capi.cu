@@ -185,6 +185,7 @@ mwmm_status make_sub_plan(const Plan &pl, int64_t rows, Plan *out) {
         o.tc_pair = pl.tc_pair;
         o.tc_fused = pl.tc_fused ? 2 : 1;  // every row block in the parent's layout of B's words
         o.tc_seg = pl.tc_seg;
+        o.tc_digit_bits = pl.digit_bits;
     }
     const bool crt = pl.form == MWMM_FORM_CRT8;  // its words follow from p and k
     mwmm_status st = mwmm::make_plan(out, rows, pl.n, pl.k, pl.p, crt ? 0 : pl.u, crt ? 0 : pl.v, pl.form, &o);
@@ -393,6 +394,7 @@ void describe_plan(const Plan &P, mwmm_plan_desc *d) {
     d->tuned_ms = P.tuned_ms;
     d->tuned_tried = P.tuned_tried;
     for (int i = 0; i < P.crt_s && i < 24; ++i) d->crt_m[i] = P.crt_m[i];
+    d->tc_digit_bits = P.form == MWMM_FORM_CRT8 || P.form == MWMM_FORM_FP64 ? 0 : P.digit_bits;
 }
 
 }  // namespace mwmm

@@ -72,6 +72,7 @@ struct TcParams {
     int32_t *S;
     int64_t nkb, A_rows, B_rows, kcb, nitems;
     int u, v, nsums, nkc, mt_count, nt_count, nb, b_wpad;
+    int f16;       // words in fp16 (9-bit digits), else bf16
     int64_t m, n;  // valid rows and columns (sums outside are not stored)
     int64_t b_wstride, b_kstride;  // bytes between consecutive B words / k-blocks
     uint32_t *sched;  // item counter of the computed items, zero at launch
@@ -95,6 +96,7 @@ struct Item {
     int s0, ndiag, nb, i0, ni, v, b_wpad;
     int rv, cv;  // rows of the tile inside m (from its first row), columns of each diagonal block inside n
     int nn;      // MMA N: ndiag nb
+    int f16;     // words in fp16, else bf16
 };
 
 // MMA N of an item.  Fitting N of a last column tile to its valid columns
@@ -121,6 +123,7 @@ __device__ __forceinline__ Item computed_item(const TcParams &P, int64_t idx) {
     it.ni = P.g_ni[grp_w];
     it.nb = P.nb;
     it.v = P.v;
+    it.f16 = P.f16;
     it.b_wstride = P.b_wstride;
     it.b_kstride = P.b_kstride;
     it.b_wpad = P.b_wpad;
@@ -176,6 +179,7 @@ __device__ __forceinline__ Item table_item(const TcParams &P, int64_t pos) {
     it.rv = d.rv;
     it.cv = d.cv;
     it.nn = item_n(it.ndiag, it.nb, it.cv);
+    it.f16 = d.f16;
     return it;
 }
 
@@ -228,8 +232,8 @@ __device__ __forceinline__ int64_t consume_item(const TcParams &P, const ItemRin
 }
 
 // Instruction descriptor of a one-CTA MMA: M = 128, N = n (a multiple of 16,
-// at most 256).
-__device__ __forceinline__ uint32_t idesc_n(int n) { return idesc_bf16(BM, n); }
+// at most 256), bf16 or fp16 words.
+__device__ __forceinline__ uint32_t idesc_n(int n, int f16) { return f16 ? idesc_f16(BM, n) : idesc_bf16(BM, n); }
 
 __device__ __forceinline__ void mma_bf16(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
                                          uint32_t acc) {
@@ -370,7 +374,7 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_consta
                 if (idx < 0) break;
                 const Item it = get_item<kTable>(P, idx);
                 const int64_t nvb = (int64_t)it.ni * it.nkbc;
-                const uint32_t idesc = idesc_n(it.nn);
+                const uint32_t idesc = idesc_n(it.nn, it.f16);
                 for (int64_t t0 = 0; alive && t0 < nvb; t0 += P.chunk_blocks, ++c) {
                     const int buf = (int)(c & 1);
                     if (!mbar_wait(&tempty[buf], (uint32_t)(((c >> 1) & 1) ^ 1), P.err)) {
@@ -588,6 +592,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS, 1)
             uint64_t g = 0, c = 0;
             bool alive = true;
             const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
+            const uint32_t idesc_pair = P.f16 ? idesc_f16(BM2, BN) : kIdescPair;
             for (int64_t idx = cid; alive && idx < P.nitems; idx += ncl) {
                 const Item it = pair_item(P, idx);
                 const int64_t nvb = (int64_t)it.ni * it.nkbc;
@@ -611,7 +616,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS, 1)
                         const uint64_t ad = sdesc(a0 + slot * kTileA2), bd = sdesc(b0 + slot * kTileB2);
 #pragma unroll
                         for (int kk = 0; kk < 4; ++kk)
-                            mma_bf16_pair(dt, ad + 2 * kk, bd + 2 * kk, kIdescPair, (t > t0 || kk > 0) ? 1u : 0u);
+                            mma_bf16_pair(dt, ad + 2 * kk, bd + 2 * kk, idesc_pair, (t > t0 || kk > 0) ? 1u : 0u);
                         mma_commit_pair(&empty[slot], 3);
                     }
                     mma_commit_pair(&tfull[buf], 3);
@@ -756,6 +761,7 @@ int launch_gemm_tc(const Plan &pl, const void *Aw, const void *Bw, int32_t *S, i
     P.v = pl.v;
     P.nsums = pl.nsums;
     P.nkc = pl.nkc;
+    P.f16 = pl.form == MWMM_FORM_INT8 && pl.digit_bits == 9;
     P.chunk_blocks = (int)(pl.tc_chunk / kTcKB);
     P.mt_count = (int)(pl.A_rows / BM);
     P.nt_count = pl.tc_nb == BN ? (int)(pl.B_rows / BN) : 1;

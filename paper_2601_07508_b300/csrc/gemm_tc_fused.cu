@@ -8,31 +8,33 @@
 // Recombination (Horner's rule, exact integer arithmetic).  A work unit owns
 // a 256 x 128 output tile (a CTA pair, 128 rows each) over a range of k and
 // visits the diagonals from the top one down:
-//     r <- (256 r + S_s) mod p,      s = u + v - 2, ..., 0,
-// with r < p held in tensor memory beside the accumulators (two 32-bit
-// columns per output), so after s = 0, r = sum_s 256^s S_s mod p.  One step
-// is y = 256 r + S_s + off, off = p ceil(2^31 / p) (so y >= 0 and y < 2^61),
-// reduced by a Barrett quotient (at most two corrections).
+//     r <- (R r + S_s) mod p,      s = u + v - 2, ..., 0,
+// (R = 2^8 or 2^9, the digit radix) with r < p held in tensor memory beside
+// the accumulators (two 32-bit columns per output), so after s = 0,
+// r = sum_s R^s S_s mod p.  One step is y = R r + S_s + off,
+// off = p ceil(2^31 / p) (so y >= 0 and y < 2^62), reduced by a Barrett
+// quotient (at most two corrections).
 //
 // Segments.  The k-range of a unit is cut into segments of `seg` k-blocks and
 // the unit runs segment by segment, every diagonal in each, so that the word
 // tiles the ~74 concurrent units read at one time -- the A and B words of
 // one segment -- stay in L2 while every diagonal that needs them runs.  Each
 // segment's sums are folded in by the same rule; between segments the
-// residue is divided by 2^(8 nsums) mod p (Montgomery steps of <= 11 bits:
+// residue is divided by R^nsums mod p (Montgomery steps of <= 11 bits:
 // r <- (r + t p) / 2^b with t = r (-p^-1) mod 2^b, exact and < p), because
-// the next segment's Horner pass multiplies it by 256^nsums again.  The
+// the next segment's Horner pass multiplies it by R^nsums again.  The
 // INT32 sums S_s of one segment hold ni x seg x 64 products of magnitude
-// <= 2^14 (ni <= min(u, v) pairs), within the same INT32 bound as the
-// unfused form's K-range.
+// <= 2^14 (2^16 for 9-bit digits; ni <= min(u, v) pairs), within the same
+// INT32 bound as the unfused form's K-range.
 //
 // K parts.  When the output has too few tiles to fill the GPU, K is split
 // into parts computed by separate units; each writes its residue to a plane
 // of partial results and a last kernel adds them mod p.
 //
 // Exactness of the word products is that of the unfused kernel (gemm_tc.cu):
-// digits of magnitude <= 128 in bf16, FP32 tensor-memory chunks of at most
-// 1024 products (partial sums <= 2^24), drained into INT32 registers.
+// digits of magnitude <= 128 in bf16 (<= 256 in fp16), FP32 tensor-memory
+// chunks of at most 1024 (256) products, so partial sums stay <= 2^24,
+// drained into INT32 registers.
 //
 // Warp roles (320 threads per CTA, two CTAs per cluster):
 //   warp 0      (both CTAs) TMA producer: the CTA's 128 A rows (16 KB) and
@@ -66,7 +68,6 @@ constexpr uint32_t kTB = (FBN / 2) * kTileBytes;        // 8 KB: the CTA's half 
 constexpr int kStg = 20;                                // staging row stride (32-bit words)
 constexpr uint32_t kStgBytes = EPI * 32 * kStg * 4;     // 20 KB
 constexpr int kSmem = FS * (kTA + kTB) + kStgBytes + 1024;
-constexpr uint32_t kIdesc = idesc_bf16(2 * FBM, FBN);
 constexpr uint32_t kTmemCols = 512;
 constexpr uint32_t kColRlo = 256, kColRhi = 384;
 constexpr int64_t kGroupN = 8;                          // column tiles per raster group
@@ -79,7 +80,9 @@ struct FusedParams {
     int64_t ntiles, nunits;       // nunits = ntiles * kparts
     int64_t kbr;                  // k-blocks per K part
     int kparts, seg, chunk_blocks;
-    int hop_bits;                 // 8 nsums
+    int hop_bits;                 // rbits nsums
+    int rbits;                    // digit width (radix 2^rbits)
+    uint32_t idesc;               // MMA descriptor (bf16 or fp16 words)
     uint32_t pinv11;              // -p^-1 mod 2^11
     int vec_c;                    // C and ldc allow 16-byte stores of two outputs
     uint64_t p, mu, off;          // mu = floor((2^64 - 1) / p), off = p ceil(2^31 / p)
@@ -121,9 +124,10 @@ __device__ __forceinline__ uint64_t reduce_barrett(uint64_t y, uint64_t p, uint6
     return r;
 }
 
-// One Horner step: (256 r + S) mod p for r < p < 2^52 and |S| < 2^31.
+// One Horner step: (R r + S) mod p for r < p < 2^52, R = 2^rbits <= 2^9 and
+// |S| < 2^31 (y < 2^61 + 2^53).
 __device__ __forceinline__ uint64_t horner(uint64_t r, int32_t S, const FusedParams &P) {
-    return reduce_barrett((r << 8) + (uint64_t)((int64_t)S + (int64_t)P.off), P.p, P.mu);
+    return reduce_barrett((r << P.rbits) + (uint64_t)((int64_t)S + (int64_t)P.off), P.p, P.mu);
 }
 
 // r 2^-bits mod p for r < p (odd p), in Montgomery steps of at most 11 bits.
@@ -292,7 +296,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(FTHREADS, 1)
                                 const uint64_t ad = sdesc(a0 + slot * kTA), bd = sdesc(b0 + slot * kTB);
 #pragma unroll
                                 for (int kk = 0; kk < 4; ++kk)  // K = 16 per MMA: +32 bytes = +2 in the address field
-                                    mma_bf16_pair(dt, ad + 2 * kk, bd + 2 * kk, kIdesc, (t > t0 || kk > 0) ? 1u : 0u);
+                                    mma_bf16_pair(dt, ad + 2 * kk, bd + 2 * kk, P.idesc, (t > t0 || kk > 0) ? 1u : 0u);
                                 mma_commit_pair(&empty[slot], 3);
                             }
                             mma_commit_pair(&tfull[buf], 3);
@@ -455,7 +459,9 @@ int launch_gemm_tc_fused(const Plan &pl, const void *Aw, const void *Bw, uint64_
     P.kbr = pl.kbr;
     P.seg = pl.tc_seg;
     P.chunk_blocks = (int)(pl.tc_chunk / kTcKB);
-    P.hop_bits = 8 * pl.nsums;
+    P.rbits = pl.digit_bits;
+    P.hop_bits = pl.digit_bits * pl.nsums;
+    P.idesc = pl.digit_bits == 9 ? idesc_f16(2 * FBM, FBN) : idesc_bf16(2 * FBM, FBN);
     P.p = pl.p;
     P.mu = ~uint64_t(0) / pl.p;
     P.off = pl.p * ((((uint64_t)1 << 31) + pl.p - 1) / pl.p);

@@ -21,8 +21,12 @@ constexpr int kF64BN = 64;              // CTA cols
 constexpr int kTcKB = 64;               // bf16 digits per k-block (128 B)
 constexpr int kTcBM = 128;              // MMA M (one CTA, TMEM lanes)
 constexpr int kTcBN = 256;              // MMA N
-constexpr int kTcMaxChunk = 1024;       // 2^24 / 2^14 digit products per FP32 chunk
-constexpr int64_t kInt32SumLimit = 131071; // floor((2^31 - 1) / 2^14): products per INT32 sum
+constexpr int kTcMaxChunk = 1024;       // 2^24 / 2^14 digit products per FP32 chunk (8-bit digits)
+constexpr int64_t kInt32SumLimit = 131071; // floor((2^31 - 1) / 2^14): products per INT32 sum (8-bit digits)
+// Digits of b bits (magnitude <= 2^(b-1)) have products of magnitude <= 2^(2b-2):
+// an FP32 chunk holds 2^(26 - 2b) of them, an INT32 sum floor((2^31 - 1) / 2^(2b-2)).
+inline int64_t tc_chunk_limit(int bits) { return int64_t(1) << (26 - 2 * bits); }
+inline int64_t int32_sum_limit(int bits) { return ((int64_t(1) << 31) - 1) >> (2 * bits - 2); }
 constexpr int kFusedSeg = 64;           // fused form: default k-blocks per segment (4096 k)
 constexpr int kFusedPairs = 74;         // fused form: CTA pairs the planner assumes (148 SMs)
 
@@ -42,7 +46,7 @@ struct TcItem {
     int64_t b_wstride, b_kstride;  // bytes between consecutive B words / k-blocks
     int32_t s0, ndiag, nb, i0, ni, v, b_wpad;
     int32_t rv, cv;          // rows of the tile inside m, columns of each diagonal block inside n
-    int32_t pad0;
+    int32_t f16;             // 1: the words are fp16 (9-bit digits), 0: bf16
 };
 
 struct Plan {
@@ -73,6 +77,7 @@ struct Plan {
     double tuned_ms = 0;
     int tuned_tried = 0;
     // INT8 form
+    int digit_bits = 8;  // 8: bf16-carried digits in [-128, 128]; 9: fp16-carried digits in [-256, 256]
     int64_t tc_chunk = 0, kc = 0;
     int tc_pair = 0;  // 1: 2-CTA kernel, A rows padded to 256
     // Fused recombination (gemm_tc_fused.cu): 256 x 128 tiles on CTA pairs,
@@ -115,6 +120,7 @@ mwmm_status make_plan(Plan *pl, int64_t m, int64_t n, int64_t k, uint64_t p, int
 uint64_t ceil_root(uint64_t p, int u);
 uint64_t block_size(uint64_t p, int u, int v);  // Prop. 3.3 / Sec. 2.2, 0 if none
 int int8_digits(uint64_t p);
+int signed_digits(uint64_t p, int bits);  // fewest balanced base-2^bits digits
 uint64_t mulmod_u64(uint64_t a, uint64_t b, uint64_t p);
 
 // launches (return cudaError_t as int)

@@ -1,8 +1,9 @@
 // Recombination of the INT8 form:
-//   C = sum_{s=0}^{u+v-2} gamma_s S_s mod p,  gamma_s = 256^s mod p,
+//   C = sum_{s=0}^{u+v-2} gamma_s S_s mod p,  gamma_s = R^s mod p,
 //   S_s = sum_{i+j=s} A_i B_j,
-// the alpha^i beta^j mod p recombination of Alg. 5 with alpha = beta = 256
-// and the pairs of equal i + j grouped.  B300's FP64 pipe runs at 1/64 of its
+// the alpha^i beta^j mod p recombination of Alg. 5 with alpha = beta = R
+// (R = 256 for 8-bit digits, 512 for 9-bit ones) and the pairs of equal
+// i + j grouped.  B300's FP64 pipe runs at 1/64 of its
 // integer rate, so the arithmetic is exact integer arithmetic, not Alg. 1 /
 // Alg. 2.
 //
@@ -12,9 +13,9 @@
 // are exact in 64 bits (at most 15 terms below 2^58), and
 //   C = (A0 + 2^26 A1 - 2^31 sum_s gamma_s) mod p,
 // which takes three Barrett-type reductions per output instead of one per
-// diagonal.  Several K-ranges: Horner's rule R <- (256 R + S_s) mod p from
-// the top diagonal down (256 R < 2^60, |sum of the ranges| < nkc 2^31, so
-// y = 256 R + S_s + off with off = p ceil(2^31 nkc / p) lies in [0, 2^64)).
+// diagonal.  Several K-ranges: Horner's rule X <- (R X + S_s) mod p from
+// the top diagonal down (R X < 2^61, |sum of the ranges| < nkc 2^31, so
+// y = R X + S_s + off with off = p ceil(2^31 nkc / p) lies in [0, 2^64)).
 #include <cstring>
 #include <vector>
 
@@ -30,6 +31,7 @@ struct RecParams {
     uint64_t *C;
     int64_t ldc, m, n, A_rows, B_rows;
     int nsums, nkc;
+    int rbits;            // digit width: radix 2^rbits
     uint64_t p, mu, off;  // mu = floor((2^64 - 1) / p)
     uint64_t mu90;        // floor(2^90 / p) when p > 2^26, else 0 (then every gh_s = 0)
     uint64_t K;           // (-2^31 sum_s gamma_s) mod p
@@ -107,7 +109,7 @@ __device__ __forceinline__ void recombine_rows(const RecParams &P, int64_t c0, i
         }
 #pragma unroll
         for (int e = 0; e < 4; ++e)
-            R[e] = reduce_u64((R[e] << 8) + (uint64_t)(x[e] + (int64_t)P.off), P.p, P.mu);
+            R[e] = reduce_u64((R[e] << P.rbits) + (uint64_t)(x[e] + (int64_t)P.off), P.p, P.mu);
     }
     uint64_t *out = P.C + row * P.ldc + c0;
 #pragma unroll
@@ -234,6 +236,7 @@ RecParams make_rec_params(const Plan &pl, const int32_t *S, uint64_t *C, int64_t
     P.B_rows = pl.B_rows;
     P.nsums = pl.nsums;
     P.nkc = pl.nkc;
+    P.rbits = pl.digit_bits;
     P.p = pl.p;
     P.vec = (reinterpret_cast<uintptr_t>(C) % 16 == 0 && ldc % 2 == 0) ? 1 : 0;
     P.mu = (~uint64_t(0)) / pl.p;
@@ -245,7 +248,7 @@ RecParams make_rec_params(const Plan &pl, const int32_t *S, uint64_t *C, int64_t
         P.gl[s] = (uint32_t)(g & ((1u << 26) - 1));
         P.gh[s] = (uint32_t)(g >> 26);
         if (s < pl.nsums) gsum = (gsum + g) % pl.p;
-        g = mulmod_u64(g, 256, pl.p);
+        g = mulmod_u64(g, uint64_t(1) << pl.digit_bits, pl.p);
     }
     const uint64_t bias = mulmod_u64(gsum, uint64_t(1) << 31, pl.p);
     P.K = (pl.p - bias) % pl.p;

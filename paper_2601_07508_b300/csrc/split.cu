@@ -7,9 +7,10 @@
 // floor(fl(T / alpha)) is the same integer, so the words are identical.
 //
 // INT8 form: the signed representative s of M mod p (M, or M - p when
-// M > (p-1)/2) is written as base-2^8 digits, s = sum_i 256^i d_i: balanced
-// digits in [-128, 127] and a top digit in [-128, 128] (the remainder); the
-// digits are stored exactly as bf16.
+// M > (p-1)/2) is written as base-2^b digits, s = sum_i R^i d_i (R = 2^b,
+// h = R / 2): balanced digits in [-h, h - 1] and a top digit in [-h, h] (the
+// remainder).  b = 8: the digits are stored exactly as bf16; b = 9: exactly
+// as fp16 (integers up to 2^11 are exact in fp16, 2^8 in bf16).
 //
 // CRT form (multimodular comparison, Sec. 5.2): word i is the signed
 // residue of M modulo the i-th modulus m_i < 256 (in [-(m_i-1)/2, (m_i-1)/2]),
@@ -21,6 +22,7 @@
 // tcgen05 shared-memory descriptors expect, and keeps the FP64 kernel's
 // shared-memory reads spread over all banks.
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include <cstring>
 #include <vector>
@@ -49,7 +51,8 @@ struct SplitParams {
     uint64_t alpha, mu;  // FP64: radix and floor((2^64 - 1) / alpha)
     int validate;
     int *err;
-    int64_t cbias;              // INT8 form: 128 (1 + 256 + ... + 256^(words-2))
+    int64_t cbias;              // INT8 form: h (1 + R + ... + R^(words-2))
+    int bits;                   // INT8 form: digit width b (8: bf16 words, 9: fp16 words)
     int crt;                    // CRT form: residues instead of digits
     float cmf[kMaxCrt];         // moduli m_i (odd primes below 256)
     float cinv[kMaxCrt];        // fl(1 / m_i), correctly rounded
@@ -71,6 +74,11 @@ __device__ __forceinline__ float byte_digit_float(uint32_t x, int i) {
 }
 __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
     return __byte_perm(__float_as_uint(lo), __float_as_uint(hi), 0x7632u);
+}
+// Two small integers (exact in fp16) packed as fp16 x 2.
+__device__ __forceinline__ uint32_t pack_f16x2(float lo, float hi) {
+    const __half2 h = __floats2half2_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t *>(&h);
 }
 
 // Signed residue of x < 2^52 modulo an odd m < 256, in [-(m-1)/2, (m-1)/2],
@@ -153,6 +161,12 @@ __device__ __forceinline__ float int8_digit(int64_t t, int w, bool last) {
     const uint32_t half = w < 4 ? (uint32_t)t : (uint32_t)((uint64_t)t >> 32);
     return byte_digit_float(half, w & 3);
 }
+// 9-bit digits the same way: c = 256 (1 + 512 + ... + 512^(u-2)), the lower
+// digits are the 9-bit fields of t minus 256, the top one t >> 9 (u-1).
+__device__ __forceinline__ float int9_digit(int64_t t, int w, bool last) {
+    if (last) return small_int_float((int)(t >> (9 * w)));
+    return small_int_float((int)(((uint64_t)t >> (9 * w)) & 511u) - 256);
+}
 
 // FP64 form: a 64 x 64 tile covers 4 k-blocks of 16 doubles, 8 granules each.
 __device__ __forceinline__ void split_fp64_tile(const SplitParams &P, uint64_t (*tile)[kST + 1], int64_t by,
@@ -190,12 +204,16 @@ __device__ __forceinline__ void split_int8_tile(const SplitParams &P, uint64_t (
         const int rr = unit / 8, g = unit % 8;
         const int64_t r = r0 + rr;
         if (r >= P.rows_pad) continue;  // a last row tile may be partial (rows_pad 16 or 32)
-        // word w of the unit's 8 entries, packed bf16, to its swizzled 16-byte granule
+        // word w of the unit's 8 entries, packed bf16 (or fp16), to its swizzled 16-byte granule
         auto store = [&](int w, const float (&f)[8]) {
             uint8_t *dst = P.out + ((int64_t)(w + P.wpad) * P.wstride + kb * P.kstride + r) * kTileBytes +
                            ((g ^ (int)(r & 7)) * 16);
-            *reinterpret_cast<uint4 *>(dst) = make_uint4(pack_bf16x2(f[0], f[1]), pack_bf16x2(f[2], f[3]),
-                                                         pack_bf16x2(f[4], f[5]), pack_bf16x2(f[6], f[7]));
+            if (P.bits == 9)
+                *reinterpret_cast<uint4 *>(dst) = make_uint4(pack_f16x2(f[0], f[1]), pack_f16x2(f[2], f[3]),
+                                                             pack_f16x2(f[4], f[5]), pack_f16x2(f[6], f[7]));
+            else
+                *reinterpret_cast<uint4 *>(dst) = make_uint4(pack_bf16x2(f[0], f[1]), pack_bf16x2(f[2], f[3]),
+                                                             pack_bf16x2(f[4], f[5]), pack_bf16x2(f[6], f[7]));
         };
         if (P.crt) {
             float xl[8][5];  // 11-bit limbs
@@ -219,8 +237,13 @@ __device__ __forceinline__ void split_int8_tile(const SplitParams &P, uint64_t (
             for (int w = 0; w < P.words; ++w) {
                 const bool last = (w == P.words - 1);
                 float f[8];
+                if (P.bits == 9) {
 #pragma unroll
-                for (int e = 0; e < 8; ++e) f[e] = int8_digit(t[e], w, last);
+                    for (int e = 0; e < 8; ++e) f[e] = int9_digit(t[e], w, last);
+                } else {
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) f[e] = int8_digit(t[e], w, last);
+                }
                 store(w, f);
             }
         }
@@ -280,8 +303,10 @@ SplitParams make_split_params(const Plan &pl, int side, const uint64_t *M, int64
     P.validate = pl.validate;
     P.err = pl.err_dev;
     P.crt = pl.form == MWMM_FORM_CRT8;
+    P.bits = pl.form == MWMM_FORM_INT8 ? pl.digit_bits : 8;
     P.cbias = 0;
-    for (int i = 0; i + 1 < P.words && !P.crt && pl.form != MWMM_FORM_FP64; ++i) P.cbias += (int64_t)128 << (8 * i);
+    for (int i = 0; i + 1 < P.words && !P.crt && pl.form != MWMM_FORM_FP64; ++i)
+        P.cbias += (int64_t)1 << (P.bits - 1 + P.bits * i);
     for (int i = 0; i < kMaxCrt; ++i) {
         const uint32_t m = i < pl.crt_s ? pl.crt_m[i] : 3;
         P.cmf[i] = (float)m;

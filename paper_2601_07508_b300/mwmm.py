@@ -40,7 +40,8 @@ class PlanOpts(ctypes.Structure):
     _fields_ = [("lambda_", ctypes.c_int64), ("validate", ctypes.c_int32), ("tc_chunk", ctypes.c_int32),
                 ("kc", ctypes.c_int64), ("tc_pair", ctypes.c_int32),
                 ("f64_concat", ctypes.c_int32), ("ksplit", ctypes.c_int32), ("autotune", ctypes.c_int32),
-                ("tc_fused", ctypes.c_int32), ("tc_seg", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
+                ("tc_fused", ctypes.c_int32), ("tc_seg", ctypes.c_int32), ("tc_digit_bits", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 1)]
 
 
 class Timing(ctypes.Structure):
@@ -62,7 +63,7 @@ class PlanDesc(ctypes.Structure):
                 ("S_off", ctypes.c_uint64), ("workspace_bytes", ctypes.c_uint64),
                 ("f64_concat", ctypes.c_int32), ("ksplit", ctypes.c_int32),
                 ("tuned_ms", ctypes.c_double), ("tuned_tried", ctypes.c_int32), ("tc_seg", ctypes.c_int32),
-                ("crt_m", ctypes.c_uint32 * 24)]
+                ("crt_m", ctypes.c_uint32 * 24), ("tc_digit_bits", ctypes.c_int32), ("pad2", ctypes.c_int32)]
 
     def as_dict(self):
         d = {}
@@ -221,7 +222,8 @@ def _ld(t) -> int:
 # --------------------------------------------------------------------------- C-named calls
 def mwmm_plan(m: int, n: int, k: int, p: int, u: int = 0, v: int = 0, form="auto", lam: int = 0,
               validate: bool = False, tc_chunk: int = 0, kc: int = 0, tc_pair: bool = False,
-              f64_concat: int = 0, ksplit: int = 0, tc_fused: int = 0, tc_seg: int = 0) -> int:
+              f64_concat: int = 0, ksplit: int = 0, tc_fused: int = 0, tc_seg: int = 0,
+              tc_digit_bits: int = 0) -> int:
     if isinstance(form, str):
         form = FORMS[form]
     h = _vp()
@@ -235,6 +237,7 @@ def mwmm_plan(m: int, n: int, k: int, p: int, u: int = 0, v: int = 0, form="auto
     o.ksplit = ksplit
     o.tc_fused = tc_fused
     o.tc_seg = tc_seg
+    o.tc_digit_bits = tc_digit_bits
     _check(lib().mwmm_plan(ctypes.byref(h), m, n, k, p, u, v, form, ctypes.byref(o)), "mwmm_plan")
     return h.value
 
@@ -601,9 +604,10 @@ class Plan:
 
     def __init__(self, m: int, n: int, k: int, p: int, u: int = 0, v: int = 0, form="auto", lam: int = 0,
                  validate: bool = False, tc_chunk: int = 0, kc: int = 0, tc_pair: bool = False,
-                 f64_concat: int = 0, ksplit: int = 0, tc_fused: int = 0, tc_seg: int = 0):
+                 f64_concat: int = 0, ksplit: int = 0, tc_fused: int = 0, tc_seg: int = 0,
+                 tc_digit_bits: int = 0):
         self.handle = mwmm_plan(m, n, k, p, u, v, form, lam, validate, tc_chunk, kc, tc_pair, f64_concat, ksplit,
-                                tc_fused, tc_seg)
+                                tc_fused, tc_seg, tc_digit_bits)
         self.info = mwmm_plan_info(self.handle)
         self.workspace = None
 

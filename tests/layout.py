@@ -5,7 +5,8 @@ import numpy as np
 def unpack_words(buf: np.ndarray, words: int, nkb: int, rows_pad: int, kind: str, wpad: int = 0,
                  kmajor: bool = False) -> np.ndarray:
     """buf: uint8 bytes of one side's word region.  Returns [words][rows_pad][nkb*kb_elems]
-    as float64 (FP64 words) or int32 (INT8 digits stored as bf16).  wpad > 0 or
+    as float64: FP64 words ("fp64"), digits stored as bf16 ("int8") or as fp16
+    ("f16", the 9-bit digits).  wpad > 0 or
     kmajor: the k-block-major layout with wpad zero words on each side (checked zero)."""
     if wpad or kmajor:
         wp = words + 2 * wpad
@@ -22,6 +23,8 @@ def unpack_words(buf: np.ndarray, words: int, nkb: int, rows_pad: int, kind: str
         out[:, :, :, g, :] = a[:, :, np.arange(rows_pad), g ^ r, :]
     if kind == "fp64":
         el = out.reshape(words, nkb, rows_pad, 128).view(np.float64)          # 16 per chunk
+    elif kind == "f16":
+        el = out.reshape(words, nkb, rows_pad, 128).view(np.float16).astype(np.float64)  # 64 fp16 per chunk
     else:
         u16 = out.reshape(words, nkb, rows_pad, 128).view(np.uint16)          # 64 bf16 per chunk
         el = (u16.astype(np.uint32) << 16).view(np.float32).astype(np.float64)

@@ -76,17 +76,42 @@ def test_fp64_auto_variant_follows_cost_model(M, oracle):
 
 
 @pytest.mark.parametrize("p", list(SWEEP.values()) + [5, 7, 257, (1 << 31) - 1])
-def test_int8_plan_digits_match_oracle(M, oracle, p):
-    h = M.mwmm_plan(100, 300, 5000, p, 0, 0, "int8")
+@pytest.mark.parametrize("bits", [0, 8, 9])
+def test_int8_plan_digits_match_oracle(M, oracle, p, bits):
+    h = M.mwmm_plan(100, 300, 5000, p, 0, 0, "int8", tc_digit_bits=bits)
     d = M.mwmm_plan_info(h)
     M.mwmm_plan_destroy(h)
-    u = oracle.int8_words(p)
-    assert (d["u"], d["v"], d["alpha"], d["nsums"]) == (u, u, 256, 2 * u - 1)
-    # INT32 sums hold kc * min(u, v) products of magnitude <= 2^14
-    assert d["kc"] % 64 == 0 and d["kc"] * min(u, u) * 2 ** 14 < 2 ** 31
+    want = bits or (9 if oracle.digit_words(p, 9) < oracle.digit_words(p, 8) else 8)
+    u = oracle.digit_words(p, want)
+    assert d["tc_digit_bits"] == want
+    assert (d["u"], d["v"], d["alpha"], d["nsums"]) == (u, u, 2 ** want, 2 * u - 1)
+    # INT32 sums hold kc * min(u, v) products of magnitude <= 2^(2 bits - 2)
+    prod = 2 ** (2 * want - 2)
+    assert d["kc"] % 64 == 0 and d["kc"] * min(u, u) * prod < 2 ** 31
     assert d["nkc"] == -(-5000 // d["kc"])
-    assert d["tc_chunk"] == 1024 and d["tc_chunk"] * 2 ** 14 <= 2 ** 24
-    assert d["A_rows"] == 128 and d["B_rows"] == 512  # m = 100: one row tile, no cluster
+    assert d["tc_chunk"] == 2 ** 24 // prod  # FP32 chunk: 1024 (8-bit) or 256 (9-bit) products
+    assert d["A_rows"] == 128 and d["B_rows"] == 512  # m = 100: one row tile
+
+
+def test_int8_digit_width_choice_on_the_sweep(M, oracle):
+    """9-bit digits where they save a digit (26 and 52 bits of the sweep),
+    8-bit ones elsewhere; explicit words of one width are checked against it."""
+    got = {}
+    for b, p in SWEEP.items():
+        h = M.mwmm_plan(64, 64, 64, p, 0, 0, "int8")
+        d = M.mwmm_plan_info(h)
+        M.mwmm_plan_destroy(h)
+        got[b] = (d["tc_digit_bits"], d["u"])
+    assert got == {20: (8, 3), 23: (8, 3), 26: (9, 3), 32: (8, 4), 40: (8, 5), 48: (8, 6), 52: (9, 6)}
+    with pytest.raises(M.MwmmError) as e:  # 6 digits of 8 bits cannot hold a 52-bit residue
+        M.mwmm_plan(64, 64, 64, SWEEP[52], 6, 6, "int8")
+    assert e.value.status == 3
+    h = M.mwmm_plan(64, 64, 64, SWEEP[52], 6, 6, "int8", tc_digit_bits=9)
+    M.mwmm_plan_destroy(h)
+    for bad in (7, 10, -1):
+        with pytest.raises(M.MwmmError) as e:
+            M.mwmm_plan(64, 64, 64, SWEEP[52], 0, 0, "int8", tc_digit_bits=bad)
+        assert e.value.status == 1
 
 
 def test_plan_errors(M):
@@ -270,9 +295,9 @@ def test_autotune_cache_file_round_trip(M, tmp_path):
     src = tmp_path / "cache.jsonl"
     src.write_text(
         '{"key": "f2.b52.m12.n12.k12.single.sm148", "form": 2, "u": 7, "v": 7, "tc_chunk": 0, "kc": 0, '
-        '"tc_pair": 0, "f64_concat": 0, "ksplit": 0, "ms": 4.250000, "tried": 3}\n'
+        '"tc_pair": 0, "tc_digit_bits": 9, "f64_concat": 0, "ksplit": 0, "ms": 4.250000, "tried": 3}\n'
         '{"key": "f1.b40.m11.n11.k11.batch.sm148", "form": 1, "u": 2, "v": 2, "tc_chunk": 0, "kc": 0, '
-        '"tc_pair": 0, "f64_concat": 1, "ksplit": 1, "ms": 59.400000, "tried": 4}\n'
+        '"tc_pair": 0, "tc_digit_bits": 0, "f64_concat": 1, "ksplit": 1, "ms": 59.400000, "tried": 4}\n'
         'not a cache line\n')
     M.mwmm_autotune_cache_load(str(src))
     assert M.mwmm_autotune_cache_entries() == 2
@@ -319,15 +344,16 @@ def test_crt_plan_errors(M):
 
 
 def test_tensor_form_choice_follows_the_cost_model(M):
-    """AUTO's tensor form for batches and serving: at 4096^3 the INT8 digits
-    at 23-24 bits (9 digit products against 8 moduli plus a costlier CRT
-    reconstruction), the CRT form from 25 bits (16 / 25 / 36 / 49 digit
-    products against 9-16 moduli); small products stay INT8 (the CRT split
-    and reconstruction grow with the moduli); k > 2^22 cannot use CRT."""
-    P = {b: inputs.largest_prime_below_pow2(b) for b in (23, 24, 26, 32, 40, 48, 52)}
-    assert M.mwmm_tensor_form(4096, 4096, 4096, P[23]) == "int8"
-    assert M.mwmm_tensor_form(4096, 4096, 4096, P[24]) == "int8"
-    for b in (26, 32, 40, 48, 52):
+    """AUTO's tensor form for batches and serving: at 4096^3 the digit form
+    at 23-27 bits (9 digit products, 9-bit digits from 25 bits, against 8-9
+    moduli plus a costlier CRT reconstruction), the CRT form from 28 bits
+    (16 / 25 / 36 / 36 digit products against 10-16 moduli); small products
+    stay INT8 (the CRT split and reconstruction grow with the moduli);
+    k > 2^22 cannot use CRT."""
+    P = {b: inputs.largest_prime_below_pow2(b) for b in (23, 24, 26, 27, 28, 32, 40, 48, 52)}
+    for b in (23, 24, 26, 27):
+        assert M.mwmm_tensor_form(4096, 4096, 4096, P[b]) == "int8", b
+    for b in (28, 32, 40, 48, 52):
         assert M.mwmm_tensor_form(4096, 4096, 4096, P[b]) == "crt8", b
         assert M.mwmm_tensor_form(64, 64, 64, P[b]) == "int8", b
     assert M.mwmm_tensor_form(64, 64, (1 << 22) + 64, P[52]) == "int8"

@@ -231,12 +231,14 @@ def test_int8_all_bitsizes_ragged(M, oracle, b):
         assert np.array_equal(C, oracle.matmul_mod(A, B, p)), (m, n, k)
 
 
-@pytest.mark.parametrize("tc_chunk,kc", [(64, 0), (192, 0), (1024, 64), (512, 320)])
-def test_int8_chunk_boundaries(M, oracle, tc_chunk, kc):
-    """FP32 chunks of 1..16 k-blocks and INT32 K-ranges of 1..5 k-blocks."""
+@pytest.mark.parametrize("bits,tc_chunk,kc", [(8, 64, 0), (8, 192, 0), (8, 1024, 64), (8, 512, 320),
+                                               (9, 64, 0), (9, 192, 0), (9, 256, 64), (9, 128, 320)])
+def test_int8_chunk_boundaries(M, oracle, bits, tc_chunk, kc):
+    """FP32 chunks of 1..16 k-blocks (1..4 with 9-bit digits) and INT32
+    K-ranges of 1..5 k-blocks."""
     p = SWEEP[52]
     A, B = inputs.problem(11, 200, 300, 777, p)
-    C, _ = gpu_product(M, A, B, p, form="int8", tc_chunk=tc_chunk, kc=kc)
+    C, _ = gpu_product(M, A, B, p, form="int8", tc_chunk=tc_chunk, kc=kc, tc_digit_bits=bits)
     assert np.array_equal(C, oracle.matmul_mod(A, B, p))
 
 
@@ -265,7 +267,7 @@ def test_int8_extreme_digits_fill_the_fp32_chunk(M, oracle, b, da, db):
     assert list(Aw) == [da] * La + [0] * (u - La) and list(Bw) == [db] * Lb + [0] * (u - Lb)
     A = np.full((130, 1024 + 64), a, dtype=np.uint64)
     B = np.full((1024 + 64, 260), bb, dtype=np.uint64)
-    C, _ = gpu_product(M, A, B, p, form="int8")
+    C, _ = gpu_product(M, A, B, p, form="int8", tc_digit_bits=8)
     assert np.all(C == (a * bb * (1024 + 64)) % p)
 
 
@@ -353,7 +355,7 @@ def test_int8_fp32_chunk_odd_increments_near_2_24(M, oracle, b, fused):
             assert np.all(np.diff(part[:CHUNK // 16]) % 2 == 1) and np.all(np.abs(part) <= 2 ** 24)
             peak = max(peak, int(np.abs(part).max()))
     assert peak > 2 ** 23.85
-    C, plan = gpu_product(M, A, B, p, form="int8", tc_fused=fused)
+    C, plan = gpu_product(M, A, B, p, form="int8", tc_fused=fused, tc_digit_bits=8)
     assert plan.info["tc_fused"] == (fused == 2)
     assert np.array_equal(C, oracle.matmul_mod(A, B, p))
 
@@ -395,7 +397,7 @@ def test_int8_fp32_chunk_small_addend_below_large_sum(M, oracle, b, sign, fused)
     last = part[CHUNK // 16 - 5:CHUNK // 16]
     assert list(np.diff(last)) == [sign] * 4 and abs(int(last[0])) == 960 * 16129
     assert np.all(np.abs(part) <= 2 ** 24) and np.abs(part).max() > 2 ** 23.85
-    C, plan = gpu_product(M, A, B, p, form="int8", tc_fused=fused)
+    C, plan = gpu_product(M, A, B, p, form="int8", tc_fused=fused, tc_digit_bits=8)
     assert plan.info["tc_fused"] == (fused == 2)
     assert np.array_equal(C, oracle.matmul_mod(A, B, p))
 
@@ -412,9 +414,113 @@ def test_int8_fp32_chunk_odd_increments_in_a_two_pair_diagonal(M, oracle, b, fus
     A, B = _odd_slices_patterns(e, p - e, 130, 260)
     Ad = oracle.split_signed8(A, p, u)
     assert np.all(np.abs(Ad[:2]) <= 127) and np.all(Ad[2:] == 0) and int(Ad[1, 64, 0]) == 127
-    C, plan = gpu_product(M, A, B, p, form="int8", tc_fused=fused)
+    C, plan = gpu_product(M, A, B, p, form="int8", tc_fused=fused, tc_digit_bits=8)
     assert plan.info["tc_fused"] == (fused == 2)
     assert np.array_equal(C, oracle.matmul_mod(A, B, p))
+
+
+# 9-bit digits (fp16): products of magnitude <= 2^16, FP32 chunks of 256.
+CHUNK9 = 256
+KDIM9 = 2 * CHUNK9 + 64   # two full chunks and one k-block
+
+
+def _chunk_partials9(a_dig, b_dig):
+    prod = (a_dig.astype(np.int64) * b_dig.astype(np.int64)).reshape(-1, 16).sum(axis=1)
+    return np.concatenate([np.cumsum(prod[i:i + CHUNK9 // 16]) for i in range(0, prod.size, CHUNK9 // 16)])
+
+
+@pytest.mark.parametrize("b", [26, 40, 52])
+@pytest.mark.parametrize("da,db", [(-256, -256), (255, 255), (-256, 255)])
+@pytest.mark.parametrize("fused", [1, 2])
+def test_f16_extreme_digits_fill_the_fp32_chunk(M, oracle, b, da, db, fused):
+    """9-bit digits at the ends of [-256, 255]: every product is +-2^16 (or
+    -65280, 65025), so a full 256-product chunk reaches |sum| = 2^24."""
+    p = SWEEP[b]
+    u = oracle.digit_words(p, 9)
+    a, bb = (da if da >= 0 else p + da), (db if db >= 0 else p + db)
+    Aw = oracle.split_signed(np.array([a], np.uint64), p, u, 9)[:, 0]
+    Bw = oracle.split_signed(np.array([bb], np.uint64), p, u, 9)[:, 0]
+    assert list(Aw) == [da] + [0] * (u - 1) and list(Bw) == [db] + [0] * (u - 1)
+    A = np.full((130, KDIM9), a, dtype=np.uint64)
+    B = np.full((KDIM9, 260), bb, dtype=np.uint64)
+    C, plan = gpu_product(M, A, B, p, form="int8", tc_digit_bits=9, tc_fused=fused)
+    assert plan.info["tc_chunk"] == CHUNK9 and plan.info["tc_fused"] == (fused == 2)
+    assert np.all(C == (a * bb * KDIM9) % p)
+
+
+@pytest.mark.parametrize("b", [26, 52])
+@pytest.mark.parametrize("fused", [1, 2])
+def test_f16_fp32_chunk_odd_increments_near_2_24(M, oracle, b, fused):
+    """9-bit digits +-255 at 15 of every 16 k positions against B digits
+    +-255: every MMA adds +-15 x 65025 (odd), a chunk's running sum walks to
+    +-16 x 975375 = +-15,606,000 (2^23.9), with zero crossings across rows."""
+    p = SWEEP[b]
+    u = oracle.digit_words(p, 9)
+    k = np.arange(KDIM9)
+    A = np.zeros((130, KDIM9), np.uint64)
+    for r in range(130):
+        t = r % 17
+        plus = ((k % CHUNK9) // 16) < t
+        A[r] = np.where(k % 16 == 15, 0, np.where(plus, 255, p - 255))
+    B = np.empty((KDIM9, 260), np.uint64)
+    B[:, 0::2] = 255
+    B[:, 1::2] = p - 255
+    Ad = oracle.split_signed(A, p, u, 9)
+    Bd = oracle.split_signed(B, p, u, 9)
+    assert np.all(Ad[1:] == 0) and np.all(Bd[1:] == 0)
+    peak = 0
+    for r in (0, 1, 8, 16):
+        for c in (0, 1):
+            part = _chunk_partials9(Ad[0, r], Bd[0, :, c])
+            assert np.all(np.diff(part[:CHUNK9 // 16]) % 2 == 1) and np.all(np.abs(part) <= 2 ** 24)
+            peak = max(peak, int(np.abs(part).max()))
+    assert peak > 2 ** 23.89
+    C, plan = gpu_product(M, A, B, p, form="int8", tc_digit_bits=9, tc_fused=fused)
+    assert plan.info["tc_chunk"] == CHUNK9
+    assert np.array_equal(C, oracle.matmul_mod(A, B, p))
+
+
+@pytest.mark.parametrize("b", [26, 52])
+@pytest.mark.parametrize("sign", [1, -1])
+def test_f16_fp32_chunk_small_addend_below_large_sum(M, oracle, b, sign):
+    """12 slices of products +-255 x 255 (+-12,484,800, 2^23.57) then four MMAs
+    each adding +-1 inside the same 256-product chunk."""
+    p = SWEEP[b]
+    u = oracle.digit_words(p, 9)
+    k = np.arange(KDIM9)
+    pos = k % CHUNK9
+    big, one = (255, 1) if sign > 0 else (p - 255, p - 1)
+    row = np.where(pos < 192, big, 0).astype(np.uint64)
+    row[(pos >= 192) & (pos % 16 == 0)] = one
+    A = np.tile(row, (129, 1))
+    A[1::2] = np.roll(row, 16)
+    B = np.empty((KDIM9, 257), np.uint64)
+    B[:, 0::2] = np.where(pos < 192, 255, 1)[:, None]
+    B[:, 1::2] = np.where(pos < 192, p - 255, p - 1)[:, None]
+    Ad = oracle.split_signed(A, p, u, 9)
+    Bd = oracle.split_signed(B, p, u, 9)
+    part = _chunk_partials9(Ad[0, 0], Bd[0, :, 0])
+    last = part[CHUNK9 // 16 - 5:CHUNK9 // 16]
+    assert list(np.diff(last)) == [sign] * 4 and abs(int(last[0])) == 192 * 65025
+    C, _ = gpu_product(M, A, B, p, form="int8", tc_digit_bits=9)
+    assert np.array_equal(C, oracle.matmul_mod(A, B, p))
+
+
+@pytest.mark.parametrize("b", [26, 40, 48, 52])
+def test_f16_digits_match_oracle_and_8bit_digits(M, oracle, b):
+    """9-bit digits (fp16 words) on ragged shapes through several chunks,
+    K-ranges and the pair and fused kernels: equal to the oracle and to the
+    8-bit digits."""
+    p = SWEEP[b]
+    for seed, (m, n, k) in enumerate([(129, 300, 777), (300, 40, 1100), (257, 260, 5500), (1, 129, 64)]):
+        A, B = inputs.problem(1200 + b + seed, m, n, k, p)
+        ref = oracle.matmul_mod(A, B, p)
+        for kw in ({}, {"tc_pair": True}, {"tc_fused": 2}, {"kc": 320, "tc_chunk": 128}):
+            C, plan = gpu_product(M, A, B, p, form="int8", tc_digit_bits=9, **kw)
+            assert plan.info["tc_digit_bits"] == 9
+            assert np.array_equal(C, ref), (m, n, k, kw)
+        C8, _ = gpu_product(M, A, B, p, form="int8", tc_digit_bits=8)
+        assert np.array_equal(C8, ref)
 
 
 @pytest.mark.parametrize("b", [20, 40, 52])
@@ -570,16 +676,18 @@ def test_validation_reports_entries_out_of_range(M):
                                          ("fp64", 32, (1, 2), 40), ("fp64", 40, (1, 4), 20), ("fp64", 52, (2, 3), 33),
                                          ("fp64", 40, (2, 2), 300),
                                          ("int8", 52, None, 290), ("int8", 23, None, 290), ("int8", 52, None, 90),
-                                         ("int8", 40, None, 20)])
+                                         ("int8", 40, None, 20), ("int8", 26, None, 290), ("int8", 52, None, 33),
+                                         ("int8", 40, "f16", 290)])
 def test_split_words_match_oracle(M, oracle, form, b, uv, n):
     p = SWEEP[b]
     m, k = 70, 150
     if form == "fp64" and n == 300:
         m = 20  # narrow m: the A words are concatenated (k-block major)
     A, B = inputs.problem(31, m, n, k, p)
-    kw = dict(u=uv[0], v=uv[1]) if uv else {}
+    kw = dict(u=uv[0], v=uv[1]) if isinstance(uv, tuple) else ({"tc_digit_bits": 9} if uv == "f16" else {})
     plan = M.Plan(m, n, k, p, form=form, **kw)
     d = plan.info
+    bits = d["tc_digit_bits"]
     for side, Mx, rows in ((0, A, m), (1, B, n)):
         words = d["u"] if side == 0 else d["v"]
         rows_pad = d["A_rows"] if side == 0 else d["B_rows"]
@@ -588,36 +696,42 @@ def test_split_words_match_oracle(M, oracle, form, b, uv, n):
         M.mwmm_split(plan.handle, side, dev(Mx), buf)
         torch.cuda.synchronize()
         kmajor = (side == 1 and d["f64_concat"] == 1) or (side == 0 and d["f64_concat"] == 2)
-        W = unpack_words(buf.cpu().numpy(), words, d["nkb"], rows_pad, form, wpad, kmajor=kmajor)
+        W = unpack_words(buf.cpu().numpy(), words, d["nkb"], rows_pad, "f16" if bits == 9 else form, wpad,
+                         kmajor=kmajor)
         src = Mx if side == 0 else Mx.T.copy()       # rows x k
         if form == "fp64":
             ref = oracle.split_alpha(src, d["alpha"] if side == 0 else d["beta"], words).astype(np.float64)
         else:
-            ref = oracle.split_signed8(src, p, words).astype(np.float64)
+            ref = oracle.split_signed(src, p, words, bits).astype(np.float64)
         assert np.array_equal(W[:, :rows, :k], ref)
         assert np.all(W[:, rows:, :] == 0) and np.all(W[:, :, k:] == 0)
 
 
-@pytest.mark.parametrize("b", [20, 52])
-def test_int8_diagonal_sums_match_oracle(M, oracle, b):
-    """S_s = sum_{i+j=s} A_i B_j read from the workspace after a product."""
+@pytest.mark.parametrize("b,bits", [(20, 0), (52, 0), (52, 8), (40, 9)])
+def test_int8_diagonal_sums_match_oracle(M, oracle, b, bits):
+    """S_s = sum_{i+j=s} A_i B_j read from the workspace after a product
+    (8- or 9-bit digits), and C = sum_s R^s S_s mod p."""
     p = SWEEP[b]
     m, n, k = 130, 260, 700
     A, B = inputs.problem(41, m, n, k, p)
-    plan = M.Plan(m, n, k, p, form="int8", kc=256)
+    plan = M.Plan(m, n, k, p, form="int8", kc=256, tc_digit_bits=bits)
     ws = plan.alloc_workspace()
     plan.matmul(dev(A), dev(B))
     assert plan.check() == 0
     d = plan.info
     S = ws[d["S_off"]:d["S_off"] + d["nsums"] * d["nkc"] * d["A_rows"] * d["B_rows"] * 4]
     S = S.cpu().numpy().view(np.int32).reshape(d["nsums"], d["nkc"], d["A_rows"], d["B_rows"])
-    u = d["u"]
-    Aw = oracle.split_signed8(A, p, u)
-    Bw = oracle.split_signed8(B, p, u)
+    u, db = d["u"], d["tc_digit_bits"]
+    assert db == (bits or (9 if b == 52 else 8))
+    Aw = oracle.split_signed(A, p, u, db)
+    Bw = oracle.split_signed(B, p, u, db)
+    total = np.zeros((d["nsums"], m, n), np.int64)
     for kc in range(d["nkc"]):
         sl = slice(kc * d["kc"], min(k, (kc + 1) * d["kc"]))
         ref = oracle.diag_sums(np.ascontiguousarray(Aw[:, :, sl]), np.ascontiguousarray(Bw[:, sl, :]))
         assert np.array_equal(S[:, kc, :m, :n].astype(np.int64), ref)
+        total += ref
+    assert np.array_equal(oracle.recombine_pow(total, 2 ** db, p), oracle.matmul_mod(A, B, p))
 
 
 @pytest.mark.parametrize("p", [5, 7, 65521, SWEEP[26], SWEEP[40], P50, P51, SWEEP[52]])
@@ -794,8 +908,8 @@ def test_int8_windowed_diagonal_sums_match_oracle(M, oracle):
     S = ws[d["S_off"]:d["S_off"] + d["nsums"] * d["nkc"] * d["A_rows"] * d["B_rows"] * 4]
     S = S.cpu().numpy().view(np.int32).reshape(d["nsums"], d["nkc"], d["A_rows"], d["B_rows"])
     u = d["u"]
-    Aw = oracle.split_signed8(A, p, u)
-    Bw = oracle.split_signed8(B, p, u)
+    Aw = oracle.split_signed(A, p, u, d["tc_digit_bits"])
+    Bw = oracle.split_signed(B, p, u, d["tc_digit_bits"])
     for kc in range(d["nkc"]):
         sl = slice(kc * d["kc"], min(k, (kc + 1) * d["kc"]))
         ref = oracle.diag_sums(np.ascontiguousarray(Aw[:, :, sl]), np.ascontiguousarray(Bw[:, sl, :]))

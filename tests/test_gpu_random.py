@@ -37,12 +37,19 @@ def _case(rng, oracle):
                   f64_concat=int(rng.integers(0, 2)), ksplit=int(rng.integers(0, 5)))
         kw["lam"] = min(kw["lam"], 10 ** 6)
     else:
+        nine = False
+        if form == "int8":
+            bits = [0, 8, 9][int(rng.integers(0, 3))]
+            kw["tc_digit_bits"] = bits
+            nine = bits == 9 or (bits == 0 and oracle.digit_words(p, 9) < oracle.digit_words(p, 8))
         if rng.random() < 0.3:
             kw["kc"] = 64 * int(rng.integers(1, 8))
         if rng.random() < 0.3:
-            kw["tc_chunk"] = 64 * int(rng.integers(1, 17))
+            kw["tc_chunk"] = 64 * int(rng.integers(1, 5 if nine else 17))  # FP32 chunk limit 256 / 1024
         if form == "int8" and rng.random() < 0.2:
             kw["tc_pair"] = True
+        if form == "int8" and rng.random() < 0.2:
+            kw["tc_fused"] = 2
     return b, p, m, n, k, form, kw
 
 

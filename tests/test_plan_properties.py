@@ -59,15 +59,20 @@ def test_int8_plans_keep_fp32_chunks_and_int32_sums_exact(M, oracle, p, m, n, k)
     d = M.mwmm_plan_info(h)
     M.mwmm_plan_destroy(h)
     u = d["u"]
-    assert u == d["v"] == oracle.int8_words(p)
-    B = 256 ** (u - 1)  # u - 1 balanced digits, top digit in [-128, 128]
-    assert 128 * B + 127 * (B - 1) // 255 >= (p - 1) // 2  # every signed representative is reached
-    assert u <= -(-(p.bit_length()) // 8)  # at most ceil(b / 8) digits for a b-bit prime
+    bits = d["tc_digit_bits"]
+    # 9-bit digits exactly when they save a digit over 8-bit ones
+    assert bits == (9 if oracle.digit_words(p, 9) < oracle.digit_words(p, 8) else 8)
+    assert d["alpha"] == d["beta"] == 2 ** bits
+    assert u == d["v"] == oracle.digit_words(p, bits)
+    R, h = 2 ** bits, 2 ** (bits - 1)
+    B = R ** (u - 1)  # u - 1 balanced digits, top digit in [-h, h]
+    assert h * B + (h - 1) * (B - 1) // (R - 1) >= (p - 1) // 2  # every signed representative is reached
+    assert u <= -(-(p.bit_length()) // bits)  # at most ceil(b / bits) digits for a b-bit prime
     if u > 1:  # and the fewest: u - 1 digits miss the largest signed representative
-        B //= 256
-        assert 128 * B + 127 * (B - 1) // 255 < (p - 1) // 2
-    assert d["tc_chunk"] * 128 * 128 <= 2 ** 24  # FP32 chunk: every partial sum exact
-    assert d["kc"] * min(u, u) * 128 * 128 <= 2 ** 31 - 1 or k == 0  # INT32 sum of one K-range
+        B //= R
+        assert h * B + (h - 1) * (B - 1) // (R - 1) < (p - 1) // 2
+    assert d["tc_chunk"] * h * h <= 2 ** 24  # FP32 chunk: every partial sum exact
+    assert d["kc"] * min(u, u) * h * h <= 2 ** 31 - 1 or k == 0  # INT32 sum of one K-range
     assert d["nkc"] == (-(-k // d["kc"]) if k else 0)
     assert d["A_rows"] >= m and d["B_rows"] >= n and d["A_rows"] % 128 == 0
 
