@@ -1,5 +1,5 @@
 // INT8-word form with the reduction and the recombination fused into the
-// word-product kernel: C = sum_s 256^s S_s mod p is accumulated in the
+// word-product kernel: C = sum_s R^s S_s mod p (R the digit radix) is accumulated in the
 // epilogue as each diagonal sum S_s = sum_{i+j=s} A_i B_j completes, so no
 // sum ever leaves the SM (Alg. 5 scales and accumulates each word product as
 // it completes; here the products of one diagonal are first summed exactly,
