@@ -781,13 +781,13 @@ def main():
         traffic_per_launch = None if any(x is None for x in tr) else sum(tr) / len(tr)
     else:
         traffic_per_launch = None
-    roofline = {"bound": "tensor", "kernel": "gemm_tc_kernel (tcgen05.mma kind::f16, INT8 digits in bf16)",
+    roofline = {"bound": "tensor", "kernel": "gemm_tc_kernel (tcgen05.mma kind::f16, 8-bit digits in bf16 or 9-bit digits in fp16)",
                 "achieved": achieved, "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
                 "frac": achieved / peaks["bf16_tflops"], "traffic": traffic_per_launch,
                 "peak_kind": "%s bf16 dense burst (cuBLAS); sustained %.1f -> frac %.3f" % (
                     peak_kind, peaks.get("bf16_tflops_sustained", 0.0),
                     achieved / peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])),
-                "algorithmic": "2 u v m n k word-product flops per launch (u, v INT8 digits per side)"}
+                "algorithmic": "2 u v m n k word-product flops per launch (u, v digits per side)"}
 
     # FP64 pipe rate, measured here on the hot GPU (after the timed region):
     # the denominator of the FP64 form's pipe fraction
@@ -913,9 +913,10 @@ def main():
         line = {"metric": METRIC, "value": value, "unit": "GOP/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "int8-in-bf16",
-                "dtype_detail": "exact integer arithmetic throughout: 8-bit digits carried exactly in bf16 x bf16 -> "
-                                "FP32 tensor memory (exact, every partial sum <= 2^24) -> INT32 sums -> 64-bit "
-                                "integer recombination mod p; results bit-exact mod p",
+                "dtype_detail": "exact integer arithmetic throughout: 8-bit digits carried exactly in bf16 (9-bit "
+                                "digits in fp16 where they save a digit) -> FP32 tensor memory (exact, every "
+                                "partial sum <= 2^24) -> INT32 sums -> 64-bit integer recombination mod p; results "
+                                "bit-exact mod p",
                 "data": "synthetic (seeded, entries uniform in [0,p))",
                 "config": workload_config(args, bits),
                 "roofline": roofline, "cpu_baseline": cpu_baseline, "e2e": e2e,
