@@ -253,6 +253,29 @@ __device__ __forceinline__ void mma_bf16(uint32_t dtmem, uint64_t adesc, uint64_
 // quarter of its replay time).  Tile rows row0 + r >= rv and, per diagonal
 // block, columns >= cv (tile padding) are not stored; column c of the
 // accumulator is column c mod nb of diagonal s0 + c / nb.
+// Adds the 128 FP32 chunk sums of this thread's TMEM lane (columns t0..t0+127)
+// to its INT32 diagonal sums: 16 columns per load, the next load in flight
+// while the current block is converted and added.  Every value is an exact
+// integer with |x| <= 2^24, so cvt.rni is exact.  The conversions (a
+// quarter-rate instruction) spread the tensor-memory reads over most of the
+// next chunk's MMAs; measured, drains that read faster (an FP32 add of
+// 1.5 * 2^23 in place of the conversion, exact below 2^22) made the whole
+// kernel slower.
+__device__ __forceinline__ void drain_add(uint32_t t0, int32_t (&acc)[128]) {
+    uint32_t ra[16], rb[16];
+    tmem_ld16_async(t0, ra);
+    tmem_wait_ld16(ra);
+#pragma unroll
+    for (int jb = 0; jb < 8; ++jb) {
+        uint32_t(&cur)[16] = (jb & 1) ? rb : ra;
+        uint32_t(&nxt)[16] = (jb & 1) ? ra : rb;
+        if (jb + 1 < 8) tmem_ld16_async(t0 + (uint32_t)((jb + 1) * 16), nxt);
+#pragma unroll
+        for (int e = 0; e < 16; ++e) acc[jb * 16 + e] += __float2int_rn(__uint_as_float(cur[e]));
+        if (jb + 1 < 8) tmem_wait_ld16(nxt);
+    }
+}
+
 __device__ __forceinline__ void store_sums(const Item &it, const int32_t (&acc)[128], int32_t *stg, int lane, int row0,
                                            int col0) {
 #pragma unroll
@@ -427,15 +450,8 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_consta
                     break;
                 }
                 tc_fence_after();
-                if (half * 128 < it.nn) {  // this warp's columns hold products (warp-uniform)
-#pragma unroll
-                    for (int jb = 0; jb < 4; ++jb) {
-                        uint32_t r[32];
-                        tmem_ld32(tlane + (uint32_t)(buf * BN + jb * 32), r);
-#pragma unroll
-                        for (int e = 0; e < 32; ++e) acc[jb * 32 + e] += __float2int_rn(__uint_as_float(r[e]));
-                    }
-                }
+                if (half * 128 < it.nn)  // this warp's columns hold products (warp-uniform)
+                    drain_add(tlane + (uint32_t)(buf * BN), acc);
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&tempty[buf]);
@@ -647,13 +663,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS, 1)
                     break;
                 }
                 tc_fence_after();
-#pragma unroll
-                for (int jb = 0; jb < 4; ++jb) {
-                    uint32_t r[32];
-                    tmem_ld32(tlane + (uint32_t)(buf * BN + jb * 32), r);
-#pragma unroll
-                    for (int e = 0; e < 32; ++e) acc[jb * 32 + e] += __float2int_rn(__uint_as_float(r[e]));
-                }
+                drain_add(tlane + (uint32_t)(buf * BN), acc);
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive_cluster(lead_tempty + (uint32_t)(buf * sizeof(uint64_t)));
