@@ -75,9 +75,14 @@ __device__ __forceinline__ float byte_digit_float(uint32_t x, int i) {
 __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
     return __byte_perm(__float_as_uint(lo), __float_as_uint(hi), 0x7632u);
 }
-// Two small integers (exact in fp16) packed as fp16 x 2.
-__device__ __forceinline__ uint32_t pack_f16x2(float lo, float hi) {
-    const __half2 h = __floats2half2_rn(lo, hi);
+// Two small integers as fp16 x 2 without the conversion pipe: for |v| < 512
+// the fp16 with bit pattern 0x6600 + v is 1536 + v exactly (binade
+// [1024, 2048), unit spacing), so one packed fp16 subtraction of 1536 leaves
+// v exactly in both halves.  lo and hi are the patterns 0x6600 + v.
+__device__ __forceinline__ uint32_t f16x2_from_biased(uint32_t lo, uint32_t hi) {
+    const uint32_t packed = __byte_perm(lo, hi, 0x5410u);
+    const uint32_t k1536 = 0x66006600u;
+    const __half2 h = __hsub2(*reinterpret_cast<const __half2 *>(&packed), *reinterpret_cast<const __half2 *>(&k1536));
     return *reinterpret_cast<const uint32_t *>(&h);
 }
 
@@ -162,10 +167,12 @@ __device__ __forceinline__ float int8_digit(int64_t t, int w, bool last) {
     return byte_digit_float(half, w & 3);
 }
 // 9-bit digits the same way: c = 256 (1 + 512 + ... + 512^(u-2)), the lower
-// digits are the 9-bit fields of t minus 256, the top one t >> 9 (u-1).
-__device__ __forceinline__ float int9_digit(int64_t t, int w, bool last) {
-    if (last) return small_int_float((int)(t >> (9 * w)));
-    return small_int_float((int)(((uint64_t)t >> (9 * w)) & 511u) - 256);
+// digits are the 9-bit fields of t minus 256, the top one t >> 9 (u-1)
+// (|digit| <= 256).  Returned as the fp16 pattern 0x6600 + digit: a lower
+// digit's field f gives 0x6600 + f - 256 = 0x6500 + f.
+__device__ __forceinline__ uint32_t int9_digit_biased(int64_t t, int w, bool last) {
+    if (last) return 0x6600u + (uint32_t)(int)(t >> (9 * w));
+    return 0x6500u + (uint32_t)(((uint64_t)t >> (9 * w)) & 511u);
 }
 
 // FP64 form: a 64 x 64 tile covers 4 k-blocks of 16 doubles, 8 granules each.
@@ -205,15 +212,14 @@ __device__ __forceinline__ void split_int8_tile(const SplitParams &P, uint64_t (
         const int64_t r = r0 + rr;
         if (r >= P.rows_pad) continue;  // a last row tile may be partial (rows_pad 16 or 32)
         // word w of the unit's 8 entries, packed bf16 (or fp16), to its swizzled 16-byte granule
+        auto dst_of = [&](int w) {
+            return reinterpret_cast<uint4 *>(P.out + ((int64_t)(w + P.wpad) * P.wstride + kb * P.kstride + r) *
+                                                         kTileBytes +
+                                             ((g ^ (int)(r & 7)) * 16));
+        };
         auto store = [&](int w, const float (&f)[8]) {
-            uint8_t *dst = P.out + ((int64_t)(w + P.wpad) * P.wstride + kb * P.kstride + r) * kTileBytes +
-                           ((g ^ (int)(r & 7)) * 16);
-            if (P.bits == 9)
-                *reinterpret_cast<uint4 *>(dst) = make_uint4(pack_f16x2(f[0], f[1]), pack_f16x2(f[2], f[3]),
-                                                             pack_f16x2(f[4], f[5]), pack_f16x2(f[6], f[7]));
-            else
-                *reinterpret_cast<uint4 *>(dst) = make_uint4(pack_bf16x2(f[0], f[1]), pack_bf16x2(f[2], f[3]),
-                                                             pack_bf16x2(f[4], f[5]), pack_bf16x2(f[6], f[7]));
+            *dst_of(w) = make_uint4(pack_bf16x2(f[0], f[1]), pack_bf16x2(f[2], f[3]), pack_bf16x2(f[4], f[5]),
+                                    pack_bf16x2(f[6], f[7]));
         };
         if (P.crt) {
             float xl[8][5];  // 11-bit limbs
@@ -236,15 +242,18 @@ __device__ __forceinline__ void split_int8_tile(const SplitParams &P, uint64_t (
             }
             for (int w = 0; w < P.words; ++w) {
                 const bool last = (w == P.words - 1);
-                float f[8];
                 if (P.bits == 9) {
+                    uint32_t h[8];
 #pragma unroll
-                    for (int e = 0; e < 8; ++e) f[e] = int9_digit(t[e], w, last);
+                    for (int e = 0; e < 8; ++e) h[e] = int9_digit_biased(t[e], w, last);
+                    *dst_of(w) = make_uint4(f16x2_from_biased(h[0], h[1]), f16x2_from_biased(h[2], h[3]),
+                                            f16x2_from_biased(h[4], h[5]), f16x2_from_biased(h[6], h[7]));
                 } else {
+                    float f[8];
 #pragma unroll
                     for (int e = 0; e < 8; ++e) f[e] = int8_digit(t[e], w, last);
+                    store(w, f);
                 }
-                store(w, f);
             }
         }
         for (int z = 0; z < P.wpad; ++z) {  // the zero words on both sides
