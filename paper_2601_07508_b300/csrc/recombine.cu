@@ -132,11 +132,9 @@ __global__ void __launch_bounds__(256) recombine_kernel(const __grid_constant__ 
 // register cap only adds spills and scheduling constraints).  Same arithmetic
 // as the nkc == 1 branch of recombine_rows.
 template <int S, bool kWide, int G>
-__device__ __forceinline__ void recombine_rows_s(const RecParams &P) {
-    const int64_t c0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4;
-    if (c0 >= P.n) return;
+__device__ __forceinline__ void recombine_quad_s(const RecParams &P, int64_t row, int64_t c0) {
     const int64_t plane = P.A_rows * P.B_rows;
-    for (int64_t row = blockIdx.y; row < P.m; row += gridDim.y) {
+    {
         const int32_t *src = P.S + row * P.B_rows + c0;
         uint64_t A0[4] = {0, 0, 0, 0}, A1[4] = {0, 0, 0, 0};
 #pragma unroll
@@ -179,6 +177,13 @@ __device__ __forceinline__ void recombine_rows_s(const RecParams &P) {
     }
 }
 
+template <int S, bool kWide, int G>
+__device__ __forceinline__ void recombine_rows_s(const RecParams &P) {
+    const int64_t c0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4;
+    if (c0 >= P.n) return;
+    for (int64_t row = blockIdx.y; row < P.m; row += gridDim.y) recombine_quad_s<S, kWide, G>(P, row, c0);
+}
+
 template <int S, bool kWide>
 __global__ void __launch_bounds__(256) recombine_kernel_s(const __grid_constant__ RecParams P) {
     recombine_rows_s<S, kWide, S>(P);
@@ -204,11 +209,34 @@ void launch_recombine_s(const RecParams &P, dim3 grid, cudaStream_t st) {
     }
 }
 
+// The (row, 4-column group) units of one batched block with the sum count
+// known at compile time (the single-product kernels' arithmetic and loads).
+template <int S, bool kWide>
+__device__ __forceinline__ void batched_units_s(const RecParams &P, int64_t cb, int64_t y0, int64_t rows,
+                                                int64_t groups) {
+    for (int64_t u = threadIdx.x; u < rows * groups; u += blockDim.x)
+        recombine_quad_s<S, kWide, (S < 5 ? S : 4)>(P, y0 + u / groups, cb + (u % groups) * 4);
+}
+
+template <int S>
+__device__ __forceinline__ bool batched_try_s(const RecParams &P, int64_t cb, int64_t y0, int64_t rows,
+                                              int64_t groups) {
+    if (P.nsums != S) return false;
+    if (P.mu90)
+        batched_units_s<S, true>(P, cb, y0, rows, groups);
+    else
+        batched_units_s<S, false>(P, cb, y0, rows, groups);
+    return true;
+}
+
 // Batched: block b handles columns [1024 z, 1024 z + 1024) of rows
 // [y0, y0 + 8) of problem jobs[b] = (problem, y0, z, 0); its threads take the
 // (row, 4-column group) units of that block in turn, so narrow problems keep
-// every thread busy.
-__global__ void __launch_bounds__(256) recombine_batched_kernel(const RecParams *probs, const int4 *jobs) {
+// every thread busy.  One K-range with an odd sum count of 3 to 15 (u = v
+// digits) takes a path specialised on that count (block-uniform branch);
+// anything else the generic loop.  Held to 64 registers like the
+// single-product kernels from 8 sums on (4 blocks per SM).
+__global__ void __launch_bounds__(256, 4) recombine_batched_kernel(const RecParams *probs, const int4 *jobs) {
     __shared__ __align__(16) RecParams P;  // staged once (all threads copy): the loops read it many times
     const int4 j = jobs[blockIdx.x];
     {
@@ -221,6 +249,11 @@ __global__ void __launch_bounds__(256) recombine_batched_kernel(const RecParams 
     const int64_t width = P.n - cb < 1024 ? P.n - cb : 1024;
     const int64_t rows = P.m - j.y < 8 ? P.m - j.y : 8;
     const int64_t groups = (width + 3) / 4;
+    if (P.nkc == 1 && (batched_try_s<3>(P, cb, j.y, rows, groups) || batched_try_s<5>(P, cb, j.y, rows, groups) ||
+                       batched_try_s<7>(P, cb, j.y, rows, groups) || batched_try_s<9>(P, cb, j.y, rows, groups) ||
+                       batched_try_s<11>(P, cb, j.y, rows, groups) || batched_try_s<13>(P, cb, j.y, rows, groups) ||
+                       batched_try_s<15>(P, cb, j.y, rows, groups)))
+        return;
     for (int64_t u = threadIdx.x; u < rows * groups; u += blockDim.x)
         recombine_rows(P, cb + (u % groups) * 4, j.y + u / groups, P.m);
 }
