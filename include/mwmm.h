@@ -139,7 +139,16 @@ typedef struct {
                          <= 256 products, INT32 sums of <= 32767 products);
                          0 = 9 when that needs fewer digits (u, v = 0 only),
                          else 8 */
-    int32_t reserved[1];
+    int32_t tc_fill;  /* INT8 and CRT forms with the diagonal sums in the
+                         workspace and kc = 0: 0 (default) = when one K
+                         range would leave the SMs under-filled (the longest
+                         work item -- a tile's diagonal, up to min(u, v) word
+                         pairs, over all of K -- longer than an SM's share of
+                         the work), shorten the K ranges until it is not
+                         (more INT32 sum planes, all added by the
+                         recombination); 1 = never.  Batches, the serving
+                         loop and mwmm_matmul_noalloc plan with 1: their
+                         launches interleave many products */
 } mwmm_plan_opts;
 
 /* What a plan decided (mwmm_plan_info). */

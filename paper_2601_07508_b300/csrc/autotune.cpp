@@ -168,6 +168,7 @@ void candidates(int form_req, int64_t m, int64_t n, int64_t k, uint64_t p, bool 
     const bool want_fp64 = (form_req == MWMM_FORM_AUTO && !batch) || form_req == MWMM_FORM_FP64;
     mwmm_plan_opts z;
     std::memset(&z, 0, sizeof(z));
+    z.tc_fill = batch ? 1 : 0;  // a batch's items fill the SMs together
     if (want_crt) {
         Plan crt;
         if (make_plan(&crt, m, n, k, p, 0, 0, MWMM_FORM_CRT8, &z) == MWMM_OK) {

@@ -398,6 +398,7 @@ mwmm_status mwmm_batch_create(mwmm_batch_t *out, const mwmm_problem *probs, int 
         o.tc_pair = 0;
         o.tc_fused = 1;    // table items write diagonal sums for the batched recombination
         o.ksplit = 1;      // batched FP64 tiles run the whole K range
+        o.tc_fill = 1;     // the batch's many items fill the SMs; no K ranges for that
         mwmm_status st = mwmm::make_plan(&b->plans[i], q.m, q.n, q.k, q.p, u, v, pf, &o);
         if (st != MWMM_OK && (u || v || o.kc)) {  // the group's words do not fit this prime: plan it alone
             o.kc = 0;

@@ -74,7 +74,10 @@ extern "C" mwmm_status mwmm_matmul_noalloc(int64_t m, int64_t n, int64_t k, uint
                                            int64_t ldc, void *stream) {
     using namespace mwmm;
     Plan pl;  // on the stack: planning allocates nothing
-    mwmm_status st = make_plan(&pl, m, n, k, p, 0, 0, MWMM_FORM_INT8, nullptr);
+    mwmm_plan_opts o0;
+    std::memset(&o0, 0, sizeof(o0));
+    o0.tc_fill = 1;  // no extra sum planes in the fixed scratch
+    mwmm_status st = make_plan(&pl, m, n, k, p, 0, 0, MWMM_FORM_INT8, &o0);
     if (st != MWMM_OK) return st;
     if (m == 0 || n == 0) return MWMM_OK;
     if (!dC || (k > 0 && (!dA || !dB)) || lda < (k > 0 ? k : 1) || ldb < (n > 0 ? n : 1) || ldc < n)

@@ -74,27 +74,33 @@ int int8_digits(uint64_t p) { return signed_digits(p, 8); }
 
 static int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
-// Cost model of the two tensor forms (seconds), calibrated on 4096^3 products
-// on B300 (7 to 16 moduli, 3 to 7 digits a side): word products at ~1.5
-// PFLOP/s of 2 m n k per product; the INT8 split (8 B read + 2 B per digit
-// written per entry) at ~5 TB/s and recombination (4 B per sum read + 8 B
-// written per output) at ~6 TB/s; the CRT split at 8 B per entry plus
-// ~0.38 ps per (entry, modulus), the CRT reconstruction at 8 B per output
-// plus ~1.0 ps per (output, modulus).
+// Cost model of the two tensor forms (seconds), calibrated on B300 on 4096^3
+// products (7 to 16 moduli, 3 to 7 digits a side) and on the 512-instance
+// batch (m, n, k in [128, 2048], 50-bit primes).  The word products take the
+// longer of their tensor time (~1.5 PFLOP/s of 2 m n k per product; 9-bit
+// digits drain their 256-product FP32 chunks four times as often, 12-15%
+// more per product) and their own DRAM traffic at ~6 TB/s: the 16-bit words,
+// read about 1.8 times over (measured on the batch), and the INT32 sums
+// written once.  Small-k products of many moduli are bound by the latter
+// (batch: the CRT instances' word products ran at 63% of the INT8 ones'
+// tensor rate).  Then the INT8 split (8 B read + 2 B per digit written per
+// entry) at ~5 TB/s and recombination (4 B per sum read + 8 B written per
+// output) at ~6 TB/s; the CRT split at 8 B per entry plus ~0.5 ps per
+// (entry, modulus), the CRT reconstruction at 8 B per output plus ~1.2 ps
+// per (output, modulus).
 static double tensor_form_cost(const Plan &pl) {
-    const double mnk2 = 2.0 * pl.m * pl.n * pl.k, mk_kn = (double)pl.m * pl.k + (double)pl.k * pl.n,
-                 mn = (double)pl.m * pl.n;
-    constexpr double kTensor = 1.5e15, kHbm = 5.0e12, kHbmRec = 6.0e12;
+    const double mnk2 = 2.0 * pl.m * pl.n * pl.k, mk = (double)pl.m * pl.k, kn = (double)pl.k * pl.n,
+                 mk_kn = mk + kn, mn = (double)pl.m * pl.n;
+    constexpr double kTensor = 1.5e15, kHbm = 5.0e12, kHbmRec = 6.0e12, kHbmGemm = 6.0e12, kWordReads = 1.8;
     if (pl.form == MWMM_FORM_CRT8) {
         const double s = pl.crt_s;
-        return s * mnk2 / kTensor + mk_kn * (8.0 / kHbm + s * 0.38e-12) +
-               mn * (8.0 / kHbm + s * (1.0e-12 + 4.0 * (pl.nkc - 1) / kHbm));
+        const double gemm = std::max(s * mnk2 / kTensor, (2.0 * s * mk_kn * kWordReads + 4.0 * s * mn * pl.nkc) / kHbmGemm);
+        return gemm + mk_kn * (8.0 / kHbm + s * 0.5e-12) + mn * (8.0 / kHbm + s * (1.2e-12 + 4.0 * (pl.nkc - 1) / kHbm));
     }
-    // 9-bit digits: 256-product FP32 chunks, drained four times as often
-    // (measured 12-15% more time per word product)
     const double drain = pl.digit_bits == 9 ? 1.15 : 1.0;
-    return (double)pl.u * pl.v * mnk2 * drain / kTensor + mk_kn * (8.0 + 2.0 * pl.u) / kHbm +
-           mn * (4.0 * pl.nsums * pl.nkc + 8.0) / kHbmRec;
+    const double gemm = std::max((double)pl.u * pl.v * mnk2 * drain / kTensor,
+                                 (2.0 * (mk * pl.u + kn * pl.v) * kWordReads + 4.0 * mn * pl.nsums * pl.nkc) / kHbmGemm);
+    return gemm + mk_kn * (8.0 + 2.0 * pl.u) / kHbm + mn * (4.0 * pl.nsums * pl.nkc + 8.0) / kHbmRec;
 }
 
 // Primes below 256, largest first (moduli of the CRT form).
@@ -326,10 +332,55 @@ mwmm_status make_plan(Plan *pl, int64_t m, int64_t n, int64_t k, uint64_t p, int
         }
         int64_t kpad = round_up(k, kTcKB);
         if (kc > kpad) kc = kpad > 0 ? kpad : kTcKB;
-        P.kc = kc;
-        P.nkc = k > 0 ? (int)ceil_div(k, kc) : 0;
         P.kb_elems = kTcKB;
         P.nkb = ceil_div(k, kTcKB);
+        // Under-filled products: the persistent kernel's time is at least
+        // its longest item (a tile's diagonal window: up to min(u, v) pairs
+        // x the K range's k-blocks; one pair for the CRT form), so shorter K
+        // ranges (more items, more sum planes) can finish sooner, while the
+        // extra planes cost recombination time.  The K-range count is the
+        // argmin of a model fitted on B300 (48 shapes from 64 x 64 x 4096 to
+        // 2048^2 x 1024, 20 and 52 bits, mean 2% and at most 19% slower than
+        // the best count measured): word products max(longest item, an SM's
+        // share of all items), with a fixed cost per item (its drain and
+        // 128 KB store: 4 us INT8, 0.5 us CRT), plus reading the sum planes
+        // (one K range: 5.7 / 3 TB/s; several, through the Horner path:
+        // 1.5 / 0.5 TB/s for INT8 / CRT).
+        if (o.tc_fill < 0 || o.tc_fill > 1) return MWMM_ERR_ARG;
+        const bool fused_req = form == MWMM_FORM_INT8 && n > kTcBN / 2 && o.tc_fused == 2;
+        if (o.kc == 0 && o.tc_fill == 0 && !fused_req && k > 0 && m > 0 && n > 0) {
+            const bool crt = form == MWMM_FORM_CRT8;
+            constexpr double kSms = 148.0;
+            const double t_kb = 2.0 * kTcBM * kTcBN * kTcKB / (1.5e15 / kSms) * (P.digit_bits == 9 ? 1.15 : 1.0);
+            const double c_item = crt ? 0.5e-6 : 4.0e-6, r_one = crt ? 3.0e12 : 5.7e12, r_many = crt ? 0.5e12 : 1.5e12;
+            int64_t tiles = ceil_div(m, kTcBM), nwin = P.nsums;
+            if (n > kTcBN / 2) {
+                tiles *= ceil_div(n, kTcBN);
+            } else if (!crt) {  // narrow n: 256 / nb diagonals side by side in one tile
+                int64_t nb = 16;
+                while (nb < n) nb *= 2;
+                nwin = ceil_div(P.nsums, std::min<int64_t>(kTcBN / nb, P.nsums));
+            }
+            const double pairs = crt ? (double)P.crt_s : (double)u * v;
+            const double total_kb = (double)tiles * pairs * (double)P.nkb, mn = (double)m * n;
+            auto cost = [&](int64_t kcb) {  // kcb: k-blocks per K range
+                const int64_t nr = ceil_div(P.nkb, kcb);
+                const double items = (double)(tiles * nwin * nr);
+                const double gemm = std::max(w * (double)kcb * t_kb + c_item, (total_kb * t_kb + items * c_item) / kSms);
+                return gemm + (double)P.nsums * nr * mn * 4.0 / (nr == 1 ? r_one : r_many);
+            };
+            int64_t best_kb = kc / kTcKB;
+            double best = cost(best_kb);
+            for (int64_t nr = ceil_div(P.nkb, best_kb) + 1; nr <= 64 && nr <= P.nkb; ++nr) {
+                const int64_t kcb = ceil_div(P.nkb, nr);
+                if (ceil_div(P.nkb, kcb) != nr) continue;  // the same ranges as a smaller count
+                const double c = cost(kcb);
+                if (c < best) { best = c; best_kb = kcb; }
+            }
+            kc = best_kb * kTcKB;
+        }
+        P.kc = kc;
+        P.nkc = k > 0 ? (int)ceil_div(k, kc) : 0;
         // Column tiles: 256 wide when n > 128; narrower n is padded to 16, 32,
         // 64 or 128 and one tile then carries 256 / nb diagonals side by side.
         P.tc_nb = kTcBN;
@@ -423,6 +474,7 @@ int choose_tensor_form(int64_t m, int64_t n, int64_t k, uint64_t p) {
     mwmm_plan_opts z;
     std::memset(&z, 0, sizeof(z));
     z.tc_fused = 1;  // batches and the serving loop run the diagonal sums through the workspace
+    z.tc_fill = 1;   // ... and interleave many products in one launch
     Plan a, c;
     if (make_plan(&a, m, n, k, p, 0, 0, MWMM_FORM_INT8, &z) != MWMM_OK) return MWMM_FORM_INT8;
     if (make_plan(&c, m, n, k, p, 0, 0, MWMM_FORM_CRT8, &z) != MWMM_OK) return MWMM_FORM_INT8;

@@ -41,7 +41,7 @@ class PlanOpts(ctypes.Structure):
                 ("kc", ctypes.c_int64), ("tc_pair", ctypes.c_int32),
                 ("f64_concat", ctypes.c_int32), ("ksplit", ctypes.c_int32), ("autotune", ctypes.c_int32),
                 ("tc_fused", ctypes.c_int32), ("tc_seg", ctypes.c_int32), ("tc_digit_bits", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 1)]
+                ("tc_fill", ctypes.c_int32)]
 
 
 class Timing(ctypes.Structure):
@@ -223,7 +223,7 @@ def _ld(t) -> int:
 def mwmm_plan(m: int, n: int, k: int, p: int, u: int = 0, v: int = 0, form="auto", lam: int = 0,
               validate: bool = False, tc_chunk: int = 0, kc: int = 0, tc_pair: bool = False,
               f64_concat: int = 0, ksplit: int = 0, tc_fused: int = 0, tc_seg: int = 0,
-              tc_digit_bits: int = 0) -> int:
+              tc_digit_bits: int = 0, tc_fill: int = 0) -> int:
     if isinstance(form, str):
         form = FORMS[form]
     h = _vp()
@@ -238,6 +238,7 @@ def mwmm_plan(m: int, n: int, k: int, p: int, u: int = 0, v: int = 0, form="auto
     o.tc_fused = tc_fused
     o.tc_seg = tc_seg
     o.tc_digit_bits = tc_digit_bits
+    o.tc_fill = tc_fill
     _check(lib().mwmm_plan(ctypes.byref(h), m, n, k, p, u, v, form, ctypes.byref(o)), "mwmm_plan")
     return h.value
 
@@ -605,9 +606,9 @@ class Plan:
     def __init__(self, m: int, n: int, k: int, p: int, u: int = 0, v: int = 0, form="auto", lam: int = 0,
                  validate: bool = False, tc_chunk: int = 0, kc: int = 0, tc_pair: bool = False,
                  f64_concat: int = 0, ksplit: int = 0, tc_fused: int = 0, tc_seg: int = 0,
-                 tc_digit_bits: int = 0):
+                 tc_digit_bits: int = 0, tc_fill: int = 0):
         self.handle = mwmm_plan(m, n, k, p, u, v, form, lam, validate, tc_chunk, kc, tc_pair, f64_concat, ksplit,
-                                tc_fused, tc_seg, tc_digit_bits)
+                                tc_fused, tc_seg, tc_digit_bits, tc_fill)
         self.info = mwmm_plan_info(self.handle)
         self.workspace = None
 

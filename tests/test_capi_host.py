@@ -343,6 +343,24 @@ def test_crt_plan_errors(M):
     assert e.value.status == 1
 
 
+@pytest.mark.parametrize("form", ["int8", "crt8"])
+def test_underfill_k_split_plans(M, form):
+    """tc_fill = 0 (default) shortens the K ranges of a product whose longest
+    item (a diagonal's pairs over all of K) exceeds an SM's share of the work;
+    large products, explicit kc, tc_fill = 1 and the fused form keep the
+    INT32-bound K range."""
+    p = SWEEP[26]
+    small = M.Plan(256, 256, 4096, p, form=form).info
+    assert small["nkc"] > 1 and small["kc"] % 64 == 0 and small["nkc"] == -(-4096 // small["kc"])
+    assert M.Plan(256, 256, 4096, p, form=form, tc_fill=1).info["nkc"] == 1
+    assert M.Plan(256, 256, 4096, p, form=form, kc=4096).info["nkc"] == 1
+    assert M.Plan(4096, 4096, 4096, p, form=form).info["nkc"] == 1
+    if form == "int8":
+        assert M.Plan(256, 256, 4096, p, form=form, tc_fused=2).info["tc_fused"] == 1
+    with pytest.raises(M.MwmmError):
+        M.Plan(256, 256, 4096, p, form=form, tc_fill=2)
+
+
 def test_tensor_form_choice_follows_the_cost_model(M):
     """AUTO's tensor form for batches and serving: at 4096^3 the digit form
     at 23-27 bits (9 digit products, 9-bit digits from 25 bits, against 8-9

@@ -161,6 +161,24 @@ def test_crt_form_extremes_and_k_ranges(M, oracle, b):
     assert np.array_equal(C, oracle.matmul_mod(A, B, p))
 
 
+@pytest.mark.parametrize("form", ["int8", "crt8"])
+@pytest.mark.parametrize("b", [20, 26, 52])
+@pytest.mark.parametrize("shape", [(512, 512, 2048), (64, 64, 4096), (200, 300, 1500)])
+def test_underfilled_products_split_k(M, oracle, form, b, shape):
+    """A product whose work items would not fill the SMs plans shorter K
+    ranges (more items, more sum planes added by the recombination); the
+    result equals the oracle's and the one-K-range plan's."""
+    m, n, k = shape
+    p = SWEEP[b]
+    A, B = inputs.problem(b + k, m, n, k, p)
+    C, plan = gpu_product(M, A, B, p, form=form)
+    C1, plan1 = gpu_product(M, A, B, p, form=form, tc_fill=1)
+    assert plan1.info["nkc"] == 1 and plan.info["nkc"] >= 1
+    assert form == "crt8" or plan.info["nkc"] > 1  # a diagonal's pairs make INT8 items long
+    want = oracle.matmul_mod(A, B, p)
+    assert np.array_equal(C, want) and np.array_equal(C1, want)
+
+
 @pytest.mark.parametrize("b", [20, 52])
 def test_crt_form_int32_sums_at_their_bound(M, oracle, b):
     """k at the INT32 K-range limit with constant columns, so each sum
@@ -168,7 +186,7 @@ def test_crt_form_int32_sums_at_their_bound(M, oracle, b):
     sums are taken over the whole 32-bit range."""
     p = SWEEP[b]
     k = 131008
-    plan = M.Plan(2, 3, k, p, form="crt8")
+    plan = M.Plan(2, 3, k, p, form="crt8", tc_fill=1)  # one K range: no split for the SMs' sake
     assert plan.info["nkc"] == 1
     m0 = plan.info["crt_m"][0]
     cols = np.array([p - 1, (m0 + 1) // 2, (m0 - 1) // 2], dtype=np.uint64)  # d = -1, -(m0-1)/2, (m0-1)/2 mod m0
@@ -184,7 +202,7 @@ def test_crt_residue_words_and_sums_match_oracle(M, oracle):
     p = SWEEP[48]
     m, n, k = 130, 260, 300
     A, B = inputs.problem(79, m, n, k, p)
-    plan = M.Plan(m, n, k, p, form="crt8")
+    plan = M.Plan(m, n, k, p, form="crt8", tc_fill=1)
     ws = plan.alloc_workspace()
     plan.matmul(dev(A), dev(B))
     assert plan.check() == 0
