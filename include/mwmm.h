@@ -449,7 +449,7 @@ void mwmm_serve_destroy(mwmm_server_t server);
  * library reserves statically on each GPU where this code is loaded, held
  * until the process exits; the caller passes only A, B and C (device
  * pointers, same conventions as mwmm_matmul).  The first call on a device
- * looks up that array's address; make it before capturing any stream.
+ * looks up that array's address and caches it.
  * Every call shares the one array, so calls that overlap on the GPU race:
  * issue them one at a time per device.  Synchronous: returns once C is
  * written.  Calls no cudaMalloc/cudaFree or other allocating routine.

@@ -20,8 +20,7 @@
 //     loaded on a GPU (at the latest on the first call on that GPU), the GPU
 //     holds the 64 MiB until the process exits.
 //   - The first call on each device looks up the array's device address
-//     (cudaGetSymbolAddress, with that device current) and caches it; make
-//     that first call before capturing any stream.
+//     (cudaGetSymbolAddress, with that device current) and caches it.
 //   - Every call uses the same array and it keeps the previous call's
 //     contents.  The kernels rewrite every word and sum they later read
 //     (padding included), and the error words are cleared at the start of
