@@ -276,20 +276,34 @@ __global__ void __launch_bounds__(256) split_int8_kernel(const __grid_constant__
     split_int8_tile(P, tile, blockIdx.y, blockIdx.x);
 }
 
-// Batched: block b splits tile blocks[b] = (job, tile row, tile col) of jobs[job].
+// Batched: CTA c splits the tiles blocks[c * per, c * per + per) (each
+// (job, tile row, tile col) of jobs[job]; a job's tiles are consecutive in
+// the list).  The job's parameters are staged into shared memory only when
+// the job changes: a CTA per tile spent a good part of its short life on
+// that copy and its barrier (measured: 4.3 TB/s against 6.2 for the
+// single-product split).
+constexpr int kSplitTilesPerCta = 8;
+
 __global__ void __launch_bounds__(256, 4) split_batched_kernel(const SplitParams *jobs, const int4 *blocks,
-                                                            int fp64) {
+                                                            int nblocks, int fp64) {
     __shared__ uint64_t tile[kST][kST + 1];
-    __shared__ __align__(16) SplitParams P;  // staged once (all threads copy): the loops read it many times
-    const int4 bl = blocks[blockIdx.x];
-    {
-        const uint32_t *src = reinterpret_cast<const uint32_t *>(jobs + bl.x);
-        uint32_t *dst = reinterpret_cast<uint32_t *>(&P);
-        for (int w = threadIdx.x; w < (int)(sizeof(SplitParams) / 4); w += blockDim.x) dst[w] = src[w];
+    __shared__ __align__(16) SplitParams P;  // the loops read it many times
+    const int b0 = blockIdx.x * kSplitTilesPerCta;
+    const int b1 = b0 + kSplitTilesPerCta < nblocks ? b0 + kSplitTilesPerCta : nblocks;
+    int job = -1;
+    for (int b = b0; b < b1; ++b) {
+        const int4 bl = blocks[b];
+        __syncthreads();  // every thread is done with the previous tile (and P)
+        if (bl.x != job) {  // block-uniform
+            const uint32_t *src = reinterpret_cast<const uint32_t *>(jobs + bl.x);
+            uint32_t *dst = reinterpret_cast<uint32_t *>(&P);
+            for (int w = threadIdx.x; w < (int)(sizeof(SplitParams) / 4); w += blockDim.x) dst[w] = src[w];
+            job = bl.x;
+            __syncthreads();
+        }
+        if (fp64) split_fp64_tile(P, tile, bl.y, bl.z);
+        else split_int8_tile(P, tile, bl.y, bl.z);
     }
-    __syncthreads();
-    if (fp64) split_fp64_tile(P, tile, bl.y, bl.z);
-    else split_int8_tile(P, tile, bl.y, bl.z);
 }
 
 SplitParams make_split_params(const Plan &pl, int side, const uint64_t *M, int64_t ld, void *words) {
@@ -353,8 +367,9 @@ void split_job(const Plan &pl, int side, const uint64_t *M, int64_t ld, void *wo
 
 int launch_split_batched(const void *jobs, const int *blocks, int nblocks, int fp64, void *stream) {
     if (nblocks == 0) return 0;
-    split_batched_kernel<<<nblocks, 256, 0, static_cast<cudaStream_t>(stream)>>>(
-        static_cast<const SplitParams *>(jobs), reinterpret_cast<const int4 *>(blocks), fp64);
+    const int ctas = (nblocks + kSplitTilesPerCta - 1) / kSplitTilesPerCta;
+    split_batched_kernel<<<ctas, 256, 0, static_cast<cudaStream_t>(stream)>>>(
+        static_cast<const SplitParams *>(jobs), reinterpret_cast<const int4 *>(blocks), nblocks, fp64);
     return (int)cudaGetLastError();
 }
 
