@@ -184,6 +184,12 @@ typedef struct {
      * g ^ (r mod 8).  Element type: double (FP64 form, kb_elems = 16) or
      * bf16 holding an integer digit (INT8 form, kb_elems = 64).  Padding is 0.
      * INT8 form: S (int32) at S_off, laid out [nsums][nkc][A_rows][B_rows];
+     * unfused, then 256 bytes (the word-product kernel's item counter) at
+     * T = S_off + the sums' bytes rounded up to 256; with tc_cert_chunk > 0,
+     * the squared-digit maxima (uint32) at T + 256: A's laid out
+     * [u][nkb][A_rows / 64], then, from T + 256 + (u nkb (A_rows / 64) 4
+     * rounded up to 256), B's laid out [v][nkb][B_rows / 64] (for each 64-row
+     * group, the largest sum over the k-block of a row's squared digits).
      * fused (tc_fused = 1): nothing at S_off unless ksplit > 1, then the K
      * parts' residues (uint64) laid out [ksplit][m][n rounded up to even].
      * FP64 form with ksplit > 1: the partial results of the K ranges
@@ -203,7 +209,11 @@ typedef struct {
     uint32_t crt_m[24];     /* CRT form: the moduli m_0 > m_1 > ... (u of them); word i of A and of B
                                holds the signed residues modulo m_i, sum plane i their product */
     int32_t tc_digit_bits;  /* INT8: 8 (bf16 words) or 9 (fp16 words); alpha = beta = 2^tc_digit_bits */
-    int32_t pad2;
+    int32_t tc_cert_chunk;  /* INT8, 9-bit digits, 256-wide column tiles: the
+                               FP32 chunk (512 products) an item runs when the
+                               splits' sums of squared digits certify that no
+                               partial sum can exceed 2^24 (Cauchy-Schwarz);
+                               items that fail keep tc_chunk.  0: not used */
 } mwmm_plan_desc;
 
 /* Plan a product of an m x k by a k x n matrix mod p.

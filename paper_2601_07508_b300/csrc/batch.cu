@@ -196,8 +196,8 @@ void build_batch_tables(const Plan *plans, const mwmm_problem *probs, uint8_t *c
 int launch_product(const Plan &pl, const uint64_t *dA, int64_t lda, const uint64_t *dB, int64_t ldb, uint64_t *dC,
                    int64_t ldc, uint8_t *ws, void *stream) {
     if (pl.m == 0 || pl.n == 0 || pl.k == 0) return 0;
-    int e = launch_split(pl, 0, dA, lda, ws + pl.A_off, stream);
-    if (!e) e = launch_split(pl, 1, dB, ldb, ws + pl.B_off, stream);
+    int e = launch_split(pl, 0, dA, lda, ws + pl.A_off, stream, plan_sq(pl, ws, 0));
+    if (!e) e = launch_split(pl, 1, dB, ldb, ws + pl.B_off, stream, plan_sq(pl, ws, 1));
     if (e) return e;
     if (pl.form == MWMM_FORM_FP64)
         return launch_gemm_fp64(pl, ws + pl.A_off, ws + pl.B_off, dC, ldc, reinterpret_cast<uint64_t *>(ws + pl.S_off),
@@ -210,7 +210,7 @@ int launch_tensor_products(const Plan &pl, uint8_t *ws, uint64_t *C, int64_t ldc
         return launch_gemm_tc_fused(pl, ws + pl.A_off, ws + pl.B_off, C, ldc, reinterpret_cast<uint64_t *>(ws + pl.S_off),
                                     err, stream);
     int32_t *S = reinterpret_cast<int32_t *>(ws + pl.S_off);
-    int e = launch_gemm_tc(pl, ws + pl.A_off, ws + pl.B_off, S, err, stream);
+    int e = launch_gemm_tc(pl, ws + pl.A_off, ws + pl.B_off, S, err, stream, plan_sq(pl, ws, 0), plan_sq(pl, ws, 1));
     if (!e) e = launch_recombine(pl, S, C, ldc, stream);
     return e;
 }

@@ -122,10 +122,10 @@ mwmm_status run_product(mwmm_plan_s *h, const uint64_t *dA, int64_t lda, const u
     mwmm_status st = take_events(h, pe);
     if (st != MWMM_OK) return st;
     rec(pe.ev[0], s);
-    int e = dA ? mwmm::launch_split(pl, 0, dA, lda, ws + pl.A_off, stream) : 0;
+    int e = dA ? mwmm::launch_split(pl, 0, dA, lda, ws + pl.A_off, stream, mwmm::plan_sq(pl, ws, 0)) : 0;
     if (e) return cuda_status(e);
     rec(pe.ev[1], s);
-    e = mwmm::launch_split(pl, 1, dB, ldb, ws + pl.B_off, stream);
+    e = mwmm::launch_split(pl, 1, dB, ldb, ws + pl.B_off, stream, mwmm::plan_sq(pl, ws, 1));
     if (e) return cuda_status(e);
     rec(pe.ev[2], s);
     if (pl.form == MWMM_FORM_FP64) {
@@ -145,7 +145,8 @@ mwmm_status run_product(mwmm_plan_s *h, const uint64_t *dA, int64_t lda, const u
         return cuda_status(e);
     }
     int32_t *S = reinterpret_cast<int32_t *>(ws + pl.S_off);
-    e = mwmm::launch_gemm_tc(pl, ws + pl.A_off, ws + pl.B_off, S, pl.err_dev, stream);
+    e = mwmm::launch_gemm_tc(pl, ws + pl.A_off, ws + pl.B_off, S, pl.err_dev, stream, mwmm::plan_sq(pl, ws, 0),
+                             mwmm::plan_sq(pl, ws, 1));
     if (e) return cuda_status(e);
     rec(pe.ev[3], s);
     e = mwmm::launch_recombine(pl, S, dC, ldc, stream);
@@ -190,6 +191,7 @@ mwmm_status make_sub_plan(const Plan &pl, int64_t rows, Plan *out) {
     const bool crt = pl.form == MWMM_FORM_CRT8;  // its words follow from p and k
     mwmm_status st = mwmm::make_plan(out, rows, pl.n, pl.k, pl.p, crt ? 0 : pl.u, crt ? 0 : pl.v, pl.form, &o);
     if (st != MWMM_OK) return st;
+    out->tc_cert_chunk = 0;  // row blocks share one workspace laid out by the pipeline: worst-case chunks
     out->err_dev = pl.err_dev;  // shared flags (owned by the full plan)
     out->device = pl.device;
     return MWMM_OK;
@@ -395,6 +397,7 @@ void describe_plan(const Plan &P, mwmm_plan_desc *d) {
     d->tuned_tried = P.tuned_tried;
     for (int i = 0; i < P.crt_s && i < 24; ++i) d->crt_m[i] = P.crt_m[i];
     d->tc_digit_bits = P.form == MWMM_FORM_CRT8 || P.form == MWMM_FORM_FP64 ? 0 : P.digit_bits;
+    d->tc_cert_chunk = P.tc_cert_chunk;
 }
 
 }  // namespace mwmm

@@ -53,7 +53,10 @@ constexpr int BM = kTcBM;  // 128
 constexpr int BN = kTcBN;  // 256
 constexpr int STAGES = 4;
 constexpr int EPI_WARPS = 8;
-constexpr int THREADS = 32 * (2 + EPI_WARPS);
+constexpr int THREADS = 32 * (3 + EPI_WARPS);       // one-CTA kernel: + the planner warp (warp 10)
+constexpr int THREADS_PAIR = 32 * (2 + EPI_WARPS);  // pair kernel
+constexpr int PLANNER_WARP = 2 + EPI_WARPS;
+constexpr int kCertBlocks = 8;  // certified chunk: 8 k-block x pair steps (512 products of 9-bit digits)
 constexpr uint32_t kTileA = BM * kTileBytes;  // 16 KB
 constexpr uint32_t kTileB = BN * kTileBytes;  // 32 KB
 constexpr uint32_t kTmemCols = 2 * BN;        // 512: two accumulator buffers
@@ -86,6 +89,9 @@ struct TcParams {
     const int64_t *cta_off;
     int chunk_blocks;
     int *err;
+    // certified chunks (computed items only): squared-digit maxima of the
+    // splits ([word][k-block][64-row group]), nullptr: worst-case chunks
+    const uint32_t *sqA, *sqB;
 };
 
 // One work item with everything the three roles need (see TcItem).
@@ -188,32 +194,92 @@ __device__ __forceinline__ Item get_item(const TcParams &P, int64_t idx) {
     return kTable ? table_item(P, idx) : computed_item(P, idx);
 }
 
-// The item sequence of one CTA, seen identically by its three roles: items
-// (computed, or rows of a batch's table) are claimed one at a time from the
-// counter by the producer lane, which publishes each index in a ring of
-// kRing slots (full: 1 arrival, the producer; empty: 1 + 8 arrivals, the MMA
-// lane and every epilogue warp).  -1 ends the sequence.
+// The item sequence of one CTA, seen identically by its roles: the planner
+// warp claims items (computed, or rows of a batch's table) one at a time
+// from the counter, works out each item's FP32 chunk and publishes index and
+// chunk in a ring of kRing slots (full: 1 arrival, the planner; empty:
+// 2 + 8 arrivals, the producer lane, the MMA lane and every epilogue warp),
+// running up to kRing items ahead of the others.  -1 ends the sequence.
 struct ItemRing {
     int64_t *idx;
+    int32_t *chunk;  // the item's FP32 chunk in k-block x pair steps
     uint64_t *full, *empty;
 };
 
-__device__ __forceinline__ int64_t produce_item(const TcParams &P, const ItemRing &R, int64_t j, bool &alive) {
+// Certified chunk of a computed item (one 256-wide diagonal tile, 9-bit
+// digits): its k-block x pair steps in the MMA order (k-block outer, pairs
+// inner), in windows of kCertBlocks.  For an output (r, c) and a step
+// (pair (i, j), k-block kb), Cauchy-Schwarz bounds the sum of any subset of
+// the step's 64 products by sqrt(SA SB), SA = sum over the k-block of
+// A_i[r][k]^2 <= the split's maximum over r's group of 64 rows, SB the same
+// for B_j's column c; so every partial sum of a window's products -- what the
+// FP32 accumulator holds, in whatever order the tensor core adds them -- is
+// at most sum_t sqrt(SA_t SB_t) <= sqrt(L sum_t SA_t SB_t) for L <= kCertBlocks
+// steps.  L sum_t SA_t SB_t <= 2^48 for every window keeps each partial sum
+// within 2^24, where FP32 is exact: then the item runs chunks of kCertBlocks
+// steps (512 products), else the worst-case chunk (256).  The whole warp
+// takes the windows in turn; every operand is an integer (sums of squares
+// <= 64 x 2^16 = 2^22).
+__device__ __forceinline__ int certified_chunk(const TcParams &P, const Item &it, int lane) {
+    if (it.ndiag != 1) return P.chunk_blocks;
+    const int64_t nvb = (int64_t)it.ni * it.nkbc;
+    const int64_t nwin = (nvb + kCertBlocks - 1) / kCertBlocks;
+    const int64_t ga = P.A_rows / 64, gb = P.B_rows / 64;
+    bool ok = true;
+    for (int64_t w = lane; w < nwin; w += 32) {
+        uint64_t sum = 0;
+#pragma unroll
+        for (int t = 0; t < kCertBlocks; ++t) {
+            const int64_t v = w * kCertBlocks + t;
+            if (v < nvb) {
+                const int64_t kb = it.kb0 + v / it.ni;
+                const int i = it.i0 + (int)(v % it.ni), jw = it.s0 - i;
+                const uint32_t *pa = P.sqA + ((int64_t)i * P.nkb + kb) * ga + 2 * it.mt;
+                const uint32_t *pb = P.sqB + ((int64_t)jw * P.nkb + kb) * gb + 4 * it.nt;
+                const uint32_t sa = max(__ldg(pa), __ldg(pa + 1));
+                const uint32_t sb = max(max(__ldg(pb), __ldg(pb + 1)), max(__ldg(pb + 2), __ldg(pb + 3)));
+                sum += (uint64_t)sa * sb;
+            }
+        }
+        if ((uint64_t)kCertBlocks * sum > (uint64_t(1) << 48)) ok = false;
+    }
+    return __all_sync(0xffffffffu, ok) ? kCertBlocks : P.chunk_blocks;
+}
+
+// The planner warp: claim the j-th item, work out its chunk, publish both.
+template <bool kTable>
+__device__ __forceinline__ int64_t plan_item(const TcParams &P, const ItemRing &R, int64_t j, bool &alive,
+                                             int lane) {
     const int slot = (int)(j % kRing);
-    if (!mbar_wait(&R.empty[slot], (uint32_t)(((j / kRing) & 1) ^ 1), P.err)) {
+    int ok = 1;
+    int64_t idx = -1;
+    if (lane == 0) {
+        ok = mbar_wait(&R.empty[slot], (uint32_t)(((j / kRing) & 1) ^ 1), P.err) ? 1 : 0;
+        if (ok) {
+            idx = (int64_t)atomicAdd(P.sched, 1u);
+            if (idx >= P.nitems) idx = -1;
+        }
+    }
+    ok = __shfl_sync(0xffffffffu, ok, 0);
+    if (!ok) {
         alive = false;
         return -1;
     }
-    int64_t idx = (int64_t)atomicAdd(P.sched, 1u);
-    if (idx >= P.nitems) idx = -1;
-    R.idx[slot] = idx;
-    mbar_arrive(&R.full[slot]);  // release: the index is visible to the waiters of this phase
+    idx = __shfl_sync(0xffffffffu, idx, 0);
+    int chunk = P.chunk_blocks;
+    if (!kTable && idx >= 0 && P.sqA) chunk = certified_chunk(P, get_item<kTable>(P, idx), lane);
+    if (lane == 0) {
+        R.idx[slot] = idx;
+        R.chunk[slot] = chunk;
+        mbar_arrive(&R.full[slot]);  // release: index and chunk are visible to the waiters of this phase
+    }
     return idx;
 }
 
 // kWarp: the whole warp waits and reads; one lane releases the slot.
 template <bool kWarp>
-__device__ __forceinline__ int64_t consume_item(const TcParams &P, const ItemRing &R, int64_t j, bool &alive) {
+__device__ __forceinline__ int64_t consume_item(const TcParams &P, const ItemRing &R, int64_t j, bool &alive,
+                                                int *chunk = nullptr) {
     const int slot = (int)(j % kRing);
     bool ok = mbar_wait(&R.full[slot], (uint32_t)((j / kRing) & 1), P.err);
     if (kWarp) ok = __all_sync(0xffffffffu, ok);
@@ -222,6 +288,7 @@ __device__ __forceinline__ int64_t consume_item(const TcParams &P, const ItemRin
         return -1;
     }
     const int64_t idx = R.idx[slot];
+    if (chunk) *chunk = R.chunk[slot];
     if (kWarp) {
         __syncwarp();
         if ((threadIdx.x & 31) == 0) mbar_arrive(&R.empty[slot]);
@@ -307,6 +374,7 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_consta
     __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES], tfull[2], tempty[2], done;
     __shared__ __align__(8) uint64_t rfull[kRing], rempty[kRing];
     __shared__ int64_t ring_idx[kRing];
+    __shared__ int32_t ring_chunk[kRing];
     __shared__ uint32_t tmem_base_sh;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -315,7 +383,7 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_consta
     uint8_t *sA = smem_raw + pad;
     uint8_t *sB = sA + STAGES * kTileA;
     int32_t *sStage = reinterpret_cast<int32_t *>(sB + STAGES * kTileB);
-    const ItemRing ring{ring_idx, rfull, rempty};
+    const ItemRing ring{ring_idx, ring_chunk, rfull, rempty};
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
@@ -328,7 +396,7 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_consta
         }
         for (int r = 0; r < kRing; ++r) {
             mbar_init(&rfull[r], 1);
-            mbar_init(&rempty[r], 1 + EPI_WARPS);
+            mbar_init(&rempty[r], 2 + EPI_WARPS);
         }
         mbar_init(&done, 1);
         fence_mbar_init();
@@ -350,7 +418,7 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_consta
             uint64_t g = 0;
             bool alive = true;
             for (int64_t j = 0; alive; ++j) {
-                const int64_t idx = produce_item(P, ring, j, alive);
+                const int64_t idx = consume_item<false>(P, ring, j, alive);
                 if (idx < 0) break;
                 const Item it = get_item<kTable>(P, idx);
                 // One thread issues every copy, so the per-stage work is kept to a
@@ -393,12 +461,13 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_consta
             bool alive = true;
             const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
             for (int64_t j = 0; alive; ++j) {
-                const int64_t idx = consume_item<false>(P, ring, j, alive);
+                int chunk = P.chunk_blocks;
+                const int64_t idx = consume_item<false>(P, ring, j, alive, &chunk);
                 if (idx < 0) break;
                 const Item it = get_item<kTable>(P, idx);
                 const int64_t nvb = (int64_t)it.ni * it.nkbc;
                 const uint32_t idesc = idesc_n(it.nn, it.f16);
-                for (int64_t t0 = 0; alive && t0 < nvb; t0 += P.chunk_blocks, ++c) {
+                for (int64_t t0 = 0; alive && t0 < nvb; t0 += chunk, ++c) {
                     const int buf = (int)(c & 1);
                     if (!mbar_wait(&tempty[buf], (uint32_t)(((c >> 1) & 1) ^ 1), P.err)) {
                         alive = false;
@@ -406,7 +475,7 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_consta
                     }
                     tc_fence_after();
                     const uint32_t dt = tmem_base + (uint32_t)(buf * BN);
-                    const int64_t tend = t0 + P.chunk_blocks < nvb ? t0 + P.chunk_blocks : nvb;
+                    const int64_t tend = t0 + chunk < nvb ? t0 + chunk : nvb;
                     for (int64_t t = t0; t < tend; ++t, ++g) {
                         const int slot = (int)(g % STAGES);
                         if (!mbar_wait(&full[slot], (uint32_t)((g / STAGES) & 1), P.err)) {
@@ -427,6 +496,10 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_consta
             mma_commit(&done);
             mbar_wait(&done, 0, P.err);
         }
+    } else if (warp == PLANNER_WARP) {  // ---------------- planner: claims, certified chunks
+        bool alive = true;
+        for (int64_t j = 0; alive; ++j)
+            if (plan_item<kTable>(P, ring, j, alive, lane) < 0) break;
     } else {  // -------------------------------- epilogue warps 2..9
         const int quarter = warp & 3;
         const int half = (warp - 2) >> 2;
@@ -434,11 +507,12 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_consta
         uint64_t c = 0;
         bool alive = true;
         for (int64_t j = 0; alive; ++j) {
-            const int64_t idx = consume_item<true>(P, ring, j, alive);
+            int chunk = P.chunk_blocks;
+            const int64_t idx = consume_item<true>(P, ring, j, alive, &chunk);
             if (idx < 0) break;
             const Item it = get_item<kTable>(P, idx);
             const int64_t nvb = (int64_t)it.ni * it.nkbc;
-            const int64_t nch = (nvb + P.chunk_blocks - 1) / P.chunk_blocks;
+            const int64_t nch = (nvb + chunk - 1) / chunk;
             int32_t acc[128];
 #pragma unroll
             for (int e = 0; e < 128; ++e) acc[e] = 0;
@@ -524,7 +598,7 @@ __device__ __forceinline__ Item pair_item(const TcParams &P, int64_t idx) {
     return it;
 }
 
-__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS, 1)
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS_PAIR, 1)
     gemm_tc_pair_kernel(const __grid_constant__ TcParams P, const __grid_constant__ CUtensorMap tmA,
                         const __grid_constant__ CUtensorMap tmB) {
     extern __shared__ uint8_t smem_raw[];
@@ -684,7 +758,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS, 1)
 
 int pair_clusters() {
     static int cached[64] = {0};
-    return max_clusters2(reinterpret_cast<const void *>(gemm_tc_pair_kernel), THREADS, kSmemPair, cached);
+    return max_clusters2(reinterpret_cast<const void *>(gemm_tc_pair_kernel), THREADS_PAIR, kSmemPair, cached);
 }
 
 }  // namespace
@@ -757,7 +831,8 @@ int encode_rows_map(CUtensorMap *map, const void *base, uint64_t rows, uint32_t 
 }
 
 
-int launch_gemm_tc(const Plan &pl, const void *Aw, const void *Bw, int32_t *S, int *err, void *stream) {
+int launch_gemm_tc(const Plan &pl, const void *Aw, const void *Bw, int32_t *S, int *err, void *stream,
+                   const uint32_t *sqA, const uint32_t *sqB) {
     TcParams P;
     std::memset(&P, 0, sizeof(P));
     P.Aw = static_cast<const uint8_t *>(Aw);
@@ -837,7 +912,7 @@ int launch_gemm_tc(const Plan &pl, const void *Aw, const void *Bw, int32_t *S, i
         int r = encode_rows_map(&tmA, Aw, (uint64_t)pl.u * pl.nkb * pl.A_rows, 128);
         if (r == 0) r = encode_rows_map(&tmB, Bw, (uint64_t)pl.v * pl.nkb * pl.B_rows, 128);
         if (r != 0) return r;
-        gemm_tc_pair_kernel<<<(unsigned)(2 * ncl), THREADS, kSmemPair, static_cast<cudaStream_t>(stream)>>>(P, tmA,
+        gemm_tc_pair_kernel<<<(unsigned)(2 * ncl), THREADS_PAIR, kSmemPair, static_cast<cudaStream_t>(stream)>>>(P, tmA,
                                                                                                             tmB);
         return (int)cudaGetLastError();
     }
@@ -845,6 +920,12 @@ int launch_gemm_tc(const Plan &pl, const void *Aw, const void *Bw, int32_t *S, i
     if (e != cudaSuccess) return (int)e;
     const int64_t sms = sm_count();
     P.sched = reinterpret_cast<uint32_t *>(reinterpret_cast<uint8_t *>(S) + (pl.sched_off - pl.S_off));
+    // certified chunks: twice the worst-case chunk, one 256-wide diagonal per item
+    if (sqA && sqB && pl.tc_cert_chunk == kCertBlocks * kTcKB && 2 * P.chunk_blocks == kCertBlocks &&
+        pl.tc_nb == BN && pl.tc_ndiag == 1) {
+        P.sqA = sqA;
+        P.sqB = sqB;
+    }
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     e = cudaMemsetAsync(P.sched, 0, sizeof(uint32_t), s);
     if (e != cudaSuccess) return (int)e;

@@ -105,6 +105,15 @@ struct Plan {
     int64_t A_wstride = 0, A_kstride = 0;
     uint64_t A_off = 0, B_off = 0, S_off = 0, ws_bytes = 0;
     uint64_t sched_off = 0;  // tensor forms (unfused): the word-product kernel's item counter (256 bytes)
+    // Certified chunks (INT8 form, 9-bit digits, one-CTA kernel, 256-wide
+    // column tiles): the split writes, per word, k-block and group of 64
+    // rows (A) or columns (B), the largest sum of squared digits over the
+    // k-block (uint32, [word][k-block][group]) at sq_off (A) and
+    // sq_off + sqB_off (B); the word-product kernel runs an item with FP32
+    // chunks of tc_cert_chunk products when Cauchy-Schwarz on these sums
+    // bounds every partial sum of each chunk by 2^24.  0: not used.
+    int tc_cert_chunk = 0;
+    uint64_t sq_off = 0, sqB_off = 0;
     // owned device resources (lazily created)
     int device = -1;
     void *own_ws = nullptr;
@@ -124,11 +133,22 @@ int signed_digits(uint64_t p, int bits);  // fewest balanced base-2^bits digits
 uint64_t mulmod_u64(uint64_t a, uint64_t b, uint64_t p);
 
 // launches (return cudaError_t as int)
-int launch_split(const Plan &pl, int side, const uint64_t *M, int64_t ld, void *words, void *stream);
+// sq: the plan's squared-digit maxima for this side (plan_sq), or nullptr
+int launch_split(const Plan &pl, int side, const uint64_t *M, int64_t ld, void *words, void *stream,
+                 uint32_t *sq = nullptr);
+// The squared-digit maxima of a plan with certified chunks in workspace ws
+// (side 0: A, 1: B), else nullptr.
+inline uint32_t *plan_sq(const Plan &pl, uint8_t *ws, int side) {
+    if (!pl.tc_cert_chunk) return nullptr;
+    return reinterpret_cast<uint32_t *>(ws + pl.sq_off + (side ? pl.sqB_off : 0));
+}
 // part: ksplit x m x n partial results (workspace at S_off) when pl.ksplit > 1
 int launch_gemm_fp64(const Plan &pl, const void *Aw, const void *Bw, uint64_t *C, int64_t ldc, uint64_t *part,
                      int *err, void *stream);
-int launch_gemm_tc(const Plan &pl, const void *Aw, const void *Bw, int32_t *S, int *err, void *stream);
+// sqA, sqB: the squared-digit maxima written by the splits (certified
+// chunks), or nullptr (worst-case chunks only)
+int launch_gemm_tc(const Plan &pl, const void *Aw, const void *Bw, int32_t *S, int *err, void *stream,
+                   const uint32_t *sqA = nullptr, const uint32_t *sqB = nullptr);
 int launch_recombine(const Plan &pl, const int32_t *S, uint64_t *C, int64_t ldc, void *stream);
 // Fused form (pl.tc_fused): word products, reduction and recombination in one
 // kernel, plus the K-part sum when pl.ksplit > 1 (R = workspace at S_off).

@@ -105,8 +105,8 @@ extern "C" mwmm_status mwmm_matmul_noalloc(int64_t m, int64_t n, int64_t k, uint
     uint8_t *ws = base + kErrBytes;
     pl.err_dev = err;
     if (cudaMemsetAsync(err, 0, kErrBytes, s) != cudaSuccess) return MWMM_ERR_CUDA;
-    if ((st = from_cuda(launch_split(pl, 0, dA, lda, ws + pl.A_off, stream))) != MWMM_OK) return st;
-    if ((st = from_cuda(launch_split(pl, 1, dB, ldb, ws + pl.B_off, stream))) != MWMM_OK) return st;
+    if ((st = from_cuda(launch_split(pl, 0, dA, lda, ws + pl.A_off, stream, plan_sq(pl, ws, 0)))) != MWMM_OK) return st;
+    if ((st = from_cuda(launch_split(pl, 1, dB, ldb, ws + pl.B_off, stream, plan_sq(pl, ws, 1)))) != MWMM_OK) return st;
     if ((st = from_cuda(launch_tensor_products(pl, ws, dC, ldc, err, stream))) != MWMM_OK) return st;
     int flags[2] = {0, 0};
     if (cudaMemcpyAsync(flags, err, sizeof(flags), cudaMemcpyDeviceToHost, s) != cudaSuccess) return MWMM_ERR_CUDA;

@@ -464,6 +464,17 @@ mwmm_status make_plan(Plan *pl, int64_t m, int64_t n, int64_t k, uint64_t p, int
             P.sched_off = P.ws_bytes;
             P.ws_bytes += 256;
         }
+        // Certified 512-product chunks for 9-bit digits (twice the
+        // worst-case 256) where each item is one 256-wide diagonal tile.
+        // (Not with an explicit tc_chunk, which fixes the chunk, nor for the
+        // pair kernel.)
+        if (form == MWMM_FORM_INT8 && P.digit_bits == 9 && !P.tc_fused && !P.tc_pair && P.tc_nb == kTcBN && k > 0 &&
+            o.tc_chunk == 0) {
+            P.tc_cert_chunk = 2 * (int)P.tc_chunk;
+            P.sq_off = P.ws_bytes;
+            P.sqB_off = align256((uint64_t)u * P.nkb * (P.A_rows / 64) * 4);
+            P.ws_bytes = align256(P.sq_off + P.sqB_off + (uint64_t)v * P.nkb * (P.B_rows / 64) * 4);
+        }
     }
     if (m == 0 || n == 0) P.ws_bytes = 0;
     *pl = P;

@@ -54,6 +54,10 @@ struct SplitParams {
     int64_t cbias;              // INT8 form: h (1 + R + ... + R^(words-2))
     int bits;                   // INT8 form: digit width b (8: bf16 words, 9: fp16 words)
     int crt;                    // CRT form: residues instead of digits
+    // 9-bit digits with certified chunks: per word w, k-block kb and group of
+    // 64 rows g, the largest sum over the k-block of a row's squared digits,
+    // at sq[(w nkb + kb) (rows_pad / 64) + g]; nullptr: not written
+    uint32_t *sq;
     float cmf[kMaxCrt];         // moduli m_i (odd primes below 256)
     float cinv[kMaxCrt];        // fl(1 / m_i), correctly rounded
     float c11[kMaxCrt], c22[kMaxCrt], c33[kMaxCrt], c44[kMaxCrt];  // 2^(11 j) mod m_i
@@ -201,12 +205,24 @@ __device__ __forceinline__ void split_fp64_tile(const SplitParams &P, uint64_t (
 }
 
 // INT8 form: a 64 x 64 tile is exactly one k-block of 64 bf16, 8 granules.
+// kSq: also the squared-digit maxima (P.sq set; a separate instantiation
+// keeps the other kernels' registers down)
+template <bool kSq>
 __device__ __forceinline__ void split_int8_tile(const SplitParams &P, uint64_t (*tile)[kST + 1], int64_t by,
                                                 int64_t bx) {
     const int64_t r0 = by * kST, l0 = bx * kST;
     load_tile(P, tile, r0, l0);
     const int64_t kb = l0 / kTcKB;
     const uint64_t half = (P.p - 1) / 2;
+    // squared-digit maxima of this tile's 64 rows, per word (kSq: its plans have rows_pad a multiple of 128, so no unit
+    // below skips and every lane takes part in the shuffles)
+    // (each unit stores its 8 digits' squares per word; one pass at the end
+    // adds a row's 8 units and takes the largest row)
+    __shared__ uint32_t s_sq[kSq ? kMaxWords * kST * 8 : 1];
+    __shared__ uint32_t s_sqmax[kMaxWords];
+    if (kSq) {
+        if (threadIdx.x < kMaxWords) s_sqmax[threadIdx.x] = 0;
+    }
     for (int unit = threadIdx.x; unit < kST * 8; unit += 256) {
         const int rr = unit / 8, g = unit % 8;
         const int64_t r = r0 + rr;
@@ -248,6 +264,15 @@ __device__ __forceinline__ void split_int8_tile(const SplitParams &P, uint64_t (
                     for (int e = 0; e < 8; ++e) h[e] = int9_digit_biased(t[e], w, last);
                     *dst_of(w) = make_uint4(f16x2_from_biased(h[0], h[1]), f16x2_from_biased(h[2], h[3]),
                                             f16x2_from_biased(h[4], h[5]), f16x2_from_biased(h[6], h[7]));
+                    if (kSq) {  // this unit's squared digits (<= 8 x 2^16)
+                        uint32_t q = 0;
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) {
+                            const int d = (int)h[e] - 0x6600;
+                            q += (uint32_t)(d * d);
+                        }
+                        s_sq[w * (kST * 8) + unit] = q;
+                    }
                 } else {
                     float f[8];
 #pragma unroll
@@ -264,6 +289,20 @@ __device__ __forceinline__ void split_int8_tile(const SplitParams &P, uint64_t (
                                        ((g ^ (int)(r & 7)) * 16)) = zero;
         }
     }
+    if (kSq) {
+        __syncthreads();
+        // row sums (<= 2^22), the largest per word: a warp covers 32 rows of one word
+        for (int i = threadIdx.x; i < P.words * kST; i += blockDim.x) {
+            const uint32_t *q = s_sq + i * 8;
+            uint32_t row = q[0] + q[1] + q[2] + q[3] + q[4] + q[5] + q[6] + q[7];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) row = max(row, __shfl_xor_sync(0xffffffffu, row, o));
+            if ((threadIdx.x & 31) == 0) atomicMax(&s_sqmax[i / kST], row);
+        }
+        __syncthreads();
+        if ((int)threadIdx.x < P.words)
+            P.sq[((int64_t)threadIdx.x * P.nkb + kb) * (P.rows_pad / kST) + by] = s_sqmax[threadIdx.x];
+    }
 }
 
 __global__ void __launch_bounds__(256) split_fp64_kernel(const __grid_constant__ SplitParams P) {
@@ -271,9 +310,10 @@ __global__ void __launch_bounds__(256) split_fp64_kernel(const __grid_constant__
     split_fp64_tile(P, tile, blockIdx.y, blockIdx.x);
 }
 
-__global__ void __launch_bounds__(256) split_int8_kernel(const __grid_constant__ SplitParams P) {
+template <bool kSq>
+__global__ void __launch_bounds__(256, 4) split_int8_kernel(const __grid_constant__ SplitParams P) {
     __shared__ uint64_t tile[kST][kST + 1];
-    split_int8_tile(P, tile, blockIdx.y, blockIdx.x);
+    split_int8_tile<kSq>(P, tile, blockIdx.y, blockIdx.x);
 }
 
 // Batched: CTA c splits the tiles blocks[c * per, c * per + per) (each
@@ -302,12 +342,13 @@ __global__ void __launch_bounds__(256, 4) split_batched_kernel(const SplitParams
             __syncthreads();
         }
         if (fp64) split_fp64_tile(P, tile, bl.y, bl.z);
-        else split_int8_tile(P, tile, bl.y, bl.z);
+        else split_int8_tile<false>(P, tile, bl.y, bl.z);
     }
 }
 
 SplitParams make_split_params(const Plan &pl, int side, const uint64_t *M, int64_t ld, void *words) {
     SplitParams P;
+    P.sq = nullptr;
     P.M = M;
     P.ld = ld;
     P.side = side;
@@ -373,8 +414,11 @@ int launch_split_batched(const void *jobs, const int *blocks, int nblocks, int f
     return (int)cudaGetLastError();
 }
 
-int launch_split(const Plan &pl, int side, const uint64_t *M, int64_t ld, void *words, void *stream) {
-    const SplitParams P = make_split_params(pl, side, M, ld, words);
+int launch_split(const Plan &pl, int side, const uint64_t *M, int64_t ld, void *words, void *stream, uint32_t *sq) {
+    SplitParams P = make_split_params(pl, side, M, ld, words);
+    // squared-digit maxima only for the certified-chunk plans' own layout
+    if (sq && pl.tc_cert_chunk && pl.form == MWMM_FORM_INT8 && pl.digit_bits == 9 && P.rows_pad % (2 * kST) == 0)
+        P.sq = sq;
     if (pl.nkb == 0 || P.rows_pad == 0) return 0;
     const int64_t kcols = pl.nkb * pl.kb_elems;
     dim3 grid((unsigned)((kcols + kST - 1) / kST), (unsigned)((P.rows_pad + kST - 1) / kST));
@@ -383,7 +427,10 @@ int launch_split(const Plan &pl, int side, const uint64_t *M, int64_t ld, void *
         // Words equal to the input when u == 1 (alpha = p): Alg. 4 has no loop.
         split_fp64_kernel<<<grid, 256, 0, s>>>(P);
     } else {
-        split_int8_kernel<<<grid, 256, 0, s>>>(P);
+        if (P.sq)
+            split_int8_kernel<true><<<grid, 256, 0, s>>>(P);
+        else
+            split_int8_kernel<false><<<grid, 256, 0, s>>>(P);
     }
     return (int)cudaGetLastError();
 }

@@ -63,7 +63,7 @@ class PlanDesc(ctypes.Structure):
                 ("S_off", ctypes.c_uint64), ("workspace_bytes", ctypes.c_uint64),
                 ("f64_concat", ctypes.c_int32), ("ksplit", ctypes.c_int32),
                 ("tuned_ms", ctypes.c_double), ("tuned_tried", ctypes.c_int32), ("tc_seg", ctypes.c_int32),
-                ("crt_m", ctypes.c_uint32 * 24), ("tc_digit_bits", ctypes.c_int32), ("pad2", ctypes.c_int32)]
+                ("crt_m", ctypes.c_uint32 * 24), ("tc_digit_bits", ctypes.c_int32), ("tc_cert_chunk", ctypes.c_int32)]
 
     def as_dict(self):
         d = {}

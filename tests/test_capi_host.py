@@ -361,6 +361,27 @@ def test_underfill_k_split_plans(M, form):
         M.Plan(256, 256, 4096, p, form=form, tc_fill=2)
 
 
+def test_certified_chunk_plans(M):
+    """9-bit digits on 256-wide column tiles get certified 512-product chunks
+    (tc_cert_chunk) and a squared-digit region after the item counter; 8-bit
+    digits, narrow n, an explicit tc_chunk, the pair kernel and the fused
+    form keep the worst-case chunk only."""
+    p26, p20 = SWEEP[26], SWEEP[20]
+    d = M.Plan(300, 700, 1000, p26, form="int8").info
+    assert d["tc_digit_bits"] == 9 and d["tc_chunk"] == 256 and d["tc_cert_chunk"] == 512
+    sums = d["nsums"] * d["nkc"] * d["A_rows"] * d["B_rows"] * 4
+    t = (d["S_off"] + sums + 255) // 256 * 256
+    sqa = d["u"] * d["nkb"] * (d["A_rows"] // 64) * 4
+    sqb = d["v"] * d["nkb"] * (d["B_rows"] // 64) * 4
+    assert d["workspace_bytes"] == (t + 256 + (sqa + 255) // 256 * 256 + sqb + 255) // 256 * 256
+    assert M.Plan(300, 700, 1000, p20, form="int8").info["tc_cert_chunk"] == 0
+    assert M.Plan(300, 100, 1000, p26, form="int8").info["tc_cert_chunk"] == 0
+    assert M.Plan(300, 700, 1000, p26, form="int8", tc_chunk=128).info["tc_cert_chunk"] == 0
+    assert M.Plan(300, 700, 1000, p26, form="int8", tc_pair=True).info["tc_cert_chunk"] == 0
+    assert M.Plan(300, 700, 1000, p26, form="int8", tc_fused=2).info["tc_cert_chunk"] == 0
+    assert M.Plan(300, 700, 1000, p26, form="crt8").info["tc_cert_chunk"] == 0
+
+
 def test_tensor_form_choice_follows_the_cost_model(M):
     """AUTO's tensor form for batches and serving: at 4096^3 the digit form
     at 23-27 bits (9 digit products, 9-bit digits from 25 bits, against 8-9

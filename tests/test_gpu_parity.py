@@ -524,6 +524,85 @@ def test_f16_fp32_chunk_small_addend_below_large_sum(M, oracle, b, sign):
     assert np.array_equal(C, oracle.matmul_mod(A, B, p))
 
 
+def _sq_regions(d):
+    """Byte offsets of the squared-digit maxima (A, B) in a certified plan's
+    workspace: after the sums and the 256-byte item counter."""
+    sums = d["nsums"] * d["nkc"] * d["A_rows"] * d["B_rows"] * 4
+    a = (d["S_off"] + sums + 255) // 256 * 256 + 256
+    return a, a + (d["u"] * d["nkb"] * (d["A_rows"] // 64) * 4 + 255) // 256 * 256
+
+
+def _sq_expected(dig, rows_pad, nkb):
+    """Per word, k-block and group of 64 rows: the largest sum over the
+    k-block of a row's squared digits (dig: [words][rows][k] signed)."""
+    w, r, k = dig.shape
+    full = np.zeros((w, rows_pad, nkb * 64), np.int64)
+    full[:, :r, :k] = dig
+    sq = (full ** 2).reshape(w, rows_pad, nkb, 64).sum(-1)          # [w][row][kb]
+    return sq.reshape(w, rows_pad // 64, 64, nkb).max(axis=2).transpose(0, 2, 1)  # [w][kb][group]
+
+
+@pytest.mark.parametrize("b", [26, 52])
+def test_f16_squared_digit_maxima_match_oracle(M, oracle, b):
+    """The splits of a certified plan write, per word, k-block and 64-row
+    group, the largest row sum of squared digits: recomputed from the
+    oracle's digits (A's rows, B's columns), ragged tiles included."""
+    p = SWEEP[b]
+    m, n, k = 300, 700, 1000
+    A, B = inputs.problem(b + 31, m, n, k, p)
+    plan = M.Plan(m, n, k, p, form="int8")
+    d = plan.info
+    assert d["tc_cert_chunk"] == 512
+    ws = plan.alloc_workspace()
+    C = host(plan.matmul(dev(A), dev(B)))
+    assert plan.check() == 0 and np.array_equal(C, oracle.matmul_mod(A, B, p))
+    oa, ob = _sq_regions(d)
+    u, v, nkb = d["u"], d["v"], d["nkb"]
+    raw = ws.cpu().numpy()
+    got_a = raw[oa:oa + u * nkb * (d["A_rows"] // 64) * 4].view(np.uint32).reshape(u, nkb, -1)
+    got_b = raw[ob:ob + v * nkb * (d["B_rows"] // 64) * 4].view(np.uint32).reshape(v, nkb, -1)
+    Ad = oracle.split_signed(A, p, u, 9).astype(np.int64)
+    Bd = oracle.split_signed(B.T.copy(), p, v, 9).astype(np.int64)
+    assert np.array_equal(got_a, _sq_expected(Ad, d["A_rows"], nkb))
+    assert np.array_equal(got_b, _sq_expected(Bd, d["B_rows"], nkb))
+
+
+@pytest.mark.parametrize("b", [26, 52])
+@pytest.mark.parametrize("digit", [181, 183, -181])
+def test_f16_certified_chunk_at_its_bound(M, oracle, b, digit):
+    """Constant digits d (odd): every product is d^2 (odd), and a 512-product
+    chunk of them sums to 512 d^2.  For |d| = 181 that is 16,773,632 (just
+    below 2^24) and the certificate 8 x 8 (64 d^2)^2 <= 2^48 holds exactly
+    at its bound, so the certified chunk runs with partial sums up to
+    2^23.9996; for 183 it fails (512 d^2 > 2^24) and the 256-product chunk
+    must run -- a wrong decision would round an odd partial sum above 2^24."""
+    p = SWEEP[b]
+    a = digit % p
+    k = 2 * 512 + 64 + 37
+    A = np.full((150, k), a, np.uint64)
+    B = np.full((k, 300), a, np.uint64)
+    u = oracle.digit_words(p, 9)
+    assert list(oracle.split_signed(np.array([a], np.uint64), p, u, 9)[:, 0]) == [digit] + [0] * (u - 1)
+    C, plan = gpu_product(M, A, B, p, form="int8")
+    assert plan.info["tc_cert_chunk"] == 512
+    assert np.all(C == (digit * digit * k) % p)
+    assert np.array_equal(C, oracle.matmul_mod(A, B, p))
+
+
+@pytest.mark.parametrize("b", [26, 52])
+def test_f16_certified_and_worst_case_items_mixed(M, oracle, b):
+    """Random digits (certified items) next to a row tile and a column tile
+    of constant 183s (items whose certificate fails): every item exact."""
+    p = SWEEP[b]
+    m, n, k = 300, 600, 1200
+    A, B = inputs.problem(b + 77, m, n, k, p)
+    A[:128] = 183
+    B[:, :256] = 183
+    C, plan = gpu_product(M, A, B, p, form="int8")
+    assert plan.info["tc_cert_chunk"] == 512
+    assert np.array_equal(C, oracle.matmul_mod(A, B, p))
+
+
 @pytest.mark.parametrize("b", [26, 40, 48, 52])
 def test_f16_digits_match_oracle_and_8bit_digits(M, oracle, b):
     """9-bit digits (fp16 words) on ragged shapes through several chunks,
