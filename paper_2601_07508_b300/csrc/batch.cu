@@ -36,6 +36,7 @@ struct mwmm_batch_s {
     int *err = nullptr;           // error words
     uint64_t ws_bytes = 0, table_bytes = 0;
     int nsplit = 0, ntc_ctas = 0, nrec = 0, nf64 = 0;
+    int cert = 0;  // some problem runs certified chunks
     int64_t nitems = 0;
     const void *d_split_jobs = nullptr;
     const int *d_split_blocks = nullptr;
@@ -92,7 +93,11 @@ static void claim_order(std::vector<mwmm::TcItem> &items, const std::vector<size
 // and whose sums start at S (see the plan layout and TcItem).  INT8: windows
 // of tc_ndiag diagonals; CRT: one window per modulus i, the pair (i, i)
 // (s0 = 2 i, so that B word s0 - i = i), its sums in plane i.
-static void tc_items(const Plan &pl, const uint8_t *Aw, const uint8_t *Bw, int32_t *S, std::vector<mwmm::TcItem> &items) {
+// Every item carries the problem's worst-case FP32 chunk (its digit width's:
+// 9-bit digits 256 products, 8-bit digits and CRT residues 1024) and, for a
+// plan with certified chunks, its squared-digit maxima (sqA, sqB).
+static void tc_items(const Plan &pl, const uint8_t *Aw, const uint8_t *Bw, int32_t *S, std::vector<mwmm::TcItem> &items,
+                     const uint32_t *sqA = nullptr, const uint32_t *sqB = nullptr) {
     const int64_t mtc = pl.A_rows / mwmm::kTcBM;
     const int64_t ntc = pl.tc_nb == mwmm::kTcBN ? pl.B_rows / mwmm::kTcBN : 1;
     const int64_t kcb = pl.kc / mwmm::kTcKB;
@@ -143,6 +148,9 @@ static void tc_items(const Plan &pl, const uint8_t *Aw, const uint8_t *Bw, int32
                     it.b_wstride = pl.B_wstride * mwmm::kTileBytes;
                     it.b_kstride = pl.B_kstride * mwmm::kTileBytes;
                     it.f16 = pl.form == MWMM_FORM_INT8 && pl.digit_bits == 9;
+                    it.chunk = (int32_t)(pl.tc_chunk / mwmm::kTcKB);
+                    it.sqA = nd == 1 ? sqA : nullptr;
+                    it.sqB = nd == 1 ? sqB : nullptr;
                     items.push_back(it);
                 }
     }
@@ -160,9 +168,12 @@ void build_batch_tables(const Plan *plans, const mwmm_problem *probs, uint8_t *c
         if (pl.m == 0 || pl.n == 0 || pl.k == 0) continue;
         if (pl.form != MWMM_FORM_FP64) prob_start.push_back(T.items.size());
         uint8_t *w = ws_base[i];
-        split_job(pl, 0, q.A, q.lda, w + pl.A_off, &T.split_jobs[split_job_bytes() * nsj], nsj, T.split_blocks);
+        uint32_t *sqA = pl.form == MWMM_FORM_INT8 ? plan_sq(pl, w, 0) : nullptr;
+        uint32_t *sqB = pl.form == MWMM_FORM_INT8 ? plan_sq(pl, w, 1) : nullptr;
+        if (sqA) T.cert = 1;
+        split_job(pl, 0, q.A, q.lda, w + pl.A_off, &T.split_jobs[split_job_bytes() * nsj], nsj, T.split_blocks, sqA);
         ++nsj;
-        split_job(pl, 1, q.B, q.ldb, w + pl.B_off, &T.split_jobs[split_job_bytes() * nsj], nsj, T.split_blocks);
+        split_job(pl, 1, q.B, q.ldb, w + pl.B_off, &T.split_jobs[split_job_bytes() * nsj], nsj, T.split_blocks, sqB);
         ++nsj;
         if (pl.form == MWMM_FORM_FP64) {
             T.f64_recs.resize(T.f64_recs.size() + fp64_job_bytes());
@@ -176,7 +187,7 @@ void build_batch_tables(const Plan *plans, const mwmm_problem *probs, uint8_t *c
                     (int)(T.crt_recs.size() / crt_job_bytes()) - 1, T.crt_jobs);
         } else {
             int32_t *S = reinterpret_cast<int32_t *>(w + pl.S_off);
-            tc_items(pl, w + pl.A_off, w + pl.B_off, S, T.items);
+            tc_items(pl, w + pl.A_off, w + pl.B_off, S, T.items, sqA, sqB);
             T.rec_recs.resize(T.rec_recs.size() + recombine_job_bytes());
             recombine_job(pl, S, q.C, q.ldc, &T.rec_recs[T.rec_recs.size() - recombine_job_bytes()],
                           (int)(T.rec_recs.size() / recombine_job_bytes()) - 1, T.rec_jobs);
@@ -254,13 +265,13 @@ uint64_t pack_batch_tables(const BatchTables &T, std::vector<uint8_t> &blob, uin
 int launch_batch_tables(const BatchTables &T, const uint8_t *dtables, const uint64_t off[kBatchTables], int fp64,
                         int chunk_blocks, int *err, void *stream) {
     int e = launch_split_batched(dtables + off[0], reinterpret_cast<const int *>(dtables + off[1]), T.nsplit, fp64,
-                                 stream);
+                                 stream, T.cert);
     if (e) return e;
     if (fp64) return launch_gemm_fp64_batched(dtables + off[6], reinterpret_cast<const int *>(dtables + off[7]),
                                               T.nf64, stream);
     e = launch_gemm_tc_table(reinterpret_cast<const TcItem *>(dtables + off[2]),
                              const_cast<int64_t *>(reinterpret_cast<const int64_t *>(dtables + off[3])),
-                             (int64_t)T.items.size(), T.ctas, chunk_blocks, err, stream);
+                             (int64_t)T.items.size(), T.ctas, chunk_blocks, err, stream, T.cert);
     if (e) return e;
     e = launch_recombine_batched(dtables + off[4], reinterpret_cast<const int *>(dtables + off[5]), T.nrec, stream);
     if (e) return e;
@@ -289,14 +300,14 @@ void free_batch(mwmm_batch_s *b) {
 
 mwmm_status record(mwmm_batch_s *b, cudaStream_t s) {
     const int fp64 = b->form == MWMM_FORM_FP64;
-    int e = mwmm::launch_split_batched(b->d_split_jobs, b->d_split_blocks, b->nsplit, fp64, s);
+    int e = mwmm::launch_split_batched(b->d_split_jobs, b->d_split_blocks, b->nsplit, fp64, s, b->cert);
     if (e) return cuda_st((cudaError_t)e);
     if (fp64) {
         e = mwmm::launch_gemm_fp64_batched(b->d_f64, b->d_f64_jobs, b->nf64, s);
         return cuda_st((cudaError_t)e);
     }
     e = mwmm::launch_gemm_tc_table(b->d_items, const_cast<int64_t *>(b->d_cta_off), b->nitems, b->ntc_ctas,
-                                   b->chunk_blocks, b->err, s);
+                                   b->chunk_blocks, b->err, s, b->cert);
     if (e) return cuda_st((cudaError_t)e);
     e = mwmm::launch_recombine_batched(b->d_rec, b->d_rec_jobs, b->nrec, s);
     if (e) return cuda_st((cudaError_t)e);
@@ -444,6 +455,7 @@ mwmm_status mwmm_batch_create(mwmm_batch_t *out, const mwmm_problem *probs, int 
     b->nf64 = T.nf64;
     b->ncrt = T.ncrt;
     b->ntc_ctas = T.ctas;
+    b->cert = T.cert;
     std::vector<uint8_t> blob;
     uint64_t off[mwmm::kBatchTables];
     const uint64_t tb = mwmm::pack_batch_tables(T, blob, off);

@@ -92,6 +92,7 @@ struct TcParams {
     // certified chunks (computed items only): squared-digit maxima of the
     // splits ([word][k-block][64-row group]), nullptr: worst-case chunks
     const uint32_t *sqA, *sqB;
+    int cert;  // some item may run certified chunks: the planner warp claims (else the producer lane)
 };
 
 // One work item with everything the three roles need (see TcItem).
@@ -103,6 +104,8 @@ struct Item {
     int rv, cv;  // rows of the tile inside m (from its first row), columns of each diagonal block inside n
     int nn;      // MMA N: ndiag nb
     int f16;     // words in fp16, else bf16
+    int chunk;   // worst-case FP32 chunk in k-block x pair steps (its digit width's)
+    const uint32_t *sqA, *sqB;  // squared-digit maxima for certified chunks, or nullptr
 };
 
 // MMA N of an item.  Fitting N of a last column tile to its valid columns
@@ -130,6 +133,9 @@ __device__ __forceinline__ Item computed_item(const TcParams &P, int64_t idx) {
     it.nb = P.nb;
     it.v = P.v;
     it.f16 = P.f16;
+    it.chunk = P.chunk_blocks;
+    it.sqA = P.sqA;
+    it.sqB = P.sqB;
     it.b_wstride = P.b_wstride;
     it.b_kstride = P.b_kstride;
     it.b_wpad = P.b_wpad;
@@ -186,6 +192,9 @@ __device__ __forceinline__ Item table_item(const TcParams &P, int64_t pos) {
     it.cv = d.cv;
     it.nn = item_n(it.ndiag, it.nb, it.cv);
     it.f16 = d.f16;
+    it.chunk = d.chunk;
+    it.sqA = d.sqA;
+    it.sqB = d.sqB;
     return it;
 }
 
@@ -224,11 +233,11 @@ struct ItemRing {
 // steps (512 products), else the worst-case chunk (256).  The whole warp
 // takes the windows in turn; every operand is an integer (sums of squares
 // <= 64 x 2^16 = 2^22).
-__device__ __forceinline__ int certified_chunk(const TcParams &P, const Item &it, int lane) {
-    if (it.ndiag != 1) return P.chunk_blocks;
+__device__ __forceinline__ int certified_chunk(const Item &it, int lane) {
+    if (it.ndiag != 1 || !it.sqA || 2 * it.chunk != kCertBlocks) return it.chunk;
     const int64_t nvb = (int64_t)it.ni * it.nkbc;
     const int64_t nwin = (nvb + kCertBlocks - 1) / kCertBlocks;
-    const int64_t ga = P.A_rows / 64, gb = P.B_rows / 64;
+    const int64_t ga = it.A_rows / 64, gb = it.B_rows / 64;
     bool ok = true;
     for (int64_t w = lane; w < nwin; w += 32) {
         uint64_t sum = 0;
@@ -238,8 +247,8 @@ __device__ __forceinline__ int certified_chunk(const TcParams &P, const Item &it
             if (v < nvb) {
                 const int64_t kb = it.kb0 + v / it.ni;
                 const int i = it.i0 + (int)(v % it.ni), jw = it.s0 - i;
-                const uint32_t *pa = P.sqA + ((int64_t)i * P.nkb + kb) * ga + 2 * it.mt;
-                const uint32_t *pb = P.sqB + ((int64_t)jw * P.nkb + kb) * gb + 4 * it.nt;
+                const uint32_t *pa = it.sqA + ((int64_t)i * it.nkb + kb) * ga + 2 * it.mt;
+                const uint32_t *pb = it.sqB + ((int64_t)jw * it.nkb + kb) * gb + 4 * it.nt;
                 const uint32_t sa = max(__ldg(pa), __ldg(pa + 1));
                 const uint32_t sb = max(max(__ldg(pb), __ldg(pb + 1)), max(__ldg(pb + 2), __ldg(pb + 3)));
                 sum += (uint64_t)sa * sb;
@@ -247,12 +256,13 @@ __device__ __forceinline__ int certified_chunk(const TcParams &P, const Item &it
         }
         if ((uint64_t)kCertBlocks * sum > (uint64_t(1) << 48)) ok = false;
     }
-    return __all_sync(0xffffffffu, ok) ? kCertBlocks : P.chunk_blocks;
+    return __all_sync(0xffffffffu, ok) ? kCertBlocks : it.chunk;
 }
 
 // The producer lane as publisher (no certified chunks): claim the j-th item,
-// publish it with the worst-case chunk, and read it as one of the slot's
+// publish it with its worst-case chunk, and read it as one of the slot's
 // consumers.
+template <bool kTable>
 __device__ __forceinline__ int64_t produce_item(const TcParams &P, const ItemRing &R, int64_t j, bool &alive) {
     const int slot = (int)(j % kRing);
     if (!mbar_wait(&R.empty[slot], (uint32_t)(((j / kRing) & 1) ^ 1), P.err)) {
@@ -262,7 +272,7 @@ __device__ __forceinline__ int64_t produce_item(const TcParams &P, const ItemRin
     int64_t idx = (int64_t)atomicAdd(P.sched, 1u);
     if (idx >= P.nitems) idx = -1;
     R.idx[slot] = idx;
-    R.chunk[slot] = P.chunk_blocks;
+    R.chunk[slot] = idx >= 0 ? get_item<kTable>(P, idx).chunk : P.chunk_blocks;
     mbar_arrive(&R.full[slot]);   // release: the index is visible to the waiters of this phase
     mbar_arrive(&R.empty[slot]);  // the producer has read it too
     return idx;
@@ -289,7 +299,7 @@ __device__ __forceinline__ int64_t plan_item(const TcParams &P, const ItemRing &
     }
     idx = __shfl_sync(0xffffffffu, idx, 0);
     int chunk = P.chunk_blocks;
-    if (!kTable && idx >= 0 && P.sqA) chunk = certified_chunk(P, get_item<kTable>(P, idx), lane);
+    if (idx >= 0) chunk = certified_chunk(get_item<kTable>(P, idx), lane);
     if (lane == 0) {
         R.idx[slot] = idx;
         R.chunk[slot] = chunk;
@@ -440,7 +450,8 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_consta
             uint64_t g = 0;
             bool alive = true;
             for (int64_t j = 0; alive; ++j) {
-                const int64_t idx = P.sqA ? consume_item<false>(P, ring, j, alive) : produce_item(P, ring, j, alive);
+                const int64_t idx =
+                    P.cert ? consume_item<false>(P, ring, j, alive) : produce_item<kTable>(P, ring, j, alive);
                 if (idx < 0) break;
                 const Item it = get_item<kTable>(P, idx);
                 // One thread issues every copy, so the per-stage work is kept to a
@@ -519,7 +530,7 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_consta
             mbar_wait(&done, 0, P.err);
         }
     } else if (warp == PLANNER_WARP) {  // ---------------- planner: claims, certified chunks
-        if (P.sqA) {
+        if (P.cert) {
             bool alive = true;
             for (int64_t j = 0; alive; ++j)
                 if (plan_item<kTable>(P, ring, j, alive, lane) < 0) break;
@@ -949,6 +960,7 @@ int launch_gemm_tc(const Plan &pl, const void *Aw, const void *Bw, int32_t *S, i
         pl.tc_nb == BN && pl.tc_ndiag == 1) {
         P.sqA = sqA;
         P.sqB = sqB;
+        P.cert = 1;
     }
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     e = cudaMemsetAsync(P.sched, 0, sizeof(uint32_t), s);
@@ -971,7 +983,7 @@ int prepare_tc_attributes() {
 }
 
 int launch_gemm_tc_table(const TcItem *items, int64_t *cta_off, int64_t nitems, int ctas, int chunk_blocks, int *err,
-                         void *stream) {
+                         void *stream, int cert) {
     if (ctas <= 0 || nitems <= 0) return 0;
     TcParams P;
     std::memset(&P, 0, sizeof(P));
@@ -979,8 +991,9 @@ int launch_gemm_tc_table(const TcItem *items, int64_t *cta_off, int64_t nitems, 
     P.cta_off = cta_off;
     P.nitems = nitems;
     P.sched = reinterpret_cast<uint32_t *>(cta_off + 2);
-    P.chunk_blocks = chunk_blocks;
+    P.chunk_blocks = chunk_blocks;  // each item carries its own chunk; this is a fallback only
     P.err = err;
+    P.cert = cert;
     cudaError_t e = set_smem_attr(reinterpret_cast<const void *>(gemm_tc_kernel<true>), kSmemBytes);
     if (e != cudaSuccess) return (int)e;
     cudaStream_t s = static_cast<cudaStream_t>(stream);

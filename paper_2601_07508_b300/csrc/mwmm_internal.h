@@ -41,12 +41,14 @@ constexpr int kFusedPairs = 74;         // fused form: CTA pairs the planner ass
 struct TcItem {
     const uint8_t *Aw, *Bw;  // word bases of the problem's A and B
     int32_t *S;              // S of diagonal s0, K-range kc, at the tile's origin (row stride B_rows)
+    const uint32_t *sqA, *sqB;  // the problem's squared-digit maxima (certified chunks), or nullptr
     int64_t A_rows, B_rows, nkb, kb0, nkbc, mt, nt;
     int64_t plane;           // int32 elements between the S planes of consecutive diagonals
     int64_t b_wstride, b_kstride;  // bytes between consecutive B words / k-blocks
     int32_t s0, ndiag, nb, i0, ni, v, b_wpad;
     int32_t rv, cv;          // rows of the tile inside m, columns of each diagonal block inside n
     int32_t f16;             // 1: the words are fp16 (9-bit digits), 0: bf16
+    int32_t chunk;           // k-block x pair steps per FP32 chunk (the problem's tc_chunk / 64)
 };
 
 struct Plan {
@@ -161,8 +163,9 @@ int launch_tensor_products(const Plan &pl, uint8_t *ws, uint64_t *C, int64_t ldc
 // batched split: job records are opaque blobs of split_job_bytes() bytes
 size_t split_job_bytes();
 void split_job(const Plan &pl, int side, const uint64_t *M, int64_t ld, void *words, void *job, int job_index,
-               std::vector<int> &blocks);
-int launch_split_batched(const void *jobs, const int *blocks, int nblocks, int fp64, void *stream);
+               std::vector<int> &blocks, uint32_t *sq = nullptr);
+// sq: some job writes squared-digit maxima (SplitParams.sq set)
+int launch_split_batched(const void *jobs, const int *blocks, int nblocks, int fp64, void *stream, int sq = 0);
 size_t recombine_job_bytes();
 void recombine_job(const Plan &pl, const int32_t *S, uint64_t *C, int64_t ldc, void *rec, int index,
                    std::vector<int> &jobs);
@@ -178,8 +181,9 @@ int prepare_kernel_attributes();  // dynamic shared-memory limits, once per devi
 int tc_sm_count();
 // Items claimed in table order from the counter at cta_off[2] (cleared by
 // the launch): cta_off = {0, nitems, counter}.
+// cert: some item carries squared-digit maxima (certified chunks)
 int launch_gemm_tc_table(const TcItem *items, int64_t *cta_off, int64_t nitems, int ctas, int chunk_blocks, int *err,
-                         void *stream);
+                         void *stream, int cert = 0);
 int launch_fmod(const double *x, int64_t count, uint64_t p, double *out, void *stream);
 int launch_mulmod(const double *x, const double *y, int64_t count, uint64_t p, double *out, void *stream);
 int launch_wait_probe(int64_t cycles, int *err, void *stream);
@@ -205,6 +209,7 @@ struct BatchTables {
     std::vector<uint8_t> crt_recs;
     std::vector<int> crt_jobs;
     int nsplit = 0, nrec = 0, nf64 = 0, ncrt = 0, ctas = 0;
+    int cert = 0;  // some problem runs certified chunks: its splits write squared-digit maxima
 };
 constexpr int kBatchTables = 10;
 // Tables for problems[0..count) whose workspaces start at ws_base[i] (device).

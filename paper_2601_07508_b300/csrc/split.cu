@@ -324,6 +324,9 @@ __global__ void __launch_bounds__(256, 4) split_int8_kernel(const __grid_constan
 // single-product split).
 constexpr int kSplitTilesPerCta = 8;
 
+// kSq: jobs with P.sq set also write their squared-digit maxima (a separate
+// instantiation, launched when some job of the batch does)
+template <bool kSq>
 __global__ void __launch_bounds__(256, 4) split_batched_kernel(const SplitParams *jobs, const int4 *blocks,
                                                             int nblocks, int fp64) {
     __shared__ uint64_t tile[kST][kST + 1];
@@ -341,8 +344,12 @@ __global__ void __launch_bounds__(256, 4) split_batched_kernel(const SplitParams
             job = bl.x;
             __syncthreads();
         }
-        if (fp64) split_fp64_tile(P, tile, bl.y, bl.z);
-        else split_int8_tile<false>(P, tile, bl.y, bl.z);
+        if (fp64)
+            split_fp64_tile(P, tile, bl.y, bl.z);
+        else if (kSq && P.sq)  // block-uniform: P is in shared memory
+            split_int8_tile<kSq>(P, tile, bl.y, bl.z);
+        else
+            split_int8_tile<false>(P, tile, bl.y, bl.z);
     }
 }
 
@@ -391,8 +398,10 @@ size_t split_job_bytes() { return sizeof(SplitParams); }
 // `job` (sizeof(SplitParams) bytes) and append its tile blocks to `blocks`
 // as (job index, tile row, tile col, 0).
 void split_job(const Plan &pl, int side, const uint64_t *M, int64_t ld, void *words, void *job, int job_index,
-               std::vector<int> &blocks) {
+               std::vector<int> &blocks, uint32_t *sq) {
     SplitParams P = make_split_params(pl, side, M, ld, words);
+    if (sq && pl.tc_cert_chunk && pl.form == MWMM_FORM_INT8 && pl.digit_bits == 9 && P.rows_pad % (2 * kST) == 0)
+        P.sq = sq;
     std::memcpy(job, &P, sizeof(P));
     if (pl.nkb == 0 || P.rows_pad == 0) return;
     const int64_t kcols = pl.nkb * pl.kb_elems;
@@ -406,11 +415,16 @@ void split_job(const Plan &pl, int side, const uint64_t *M, int64_t ld, void *wo
         }
 }
 
-int launch_split_batched(const void *jobs, const int *blocks, int nblocks, int fp64, void *stream) {
+int launch_split_batched(const void *jobs, const int *blocks, int nblocks, int fp64, void *stream, int sq) {
     if (nblocks == 0) return 0;
     const int ctas = (nblocks + kSplitTilesPerCta - 1) / kSplitTilesPerCta;
-    split_batched_kernel<<<ctas, 256, 0, static_cast<cudaStream_t>(stream)>>>(
-        static_cast<const SplitParams *>(jobs), reinterpret_cast<const int4 *>(blocks), nblocks, fp64);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (sq && !fp64)
+        split_batched_kernel<true><<<ctas, 256, 0, s>>>(static_cast<const SplitParams *>(jobs),
+                                                         reinterpret_cast<const int4 *>(blocks), nblocks, fp64);
+    else
+        split_batched_kernel<false><<<ctas, 256, 0, s>>>(static_cast<const SplitParams *>(jobs),
+                                                          reinterpret_cast<const int4 *>(blocks), nblocks, fp64);
     return (int)cudaGetLastError();
 }
 

@@ -147,3 +147,27 @@ def test_multi_prime_batch_512_instances(M, oracle):
     assert fb.check() == 0
     for (_, _, C, _), R in zip(fitems, ref):
         assert torch.equal(C, R)
+
+
+@pytest.mark.parametrize("digit", [255, -255, 181])
+def test_batch_9bit_items_chunk_exactly(M, oracle, digit):
+    """Table items of 9-bit digits d at 15 of every 16 k positions (0 at the
+    16th): every K = 16 MMA adds an odd 15 d^2 (up to 975375) over K of
+    1300, so every FP32 chunk must stay within 2^24 (256 products; 512 when
+    certified, as for 181 but not 255), else a partial sum above 2^24
+    rounds.  Wide and narrow column tiles, next to an 8-bit-digit problem in
+    the same batch; every C equals the oracle."""
+    probs = []
+    for (m, n, k, b) in [(300, 400, 1300, 52), (150, 90, 1300, 26), (200, 300, 1300, 20)]:
+        p = inputs.largest_prime_below_pow2(b)
+        a = digit % p
+        A = np.full((m, k), a, np.uint64)
+        A[:, np.arange(k) % 16 == 15] = 0
+        probs.append((A, np.full((k, n), a, np.uint64), p))
+    items = [(_dev(A), _dev(B), torch.full((A.shape[0], B.shape[1]), -1, dtype=torch.int64, device="cuda"), p)
+             for A, B, p in probs]
+    batch = M.Batch(items, form="int8")
+    batch.run()
+    assert batch.check() == 0
+    for (A, B, p), (_, _, C, _) in zip(probs, items):
+        assert np.array_equal(C.cpu().numpy().view(np.uint64), oracle.matmul_mod(A, B, p))

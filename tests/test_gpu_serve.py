@@ -194,3 +194,30 @@ def test_serve_admission_against_budget(M, oracle):
     srv.close()
     for (A, B), (_, _, C) in zip(reqs, dev):
         assert np.array_equal(C.cpu().numpy().view(np.uint64), oracle.matmul_mod(A, B, p))
+
+
+def test_serve_9bit_table_requests_chunk_exactly(M, oracle):
+    """Small requests (batched table items) of 9-bit digits 255 at 15 of
+    every 16 k positions against -255: every K = 16 MMA adds an odd
+    -15 x 65025, so over K of 1300 each FP32 chunk is exact only at 256
+    products; every result equals the oracle."""
+    reqs = []
+    for (m, n, k, b) in [(100, 300, 1300, 52), (150, 90, 1300, 26), (120, 260, 1300, 35)]:
+        p = inputs.largest_prime_below_pow2(b)
+        A = np.full((m, k), 255, np.uint64)
+        A[:, np.arange(k) % 16 == 15] = 0
+        reqs.append((A, np.full((k, n), p - 255, np.uint64), p))
+    dev = [(_dev(A), _dev(B), torch.full((A.shape[0], B.shape[1]), -1, dtype=torch.int64, device="cuda"), p)
+           for A, B, p in reqs]
+    torch.cuda.synchronize()
+    srv = M.Server(2 << 30, max_inflight=2, max_batch=16, form="int8")
+    tickets = []
+    for dA, dB, C, p in dev:
+        st, t = srv.submit(dA, dB, C, p)
+        assert st == 0
+        tickets.append(t)
+    for t in tickets:
+        assert srv.wait(t, 60000) == 0
+    srv.close()
+    for (A, B, p), (_, _, C, _) in zip(reqs, dev):
+        assert np.array_equal(C.cpu().numpy().view(np.uint64), oracle.matmul_mod(A, B, p))
