@@ -324,11 +324,12 @@ __global__ void __launch_bounds__(256, 4) split_int8_kernel(const __grid_constan
 // single-product split).
 constexpr int kSplitTilesPerCta = 8;
 
-// kSq: jobs with P.sq set also write their squared-digit maxima (a separate
-// instantiation, launched when some job of the batch does)
+// kSq: jobs with P.sq set also write their squared-digit maxima (its own
+// kernel, launched when some job of the batch does; held to 3 CTAs per SM,
+// where 4 would spill)
 template <bool kSq>
-__global__ void __launch_bounds__(256, 4) split_batched_kernel(const SplitParams *jobs, const int4 *blocks,
-                                                            int nblocks, int fp64) {
+__device__ __forceinline__ void split_batched_body(const SplitParams *jobs, const int4 *blocks, int nblocks,
+                                                   int fp64) {
     __shared__ uint64_t tile[kST][kST + 1];
     __shared__ __align__(16) SplitParams P;  // the loops read it many times
     const int b0 = blockIdx.x * kSplitTilesPerCta;
@@ -351,6 +352,16 @@ __global__ void __launch_bounds__(256, 4) split_batched_kernel(const SplitParams
         else
             split_int8_tile<false>(P, tile, bl.y, bl.z);
     }
+}
+
+__global__ void __launch_bounds__(256, 4) split_batched_kernel(const SplitParams *jobs, const int4 *blocks,
+                                                            int nblocks, int fp64) {
+    split_batched_body<false>(jobs, blocks, nblocks, fp64);
+}
+
+__global__ void __launch_bounds__(256, 3) split_batched_sq_kernel(const SplitParams *jobs, const int4 *blocks,
+                                                               int nblocks, int fp64) {
+    split_batched_body<true>(jobs, blocks, nblocks, fp64);
 }
 
 SplitParams make_split_params(const Plan &pl, int side, const uint64_t *M, int64_t ld, void *words) {
@@ -420,11 +431,11 @@ int launch_split_batched(const void *jobs, const int *blocks, int nblocks, int f
     const int ctas = (nblocks + kSplitTilesPerCta - 1) / kSplitTilesPerCta;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (sq && !fp64)
-        split_batched_kernel<true><<<ctas, 256, 0, s>>>(static_cast<const SplitParams *>(jobs),
-                                                         reinterpret_cast<const int4 *>(blocks), nblocks, fp64);
+        split_batched_sq_kernel<<<ctas, 256, 0, s>>>(static_cast<const SplitParams *>(jobs),
+                                                      reinterpret_cast<const int4 *>(blocks), nblocks, fp64);
     else
-        split_batched_kernel<false><<<ctas, 256, 0, s>>>(static_cast<const SplitParams *>(jobs),
-                                                          reinterpret_cast<const int4 *>(blocks), nblocks, fp64);
+        split_batched_kernel<<<ctas, 256, 0, s>>>(static_cast<const SplitParams *>(jobs),
+                                                   reinterpret_cast<const int4 *>(blocks), nblocks, fp64);
     return (int)cudaGetLastError();
 }
 
