@@ -120,10 +120,12 @@ __device__ __forceinline__ Item computed_item(const TcParams &P, int64_t idx) {
     Item it;
     const int64_t mtc = P.mt_count;
     // item idx -> (tile, K-range kc, window grp_w): windows heaviest first,
-    // every tile of a window before the next window
+    // every tile of a window before the next window, every second pass over
+    // the tiles in reverse so that it starts on the tiles (and the words they
+    // share) the pass before has just left in L2
     const int64_t ntiles = mtc * P.nt_count;
-    const int64_t tile = idx % ntiles;
     const int64_t rest = idx / ntiles;
+    const int64_t tile = (rest & 1) ? ntiles - 1 - idx % ntiles : idx % ntiles;
     const int kc = (int)(rest % P.nkc);
     const int grp_w = (int)(rest / P.nkc);
     it.s0 = P.g_s0[grp_w];
