@@ -766,7 +766,9 @@ def main():
         gemm_flops += 2.0 * words * n ** 3 * calls
         gemm_ms += t["gemm_ms"]
         per_bits[str(b)] = {
-            "p": p, "int8_words": [d["u"], d["v"]], "int8_gops": 2.0 * n ** 3 / (t["total_ms"] / calls) / 1e6,
+            "p": p, "int8_words": [d["u"], d["v"]], "int8_digit_bits": d["tc_digit_bits"],
+            "int8_kernel": "gemm_tc_pair_kernel" if d["tc_pair"] else "gemm_tc_kernel",
+            "int8_gops": 2.0 * n ** 3 / (t["total_ms"] / calls) / 1e6,
             "int8_ms": t["total_ms"] / calls,
             "int8_phase_ms": {"split_a": t["split_a_ms"] / calls, "split_b": t["split_b_ms"] / calls,
                               "word_products": t["gemm_ms"] / calls, "recombine": t["recombine_ms"] / calls},
@@ -781,7 +783,11 @@ def main():
         traffic_per_launch = None if any(x is None for x in tr) else sum(tr) / len(tr)
     else:
         traffic_per_launch = None
-    roofline = {"bound": "tensor", "kernel": "gemm_tc_kernel (tcgen05.mma kind::f16, 8-bit digits in bf16 or 9-bit digits in fp16)",
+    kernels = sorted({v["int8_kernel"] for v in per_bits.values()})
+    roofline = {"bound": "tensor",
+                "kernel": " + ".join(kernels) + " (tcgen05.mma kind::f16; the planner's tile kernel per bitsize: "
+                          "gemm_tc_pair_kernel = 256 x 256 tiles on SM pairs, cta_group::2, 8-bit digits in bf16; "
+                          "gemm_tc_kernel = 128 x 256 tiles, one CTA, 9-bit digits in fp16)",
                 "achieved": achieved, "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
                 "frac": achieved / peaks["bf16_tflops"], "traffic": traffic_per_launch,
                 "peak_kind": "%s bf16 dense burst (cuBLAS); sustained %.1f -> frac %.3f" % (

@@ -105,11 +105,15 @@ typedef struct {
                          64 in [64, 1024] (0: 1024) */
     int64_t kc;       /* INT8 form: k-range of one INT32 sum, a multiple of 64
                          (0: the largest allowed by |S_s| < 2^31) */
-    int32_t tc_pair;  /* INT8 form, m > 128, n > 128: nonzero uses the two-CTA
-                         tcgen05 kernel (256 x 256 tiles on an SM pair,
-                         cta_group::2) instead of the one-CTA kernel (128 x 256
-                         tiles).  Bit-exact; measured on B300 within 3% of the
-                         one-CTA kernel either way; default 0 */
+    int32_t tc_pair;  /* INT8 and CRT forms, m > 128, n > 128: the tile kernel.
+                         1 = the two-CTA tcgen05 kernel (256 x 256 tiles on an
+                         SM pair, cta_group::2), -1 = the one-CTA kernel
+                         (128 x 256 tiles), 0 = the planner's choice: two-CTA
+                         for 8-bit digits when m >= 1024, 256-row tiles pad
+                         m by at most 3% and there are at least 296 items
+                         (measured on B300: 3-4% faster there), else one-CTA.
+                         Results are identical either way; other values:
+                         MWMM_ERR_ARG */
     int32_t f64_concat; /* FP64 form, Alg. 6: 0 = automatic (when min(m, n) < 64,
                          concatenate the words of the narrower side: B's
                          along n when n <= m and 2 <= v <= 4, else A's along m

@@ -186,7 +186,7 @@ void candidates(int form_req, int64_t m, int64_t n, int64_t k, uint64_t p, bool 
             std::vector<int64_t> kcs = {0};
             const int64_t half = (k / 2 + kTcKB - 1) / kTcKB * kTcKB;
             if (base.nkc == 1 && k >= 2048 && half < base.kc) kcs.push_back(half);
-            std::vector<int> pairs = {0};
+            std::vector<int> pairs = {-1};  // one-CTA tiles; the two-CTA kernel where it applies
             if (!batch && m > kTcBM && n > kTcBN / 2) pairs.push_back(1);
             for (int64_t kc : kcs)
                 for (int pair : pairs) {

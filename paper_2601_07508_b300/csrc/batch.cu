@@ -406,7 +406,7 @@ mwmm_status mwmm_batch_create(mwmm_batch_t *out, const mwmm_problem *probs, int 
             v = t.v;
         }
         o.lambda = 0;      // per-problem block sizes: always the bound
-        o.tc_pair = 0;
+        o.tc_pair = -1;    // table items are one-CTA tiles
         o.tc_fused = 1;    // table items write diagonal sums for the batched recombination
         o.ksplit = 1;      // batched FP64 tiles run the whole K range
         o.tc_fill = 1;     // the batch's many items fill the SMs; no K ranges for that

@@ -183,7 +183,7 @@ mwmm_status make_sub_plan(const Plan &pl, int64_t rows, Plan *out) {
     } else {
         o.tc_chunk = (int32_t)pl.tc_chunk;
         o.kc = pl.tc_fused ? 0 : pl.kc;
-        o.tc_pair = pl.tc_pair;
+        o.tc_pair = pl.tc_pair ? 1 : -1;  // the parent's tile kernel
         o.tc_fused = pl.tc_fused ? 2 : 1;  // every row block in the parent's layout of B's words
         o.tc_seg = pl.tc_seg;
         o.tc_digit_bits = pl.digit_bits;

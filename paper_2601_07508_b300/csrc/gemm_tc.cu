@@ -54,7 +54,7 @@ constexpr int BN = kTcBN;  // 256
 constexpr int STAGES = 4;
 constexpr int EPI_WARPS = 8;
 constexpr int THREADS = 32 * (3 + EPI_WARPS);       // one-CTA kernel: + the planner warp (warp 10)
-constexpr int THREADS_PAIR = 32 * (2 + EPI_WARPS);  // pair kernel
+constexpr int THREADS_PAIR = THREADS;              // pair kernel: the same roles
 constexpr int PLANNER_WARP = 2 + EPI_WARPS;
 constexpr int kCertBlocks = 8;  // certified chunk: 8 k-block x pair steps (512 products of 9-bit digits)
 constexpr uint32_t kTileA = BM * kTileBytes;  // 16 KB
@@ -234,7 +234,9 @@ struct ItemRing {
 // within 2^24, where FP32 is exact: then the item runs chunks of kCertBlocks
 // steps (512 products), else the worst-case chunk (256).  The whole warp
 // takes the windows in turn; every operand is an integer (sums of squares
-// <= 64 x 2^16 = 2^22).
+// <= 64 x 2^16 = 2^22).  kAG: 64-row groups per row tile (2 for 128 rows,
+// 4 for the pair kernel's 256).
+template <int kAG>
 __device__ __forceinline__ int certified_chunk(const Item &it, int lane) {
     if (it.ndiag != 1 || !it.sqA || 2 * it.chunk != kCertBlocks) return it.chunk;
     const int64_t nvb = (int64_t)it.ni * it.nkbc;
@@ -249,9 +251,11 @@ __device__ __forceinline__ int certified_chunk(const Item &it, int lane) {
             if (v < nvb) {
                 const int64_t kb = it.kb0 + v / it.ni;
                 const int i = it.i0 + (int)(v % it.ni), jw = it.s0 - i;
-                const uint32_t *pa = it.sqA + ((int64_t)i * it.nkb + kb) * ga + 2 * it.mt;
+                const uint32_t *pa = it.sqA + ((int64_t)i * it.nkb + kb) * ga + kAG * it.mt;
                 const uint32_t *pb = it.sqB + ((int64_t)jw * it.nkb + kb) * gb + 4 * it.nt;
-                const uint32_t sa = max(__ldg(pa), __ldg(pa + 1));
+                uint32_t sa = __ldg(pa);
+#pragma unroll
+                for (int q = 1; q < kAG; ++q) sa = max(sa, __ldg(pa + q));
                 const uint32_t sb = max(max(__ldg(pb), __ldg(pb + 1)), max(__ldg(pb + 2), __ldg(pb + 3)));
                 sum += (uint64_t)sa * sb;
             }
@@ -301,7 +305,7 @@ __device__ __forceinline__ int64_t plan_item(const TcParams &P, const ItemRing &
     }
     idx = __shfl_sync(0xffffffffu, idx, 0);
     int chunk = P.chunk_blocks;
-    if (idx >= 0) chunk = certified_chunk(get_item<kTable>(P, idx), lane);
+    if (idx >= 0) chunk = certified_chunk<2>(get_item<kTable>(P, idx), lane);
     if (lane == 0) {
         R.idx[slot] = idx;
         R.chunk[slot] = chunk;
@@ -585,27 +589,39 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_consta
 // computes a 256 x 256 tile with tcgen05.mma.cta_group::2 (M = 256 split over
 // the pair, each CTA holding its 128 rows of A and its 128-row half of B).
 // Each SM then receives 32 KB of operands per 64-wide k-block instead of
-// 48 KB, and 6 stages fit in shared memory.  Roles per CTA as above; only the
-// even CTA ("leader") issues MMAs.  Both CTAs load their halves with tensor
-// TMA (.cta_group::2), whose completion lands directly on the leader's
-// barrier, so the leader waits on one barrier per stage; its commits are
-// multicast to both CTAs.  The word tiles are already in their shared-memory
-// order, so the tensor maps describe them as plain 2-D arrays of 128-byte rows
-// (no TMA swizzle).
+// 48 KB, and 6 stages fit in shared memory.  Roles per CTA as in the one-CTA
+// kernel; only the even CTA ("leader") issues MMAs.  Both CTAs load their
+// halves with tensor TMA (.cta_group::2), whose completion lands directly on
+// the leader's barrier, so the leader waits on one barrier per stage; its
+// commits are multicast to both CTAs.  The word tiles are already in their
+// shared-memory order, so the tensor maps describe them as plain 2-D arrays
+// of 128-byte rows (no TMA swizzle).
+//
+// Items are claimed as in the one-CTA kernel, by the leader alone: its
+// publisher (the planner warp with certified chunks, else its producer lane)
+// writes each index and chunk into both CTAs' rings (the peer's through
+// distributed shared memory, then a release arrive on the peer's barrier),
+// and every consumer of both CTAs releases the slot on the leader's empty
+// barrier.  Item order, k-block-outer loads and certified chunks follow the
+// one-CTA kernel.
 constexpr int P_STAGES = 6;
 constexpr int BM2 = 256;
 constexpr uint32_t kTileA2 = 128 * kTileBytes;  // own 128 rows of A: 16 KB
 constexpr uint32_t kTileB2 = 128 * kTileBytes;  // own half of B: 16 KB
 constexpr int kSmemPair = P_STAGES * (kTileA2 + kTileB2) + kStageBytes + 1024;
 constexpr uint32_t kIdescPair = idesc_bf16(BM2, BN);
+// consumers of a ring slot: both CTAs' producer lanes and epilogue warps, and
+// the leader's MMA lane
+constexpr int kPairRingConsumers = 2 * (1 + EPI_WARPS) + 1;
 
 __device__ __forceinline__ Item pair_item(const TcParams &P, int64_t idx) {
     // tiles of 256 rows: mt counts 256-row tiles here; A_rows % 256 == 0
     Item it;
     const int64_t mt2 = P.mt_count / 2;
     const int64_t ntiles = mt2 * P.nt_count;
-    const int64_t tile = idx % ntiles;
     const int64_t rest = idx / ntiles;
+    // every second pass over the tiles in reverse, as in computed_item
+    const int64_t tile = (rest & 1) ? ntiles - 1 - idx % ntiles : idx % ntiles;
     const int kc = (int)(rest % P.nkc);
     const int grp_w = (int)(rest / P.nkc);  // nb = 256: one diagonal per window
     it.s0 = P.g_s0[grp_w];
@@ -614,6 +630,10 @@ __device__ __forceinline__ Item pair_item(const TcParams &P, int64_t idx) {
     it.i0 = P.g_i0[grp_w];
     it.ni = P.g_ni[grp_w];
     it.v = P.v;
+    it.f16 = P.f16;
+    it.chunk = P.chunk_blocks;
+    it.sqA = P.sqA;
+    it.sqB = P.sqB;
     const int64_t gsz = mt2 * kGroupN;
     const int64_t grp = tile / gsz, t = tile % gsz;
     const int64_t width = P.nt_count - grp * kGroupN < kGroupN ? P.nt_count - grp * kGroupN : kGroupN;
@@ -632,7 +652,77 @@ __device__ __forceinline__ Item pair_item(const TcParams &P, int64_t idx) {
     const int64_t rv = P.m - it.mt * BM2, cv = P.n - it.nt * BN;  // clipped to the 256 x 256 tile
     it.rv = (int)(rv < BM2 ? rv : BM2);
     it.cv = (int)(cv < BN ? cv : BN);
+    it.nn = BN;
     return it;
+}
+
+// The ring of one CTA of a pair, with the cluster addresses the leader's
+// publisher writes to (the peer's slots and full barriers) and the consumers
+// release to (the leader's empty barriers).
+struct PairRing {
+    int64_t *idx;
+    int32_t *chunk;
+    uint64_t *full, *empty;  // empty: used in the leader only
+    uint32_t peer_idx, peer_chunk, peer_full, lead_empty;
+};
+
+// Leader: claim the j-th item (lane 0), work out its chunk (the whole warp
+// when kWarp, certified chunks), publish it to both CTAs.  The slot's
+// previous readers in both CTAs have released it (acquire at cluster scope
+// orders this lane's stores into the peer after the peer's reads).
+template <bool kWarp>
+__device__ __forceinline__ int64_t pair_publish(const TcParams &P, const PairRing &R, int64_t j, bool &alive,
+                                                int lane) {
+    const int slot = (int)(j % kRing);
+    int ok = 1;
+    int64_t idx = -1;
+    if (lane == 0) {
+        ok = mbar_wait_cluster(&R.empty[slot], (uint32_t)(((j / kRing) & 1) ^ 1), P.err) ? 1 : 0;
+        if (ok) {
+            idx = (int64_t)atomicAdd(P.sched, 1u);
+            if (idx >= P.nitems) idx = -1;
+        }
+    }
+    if (kWarp) {
+        ok = __shfl_sync(0xffffffffu, ok, 0);
+        idx = __shfl_sync(0xffffffffu, idx, 0);
+    }
+    if (!ok) {
+        alive = false;
+        return -1;
+    }
+    int chunk = P.chunk_blocks;
+    if (kWarp && idx >= 0) chunk = certified_chunk<4>(pair_item(P, idx), lane);
+    if (lane == 0) {
+        R.idx[slot] = idx;
+        R.chunk[slot] = chunk;
+        st_cluster_u64(R.peer_idx + (uint32_t)(slot * sizeof(int64_t)), (uint64_t)idx);
+        st_cluster_u32(R.peer_chunk + (uint32_t)(slot * sizeof(int32_t)), (uint32_t)chunk);
+        mbar_arrive(&R.full[slot]);
+        // release at cluster scope: the two stores above are visible to the
+        // peer's waiters of this phase
+        mbar_arrive_cluster(R.peer_full + (uint32_t)(slot * sizeof(uint64_t)));
+    }
+    return idx;
+}
+
+// Any role of either CTA: wait for the j-th item in this CTA's ring, read it,
+// release the slot on the leader's empty barrier (one lane when kWarp).
+template <bool kWarp>
+__device__ __forceinline__ int64_t pair_consume(const TcParams &P, const PairRing &R, int64_t j, bool &alive,
+                                                int *chunk) {
+    const int slot = (int)(j % kRing);
+    bool ok = mbar_wait_cluster(&R.full[slot], (uint32_t)((j / kRing) & 1), P.err);
+    if (kWarp) ok = __all_sync(0xffffffffu, ok);
+    if (!ok) {
+        alive = false;
+        return -1;
+    }
+    const int64_t idx = R.idx[slot];
+    if (chunk) *chunk = R.chunk[slot];
+    if (kWarp) __syncwarp();
+    if (!kWarp || (threadIdx.x & 31) == 0) mbar_arrive_cluster(R.lead_empty + (uint32_t)(slot * sizeof(uint64_t)));
+    return idx;
 }
 
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS_PAIR, 1)
@@ -640,6 +730,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS_PAIR, 1)
                         const __grid_constant__ CUtensorMap tmB) {
     extern __shared__ uint8_t smem_raw[];
     __shared__ __align__(8) uint64_t full[P_STAGES], empty[P_STAGES], tfull[2], tempty[2], done;
+    __shared__ __align__(8) uint64_t rfull[kRing], rempty[kRing];
+    __shared__ int64_t ring_idx[kRing];
+    __shared__ int32_t ring_chunk[kRing];
     __shared__ uint32_t tmem_base_sh;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -650,6 +743,14 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS_PAIR, 1)
     uint8_t *sA = smem_raw + pad;
     uint8_t *sB = sA + P_STAGES * kTileA2;
     int32_t *sStage = reinterpret_cast<int32_t *>(sB + P_STAGES * kTileB2);
+    const PairRing ring{ring_idx,
+                        ring_chunk,
+                        rfull,
+                        rempty,
+                        peer_addr(&ring_idx[0], 1),
+                        peer_addr(&ring_chunk[0], 1),
+                        peer_addr(&rfull[0], 1),
+                        peer_addr(&rempty[0], 0)};
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < P_STAGES; ++s) {
@@ -659,6 +760,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS_PAIR, 1)
         for (int b = 0; b < 2; ++b) {
             mbar_init(&tfull[b], 1);
             mbar_init(&tempty[b], 2 * EPI_WARPS);  // both CTAs' epilogue warps (leader's copy)
+        }
+        for (int r = 0; r < kRing; ++r) {
+            mbar_init(&rfull[r], 1);
+            mbar_init(&rempty[r], kPairRingConsumers);  // leader's copy
         }
         mbar_init(&done, 1);
         fence_mbar_init();
@@ -674,23 +779,32 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS_PAIR, 1)
     cluster_sync_all();  // barriers of both CTAs initialised, TMEM allocated
     tc_fence_after();
     const uint32_t tmem_base = tmem_base_sh;
-    const int64_t cid = blockIdx.x >> 1, ncl = gridDim.x >> 1;
 
     if (warp == 0) {
         if (lane == 0) {  // ---------------- TMA producer (both CTAs)
             const uint32_t lead_full = peer_addr(&full[0], 0);
             uint64_t g = 0;
             bool alive = true;
-            for (int64_t idx = cid; alive && idx < P.nitems; idx += ncl) {
+            for (int64_t j = 0; alive; ++j) {
+                int64_t idx;
+                if (leader && !P.cert) {  // the leader's producer publishes, then reads as a consumer
+                    idx = pair_publish<false>(P, ring, j, alive, 0);
+                    if (alive) mbar_arrive(&rempty[(int)(j % kRing)]);
+                } else {
+                    idx = pair_consume<false>(P, ring, j, alive, nullptr);
+                }
+                if (idx < 0) break;
                 const Item it = pair_item(P, idx);
-                for (int ii = 0; alive && ii < it.ni; ++ii) {
-                    const int i = it.i0 + ii;
-                    const int j = it.s0 - i;
-                    // row coordinates of the tensor maps (the host checks they fit int32)
-                    int32_t ya = (int32_t)(((int64_t)i * it.nkb + it.kb0) * it.A_rows + it.mt * BM2 + rank * 128);
-                    int32_t yb = (int32_t)(((int64_t)j * it.nkb + it.kb0) * it.B_rows + it.nt * BN + rank * 128);
-                    for (int64_t kb = 0; kb < it.nkbc;
-                         ++kb, ++g, ya += (int32_t)it.A_rows, yb += (int32_t)it.B_rows) {
+                // k-block outer, the diagonal's pairs inner (as in the one-CTA kernel)
+                for (int64_t kb = 0; alive && kb < it.nkbc; ++kb) {
+                    for (int ii = 0; ii < it.ni; ++ii, ++g) {
+                        const int i = it.i0 + ii;
+                        const int jw = it.s0 - i;
+                        // row coordinates of the tensor maps (the host checks they fit int32)
+                        const int32_t ya = (int32_t)(((int64_t)i * it.nkb + it.kb0 + kb) * it.A_rows + it.mt * BM2 +
+                                                     rank * 128);
+                        const int32_t yb = (int32_t)(((int64_t)jw * it.nkb + it.kb0 + kb) * it.B_rows + it.nt * BN +
+                                                     rank * 128);
                         const int slot = (int)(g % P_STAGES);
                         if (!mbar_wait(&empty[slot], (uint32_t)(((g / P_STAGES) & 1) ^ 1), P.err)) {
                             alive = false;
@@ -720,10 +834,13 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS_PAIR, 1)
             bool alive = true;
             const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
             const uint32_t idesc_pair = P.f16 ? idesc_f16(BM2, BN) : kIdescPair;
-            for (int64_t idx = cid; alive && idx < P.nitems; idx += ncl) {
+            for (int64_t j = 0; alive; ++j) {
+                int chunk = P.chunk_blocks;
+                const int64_t idx = pair_consume<false>(P, ring, j, alive, &chunk);
+                if (idx < 0) break;
                 const Item it = pair_item(P, idx);
                 const int64_t nvb = (int64_t)it.ni * it.nkbc;
-                for (int64_t t0 = 0; alive && t0 < nvb; t0 += P.chunk_blocks, ++c) {
+                for (int64_t t0 = 0; alive && t0 < nvb; t0 += chunk, ++c) {
                     const int buf = (int)(c & 1);
                     if (!mbar_wait(&tempty[buf], (uint32_t)(((c >> 1) & 1) ^ 1), P.err)) {
                         alive = false;
@@ -731,7 +848,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS_PAIR, 1)
                     }
                     tc_fence_after();
                     const uint32_t dt = tmem_base + (uint32_t)(buf * BN);
-                    const int64_t tend = t0 + P.chunk_blocks < nvb ? t0 + P.chunk_blocks : nvb;
+                    const int64_t tend = t0 + chunk < nvb ? t0 + chunk : nvb;
                     for (int64_t t = t0; t < tend; ++t, ++g) {
                         const int slot = (int)(g % P_STAGES);
                         const uint32_t par = (uint32_t)((g / P_STAGES) & 1);
@@ -752,6 +869,12 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS_PAIR, 1)
             mma_commit_pair(&done, 1);
             mbar_wait(&done, 0, P.err);
         }
+    } else if (warp == PLANNER_WARP) {  // ---------------- planner (leader, certified chunks)
+        if (leader && P.cert) {
+            bool alive = true;
+            for (int64_t j = 0; alive; ++j)
+                if (pair_publish<true>(P, ring, j, alive, lane) < 0) break;
+        }
     } else {  // -------------------------------- epilogue warps 2..9 (both CTAs)
         const int quarter = warp & 3;
         const int half = (warp - 2) >> 2;
@@ -759,10 +882,13 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS_PAIR, 1)
         const uint32_t lead_tempty = peer_addr(&tempty[0], 0);
         uint64_t c = 0;
         bool alive = true;
-        for (int64_t idx = cid; alive && idx < P.nitems; idx += ncl) {
+        for (int64_t j = 0; alive; ++j) {
+            int chunk = P.chunk_blocks;
+            const int64_t idx = pair_consume<true>(P, ring, j, alive, &chunk);
+            if (idx < 0) break;
             const Item it = pair_item(P, idx);
             const int64_t nvb = (int64_t)it.ni * it.nkbc;
-            const int64_t nch = (nvb + P.chunk_blocks - 1) / P.chunk_blocks;
+            const int64_t nch = (nvb + chunk - 1) / chunk;
             int32_t acc[128];
 #pragma unroll
             for (int e = 0; e < 128; ++e) acc[e] = 0;
@@ -938,6 +1064,15 @@ int launch_gemm_tc(const Plan &pl, const void *Aw, const void *Bw, int32_t *S, i
         P.g_plane[g] = g < ng ? gpl[order[g]] : 0;
     }
     if (P.nitems == 0) return 0;
+    P.sched = reinterpret_cast<uint32_t *>(reinterpret_cast<uint8_t *>(S) + (pl.sched_off - pl.S_off));
+    // certified chunks: twice the worst-case chunk, one 256-wide diagonal per item
+    if (sqA && sqB && pl.tc_cert_chunk == kCertBlocks * kTcKB && 2 * P.chunk_blocks == kCertBlocks &&
+        pl.tc_nb == BN && pl.tc_ndiag == 1) {
+        P.sqA = sqA;
+        P.sqB = sqB;
+        P.cert = 1;
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (pl.tc_pair) {
         P.nitems = (int64_t)(P.mt_count / 2) * P.nt_count * nwin * pl.nkc;
         cudaError_t e = set_smem_attr(reinterpret_cast<const void *>(gemm_tc_pair_kernel), kSmemPair);
@@ -949,22 +1084,14 @@ int launch_gemm_tc(const Plan &pl, const void *Aw, const void *Bw, int32_t *S, i
         int r = encode_rows_map(&tmA, Aw, (uint64_t)pl.u * pl.nkb * pl.A_rows, 128);
         if (r == 0) r = encode_rows_map(&tmB, Bw, (uint64_t)pl.v * pl.nkb * pl.B_rows, 128);
         if (r != 0) return r;
-        gemm_tc_pair_kernel<<<(unsigned)(2 * ncl), THREADS_PAIR, kSmemPair, static_cast<cudaStream_t>(stream)>>>(P, tmA,
-                                                                                                            tmB);
+        e = cudaMemsetAsync(P.sched, 0, sizeof(uint32_t), s);
+        if (e != cudaSuccess) return (int)e;
+        gemm_tc_pair_kernel<<<(unsigned)(2 * ncl), THREADS_PAIR, kSmemPair, s>>>(P, tmA, tmB);
         return (int)cudaGetLastError();
     }
     cudaError_t e = set_smem_attr(reinterpret_cast<const void *>(gemm_tc_kernel<false>), kSmemBytes);
     if (e != cudaSuccess) return (int)e;
     const int64_t sms = sm_count();
-    P.sched = reinterpret_cast<uint32_t *>(reinterpret_cast<uint8_t *>(S) + (pl.sched_off - pl.S_off));
-    // certified chunks: twice the worst-case chunk, one 256-wide diagonal per item
-    if (sqA && sqB && pl.tc_cert_chunk == kCertBlocks * kTcKB && 2 * P.chunk_blocks == kCertBlocks &&
-        pl.tc_nb == BN && pl.tc_ndiag == 1) {
-        P.sqA = sqA;
-        P.sqB = sqB;
-        P.cert = 1;
-    }
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
     e = cudaMemsetAsync(P.sched, 0, sizeof(uint32_t), s);
     if (e != cudaSuccess) return (int)e;
     const unsigned grid = (unsigned)(P.nitems < sms ? P.nitems : sms);

@@ -29,6 +29,8 @@ inline int64_t tc_chunk_limit(int bits) { return int64_t(1) << (26 - 2 * bits); 
 inline int64_t int32_sum_limit(int bits) { return ((int64_t(1) << 31) - 1) >> (2 * bits - 2); }
 constexpr int kFusedSeg = 64;           // fused form: default k-blocks per segment (4096 k)
 constexpr int kFusedPairs = 74;         // fused form: CTA pairs the planner assumes (148 SMs)
+constexpr int64_t kPairMinM = 1024;     // default two-CTA kernel: rows at least
+constexpr int64_t kPairMinItems = 4 * 74;  // and at least four waves of 256 x 256 items
 
 // One work item of the tcgen05 kernel: the word products of the diagonals
 // s0 .. s0 + ndiag - 1 over k-blocks [kb0, kb0 + nkbc) for the 128-row tile mt
@@ -81,7 +83,7 @@ struct Plan {
     // INT8 form
     int digit_bits = 8;  // 8: bf16-carried digits in [-128, 128]; 9: fp16-carried digits in [-256, 256]
     int64_t tc_chunk = 0, kc = 0;
-    int tc_pair = 0;  // 1: 2-CTA kernel, A rows padded to 256
+    int tc_pair = 0;  // 1: 2-CTA kernel, A rows padded to 256 (the planner's choice or the caller's)
     // Fused recombination (gemm_tc_fused.cu): 256 x 128 tiles on CTA pairs,
     // A rows padded to 256 and B rows to 128; segments of tc_seg k-blocks;
     // K parts = ksplit (of kbr k-blocks), their residues in ksplit planes of

@@ -390,8 +390,22 @@ mwmm_status make_plan(Plan *pl, int64_t m, int64_t n, int64_t k, uint64_t p, int
         }
         P.tc_ndiag = kTcBN / P.tc_nb < P.nsums ? kTcBN / P.tc_nb : P.nsums;
         if (form == MWMM_FORM_CRT8) P.tc_ndiag = 1;  // each modulus pairs A_i with B_i only: no windows
-        // the 2-CTA kernel (opt-in) computes 256 x 256 tiles
-        P.tc_pair = (m > kTcBM && P.tc_nb == kTcBN && o.tc_pair) ? 1 : 0;
+        // Tile kernel.  The two-CTA kernel (256 x 256 tiles on an SM pair)
+        // runs on request (tc_pair = 1), never with tc_pair = -1, and by
+        // default (0) for 8-bit digits on products large enough that 256-row
+        // tiles add at most 3% padding and leave several waves of items:
+        // measured on B300 at 4096^3, 3-4% faster than the one-CTA kernel at
+        // 20, 40 and 48 bits.  With 9-bit digits (drains twice as often, each
+        // finished on both SMs before the pair reuses an accumulator) it was
+        // level at 52 bits and 2% slower at 26, so those keep one CTA per tile.
+        if (o.tc_pair < -1 || o.tc_pair > 1) return MWMM_ERR_ARG;
+        bool pair = o.tc_pair == 1;
+        if (o.tc_pair == 0 && form == MWMM_FORM_INT8 && P.digit_bits == 8 && P.tc_nb == kTcBN && m >= kPairMinM) {
+            const int64_t rows1 = round_up(m, kTcBM), rows2 = round_up(m, 2 * kTcBM);
+            const int64_t items = (rows2 / (2 * kTcBM)) * ceil_div(n, kTcBN) * P.nsums * P.nkc;
+            pair = rows2 * 32 <= rows1 * 33 && items >= kPairMinItems;
+        }
+        P.tc_pair = (m > kTcBM && P.tc_nb == kTcBN && pair) ? 1 : 0;
         // Fused recombination (INT8 form, n > 128) on request (tc_fused = 2):
         // its 256 x 128 pair tiles run the word products at about 60% of the
         // one-CTA 128 x 256 kernel's rate on B300, so the default keeps the
@@ -466,9 +480,8 @@ mwmm_status make_plan(Plan *pl, int64_t m, int64_t n, int64_t k, uint64_t p, int
         }
         // Certified 512-product chunks for 9-bit digits (twice the
         // worst-case 256) where each item is one 256-wide diagonal tile.
-        // (Not with an explicit tc_chunk, which fixes the chunk, nor for the
-        // pair kernel.)
-        if (form == MWMM_FORM_INT8 && P.digit_bits == 9 && !P.tc_fused && !P.tc_pair && P.tc_nb == kTcBN && k > 0 &&
+        // (Not with an explicit tc_chunk, which fixes the chunk.)
+        if (form == MWMM_FORM_INT8 && P.digit_bits == 9 && !P.tc_fused && P.tc_nb == kTcBN && k > 0 &&
             o.tc_chunk == 0) {
             P.tc_cert_chunk = 2 * (int)P.tc_chunk;
             P.sq_off = P.ws_bytes;

@@ -221,7 +221,7 @@ def _ld(t) -> int:
 
 # --------------------------------------------------------------------------- C-named calls
 def mwmm_plan(m: int, n: int, k: int, p: int, u: int = 0, v: int = 0, form="auto", lam: int = 0,
-              validate: bool = False, tc_chunk: int = 0, kc: int = 0, tc_pair: bool = False,
+              validate: bool = False, tc_chunk: int = 0, kc: int = 0, tc_pair: Optional[bool] = None,
               f64_concat: int = 0, ksplit: int = 0, tc_fused: int = 0, tc_seg: int = 0,
               tc_digit_bits: int = 0, tc_fill: int = 0) -> int:
     if isinstance(form, str):
@@ -232,7 +232,8 @@ def mwmm_plan(m: int, n: int, k: int, p: int, u: int = 0, v: int = 0, form="auto
     o.validate = 1 if validate else 0
     o.tc_chunk = tc_chunk
     o.kc = kc
-    o.tc_pair = 1 if tc_pair else 0
+    # None: the planner's choice; True / False: the two-CTA / one-CTA kernel; an int is passed as is
+    o.tc_pair = 0 if tc_pair is None else ((1 if tc_pair else -1) if isinstance(tc_pair, bool) else int(tc_pair))
     o.f64_concat = f64_concat
     o.ksplit = ksplit
     o.tc_fused = tc_fused
@@ -604,7 +605,7 @@ class Plan:
     """Owns a plan handle: ``Plan(m, n, k, p, form="int8")``, then ``.matmul(A, B)``."""
 
     def __init__(self, m: int, n: int, k: int, p: int, u: int = 0, v: int = 0, form="auto", lam: int = 0,
-                 validate: bool = False, tc_chunk: int = 0, kc: int = 0, tc_pair: bool = False,
+                 validate: bool = False, tc_chunk: int = 0, kc: int = 0, tc_pair: Optional[bool] = None,
                  f64_concat: int = 0, ksplit: int = 0, tc_fused: int = 0, tc_seg: int = 0,
                  tc_digit_bits: int = 0, tc_fill: int = 0):
         self.handle = mwmm_plan(m, n, k, p, u, v, form, lam, validate, tc_chunk, kc, tc_pair, f64_concat, ksplit,

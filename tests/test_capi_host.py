@@ -162,6 +162,39 @@ def test_int8_unfused_plan_tile_kernel_choice(M, m, n, pair, want_pair, want_row
     assert d["workspace_bytes"] >= d["S_off"] + d["nsums"] * d["nkc"] * d["A_rows"] * d["B_rows"] * 4
 
 
+@pytest.mark.parametrize("m,n,k,b,form,want", [
+    (4096, 4096, 4096, 20, "int8", 1),   # 8-bit digits, 16 x 16 x 5 = 1280 pair items
+    (4096, 4096, 4096, 48, "int8", 1),
+    (2048, 2048, 2048, 20, "int8", 1),   # 8 x 8 x 5 = 320 items
+    (4096, 4096, 4096, 26, "int8", 0),   # 9-bit digits: one CTA per tile
+    (4096, 4096, 4096, 52, "int8", 0),
+    (1024, 1024, 4096, 20, "int8", 0),   # 4 x 4 x 5 = 80 items: too few waves of pairs
+    (1100, 4096, 4096, 20, "int8", 0),   # 1280 rows instead of 1152: 11% padding
+    (4000, 4096, 4096, 40, "int8", 1),   # 4096 rows either way
+    (900, 8192, 4096, 20, "int8", 0),    # m < 1024
+    (4096, 100, 4096, 20, "int8", 0),    # narrow n: diagonal windows, one-CTA kernel
+    (4096, 4096, 4096, 40, "crt8", 0),   # the CRT form keeps one CTA per tile unless asked
+])
+def test_default_tile_kernel_choice(M, m, n, k, b, form, want):
+    """tc_pair = 0 (None in Python): the two-CTA kernel for 8-bit digits on
+    large products (m >= 1024, at most 3% more padded rows, >= 296 items of
+    256 x 256), else one CTA per tile; True / False force either kernel."""
+    p = SWEEP[b] if b in SWEEP else inputs.largest_prime_below_pow2(b)
+    d = M.Plan(m, n, k, p, form=form).info
+    assert d["tc_pair"] == want
+    assert d["A_rows"] % (256 if want else 128) == 0
+    assert M.Plan(m, n, k, p, form=form, tc_pair=False).info["tc_pair"] == 0
+    if n > 128:
+        assert M.Plan(m, n, k, p, form=form, tc_pair=True).info["tc_pair"] == 1
+
+
+def test_tile_kernel_option_range(M):
+    p = SWEEP[20]
+    for bad in (2, -2):
+        with pytest.raises(M.MwmmError):
+            M.mwmm_plan(4096, 4096, 4096, p, 0, 0, "int8", tc_pair=bad)
+
+
 @pytest.mark.parametrize("m,n,opt,want", [
     (700, 300, 0, 0), (700, 300, 1, 0),   # default and 1: diagonal sums in the workspace
     (700, 300, 2, 1), (129, 129, 2, 1),   # 2: fused whenever n > 128
@@ -364,8 +397,8 @@ def test_underfill_k_split_plans(M, form):
 def test_certified_chunk_plans(M):
     """9-bit digits on 256-wide column tiles get certified 512-product chunks
     (tc_cert_chunk) and a squared-digit region after the item counter; 8-bit
-    digits, narrow n, an explicit tc_chunk, the pair kernel and the fused
-    form keep the worst-case chunk only."""
+    digits, narrow n, an explicit tc_chunk and the fused form keep the
+    worst-case chunk only; the pair kernel certifies too."""
     p26, p20 = SWEEP[26], SWEEP[20]
     d = M.Plan(300, 700, 1000, p26, form="int8").info
     assert d["tc_digit_bits"] == 9 and d["tc_chunk"] == 256 and d["tc_cert_chunk"] == 512
@@ -377,7 +410,8 @@ def test_certified_chunk_plans(M):
     assert M.Plan(300, 700, 1000, p20, form="int8").info["tc_cert_chunk"] == 0
     assert M.Plan(300, 100, 1000, p26, form="int8").info["tc_cert_chunk"] == 0
     assert M.Plan(300, 700, 1000, p26, form="int8", tc_chunk=128).info["tc_cert_chunk"] == 0
-    assert M.Plan(300, 700, 1000, p26, form="int8", tc_pair=True).info["tc_cert_chunk"] == 0
+    dp = M.Plan(300, 700, 1000, p26, form="int8", tc_pair=True).info
+    assert dp["tc_pair"] == 1 and dp["tc_cert_chunk"] == 512
     assert M.Plan(300, 700, 1000, p26, form="int8", tc_fused=2).info["tc_cert_chunk"] == 0
     assert M.Plan(300, 700, 1000, p26, form="crt8").info["tc_cert_chunk"] == 0
 

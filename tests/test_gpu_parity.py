@@ -543,16 +543,18 @@ def _sq_expected(dig, rows_pad, nkb):
 
 
 @pytest.mark.parametrize("b", [26, 52])
-def test_f16_squared_digit_maxima_match_oracle(M, oracle, b):
+@pytest.mark.parametrize("pair", [False, True])
+def test_f16_squared_digit_maxima_match_oracle(M, oracle, b, pair):
     """The splits of a certified plan write, per word, k-block and 64-row
     group, the largest row sum of squared digits: recomputed from the
-    oracle's digits (A's rows, B's columns), ragged tiles included."""
+    oracle's digits (A's rows, B's columns), ragged tiles included (128- and
+    256-row tiles)."""
     p = SWEEP[b]
     m, n, k = 300, 700, 1000
     A, B = inputs.problem(b + 31, m, n, k, p)
-    plan = M.Plan(m, n, k, p, form="int8")
+    plan = M.Plan(m, n, k, p, form="int8", tc_pair=pair)
     d = plan.info
-    assert d["tc_cert_chunk"] == 512
+    assert d["tc_cert_chunk"] == 512 and d["tc_pair"] == pair
     ws = plan.alloc_workspace()
     C = host(plan.matmul(dev(A), dev(B)))
     assert plan.check() == 0 and np.array_equal(C, oracle.matmul_mod(A, B, p))
@@ -569,13 +571,15 @@ def test_f16_squared_digit_maxima_match_oracle(M, oracle, b):
 
 @pytest.mark.parametrize("b", [26, 52])
 @pytest.mark.parametrize("digit", [181, 183, -181])
-def test_f16_certified_chunk_at_its_bound(M, oracle, b, digit):
+@pytest.mark.parametrize("pair", [False, True])
+def test_f16_certified_chunk_at_its_bound(M, oracle, b, digit, pair):
     """Constant digits d (odd): every product is d^2 (odd), and a 512-product
     chunk of them sums to 512 d^2.  For |d| = 181 that is 16,773,632 (just
     below 2^24) and the certificate 8 x 8 (64 d^2)^2 <= 2^48 holds exactly
     at its bound, so the certified chunk runs with partial sums up to
     2^23.9996; for 183 it fails (512 d^2 > 2^24) and the 256-product chunk
-    must run -- a wrong decision would round an odd partial sum above 2^24."""
+    must run -- a wrong decision would round an odd partial sum above 2^24.
+    Both the one-CTA and the pair kernel (256-row tiles)."""
     p = SWEEP[b]
     a = digit % p
     k = 2 * 512 + 64 + 37
@@ -583,23 +587,24 @@ def test_f16_certified_chunk_at_its_bound(M, oracle, b, digit):
     B = np.full((k, 300), a, np.uint64)
     u = oracle.digit_words(p, 9)
     assert list(oracle.split_signed(np.array([a], np.uint64), p, u, 9)[:, 0]) == [digit] + [0] * (u - 1)
-    C, plan = gpu_product(M, A, B, p, form="int8")
-    assert plan.info["tc_cert_chunk"] == 512
+    C, plan = gpu_product(M, A, B, p, form="int8", tc_pair=pair)
+    assert plan.info["tc_cert_chunk"] == 512 and plan.info["tc_pair"] == pair
     assert np.all(C == (digit * digit * k) % p)
     assert np.array_equal(C, oracle.matmul_mod(A, B, p))
 
 
 @pytest.mark.parametrize("b", [26, 52])
-def test_f16_certified_and_worst_case_items_mixed(M, oracle, b):
+@pytest.mark.parametrize("pair", [False, True])
+def test_f16_certified_and_worst_case_items_mixed(M, oracle, b, pair):
     """Random digits (certified items) next to a row tile and a column tile
     of constant 183s (items whose certificate fails): every item exact."""
     p = SWEEP[b]
-    m, n, k = 300, 600, 1200
+    m, n, k = 600, 600, 1200
     A, B = inputs.problem(b + 77, m, n, k, p)
     A[:128] = 183
     B[:, :256] = 183
-    C, plan = gpu_product(M, A, B, p, form="int8")
-    assert plan.info["tc_cert_chunk"] == 512
+    C, plan = gpu_product(M, A, B, p, form="int8", tc_pair=pair)
+    assert plan.info["tc_cert_chunk"] == 512 and plan.info["tc_pair"] == pair
     assert np.array_equal(C, oracle.matmul_mod(A, B, p))
 
 
