@@ -783,6 +783,10 @@ def main():
         traffic_per_launch = None if any(x is None for x in tr) else sum(tr) / len(tr)
     else:
         traffic_per_launch = None
+    try:  # SMs, one-CTA kernel CTAs and pair clusters the device holds at once
+        residency = mwmm.mwmm_tc_residency()
+    except mwmm.MwmmError:
+        residency = None
     kernels = sorted({v["int8_kernel"] for v in per_bits.values()})
     roofline = {"bound": "tensor",
                 "kernel": " + ".join(kernels) + " (tcgen05.mma kind::f16; the planner's tile kernel per bitsize: "
@@ -930,6 +934,7 @@ def main():
                 "batched_multi_prime": batched, "shapes_50bit": shapes, "unbalanced_block_wiedemann": unbalanced,
                 "variant_sweep": sweep,
                 "fp64_pipe_peak_gflops": fp64_peak, "fp64_pipe_peak_kind": fp64_peak_kind,
+                "tc_residency": residency,
                 "product_counts_fp64_words": product_counts(n),
                 "serve": serve}
         print(json.dumps(line))

@@ -520,6 +520,15 @@ mwmm_status mwmm_selftest_wait_timeout(int64_t cycles, void *stream);
  * Errors: MWMM_ERR_ARG, MWMM_ERR_CUDA. */
 mwmm_status mwmm_measure_fp64_rate(int64_t iters, double *gflops, void *stream);
 
+/* Residency diagnostic (no counterpart in the paper): on the current device,
+ * *sms = its SM count, *ctas = CTAs of the one-CTA word-product kernel that
+ * can be resident at once (its persistent grid), *pair_clusters = clusters
+ * of two CTAs of the pair kernel (tc_pair) that can be resident at once
+ * (cudaOccupancyMaxActiveClusters: at most sms / 2, fewer where the device's
+ * SMs do not all pair up).  Any pointer may be NULL.  Errors: MWMM_ERR_CUDA
+ * (no device, or a query failed). */
+mwmm_status mwmm_tc_residency(int32_t *sms, int32_t *ctas, int32_t *pair_clusters);
+
 /* ---- per-phase timing (CUDA events on the call's stream) ----
  * When timing is on, every mwmm_matmul / mwmm_matmul_host call records events
  * around its phases: the split of A, the split of B (Alg. 4 or INT8 digits),

@@ -74,3 +74,12 @@ extern "C" mwmm_status mwmm_measure_fp64_rate(int64_t iters, double *gflops, voi
     *gflops = 2.0 * 16.0 * (double)iters * (double)blocks * mwmm::kDiagThreads / (ms * 1e-3) / 1e9;
     return MWMM_OK;
 }
+
+extern "C" mwmm_status mwmm_tc_residency(int32_t *sms, int32_t *ctas, int32_t *pair_clusters) {
+    int s = 0, c = 0, p = 0;
+    if (mwmm::tc_residency(&s, &c, &p) != 0) return MWMM_ERR_CUDA;
+    if (sms) *sms = s;
+    if (ctas) *ctas = c;
+    if (pair_clusters) *pair_clusters = p;
+    return MWMM_OK;
+}

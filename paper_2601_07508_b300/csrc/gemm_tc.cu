@@ -1101,6 +1101,31 @@ int launch_gemm_tc(const Plan &pl, const void *Aw, const void *Bw, int32_t *S, i
 
 int tc_sm_count() { return sm_count(); }
 
+int tc_pairs_fill_device() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        (void)cudaGetLastError();  // no device here: clear the error, answer unknown
+        return -1;
+    }
+    const int clusters = pair_clusters();
+    if (clusters <= 0) return -1;
+    return 2 * clusters >= sm_count() ? 1 : 0;
+}
+
+int tc_residency(int *sms, int *ctas, int *clusters) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return (int)cudaErrorNoDevice;
+    cudaError_t e = set_smem_attr(reinterpret_cast<const void *>(gemm_tc_kernel<false>), kSmemBytes);
+    if (e != cudaSuccess) return (int)e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gemm_tc_kernel<false>, THREADS, kSmemBytes);
+    if (e != cudaSuccess) return (int)e;
+    *sms = sm_count();
+    *ctas = per_sm * *sms;
+    *clusters = pair_clusters();
+    return *clusters > 0 ? 0 : (int)cudaErrorUnknown;
+}
+
 int prepare_tc_attributes() {
     cudaError_t e = set_smem_attr(reinterpret_cast<const void *>(gemm_tc_kernel<false>), kSmemBytes);
     if (e == cudaSuccess) e = set_smem_attr(reinterpret_cast<const void *>(gemm_tc_kernel<true>), kSmemBytes);

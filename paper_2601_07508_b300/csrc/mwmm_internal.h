@@ -181,6 +181,12 @@ void fp64_job(const Plan &pl, const void *Aw, const void *Bw, uint64_t *C, int64
 int launch_gemm_fp64_batched(const void *probs, const int *jobs, int njobs, void *stream);
 int prepare_kernel_attributes();  // dynamic shared-memory limits, once per device (call before capturing)
 int tc_sm_count();
+// SM count, resident CTAs of the one-CTA word-product kernel, co-resident
+// clusters of the pair kernel on the current device (cudaError_t).
+int tc_residency(int *sms, int *ctas, int *clusters);
+// 1 when the pair kernel's co-resident clusters cover every SM of the
+// current device, 0 when they do not, -1 when unknown (no device).
+int tc_pairs_fill_device();
 // Items claimed in table order from the counter at cta_off[2] (cleared by
 // the launch): cta_off = {0, nitems, counter}.
 // cert: some item carries squared-digit maxima (certified chunks)

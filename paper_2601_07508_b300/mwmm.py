@@ -130,6 +130,7 @@ def lib() -> ctypes.CDLL:
     L.mwmm_fmod.argtypes = [_vp, _i64, _u64, _vp, _vp]
     L.mwmm_selftest_wait_timeout.argtypes = [_i64, _vp]
     L.mwmm_measure_fp64_rate.argtypes = [_i64, ctypes.POINTER(ctypes.c_double), _vp]
+    L.mwmm_tc_residency.argtypes = [ctypes.POINTER(ctypes.c_int32)] * 3
     L.mwmm_plan_autotuned.argtypes = [ctypes.POINTER(_vp), _i64, _i64, _i64, _u64, ctypes.c_int, _vp, _i64, _vp,
                                       _i64, _vp]
     L.mwmm_autotune_cache_entries.restype = ctypes.c_int64
@@ -389,6 +390,14 @@ def mwmm_measure_fp64_rate(iters: int = 1 << 16, stream=None) -> float:
     g = ctypes.c_double(0)
     _check(lib().mwmm_measure_fp64_rate(iters, ctypes.byref(g), _stream_ptr(stream)), "mwmm_measure_fp64_rate")
     return g.value
+
+
+def mwmm_tc_residency() -> dict:
+    """SM count, resident CTAs of the one-CTA word-product kernel and
+    co-resident clusters of the pair kernel on the current device."""
+    v = [ctypes.c_int32(0) for _ in range(3)]
+    _check(lib().mwmm_tc_residency(*[ctypes.byref(x) for x in v]), "mwmm_tc_residency")
+    return {"sms": v[0].value, "ctas": v[1].value, "pair_clusters": v[2].value}
 
 
 def mwmm_selftest_wait_timeout(cycles: int, stream=None) -> int:

@@ -878,6 +878,20 @@ def test_int8_pair_and_single_cta_kernels(M, oracle, shape, b):
         assert np.array_equal(C, ref), pair
 
 
+def test_tc_residency_and_pipe_rate_diagnostics(M):
+    """The residency diagnostic: the device's SM count, one resident CTA of
+    the word-product kernel per SM, and between one and sms / 2 pair
+    clusters; the FP64 rate diagnostic returns a positive rate below the
+    nominal 2 flops x 2 DFMA per clock per SM at 2.5 GHz."""
+    import torch
+    r = M.mwmm_tc_residency()
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    assert r["sms"] == sms and r["ctas"] == sms
+    assert 1 <= r["pair_clusters"] <= sms // 2
+    g = M.mwmm_measure_fp64_rate(1 << 12)
+    assert 0 < g < 4 * sms * 2.5
+
+
 # ------------------------------------------------------------------ fused recombination (INT8 form)
 FUSED_SHAPES = [(129, 129, 65), (257, 300, 777), (700, 520, 1100), (513, 385, 64), (300, 1000, 2000)]
 
