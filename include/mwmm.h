@@ -110,8 +110,10 @@ typedef struct {
                          SM pair, cta_group::2), -1 = the one-CTA kernel
                          (128 x 256 tiles), 0 = the planner's choice: two-CTA
                          for 8-bit digits when m >= 1024, 256-row tiles pad
-                         m by at most 3% and there are at least 296 items
-                         (measured on B300: 3-4% faster there), else one-CTA.
+                         m by at most 3%, there are at least 296 items and
+                         (with a device present) the kernel's co-resident
+                         clusters cover every SM (mwmm_tc_residency);
+                         measured on B300: 3-4% faster there; else one-CTA.
                          Results are identical either way; other values:
                          MWMM_ERR_ARG */
     int32_t f64_concat; /* FP64 form, Alg. 6: 0 = automatic (when min(m, n) < 64,
