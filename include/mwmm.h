@@ -109,7 +109,8 @@ typedef struct {
                          1 = the two-CTA tcgen05 kernel (256 x 256 tiles on an
                          SM pair, cta_group::2), -1 = the one-CTA kernel
                          (128 x 256 tiles), 0 = the planner's choice: two-CTA
-                         for 8-bit digits when m >= 1024, 256-row tiles pad
+                         for 8-bit digits and CRT residues when m >= 1024,
+                         256-row tiles pad
                          m by at most 3%, there are at least 296 items and
                          (with a device present) the kernel's co-resident
                          clusters cover every SM (mwmm_tc_residency);

@@ -392,16 +392,18 @@ mwmm_status make_plan(Plan *pl, int64_t m, int64_t n, int64_t k, uint64_t p, int
         if (form == MWMM_FORM_CRT8) P.tc_ndiag = 1;  // each modulus pairs A_i with B_i only: no windows
         // Tile kernel.  The two-CTA kernel (256 x 256 tiles on an SM pair)
         // runs on request (tc_pair = 1), never with tc_pair = -1, and by
-        // default (0) for 8-bit digits on products large enough that 256-row
-        // tiles add at most 3% padding and leave several waves of items, on a
-        // device whose SMs all pair up (when one is present): measured on B300
-        // at 4096^3, 3-4% faster than the one-CTA kernel at 20 to 48 bits.
-        // With 9-bit digits (drains twice as often, each finished on both SMs
-        // before the pair reuses an accumulator) it was level at 52 bits and
-        // 2% slower at 26, so those keep one CTA per tile.
+        // default (0) for 8-bit digits and CRT residues (1024-product chunks)
+        // on products large enough that 256-row tiles add at most 3% padding
+        // and leave several waves of items, on a device whose SMs all pair up
+        // (when one is present): measured on B300 at 4096^3, 3-4% faster than
+        // the one-CTA kernel at 20 to 48 bits and 4% on the CRT form's
+        // products at 32-52 bits.  With 9-bit digits (drains twice as often,
+        // each finished on both SMs before the pair reuses an accumulator) it
+        // was level at 52 bits and 2% slower at 26, so those keep one CTA.
         if (o.tc_pair < -1 || o.tc_pair > 1) return MWMM_ERR_ARG;
         bool pair = o.tc_pair == 1;
-        if (o.tc_pair == 0 && form == MWMM_FORM_INT8 && P.digit_bits == 8 && P.tc_nb == kTcBN && m >= kPairMinM) {
+        const bool chunk1024 = (form == MWMM_FORM_INT8 && P.digit_bits == 8) || form == MWMM_FORM_CRT8;
+        if (o.tc_pair == 0 && chunk1024 && P.tc_nb == kTcBN && m >= kPairMinM) {
             const int64_t rows1 = round_up(m, kTcBM), rows2 = round_up(m, 2 * kTcBM);
             const int64_t items = (rows2 / (2 * kTcBM)) * ceil_div(n, kTcBN) * P.nsums * P.nkc;
             pair = rows2 * 32 <= rows1 * 33 && items >= kPairMinItems && tc_pairs_fill_device() != 0;

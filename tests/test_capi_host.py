@@ -173,12 +173,15 @@ def test_int8_unfused_plan_tile_kernel_choice(M, m, n, pair, want_pair, want_row
     (4000, 4096, 4096, 40, "int8", 1),   # 4096 rows either way
     (900, 8192, 4096, 20, "int8", 0),    # m < 1024
     (4096, 100, 4096, 20, "int8", 0),    # narrow n: diagonal windows, one-CTA kernel
-    (4096, 4096, 4096, 40, "crt8", 0),   # the CRT form keeps one CTA per tile unless asked
+    (4096, 4096, 4096, 40, "crt8", 1),   # CRT residues: 1024-product chunks, as 8-bit digits
+    (4096, 4096, 512, 52, "crt8", 1),
+    (1024, 1024, 4096, 52, "crt8", 0),   # 4 x 4 x 16 = 256 items
 ])
 def test_default_tile_kernel_choice(M, m, n, k, b, form, want):
-    """tc_pair = 0 (None in Python): the two-CTA kernel for 8-bit digits on
-    large products (m >= 1024, at most 3% more padded rows, >= 296 items of
-    256 x 256), else one CTA per tile; True / False force either kernel."""
+    """tc_pair = 0 (None in Python): the two-CTA kernel for 8-bit digits and
+    CRT residues on large products (m >= 1024, at most 3% more padded rows,
+    >= 296 items of 256 x 256), else one CTA per tile; True / False force
+    either kernel."""
     p = SWEEP[b] if b in SWEEP else inputs.largest_prime_below_pow2(b)
     d = M.Plan(m, n, k, p, form=form).info
     assert d["tc_pair"] == want
