@@ -335,6 +335,18 @@ def _chunk_partials(a_dig: np.ndarray, b_dig: np.ndarray) -> np.ndarray:
     return np.concatenate([np.cumsum(prod[i:i + CHUNK // 16]) for i in range(0, prod.size, CHUNK // 16)])
 
 
+def _kernel(fused):
+    """Plan options for the word-product kernel under test: 1 = one CTA per
+    tile, "pair" = CTA pairs (256 x 256 tiles, cta_group::2), 2 = the fused
+    form (256 x 128 tiles on CTA pairs, recombination in the epilogue)."""
+    return dict(tc_fused=2) if fused == 2 else dict(tc_fused=1, tc_pair=(fused == "pair"))
+
+
+def _kernel_ok(plan, fused) -> bool:
+    d = plan.info
+    return d["tc_fused"] == (fused == 2) and d["tc_pair"] == (fused == "pair")
+
+
 def _odd_slices_patterns(pos: int, neg: int, rows: int, cols: int):
     """A (rows x KDIM) and B (KDIM x cols) over {0, pos, neg}: A row r has
     the value at 15 of every 16 k positions (0 at k % 16 == 15), with sign +
@@ -354,7 +366,7 @@ def _odd_slices_patterns(pos: int, neg: int, rows: int, cols: int):
 
 
 @pytest.mark.parametrize("b", [20, 40, 52])
-@pytest.mark.parametrize("fused", [1, 2])
+@pytest.mark.parametrize("fused", [1, "pair", 2])
 def test_int8_fp32_chunk_odd_increments_near_2_24(M, oracle, b, fused):
     """Digits +-127 at 15 of every 16 k positions against B digits +-127: every
     MMA adds +-15 x 16129 (odd), and a chunk's running sum walks up to
@@ -373,8 +385,8 @@ def test_int8_fp32_chunk_odd_increments_near_2_24(M, oracle, b, fused):
             assert np.all(np.diff(part[:CHUNK // 16]) % 2 == 1) and np.all(np.abs(part) <= 2 ** 24)
             peak = max(peak, int(np.abs(part).max()))
     assert peak > 2 ** 23.85
-    C, plan = gpu_product(M, A, B, p, form="int8", tc_fused=fused, tc_digit_bits=8)
-    assert plan.info["tc_fused"] == (fused == 2)
+    C, plan = gpu_product(M, A, B, p, form="int8", **_kernel(fused), tc_digit_bits=8)
+    assert _kernel_ok(plan, fused)
     assert np.array_equal(C, oracle.matmul_mod(A, B, p))
 
 
@@ -400,7 +412,7 @@ def _small_addend_patterns(big_pos, big_neg, one_pos, one_neg, sign):
 
 @pytest.mark.parametrize("b", [20, 52])
 @pytest.mark.parametrize("sign", [1, -1])
-@pytest.mark.parametrize("fused", [1, 2])
+@pytest.mark.parametrize("fused", [1, "pair", 2])
 def test_int8_fp32_chunk_small_addend_below_large_sum(M, oracle, b, sign, fused):
     """A chunk first sums 960 products of +-16129 (reaching +-15,483,840,
     2^23.88), then four MMAs that each add +-1 (one product 1 x 1 in 16): the
@@ -415,13 +427,13 @@ def test_int8_fp32_chunk_small_addend_below_large_sum(M, oracle, b, sign, fused)
     last = part[CHUNK // 16 - 5:CHUNK // 16]
     assert list(np.diff(last)) == [sign] * 4 and abs(int(last[0])) == 960 * 16129
     assert np.all(np.abs(part) <= 2 ** 24) and np.abs(part).max() > 2 ** 23.85
-    C, plan = gpu_product(M, A, B, p, form="int8", tc_fused=fused, tc_digit_bits=8)
-    assert plan.info["tc_fused"] == (fused == 2)
+    C, plan = gpu_product(M, A, B, p, form="int8", **_kernel(fused), tc_digit_bits=8)
+    assert _kernel_ok(plan, fused)
     assert np.array_equal(C, oracle.matmul_mod(A, B, p))
 
 
 @pytest.mark.parametrize("b", [20, 40, 52])
-@pytest.mark.parametrize("fused", [1, 2])
+@pytest.mark.parametrize("fused", [1, "pair", 2])
 def test_int8_fp32_chunk_odd_increments_in_a_two_pair_diagonal(M, oracle, b, fused):
     """Digits 0 and 1 both at +-127 (entries +-(127 + 127 x 256)): diagonal 1
     concatenates the pairs (0,1) and (1,0) along K, so its chunks span both
@@ -432,8 +444,8 @@ def test_int8_fp32_chunk_odd_increments_in_a_two_pair_diagonal(M, oracle, b, fus
     A, B = _odd_slices_patterns(e, p - e, 130, 260)
     Ad = oracle.split_signed8(A, p, u)
     assert np.all(np.abs(Ad[:2]) <= 127) and np.all(Ad[2:] == 0) and int(Ad[1, 64, 0]) == 127
-    C, plan = gpu_product(M, A, B, p, form="int8", tc_fused=fused, tc_digit_bits=8)
-    assert plan.info["tc_fused"] == (fused == 2)
+    C, plan = gpu_product(M, A, B, p, form="int8", **_kernel(fused), tc_digit_bits=8)
+    assert _kernel_ok(plan, fused)
     assert np.array_equal(C, oracle.matmul_mod(A, B, p))
 
 
@@ -449,7 +461,7 @@ def _chunk_partials9(a_dig, b_dig):
 
 @pytest.mark.parametrize("b", [26, 40, 52])
 @pytest.mark.parametrize("da,db", [(-256, -256), (255, 255), (-256, 255)])
-@pytest.mark.parametrize("fused", [1, 2])
+@pytest.mark.parametrize("fused", [1, "pair", 2])
 def test_f16_extreme_digits_fill_the_fp32_chunk(M, oracle, b, da, db, fused):
     """9-bit digits at the ends of [-256, 255]: every product is +-2^16 (or
     -65280, 65025), so a full 256-product chunk reaches |sum| = 2^24."""
@@ -461,13 +473,13 @@ def test_f16_extreme_digits_fill_the_fp32_chunk(M, oracle, b, da, db, fused):
     assert list(Aw) == [da] + [0] * (u - 1) and list(Bw) == [db] + [0] * (u - 1)
     A = np.full((130, KDIM9), a, dtype=np.uint64)
     B = np.full((KDIM9, 260), bb, dtype=np.uint64)
-    C, plan = gpu_product(M, A, B, p, form="int8", tc_digit_bits=9, tc_fused=fused)
-    assert plan.info["tc_chunk"] == CHUNK9 and plan.info["tc_fused"] == (fused == 2)
+    C, plan = gpu_product(M, A, B, p, form="int8", tc_digit_bits=9, **_kernel(fused))
+    assert plan.info["tc_chunk"] == CHUNK9 and _kernel_ok(plan, fused)
     assert np.all(C == (a * bb * KDIM9) % p)
 
 
 @pytest.mark.parametrize("b", [26, 52])
-@pytest.mark.parametrize("fused", [1, 2])
+@pytest.mark.parametrize("fused", [1, "pair", 2])
 def test_f16_fp32_chunk_odd_increments_near_2_24(M, oracle, b, fused):
     """9-bit digits +-255 at 15 of every 16 k positions against B digits
     +-255: every MMA adds +-15 x 65025 (odd), a chunk's running sum walks to
@@ -493,8 +505,8 @@ def test_f16_fp32_chunk_odd_increments_near_2_24(M, oracle, b, fused):
             assert np.all(np.diff(part[:CHUNK9 // 16]) % 2 == 1) and np.all(np.abs(part) <= 2 ** 24)
             peak = max(peak, int(np.abs(part).max()))
     assert peak > 2 ** 23.89
-    C, plan = gpu_product(M, A, B, p, form="int8", tc_digit_bits=9, tc_fused=fused)
-    assert plan.info["tc_chunk"] == CHUNK9
+    C, plan = gpu_product(M, A, B, p, form="int8", tc_digit_bits=9, **_kernel(fused))
+    assert plan.info["tc_chunk"] == CHUNK9 and _kernel_ok(plan, fused)
     assert np.array_equal(C, oracle.matmul_mod(A, B, p))
 
 
@@ -626,7 +638,8 @@ def test_f16_digits_match_oracle_and_8bit_digits(M, oracle, b):
 
 
 @pytest.mark.parametrize("b", [20, 40, 52])
-def test_crt_fp32_chunk_odd_increments_near_2_24(M, oracle, b):
+@pytest.mark.parametrize("pair", [False, True])
+def test_crt_fp32_chunk_odd_increments_near_2_24(M, oracle, b, pair):
     """The CRT form's chunks: entries with residue +-125 modulo 251 (the
     first modulus; 125 and 126 = 251 - 125) at 15 of every 16 k positions,
     so the modulus-251 product adds +-15 x 15625 (odd) per slice and climbs
@@ -641,14 +654,15 @@ def test_crt_fp32_chunk_odd_increments_near_2_24(M, oracle, b):
     part = _chunk_partials(R[0, 64], Rb[0, :, 0])
     assert np.all(np.diff(part[:CHUNK // 16]) % 2 == 1) and np.abs(part).max() > 2 ** 23.8
     assert np.all(np.abs(part) <= 2 ** 24)
-    C, plan = gpu_product(M, A, B, p, form="crt8")
-    assert plan.info["crt_m"][0] == 251 and plan.info["tc_chunk"] == CHUNK
+    C, plan = gpu_product(M, A, B, p, form="crt8", tc_pair=pair)
+    assert plan.info["crt_m"][0] == 251 and plan.info["tc_chunk"] == CHUNK and plan.info["tc_pair"] == pair
     assert np.array_equal(C, oracle.matmul_mod(A, B, p))
 
 
 @pytest.mark.parametrize("b", [20, 52])
 @pytest.mark.parametrize("sign", [1, -1])
-def test_crt_fp32_chunk_small_addend_below_large_sum(M, oracle, b, sign):
+@pytest.mark.parametrize("pair", [False, True])
+def test_crt_fp32_chunk_small_addend_below_large_sum(M, oracle, b, sign, pair):
     """CRT residues modulo 251: 960 products of +-125 x 125 (15,000,000,
     2^23.84), then four MMAs adding +-1 (residues 1 x 1) in the same chunk;
     126 and 250 are the residues -125 and -1."""
@@ -662,7 +676,8 @@ def test_crt_fp32_chunk_small_addend_below_large_sum(M, oracle, b, sign):
     last = part[CHUNK // 16 - 5:CHUNK // 16]
     assert list(np.diff(last)) == [sign] * 4 and abs(int(last[0])) == 960 * 15625
     assert np.all(np.abs(part) <= 2 ** 24)
-    C, _ = gpu_product(M, A, B, p, form="crt8")
+    C, plan = gpu_product(M, A, B, p, form="crt8", tc_pair=pair)
+    assert plan.info["tc_pair"] == pair
     assert np.array_equal(C, oracle.matmul_mod(A, B, p))
 
 
