@@ -93,6 +93,9 @@ struct TcParams {
     // splits ([word][k-block][64-row group]), nullptr: worst-case chunks
     const uint32_t *sqA, *sqB;
     int cert;  // some item may run certified chunks: the planner warp claims (else the producer lane)
+    // computed items: every second run of `wave` claims (one per resident CTA
+    // or CTA pair) walks its k-blocks last to first; 0: all first to last
+    int64_t wave;
 };
 
 // One work item with everything the three roles need (see TcItem).
@@ -106,7 +109,18 @@ struct Item {
     int f16;     // words in fp16, else bf16
     int chunk;   // worst-case FP32 chunk in k-block x pair steps (its digit width's)
     const uint32_t *sqA, *sqB;  // squared-digit maxima for certified chunks, or nullptr
+    int krev;    // k-blocks last to first
 };
+
+// The k-block (from kb0) of an item's kb-th step in its k order.
+__device__ __forceinline__ int64_t item_kb(const Item &it, int64_t kb) { return it.krev ? it.nkbc - 1 - kb : kb; }
+
+// Claims that run while the previous `wave` claims finish walk K the other
+// way, so they start on the k-slabs of the words (the column tiles a raster
+// group shares) that those left in L2 last.
+__device__ __forceinline__ int wave_krev(const TcParams &P, int64_t idx) {
+    return P.wave > 0 ? (int)((idx / P.wave) & 1) : 0;
+}
 
 // MMA N of an item.  Fitting N of a last column tile to its valid columns
 // (rounded up to 16) was measured: it made the 512-instance batch 33% slower
@@ -164,6 +178,7 @@ __device__ __forceinline__ Item computed_item(const TcParams &P, int64_t idx) {
     it.rv = (int)(rv < BM ? rv : BM);
     it.cv = (int)(cv < P.nb ? cv : P.nb);
     it.nn = item_n(it.ndiag, it.nb, it.cv);
+    it.krev = wave_krev(P, idx);
     return it;
 }
 
@@ -197,6 +212,7 @@ __device__ __forceinline__ Item table_item(const TcParams &P, int64_t pos) {
     it.chunk = d.chunk;
     it.sqA = d.sqA;
     it.sqB = d.sqB;
+    it.krev = 0;
     return it;
 }
 
@@ -249,7 +265,7 @@ __device__ __forceinline__ int certified_chunk(const Item &it, int lane) {
         for (int t = 0; t < kCertBlocks; ++t) {
             const int64_t v = w * kCertBlocks + t;
             if (v < nvb) {
-                const int64_t kb = it.kb0 + v / it.ni;
+                const int64_t kb = it.kb0 + item_kb(it, v / it.ni);
                 const int i = it.i0 + (int)(v % it.ni), jw = it.s0 - i;
                 const uint32_t *pa = it.sqA + ((int64_t)i * it.nkb + kb) * ga + kAG * it.mt;
                 const uint32_t *pb = it.sqB + ((int64_t)jw * it.nkb + kb) * gb + 4 * it.nt;
@@ -473,9 +489,10 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_consta
                 const int64_t a_wstep = it.nkb * it.A_rows * kTileBytes;  // next A word, same k-block
                 for (int64_t kb = 0; alive && kb < it.nkbc; ++kb) {
                     const uint8_t *a =
-                        it.Aw + (((int64_t)it.i0 * it.nkb + it.kb0 + kb) * it.A_rows + it.mt * BM) * kTileBytes;
+                        it.Aw + (((int64_t)it.i0 * it.nkb + it.kb0 + item_kb(it, kb)) * it.A_rows + it.mt * BM) *
+                                    kTileBytes;
                     const uint8_t *b = it.Bw + (int64_t)(it.s0 - it.i0 + it.b_wpad) * it.b_wstride +
-                                       (it.kb0 + kb) * it.b_kstride + it.nt * it.nb * kTileBytes;
+                                       (it.kb0 + item_kb(it, kb)) * it.b_kstride + it.nt * it.nb * kTileBytes;
                     for (int ii = 0; ii < it.ni; ++ii, ++g, a += a_wstep, b -= it.b_wstride) {
                         const int slot = (int)(g % STAGES);
                         if (!mbar_wait(&empty[slot], (uint32_t)(((g / STAGES) & 1) ^ 1), P.err)) {
@@ -653,6 +670,7 @@ __device__ __forceinline__ Item pair_item(const TcParams &P, int64_t idx) {
     it.rv = (int)(rv < BM2 ? rv : BM2);
     it.cv = (int)(cv < BN ? cv : BN);
     it.nn = BN;
+    it.krev = wave_krev(P, idx);
     return it;
 }
 
@@ -801,9 +819,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS_PAIR, 1)
                         const int i = it.i0 + ii;
                         const int jw = it.s0 - i;
                         // row coordinates of the tensor maps (the host checks they fit int32)
-                        const int32_t ya = (int32_t)(((int64_t)i * it.nkb + it.kb0 + kb) * it.A_rows + it.mt * BM2 +
+                        const int64_t kbe = it.kb0 + item_kb(it, kb);
+                        const int32_t ya = (int32_t)(((int64_t)i * it.nkb + kbe) * it.A_rows + it.mt * BM2 +
                                                      rank * 128);
-                        const int32_t yb = (int32_t)(((int64_t)jw * it.nkb + it.kb0 + kb) * it.B_rows + it.nt * BN +
+                        const int32_t yb = (int32_t)(((int64_t)jw * it.nkb + kbe) * it.B_rows + it.nt * BN +
                                                      rank * 128);
                         const int slot = (int)(g % P_STAGES);
                         if (!mbar_wait(&empty[slot], (uint32_t)(((g / P_STAGES) & 1) ^ 1), P.err)) {
@@ -1080,6 +1099,7 @@ int launch_gemm_tc(const Plan &pl, const void *Aw, const void *Bw, int32_t *S, i
         const int clusters = pair_clusters();
         if (clusters <= 0) return (int)cudaErrorLaunchOutOfResources;
         const int64_t ncl = P.nitems < clusters ? P.nitems : clusters;
+        P.wave = ncl;
         CUtensorMap tmA, tmB;
         int r = encode_rows_map(&tmA, Aw, (uint64_t)pl.u * pl.nkb * pl.A_rows, 128);
         if (r == 0) r = encode_rows_map(&tmB, Bw, (uint64_t)pl.v * pl.nkb * pl.B_rows, 128);
@@ -1095,6 +1115,7 @@ int launch_gemm_tc(const Plan &pl, const void *Aw, const void *Bw, int32_t *S, i
     e = cudaMemsetAsync(P.sched, 0, sizeof(uint32_t), s);
     if (e != cudaSuccess) return (int)e;
     const unsigned grid = (unsigned)(P.nitems < sms ? P.nitems : sms);
+    P.wave = grid;
     gemm_tc_kernel<false><<<grid, THREADS, kSmemBytes, s>>>(P);
     return (int)cudaGetLastError();
 }
