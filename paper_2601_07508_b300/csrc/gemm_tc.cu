@@ -159,10 +159,12 @@ __device__ __forceinline__ Item computed_item(const TcParams &P, int64_t idx) {
     // ~148 tiles running at once cover about 18 row tiles x 8 column tiles,
     // the aspect that minimises the words they read (a B column tile is twice
     // the bytes of an A row tile), so fewer word tiles are fetched twice.
+    // Odd groups take their rows bottom up, so a group starts on the row
+    // tiles the previous one ended on.
     const int64_t gsz = mtc * kGroupN;
     const int64_t grp = tile / gsz, t = tile % gsz;
     const int64_t width = P.nt_count - grp * kGroupN < kGroupN ? P.nt_count - grp * kGroupN : kGroupN;
-    it.mt = t / width;
+    it.mt = (grp & 1) ? mtc - 1 - t / width : t / width;
     it.nt = grp * kGroupN + t % width;
     it.kb0 = (int64_t)kc * P.kcb;
     const int64_t left = P.nkb - it.kb0;
@@ -654,7 +656,7 @@ __device__ __forceinline__ Item pair_item(const TcParams &P, int64_t idx) {
     const int64_t gsz = mt2 * kGroupN;
     const int64_t grp = tile / gsz, t = tile % gsz;
     const int64_t width = P.nt_count - grp * kGroupN < kGroupN ? P.nt_count - grp * kGroupN : kGroupN;
-    it.mt = t / width;  // 256-row tile index
+    it.mt = (grp & 1) ? mt2 - 1 - t / width : t / width;  // 256-row tile index; odd groups bottom up
     it.nt = grp * kGroupN + t % width;
     it.kb0 = (int64_t)kc * P.kcb;
     const int64_t left = P.nkb - it.kb0;
