@@ -893,6 +893,26 @@ def test_int8_pair_and_single_cta_kernels(M, oracle, shape, b):
         assert np.array_equal(C, ref), pair
 
 
+@pytest.mark.parametrize("form,b", [("int8", 20), ("int8", 40), ("int8", 52), ("crt8", 32), ("crt8", 52)])
+@pytest.mark.parametrize("kc", [0, 320])
+def test_pair_kernel_k_ranges_and_forms(M, oracle, form, b, kc):
+    """The pair kernel on ragged shapes (partial 256-row and 256-column
+    tiles) with the planner's K ranges or explicit ones (kc = 320: 5 k-blocks
+    per range, a last short range), 8-bit digits, 9-bit digits with certified
+    chunks, and CRT residues: equal to the oracle and to the one-CTA kernel."""
+    p = SWEEP[b]
+    m, n, k = 515, 700, 1500
+    A, B = inputs.problem(7000 + b + kc, m, n, k, p)
+    ref = oracle.matmul_mod(A, B, p)
+    kw = dict(kc=kc) if kc else {}
+    C1, plan1 = gpu_product(M, A, B, p, form=form, tc_pair=True, **kw)
+    C0, plan0 = gpu_product(M, A, B, p, form=form, tc_pair=False, **kw)
+    assert plan1.info["tc_pair"] == 1 and plan0.info["tc_pair"] == 0
+    if kc:
+        assert plan1.info["nkc"] == -(-k // kc)  # else the planner's fill model picks the ranges
+    assert np.array_equal(C1, ref) and np.array_equal(C0, ref)
+
+
 def test_tc_residency_and_pipe_rate_diagnostics(M):
     """The residency diagnostic: the device's SM count, one resident CTA of
     the word-product kernel per SM, and between one and sms / 2 pair
