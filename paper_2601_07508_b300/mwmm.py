@@ -220,6 +220,26 @@ def _ld(t) -> int:
     return max(t.stride(0), 1)
 
 
+# The C entry points see a pointer and a leading dimension per matrix, not
+# its extent: a matrix smaller than the plan's product, or one on another
+# device, would be read or written out of bounds by the kernels.  The binding
+# checks both before any call.
+def _shape(t, rows: int, cols: int, what: str):
+    if len(t.shape) != 2 or (int(t.shape[0]), int(t.shape[1])) != (rows, cols):
+        raise ValueError("%s is %s; the product needs %d x %d" % (what, tuple(t.shape), rows, cols))
+
+
+def _one_device(*ts):
+    devs = {t.device for t in ts if t is not None}
+    if len(devs) > 1:
+        raise ValueError("operands on different devices: %s" % sorted(str(d) for d in devs))
+
+
+def _plan_mnk(h: int, info: Optional[dict] = None):
+    d = info if info is not None else mwmm_plan_info(h)
+    return int(d["m"]), int(d["n"]), int(d["k"])
+
+
 # --------------------------------------------------------------------------- C-named calls
 def mwmm_plan(m: int, n: int, k: int, p: int, u: int = 0, v: int = 0, form="auto", lam: int = 0,
               validate: bool = False, tc_chunk: int = 0, kc: int = 0, tc_pair: Optional[bool] = None,
@@ -260,6 +280,11 @@ def mwmm_plan_autotuned(m: int, n: int, k: int, p: int, form="auto", A=None, B=N
     dt = _u64_dtypes()
     a = _dev_ptr(A, dt) if A is not None else None
     b = _dev_ptr(B, dt) if B is not None else None
+    if A is not None:
+        _shape(A, m, k, "A")
+    if B is not None:
+        _shape(B, k, n, "B")
+    _one_device(A, B)
     h = _vp()
     _check(lib().mwmm_plan_autotuned(ctypes.byref(h), m, n, k, p, form, a, _ld(A) if A is not None else 0, b,
                                      _ld(B) if B is not None else 0, _stream_ptr(stream)), "mwmm_plan_autotuned")
@@ -292,9 +317,16 @@ def mwmm_workspace_size(h: int) -> int:
     return int(lib().mwmm_workspace_size(h))
 
 
-def mwmm_matmul(h: int, A, B, C, workspace=None, stream=None):
-    """C = A B mod p on device tensors (int64 or uint64 holding entries < p)."""
+def mwmm_matmul(h: int, A, B, C, workspace=None, stream=None, info: Optional[dict] = None):
+    """C = A B mod p on device tensors (int64 or uint64 holding entries < p).
+    A must be m x k, B k x n and C m x n for the plan's m, n, k, all on one
+    device (ValueError otherwise)."""
     dt = _u64_dtypes()
+    m, n, k = _plan_mnk(h, info)
+    _shape(A, m, k, "A")
+    _shape(B, k, n, "B")
+    _shape(C, m, n, "C")
+    _one_device(A, B, C, workspace)
     ws_ptr, ws_bytes = None, 0
     if workspace is not None:
         ws_ptr, ws_bytes = _dev_ptr(workspace), workspace.numel() * workspace.element_size()
@@ -302,9 +334,13 @@ def mwmm_matmul(h: int, A, B, C, workspace=None, stream=None):
                              ws_ptr, ws_bytes, _stream_ptr(stream)), "mwmm_matmul")
 
 
-def mwmm_matmul_reuse_a(h: int, B, C, workspace=None, stream=None):
+def mwmm_matmul_reuse_a(h: int, B, C, workspace=None, stream=None, info: Optional[dict] = None):
     """C = A B mod p with the A words left in the workspace by the last product."""
     dt = _u64_dtypes()
+    m, n, k = _plan_mnk(h, info)
+    _shape(B, k, n, "B")
+    _shape(C, m, n, "C")
+    _one_device(B, C, workspace)
     ws_ptr, ws_bytes = None, 0
     if workspace is not None:
         ws_ptr, ws_bytes = _dev_ptr(workspace), workspace.numel() * workspace.element_size()
@@ -317,6 +353,10 @@ def mwmm_matmul_host(h: int, A: np.ndarray, B: np.ndarray, C: np.ndarray, stream
     for x in (A, B, C):
         if x.dtype not in (np.uint64, np.int64) or not x.flags["C_CONTIGUOUS"]:
             raise TypeError("host matrices must be C-contiguous uint64/int64")
+    m, n, k = _plan_mnk(h)
+    _shape(A, m, k, "A")
+    _shape(B, k, n, "B")
+    _shape(C, m, n, "C")
     _check(lib().mwmm_matmul_host(h, A.ctypes.data, max(A.shape[1], 1), B.ctypes.data, max(B.shape[1], 1),
                                   C.ctypes.data, max(C.shape[1], 1), _stream_ptr(stream)), "mwmm_matmul_host")
 
@@ -367,6 +407,22 @@ def mwmm_plan_destroy(h: int):
 
 
 def mwmm_split(h: int, side: int, M, words, stream=None):
+    """Words of A (side 0, M is m x k) or of B (side 1, M is k x n) into the
+    byte tensor `words`, which must hold the side's whole word region."""
+    d = mwmm_plan_info(h)
+    m, n, k = _plan_mnk(h, d)
+    if side == 0:
+        _shape(M, m, k, "A")
+        need = d["u"] * d["nkb"] * d["A_rows"] * 128
+    elif side == 1:
+        _shape(M, k, n, "B")
+        need = (d["v"] + 2 * d["B_wpad"]) * d["nkb"] * d["B_rows"] * 128
+    else:
+        raise ValueError("side is 0 (A) or 1 (B)")
+    if words.numel() * words.element_size() < need:
+        raise ValueError("words holds %d bytes; the side's words take %d" % (words.numel() * words.element_size(),
+                                                                            need))
+    _one_device(M, words)
     _check(lib().mwmm_split(h, side, _dev_ptr(M, _u64_dtypes()), _ld(M), _dev_ptr(words), _stream_ptr(stream)),
            "mwmm_split")
 
@@ -427,10 +483,16 @@ def mwmm_version() -> str:
 def _problems(items):
     """items: sequence of (A, B, C, p) device tensors (row-major)."""
     arr = (Problem * len(items))()
+    for i, (A, B, C, p) in enumerate(items):  # every problem checked before any pointer is taken
+        if len(A.shape) != 2 or len(B.shape) != 2:
+            raise ValueError("problem %d: A and B must be 2-D matrices" % i)
+        _shape(B, int(A.shape[1]), int(B.shape[1]), "B of problem %d" % i)
+        _shape(C, int(A.shape[0]), int(B.shape[1]), "C of problem %d" % i)
+        _one_device(A, B, C)
     for i, (A, B, C, p) in enumerate(items):
         dt = _u64_dtypes()
-        arr[i].m, arr[i].k = A.shape
-        arr[i].n = B.shape[1]
+        arr[i].m, arr[i].k = int(A.shape[0]), int(A.shape[1])
+        arr[i].n = int(B.shape[1])
         arr[i].p = p
         arr[i].A, arr[i].lda = _dev_ptr(A, dt), _ld(A)
         arr[i].B, arr[i].ldb = _dev_ptr(B, dt), _ld(B)
@@ -655,7 +717,7 @@ class Plan:
         import torch
         if C is None:
             C = torch.empty((self.info["m"], self.info["n"]), dtype=A.dtype, device=A.device)
-        mwmm_matmul(self.handle, A, B, C, self.alloc_workspace(A.device), stream)
+        mwmm_matmul(self.handle, A, B, C, self.alloc_workspace(A.device), stream, self.info)
         return C
 
     def matmul_reuse_a(self, B, C=None, stream=None):
@@ -663,7 +725,7 @@ class Plan:
         import torch
         if C is None:
             C = torch.empty((self.info["m"], self.info["n"]), dtype=B.dtype, device=B.device)
-        mwmm_matmul_reuse_a(self.handle, B, C, self.alloc_workspace(B.device), stream)
+        mwmm_matmul_reuse_a(self.handle, B, C, self.alloc_workspace(B.device), stream, self.info)
         return C
 
     def matmul_host(self, A: np.ndarray, B: np.ndarray) -> np.ndarray:

@@ -4,6 +4,7 @@ oracle's block sizes and the paper's variant choices."""
 import ctypes
 import os
 
+import numpy as np
 import pytest
 
 from paper_2601_07508_b300 import build, inputs
@@ -453,3 +454,38 @@ def test_noalloc_wrapper_rejects_mismatched_operands_before_any_launch(M):
         M.mwmm_matmul_noalloc(A, torch.zeros(6, dtype=torch.int64), torch.zeros((8, 4), dtype=torch.int64), p)
     with pytest.raises(ValueError, match="CUDA device"):
         M.mwmm_matmul_noalloc(A, torch.zeros((6, 4), dtype=torch.int64), torch.zeros((8, 4), dtype=torch.int64), p)
+
+
+def test_bindings_reject_operands_that_do_not_match_the_product(M):
+    """Every binding that hands matrices to the C ABI passes only pointers and
+    leading dimensions, so it checks the operands' shapes against the plan's
+    m x k, k x n and m x n (and, for device calls, that they share a device)
+    first: a smaller matrix would otherwise be read or written past its end
+    by the kernels.  The checks raise ValueError before any library call."""
+    torch = pytest.importorskip("torch")
+    p = SWEEP[40]
+    plan = M.Plan(8, 4, 6, p, form="int8")
+    z = lambda *s: torch.zeros(s, dtype=torch.int64)  # noqa: E731
+    with pytest.raises(ValueError, match="A is"):
+        M.mwmm_matmul(plan.handle, z(8, 5), z(6, 4), z(8, 4))
+    with pytest.raises(ValueError, match="B is"):
+        plan.matmul(z(8, 6), z(5, 4), z(8, 4))
+    with pytest.raises(ValueError, match="C is"):
+        plan.matmul(z(8, 6), z(6, 4), z(4, 8))
+    with pytest.raises(ValueError, match="C is"):
+        plan.matmul_reuse_a(z(6, 4), z(8, 3))
+    with pytest.raises(ValueError, match="B is"):
+        M.mwmm_matmul_host(plan.handle, np.zeros((8, 6), np.uint64), np.zeros((6, 3), np.uint64),
+                           np.zeros((8, 4), np.uint64))
+    with pytest.raises(ValueError, match="C is"):
+        M.mwmm_matmul_host(plan.handle, np.zeros((8, 6), np.uint64), np.zeros((6, 4), np.uint64),
+                           np.zeros((8, 3), np.uint64))
+    with pytest.raises(ValueError, match="A is"):
+        M.mwmm_split(plan.handle, 0, z(8, 7), torch.zeros(1 << 20, dtype=torch.uint8))
+    with pytest.raises(ValueError, match="words holds"):
+        M.mwmm_split(plan.handle, 1, z(6, 4), torch.zeros(16, dtype=torch.uint8))
+    # batches and the serving loop take each problem's m, k from A and n from B
+    with pytest.raises(ValueError, match="B of problem 1"):
+        M._problems([(z(8, 6), z(6, 4), z(8, 4), p), (z(8, 6), z(7, 4), z(8, 4), p)])
+    with pytest.raises(ValueError, match="C of problem 0"):
+        M._problems([(z(8, 6), z(6, 4), z(8, 5), p)])
