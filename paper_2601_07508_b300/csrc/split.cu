@@ -170,14 +170,10 @@ __device__ __forceinline__ float int8_digit(int64_t t, int w, bool last) {
     const uint32_t half = w < 4 ? (uint32_t)t : (uint32_t)((uint64_t)t >> 32);
     return byte_digit_float(half, w & 3);
 }
-// 9-bit digits the same way: c = 256 (1 + 512 + ... + 512^(u-2)), the lower
-// digits are the 9-bit fields of t minus 256, the top one t >> 9 (u-1)
-// (|digit| <= 256).  Returned as the fp16 pattern 0x6600 + digit: a lower
-// digit's field f gives 0x6600 + f - 256 = 0x6500 + f.
-__device__ __forceinline__ uint32_t int9_digit_biased(int64_t t, int w, bool last) {
-    if (last) return 0x6600u + (uint32_t)(int)(t >> (9 * w));
-    return 0x6500u + (uint32_t)(((uint64_t)t >> (9 * w)) & 511u);
-}
+// 9-bit digits the same way (in split_int8_tile): c = 256 (1 + 512 + ... +
+// 512^(u-2)), the lower digits are the 9-bit fields of t minus 256, the top
+// one t >> 9 (u-1) (|digit| <= 256), each taken as the fp16 pattern
+// 0x6600 + digit: a lower digit's field f gives 0x6600 + f - 256 = 0x6500 + f.
 
 // FP64 form: a 64 x 64 tile covers 4 k-blocks of 16 doubles, 8 granules each.
 __device__ __forceinline__ void split_fp64_tile(const SplitParams &P, uint64_t (*tile)[kST + 1], int64_t by,
@@ -223,47 +219,60 @@ __device__ __forceinline__ void split_int8_tile(const SplitParams &P, uint64_t (
     if (kSq) {
         if (threadIdx.x < kMaxWords) s_sqmax[threadIdx.x] = 0;
     }
+    // Loop invariants read once per tile: in the batched kernels P sits in
+    // shared memory, where every field read inside the loops below would be
+    // a shared-memory load.
+    const int words = P.words, wpad = P.wpad;
+    const bool crt = P.crt != 0, nine = P.bits == 9;
+    const int64_t rows_pad = P.rows_pad;
+    const int64_t wbytes = P.wstride * kTileBytes;  // bytes between consecutive words
+    uint8_t *const out_kb = P.out + kb * P.kstride * kTileBytes;
+    const int64_t pm = (int64_t)P.p, cbias = P.cbias;
     for (int unit = threadIdx.x; unit < kST * 8; unit += 256) {
         const int rr = unit / 8, g = unit % 8;
         const int64_t r = r0 + rr;
-        if (r >= P.rows_pad) continue;  // a last row tile may be partial (rows_pad 16 or 32)
-        // word w of the unit's 8 entries, packed bf16 (or fp16), to its swizzled 16-byte granule
-        auto dst_of = [&](int w) {
-            return reinterpret_cast<uint4 *>(P.out + ((int64_t)(w + P.wpad) * P.wstride + kb * P.kstride + r) *
-                                                         kTileBytes +
-                                             ((g ^ (int)(r & 7)) * 16));
+        if (r >= rows_pad) continue;  // a last row tile may be partial (rows_pad 16 or 32)
+        // the unit's 16-byte granule of word 0 (words follow every wbytes bytes);
+        // each word holds the unit's 8 entries packed bf16 (or fp16)
+        uint8_t *const gran = out_kb + r * kTileBytes + ((g ^ (int)(r & 7)) * 16);
+        uint8_t *dst = gran + wpad * wbytes;
+        auto store = [&](const float (&f)[8]) {
+            *reinterpret_cast<uint4 *>(dst) = make_uint4(pack_bf16x2(f[0], f[1]), pack_bf16x2(f[2], f[3]),
+                                                         pack_bf16x2(f[4], f[5]), pack_bf16x2(f[6], f[7]));
         };
-        auto store = [&](int w, const float (&f)[8]) {
-            *dst_of(w) = make_uint4(pack_bf16x2(f[0], f[1]), pack_bf16x2(f[2], f[3]), pack_bf16x2(f[4], f[5]),
-                                    pack_bf16x2(f[6], f[7]));
-        };
-        if (P.crt) {
+        if (crt) {
             float xl[8][5];  // 11-bit limbs
 #pragma unroll
             for (int e = 0; e < 8; ++e) limbs11(tile[rr][8 * g + e], xl[e]);
-            for (int w = 0; w < P.words; ++w) {
+            for (int w = 0; w < words; ++w, dst += wbytes) {
                 const float m = P.cmf[w], inv = P.cinv[w], c11 = P.c11[w], c22 = P.c22[w], c33 = P.c33[w],
                             c44 = P.c44[w];
                 float f[8];
 #pragma unroll
                 for (int e = 0; e < 8; ++e) f[e] = signed_residue(xl[e], m, inv, c11, c22, c33, c44);
-                store(w, f);
+                store(f);
             }
         } else {
             int64_t t[8];  // signed representative + digit bias
 #pragma unroll
             for (int e = 0; e < 8; ++e) {
-                const uint64_t x = tile[rr][8 * g + e];
-                t[e] = ((x <= half) ? (int64_t)x : (int64_t)x - (int64_t)P.p) + P.cbias;
+                const int64_t x = (int64_t)tile[rr][8 * g + e];
+                t[e] = ((uint64_t)x <= half ? x : x - pm) + cbias;
             }
-            for (int w = 0; w < P.words; ++w) {
-                const bool last = (w == P.words - 1);
-                if (P.bits == 9) {
+            if (nine) {
+                // digits from the bottom up: t >> 9 w kept in t (arithmetic
+                // shift), so each word takes one constant shift per entry
+                for (int w = 0; w < words; ++w, dst += wbytes) {
+                    const bool last = (w == words - 1);
                     uint32_t h[8];
 #pragma unroll
-                    for (int e = 0; e < 8; ++e) h[e] = int9_digit_biased(t[e], w, last);
-                    *dst_of(w) = make_uint4(f16x2_from_biased(h[0], h[1]), f16x2_from_biased(h[2], h[3]),
-                                            f16x2_from_biased(h[4], h[5]), f16x2_from_biased(h[6], h[7]));
+                    for (int e = 0; e < 8; ++e) {
+                        h[e] = last ? 0x6600u + (uint32_t)(int)t[e] : 0x6500u + ((uint32_t)t[e] & 511u);
+                        t[e] >>= 9;
+                    }
+                    *reinterpret_cast<uint4 *>(dst) =
+                        make_uint4(f16x2_from_biased(h[0], h[1]), f16x2_from_biased(h[2], h[3]),
+                                   f16x2_from_biased(h[4], h[5]), f16x2_from_biased(h[6], h[7]));
                     if (kSq) {  // this unit's squared digits (<= 8 x 2^16)
                         uint32_t q = 0;
 #pragma unroll
@@ -273,20 +282,21 @@ __device__ __forceinline__ void split_int8_tile(const SplitParams &P, uint64_t (
                         }
                         s_sq[w * (kST * 8) + unit] = q;
                     }
-                } else {
+                }
+            } else {
+                for (int w = 0; w < words; ++w, dst += wbytes) {
+                    const bool last = (w == words - 1);
                     float f[8];
 #pragma unroll
                     for (int e = 0; e < 8; ++e) f[e] = int8_digit(t[e], w, last);
-                    store(w, f);
+                    store(f);
                 }
             }
         }
-        for (int z = 0; z < P.wpad; ++z) {  // the zero words on both sides
-            const int64_t base = kb * P.kstride + r;
-            const uint4 zero = make_uint4(0, 0, 0, 0);
-            *reinterpret_cast<uint4 *>(P.out + ((int64_t)z * P.wstride + base) * kTileBytes + ((g ^ (int)(r & 7)) * 16)) = zero;
-            *reinterpret_cast<uint4 *>(P.out + ((int64_t)(P.wpad + P.words + z) * P.wstride + base) * kTileBytes +
-                                       ((g ^ (int)(r & 7)) * 16)) = zero;
+        const uint4 zero = make_uint4(0, 0, 0, 0);
+        for (int z = 0; z < wpad; ++z) {  // the zero words on both sides
+            *reinterpret_cast<uint4 *>(gran + z * wbytes) = zero;
+            *reinterpret_cast<uint4 *>(gran + (wpad + words + z) * wbytes) = zero;
         }
     }
     if (kSq) {
@@ -327,9 +337,8 @@ constexpr int kSplitTilesPerCta = 8;
 // kSq: jobs with P.sq set also write their squared-digit maxima (its own
 // kernel, launched when some job of the batch does; held to 3 CTAs per SM,
 // where 4 would spill)
-template <bool kSq>
-__device__ __forceinline__ void split_batched_body(const SplitParams *jobs, const int4 *blocks, int nblocks,
-                                                   int fp64) {
+template <bool kSq, bool kFp64>
+__device__ __forceinline__ void split_batched_body(const SplitParams *jobs, const int4 *blocks, int nblocks) {
     __shared__ uint64_t tile[kST][kST + 1];
     __shared__ __align__(16) SplitParams P;  // the loops read it many times
     const int b0 = blockIdx.x * kSplitTilesPerCta;
@@ -345,7 +354,7 @@ __device__ __forceinline__ void split_batched_body(const SplitParams *jobs, cons
             job = bl.x;
             __syncthreads();
         }
-        if (fp64)
+        if (kFp64)
             split_fp64_tile(P, tile, bl.y, bl.z);
         else if (kSq && P.sq)  // block-uniform: P is in shared memory
             split_int8_tile<kSq>(P, tile, bl.y, bl.z);
@@ -354,14 +363,17 @@ __device__ __forceinline__ void split_batched_body(const SplitParams *jobs, cons
     }
 }
 
+// One kernel per job kind, so that each carries only its own path's registers:
+// FP64 words, INT8 digits / CRT residues, and the same with squared-digit maxima.
+template <bool kFp64>
 __global__ void __launch_bounds__(256, 4) split_batched_kernel(const SplitParams *jobs, const int4 *blocks,
-                                                            int nblocks, int fp64) {
-    split_batched_body<false>(jobs, blocks, nblocks, fp64);
+                                                            int nblocks) {
+    split_batched_body<false, kFp64>(jobs, blocks, nblocks);
 }
 
 __global__ void __launch_bounds__(256, 3) split_batched_sq_kernel(const SplitParams *jobs, const int4 *blocks,
-                                                               int nblocks, int fp64) {
-    split_batched_body<true>(jobs, blocks, nblocks, fp64);
+                                                               int nblocks) {
+    split_batched_body<true, false>(jobs, blocks, nblocks);
 }
 
 SplitParams make_split_params(const Plan &pl, int side, const uint64_t *M, int64_t ld, void *words) {
@@ -430,12 +442,14 @@ int launch_split_batched(const void *jobs, const int *blocks, int nblocks, int f
     if (nblocks == 0) return 0;
     const int ctas = (nblocks + kSplitTilesPerCta - 1) / kSplitTilesPerCta;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    if (sq && !fp64)
-        split_batched_sq_kernel<<<ctas, 256, 0, s>>>(static_cast<const SplitParams *>(jobs),
-                                                      reinterpret_cast<const int4 *>(blocks), nblocks, fp64);
+    const SplitParams *J = static_cast<const SplitParams *>(jobs);
+    const int4 *blk = reinterpret_cast<const int4 *>(blocks);
+    if (fp64)
+        split_batched_kernel<true><<<ctas, 256, 0, s>>>(J, blk, nblocks);
+    else if (sq)
+        split_batched_sq_kernel<<<ctas, 256, 0, s>>>(J, blk, nblocks);
     else
-        split_batched_kernel<<<ctas, 256, 0, s>>>(static_cast<const SplitParams *>(jobs),
-                                                   reinterpret_cast<const int4 *>(blocks), nblocks, fp64);
+        split_batched_kernel<false><<<ctas, 256, 0, s>>>(J, blk, nblocks);
     return (int)cudaGetLastError();
 }
 

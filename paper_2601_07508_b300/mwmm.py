@@ -224,8 +224,12 @@ def _ld(t) -> int:
 # its extent: a matrix smaller than the plan's product, or one on another
 # device, would be read or written out of bounds by the kernels.  The binding
 # checks both before any call.
-def _shape(t, rows: int, cols: int, what: str):
-    if len(t.shape) != 2 or (int(t.shape[0]), int(t.shape[1])) != (rows, cols):
+def _shape(t, rows: int, cols: int, what: str, k: int = -1):
+    """rows x cols exactly; where the extent is the product's k and k = 0
+    (an empty sum: nothing is read), any extent."""
+    ok = len(t.shape) == 2 and all(int(t.shape[i]) == want or (k == 0 and want == 0)
+                                   for i, want in enumerate((rows, cols)))
+    if not ok:
         raise ValueError("%s is %s; the product needs %d x %d" % (what, tuple(t.shape), rows, cols))
 
 
@@ -281,9 +285,9 @@ def mwmm_plan_autotuned(m: int, n: int, k: int, p: int, form="auto", A=None, B=N
     a = _dev_ptr(A, dt) if A is not None else None
     b = _dev_ptr(B, dt) if B is not None else None
     if A is not None:
-        _shape(A, m, k, "A")
+        _shape(A, m, k, "A", k)
     if B is not None:
-        _shape(B, k, n, "B")
+        _shape(B, k, n, "B", k)
     _one_device(A, B)
     h = _vp()
     _check(lib().mwmm_plan_autotuned(ctypes.byref(h), m, n, k, p, form, a, _ld(A) if A is not None else 0, b,
@@ -323,8 +327,8 @@ def mwmm_matmul(h: int, A, B, C, workspace=None, stream=None, info: Optional[dic
     device (ValueError otherwise)."""
     dt = _u64_dtypes()
     m, n, k = _plan_mnk(h, info)
-    _shape(A, m, k, "A")
-    _shape(B, k, n, "B")
+    _shape(A, m, k, "A", k)
+    _shape(B, k, n, "B", k)
     _shape(C, m, n, "C")
     _one_device(A, B, C, workspace)
     ws_ptr, ws_bytes = None, 0
@@ -338,7 +342,7 @@ def mwmm_matmul_reuse_a(h: int, B, C, workspace=None, stream=None, info: Optiona
     """C = A B mod p with the A words left in the workspace by the last product."""
     dt = _u64_dtypes()
     m, n, k = _plan_mnk(h, info)
-    _shape(B, k, n, "B")
+    _shape(B, k, n, "B", k)
     _shape(C, m, n, "C")
     _one_device(B, C, workspace)
     ws_ptr, ws_bytes = None, 0
@@ -354,8 +358,8 @@ def mwmm_matmul_host(h: int, A: np.ndarray, B: np.ndarray, C: np.ndarray, stream
         if x.dtype not in (np.uint64, np.int64) or not x.flags["C_CONTIGUOUS"]:
             raise TypeError("host matrices must be C-contiguous uint64/int64")
     m, n, k = _plan_mnk(h)
-    _shape(A, m, k, "A")
-    _shape(B, k, n, "B")
+    _shape(A, m, k, "A", k)
+    _shape(B, k, n, "B", k)
     _shape(C, m, n, "C")
     _check(lib().mwmm_matmul_host(h, A.ctypes.data, max(A.shape[1], 1), B.ctypes.data, max(B.shape[1], 1),
                                   C.ctypes.data, max(C.shape[1], 1), _stream_ptr(stream)), "mwmm_matmul_host")
@@ -412,10 +416,10 @@ def mwmm_split(h: int, side: int, M, words, stream=None):
     d = mwmm_plan_info(h)
     m, n, k = _plan_mnk(h, d)
     if side == 0:
-        _shape(M, m, k, "A")
+        _shape(M, m, k, "A", k)
         need = d["u"] * d["nkb"] * d["A_rows"] * 128
     elif side == 1:
-        _shape(M, k, n, "B")
+        _shape(M, k, n, "B", k)
         need = (d["v"] + 2 * d["B_wpad"]) * d["nkb"] * d["B_rows"] * 128
     else:
         raise ValueError("side is 0 (A) or 1 (B)")
