@@ -122,11 +122,11 @@ __device__ __forceinline__ int wave_krev(const TcParams &P, int64_t idx) {
     return P.wave > 0 ? (int)((idx / P.wave) & 1) : 0;
 }
 
-// MMA N of an item.  Fitting N of a last column tile to its valid columns
-// (rounded up to 16) was measured: it made the 512-instance batch 33% slower
-// on B300, so every tile runs its full width.
+// MMA N of an item: a single-diagonal tile runs only its valid columns,
+// rounded up to 16 (the MMA's N step for M = 128), so the last column tile
+// of a ragged product copies and multiplies no more B rows than it needs.
 __device__ __forceinline__ int item_n(int ndiag, int nb, int cv) {
-    (void)cv;
+    if (ndiag == 1 && cv < nb) return cv < 16 ? 16 : (cv + 15) & ~15;
     return ndiag * nb;
 }
 
