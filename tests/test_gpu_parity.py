@@ -1169,3 +1169,31 @@ def test_plans_on_host_threads_launching_together_in_a_fresh_process(M, oracle, 
         p = inputs.largest_prime_below_pow2(b)
         A, B = inputs.problem(7800 + i, m, n, k, p)
         assert np.array_equal(np.load(tmp_path / ("c%d.npy" % i)), oracle.matmul_mod(A, B, p)), i
+
+
+@pytest.mark.parametrize("form,b,pair", [("int8", 20, False), ("int8", 52, False), ("crt8", 40, False),
+                                         ("int8", 20, True)])
+def test_ragged_last_column_tile_widths(M, oracle, form, b, pair):
+    """The one-CTA kernel runs a last column tile of c < 256 valid columns
+    at N = c rounded up to 16 (MMA width and B rows copied), alone and as a
+    batch's table item; c on both sides of each multiple of 16.  The pair
+    kernel keeps full 256-wide tiles; it runs the same shapes."""
+    p = SWEEP[b]
+    m, k = 150, 200
+    items, refs = [], []
+    for i, c in enumerate((1, 15, 16, 17, 112, 127, 129, 241, 255)):
+        n = 256 + c
+        A, B = inputs.problem(1700 + 10 * b + i, m, n, k, p)
+        ref = oracle.matmul_mod(A, B, p)
+        C, plan = gpu_product(M, A, B, p, form=form, tc_pair=pair)
+        assert plan.info["tc_pair"] == (1 if pair else 0)
+        assert np.array_equal(C, ref), (form, b, n)
+        if not pair:
+            items.append((dev(A), dev(B), torch.full((m, n), -1, dtype=torch.int64, device="cuda"), p))
+            refs.append(ref)
+    if items:
+        bt = M.Batch(items, form=form)
+        bt.run()
+        assert bt.check() == 0
+        for (_, _, C, _), ref in zip(items, refs):
+            assert np.array_equal(host(C), ref), (form, b, C.shape)
