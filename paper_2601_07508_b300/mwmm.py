@@ -234,9 +234,16 @@ def _shape(t, rows: int, cols: int, what: str, k: int = -1):
 
 
 def _one_device(*ts):
+    """One device for all operands, and for CUDA tensors the current one (the
+    kernels run on the current device)."""
     devs = {t.device for t in ts if t is not None}
     if len(devs) > 1:
         raise ValueError("operands on different devices: %s" % sorted(str(d) for d in devs))
+    d = next(iter(devs), None)
+    if d is not None and d.type == "cuda":
+        import torch
+        if d.index is not None and d.index != torch.cuda.current_device():
+            raise ValueError("operands on %s while cuda:%d is current" % (d, torch.cuda.current_device()))
 
 
 def _plan_mnk(h: int, info: Optional[dict] = None):
