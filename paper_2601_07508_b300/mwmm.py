@@ -6,7 +6,10 @@ PyTorch supplies device memory and streams.  If the library has not been
 built, or cannot be loaded, every call raises: there is no CPU fallback.
 
 The functions carry the C names (mwmm_plan, mwmm_matmul, ...); ``Plan`` is a
-small owner object around a plan handle.
+small owner object around a plan handle.  Before any call that hands
+matrices to the library, the binding checks their shapes against the
+product and that they share the current device (ValueError otherwise): the
+C entry points receive pointers and leading dimensions only.
 """
 from __future__ import annotations
 
