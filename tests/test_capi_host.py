@@ -489,3 +489,24 @@ def test_bindings_reject_operands_that_do_not_match_the_product(M):
         M._problems([(z(8, 6), z(6, 4), z(8, 4), p), (z(8, 6), z(7, 4), z(8, 4), p)])
     with pytest.raises(ValueError, match="C of problem 0"):
         M._problems([(z(8, 6), z(6, 4), z(8, 5), p)])
+
+
+def test_binding_shape_check_edge_cases(M):
+    """Empty products: a plan with k = 0 reads no A or B entries, so their k
+    extent is free (a 1-column stand-in is accepted); C must still be m x n.
+    m = 0 or n = 0 needs exactly empty operands on that side."""
+    torch = pytest.importorskip("torch")
+    z = lambda *s: torch.zeros(s, dtype=torch.int64)  # noqa: E731
+    M._shape(z(7, 1), 7, 0, "A", 0)
+    M._shape(z(1, 9), 0, 9, "B", 0)
+    M._shape(z(7, 0), 7, 0, "A", 0)
+    with pytest.raises(ValueError, match="C is"):
+        M._shape(z(7, 1), 7, 0, "C")  # the k = 0 freedom is for A and B only
+    with pytest.raises(ValueError, match="A is"):
+        M._shape(z(6, 1), 7, 0, "A", 0)  # rows still count
+    M._shape(z(0, 5), 0, 5, "A", 5)
+    with pytest.raises(ValueError, match="A is"):
+        M._shape(z(1, 5), 0, 5, "A", 5)
+    with pytest.raises(ValueError, match="B is"):
+        M._shape(z(5), 5, 1, "B", 5)  # not a matrix
+    M._one_device(z(2, 2), None, z(2, 2))  # CPU tensors: one device, no current-device rule
